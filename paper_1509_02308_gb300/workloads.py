@@ -1,0 +1,191 @@
+"""Seeded synthetic inputs: cache geometries and P-chase run descriptors.
+
+This module only draws descriptors (which geometry, which array size, stride
+and length); it holds none of the method's arithmetic: no trace is walked and
+no cache is simulated here.  Both the CUDA path and the CPU oracle take their
+inputs from it.  It imports numpy only.
+
+Random draws use SplitMix64 streams (Steele, Lea & Flood, OOPSLA 2014): the
+stream seeded with x yields mix(x + k*gamma) for k = 1, 2, ...
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+LRU, FIFO, RANDOM = 0, 1, 2
+POLICY_NAMES = ("LRU", "FIFO", "RANDOM")
+_M64 = 0xFFFFFFFFFFFFFFFF
+_GAMMA = 0x9E3779B97F4A7C15
+
+
+class SplitMix64:
+    """SplitMix64 stream (published definition), for drawing inputs only."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _M64
+
+    def next(self) -> int:
+        self.state = (self.state + _GAMMA) & _M64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        return z ^ (z >> 31)
+
+    def below(self, n: int) -> int:
+        """Integer in [0, n) from the high 32 bits (multiply-shift)."""
+        return ((self.next() >> 32) * n) >> 32
+
+    def unit(self) -> float:
+        """Float in [0, 1) from the high 53 bits."""
+        return (self.next() >> 11) * (1.0 / 9007199254740992.0)
+
+
+@dataclass(frozen=True)
+class Geom:
+    """Cache geometry: capacity C and line size b in bytes, ways a, sets T."""
+    C: int
+    b: int
+    ways: int
+    sets: int
+    policy: int = LRU
+    seed: int = 0
+
+    def row(self):
+        return (self.C, self.b, self.ways, self.sets, self.policy)
+
+
+@dataclass(frozen=True)
+class Run:
+    """One P-chase run: array of n_elems 4-byte elements, stride in elements,
+    `length` accesses of which the first `warmup` form the warm-up pass.
+    `chain` (optional) is a caller-built next-index array that replaces the
+    uniform stride (a non-uniform chain in the style of Fig. 10)."""
+    n_elems: int
+    stride: int
+    length: int
+    warmup: int
+    chain: np.ndarray | None = None
+
+
+# ----------------------------------------------------------------- geometries
+CAPACITIES = sorted([1 << k for k in range(10, 19)] + [3 << k for k in range(9, 17)])
+LINE_SIZES = (32, 64, 128, 256)
+WAY_CHOICES = (1, 2, 4, 8, 16, 32, 0)  # 0 = fully associative (ways = C / b)
+
+
+def geometry_grid(capacities=CAPACITIES, line_sizes=LINE_SIZES, way_choices=WAY_CHOICES):
+    """Every (C, b, ways, T) with ways * b dividing C, without duplicates.
+
+    Capacities {2^k, 3*2^k} in [1 KB, 256 KB], b in {32..256} B, ways in
+    {1..32, full}."""
+    out = []
+    seen = set()
+    for C in capacities:
+        for b in line_sizes:
+            if C % b:
+                continue
+            lines = C // b
+            for w in way_choices:
+                a = lines if w == 0 else w
+                if a > lines or lines % a:
+                    continue
+                key = (C, b, a)
+                if key in seen:
+                    continue
+                seen.add(key)
+                out.append((C, b, a, lines // a))
+    return out
+
+
+# ------------------------------------------------------------------- config 1
+def config1():
+    """One LRU cache (16 KB, 128 B lines, 4 ways, 32 sets); arrays of 12 KB to
+    24 KB in 128 B steps, stride 128 B, one warm-up pass plus two passes."""
+    g = Geom(16384, 128, 4, 32, LRU, 0)
+    runs = []
+    for nbytes in range(12288, 24576 + 1, 128):
+        n = nbytes // 4
+        s = 128 // 4
+        per_pass = n // s
+        runs.append(Run(n, s, 3 * per_pass, per_pass))
+    return g, runs
+
+
+# ------------------------------------------------------------------- config 2
+def config2(n_items: int = 4096, seed_base: int = 0x5EED0002,
+            min_len: int = 1024, max_len: int = 1 << 20):
+    """Batched-simulation workload: item i is one geometry and one uniform run.
+
+    Stream i (seed seed_base + i) draws, in order: a geometry uniformly from
+    geometry_grid(); a policy from {LRU, FIFO, RANDOM}; a policy seed; a stride
+    of 4 * 2^u bytes, u uniform on {0..10}; v uniform on [-1, 1) giving the
+    array size round_down(C * 2^v, stride) (at least one stride); and a length
+    L = floor(min_len * (max_len / min_len)^x), x uniform on [0, 1).  The
+    warm-up is the first pass (array size / stride accesses, at most L)."""
+    grid = geometry_grid()
+    geoms, runs = [], []
+    for i in range(n_items):
+        r = SplitMix64(seed_base + i)
+        C, b, a, T = grid[r.below(len(grid))]
+        policy = r.below(3)
+        pseed = r.next()
+        sbytes = 4 << r.below(11)
+        v = 2.0 * r.unit() - 1.0
+        nbytes = int(C * (2.0 ** v)) // sbytes * sbytes
+        nbytes = max(nbytes, sbytes)
+        L = int(min_len * (max_len / min_len) ** r.unit())
+        L = max(min_len, min(L, max_len))
+        n, s = nbytes // 4, sbytes // 4
+        per_pass = n // s
+        geoms.append(Geom(C, b, a, T, policy, pseed))
+        runs.append(Run(n, s, L, min(per_pass, L)))
+    return geoms, runs
+
+
+def random_small_geoms(n: int, seed: int, max_lines: int = 64,
+                       line_sizes=(4, 8, 16, 32, 64), policies=(LRU, FIFO, RANDOM)):
+    """Small geometries with arbitrary T (including T not a power of two)."""
+    r = SplitMix64(seed)
+    out = []
+    while len(out) < n:
+        b = line_sizes[r.below(len(line_sizes))]
+        lines = 1 + r.below(max_lines)
+        divs = [d for d in range(1, lines + 1) if lines % d == 0]
+        a = divs[r.below(len(divs))]
+        T = lines // a
+        out.append(Geom(lines * b, b, a, T, policies[r.below(len(policies))], r.next()))
+    return out
+
+
+def random_index_trace(n: int, n_elems: int, seed: int, hot: int = 0) -> np.ndarray:
+    """A general (non-chain) index trace: uniform indices below n_elems, with
+    an optional fraction hot/16 of accesses drawn from the first 64 elements."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = rng.integers(0, n_elems, size=n, dtype=np.uint64).astype(np.uint32)
+    if hot:
+        m = rng.integers(0, 16, size=n) < hot
+        t[m] = rng.integers(0, min(64, n_elems), size=int(m.sum()), dtype=np.uint64).astype(np.uint32)
+    return t
+
+
+def total_accesses(runs) -> int:
+    return int(sum(r.length for r in runs))
+
+
+def describe_config2(geoms, runs) -> dict:
+    L = np.array([r.length for r in runs], dtype=np.float64)
+    return {
+        "items": len(runs),
+        "accesses": int(L.sum()),
+        "mean_len": float(L.mean()),
+        "max_len": int(L.max()),
+        "policies": [int(sum(g.policy == p for g in geoms)) for p in range(3)],
+        "fully_assoc": int(sum(g.sets == 1 for g in geoms)),
+    }
+
+
+def log2i(x: int) -> int:
+    return int(math.log2(x))

@@ -1,0 +1,376 @@
+"""Pins for the CPU oracle: the paper's worked examples, closed forms,
+special cases and brute force.  None of these calls a GPU."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import golden
+from paper_1509_02308_gb300 import workloads as W
+
+
+def steady_misses_per_pass(C, b, a, T, n_elems, s_elems, passes=3, policy=oracle.LRU):
+    per = n_elems // math.gcd(n_elems, s_elems)
+    tr = oracle.pchase_trace(n_elems, s_elems, per * passes)
+    m = oracle.cache_sim(C, b, a, T, policy, tr)
+    return [int(m[p * per:(p + 1) * per].sum()) for p in range(passes)], m, per
+
+
+# ------------------------------------------------------------------ chain walk
+def test_listing1_chain_closed_form():
+    # Listing 1 walked from j = 0 visits (t * s) mod N.
+    for n, s in [(13, 1), (100, 7), (4096, 32), (96, 64), (1, 1), (5, 5)]:
+        tr = oracle.pchase_trace(n, s, 3 * n + 1)
+        t = np.arange(tr.size, dtype=np.uint64)
+        assert np.array_equal(tr.astype(np.uint64), (t * s) % n)
+
+
+def test_walk_rejects_chain_outside_array():
+    A = np.array([1, 2, 7], dtype=np.uint32)
+    with pytest.raises(oracle.OracleError):
+        oracle.pchase_walk(A, 10)
+
+
+# ------------------------------------------------------------------- Fig. 3
+def test_fig3_periodic_pattern():
+    g = golden("fig3_periodic.json")
+    c = g["cache"]
+    wb = c["word_bytes"]
+    C, b = c["words"] * wb, c["line_words"] * wb
+    n = g["array_words"]
+    tr = oracle.pchase_trace(n, g["stride_words"], n * 6)
+    m = oracle.cache_sim(C, b, c["ways"], c["sets"], oracle.LRU, tr)
+    want = np.zeros(n, dtype=np.uint8)
+    want[np.array(g["steady_pass_misses_1based_words"]) - 1] = 1
+    for p in range(1, 6):
+        assert np.array_equal(m[p * n:(p + 1) * n], want), p
+    # the pattern repeats with period 13 = the array length
+    assert np.array_equal(m[n:2 * n], m[4 * n:5 * n])
+
+
+# ------------------------------------------------------------------- Fig. 9
+def _fig9_trace(g):
+    line_elems = 128 // 4
+    lines = g["initial_ways"] + g["reads"]
+    return np.array([x * line_elems for x in lines], dtype=np.uint32)
+
+
+def test_fig9_transcript_replay():
+    g = golden("fig9_transcript.json")
+    tr = _fig9_trace(g)
+    victims = np.array(g["replaced_way_per_miss_1based"], dtype=np.uint32) - 1
+    m, fin = oracle.cache_sim(4 * 128, 128, 4, 1, oracle.REPLAY, tr, victims=victims,
+                              want_final=True)
+    k = len(g["initial_ways"])
+    assert m[:k].tolist() == [1] * k  # the four fills
+    got = "".join("M" if x else "H" for x in m[k:])
+    assert got == g["status"]
+    assert [int(x) // 1 for x in fin] == g["final_ways"]
+
+
+def test_fig9_under_lru_everything_misses():
+    g = golden("fig9_transcript.json")
+    tr = _fig9_trace(g)
+    m = oracle.cache_sim(4 * 128, 128, 4, 1, oracle.LRU, tr)
+    assert m[len(g["initial_ways"]):].all()
+
+
+def test_replay_runs_out_of_victims():
+    g = golden("fig9_transcript.json")
+    with pytest.raises(oracle.OracleError):
+        oracle.cache_sim(512, 128, 4, 1, oracle.REPLAY, _fig9_trace(g),
+                         victims=np.array([1], dtype=np.uint32))
+
+
+# ------------------------------------------------------ Eq. (2), config 1
+def test_eq2_exact_over_config1():
+    g = golden("closed_forms.json")["config1"]
+    C, b, a, T = g["C"], g["b"], g["ways"], g["sets"]
+    tot_acc = tot_miss = 0
+    geo, runs = W.config1()
+    assert len(runs) == g["traces"]
+    for run in runs:
+        nb = run.n_elems * 4
+        k = (nb - C) // b
+        per, m, pp = steady_misses_per_pass(C, b, a, T, run.n_elems, run.stride, passes=3)
+        lines = nb // b
+        assert per[0] == lines  # the warm-up pass misses every line once
+        want = 0 if k <= 0 else (k * (a + 1) if k <= T else lines)
+        assert per[1] == want and per[2] == want, (nb, per)
+        tot_acc += m.size
+        tot_miss += int(m.sum())
+    assert tot_acc == g["accesses"]
+    assert tot_miss == g["misses"]
+
+
+def test_step2_line_size_jump():
+    g = golden("closed_forms.json")["step2"]
+    C, b, a, T = g["C"], g["b"], g["ways"], g["sets"]
+    s = g["stride_bytes"] // 4
+    for nb_str, want in g["misses_per_pass"].items():
+        per, _, _ = steady_misses_per_pass(C, b, a, T, int(nb_str) // 4, s)
+        assert per[1] == want and per[2] == want, (nb_str, per)
+    # step 1: C is the largest N at which every access after warm-up hits
+    for nb in (C - 4, C):
+        per, _, _ = steady_misses_per_pass(C, b, a, T, nb // 4, s)
+        assert per[1] == 0 and per[2] == 0
+
+
+def test_eq1_saavedra_rates():
+    C, b, a, T = 1024, 64, 2, 8
+    n_bytes = 64 * 1024
+    for s_bytes in (4, 8, 16, 32):
+        per, _, pp = steady_misses_per_pass(C, b, a, T, n_bytes // 4, s_bytes // 4)
+        assert per[2] * b == pp * s_bytes  # rate s / b
+    for s_bytes in (64, 128, 1024, 8192, 16384):  # b <= s < N / a
+        per, _, pp = steady_misses_per_pass(C, b, a, T, n_bytes // 4, s_bytes // 4)
+        assert per[2] == pp
+    per, _, pp = steady_misses_per_pass(C, b, a, T, n_bytes // 4, n_bytes // a // 4)
+    assert per[2] == 0  # s = N / a: the a visited lines share one set and fit
+
+
+def test_texture_l1_sweep_fig5_shape():
+    # Sec. 4.3: 12 KB, 32 B lines, 4 sets of 96 lines; s = 32 B, N = 12 KB..12.5 KB.
+    t4 = golden("table4_geometries.json")["caches"][1]
+    C, b, T = t4["C"], t4["b"], t4["T"]
+    a = C // (T * b)
+    assert a == 96
+    prev = None
+    for k in range(0, 17):
+        nb = C + k * b
+        per, _, _ = steady_misses_per_pass(C, b, a, T, nb // 4, b // 4)
+        want = 0 if k == 0 else (k * (a + 1) if k <= T else nb // b)
+        assert per[2] == want
+        if prev is not None:
+            assert per[2] >= prev
+        prev = per[2]
+
+
+# --------------------------------------------------------------- invariants
+def test_all_hits_after_warmup_when_array_fits():
+    for g in W.random_small_geoms(40, seed=11, max_lines=32):
+        for s in (1, 2, 3):
+            n = g.C // 4  # N = C elements' worth of bytes
+            tr = oracle.pchase_trace(n, s, 4 * n)
+            m = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed)
+            per = n // math.gcd(n, s)
+            assert m[per:].sum() == 0, g
+
+
+def test_lru_equals_fifo_on_uniform_chains():
+    for g in W.random_small_geoms(60, seed=5, max_lines=48, policies=(W.LRU,)):
+        for nmul, s in ((1.5, 1), (2.0, 3), (1.25, 2), (3.0, 5)):
+            n = max(1, int(g.C // 4 * nmul))
+            tr = oracle.pchase_trace(n, s, 3 * n)
+            a = oracle.cache_sim(g.C, g.b, g.ways, g.sets, oracle.LRU, tr)
+            f = oracle.cache_sim(g.C, g.b, g.ways, g.sets, oracle.FIFO, tr)
+            assert np.array_equal(a, f)
+
+
+def test_lru_differs_from_fifo_on_retouch_chain():
+    # a hot line re-read between streaming lines stays under LRU, leaves under FIFO
+    b = 16
+    C, a, T = 4 * b, 4, 1
+    hot = 0
+    stream = [(i + 1) * (b // 4) for i in range(8)]
+    tr = []
+    for p in range(4):
+        for x in stream:
+            tr += [hot, x]
+    tr = np.array(tr, dtype=np.uint32)
+    ml = oracle.cache_sim(C, b, a, T, oracle.LRU, tr)
+    mf = oracle.cache_sim(C, b, a, T, oracle.FIFO, tr)
+    assert ml[2::2].sum() == 0  # hot re-reads always hit under LRU
+    assert mf[2::2].sum() > 0
+
+
+def test_direct_mapped_policies_agree():
+    for g in W.random_small_geoms(30, seed=9, max_lines=16):
+        lines = g.C // g.b
+        tr = W.random_index_trace(300, lines * g.b // 4 * 3, seed=g.seed % 1000)
+        outs = [oracle.cache_sim(g.C, g.b, 1, lines, p, tr, seed=123) for p in range(3)]
+        assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+# ------------------------------------------------------ brute force vs lists
+def _list_model(C, b, a, T, policy, seed, trace):
+    """Sets as Python lists: LRU keeps recency order, FIFO insertion order,
+    RANDOM explicit way slots.  Written independently of the oracle's
+    stamp-based bookkeeping."""
+    sets = [[] for _ in range(T)]
+    slots = [[None] * a for _ in range(T)]
+    ev = [0] * T
+    out = []
+    for idx in trace:
+        line = (4 * int(idx)) // b
+        s = line % T
+        if policy == oracle.RANDOM:
+            if line in slots[s]:
+                out.append(0)
+                continue
+            out.append(1)
+            if None in slots[s]:
+                slots[s][slots[s].index(None)] = line
+            else:
+                slots[s][oracle.random_victim(seed, s, ev[s], a)] = line
+                ev[s] += 1
+            continue
+        lst = sets[s]
+        if line in lst:
+            out.append(0)
+            if policy == oracle.LRU:
+                lst.remove(line)
+                lst.append(line)
+            continue
+        out.append(1)
+        if len(lst) == a:
+            lst.pop(0)
+        lst.append(line)
+    return np.array(out, dtype=np.uint8)
+
+
+def test_bruteforce_tiny_caches_random_traces():
+    rng = np.random.Generator(np.random.PCG64(2024))
+    n_checked = 0
+    for b in (4, 8, 16):
+        for lines in range(1, 9):
+            for a in [d for d in range(1, lines + 1) if lines % d == 0]:
+                T = lines // a
+                for policy in (oracle.LRU, oracle.FIFO, oracle.RANDOM):
+                    for _ in range(12):
+                        L = int(rng.integers(1, 40))
+                        n_lines = int(rng.integers(1, 2 * lines + 3))
+                        tr = rng.integers(0, n_lines * b // 4, size=L).astype(np.uint32)
+                        got = oracle.cache_sim(lines * b, b, a, T, policy, tr, seed=77)
+                        want = _list_model(lines * b, b, a, T, policy, 77, tr)
+                        assert np.array_equal(got, want), (b, lines, a, policy, tr)
+                        n_checked += 1
+    assert n_checked > 1000
+
+
+def test_bruteforce_every_short_sequence():
+    # every sequence of 5 lines drawn from 4 lines, on three small caches
+    import itertools
+    for (lines, a) in ((2, 2), (4, 2), (3, 3)):
+        T = lines // a
+        b = 8
+        for seq in itertools.product(range(4), repeat=5):
+            tr = np.array([x * (b // 4) for x in seq], dtype=np.uint32)
+            for policy in (oracle.LRU, oracle.FIFO):
+                got = oracle.cache_sim(lines * b, b, a, T, policy, tr)
+                want = _list_model(lines * b, b, a, T, policy, 0, tr)
+                assert np.array_equal(got, want)
+
+
+# --------------------------------------------------------------- RANDOM
+def test_splitmix64_published_vectors():
+    # SplitMix64 seeded with 0: its first two outputs
+    assert oracle.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+
+
+def test_random_victims_uniform_chi2():
+    from scipy.stats import chisquare
+    for ways in (3, 4, 7, 16, 96):
+        n = 200 * ways
+        v = [oracle.random_victim(0xABCDEF, 5, k, ways) for k in range(n)]
+        cnt = np.bincount(v, minlength=ways)
+        assert cnt.size == ways
+        assert chisquare(cnt).pvalue > 1e-3
+
+
+def test_random_policy_depends_only_on_seed():
+    g = W.Geom(1024, 32, 4, 8, W.RANDOM, 99)
+    tr = oracle.pchase_trace(640, 8, 5000)
+    a = oracle.cache_sim(g.C, g.b, g.ways, g.sets, oracle.RANDOM, tr, seed=1)
+    b = oracle.cache_sim(g.C, g.b, g.ways, g.sets, oracle.RANDOM, tr, seed=1)
+    c = oracle.cache_sim(g.C, g.b, g.ways, g.sets, oracle.RANDOM, tr, seed=2)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+# ----------------------------------------------------------------- banks
+def test_bank_degree_is_gcd():
+    for s in range(1, 65):
+        words = [t * s for t in range(32)]
+        assert oracle.bank_degree(words) == math.gcd(s, 32), s
+
+
+def test_bank_fig14_stride2_and_broadcast():
+    words = [t * 2 for t in range(32)]
+    assert words[0] % 32 == words[16] % 32 == 0 and words[16] == 32
+    assert oracle.bank_degree(words) == 2
+    assert oracle.bank_degree([5] * 32) == 1  # same word: broadcast
+    assert oracle.bank_degree(list(range(32))) == 1  # odd stride 1
+    assert oracle.bank_degree([0, 32, 64, 96]) == 4
+
+
+# --------------------------------------------------------------- classify
+def test_classify_two_levels_with_spikes():
+    rng = np.random.Generator(np.random.PCG64(3))
+    truth = (rng.random(4000) < 0.3).astype(np.uint8)
+    lat = np.where(truth == 1, 400.0, 100.0) * (1 + 0.02 * rng.standard_normal(4000))
+    got, thr = oracle.classify(lat.astype(np.float32))
+    assert np.array_equal(got, truth) and 100 < thr < 400
+    # a few huge spikes on misses move nothing
+    lat2 = lat.copy()
+    spikes = np.where(truth == 1)[0][:15]
+    lat2[spikes] *= 10
+    got2, thr2 = oracle.classify(lat2.astype(np.float32))
+    assert np.array_equal(got2, truth) and abs(thr2 - thr) < 50
+
+
+def test_classify_flat_and_empty():
+    got, _ = oracle.classify(np.full(100, 7.0, dtype=np.float32))
+    assert got.sum() == 0
+    got, _ = oracle.classify(np.zeros(0, dtype=np.float32))
+    assert got.size == 0
+
+
+def test_mean_latency_model():
+    assert oracle.mean_latency(100.0, 300.0, 0.0) == 100.0
+    assert oracle.mean_latency(100.0, 300.0, 1.0) == 400.0
+    assert oracle.mean_latency(100.0, 300.0, 0.25) == 175.0
+
+
+# ------------------------------------------------------------------ matcher
+def _small_plan(C0):
+    runs = []
+    for nb in (C0 // 2, C0 - 4, C0, C0 + 4, C0 + 32, C0 + 36, C0 + 64, C0 + 132, 2 * C0):
+        runs.append((nb // 4, 1))
+    for nb in (C0 + 64, C0 + 256, 2 * C0, 4 * C0):
+        runs.append((nb // 4, 16))
+    traces = []
+    for n, s in runs:
+        per = n // math.gcd(n, s)
+        traces.append(oracle.pchase_trace(n, s, 3 * per))
+    return traces
+
+
+def test_match_round_trip_small_grid():
+    grid = W.geometry_grid(capacities=(512, 768, 1024), line_sizes=(32, 64),
+                           way_choices=(1, 2, 4, 0))
+    cands = np.array([(C, b, a, T, p) for (C, b, a, T) in grid for p in (0, 1)],
+                     dtype=np.uint32)
+    seeds = np.zeros(len(cands), dtype=np.uint64)
+    traces = _small_plan(768)
+    for truth in ((768, 64, 4, 3, 0), (768, 32, 2, 12, 0), (512, 32, 16, 1, 0)):
+        obs = [oracle.cache_sim(*truth[:4], truth[4], t) for t in traces]
+        dist = oracle.match(cands, seeds, traces, obs)
+        ti = [i for i, c in enumerate(cands.tolist()) if tuple(c) == truth][0]
+        assert dist[ti] == 0
+        pick, nb = oracle.canonical_pick(cands, dist)
+        assert dist[pick] == 0 and nb >= 1
+        # the pick is indistinguishable from the truth on this plan
+        for t in traces:
+            assert np.array_equal(oracle.cache_sim(*cands[pick][:4], int(cands[pick][4]), t),
+                                  oracle.cache_sim(*truth[:4], truth[4], t))
+
+
+def test_canonical_order():
+    cands = np.array([(1024, 32, 4, 8, 1), (1024, 64, 4, 4, 0), (1024, 32, 4, 8, 0),
+                      (1024, 64, 2, 8, 0), (2048, 64, 2, 16, 0)], dtype=np.uint32)
+    dist = np.array([0, 0, 0, 0, 0], dtype=np.uint64)
+    assert oracle.canonical_pick(cands, dist) == (3, 5)
+    dist = np.array([0, 3, 0, 1, 1], dtype=np.uint64)
+    assert oracle.canonical_pick(cands, dist) == (2, 2)
