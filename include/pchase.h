@@ -1,0 +1,325 @@
+/*
+ * pchase.h - C ABI of the GB300 (sm_103a) fine-grained P-chase library.
+ *
+ * The library mechanises the method of Mei & Chu, "Dissecting GPU Memory
+ * Hierarchy through Microbenchmarking" (arXiv:1509.02308):
+ *   - P-chase trace construction (Listing 1, Sec. 4.1; non-uniform chains of
+ *     Fig. 10, Sec. 5.2),
+ *   - a batched set-associative cache simulator over many geometries
+ *     (Assumptions 1-3 and Fig. 2, Sec. 4.1),
+ *   - latency -> hit/miss classification and the exhaustive geometry matcher
+ *     (the two-stage procedure of Fig. 6, Sec. 4.2),
+ *   - probe kernels for the GPU itself: fine-grained P-chase (Listing 3,
+ *     Sec. 4.2), shared-memory bank conflicts (Listing 4, Sec. 6.2) and
+ *     global-memory throughput (Sec. 5.1).
+ *
+ * Conventions for every call:
+ *   - Array indices are 4-byte elements; the byte address of element j is 4*j
+ *     (Sec. 4.2 counts N and s in elements, Sec. 4.3 uses 4-byte elements).
+ *   - The caller allocates and owns every buffer.  Pointers marked "device"
+ *     must be device memory of the current CUDA device; pointers marked "host"
+ *     are ordinary host memory.  The library keeps no pointer after a call
+ *     returns, except inside an explicitly created handle (pchase_sim_plan).
+ *   - Device work is queued on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream) and is asynchronous unless the call says otherwise.
+ *   - Every call returns a pchase_status.  Host-side validation failures are
+ *     returned before anything is queued.  Errors found by a kernel while it
+ *     runs (an index >= N, a chain leaving its array, a bounded wait that gave
+ *     up) are OR-ed into the caller's device status word as PCHASE_DEV_* bits;
+ *     the call itself cannot see them.  pchase_last_error_string() describes
+ *     the last host-side failure of the calling thread.
+ */
+#ifndef PCHASE_H
+#define PCHASE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pchase_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    PCHASE_OK = 0,
+    PCHASE_EINVAL = 1,   /* bad argument or geometry (T*a*b != C, b not a power of two, ...) */
+    PCHASE_ERANGE = 2,   /* a size above a stated limit, or a buffer too small */
+    PCHASE_ENOMEM = 3,   /* host allocation failed */
+    PCHASE_ETIMEOUT = 4, /* a bounded wait gave up */
+    PCHASE_ECUDA = 5     /* a CUDA runtime call failed; see pchase_last_error_string() */
+} pchase_status;
+
+/* Bits a kernel ORs into the caller's device status word (uint32). */
+#define PCHASE_DEV_INDEX_RANGE 1u   /* a trace index was >= n_elems; the access was skipped */
+#define PCHASE_DEV_CHAIN_RANGE 2u   /* a chain pointed outside its array; the walk stopped */
+#define PCHASE_DEV_TIMEOUT 4u       /* a probe's iteration cap ended a loop */
+
+typedef enum { PCHASE_LRU = 0, PCHASE_FIFO = 1, PCHASE_RANDOM = 2 } pchase_policy;
+
+/*
+ * Cache geometry (Assumption 1, Sec. 4.1): `sets` (T) sets of `ways` (a) lines
+ * of `line_bytes` (b) bytes, C = T*a*b.  b must be a power of two >= 4.
+ * Lines map to sets by set = line mod T with line = (4*index) / b (the
+ * modular reading of Assumption 2; `mapping` must be 0).  Replacement:
+ * LRU (Assumption 3), FIFO, or RANDOM, whose k-th eviction in set s takes way
+ *   floor(((h >> 32) * a) / 2^32),  h = SplitMix64(seed ^ (s << 40) ^ k),
+ * SplitMix64 being the first output of Steele-Lea-Flood's generator whose
+ * state is its argument.  A miss fills the lowest-numbered invalid way first.
+ * 32 bytes.
+ */
+typedef struct {
+    uint32_t C_bytes;
+    uint32_t line_bytes;
+    uint32_t ways;
+    uint32_t sets;
+    uint32_t policy;  /* pchase_policy */
+    uint32_t mapping; /* 0: set = line mod T */
+    uint64_t seed;    /* RANDOM only */
+} pchase_geom;
+
+/*
+ * One access trace.  `idx` (device) holds `len` element indices, each below
+ * `n_elems`; idx == NULL selects the analytic uniform chain of Listing 1 walked
+ * from j = 0, whose access t visits (t * stride) mod n_elems.  The first
+ * `warmup` accesses (the preheat pass of Listing 3) are counted apart.
+ * len < 2^31.  32 bytes.
+ */
+typedef struct {
+    const uint32_t *idx;
+    uint64_t len;
+    uint64_t warmup;
+    uint32_t n_elems;
+    uint32_t stride;
+} pchase_trace;
+
+/* One simulation item: geometry `geom` replays trace `trace`. */
+typedef struct {
+    uint32_t geom;
+    uint32_t trace;
+} pchase_pair;
+
+/* ------------------------------------------------------------------ S1 */
+
+/*
+ * Listing 1 (Sec. 4.1) and the chase of Listings 2-3: writes into trace_out
+ * (device, len uint32) the indices visited by j = A[j] from j = 0.
+ *   next == NULL: uniform chain A[i] = (i + stride) mod n_elems, so
+ *                 trace_out[t] = (t * stride) mod n_elems (parallel).
+ *   next != NULL: caller-built chain (device, n_elems entries), such as the
+ *                 non-uniform chains of Fig. 10; walked by one thread.  A
+ *                 link >= n_elems sets PCHASE_DEV_CHAIN_RANGE in *dev_status
+ *                 (device) and the rest of trace_out is left unwritten.
+ * array_out (device, n_elems uint32, may be NULL) receives the uniform array
+ * of Listing 1 itself, for the probe of pchase_probe_latency.
+ * Errors: EINVAL if n_elems == 0, or next != NULL and dev_status == NULL.
+ */
+int pchase_build(uint32_t n_elems, uint32_t stride, const uint32_t *next, uint64_t len,
+                 uint32_t *trace_out, uint32_t *array_out, uint32_t *dev_status,
+                 pchase_stream_t stream);
+
+/*
+ * Batched uniform chains: trace i (host descriptor traces[i], idx ignored) is
+ * written to trace_out + word_offsets[i] (host offsets, in uint32 elements).
+ * One launch for all n traces.
+ */
+int pchase_build_batch(const pchase_trace *traces, uint32_t n, uint32_t *trace_out,
+                       const uint64_t *word_offsets, pchase_stream_t stream);
+
+/* ---------------------------------------------------------- S2, S3, S6 */
+
+/*
+ * Tuning knobs of the simulator, chosen by the autotuner or left at their
+ * defaults (pass NULL).  See pchase_sim_plan_create.
+ */
+typedef struct {
+    uint32_t scan_max_ways;      /* a <= this: way-scan sets; above: line-table sets (default 8) */
+    uint32_t smem_budget_bytes;  /* shared memory per CTA (default 96 KB) */
+    uint32_t max_warps_per_cta;  /* (default 16) */
+    uint32_t ctas_per_sm_cap;    /* 0 = as many as fit */
+} pchase_tune;
+
+typedef struct pchase_sim_plan pchase_sim_plan;
+
+/*
+ * Plans a batch of simulation items on the host (no device work).  Item i is
+ * pairs[i]; pairs == NULL means all n_geom x n_trace combinations, item
+ * g * n_trace + t.  geoms, traces and pairs are host arrays; the trace index
+ * pointers inside `traces` are device pointers used later by pchase_sim_run.
+ * The plan sorts items longest first into shared-memory size classes, one
+ * persistent kernel per class (S6).  Errors: EINVAL for a bad geometry,
+ * pair or trace; ERANGE if a geometry is too large for any class
+ * (more than 65535 lines, or state above the workspace limits).
+ */
+int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom,
+                           const pchase_trace *traces, uint32_t n_trace,
+                           const pchase_pair *pairs, uint32_t n_pairs,
+                           const pchase_tune *tune, pchase_sim_plan **plan_out);
+void pchase_sim_plan_destroy(pchase_sim_plan *plan);
+
+/* Bytes of device workspace pchase_sim_run needs for this plan. */
+size_t pchase_sim_plan_workspace_bytes(const pchase_sim_plan *plan);
+/* Number of items, and of bitmap words when the plan lays bitmaps out itself. */
+uint64_t pchase_sim_plan_items(const pchase_sim_plan *plan);
+uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);
+
+/*
+ * Copies the plan's tables into `workspace` (device, at least
+ * pchase_sim_plan_workspace_bytes, 256-byte aligned).  Needed once per
+ * workspace before any number of pchase_sim_run calls.  Uses pageable-host
+ * cudaMemcpyAsync, so it must not be called during stream capture.
+ */
+int pchase_sim_plan_upload(const pchase_sim_plan *plan, void *workspace, size_t workspace_bytes,
+                           pchase_stream_t stream);
+
+/*
+ * Runs the planned batch: every item replays its trace through its geometry
+ * from an empty cache.  Outputs (all device):
+ *   bitmaps: per item ceil(len/32) uint32 words, bit t%32 of word t/32 is 1
+ *     when access t misses (LSB first); item i starts at word_offsets[i]
+ *     (device, uint64) or, when word_offsets == NULL, at the plan's own
+ *     back-to-back layout (pchase_sim_plan_bitmap_words words in total).
+ *     bitmaps may be NULL to skip them.
+ *   miss_counts: 2 uint64 per item: misses over all accesses, and misses
+ *     after the first `warmup` accesses.  May be NULL.
+ *   dev_status: uint32 status word (PCHASE_DEV_* bits); may be NULL.
+ * Only kernel launches and a memset are queued (no host copies), so the call
+ * can be captured into a CUDA graph; the work fans out over internal streams
+ * that join back into `stream`.
+ */
+int pchase_sim_run(const pchase_sim_plan *plan, void *workspace, uint32_t *bitmaps,
+                   const uint64_t *word_offsets, uint64_t *miss_counts, uint32_t *dev_status,
+                   pchase_stream_t stream);
+
+/*
+ * One-shot form of the three calls above (plan, upload, run, destroy) for a
+ * caller-provided workspace; returns ERANGE with *workspace_bytes set to the
+ * need when workspace_bytes is too small (workspace may then be NULL).
+ */
+int cache_sim_batch(const pchase_geom *geoms, uint32_t n_geom, const pchase_trace *traces,
+                    uint32_t n_trace, const pchase_pair *pairs, uint32_t n_pairs,
+                    uint32_t *bitmaps, const uint64_t *word_offsets, uint64_t *miss_counts,
+                    uint32_t *dev_status, void *workspace, size_t *workspace_bytes,
+                    pchase_stream_t stream);
+
+/* --------------------------------------------------------------- S4, S5 */
+
+/*
+ * Latency -> hit/miss (S4).  Sec. 4.1 models a P-chase latency as t0 (hit)
+ * or t0 + t_m (miss); the paper states no cut rule.  Reading: over one
+ * observation (the `n` latencies lat[offset[o] .. offset[o+1]), device
+ * float), set aside the largest floor(n/200) values, find the largest gap
+ * between consecutive distinct kept values (the lowest one on ties) and cut at
+ * (lo + hi) * 0.5f; a latency above the cut is a miss.  No gap: all hits.
+ * Writes packed miss bits (LSB first) for observation o at
+ * bits_out + bit_word_offsets[o] (device) and the cut to thresh_out[o].
+ * offsets, bit_word_offsets: device uint64, n_obs + 1 and n_obs entries.
+ * Work buffers: `workspace` (device) of pchase_classify_workspace_bytes.
+ */
+size_t pchase_classify_workspace_bytes(uint32_t n_obs, uint64_t max_len);
+int pchase_classify(const float *lat, const uint64_t *offsets, uint32_t n_obs,
+                    uint64_t max_len, uint32_t *bits_out, const uint64_t *bit_word_offsets,
+                    float *thresh_out, void *workspace, pchase_stream_t stream);
+
+/*
+ * Exhaustive matcher (S5), the mechanised form of Fig. 6 (Sec. 4.2): every
+ * plan item (candidate g, plan trace t) is replayed and compared with the
+ * observed miss bits of trace t (observed + obs_word_offsets[t], device); the
+ * Hamming distance summed over the candidate's traces goes to dist_out[g]
+ * (device uint64, zeroed by the call).  `plan` must have been created with
+ * pairs == NULL over (candidates x plan traces); `stop_above`: an item stops
+ * once its own distance exceeds it (UINT64_MAX: never), which keeps exact
+ * answers for every candidate whose distance stays <= stop_above.
+ */
+int pchase_match_run(const pchase_sim_plan *plan, void *workspace, const uint32_t *observed,
+                     const uint64_t *obs_word_offsets, uint64_t stop_above, uint64_t *dist_out,
+                     uint32_t *dev_status, pchase_stream_t stream);
+
+/*
+ * Canonical pick (device, one thread block): among n_cand candidates (geoms,
+ * device) with distances dist (device), the smallest distance wins, then
+ * policy LRU < FIFO < RANDOM, then the larger line size, then fewer ways, then
+ * the smaller capacity (identifiability reading of Sec. 4.2: geometries that
+ * no plan point separates are reported as one class).  Writes the pick's
+ * index and the number of candidates at the smallest distance to
+ * pick_out[0], pick_out[1] (device uint32).
+ */
+int pchase_canonical_pick(const pchase_geom *geoms, const uint64_t *dist, uint32_t n_cand,
+                          uint32_t *pick_out, pchase_stream_t stream);
+
+/*
+ * S4 + S5 in one call for one observation: classify the latencies of all plan
+ * traces together, match against every candidate, pick.  lat (device float)
+ * holds the plan traces' latencies back to back in trace order; the plan must
+ * be a candidates x traces plan whose workspace was uploaded.  Outputs (device):
+ * dist_out[n_cand] (uint64), pick_out[2] (uint32).  Extra device work buffer
+ * `scratch` of pchase_infer_scratch_bytes(plan).
+ */
+size_t pchase_infer_scratch_bytes(const pchase_sim_plan *plan);
+int infer_geometry(const pchase_sim_plan *plan, void *workspace, const float *lat,
+                   void *scratch, uint64_t *dist_out, uint32_t *pick_out, uint32_t *dev_status,
+                   pchase_stream_t stream);
+
+/* --------------------------------------------------------------- S8-S10 */
+
+/*
+ * Fine-grained P-chase probe (Listing 3, Sec. 4.2) on this GPU.  One thread
+ * walks j = array[j] (device chain of n_elems entries, e.g. from
+ * pchase_build) from j = start: it first runs `warmup` untimed accesses (the
+ * preheat), then `iters` timed ones.  Each timed access reads clock64 before
+ * the load and after a dependent store of the loaded index into shared
+ * memory, buffering up to 256 latencies and indices in shared memory before
+ * copying them out; lat_out[i] is the raw cycle count of access i minus
+ * overhead_out[0], the measured cost of the same clock + dependent-store
+ * sequence around a shared-memory load. idx_out[i] is the index visited by
+ * access i.  cache_mode: 0 = ld.global.ca (L1 and L2), 1 = ld.global.cg
+ * (L2 only), 2 = ld.global.nc (read-only path).  Device outputs: lat_out,
+ * idx_out (iters uint32 each), overhead_out (2 uint32: store+clock segment,
+ * back-to-back clock64 reads).  Limits: iters <= 1<<24, warmup <= 1<<26.
+ * A link >= n_elems sets PCHASE_DEV_CHAIN_RANGE and stops the walk.
+ */
+int pchase_probe_latency(const uint32_t *array, uint32_t n_elems, uint32_t start,
+                         uint32_t warmup, uint32_t iters, int cache_mode, uint32_t *lat_out,
+                         uint32_t *idx_out, uint32_t *overhead_out, uint32_t *dev_status,
+                         pchase_stream_t stream);
+
+/*
+ * Shared-memory stride probe (Listing 4, Sec. 6.2): one warp; lane t starts
+ * at word t*stride and follows 64 dependent reads of a self-pointing word, for
+ * every stride in [1, max_stride] (max_stride <= 64).  cycles_out[s-1]
+ * (device float) is the mean clock64 cycles per access of stride s (median of
+ * `repeats` timed rounds, repeats in [1, 64]); degree_out[s-1] (device uint32)
+ * is the conflict degree the bank model predicts for the same request (32
+ * banks of 4-byte words, equal words broadcast).
+ */
+int pchase_probe_smem_bank(uint32_t max_stride, uint32_t repeats, float *cycles_out,
+                           uint32_t *degree_out, pchase_stream_t stream);
+
+/*
+ * Global-memory throughput probe (Sec. 5.1, Table 5).  kind: 0 read, 1 write,
+ * 2 copy (counts 2 * bytes, as the paper does).  vec_bytes: 4 (fp32) or 16
+ * (int4).  ctas, threads: launch shape (threads a multiple of 32, <= 1024);
+ * ilp: independent vectors per thread per loop trip (1, 2, 4 or 8).  src,
+ * dst: device buffers of `bytes` (bytes a multiple of vec_bytes * ilp;
+ * src unused for write, dst unused... for read a 4-byte device sink is dst).
+ * SYNCHRONOUS: runs `reps` timed launches after one warm-up launch, timing
+ * each with CUDA events on `stream`, and returns the median GB/s (1e9 B/s)
+ * in *gbs_out (host).
+ */
+int pchase_probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas,
+                                   uint32_t threads, uint32_t ilp, const void *src, void *dst,
+                                   uint64_t bytes, uint32_t reps, double *gbs_out,
+                                   pchase_stream_t stream);
+
+/* ------------------------------------------------------------- library */
+
+const char *pchase_last_error_string(void);
+const char *pchase_version(void);
+/* Number of SMs of the current device (0 if none). */
+int pchase_device_sm_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCHASE_H */

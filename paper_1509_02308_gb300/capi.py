@@ -1,0 +1,148 @@
+"""Thin ctypes binding of include/pchase.h.
+
+Argument marshalling only: every step runs in the CUDA library
+(_build/libpchase.so).  There is no CPU fallback; if the library cannot be
+loaded every call raises.  Device buffers are torch CUDA tensors; streams
+default to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpchase.so")
+
+OK, EINVAL, ERANGE, ENOMEM, ETIMEOUT, ECUDA = range(6)
+DEV_INDEX_RANGE, DEV_CHAIN_RANGE, DEV_TIMEOUT = 1, 2, 4
+LRU, FIFO, RANDOM = 0, 1, 2
+
+_c_u32, _c_u64, _c_p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("C_bytes", _c_u32), ("line_bytes", _c_u32), ("ways", _c_u32),
+                ("sets", _c_u32), ("policy", _c_u32), ("mapping", _c_u32), ("seed", _c_u64)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("idx", _c_p), ("len", _c_u64), ("warmup", _c_u64), ("n_elems", _c_u32),
+                ("stride", _c_u32)]
+
+
+class Pair(ctypes.Structure):
+    _fields_ = [("geom", _c_u32), ("trace", _c_u32)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("scan_max_ways", _c_u32), ("smem_budget_bytes", _c_u32),
+                ("max_warps_per_cta", _c_u32), ("ctas_per_sm_cap", _c_u32)]
+
+
+assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32
+
+# every exported symbol of include/pchase.h with (restype, argtypes)
+SIGNATURES = {
+    "pchase_build": (ctypes.c_int, [_c_u32, _c_u32, _c_p, _c_u64, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_build_batch": (ctypes.c_int, [_c_p, _c_u32, _c_p, _c_p, _c_p]),
+    "pchase_sim_plan_create": (ctypes.c_int, [_c_p, _c_u32, _c_p, _c_u32, _c_p, _c_u32, _c_p,
+                                              ctypes.POINTER(_c_p)]),
+    "pchase_sim_plan_destroy": (None, [_c_p]),
+    "pchase_sim_plan_workspace_bytes": (ctypes.c_size_t, [_c_p]),
+    "pchase_sim_plan_items": (_c_u64, [_c_p]),
+    "pchase_sim_plan_bitmap_words": (_c_u64, [_c_p]),
+    "pchase_sim_plan_upload": (ctypes.c_int, [_c_p, _c_p, ctypes.c_size_t, _c_p]),
+    "pchase_sim_run": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "cache_sim_batch": (ctypes.c_int, [_c_p, _c_u32, _c_p, _c_u32, _c_p, _c_u32, _c_p, _c_p, _c_p,
+                                       _c_p, _c_p, ctypes.POINTER(ctypes.c_size_t), _c_p]),
+    "pchase_classify_workspace_bytes": (ctypes.c_size_t, [_c_u32, _c_u64]),
+    "pchase_classify": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_u64, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_match_run": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_u64, _c_p, _c_p, _c_p]),
+    "pchase_canonical_pick": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_p, _c_p]),
+    "pchase_infer_scratch_bytes": (ctypes.c_size_t, [_c_p]),
+    "infer_geometry": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_probe_latency": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.c_int,
+                                            _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_probe_smem_bank": (ctypes.c_int, [_c_u32, _c_u32, _c_p, _c_p, _c_p]),
+    "pchase_probe_global_throughput": (ctypes.c_int, [ctypes.c_int, _c_u32, _c_u32, _c_u32,
+                                                      _c_u32, _c_p, _c_p, _c_u64, _c_u32,
+                                                      ctypes.POINTER(ctypes.c_double), _c_p]),
+    "pchase_last_error_string": (ctypes.c_char_p, []),
+    "pchase_version": (ctypes.c_char_p, []),
+    "pchase_device_sm_count": (ctypes.c_int, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PchaseError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pchase status {code}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Loads the CUDA library (building it first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                from . import build as _b
+                _b.build()
+            L = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != OK:
+        raise PchaseError(rc, load().pchase_last_error_string().decode())
+
+
+def ptr(t) -> int | None:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def stream_handle(stream=None) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream) or None
+
+
+def geom_array(geoms) -> ctypes.Array:
+    arr = (Geom * max(1, len(geoms)))()
+    for i, g in enumerate(geoms):
+        arr[i] = Geom(g.C, g.b, g.ways, g.sets, g.policy, 0, g.seed & 0xFFFFFFFFFFFFFFFF)
+    return arr
+
+
+def trace_array(descs) -> ctypes.Array:
+    """descs: iterable of (idx_tensor_or_None, len, warmup, n_elems, stride)."""
+    descs = list(descs)
+    arr = (Trace * max(1, len(descs)))()
+    for i, (t, L, w, n, s) in enumerate(descs):
+        arr[i] = Trace(ptr(t), L, w, n, s)
+    return arr
+
+
+def pair_array(pairs) -> ctypes.Array:
+    pairs = list(pairs)
+    arr = (Pair * max(1, len(pairs)))()
+    for i, (g, t) in enumerate(pairs):
+        arr[i] = Pair(g, t)
+    return arr
+
+
+def u64_array(vals) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(vals, dtype=np.uint64))

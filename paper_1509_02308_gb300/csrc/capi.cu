@@ -1,0 +1,609 @@
+// C ABI entry points (include/pchase.h): argument checks, the simulation
+// planner, workspace layout, and launches.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pchase_internal.cuh"
+
+namespace pchase {
+cudaError_t build_uniform(uint32_t n, uint32_t s, uint64_t len, uint32_t *trace,
+                          uint32_t *array_out, cudaStream_t st, int sms);
+cudaError_t build_chain(const uint32_t *next, uint32_t n, uint64_t len, uint32_t *trace,
+                        uint32_t *status, cudaStream_t st);
+cudaError_t build_uniform_batch(const pchase_trace *traces, uint32_t count, uint32_t *out,
+                                const uint64_t *offsets, cudaStream_t st);
+size_t classify_meta_bytes(uint32_t n_obs);
+size_t classify_bucket_bytes(uint32_t n_obs, uint64_t max_len);
+cudaError_t classify_thresholds(const float *lat, const uint64_t *offsets, uint32_t n_obs,
+                                uint64_t max_len, void *meta_mem, void *bucket_mem,
+                                float *thresh_out, cudaStream_t st, int sms);
+cudaError_t classify_bits(const float *lat, const uint64_t *seg_offsets, int per_seg,
+                          uint32_t n_seg, uint64_t max_seg_len, const void *meta_mem,
+                          uint32_t *bits, const uint64_t *word_offsets, cudaStream_t st, int sms);
+cudaError_t canonical_pick(const pchase_geom *geoms, const uint64_t *dist, uint32_t n,
+                           uint32_t *pick, cudaStream_t st);
+cudaError_t probe_latency(const uint32_t *A, uint32_t n, uint32_t start, uint32_t warmup,
+                          uint32_t iters, int mode, uint32_t *lat, uint32_t *idx, uint32_t *ovh,
+                          uint32_t *status, cudaStream_t st);
+cudaError_t probe_smem(uint32_t max_stride, uint32_t repeats, float *cycles, uint32_t *degree,
+                       cudaStream_t st);
+cudaError_t probe_gmem(int kind, uint32_t vec_bytes, uint32_t ctas, uint32_t threads,
+                       uint32_t ilp, const void *src, void *dst, uint64_t bytes, uint32_t reps,
+                       double *gbs, cudaStream_t st);
+}  // namespace pchase
+
+using namespace pchase;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    g_err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return PCHASE_ECUDA;
+}
+
+#define PCHASE_CUDA(call, where)                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+uint32_t ilog2(uint32_t x) {
+    uint32_t l = 0;
+    while ((1u << l) < x) ++l;
+    return l;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+constexpr uint32_t kMaxLines = 65535;
+constexpr uint32_t kMaxArena = 232448;  // 227 KB, one warp per CTA
+constexpr uint32_t kMaxClasses = 24;
+const uint32_t kCaps[] = {512,   1024,  2048,  3072,   4096,   6144,   8192,   12288,
+                          16384, 24576, 32768, 49152,  65536,  98304,  131072, 163840,
+                          196608, kMaxArena};
+
+int check_geom(const pchase_geom &g, uint32_t i) {
+    char buf[160];
+    if (g.line_bytes < 4 || !is_pow2(g.line_bytes)) {
+        snprintf(buf, sizeof buf, "geometry %u: line size %u is not a power of two >= 4", i,
+                 g.line_bytes);
+        return fail(PCHASE_EINVAL, buf);
+    }
+    if (g.ways == 0 || g.sets == 0 ||
+        (uint64_t)g.sets * g.ways * g.line_bytes != (uint64_t)g.C_bytes) {
+        snprintf(buf, sizeof buf, "geometry %u: sets*ways*line (%u*%u*%u) != C (%u)", i, g.sets,
+                 g.ways, g.line_bytes, g.C_bytes);
+        return fail(PCHASE_EINVAL, buf);
+    }
+    if (g.policy > PCHASE_RANDOM || g.mapping != 0) {
+        snprintf(buf, sizeof buf, "geometry %u: unknown policy %u or mapping %u", i, g.policy,
+                 g.mapping);
+        return fail(PCHASE_EINVAL, buf);
+    }
+    if ((uint64_t)g.sets * g.ways > kMaxLines) {
+        snprintf(buf, sizeof buf, "geometry %u: %llu lines is above the limit of %u", i,
+                 (unsigned long long)g.sets * g.ways, kMaxLines);
+        return fail(PCHASE_ERANGE, buf);
+    }
+    return PCHASE_OK;
+}
+
+int check_trace(const pchase_trace &t, uint32_t i) {
+    char buf[160];
+    if (t.n_elems == 0) {
+        snprintf(buf, sizeof buf, "trace %u: n_elems is 0", i);
+        return fail(PCHASE_EINVAL, buf);
+    }
+    if (t.len >= (1ull << 31)) {
+        snprintf(buf, sizeof buf, "trace %u: length %llu is not below 2^31", i,
+                 (unsigned long long)t.len);
+        return fail(PCHASE_ERANGE, buf);
+    }
+    return PCHASE_OK;
+}
+
+}  // namespace
+
+struct pchase_sim_plan {
+    std::vector<SimItem> items;
+    std::vector<ClassLaunch> classes;
+    uint64_t bitmap_words = 0;
+    uint64_t n_items = 0;
+    size_t ws_bytes = 0, off_items = 0, off_geoms = 0, off_seg = 0, off_obs_words = 0,
+           off_pool = 0;
+    bool cross = false;
+    uint32_t n_geom = 0, n_trace = 0;
+    std::vector<pchase_geom> geoms;
+    std::vector<uint64_t> seg_offsets;     // n_trace + 1 (element offsets of trace latencies)
+    std::vector<uint64_t> obs_word_offsets;  // n_trace
+    uint64_t obs_words = 0, total_len = 0, max_trace_len = 0;
+    // runtime state, made on the first run
+    int device = -1, sms = 0;
+    std::vector<int> grids;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+
+    ~pchase_sim_plan() {
+        for (auto s : streams) cudaStreamDestroy(s);
+        for (auto e : joins) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+    }
+};
+
+namespace {
+
+int plan_runtime(pchase_sim_plan *p) {
+    int dev = 0;
+    PCHASE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (p->device >= 0) {
+        if (dev != p->device) return fail(PCHASE_EINVAL, "plan used on another device");
+        return PCHASE_OK;
+    }
+    p->sms = sm_count();
+    if (p->sms <= 0) return fail(PCHASE_ECUDA, "no CUDA device");
+    for (const ClassLaunch &c : p->classes) {
+        int per = sim_max_ctas_per_sm(c, false);
+        if (per <= 0) return fail(PCHASE_ECUDA, "simulator kernel cannot be resident");
+        const uint64_t need = (c.count + c.warps - 1) / c.warps;
+        const uint64_t cap = (uint64_t)per * p->sms;
+        p->grids.push_back((int)std::max<uint64_t>(1, std::min(need, cap)));
+        cudaStream_t s;
+        PCHASE_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
+        p->streams.push_back(s);
+        cudaEvent_t e;
+        PCHASE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        p->joins.push_back(e);
+    }
+    PCHASE_CUDA(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming), "cudaEventCreate");
+    p->device = dev;
+    return PCHASE_OK;
+}
+
+int plan_launch(pchase_sim_plan *p, void *ws, const SimOut &out, cudaStream_t st) {
+    int rc = plan_runtime(p);
+    if (rc) return rc;
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    PCHASE_CUDA(cudaMemsetAsync(w, 0, 256, st), "cudaMemsetAsync(queues)");
+    SimOut o = out;
+    if (!o.status) o.status = reinterpret_cast<uint32_t *>(w + 128);
+    const SimItem *items = reinterpret_cast<const SimItem *>(w + p->off_items);
+    PCHASE_CUDA(cudaEventRecord(p->fork, st), "cudaEventRecord");
+    for (size_t c = 0; c < p->classes.size(); ++c) {
+        PCHASE_CUDA(cudaStreamWaitEvent(p->streams[c], p->fork, 0), "cudaStreamWaitEvent");
+        uint32_t *queue = reinterpret_cast<uint32_t *>(w) + c;
+        PCHASE_CUDA(launch_sim_class(items, p->classes[c], queue, p->grids[c], o, false,
+                                     p->streams[c]),
+                    "simulator launch");
+        PCHASE_CUDA(cudaEventRecord(p->joins[c], p->streams[c]), "cudaEventRecord");
+        PCHASE_CUDA(cudaStreamWaitEvent(st, p->joins[c], 0), "cudaStreamWaitEvent");
+    }
+    return PCHASE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pchase_last_error_string(void) { return g_err.c_str(); }
+const char *pchase_version(void) { return "pchase-gb300 0.1 (sm_103a)"; }
+int pchase_device_sm_count(void) { return sm_count(); }
+
+int pchase_build(uint32_t n_elems, uint32_t stride, const uint32_t *next, uint64_t len,
+                 uint32_t *trace_out, uint32_t *array_out, uint32_t *dev_status,
+                 pchase_stream_t stream) {
+    if (n_elems == 0) return fail(PCHASE_EINVAL, "pchase_build: n_elems is 0");
+    if (len && !trace_out) return fail(PCHASE_EINVAL, "pchase_build: trace_out is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (next) {
+        if (!dev_status) return fail(PCHASE_EINVAL, "pchase_build: chain walk needs dev_status");
+        PCHASE_CUDA(build_chain(next, n_elems, len, trace_out, dev_status, st), "chain walk");
+        if (array_out) PCHASE_CUDA(build_uniform(n_elems, stride, 0, nullptr, array_out, st, sm_count()),
+                                   "uniform array");
+        return PCHASE_OK;
+    }
+    PCHASE_CUDA(build_uniform(n_elems, stride, len, trace_out, array_out, st, sm_count()),
+                "uniform trace");
+    return PCHASE_OK;
+}
+
+int pchase_build_batch(const pchase_trace *traces, uint32_t n, uint32_t *trace_out,
+                       const uint64_t *word_offsets, pchase_stream_t stream) {
+    if (n == 0) return PCHASE_OK;
+    if (!traces || !trace_out || !word_offsets)
+        return fail(PCHASE_EINVAL, "pchase_build_batch: NULL argument");
+    for (uint32_t i = 0; i < n; ++i) {
+        if (traces[i].n_elems == 0) return fail(PCHASE_EINVAL, "pchase_build_batch: n_elems is 0");
+    }
+    PCHASE_CUDA(build_uniform_batch(traces, n, trace_out, word_offsets,
+                                    reinterpret_cast<cudaStream_t>(stream)),
+                "batched uniform traces");
+    return PCHASE_OK;
+}
+
+int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pchase_trace *traces,
+                           uint32_t n_trace, const pchase_pair *pairs, uint32_t n_pairs,
+                           const pchase_tune *tune, pchase_sim_plan **plan_out) {
+    if (!plan_out) return fail(PCHASE_EINVAL, "plan_out is NULL");
+    *plan_out = nullptr;
+    if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
+        return fail(PCHASE_EINVAL, "NULL descriptor array");
+    pchase_tune tn{8, 96 * 1024, 16, 0};
+    if (tune) {
+        if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
+        if (tune->smem_budget_bytes) tn.smem_budget_bytes = std::min(tune->smem_budget_bytes, kMaxArena);
+        if (tune->max_warps_per_cta) tn.max_warps_per_cta = std::min<uint32_t>(tune->max_warps_per_cta, 16);
+        tn.ctas_per_sm_cap = tune->ctas_per_sm_cap;
+    }
+    for (uint32_t i = 0; i < n_geom; ++i) {
+        int rc = check_geom(geoms[i], i);
+        if (rc) return rc;
+    }
+    for (uint32_t i = 0; i < n_trace; ++i) {
+        int rc = check_trace(traces[i], i);
+        if (rc) return rc;
+    }
+    auto *p = new (std::nothrow) pchase_sim_plan();
+    if (!p) return fail(PCHASE_ENOMEM, "plan allocation");
+    p->cross = pairs == nullptr;
+    p->n_geom = n_geom;
+    p->n_trace = n_trace;
+    p->geoms.assign(geoms, geoms + n_geom);
+    const uint64_t n_items = p->cross ? (uint64_t)n_geom * n_trace : n_pairs;
+    if (n_items > 0xFFFFFFFFull) {
+        delete p;
+        return fail(PCHASE_ERANGE, "more than 2^32-1 items");
+    }
+    p->n_items = n_items;
+    // per-trace layouts used by the matcher
+    p->seg_offsets.resize(n_trace + 1, 0);
+    p->obs_word_offsets.resize(n_trace, 0);
+    for (uint32_t t = 0; t < n_trace; ++t) {
+        p->seg_offsets[t + 1] = p->seg_offsets[t] + traces[t].len;
+        p->obs_word_offsets[t] = p->obs_words;
+        p->obs_words += (traces[t].len + 31) / 32;
+        p->max_trace_len = std::max<uint64_t>(p->max_trace_len, traces[t].len);
+    }
+    p->total_len = p->seg_offsets[n_trace];
+
+    std::vector<SimItem> items;
+    try {
+        items.resize(n_items);
+    } catch (...) {
+        delete p;
+        return fail(PCHASE_ENOMEM, "item table allocation");
+    }
+    uint64_t word = 0;
+    for (uint64_t i = 0; i < n_items; ++i) {
+        uint32_t g, t;
+        if (p->cross) {
+            g = (uint32_t)(i / n_trace);
+            t = (uint32_t)(i % n_trace);
+        } else {
+            g = pairs[i].geom;
+            t = pairs[i].trace;
+            if (g >= n_geom || t >= n_trace) {
+                delete p;
+                return fail(PCHASE_EINVAL, "pair refers to a missing geometry or trace");
+            }
+        }
+        const pchase_geom &G = geoms[g];
+        const pchase_trace &Tr = traces[t];
+        SimItem &it = items[i];
+        memset(&it, 0, sizeof it);
+        it.idx = Tr.idx;
+        it.len = (uint32_t)Tr.len;
+        it.warmup = (uint32_t)std::min<uint64_t>(Tr.warmup, Tr.len);
+        it.n_elems = Tr.n_elems;
+        it.stride = Tr.stride % Tr.n_elems;
+        it.ways = G.ways;
+        it.sets = G.sets;
+        const DivMagic dm = make_div_magic(G.sets);
+        it.magic_m = dm.m;
+        it.s1 = (uint8_t)dm.s1;
+        it.s2 = (uint8_t)dm.s2;
+        it.policy = (uint8_t)G.policy;
+        it.lsh = ilog2(G.line_bytes) - 2;
+        it.seed = G.seed;
+        it.word_off = word;
+        word += (Tr.len + 31) / 32;
+        it.out_item = (uint32_t)i;
+        it.cand = g;
+        it.obs = t;
+        const uint64_t lines = (uint64_t)G.sets * G.ways;
+        uint64_t arena;
+        if (G.ways <= tn.scan_max_ways) {
+            it.mode = kModeScan;
+            arena = 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * G.sets : 0);
+        } else {
+            it.mode = kModeTable;
+            it.table_n = ((Tr.n_elems - 1) >> it.lsh) + 1;
+            arena = 8ull * G.sets + 4 * lines + (G.policy == PCHASE_LRU ? 4 * lines : 0) +
+                    2ull * it.table_n;
+        }
+        arena = align16(arena);
+        if (arena > kMaxArena) {
+            delete p;
+            char buf[200];
+            snprintf(buf, sizeof buf,
+                     "item %llu needs %llu bytes of set state, above the %u-byte limit",
+                     (unsigned long long)i, (unsigned long long)arena, kMaxArena);
+            return fail(PCHASE_ERANGE, buf);
+        }
+        it.arena_bytes = (uint32_t)arena;
+    }
+    p->bitmap_words = word;
+
+    // size classes, longest items first inside each class
+    std::vector<int> cls(n_items);
+    const int ncap = (int)(sizeof kCaps / sizeof kCaps[0]);
+    for (uint64_t i = 0; i < n_items; ++i) {
+        int c = 0;
+        while (kCaps[c] < items[i].arena_bytes) ++c;
+        cls[i] = c;
+    }
+    std::vector<uint64_t> order(n_items);
+    for (uint64_t i = 0; i < n_items; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
+        if (cls[x] != cls[y]) return cls[x] > cls[y];
+        return items[x].len > items[y].len;
+    });
+    p->items.reserve(n_items);
+    for (uint64_t k = 0; k < n_items; ++k) p->items.push_back(items[order[k]]);
+    for (uint64_t k = 0; k < n_items;) {
+        const int c = cls[order[k]];
+        uint64_t e = k;
+        while (e < n_items && cls[order[e]] == c) ++e;
+        ClassLaunch L;
+        L.first = (uint32_t)k;
+        L.count = (uint32_t)(e - k);
+        L.arena_bytes = kCaps[c];
+        uint32_t w = tn.smem_budget_bytes / kCaps[c];
+        w = std::max<uint32_t>(1, std::min<uint32_t>(w, tn.max_warps_per_cta));
+        L.warps = w;
+        p->classes.push_back(L);
+        k = e;
+    }
+    (void)ncap;
+    if (p->classes.size() > kMaxClasses) {
+        delete p;
+        return fail(PCHASE_ERANGE, "too many size classes");
+    }
+    // workspace: [queues + status: 256][items][geoms][seg offsets][obs word offsets][pool]
+    size_t off = 256;
+    p->off_items = off;
+    off = align256(off + n_items * sizeof(SimItem));
+    p->off_geoms = off;
+    off = align256(off + (size_t)n_geom * sizeof(pchase_geom));
+    p->off_seg = off;
+    off = align256(off + (size_t)(n_trace + 1) * sizeof(uint64_t));
+    p->off_obs_words = off;
+    off = align256(off + (size_t)n_trace * sizeof(uint64_t));
+    p->off_pool = off;
+    off = align256(off + 2 * sizeof(uint64_t));
+    p->ws_bytes = off;
+    *plan_out = p;
+    return PCHASE_OK;
+}
+
+void pchase_sim_plan_destroy(pchase_sim_plan *plan) { delete plan; }
+
+size_t pchase_sim_plan_workspace_bytes(const pchase_sim_plan *plan) {
+    return plan ? plan->ws_bytes : 0;
+}
+uint64_t pchase_sim_plan_items(const pchase_sim_plan *plan) { return plan ? plan->n_items : 0; }
+uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan) {
+    return plan ? plan->bitmap_words : 0;
+}
+
+int pchase_sim_plan_upload(const pchase_sim_plan *plan, void *workspace, size_t workspace_bytes,
+                           pchase_stream_t stream) {
+    if (!plan || !workspace) return fail(PCHASE_EINVAL, "plan or workspace is NULL");
+    if (workspace_bytes < plan->ws_bytes) return fail(PCHASE_ERANGE, "workspace too small");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255)
+        return fail(PCHASE_EINVAL, "workspace is not 256-byte aligned");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *w = static_cast<uint8_t *>(workspace);
+    if (!plan->items.empty())
+        PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_items, plan->items.data(),
+                                    plan->items.size() * sizeof(SimItem), cudaMemcpyHostToDevice, st),
+                    "upload items");
+    if (!plan->geoms.empty())
+        PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_geoms, plan->geoms.data(),
+                                    plan->geoms.size() * sizeof(pchase_geom), cudaMemcpyHostToDevice,
+                                    st),
+                    "upload geometries");
+    PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_seg, plan->seg_offsets.data(),
+                                plan->seg_offsets.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                st),
+                "upload offsets");
+    if (!plan->obs_word_offsets.empty())
+        PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_obs_words, plan->obs_word_offsets.data(),
+                                    plan->obs_word_offsets.size() * sizeof(uint64_t),
+                                    cudaMemcpyHostToDevice, st),
+                    "upload word offsets");
+    const uint64_t pool[2] = {0, plan->total_len};
+    PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_pool, pool, sizeof pool, cudaMemcpyHostToDevice, st),
+                "upload pooled offsets");
+    return PCHASE_OK;
+}
+
+int pchase_sim_run(const pchase_sim_plan *plan, void *workspace, uint32_t *bitmaps,
+                   const uint64_t *word_offsets, uint64_t *miss_counts, uint32_t *dev_status,
+                   pchase_stream_t stream) {
+    if (!plan || !workspace) return fail(PCHASE_EINVAL, "plan or workspace is NULL");
+    if (plan->n_items == 0) return PCHASE_OK;
+    SimOut out{};
+    out.bitmaps = bitmaps;
+    out.word_offsets = word_offsets;
+    out.miss_counts = miss_counts;
+    out.status = dev_status;
+    return plan_launch(const_cast<pchase_sim_plan *>(plan), workspace, out,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+int cache_sim_batch(const pchase_geom *geoms, uint32_t n_geom, const pchase_trace *traces,
+                    uint32_t n_trace, const pchase_pair *pairs, uint32_t n_pairs,
+                    uint32_t *bitmaps, const uint64_t *word_offsets, uint64_t *miss_counts,
+                    uint32_t *dev_status, void *workspace, size_t *workspace_bytes,
+                    pchase_stream_t stream) {
+    if (!workspace_bytes) return fail(PCHASE_EINVAL, "workspace_bytes is NULL");
+    pchase_sim_plan *p = nullptr;
+    int rc = pchase_sim_plan_create(geoms, n_geom, traces, n_trace, pairs, n_pairs, nullptr, &p);
+    if (rc) return rc;
+    if (!workspace || *workspace_bytes < p->ws_bytes) {
+        *workspace_bytes = p->ws_bytes;
+        pchase_sim_plan_destroy(p);
+        return fail(PCHASE_ERANGE, "workspace too small; *workspace_bytes holds the need");
+    }
+    rc = pchase_sim_plan_upload(p, workspace, *workspace_bytes, stream);
+    if (!rc) rc = pchase_sim_run(p, workspace, bitmaps, word_offsets, miss_counts, dev_status, stream);
+    pchase_sim_plan_destroy(p);
+    return rc;
+}
+
+size_t pchase_classify_workspace_bytes(uint32_t n_obs, uint64_t max_len) {
+    return classify_meta_bytes(n_obs) + align256(classify_bucket_bytes(n_obs, max_len));
+}
+
+int pchase_classify(const float *lat, const uint64_t *offsets, uint32_t n_obs, uint64_t max_len,
+                    uint32_t *bits_out, const uint64_t *bit_word_offsets, float *thresh_out,
+                    void *workspace, pchase_stream_t stream) {
+    if (n_obs == 0) return PCHASE_OK;
+    if (!lat || !offsets || !bits_out || !bit_word_offsets || !workspace)
+        return fail(PCHASE_EINVAL, "pchase_classify: NULL argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *w = static_cast<uint8_t *>(workspace);
+    void *meta = w;
+    void *bk = w + classify_meta_bytes(n_obs);
+    const int sms = sm_count();
+    PCHASE_CUDA(classify_thresholds(lat, offsets, n_obs, max_len, meta, bk, thresh_out, st, sms),
+                "classify thresholds");
+    PCHASE_CUDA(classify_bits(lat, offsets, 1, n_obs, max_len,
+                              meta, bits_out, bit_word_offsets, st, sms),
+                "classify bits");
+    return PCHASE_OK;
+}
+
+int pchase_match_run(const pchase_sim_plan *plan, void *workspace, const uint32_t *observed,
+                     const uint64_t *obs_word_offsets, uint64_t stop_above, uint64_t *dist_out,
+                     uint32_t *dev_status, pchase_stream_t stream) {
+    if (!plan || !workspace || !observed || !obs_word_offsets || !dist_out)
+        return fail(PCHASE_EINVAL, "pchase_match_run: NULL argument");
+    if (!plan->cross) return fail(PCHASE_EINVAL, "matcher needs a candidates x traces plan");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PCHASE_CUDA(cudaMemsetAsync(dist_out, 0, (size_t)plan->n_geom * sizeof(uint64_t), st),
+                "cudaMemsetAsync(dist)");
+    if (plan->n_items == 0) return PCHASE_OK;
+    SimOut out{};
+    out.status = dev_status;
+    out.observed = observed;
+    out.obs_word_offsets = obs_word_offsets;
+    out.stop_above = stop_above;
+    out.dist = dist_out;
+    return plan_launch(const_cast<pchase_sim_plan *>(plan), workspace, out, st);
+}
+
+int pchase_canonical_pick(const pchase_geom *geoms, const uint64_t *dist, uint32_t n_cand,
+                          uint32_t *pick_out, pchase_stream_t stream) {
+    if (!geoms || !dist || !pick_out) return fail(PCHASE_EINVAL, "pchase_canonical_pick: NULL");
+    PCHASE_CUDA(canonical_pick(geoms, dist, n_cand, pick_out, reinterpret_cast<cudaStream_t>(stream)),
+                "canonical pick");
+    return PCHASE_OK;
+}
+
+size_t pchase_infer_scratch_bytes(const pchase_sim_plan *plan) {
+    if (!plan) return 0;
+    return classify_meta_bytes(1) + align256(classify_bucket_bytes(1, plan->total_len)) +
+           align256(plan->obs_words * sizeof(uint32_t) + 4);
+}
+
+int infer_geometry(const pchase_sim_plan *plan, void *workspace, const float *lat, void *scratch,
+                   uint64_t *dist_out, uint32_t *pick_out, uint32_t *dev_status,
+                   pchase_stream_t stream) {
+    if (!plan || !workspace || !lat || !scratch || !dist_out || !pick_out)
+        return fail(PCHASE_EINVAL, "infer_geometry: NULL argument");
+    if (!plan->cross) return fail(PCHASE_EINVAL, "infer_geometry needs a candidates x traces plan");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *w = static_cast<uint8_t *>(workspace);
+    uint8_t *s = static_cast<uint8_t *>(scratch);
+    void *meta = s;
+    void *bk = s + classify_meta_bytes(1);
+    uint32_t *obs = reinterpret_cast<uint32_t *>(s + classify_meta_bytes(1) +
+                                                 align256(classify_bucket_bytes(1, plan->total_len)));
+    const uint64_t *pool = reinterpret_cast<const uint64_t *>(w + plan->off_pool);
+    const uint64_t *seg = reinterpret_cast<const uint64_t *>(w + plan->off_seg);
+    const uint64_t *owo = reinterpret_cast<const uint64_t *>(w + plan->off_obs_words);
+    const int sms = sm_count();
+    PCHASE_CUDA(classify_thresholds(lat, pool, 1, plan->total_len, meta, bk, nullptr, st, sms),
+                "classify thresholds");
+    PCHASE_CUDA(classify_bits(lat, seg, 0, plan->n_trace, plan->max_trace_len, meta, obs, owo,
+                              st, sms),
+                "classify bits");
+    int rc = pchase_match_run(plan, workspace, obs, owo, UINT64_MAX, dist_out, dev_status, stream);
+    if (rc) return rc;
+    PCHASE_CUDA(canonical_pick(reinterpret_cast<const pchase_geom *>(w + plan->off_geoms), dist_out,
+                               plan->n_geom, pick_out, st),
+                "canonical pick");
+    return PCHASE_OK;
+}
+
+int pchase_probe_latency(const uint32_t *array, uint32_t n_elems, uint32_t start, uint32_t warmup,
+                         uint32_t iters, int cache_mode, uint32_t *lat_out, uint32_t *idx_out,
+                         uint32_t *overhead_out, uint32_t *dev_status, pchase_stream_t stream) {
+    if (!array || n_elems == 0 || !dev_status || (iters && (!lat_out || !idx_out)))
+        return fail(PCHASE_EINVAL, "pchase_probe_latency: bad argument");
+    if (iters > (1u << 24) || warmup > (1u << 26))
+        return fail(PCHASE_ERANGE, "pchase_probe_latency: iters or warmup above the limit");
+    if (cache_mode < 0 || cache_mode > 2) return fail(PCHASE_EINVAL, "unknown cache_mode");
+    PCHASE_CUDA(probe_latency(array, n_elems, start, warmup, iters, cache_mode, lat_out, idx_out,
+                              overhead_out, dev_status, reinterpret_cast<cudaStream_t>(stream)),
+                "latency probe");
+    return PCHASE_OK;
+}
+
+int pchase_probe_smem_bank(uint32_t max_stride, uint32_t repeats, float *cycles_out,
+                           uint32_t *degree_out, pchase_stream_t stream) {
+    if (max_stride < 1 || max_stride > 64 || repeats < 1 || repeats > 64 || !cycles_out || !degree_out)
+        return fail(PCHASE_EINVAL, "pchase_probe_smem_bank: bad argument");
+    PCHASE_CUDA(probe_smem(max_stride, repeats, cycles_out, degree_out,
+                           reinterpret_cast<cudaStream_t>(stream)),
+                "smem probe");
+    return PCHASE_OK;
+}
+
+int pchase_probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas, uint32_t threads,
+                                   uint32_t ilp, const void *src, void *dst, uint64_t bytes,
+                                   uint32_t reps, double *gbs_out, pchase_stream_t stream) {
+    if (kind < 0 || kind > 2 || (vec_bytes != 4 && vec_bytes != 16) || ctas == 0 || threads == 0 ||
+        threads > 1024 || (threads & 31) || (ilp != 1 && ilp != 2 && ilp != 4 && ilp != 8) ||
+        reps == 0 || reps > 1000 || !gbs_out || !dst || (kind != 1 && !src) || bytes == 0 ||
+        bytes % ((uint64_t)vec_bytes * ilp))
+        return fail(PCHASE_EINVAL, "pchase_probe_global_throughput: bad argument");
+    PCHASE_CUDA(probe_gmem(kind, vec_bytes, ctas, threads, ilp, src, dst, bytes, reps, gbs_out,
+                           reinterpret_cast<cudaStream_t>(stream)),
+                "throughput probe");
+    return PCHASE_OK;
+}
+
+}  // extern "C"

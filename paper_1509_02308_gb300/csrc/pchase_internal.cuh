@@ -1,0 +1,111 @@
+// Internal declarations shared by the library's translation units.
+// Device code targets sm_103a only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pchase.h"
+
+namespace pchase {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kInvalidLine = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------- division
+// Unsigned division of 32-bit n by an invariant d >= 1 with one multiply-high,
+// after Granlund & Montgomery, "Division by invariant integers using
+// multiplication" (PLDI 1994), Fig. 4.1: with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n),
+// q = (t + ((n - t) >> min(l,1))) >> max(l-1, 0).  Exact for every 32-bit n.
+struct DivMagic {
+    uint32_t d;
+    uint32_t m;
+    uint32_t s1;
+    uint32_t s2;
+};
+
+__host__ inline DivMagic make_div_magic(uint32_t d) {
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    DivMagic r;
+    r.d = d;
+    r.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+    r.s1 = l < 1 ? l : 1;
+    r.s2 = l > 1 ? l - 1 : 0;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t div_q(uint32_t n, uint32_t m, uint32_t s1, uint32_t s2) {
+    uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+}
+
+// ------------------------------------------------------------ SplitMix64
+// First output of the SplitMix64 generator (Steele, Lea & Flood, OOPSLA 2014)
+// whose state is x: advance by the golden-ratio increment, then two
+// xor-shift-multiply rounds and a final xor-shift.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Victim way of the k-th eviction of set `set` under the RANDOM policy.
+__device__ __forceinline__ uint32_t random_way(uint64_t seed, uint32_t set, uint32_t k,
+                                               uint32_t ways) {
+    uint64_t h = splitmix64(seed ^ ((uint64_t)set << 40) ^ (uint64_t)k);
+    return (uint32_t)(((h >> 32) * (uint64_t)ways) >> 32);
+}
+
+// ------------------------------------------------------------ plan items
+enum SetMode : uint8_t { kModeScan = 0, kModeTable = 1 };
+
+// One simulation item as the kernels read it (64-bit aligned, 80 bytes).
+struct SimItem {
+    const uint32_t *idx;  // NULL: analytic uniform chain
+    uint32_t len;
+    uint32_t warmup;
+    uint32_t n_elems;
+    uint32_t stride;      // analytic chains, already reduced mod n_elems
+    uint32_t ways;
+    uint32_t sets;
+    uint32_t magic_m;     // set = line mod sets, by DivMagic of `sets`
+    uint8_t s1, s2, policy, mode;
+    uint32_t lsh;         // line = index >> lsh  (b = 4 << lsh)
+    uint32_t table_n;     // line-table entries (kModeTable)
+    uint64_t seed;
+    uint64_t word_off;    // plan-owned bitmap layout
+    uint32_t out_item;    // caller's item number
+    uint32_t cand;        // matcher: candidate
+    uint32_t obs;         // matcher: observed trace
+    uint32_t arena_bytes; // state bytes this item needs
+};
+
+struct ClassLaunch {
+    uint32_t first;       // index of the class's first item in the sorted table
+    uint32_t count;
+    uint32_t arena_bytes; // per warp
+    uint32_t warps;       // per CTA
+};
+
+// Simulation output sinks.
+struct SimOut {
+    uint32_t *bitmaps;
+    const uint64_t *word_offsets;  // NULL: item.word_off
+    uint64_t *miss_counts;
+    uint32_t *status;
+    // matcher
+    const uint32_t *observed;
+    const uint64_t *obs_word_offsets;
+    uint64_t stop_above;
+    uint64_t *dist;
+};
+
+// Kernel launchers (sim.cu)
+cudaError_t launch_sim_class(const SimItem *items, const ClassLaunch &cls, uint32_t *queue,
+                             int grid, const SimOut &out, bool hamming, cudaStream_t st);
+int sim_max_ctas_per_sm(const ClassLaunch &cls, bool hamming);
+
+}  // namespace pchase

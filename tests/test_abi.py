@@ -1,0 +1,111 @@
+"""The C-ABI library loads, exports every symbol include/pchase.h declares,
+and validates its host-side arguments.  No GPU work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1509_02308_gb300 import capi as C
+from paper_1509_02308_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pchase.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_library_exports_every_declared_symbol():
+    L = C.load()
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(C.SIGNATURES), set(names) ^ set(C.SIGNATURES)
+
+
+def test_version_string():
+    assert b"sm_103a" in C.load().pchase_version()
+
+
+def _plan(geoms, traces, pairs=None):
+    L = C.load()
+    ga, ta = C.geom_array(geoms), C.trace_array(traces)
+    pa = C.pair_array(pairs) if pairs is not None else None
+    h = ctypes.c_void_p()
+    rc = L.pchase_sim_plan_create(ctypes.addressof(ga), len(geoms), ctypes.addressof(ta),
+                                  len(traces), ctypes.addressof(pa) if pa is not None else None,
+                                  len(pairs) if pairs else 0, None, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("geom,code", [
+    (W.Geom(1024, 48, 2, 8), C.EINVAL),       # b not a power of two
+    (W.Geom(1024, 32, 2, 8), C.EINVAL),       # T*a*b != C
+    (W.Geom(1024, 2, 4, 128), C.EINVAL),      # b < 4
+    (W.Geom(1024, 32, 0, 32), C.EINVAL),      # no ways
+    (W.Geom(1 << 22, 32, 1 << 17, 1), C.ERANGE),  # 131072 lines
+    (W.Geom(1024, 32, 4, 8, 7), C.EINVAL),    # unknown policy
+])
+def test_plan_rejects_bad_geometry(geom, code):
+    rc, h = _plan([geom], [(None, 10, 0, 100, 1)])
+    assert rc == code
+    assert C.load().pchase_last_error_string()
+
+
+def test_plan_rejects_bad_trace_and_pair():
+    g = W.Geom(1024, 32, 4, 8)
+    rc, _ = _plan([g], [(None, 10, 0, 0, 1)])
+    assert rc == C.EINVAL
+    rc, _ = _plan([g], [(None, 1 << 31, 0, 10, 1)])
+    assert rc == C.ERANGE
+    rc, _ = _plan([g], [(None, 10, 0, 10, 1)], pairs=[(0, 1)])
+    assert rc == C.EINVAL
+
+
+def test_plan_sizes_and_layout():
+    L = C.load()
+    geoms = [W.Geom(16384, 128, 4, 32), W.Geom(12288, 32, 96, 4, W.FIFO)]
+    traces = [(None, 100, 10, 4096, 32), (None, 33, 0, 3072, 1), (None, 0, 0, 5, 1)]
+    rc, h = _plan(geoms, traces)
+    assert rc == C.OK
+    try:
+        assert L.pchase_sim_plan_items(h) == 6
+        assert L.pchase_sim_plan_bitmap_words(h) == 2 * (4 + 2 + 0)
+        assert L.pchase_sim_plan_workspace_bytes(h) >= 256 + 6 * 80
+    finally:
+        L.pchase_sim_plan_destroy(h)
+
+
+def test_item_too_large_for_shared_memory_is_refused():
+    # fully associative 65535-line cache over a 64 Mi-element array: the line
+    # table alone exceeds the largest class
+    rc, _ = _plan([W.Geom(65535 * 32, 32, 65535, 1)], [(None, 10, 0, 1 << 26, 1)])
+    assert rc == C.ERANGE
+
+
+def test_one_shot_reports_workspace_need():
+    L = C.load()
+    ga = C.geom_array([W.Geom(16384, 128, 4, 32)])
+    ta = C.trace_array([(None, 100, 10, 4096, 32)])
+    need = ctypes.c_size_t(0)
+    rc = L.cache_sim_batch(ctypes.addressof(ga), 1, ctypes.addressof(ta), 1, None, 0, None, None,
+                           None, None, None, ctypes.byref(need), None)
+    assert rc == C.ERANGE and need.value >= 256
+
+
+def test_probe_argument_checks():
+    L = C.load()
+    g = ctypes.c_double()
+    assert L.pchase_probe_global_throughput(5, 4, 1, 32, 1, 1, 1, 64, 1, ctypes.byref(g), None) == C.EINVAL
+    assert L.pchase_probe_global_throughput(0, 8, 1, 32, 1, 1, 1, 64, 1, ctypes.byref(g), None) == C.EINVAL
+    assert L.pchase_probe_global_throughput(0, 4, 1, 33, 1, 1, 1, 64, 1, ctypes.byref(g), None) == C.EINVAL
+    assert L.pchase_probe_smem_bank(0, 1, 1, 1, None) == C.EINVAL
+    assert L.pchase_probe_smem_bank(65, 1, 1, 1, None) == C.EINVAL
+    assert L.pchase_probe_latency(1, 0, 0, 0, 1, 0, 1, 1, 1, 1, None) == C.EINVAL
+    assert L.pchase_probe_latency(1, 10, 0, 0, (1 << 24) + 1, 0, 1, 1, 1, 1, None) == C.ERANGE
+    assert L.pchase_build(0, 1, None, 10, 1, None, None, None) == C.EINVAL

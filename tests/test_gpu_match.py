@@ -1,0 +1,142 @@
+"""Parity of S4 (classification), S5 (matcher) and the canonical pick with
+the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1509_02308_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1509_02308_gb300 import api
+
+
+def synth_latency(miss: np.ndarray, seed: int, t0=100.0, tm=300.0, jitter=0.02, spikes=0.005):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lat = (t0 + tm * miss) * (1.0 + jitter * rng.standard_normal(miss.size))
+    sp = rng.random(miss.size) < spikes
+    lat[sp] *= rng.uniform(2, 10, size=int(sp.sum()))
+    return lat.astype(np.float32)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 199, 200, 201, 1000, 4097, 65536, 300001])
+def test_classify_matches_oracle(n):
+    rng = np.random.Generator(np.random.PCG64(n))
+    miss = (rng.random(n) < 0.35).astype(np.uint8)
+    lat = synth_latency(miss, n)
+    bits, w, thr = api.pchase_classify([torch.from_numpy(lat).cuda()])
+    want, wthr = oracle.classify(lat)
+    got = api.unpack_bits(bits.cpu().numpy().view(np.uint32), n)
+    assert np.float32(thr[0].item()) == np.float32(wthr)
+    assert np.array_equal(got, want)
+
+
+def test_classify_edge_cases_batch():
+    cases = [np.full(50, 7.0), np.array([5.0]), np.array([1.0, 2.0]), np.array([-3.0, 4.0, 4.0, -3.0]),
+             np.repeat([10.0, 10.0, 50.0], 100), np.arange(1000, dtype=np.float64),
+             np.concatenate([np.full(1000, 100.0), np.full(3, 1e6)]),
+             np.array([0.0, 1.0, 3.0, 6.0, 10.0, 15.0])]
+    lats = [torch.from_numpy(c.astype(np.float32)).cuda() for c in cases]
+    bits, w, thr = api.pchase_classify(lats)
+    b = bits.cpu().numpy().view(np.uint32)
+    for i, c in enumerate(cases):
+        want, wthr = oracle.classify(c.astype(np.float32))
+        got = api.unpack_bits(b[int(w[i]):], c.size)
+        assert np.float32(thr[i].item()) == np.float32(wthr), (i, thr[i].item(), wthr)
+        assert np.array_equal(got, want), i
+
+
+def small_candidates():
+    grid = W.geometry_grid(capacities=(512, 768, 1024, 1536), line_sizes=(32, 64),
+                           way_choices=(1, 2, 4, 8, 0))
+    return [W.Geom(C, b, a, T, p, 1234 + i) for i, (C, b, a, T) in enumerate(grid)
+            for p in (0, 1, 2)]
+
+
+def small_plan(C0=768):
+    runs = []
+    for nb in (C0 // 2, C0 - 4, C0, C0 + 4, C0 + 32, C0 + 36, C0 + 64, C0 + 132, 2 * C0):
+        n = nb // 4
+        runs.append(W.Run(n, 1, 3 * n, n))
+    for nb in (C0 + 64, C0 + 256, 2 * C0, 4 * C0):
+        n = nb // 4
+        runs.append(W.Run(n, 16, 3 * (n // 16), n // 16))
+    return runs
+
+
+def test_match_distances_equal_oracle():
+    cands = small_candidates()
+    runs = small_plan()
+    host = [oracle.pchase_trace(r.n_elems, r.stride, r.length) for r in runs]
+    truth = W.Geom(768, 64, 4, 3, W.LRU)
+    obs_host = [oracle.cache_sim(truth.C, truth.b, truth.ways, truth.sets, 0, t) for t in host]
+    # observed bitmaps with a few flipped bits so distances are not all 0
+    rng = np.random.Generator(np.random.PCG64(5))
+    for o in obs_host:
+        flip = rng.random(o.size) < 0.01
+        o[flip] ^= 1
+    traces = [(torch.from_numpy(t.view(np.int32)).cuda(), r.length, r.warmup, r.n_elems, r.stride)
+              for t, r in zip(host, runs)]
+    plan = api.SimPlan(cands, traces)
+    words, offs = [], [0]
+    for o in obs_host:
+        wv = np.packbits(o, bitorder="little")
+        wv = np.concatenate([wv, np.zeros((-wv.size) % 4, dtype=np.uint8)]).view(np.uint32)
+        words.append(wv)
+        offs.append(offs[-1] + wv.size)
+    obs = torch.from_numpy(np.concatenate(words).view(np.int32)).cuda()
+    owo = torch.tensor(offs[:-1], dtype=torch.int64, device="cuda")
+    dist = plan.match(obs, owo).cpu().numpy().astype(np.uint64)
+    rows = np.array([g.row() for g in cands], dtype=np.uint32)
+    seeds = np.array([g.seed for g in cands], dtype=np.uint64)
+    want = oracle.match(rows, seeds, host, obs_host)
+    assert np.array_equal(dist, want)
+    # early stop keeps every candidate at or under the bound exact
+    bound = int(np.sort(want)[5])
+    d2 = plan.match(obs, owo, stop_above=bound).cpu().numpy().astype(np.uint64)
+    assert np.array_equal(d2[want <= bound], want[want <= bound])
+    assert (d2[want > bound] > bound).all()
+    # canonical pick
+    pick = api.pchase_canonical_pick(cands, torch.from_numpy(want.astype(np.int64)).cuda())
+    pi, nb = oracle.canonical_pick(rows, want)
+    assert int(pick[0]) == pi and int(pick[1]) == nb
+
+
+def test_infer_geometry_round_trip():
+    cands = small_candidates()
+    runs = small_plan()
+    host = [oracle.pchase_trace(r.n_elems, r.stride, r.length) for r in runs]
+    traces = [(torch.from_numpy(t.view(np.int32)).cuda(), r.length, r.warmup, r.n_elems, r.stride)
+              for t, r in zip(host, runs)]
+    plan = api.SimPlan(cands, traces)
+    rows = np.array([g.row() for g in cands], dtype=np.uint32)
+    seeds = np.array([g.seed for g in cands], dtype=np.uint64)
+    for ti, truth in enumerate([cands[10], cands[37], cands[len(cands) - 5]]):
+        miss = [oracle.cache_sim(truth.C, truth.b, truth.ways, truth.sets, truth.policy, t,
+                                 seed=truth.seed) for t in host]
+        lat = np.concatenate([synth_latency(m, 100 + ti * 7 + k, spikes=0.0)
+                              for k, m in enumerate(miss)])
+        dist, pick = plan.infer(torch.from_numpy(lat).cuda())
+        torch.cuda.synchronize()
+        # oracle: same pooled classification, match, pick
+        obits, _ = oracle.classify(lat)
+        obs, o = [], 0
+        for r in runs:
+            obs.append(obits[o:o + r.length])
+            o += r.length
+        want = oracle.match(rows, seeds, host, obs)
+        assert np.array_equal(dist.cpu().numpy().astype(np.uint64), want)
+        pi, nb = oracle.canonical_pick(rows, want)
+        assert int(pick[0]) == pi and int(pick[1]) == nb
+        assert want[pi] == 0
+        # the pick is indistinguishable from the truth on this plan
+        for t in host:
+            g = cands[pi]
+            assert np.array_equal(
+                oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, t, seed=g.seed),
+                oracle.cache_sim(truth.C, truth.b, truth.ways, truth.sets, truth.policy, t,
+                                 seed=truth.seed))

@@ -1,0 +1,73 @@
+"""Probes on the GPU itself.  Hardware has no oracle, so these check
+invariants: the predicted bank degree, latency plateaus, index traces that
+equal the chain walk, and throughput below the HBM peak."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1509_02308_gb300 import api
+
+
+def test_smem_bank_degree_and_latency_shape():
+    cyc, deg = api.pchase_probe_smem_bank(64, repeats=9)
+    cyc, deg = cyc.cpu().numpy(), deg.cpu().numpy()
+    for s in range(1, 65):
+        words = [t * s for t in range(32)]
+        assert deg[s - 1] == math.gcd(s, 32) == oracle.bank_degree(words)
+    assert (cyc > 0).all()
+    by_deg = {d: np.median(cyc[deg == d]) for d in (1, 2, 4, 8, 16, 32)}
+    # latency grows with the conflict degree (Table 7's trend)
+    assert by_deg[32] > by_deg[8] > by_deg[1]
+    assert by_deg[2] >= by_deg[1] * 0.95
+
+
+def test_pchase_probe_index_trace_and_plateaus():
+    # small array: every timed access after the preheat is an L1 hit
+    n_small = 1024  # 4 KB
+    _, arr = api.pchase_build(n_small, 8, 1, with_array=True)
+    lat, idx, ovh, st = api.pchase_probe_latency(arr, n_small, iters=512, warmup=256, cache_mode=0)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    i = idx.cpu().numpy().view(np.uint32)
+    walk = oracle.pchase_trace(n_small, 8, 256 + 512)[256:]
+    assert np.array_equal(i, walk)
+    small = np.median(lat.cpu().numpy().view(np.uint32))
+    o = ovh.cpu().numpy()
+    assert o[0] > 0 and o[1] > 0
+    # large array, 4 KB stride, L2-only loads: every access leaves the SM
+    n_big = 64 << 20  # 256 MB
+    _, arr2 = api.pchase_build(n_big, 1024, 1, with_array=True)
+    lat2, idx2, _, st2 = api.pchase_probe_latency(arr2, n_big, iters=2048, warmup=0, cache_mode=1)
+    torch.cuda.synchronize()
+    assert int(st2.item()) == 0
+    big = np.median(lat2.cpu().numpy().view(np.uint32))
+    assert big > 2 * small, (small, big)
+    assert np.array_equal(idx2.cpu().numpy().view(np.uint32),
+                          (np.arange(2048, dtype=np.uint64) * 1024 % n_big).astype(np.uint32))
+
+
+def test_pchase_probe_bad_chain_sets_status():
+    chain = torch.tensor([1, 2, 100, 0], dtype=torch.int32, device="cuda")
+    lat, idx, ovh, st = api.pchase_probe_latency(chain, 4, iters=8)
+    torch.cuda.synchronize()
+    assert int(st.item()) & 2
+
+
+def test_global_throughput_is_plausible():
+    nbytes = 1 << 30
+    a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    res = {}
+    for kind in (0, 1, 2):
+        res[kind] = api.pchase_probe_global_throughput(kind, 16, sms * 4, 256, 4, a, b, nbytes, reps=5)
+        assert 500.0 < res[kind] < 8000.0 * 1.05, (kind, res[kind])
+    small = api.pchase_probe_global_throughput(2, 4, 1, 32, 1, a, b, 1 << 20, reps=3)
+    assert 0 < small < res[2]
