@@ -137,6 +137,8 @@ typedef struct {
     uint32_t smem_budget_bytes;  /* shared memory per CTA (default 96 KB) */
     uint32_t max_warps_per_cta;  /* (default 16) */
     uint32_t ctas_per_sm_cap;    /* 0 = as many as fit */
+    uint32_t batch_max_sets;     /* T <= this: whole-step batch resolution per set (default 8;
+                                    0 keeps the default, 0xFFFFFFFF disables batch mode) */
 } pchase_tune;
 
 typedef struct pchase_sim_plan pchase_sim_plan;
@@ -162,6 +164,8 @@ size_t pchase_sim_plan_workspace_bytes(const pchase_sim_plan *plan);
 /* Number of items, and of bitmap words when the plan lays bitmaps out itself. */
 uint64_t pchase_sim_plan_items(const pchase_sim_plan *plan);
 uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);
+/* Kernel launches one pchase_sim_run (or pchase_match_run) queues. */
+uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
 
 /*
  * Copies the plan's tables into `workspace` (device, at least
@@ -251,14 +255,16 @@ int pchase_canonical_pick(const pchase_geom *geoms, const uint64_t *dist, uint32
  * S4 + S5 in one call for one observation: classify the latencies of all plan
  * traces together, match against every candidate, pick.  lat (device float)
  * holds the plan traces' latencies back to back in trace order; the plan must
- * be a candidates x traces plan whose workspace was uploaded.  Outputs (device):
+ * be a candidates x traces plan whose workspace was uploaded.  stop_above as
+ * in pchase_match_run (UINT64_MAX: every distance exact; a bound B keeps the
+ * pick exact whenever some candidate is within B).  Outputs (device):
  * dist_out[n_cand] (uint64), pick_out[2] (uint32).  Extra device work buffer
  * `scratch` of pchase_infer_scratch_bytes(plan).
  */
 size_t pchase_infer_scratch_bytes(const pchase_sim_plan *plan);
 int infer_geometry(const pchase_sim_plan *plan, void *workspace, const float *lat,
-                   void *scratch, uint64_t *dist_out, uint32_t *pick_out, uint32_t *dev_status,
-                   pchase_stream_t stream);
+                   void *scratch, uint64_t stop_above, uint64_t *dist_out, uint32_t *pick_out,
+                   uint32_t *dev_status, pchase_stream_t stream);
 
 /* --------------------------------------------------------------- S8-S10 */
 

@@ -70,7 +70,8 @@ class SimPlan:
         tn = None
         if tune:
             tn = C.Tune(tune.get("scan_max_ways", 0), tune.get("smem_budget_bytes", 0),
-                        tune.get("max_warps_per_cta", 0), tune.get("ctas_per_sm_cap", 0))
+                        tune.get("max_warps_per_cta", 0), tune.get("ctas_per_sm_cap", 0),
+                        tune.get("batch_max_sets", 0))
         h = ctypes.c_void_p()
         C.check(self.L.pchase_sim_plan_create(
             ctypes.addressof(ga), len(self.geoms), ctypes.addressof(ta), len(self.traces),
@@ -81,6 +82,7 @@ class SimPlan:
         self.n_items = int(self.L.pchase_sim_plan_items(h))
         self.bitmap_words = int(self.L.pchase_sim_plan_bitmap_words(h))
         self.ws_bytes = int(self.L.pchase_sim_plan_workspace_bytes(h))
+        self.launches = int(self.L.pchase_sim_plan_launches(h))
         self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=DEV)
         self._ws = (C.ptr(self.workspace) + 255) & ~255
         C.check(self.L.pchase_sim_plan_upload(h, self._ws, self.ws_bytes, C.stream_handle(stream)))
@@ -120,15 +122,15 @@ class SimPlan:
                                         C.stream_handle(stream)))
         return dist
 
-    def infer(self, lat: torch.Tensor, status=None, stream=None):
+    def infer(self, lat: torch.Tensor, stop_above: int = 2**64 - 1, status=None, stream=None):
         scratch_b = int(self.L.pchase_infer_scratch_bytes(self.h))
         if getattr(self, "_scratch", None) is None or self._scratch.numel() < scratch_b + 256:
             self._scratch = torch.empty(scratch_b + 256, dtype=torch.uint8, device=DEV)
         sp = (C.ptr(self._scratch) + 255) & ~255
         dist = torch.empty(max(1, len(self.geoms)), dtype=torch.int64, device=DEV)
         pick = torch.empty(2, dtype=torch.int32, device=DEV)
-        C.check(self.L.infer_geometry(self.h, self._ws, C.ptr(lat), sp, C.ptr(dist), C.ptr(pick),
-                                      C.ptr(status), C.stream_handle(stream)))
+        C.check(self.L.infer_geometry(self.h, self._ws, C.ptr(lat), sp, stop_above, C.ptr(dist),
+                                      C.ptr(pick), C.ptr(status), C.stream_handle(stream)))
         return dist, pick
 
 

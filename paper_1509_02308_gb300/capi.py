@@ -39,7 +39,8 @@ class Pair(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("scan_max_ways", _c_u32), ("smem_budget_bytes", _c_u32),
-                ("max_warps_per_cta", _c_u32), ("ctas_per_sm_cap", _c_u32)]
+                ("max_warps_per_cta", _c_u32), ("ctas_per_sm_cap", _c_u32),
+                ("batch_max_sets", _c_u32)]
 
 
 assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32
@@ -54,6 +55,7 @@ SIGNATURES = {
     "pchase_sim_plan_workspace_bytes": (ctypes.c_size_t, [_c_p]),
     "pchase_sim_plan_items": (_c_u64, [_c_p]),
     "pchase_sim_plan_bitmap_words": (_c_u64, [_c_p]),
+    "pchase_sim_plan_launches": (_c_u32, [_c_p]),
     "pchase_sim_plan_upload": (ctypes.c_int, [_c_p, _c_p, ctypes.c_size_t, _c_p]),
     "pchase_sim_run": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
     "cache_sim_batch": (ctypes.c_int, [_c_p, _c_u32, _c_p, _c_u32, _c_p, _c_u32, _c_p, _c_p, _c_p,
@@ -63,7 +65,7 @@ SIGNATURES = {
     "pchase_match_run": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_u64, _c_p, _c_p, _c_p]),
     "pchase_canonical_pick": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_p, _c_p]),
     "pchase_infer_scratch_bytes": (ctypes.c_size_t, [_c_p]),
-    "infer_geometry": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "infer_geometry": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_u64, _c_p, _c_p, _c_p, _c_p]),
     "pchase_probe_latency": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.c_int,
                                             _c_p, _c_p, _c_p, _c_p, _c_p]),
     "pchase_probe_smem_bank": (ctypes.c_int, [_c_u32, _c_u32, _c_p, _c_p, _c_p]),

@@ -248,8 +248,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     *plan_out = nullptr;
     if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
         return fail(PCHASE_EINVAL, "NULL descriptor array");
-    pchase_tune tn{8, 96 * 1024, 16, 0};
+    pchase_tune tn{8, 96 * 1024, 16, 0, 8};
     if (tune) {
+        if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
         if (tune->smem_budget_bytes) tn.smem_budget_bytes = std::min(tune->smem_budget_bytes, kMaxArena);
         if (tune->max_warps_per_cta) tn.max_warps_per_cta = std::min<uint32_t>(tune->max_warps_per_cta, 16);
@@ -332,7 +333,19 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         it.obs = t;
         const uint64_t lines = (uint64_t)G.sets * G.ways;
         uint64_t arena;
-        if (G.ways <= tn.scan_max_ways) {
+        uint32_t ring = 256;
+        while (ring < G.ways + 128) ring <<= 1;
+        const uint32_t table_n = ((Tr.n_elems - 1) >> it.lsh) + 1;
+        uint64_t batch_arena = 256 + 16ull * G.sets + 2ull * table_n;
+        if (G.policy == PCHASE_LRU) batch_arena += 4ull * G.sets * ring;
+        else batch_arena += ((4 * lines + 15) & ~15ull) + (G.policy == PCHASE_RANDOM ? 8 * lines : 0);
+        batch_arena = align16(batch_arena);
+        if (G.sets <= tn.batch_max_sets && batch_arena <= kMaxArena && ring <= 32768) {
+            it.mode = kModeBatch;
+            it.table_n = table_n;
+            it.ring = ring;
+            arena = batch_arena;
+        } else if (G.ways <= tn.scan_max_ways) {
             it.mode = kModeScan;
             arena = 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * G.sets : 0);
         } else {
@@ -364,9 +377,20 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     }
     std::vector<uint64_t> order(n_items);
     for (uint64_t i = 0; i < n_items; ++i) order[i] = i;
+    // expected cost: steps x rounds a step needs (heads of one set act in turn
+    // in scan and table mode; batch mode resolves a set's heads together)
+    std::vector<double> cost(n_items);
+    for (uint64_t i = 0; i < n_items; ++i) {
+        const SimItem &x = items[i];
+        const double steps = (x.len + 31) / 32;
+        double rounds = 1.0;
+        if (x.mode != kModeBatch) rounds = std::max(1.0, 32.0 / std::max(1u, x.sets));
+        else rounds = 1.5 + 0.25 * x.sets;
+        cost[i] = steps * (1.0 + 0.5 * rounds) * (x.mode == kModeTable ? 1.5 : 1.0);
+    }
     std::stable_sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
         if (cls[x] != cls[y]) return cls[x] > cls[y];
-        return items[x].len > items[y].len;
+        return cost[x] > cost[y];
     });
     p->items.reserve(n_items);
     for (uint64_t k = 0; k < n_items; ++k) p->items.push_back(items[order[k]]);
@@ -414,6 +438,9 @@ size_t pchase_sim_plan_workspace_bytes(const pchase_sim_plan *plan) {
 uint64_t pchase_sim_plan_items(const pchase_sim_plan *plan) { return plan ? plan->n_items : 0; }
 uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan) {
     return plan ? plan->bitmap_words : 0;
+}
+uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
+    return plan ? (uint32_t)plan->classes.size() : 0;
 }
 
 int pchase_sim_plan_upload(const pchase_sim_plan *plan, void *workspace, size_t workspace_bytes,
@@ -539,8 +566,8 @@ size_t pchase_infer_scratch_bytes(const pchase_sim_plan *plan) {
 }
 
 int infer_geometry(const pchase_sim_plan *plan, void *workspace, const float *lat, void *scratch,
-                   uint64_t *dist_out, uint32_t *pick_out, uint32_t *dev_status,
-                   pchase_stream_t stream) {
+                   uint64_t stop_above, uint64_t *dist_out, uint32_t *pick_out,
+                   uint32_t *dev_status, pchase_stream_t stream) {
     if (!plan || !workspace || !lat || !scratch || !dist_out || !pick_out)
         return fail(PCHASE_EINVAL, "infer_geometry: NULL argument");
     if (!plan->cross) return fail(PCHASE_EINVAL, "infer_geometry needs a candidates x traces plan");
@@ -560,7 +587,7 @@ int infer_geometry(const pchase_sim_plan *plan, void *workspace, const float *la
     PCHASE_CUDA(classify_bits(lat, seg, 0, plan->n_trace, plan->max_trace_len, meta, obs, owo,
                               st, sms),
                 "classify bits");
-    int rc = pchase_match_run(plan, workspace, obs, owo, UINT64_MAX, dist_out, dev_status, stream);
+    int rc = pchase_match_run(plan, workspace, obs, owo, stop_above, dist_out, dev_status, stream);
     if (rc) return rc;
     PCHASE_CUDA(canonical_pick(reinterpret_cast<const pchase_geom *>(w + plan->off_geoms), dist_out,
                                plan->n_geom, pick_out, st),

@@ -60,9 +60,9 @@ __device__ __forceinline__ uint32_t random_way(uint64_t seed, uint32_t set, uint
 }
 
 // ------------------------------------------------------------ plan items
-enum SetMode : uint8_t { kModeScan = 0, kModeTable = 1 };
+enum SetMode : uint8_t { kModeScan = 0, kModeTable = 1, kModeBatch = 2 };
 
-// One simulation item as the kernels read it (64-bit aligned, 80 bytes).
+// One simulation item as the kernels read it (64-bit aligned, 88 bytes).
 struct SimItem {
     const uint32_t *idx;  // NULL: analytic uniform chain
     uint32_t len;
@@ -81,6 +81,8 @@ struct SimItem {
     uint32_t cand;        // matcher: candidate
     uint32_t obs;         // matcher: observed trace
     uint32_t arena_bytes; // state bytes this item needs
+    uint32_t ring;        // batch-mode LRU: recency ring entries per set (power of two)
+    uint32_t pad;
 };
 
 struct ClassLaunch {

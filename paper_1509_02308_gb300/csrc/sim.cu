@@ -10,20 +10,23 @@
 //   * one warp per item (geometry x trace), pulled from a per-class atomic
 //     queue by persistent CTAs; the item's whole cache state lives in the
 //     warp's slice of shared memory;
-//   * the warp streams the trace 32 consecutive accesses at a time (one
-//     coalesced 128-byte load; analytic uniform chains are generated in
-//     registers instead), decodes set and line in registers, and marks the
-//     accesses that repeat the previous access's line: such an access is a hit
-//     under every policy and changes no recency order, so only run heads touch
-//     set state;
-//   * heads in different sets are independent, heads in the same set must go
-//     in trace order: __match_any_sync groups the heads by set, and a head of
-//     rank r inside its group acts in round r;
-//   * one access is resolved by one lane: "scan" sets (few ways) keep
-//     {line, stamp} per way and scan them; "table" sets (many ways) find the
-//     way through a per-item line table (line -> way + 1) and keep LRU order
-//     as a doubly linked list, FIFO order as a ring pointer;
-//   * miss bits come from __ballot_sync, 32 steps are buffered one word per
+//   * the warp streams the trace 32 consecutive accesses per step (coalesced
+//     128-byte loads issued six steps ahead; analytic uniform chains are
+//     generated in registers instead), decodes set and line in registers, and
+//     marks accesses that repeat the previous access's line: such an access
+//     hits under every policy and changes no replacement order, so only run
+//     heads touch set state;
+//   * heads in different sets are independent; heads in one set must act in
+//     trace order.  Three set modes:
+//       scan  (few ways, many sets): a head of rank r among the step's heads
+//             of its set acts in round r (__match_any_sync groups them); the
+//             lane scans the set's {line, stamp} ways;
+//       table (many ways, many sets): the same rounds, with a per-item line
+//             table (line -> way + 1), LRU order as a doubly linked list and
+//             FIFO order as a ring pointer;
+//       batch (few sets): all heads of a set are resolved together, one lane
+//             each, without rounds (see the batch section below);
+//   * miss bits come from __ballot_sync; 32 steps are buffered one word per
 //     lane and stored as one coalesced 128-byte write.
 #include "pchase_internal.cuh"
 
@@ -41,6 +44,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 constexpr uint16_t kNil = 0xFFFF;
+constexpr int32_t kBig = 0x3FFFFFFF;
+constexpr uint32_t kStale = 0xFFFFFFFFu;
 
 // ----------------------------------------------------------- scan sets
 // Arena: uint2 slot[T*a] = {line, stamp}; RANDOM adds uint32 evictions[T].
@@ -198,10 +203,413 @@ struct TableSets {
     }
 };
 
-// --------------------------------------------------------------- item loop
+// Rounds driver for scan and table sets: a head of rank r inside its set's
+// group of heads acts in round r.
 template <typename Sets>
-__device__ __forceinline__ void run_item(const SimItem &it, Sets &S, const SimOut &out,
-                                         int lane) {
+struct RoundResolver {
+    Sets S;
+    __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t t,
+                                            int lane, uint32_t lt, uint32_t) {
+        const uint32_t key = head ? set : (0x80000000u | (uint32_t)lane);
+        const uint32_t peers = __match_any_sync(kFull, key);
+        const uint32_t rank = __popc(peers & lt);
+        const uint32_t rounds = __reduce_max_sync(kFull, head ? rank + 1 : 0u);
+        bool miss = false;
+        for (uint32_t r = 0; r < rounds; ++r) {
+            if (head && rank == r) miss = S.access(set, line, t);
+            __syncwarp();
+        }
+        return miss;
+    }
+};
+
+// ------------------------------------------------------------ batch sets
+// For items with few sets each step has many heads per set.  The step's heads
+// are first regrouped so every set's heads sit on consecutive lanes in trace
+// order; then each set's group is resolved at once.
+//
+// FIFO and RANDOM: the k-th miss of a group (k = 0, 1, ...) goes to a way
+// fixed in advance (FIFO: (p + L + k) mod a; RANDOM: the lowest invalid way
+// while the set fills, then the SplitMix64 way of its eviction number).  A
+// line held in way w is evicted by the first miss k whose way is w (its
+// eviction index e); an access misses exactly when the number of misses
+// before it in its group exceeds the eviction index of its line, and a line
+// inserted by miss k next leaves at the next k' > k with the same way.  The
+// outcome vector is the fixed point of that rule; any fixed point equals the
+// sequential answer (a lane depends only on earlier lanes), and 32 rounds of
+// the rule reach it from any start, usually 1-2 from the start used here.
+//
+// LRU: by the stack property an access hits exactly when fewer than a
+// distinct lines were used since the previous use of its line.  Recency is a
+// per-set ring of lines in use order (an entry goes stale when its line is
+// used again); the 32 oldest live entries (the tail window) give the exact
+// depth of every line that could fall out within one step, every other
+// resident line is a sure hit.  After the decisions the step's lines are
+// appended in last-use order and the oldest non-step lines are evicted so
+// that a lines stay live; the ring is compacted when it nears full.
+struct Grouped {
+    uint32_t x, set;   // line and set of the head now on this lane
+    bool act;          // lane holds a head
+    uint32_t gmask;    // lanes of this head's set group
+    uint32_t gb;       // first lane of the group
+    uint32_t dest;     // where this lane's own head went
+};
+
+__device__ __forceinline__ Grouped group_heads(uint32_t line, uint32_t set, bool head, int lane,
+                                               uint32_t lt, uint32_t *perm) {
+    const uint32_t key = head ? set : (0x80000000u | (uint32_t)lane);
+    const uint32_t gm = __match_any_sync(kFull, key);
+    const bool leader = head && (gm & lt) == 0;
+    const uint32_t size = leader ? (uint32_t)__popc(gm) : 0u;
+    uint32_t inc = size;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += v;
+    }
+    const uint32_t base = __shfl_sync(kFull, inc - size, __ffs(gm) - 1);
+    const uint32_t dest = base + __popc(gm & lt);
+    const uint32_t nh = __popc(__ballot_sync(kFull, head));
+    if (head) perm[dest] = (uint32_t)lane;
+    __syncwarp();
+    const bool act = (uint32_t)lane < nh;
+    const uint32_t src = act ? perm[lane] : (uint32_t)lane;
+    __syncwarp();
+    Grouped g;
+    g.x = __shfl_sync(kFull, line, src);
+    g.set = __shfl_sync(kFull, set, src);
+    g.act = act;
+    g.gmask = __match_any_sync(kFull, act ? g.set : (0x80000000u | (uint32_t)lane));
+    g.gb = __ffs(g.gmask) - 1;
+    g.dest = dest;
+    return g;
+}
+
+// mask of lanes whose key is below this lane's threshold (keys, thresholds < 64)
+__device__ __forceinline__ uint32_t lanes_below(uint32_t key, uint32_t thr) {
+    uint32_t less = 0, eq = kFull;
+#pragma unroll
+    for (int b = 5; b >= 0; --b) {
+        const uint32_t plane = __ballot_sync(kFull, (key >> b) & 1u);
+        if ((thr >> b) & 1u) {
+            less |= eq & ~plane;
+            eq &= plane;
+        } else {
+            eq &= ~plane;
+        }
+    }
+    return less;
+}
+
+// FIFO / RANDOM.  Arena: uint4 meta[T] ({p, L} or {filled, evictions});
+// uint32 sline[T*a]; (RANDOM) uint2 scr[T*a]; uint16 tab[table_n] (way + 1).
+template <int POLICY>
+struct BatchFR {
+    uint4 *meta;
+    uint32_t *sline;
+    uint2 *scr;
+    uint16_t *tab;
+    uint32_t *perm;
+    uint32_t ways;
+    uint64_t seed;
+
+    __device__ __forceinline__ void init(uint8_t *arena, const SimItem &it, int lane) {
+        ways = it.ways;
+        seed = it.seed;
+        const uint32_t n = it.sets * ways;
+        size_t off = 0;
+        perm = reinterpret_cast<uint32_t *>(arena);
+        off += 256;
+        meta = reinterpret_cast<uint4 *>(arena + off);
+        off += 16ull * it.sets;
+        sline = reinterpret_cast<uint32_t *>(arena + off);
+        off += (4ull * n + 15) & ~15ull;
+        if (POLICY == PCHASE_RANDOM) {
+            scr = reinterpret_cast<uint2 *>(arena + off);
+            off += 8ull * n;
+        }
+        tab = reinterpret_cast<uint16_t *>(arena + off);
+        for (uint32_t i = lane; i < it.sets; i += 32) meta[i] = make_uint4(0, 0, 0, 0);
+        for (uint32_t i = lane; i < n; i += 32) sline[i] = kInvalidLine;
+        if (POLICY == PCHASE_RANDOM)
+            for (uint32_t i = lane; i < n; i += 32) scr[i] = make_uint2(0, 0);
+        uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
+        for (uint32_t i = lane; i < (it.table_n + 1) / 2; i += 32) t32[i] = 0;
+    }
+
+    __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t,
+                                            int lane, uint32_t lt, uint32_t stamp) {
+        if (__ballot_sync(kFull, head) == 0) return false;
+        const Grouped g = group_heads(line, set, head, lane, lt, perm);
+        const uint32_t a = ways;
+        const uint32_t ltg = g.gmask & lt;
+        const uint32_t r = (uint32_t)lane - g.gb;
+        const uint4 m = g.act ? meta[g.set] : make_uint4(0, 0, 0, 0);
+        const uint32_t w1 = g.act ? tab[g.x] : 0u;
+        const uint32_t lm = __match_any_sync(kFull, g.act ? g.x : (0x80000000u | (uint32_t)lane));
+        const uint32_t pm = lm & lt;
+        const int prev = pm ? 31 - __clz(pm) : -1;
+        // way of the group's r-th miss, and whether it evicts
+        uint32_t insw;
+        bool evicts;
+        if (POLICY == PCHASE_FIFO) {
+            evicts = m.y + r >= a;
+            insw = (m.x + m.y + r) % a;
+        } else {
+            const uint32_t k = m.x + r;
+            evicts = k >= a;
+            insw = evicts ? random_way(seed, g.set, m.y + (k - a), a) : k;
+        }
+        // next group rank with the same way
+        const uint32_t sw = __match_any_sync(kFull, g.act ? g.set * a + insw
+                                                           : (0x80000000u | (uint32_t)lane));
+        const uint32_t above = sw & ~(lt | (1u << lane));
+        const int32_t nx = above ? (int32_t)(__ffs(above) - 1 - g.gb) : kBig;
+        // eviction index of this line's way (first group rank targeting it)
+        int32_t e0 = -1;
+        if (POLICY == PCHASE_FIFO) {
+            if (w1) e0 = (int32_t)(((w1 - 1 + a - m.x) % a) + (a - m.y));
+        } else {
+            if (g.act && (sw & lt) == 0) scr[g.set * a + insw] = make_uint2(stamp, r);
+            __syncwarp();
+            if (w1) {
+                const uint2 q = scr[g.set * a + w1 - 1];
+                e0 = q.x == stamp ? (int32_t)q.y : kBig;
+            }
+        }
+        // fixed point over (miss, eviction index after this access)
+        bool miss = g.act && (w1 == 0 ? prev < 0 : e0 < (int32_t)r);
+        int32_t eaft = miss ? kBig : e0;
+        for (int it = 0; it < 33; ++it) {
+            const uint32_t bal = __ballot_sync(kFull, miss);
+            const int32_t mi = __popc(bal & ltg);
+            const int32_t pe = __shfl_sync(kFull, eaft, prev < 0 ? lane : prev);
+            const int32_t epre = prev < 0 ? e0 : pe;
+            const bool nm = g.act && mi > epre;
+            const int32_t nxm = __shfl_sync(kFull, nx, (g.gb + (uint32_t)mi) & 31u);
+            const int32_t ne = nm ? nxm : epre;
+            const bool same = nm == miss && ne == eaft;
+            miss = nm;
+            eaft = ne;
+            if (__all_sync(kFull, same)) break;
+        }
+        // state update
+        const uint32_t bal = __ballot_sync(kFull, miss);
+        const uint32_t mi = __popc(bal & ltg);
+        const uint32_t M = __popc(bal & g.gmask);
+        const uint32_t myw = __shfl_sync(kFull, insw, (g.gb + mi) & 31u);
+        const bool myev = __shfl_sync(kFull, evicts ? 1u : 0u, (g.gb + mi) & 31u) != 0;
+        const uint32_t smw = __match_any_sync(kFull, miss ? g.set * a + myw
+                                                         : (0x80000000u | (uint32_t)lane));
+        const uint32_t below = smw & lt;
+        const bool last = miss && (smw & ~(lt | (1u << lane))) == 0;
+        const uint32_t prev_line = __shfl_sync(kFull, g.x, below ? 31 - __clz(below) : lane);
+        if (miss && (below || myev)) {
+            const uint32_t old = below ? prev_line : sline[g.set * a + myw];
+            tab[old] = 0;
+        }
+        __syncwarp();
+        if (last) {
+            sline[g.set * a + myw] = g.x;
+            tab[g.x] = (uint16_t)(myw + 1);
+        }
+        if (g.act && (uint32_t)lane == g.gb) {
+            uint4 n = m;
+            if (POLICY == PCHASE_FIFO) {
+                const uint32_t tot = m.y + M;
+                n.y = tot < a ? tot : a;
+                n.x = (m.x + (tot > a ? tot - a : 0u)) % a;
+            } else {
+                const uint32_t tot = m.x + M;
+                n.x = tot < a ? tot : a;
+                n.y = m.y + (tot > a ? tot - a : 0u);
+            }
+            meta[g.set] = n;
+        }
+        __syncwarp();
+        return __shfl_sync(kFull, miss ? 1u : 0u, head ? g.dest : (uint32_t)lane) != 0 && head;
+    }
+};
+
+// LRU.  Arena: uint32 perm[32] + window scratch[16]; uint4 meta[T] =
+// {tail, head, live, -} (monotone ring positions); uint32 ring[T*R];
+// uint16 tab[table_n] (ring index + 1).
+struct BatchLRU {
+    uint4 *meta;
+    uint32_t *ring;
+    uint16_t *tab;
+    uint32_t *perm, *wsc;
+    uint32_t ways, R, rmask;
+
+    __device__ __forceinline__ void init(uint8_t *arena, const SimItem &it, int lane) {
+        ways = it.ways;
+        R = it.ring;
+        rmask = R - 1;
+        size_t off = 0;
+        perm = reinterpret_cast<uint32_t *>(arena);
+        wsc = perm + 32;
+        off += 256;
+        meta = reinterpret_cast<uint4 *>(arena + off);
+        off += 16ull * it.sets;
+        ring = reinterpret_cast<uint32_t *>(arena + off);
+        off += 4ull * it.sets * R;
+        tab = reinterpret_cast<uint16_t *>(arena + off);
+        for (uint32_t i = lane; i < it.sets; i += 32) meta[i] = make_uint4(0, 0, 0, 0);
+        uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
+        for (uint32_t i = lane; i < (it.table_n + 1) / 2; i += 32) t32[i] = 0;
+    }
+
+    // Moves the live entries of [tail, head) down to start at tail.
+    __device__ __forceinline__ uint4 compact(uint32_t set, uint4 m, int lane, uint32_t lt) {
+        uint32_t *rg = ring + (size_t)set * R;
+        uint32_t done = 0;
+        for (uint32_t p0 = m.x; p0 < m.y; p0 += 32) {
+            const uint32_t p = p0 + (uint32_t)lane;
+            const uint32_t e = p < m.y ? rg[p & rmask] : kStale;
+            const bool live = e != kStale;
+            const uint32_t bal = __ballot_sync(kFull, live);
+            __syncwarp();
+            if (live) {
+                const uint32_t d = (m.x + done + __popc(bal & lt)) & rmask;
+                rg[d] = e;
+                tab[e] = (uint16_t)(d + 1);
+            }
+            __syncwarp();
+            done += __popc(bal);
+        }
+        m.y = m.x + done;
+        if (lane == 0) meta[set] = m;
+        __syncwarp();
+        return m;
+    }
+
+    __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t,
+                                            int lane, uint32_t lt, uint32_t) {
+        if (__ballot_sync(kFull, head) == 0) return false;
+        const Grouped g = group_heads(line, set, head, lane, lt, perm);
+        const uint32_t a = ways;
+        const uint32_t lm = __match_any_sync(kFull, g.act ? g.x : (0x80000000u | (uint32_t)lane));
+        const uint32_t pm = lm & lt;
+        const int prev = pm ? 31 - __clz(pm) : -1;
+        const bool first = g.act && prev < 0;
+        const bool lastocc = g.act && (lm & ~(lt | (1u << lane))) == 0;
+        bool miss = false;
+        uint32_t leaders = __ballot_sync(kFull, g.act && (uint32_t)lane == g.gb);
+        while (leaders) {
+            const uint32_t gl = __ffs(leaders) - 1;
+            leaders &= leaders - 1;
+            const uint32_t s = __shfl_sync(kFull, g.set, gl);
+            const uint32_t gm = __shfl_sync(kFull, g.gmask, gl);
+            const bool mine = (gm >> lane) & 1u;
+            uint32_t *rg = ring + (size_t)s * R;
+            uint4 m = meta[s];
+            if (m.y - m.x > R - 64) m = compact(s, m, lane, lt);
+            // tail window: chunks of 32 positions until 32 live entries
+            uint32_t nlive = 0, nch = 0;
+            for (int pass = 0; pass < 2; ++pass) {
+                nlive = 0;
+                nch = 0;
+                for (uint32_t c = 0; c < 8; ++c) {
+                    const uint32_t p = m.x + 32 * c + (uint32_t)lane;
+                    const uint32_t e = p < m.y ? rg[p & rmask] : kStale;
+                    const uint32_t bal = __ballot_sync(kFull, e != kStale);
+                    if (lane == 0) {
+                        wsc[c] = bal;
+                        wsc[8 + c] = nlive;
+                    }
+                    nlive += __popc(bal);
+                    nch = c + 1;
+                    if (nlive >= 32 || m.x + 32 * (c + 1) >= m.y) break;
+                }
+                if (nlive >= 32 || m.x + 32 * nch >= m.y) break;
+                m = compact(s, m, lane, lt);  // stale entries hid the window
+            }
+            __syncwarp();
+            // depth of each head's line
+            const uint32_t w1 = mine ? tab[g.x] : 0u;
+            uint32_t rank = 32;  // 32: resident above the window (sure hit)
+            if (w1) {
+                const uint32_t off = (w1 - 1 - m.x) & rmask;
+                const uint32_t c = off >> 5;
+                if (c < nch) {
+                    const uint32_t rk = wsc[8 + c] + __popc(wsc[c] & ((1u << (off & 31)) - 1u));
+                    if (rk < 32) rank = rk;
+                }
+            }
+            // lines older than this one or new, first used earlier in the step
+            const uint32_t key = (mine && first) ? (w1 == 0 ? 0u : rank + 1) : 63u;
+            const uint32_t older = lanes_below(key, rank + 1) & gm & lt;
+            // distinct lines strictly between a repeat and its previous use
+            const uint32_t pkey = mine ? (uint32_t)(prev + 1) : 63u;
+            const uint32_t pthr = prev < 0 ? 0u : (uint32_t)prev + 1;
+            const uint32_t between = lanes_below(pkey, pthr) & gm & lt &
+                                     ~((prev < 0) ? 0u : ((2u << prev) - 1u));
+            if (mine) {
+                if (first) {
+                    if (w1 == 0) miss = true;
+                    else if (rank < 32) miss = (m.z - 1 - rank) + __popc(older) >= a;
+                } else {
+                    miss = (uint32_t)__popc(between) >= a;
+                }
+            }
+            // ----- update this set
+            const uint32_t D = __popc(__ballot_sync(kFull, mine && lastocc));
+            const uint32_t Rb = __popc(__ballot_sync(kFull, mine && first && w1 != 0));
+            if (mine && first && w1) rg[w1 - 1] = kStale;
+            __syncwarp();
+            const uint32_t keep_old = D <= a ? a - D : 0u;
+            const uint32_t old_live = m.z - Rb;
+            const uint32_t E = old_live > keep_old ? old_live - keep_old : 0u;
+            uint32_t done = 0;
+            uint32_t new_tail = m.x + 32 * nch < m.y ? m.x + 32 * nch : m.y;
+            bool tail_set = false;
+            for (uint32_t c = 0; c < nch; ++c) {
+                const uint32_t p = m.x + 32 * c + (uint32_t)lane;
+                const uint32_t e = p < m.y ? rg[p & rmask] : kStale;
+                const bool live = e != kStale;
+                const uint32_t bal = __ballot_sync(kFull, live);
+                const uint32_t rk = done + __popc(bal & lt);
+                const bool ev = live && rk < E;
+                if (ev) {
+                    tab[e] = 0;
+                    rg[p & rmask] = kStale;
+                }
+                const uint32_t keep = __ballot_sync(kFull, live && !ev);
+                if (!tail_set && keep) {
+                    new_tail = m.x + 32 * c + (__ffs(keep) - 1);
+                    tail_set = true;
+                }
+                done += __popc(bal);
+            }
+            // append the step's lines in last-use order
+            const uint32_t q = __popc(__ballot_sync(kFull, mine && lastocc) & lt);
+            if (mine && lastocc) {
+                const uint32_t p = (m.y + q) & rmask;
+                if (D > a && q < D - a) {
+                    rg[p] = kStale;
+                    tab[g.x] = 0;
+                } else {
+                    rg[p] = g.x;
+                    tab[g.x] = (uint16_t)(p + 1);
+                }
+            }
+            if (lane == 0) {
+                uint4 n;
+                n.x = new_tail;
+                n.y = m.y + D;
+                n.z = D <= a ? old_live - E + D : a;
+                n.w = 0;
+                meta[s] = n;
+            }
+            __syncwarp();
+        }
+        return __shfl_sync(kFull, miss ? 1u : 0u, head ? g.dest : (uint32_t)lane) != 0 && head;
+    }
+};
+
+// --------------------------------------------------------------- item loop
+template <typename Res>
+__device__ __forceinline__ void run_item(const SimItem &it, Res &R, const SimOut &out, int lane) {
     const uint32_t len = it.len;
     const uint32_t *__restrict__ idxp = it.idx;
     const uint32_t N = it.n_elems;
@@ -222,16 +630,26 @@ __device__ __forceinline__ void run_item(const SimItem &it, Sets &S, const SimOu
         ainc = (uint32_t)((32ull * it.stride) % N);
     }
     const uint32_t nsteps = (len + 31) >> 5;
-    uint32_t nxt = (idxp && (uint32_t)lane < len) ? idxp[lane] : 0;
+    // explicit traces: loads issued six steps ahead
+    auto fetch = [&](uint32_t st) -> uint32_t {
+        const uint32_t t = (st << 5) + (uint32_t)lane;
+        return (idxp && t < len) ? idxp[t] : 0u;
+    };
+    uint32_t q0 = fetch(0), q1 = fetch(1), q2 = fetch(2), q3 = fetch(3), q4 = fetch(4),
+             q5 = fetch(5);
 
     for (uint32_t st = 0; st < nsteps; ++st) {
         const uint32_t t = (st << 5) + lane;
         bool active = t < len;
         uint32_t j;
         if (idxp) {
-            j = nxt;
-            const uint32_t t2 = t + 32;
-            nxt = (t2 < len) ? idxp[t2] : 0;
+            j = q0;
+            q0 = q1;
+            q1 = q2;
+            q2 = q3;
+            q3 = q4;
+            q4 = q5;
+            q5 = fetch(st + 6);
         } else {
             j = aj;
             aj = (aj >= N - ainc) ? aj - (N - ainc) : aj + ainc;
@@ -247,15 +665,8 @@ __device__ __forceinline__ void run_item(const SimItem &it, Sets &S, const SimOu
         carry = __shfl_sync(kFull, line, 31);
         const bool head = active && line != prev;
 
-        const uint32_t key = head ? set : (0x80000000u | (uint32_t)lane);
-        const uint32_t peers = __match_any_sync(kFull, key);
-        const uint32_t rank = __popc(peers & lt);
-        const uint32_t rounds = __reduce_max_sync(kFull, head ? rank + 1 : 0u);
-        bool miss = false;
-        for (uint32_t r = 0; r < rounds; ++r) {
-            if (head && rank == r) miss = S.access(set, line, t);
-            __syncwarp();
-        }
+        const bool miss = R.resolve(line, set, head, t, lane, lt, st + 1);
+
         const uint32_t bits = __ballot_sync(kFull, miss);
         const uint32_t after = __ballot_sync(kFull, active && t >= it.warmup);
         tot += __popc(bits);
@@ -289,12 +700,12 @@ __device__ __forceinline__ void run_item(const SimItem &it, Sets &S, const SimOu
 }
 
 template <int POLICY, int A>
-__device__ __forceinline__ void run_scan(const SimItem &it, uint32_t arena_off, const SimOut &out,
+__device__ __forceinline__ void run_scan(const SimItem &it, uint32_t arena, const SimOut &out,
                                          int lane) {
-    ScanSets<POLICY, A> S;
-    S.init(g_smem + arena_off, it, lane);
+    RoundResolver<ScanSets<POLICY, A>> R;
+    R.S.init(g_smem + arena, it, lane);
     __syncwarp();
-    run_item(it, S, out, lane);
+    run_item(it, R, out, lane);
 }
 
 template <int POLICY>
@@ -305,8 +716,6 @@ __device__ __noinline__ void run_scan_any(const SimItem &it, uint32_t arena, con
         case 2: run_scan<POLICY, 2>(it, arena, out, lane); break;
         case 4: run_scan<POLICY, 4>(it, arena, out, lane); break;
         case 8: run_scan<POLICY, 8>(it, arena, out, lane); break;
-        case 16: run_scan<POLICY, 16>(it, arena, out, lane); break;
-        case 32: run_scan<POLICY, 32>(it, arena, out, lane); break;
         default: run_scan<POLICY, 0>(it, arena, out, lane); break;
     }
 }
@@ -314,10 +723,27 @@ __device__ __noinline__ void run_scan_any(const SimItem &it, uint32_t arena, con
 template <int POLICY>
 __device__ __noinline__ void run_table(const SimItem &it, uint32_t arena, const SimOut &out,
                                        int lane) {
-    TableSets<POLICY> S;
-    S.init(g_smem + arena, it, lane);
+    RoundResolver<TableSets<POLICY>> R;
+    R.S.init(g_smem + arena, it, lane);
     __syncwarp();
-    run_item(it, S, out, lane);
+    run_item(it, R, out, lane);
+}
+
+template <int POLICY>
+__device__ __noinline__ void run_batch_fr(const SimItem &it, uint32_t arena, const SimOut &out,
+                                          int lane) {
+    BatchFR<POLICY> R;
+    R.init(g_smem + arena, it, lane);
+    __syncwarp();
+    run_item(it, R, out, lane);
+}
+
+__device__ __noinline__ void run_batch_lru(const SimItem &it, uint32_t arena, const SimOut &out,
+                                           int lane) {
+    BatchLRU R;
+    R.init(g_smem + arena, it, lane);
+    __syncwarp();
+    run_item(it, R, out, lane);
 }
 
 __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ items,
@@ -336,10 +762,14 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
             if (it.policy == PCHASE_LRU) run_scan_any<PCHASE_LRU>(it, arena, out, lane);
             else if (it.policy == PCHASE_FIFO) run_scan_any<PCHASE_FIFO>(it, arena, out, lane);
             else run_scan_any<PCHASE_RANDOM>(it, arena, out, lane);
-        } else {
+        } else if (it.mode == kModeTable) {
             if (it.policy == PCHASE_LRU) run_table<PCHASE_LRU>(it, arena, out, lane);
             else if (it.policy == PCHASE_FIFO) run_table<PCHASE_FIFO>(it, arena, out, lane);
             else run_table<PCHASE_RANDOM>(it, arena, out, lane);
+        } else {
+            if (it.policy == PCHASE_LRU) run_batch_lru(it, arena, out, lane);
+            else if (it.policy == PCHASE_FIFO) run_batch_fr<PCHASE_FIFO>(it, arena, out, lane);
+            else run_batch_fr<PCHASE_RANDOM>(it, arena, out, lane);
         }
         __syncwarp();
     }
