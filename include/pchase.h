@@ -166,6 +166,12 @@ uint64_t pchase_sim_plan_items(const pchase_sim_plan *plan);
 uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);
 /* Kernel launches one pchase_sim_run (or pchase_match_run) queues. */
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
+/*
+ * Writes a one-line text description of the plan (items per set mode, size
+ * classes, the per-CTA slot mix) into buf (host, `bytes` long, always
+ * NUL-terminated); returns the length the full text needs.
+ */
+size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes);
 
 /*
  * Copies the plan's tables into `workspace` (device, at least
@@ -194,6 +200,16 @@ int pchase_sim_plan_upload(const pchase_sim_plan *plan, void *workspace, size_t 
 int pchase_sim_run(const pchase_sim_plan *plan, void *workspace, uint32_t *bitmaps,
                    const uint64_t *word_offsets, uint64_t *miss_counts, uint32_t *dev_status,
                    pchase_stream_t stream);
+
+/*
+ * pchase_sim_run that also records, per item i (in the caller's numbering),
+ * timeline[4i .. 4i+3] = {start ns, end ns (the GPU's global timer), SM id,
+ * warp slot}; timeline is a device buffer of 4 * items uint64.  For
+ * load-balance diagnosis and the autotuner.
+ */
+int pchase_sim_run_profiled(const pchase_sim_plan *plan, void *workspace, uint32_t *bitmaps,
+                            const uint64_t *word_offsets, uint64_t *miss_counts,
+                            uint32_t *dev_status, uint64_t *timeline, pchase_stream_t stream);
 
 /*
  * One-shot form of the three calls above (plan, upload, run, destroy) for a

@@ -83,6 +83,9 @@ class SimPlan:
         self.bitmap_words = int(self.L.pchase_sim_plan_bitmap_words(h))
         self.ws_bytes = int(self.L.pchase_sim_plan_workspace_bytes(h))
         self.launches = int(self.L.pchase_sim_plan_launches(h))
+        buf = ctypes.create_string_buffer(4096)
+        self.L.pchase_sim_plan_describe(h, buf, 4096)
+        self.description = buf.value.decode()
         self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=DEV)
         self._ws = (C.ptr(self.workspace) + 255) & ~255
         C.check(self.L.pchase_sim_plan_upload(h, self._ws, self.ws_bytes, C.stream_handle(stream)))
@@ -113,6 +116,16 @@ class SimPlan:
         C.check(self.L.pchase_sim_run(self.h, self._ws, C.ptr(bitmaps) if want_bitmaps else None,
                                       None, C.ptr(counts), C.ptr(status), C.stream_handle(stream)))
         return bitmaps, counts
+
+    def run_profiled(self, stream=None):
+        """run() that also returns the per-item timeline (int64 [items, 4]:
+        start ns, end ns, SM id, warp slot)."""
+        bitmaps = _u32(max(1, self.bitmap_words))
+        counts = torch.empty(2 * max(1, self.n_items), dtype=torch.int64, device=DEV)
+        tl = torch.zeros(4 * max(1, self.n_items), dtype=torch.int64, device=DEV)
+        C.check(self.L.pchase_sim_run_profiled(self.h, self._ws, C.ptr(bitmaps), None, C.ptr(counts),
+                                               None, C.ptr(tl), C.stream_handle(stream)))
+        return bitmaps, counts, tl.view(-1, 4)
 
     def match(self, observed: torch.Tensor, obs_word_offsets: torch.Tensor,
               stop_above: int = 2**64 - 1, status=None, stream=None) -> torch.Tensor:

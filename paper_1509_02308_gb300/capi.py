@@ -56,8 +56,10 @@ SIGNATURES = {
     "pchase_sim_plan_items": (_c_u64, [_c_p]),
     "pchase_sim_plan_bitmap_words": (_c_u64, [_c_p]),
     "pchase_sim_plan_launches": (_c_u32, [_c_p]),
+    "pchase_sim_plan_describe": (ctypes.c_size_t, [_c_p, ctypes.c_char_p, ctypes.c_size_t]),
     "pchase_sim_plan_upload": (ctypes.c_int, [_c_p, _c_p, ctypes.c_size_t, _c_p]),
     "pchase_sim_run": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_sim_run_profiled": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
     "cache_sim_batch": (ctypes.c_int, [_c_p, _c_u32, _c_p, _c_u32, _c_p, _c_u32, _c_p, _c_p, _c_p,
                                        _c_p, _c_p, ctypes.POINTER(ctypes.c_size_t), _c_p]),
     "pchase_classify_workspace_bytes": (ctypes.c_size_t, [_c_u32, _c_u64]),

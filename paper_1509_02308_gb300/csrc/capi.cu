@@ -77,7 +77,6 @@ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 constexpr uint32_t kMaxLines = 65535;
 constexpr uint32_t kMaxArena = 232448;  // 227 KB, one warp per CTA
-constexpr uint32_t kMaxClasses = 24;
 const uint32_t kCaps[] = {512,   1024,  2048,  3072,   4096,   6144,   8192,   12288,
                           16384, 24576, 32768, 49152,  65536,  98304,  131072, 163840,
                           196608, kMaxArena};
@@ -126,7 +125,10 @@ int check_trace(const pchase_trace &t, uint32_t i) {
 
 struct pchase_sim_plan {
     std::vector<SimItem> items;
-    std::vector<ClassLaunch> classes;
+    SlotLayout layout{};
+    SlotLayout jumbo{};   // items too large for the main slot mix (nwarps 0: none)
+    uint32_t jumbo_first_class = 0;
+    uint64_t n_jumbo = 0;
     uint64_t bitmap_words = 0;
     uint64_t n_items = 0;
     size_t ws_bytes = 0, off_items = 0, off_geoms = 0, off_seg = 0, off_obs_words = 0,
@@ -137,17 +139,15 @@ struct pchase_sim_plan {
     std::vector<uint64_t> seg_offsets;     // n_trace + 1 (element offsets of trace latencies)
     std::vector<uint64_t> obs_word_offsets;  // n_trace
     uint64_t obs_words = 0, total_len = 0, max_trace_len = 0;
-    // runtime state, made on the first run
-    int device = -1, sms = 0;
-    std::vector<int> grids;
-    std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> joins;
-    cudaEvent_t fork = nullptr;
+    // runtime state, set on the first run
+    int device = -1, sms = 0, grid = 0, jgrid = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 
     ~pchase_sim_plan() {
-        for (auto s : streams) cudaStreamDestroy(s);
-        for (auto e : joins) cudaEventDestroy(e);
+        if (side) cudaStreamDestroy(side);
         if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
     }
 };
 
@@ -162,20 +162,20 @@ int plan_runtime(pchase_sim_plan *p) {
     }
     p->sms = sm_count();
     if (p->sms <= 0) return fail(PCHASE_ECUDA, "no CUDA device");
-    for (const ClassLaunch &c : p->classes) {
-        int per = sim_max_ctas_per_sm(c, false);
+    if (p->layout.nwarps) {
+        const int per = sim_max_ctas_per_sm(p->layout);
         if (per <= 0) return fail(PCHASE_ECUDA, "simulator kernel cannot be resident");
-        const uint64_t need = (c.count + c.warps - 1) / c.warps;
-        const uint64_t cap = (uint64_t)per * p->sms;
-        p->grids.push_back((int)std::max<uint64_t>(1, std::min(need, cap)));
-        cudaStream_t s;
-        PCHASE_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
-        p->streams.push_back(s);
-        cudaEvent_t e;
-        PCHASE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
-        p->joins.push_back(e);
+        p->grid = (int)std::max<uint64_t>(
+            1, std::min<uint64_t>((uint64_t)per * p->sms, p->n_items - p->n_jumbo));
     }
-    PCHASE_CUDA(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming), "cudaEventCreate");
+    if (p->jumbo.nwarps) {
+        const int per = sim_max_ctas_per_sm(p->jumbo);
+        if (per <= 0) return fail(PCHASE_ECUDA, "simulator kernel cannot be resident");
+        p->jgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)per * p->sms, p->n_jumbo));
+        PCHASE_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "cudaStreamCreate");
+        PCHASE_CUDA(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming), "cudaEventCreate");
+        PCHASE_CUDA(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming), "cudaEventCreate");
+    }
     p->device = dev;
     return PCHASE_OK;
 }
@@ -188,16 +188,17 @@ int plan_launch(pchase_sim_plan *p, void *ws, const SimOut &out, cudaStream_t st
     SimOut o = out;
     if (!o.status) o.status = reinterpret_cast<uint32_t *>(w + 128);
     const SimItem *items = reinterpret_cast<const SimItem *>(w + p->off_items);
-    PCHASE_CUDA(cudaEventRecord(p->fork, st), "cudaEventRecord");
-    for (size_t c = 0; c < p->classes.size(); ++c) {
-        PCHASE_CUDA(cudaStreamWaitEvent(p->streams[c], p->fork, 0), "cudaStreamWaitEvent");
-        uint32_t *queue = reinterpret_cast<uint32_t *>(w) + c;
-        PCHASE_CUDA(launch_sim_class(items, p->classes[c], queue, p->grids[c], o, false,
-                                     p->streams[c]),
-                    "simulator launch");
-        PCHASE_CUDA(cudaEventRecord(p->joins[c], p->streams[c]), "cudaEventRecord");
-        PCHASE_CUDA(cudaStreamWaitEvent(st, p->joins[c], 0), "cudaStreamWaitEvent");
+    uint32_t *queues = reinterpret_cast<uint32_t *>(w);
+    if (p->jumbo.nwarps) {
+        // jumbo items first, on a side stream joined back before returning
+        PCHASE_CUDA(cudaEventRecord(p->fork, st), "cudaEventRecord");
+        PCHASE_CUDA(cudaStreamWaitEvent(p->side, p->fork, 0), "cudaStreamWaitEvent");
+        PCHASE_CUDA(launch_sim(items, p->jumbo, queues, p->jgrid, o, p->side), "jumbo launch");
+        PCHASE_CUDA(cudaEventRecord(p->join, p->side), "cudaEventRecord");
     }
+    if (p->layout.nwarps)
+        PCHASE_CUDA(launch_sim(items, p->layout, queues, p->grid, o, st), "simulator launch");
+    if (p->jumbo.nwarps) PCHASE_CUDA(cudaStreamWaitEvent(st, p->join, 0), "cudaStreamWaitEvent");
     return PCHASE_OK;
 }
 
@@ -248,12 +249,13 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     *plan_out = nullptr;
     if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
         return fail(PCHASE_EINVAL, "NULL descriptor array");
-    pchase_tune tn{8, 96 * 1024, 16, 0, 8};
+    pchase_tune tn{8, 220 * 1024, 16, 0, 8};
     if (tune) {
         if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
         if (tune->smem_budget_bytes) tn.smem_budget_bytes = std::min(tune->smem_budget_bytes, kMaxArena);
-        if (tune->max_warps_per_cta) tn.max_warps_per_cta = std::min<uint32_t>(tune->max_warps_per_cta, 16);
+        if (tune->max_warps_per_cta)
+            tn.max_warps_per_cta = std::min<uint32_t>(tune->max_warps_per_cta, kMaxWarpsPerCta);
         tn.ctas_per_sm_cap = tune->ctas_per_sm_cap;
     }
     for (uint32_t i = 0; i < n_geom; ++i) {
@@ -394,24 +396,118 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     });
     p->items.reserve(n_items);
     for (uint64_t k = 0; k < n_items; ++k) p->items.push_back(items[order[k]]);
-    for (uint64_t k = 0; k < n_items;) {
-        const int c = cls[order[k]];
-        uint64_t e = k;
-        while (e < n_items && cls[order[e]] == c) ++e;
-        ClassLaunch L;
-        L.first = (uint32_t)k;
-        L.count = (uint32_t)(e - k);
-        L.arena_bytes = kCaps[c];
-        uint32_t w = tn.smem_budget_bytes / kCaps[c];
-        w = std::max<uint32_t>(1, std::min<uint32_t>(w, tn.max_warps_per_cta));
-        L.warps = w;
-        p->classes.push_back(L);
-        k = e;
-    }
-    (void)ncap;
-    if (p->classes.size() > kMaxClasses) {
-        delete p;
-        return fail(PCHASE_ERANGE, "too many size classes");
+    // queues: one per size class, smallest class first
+    SlotLayout &L = p->layout;
+    memset(&L, 0, sizeof L);
+    std::vector<double> work(ncap, 0.0);
+    int top = -1;
+    uint32_t nclass = 0;
+    {
+        // classes present, in increasing cap order, renumbered 0..nclass-1
+        std::vector<int> present;
+        for (int c = 0; c < ncap; ++c) {
+            bool any = false;
+            for (uint64_t i = 0; i < n_items && !any; ++i) any = cls[i] == c;
+            if (any) present.push_back(c);
+        }
+        nclass = (uint32_t)present.size();
+        if (nclass > (uint32_t)kMaxClasses) {
+            delete p;
+            return fail(PCHASE_ERANGE, "too many size classes");
+        }
+        // sorted table is class-descending: find each class's run
+        for (uint32_t q = 0; q < nclass; ++q) {
+            const int c = present[q];
+            uint64_t first = n_items, count = 0;
+            for (uint64_t k = 0; k < n_items; ++k)
+                if (cls[order[k]] == c) {
+                    if (first == n_items) first = k;
+                    ++count;
+                    work[q] += cost[order[k]];
+                }
+            L.cls_first[q] = (uint32_t)first;
+            L.cls_count[q] = (uint32_t)count;
+        }
+        L.nclasses = nclass;
+        top = (int)nclass - 1;
+        // Slot mix.  Classes whose arena exceeds half the CTA budget ("jumbo")
+        // get a launch of their own, one warp per CTA.  For the others, slots
+        // are added one at a time to minimise the estimated makespan
+        // max_q (work of classes >= q) / (slots that can hold class q), since a
+        // slot also serves every smaller class.
+        std::vector<uint32_t> caps(nclass), slots(nclass, 0);
+        for (uint32_t q = 0; q < nclass; ++q) caps[q] = kCaps[present[q]];
+        const uint32_t budget = tn.smem_budget_bytes;
+        int main_top = -1;
+        for (uint32_t q = 0; q < nclass; ++q)
+            if (caps[q] * 2 <= budget) main_top = (int)q;
+        p->jumbo_first_class = (uint32_t)(main_top + 1);
+        auto makespan = [&](const std::vector<uint32_t> &sl) {
+            double worst = 0.0, wsum = 0.0;
+            uint32_t ssum = 0;
+            for (int q = main_top; q >= 0; --q) {
+                wsum += work[q];
+                ssum += sl[q];
+                if (wsum > 0.0) worst = std::max(worst, ssum ? wsum / ssum : 1e300);
+            }
+            return worst;
+        };
+        uint32_t used = 0, nw = 0;
+        if (main_top >= 0) {
+            slots[main_top] = 1;
+            used = caps[main_top];
+            nw = 1;
+            while (nw < tn.max_warps_per_cta) {
+                int best = -1;
+                double best_ms = makespan(slots);
+                for (int q = 0; q <= main_top; ++q) {
+                    if (used + caps[q] > budget) continue;
+                    slots[q] += 1;
+                    const double ms = makespan(slots);
+                    slots[q] -= 1;
+                    if (ms < best_ms * (1.0 - 1e-9)) { best_ms = ms; best = q; }
+                }
+                if (best < 0) {
+                    // no slot lowers the makespan: spend what is left on the
+                    // smallest class with work (more warps to hide latency)
+                    for (int q = 0; q <= main_top; ++q)
+                        if (work[q] > 0.0 && used + caps[q] <= budget) { best = q; break; }
+                    if (best < 0) break;
+                }
+                slots[best] += 1;
+                used += caps[best];
+                nw += 1;
+            }
+        }
+        uint32_t off = 0, w = 0;
+        for (int q = main_top; q >= 0; --q)
+            for (uint32_t k = 0; k < slots[q]; ++k) {
+                L.warp_class[w] = (uint32_t)q;
+                L.warp_off[w] = off;
+                off += caps[q];
+                ++w;
+            }
+        L.nwarps = w;
+        L.smem_bytes = off;
+        // jumbo layout: one warp, the largest jumbo arena; serves jumbo classes
+        SlotLayout &J = p->jumbo;
+        memset(&J, 0, sizeof J);
+        J.nclasses = nclass;
+        for (uint32_t q = 0; q < nclass; ++q) {
+            J.cls_first[q] = L.cls_first[q];
+            J.cls_count[q] = L.cls_count[q];
+        }
+        if (main_top + 1 < (int)nclass) {
+            J.nwarps = 1;
+            J.warp_class[0] = nclass - 1;
+            J.warp_off[0] = 0;
+            J.smem_bytes = caps[nclass - 1];
+            // the jumbo warp must not steal main classes
+            J.pad = (uint32_t)(main_top + 1);
+            uint64_t nj = 0;
+            for (uint32_t q = main_top + 1; q < nclass; ++q) nj += L.cls_count[q];
+            p->n_jumbo = nj;
+        }
     }
     // workspace: [queues + status: 256][items][geoms][seg offsets][obs word offsets][pool]
     size_t off = 256;
@@ -440,7 +536,41 @@ uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan) {
     return plan ? plan->bitmap_words : 0;
 }
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
-    return plan ? (uint32_t)plan->classes.size() : 0;
+    if (!plan) return 0;
+    return (plan->layout.nwarps ? 1u : 0u) + (plan->jumbo.nwarps ? 1u : 0u);
+}
+
+size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes) {
+    std::string d;
+    if (plan) {
+        uint64_t modes[3] = {0, 0, 0};
+        for (const SimItem &it : plan->items) modes[it.mode < 3 ? it.mode : 0]++;
+        char tmp[256];
+        snprintf(tmp, sizeof tmp,
+                 "items=%llu scan=%llu table=%llu batch=%llu jumbo=%llu classes=%u warps=%u smem=%u slots=",
+                 (unsigned long long)plan->n_items, (unsigned long long)modes[0],
+                 (unsigned long long)modes[1], (unsigned long long)modes[2],
+                 (unsigned long long)plan->n_jumbo, plan->layout.nclasses, plan->layout.nwarps,
+                 plan->layout.smem_bytes);
+        d = tmp;
+        for (uint32_t w = 0; w < plan->layout.nwarps; ++w) {
+            const uint32_t next = w + 1 < plan->layout.nwarps ? plan->layout.warp_off[w + 1]
+                                                              : plan->layout.smem_bytes;
+            snprintf(tmp, sizeof tmp, "%s%u", w ? "," : "", next - plan->layout.warp_off[w]);
+            d += tmp;
+        }
+        d += " class_items=";
+        for (uint32_t q = 0; q < plan->layout.nclasses; ++q) {
+            snprintf(tmp, sizeof tmp, "%s%u", q ? "," : "", plan->layout.cls_count[q]);
+            d += tmp;
+        }
+    }
+    if (buf && bytes) {
+        const size_t n = d.size() < bytes - 1 ? d.size() : bytes - 1;
+        memcpy(buf, d.data(), n);
+        buf[n] = 0;
+    }
+    return d.size();
 }
 
 int pchase_sim_plan_upload(const pchase_sim_plan *plan, void *workspace, size_t workspace_bytes,
@@ -485,6 +615,21 @@ int pchase_sim_run(const pchase_sim_plan *plan, void *workspace, uint32_t *bitma
     out.word_offsets = word_offsets;
     out.miss_counts = miss_counts;
     out.status = dev_status;
+    return plan_launch(const_cast<pchase_sim_plan *>(plan), workspace, out,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+int pchase_sim_run_profiled(const pchase_sim_plan *plan, void *workspace, uint32_t *bitmaps,
+                            const uint64_t *word_offsets, uint64_t *miss_counts,
+                            uint32_t *dev_status, uint64_t *timeline, pchase_stream_t stream) {
+    if (!plan || !workspace || !timeline) return fail(PCHASE_EINVAL, "plan, workspace or timeline is NULL");
+    if (plan->n_items == 0) return PCHASE_OK;
+    SimOut out{};
+    out.bitmaps = bitmaps;
+    out.word_offsets = word_offsets;
+    out.miss_counts = miss_counts;
+    out.status = dev_status;
+    out.timeline = timeline;
     return plan_launch(const_cast<pchase_sim_plan *>(plan), workspace, out,
                        reinterpret_cast<cudaStream_t>(stream));
 }

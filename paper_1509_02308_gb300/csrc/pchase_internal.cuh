@@ -85,11 +85,20 @@ struct SimItem {
     uint32_t pad;
 };
 
-struct ClassLaunch {
-    uint32_t first;       // index of the class's first item in the sorted table
-    uint32_t count;
-    uint32_t arena_bytes; // per warp
-    uint32_t warps;       // per CTA
+// One launch serves every item.  Each CTA holds the same mix of per-warp
+// shared-memory arenas ("slots"); warp w serves size class warp_class[w]
+// first and then takes items of smaller classes.
+constexpr int kMaxWarpsPerCta = 16;
+constexpr int kMaxClasses = 24;
+struct SlotLayout {
+    uint32_t nwarps;                          // warps per CTA
+    uint32_t nclasses;
+    uint32_t smem_bytes;                      // dynamic shared memory per CTA
+    uint32_t pad;                             // lowest class a warp may take
+    uint32_t warp_class[kMaxWarpsPerCta];     // class served first by warp w
+    uint32_t warp_off[kMaxWarpsPerCta];       // byte offset of warp w's arena
+    uint32_t cls_first[kMaxClasses];          // first item of class c (sorted table)
+    uint32_t cls_count[kMaxClasses];
 };
 
 // Simulation output sinks.
@@ -103,11 +112,13 @@ struct SimOut {
     const uint64_t *obs_word_offsets;
     uint64_t stop_above;
     uint64_t *dist;
+    // optional per-item timeline (4 uint64 per item)
+    uint64_t *timeline;
 };
 
 // Kernel launchers (sim.cu)
-cudaError_t launch_sim_class(const SimItem *items, const ClassLaunch &cls, uint32_t *queue,
-                             int grid, const SimOut &out, bool hamming, cudaStream_t st);
-int sim_max_ctas_per_sm(const ClassLaunch &cls, bool hamming);
+cudaError_t launch_sim(const SimItem *items, const SlotLayout &layout, uint32_t *queues, int grid,
+                       const SimOut &out, cudaStream_t st);
+int sim_max_ctas_per_sm(const SlotLayout &layout);
 
 }  // namespace pchase

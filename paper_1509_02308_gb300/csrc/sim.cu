@@ -76,9 +76,7 @@ struct ScanSets {
         int hit = -1;
         uint32_t best = 0xFFFFFFFFu;
         uint32_t bw = 0;
-#pragma unroll
-        for (uint32_t w = 0; w < (A ? A : 32); ++w) {
-            if (!A && w >= a) break;
+        for (uint32_t w = 0; w < a; ++w) {
             const uint2 e = s[w];
             if (e.x == line) hit = (int)w;
             if (e.y < best) { best = e.y; bw = w; }
@@ -608,19 +606,29 @@ struct BatchLRU {
 };
 
 // --------------------------------------------------------------- item loop
+// One step (32 accesses) per trip.  The code is kept small on purpose: warps
+// of many different items (policies, set modes) share each SM, and a larger
+// loop body multiplied by every variant stops fitting the instruction cache.
+constexpr uint32_t kUnroll = 1;
+
 template <typename Res>
-__device__ __forceinline__ void run_item(const SimItem &it, Res &R, const SimOut &out, int lane) {
+__device__ __forceinline__ void run_item(const SimItem it, Res &R, const SimOut out, int lane) {
     const uint32_t len = it.len;
     const uint32_t *__restrict__ idxp = it.idx;
     const uint32_t N = it.n_elems;
+    const uint32_t lsh = it.lsh, sets = it.sets, mm = it.magic_m, s1 = it.s1, s2 = it.s2;
+    const uint32_t warmup = it.warmup;
     const uint32_t lt = lanemask_lt();
     const bool ham = out.dist != nullptr;
+    uint32_t *const bitmaps = out.bitmaps;
+    const uint32_t *const observed = out.observed;
+    const uint64_t stop_above = out.stop_above;
     const uint64_t wbase = out.word_offsets ? out.word_offsets[it.out_item] : it.word_off;
     const uint64_t obase = ham ? out.obs_word_offsets[it.obs] : 0;
 
     uint32_t carry = kInvalidLine;
     uint32_t myword = 0;
-    uint32_t tot = 0, aft = 0;
+    uint32_t tot = 0, aft = 0, bad = 0;
     uint64_t dsum = 0;  // Hamming distance so far (warp-uniform)
 
     // analytic chain: access t visits (t * stride) mod N
@@ -630,66 +638,72 @@ __device__ __forceinline__ void run_item(const SimItem &it, Res &R, const SimOut
         ainc = (uint32_t)((32ull * it.stride) % N);
     }
     const uint32_t nsteps = (len + 31) >> 5;
-    // explicit traces: loads issued six steps ahead
-    auto fetch = [&](uint32_t st) -> uint32_t {
-        const uint32_t t = (st << 5) + (uint32_t)lane;
-        return (idxp && t < len) ? idxp[t] : 0u;
-    };
-    uint32_t q0 = fetch(0), q1 = fetch(1), q2 = fetch(2), q3 = fetch(3), q4 = fetch(4),
-             q5 = fetch(5);
-
-    for (uint32_t st = 0; st < nsteps; ++st) {
-        const uint32_t t = (st << 5) + lane;
-        bool active = t < len;
-        uint32_t j;
-        if (idxp) {
-            j = q0;
-            q0 = q1;
-            q1 = q2;
-            q2 = q3;
-            q3 = q4;
-            q4 = q5;
-            q5 = fetch(st + 6);
-        } else {
-            j = aj;
-            aj = (aj >= N - ainc) ? aj - (N - ainc) : aj + ainc;
-        }
-        if (active && j >= N) {
-            atomicOr(out.status, PCHASE_DEV_INDEX_RANGE);
-            active = false;
-        }
-        const uint32_t line = j >> it.lsh;
-        const uint32_t set = line - div_q(line, it.magic_m, it.s1, it.s2) * it.sets;
-        uint32_t prev = __shfl_up_sync(kFull, line, 1);
-        if (lane == 0) prev = carry;
-        carry = __shfl_sync(kFull, line, 31);
-        const bool head = active && line != prev;
-
-        const bool miss = R.resolve(line, set, head, t, lane, lt, st + 1);
-
-        const uint32_t bits = __ballot_sync(kFull, miss);
-        const uint32_t after = __ballot_sync(kFull, active && t >= it.warmup);
-        tot += __popc(bits);
-        aft += __popc(bits & after);
-        const uint32_t slot = st & 31;
-        if ((uint32_t)lane == slot) myword = bits;
-        if (slot == 31 || st + 1 == nsteps) {
-            const uint64_t w0 = (uint64_t)(st & ~31u);
-            uint32_t dl = 0;
-            if ((uint32_t)lane <= slot) {
-                if (ham) {
-                    dl = __popc(out.observed[obase + w0 + lane] ^ myword);
-                } else if (out.bitmaps) {
-                    out.bitmaps[wbase + w0 + lane] = myword;
-                }
-            }
-            myword = 0;
-            if (ham) {
-                dsum += __reduce_add_sync(kFull, dl);
-                if (dsum > out.stop_above) break;
-            }
-        }
+    // explicit traces: the next block's loads are issued one block ahead
+    uint32_t pf[kUnroll];
+#pragma unroll
+    for (uint32_t u = 0; u < kUnroll; ++u) {
+        const uint32_t t = (u << 5) + (uint32_t)lane;
+        pf[u] = (idxp && t < len) ? idxp[t] : 0u;
     }
+
+    for (uint32_t st0 = 0; st0 < nsteps; st0 += kUnroll) {
+        uint32_t line[kUnroll], set[kUnroll];
+        bool head[kUnroll];
+        // ---- decode four steps (no cache state involved)
+#pragma unroll
+        for (uint32_t u = 0; u < kUnroll; ++u) {
+            const uint32_t t = ((st0 + u) << 5) + (uint32_t)lane;
+            bool active = t < len;
+            uint32_t j;
+            if (idxp) {
+                j = pf[u];
+                const uint32_t tn = t + (kUnroll << 5);
+                pf[u] = tn < len ? idxp[tn] : 0u;
+            } else {
+                j = aj;
+                aj = (aj >= N - ainc) ? aj - (N - ainc) : aj + ainc;
+            }
+            if (active && j >= N) {
+                bad = 1;
+                active = false;
+            }
+            const uint32_t ln = j >> lsh;
+            line[u] = ln;
+            set[u] = ln - div_q(ln, mm, s1, s2) * sets;
+            uint32_t prev = __shfl_up_sync(kFull, ln, 1);
+            if (lane == 0) prev = carry;
+            carry = __shfl_sync(kFull, ln, 31);
+            head[u] = active && ln != prev;
+        }
+        // ---- state updates in trace order, then the step's miss word
+#pragma unroll
+        for (uint32_t u = 0; u < kUnroll; ++u) {
+            const uint32_t st = st0 + u;
+            const uint32_t t = (st << 5) + (uint32_t)lane;
+            const bool miss = R.resolve(line[u], set[u], head[u], t, lane, lt, st + 1);
+            const uint32_t bits = __ballot_sync(kFull, miss);
+            // accesses at or after the warm-up within this step
+            const uint32_t base = st << 5;
+            const uint32_t after = base >= warmup ? kFull
+                                 : (warmup - base >= 32 ? 0u : ~((1u << (warmup - base)) - 1u));
+            tot += __popc(bits);
+            aft += __popc(bits & after);
+            const uint32_t slot = st & 31;
+            if ((uint32_t)lane == slot) myword = bits;
+            if (st < nsteps && (slot == 31 || st + 1 == nsteps)) {
+                const uint64_t w0 = (uint64_t)(st & ~31u);
+                uint32_t dl = 0;
+                if ((uint32_t)lane <= slot) {
+                    if (ham) dl = __popc(observed[obase + w0 + lane] ^ myword);
+                    else if (bitmaps) bitmaps[wbase + w0 + lane] = myword;
+                }
+                myword = 0;
+                if (ham) dsum += __reduce_add_sync(kFull, dl);
+            }
+        }
+        if (ham && dsum > stop_above) break;
+    }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(out.status, PCHASE_DEV_INDEX_RANGE);
     if (ham) {
         if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(out.dist + it.cand),
                                  (unsigned long long)dsum);
@@ -700,7 +714,7 @@ __device__ __forceinline__ void run_item(const SimItem &it, Res &R, const SimOut
 }
 
 template <int POLICY, int A>
-__device__ __forceinline__ void run_scan(const SimItem &it, uint32_t arena, const SimOut &out,
+__device__ __forceinline__ void run_scan(const SimItem it, uint32_t arena, const SimOut out,
                                          int lane) {
     RoundResolver<ScanSets<POLICY, A>> R;
     R.S.init(g_smem + arena, it, lane);
@@ -709,19 +723,14 @@ __device__ __forceinline__ void run_scan(const SimItem &it, uint32_t arena, cons
 }
 
 template <int POLICY>
-__device__ __noinline__ void run_scan_any(const SimItem &it, uint32_t arena, const SimOut &out,
+__device__ __noinline__ void run_scan_any(const SimItem it, uint32_t arena, const SimOut out,
                                           int lane) {
-    switch (it.ways) {
-        case 1: run_scan<POLICY, 1>(it, arena, out, lane); break;
-        case 2: run_scan<POLICY, 2>(it, arena, out, lane); break;
-        case 4: run_scan<POLICY, 4>(it, arena, out, lane); break;
-        case 8: run_scan<POLICY, 8>(it, arena, out, lane); break;
-        default: run_scan<POLICY, 0>(it, arena, out, lane); break;
-    }
+    if (it.ways == 1) run_scan<POLICY, 1>(it, arena, out, lane);
+    else run_scan<POLICY, 0>(it, arena, out, lane);
 }
 
 template <int POLICY>
-__device__ __noinline__ void run_table(const SimItem &it, uint32_t arena, const SimOut &out,
+__device__ __noinline__ void run_table(const SimItem it, uint32_t arena, const SimOut out,
                                        int lane) {
     RoundResolver<TableSets<POLICY>> R;
     R.S.init(g_smem + arena, it, lane);
@@ -730,7 +739,7 @@ __device__ __noinline__ void run_table(const SimItem &it, uint32_t arena, const 
 }
 
 template <int POLICY>
-__device__ __noinline__ void run_batch_fr(const SimItem &it, uint32_t arena, const SimOut &out,
+__device__ __noinline__ void run_batch_fr(const SimItem it, uint32_t arena, const SimOut out,
                                           int lane) {
     BatchFR<POLICY> R;
     R.init(g_smem + arena, it, lane);
@@ -738,7 +747,7 @@ __device__ __noinline__ void run_batch_fr(const SimItem &it, uint32_t arena, con
     run_item(it, R, out, lane);
 }
 
-__device__ __noinline__ void run_batch_lru(const SimItem &it, uint32_t arena, const SimOut &out,
+__device__ __noinline__ void run_batch_lru(const SimItem it, uint32_t arena, const SimOut out,
                                            int lane) {
     BatchLRU R;
     R.init(g_smem + arena, it, lane);
@@ -747,54 +756,68 @@ __device__ __noinline__ void run_batch_lru(const SimItem &it, uint32_t arena, co
 }
 
 __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ items,
-                                                  ClassLaunch cls, uint32_t *queue,
-                                                  SimOut out) {
+                                                  const __grid_constant__ SlotLayout L,
+                                                  uint32_t *queues, SimOut out) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const uint32_t arena = (uint32_t)warp * cls.arena_bytes;
-    for (;;) {
-        uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(queue, 1u);
-        k = __shfl_sync(kFull, k, 0);
-        if (k >= cls.count) break;
-        const SimItem it = items[cls.first + k];
-        if (it.mode == kModeScan) {
-            if (it.policy == PCHASE_LRU) run_scan_any<PCHASE_LRU>(it, arena, out, lane);
-            else if (it.policy == PCHASE_FIFO) run_scan_any<PCHASE_FIFO>(it, arena, out, lane);
-            else run_scan_any<PCHASE_RANDOM>(it, arena, out, lane);
-        } else if (it.mode == kModeTable) {
-            if (it.policy == PCHASE_LRU) run_table<PCHASE_LRU>(it, arena, out, lane);
-            else if (it.policy == PCHASE_FIFO) run_table<PCHASE_FIFO>(it, arena, out, lane);
-            else run_table<PCHASE_RANDOM>(it, arena, out, lane);
-        } else {
-            if (it.policy == PCHASE_LRU) run_batch_lru(it, arena, out, lane);
-            else if (it.policy == PCHASE_FIFO) run_batch_fr<PCHASE_FIFO>(it, arena, out, lane);
-            else run_batch_fr<PCHASE_RANDOM>(it, arena, out, lane);
+    const uint32_t arena = L.warp_off[warp];
+    for (int c = (int)L.warp_class[warp]; c >= (int)L.pad; --c) {
+        for (;;) {
+            uint32_t k = 0;
+            if (lane == 0) k = atomicAdd(queues + c, 1u);
+            k = __shfl_sync(kFull, k, 0);
+            if (k >= L.cls_count[c]) break;
+            const SimItem it = items[L.cls_first[c] + k];
+            uint64_t t_start = 0;
+            if (out.timeline) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+            if (it.mode == kModeScan) {
+                if (it.policy == PCHASE_LRU) run_scan_any<PCHASE_LRU>(it, arena, out, lane);
+                else if (it.policy == PCHASE_FIFO) run_scan_any<PCHASE_FIFO>(it, arena, out, lane);
+                else run_scan_any<PCHASE_RANDOM>(it, arena, out, lane);
+            } else if (it.mode == kModeTable) {
+                if (it.policy == PCHASE_LRU) run_table<PCHASE_LRU>(it, arena, out, lane);
+                else if (it.policy == PCHASE_FIFO) run_table<PCHASE_FIFO>(it, arena, out, lane);
+                else run_table<PCHASE_RANDOM>(it, arena, out, lane);
+            } else {
+                if (it.policy == PCHASE_LRU) run_batch_lru(it, arena, out, lane);
+                else if (it.policy == PCHASE_FIFO) run_batch_fr<PCHASE_FIFO>(it, arena, out, lane);
+                else run_batch_fr<PCHASE_RANDOM>(it, arena, out, lane);
+            }
+            __syncwarp();
+            if (out.timeline && lane == 0) {
+                uint64_t t_end, sm;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+                uint32_t smid;
+                asm("mov.u32 %0, %%smid;" : "=r"(smid));
+                sm = smid;
+                uint64_t *tl = out.timeline + 4ull * it.out_item;
+                tl[0] = t_start;
+                tl[1] = t_end;
+                tl[2] = sm;
+                tl[3] = (uint64_t)warp;
+            }
         }
-        __syncwarp();
     }
 }
 
 }  // namespace
 
-cudaError_t launch_sim_class(const SimItem *items, const ClassLaunch &cls, uint32_t *queue,
-                             int grid, const SimOut &out, bool, cudaStream_t st) {
-    const size_t smem = (size_t)cls.arena_bytes * cls.warps;
+cudaError_t launch_sim(const SimItem *items, const SlotLayout &layout, uint32_t *queues, int grid,
+                       const SimOut &out, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)layout.smem_bytes);
     if (e != cudaSuccess) return e;
-    sim_kernel<<<grid, cls.warps * 32, smem, st>>>(items, cls, queue, out);
+    sim_kernel<<<grid, layout.nwarps * 32, layout.smem_bytes, st>>>(items, layout, queues, out);
     return cudaGetLastError();
 }
 
-int sim_max_ctas_per_sm(const ClassLaunch &cls, bool) {
-    const size_t smem = (size_t)cls.arena_bytes * cls.warps;
-    if (cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+int sim_max_ctas_per_sm(const SlotLayout &layout) {
+    if (cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)layout.smem_bytes) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_kernel, cls.warps * 32, smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_kernel, layout.nwarps * 32,
+                                                      layout.smem_bytes) != cudaSuccess)
         return 0;
     return n;
 }
