@@ -333,6 +333,106 @@ int pchase_probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas,
                                    uint64_t bytes, uint32_t reps, double *gbs_out,
                                    pchase_stream_t stream);
 
+/* ------------------------------------------------------------------ S7 */
+
+/*
+ * Learned inverse (a build extension, not in the paper): a 1-D convolutional
+ * network maps a normalised mean-latency trace over the 512 points of a probe
+ * plan to (capacity class, line-size class, ways class, policy), with an
+ * exhaustive least-squares matcher as fallback and judge.  The trace model is
+ * Sec. 4.1's t = t0 + t_m * r, r being each point's miss rate.
+ *
+ * Network: 4 x [conv1d k=5, stride 2, pad 2, 64 channels, GELU] (512 -> 32
+ * positions), flatten 2048 -> FC 256 + GELU -> FC 31 logits, read as heads of
+ * 17 (capacity), 4 (line size), 7 (ways), 3 (policy).  BF16 GEMM operands,
+ * FP32 accumulation; FP32 master weights, Adam moments and gradients.
+ *
+ * Buffers: the caller allocates `params` (pchase_inverse_param_bytes; its
+ * first 4 * param_count bytes are the FP32 weights in layer order, each
+ * layer's weight matrix [out][in] row-major then its bias; a convolution's
+ * input column is kk * in_channels + channel) and `work`
+ * (pchase_inverse_work_bytes), both device memory.  The handle only records
+ * sizes and offsets.
+ */
+typedef struct pchase_inverse pchase_inverse;
+
+/* max_batch in [1, 65536]: the largest batch a train step or one inference
+ * chunk processes. */
+int pchase_inverse_create(uint32_t max_batch, pchase_inverse **out);
+void pchase_inverse_destroy(pchase_inverse *h);
+uint64_t pchase_inverse_param_count(const pchase_inverse *h);
+size_t pchase_inverse_param_bytes(const pchase_inverse *h);
+size_t pchase_inverse_work_bytes(const pchase_inverse *h);
+
+/* Uniform init of every weight in +-sqrt(6 / fan_in) (SplitMix64 keyed on
+ * seed and index), biases 0, Adam moments 0. */
+int pchase_inverse_init(const pchase_inverse *h, void *params, uint64_t seed,
+                        pchase_stream_t stream);
+
+/*
+ * Synthetic traces from a miss-rate table (device `rates`, n_geoms x 512
+ * FP32) and per-geometry targets (device, n_geoms x 4 uint32 class labels).
+ * Sample i (global number first + i) draws its geometry, t0, t1 = t0 * rho,
+ * per-point Gaussian jitter and spikes from SplitMix64 keyed on (seed, number,
+ * point); noise (host, 8 floats) = {t0_lo, t0_hi, rho_lo, rho_hi, sigma,
+ * spike_probability, spike_lo, spike_hi}.  Outputs (device): x_out n x 512
+ * FP32 in [0, 1] (min-max normalised), labels_out n x 4, truth_out n
+ * geometry indices (may be NULL).
+ */
+int pchase_inverse_synth(const float *rates, const uint32_t *targets, uint32_t n_geoms,
+                         uint64_t seed, uint64_t first, uint32_t n, const float *noise,
+                         float *x_out, uint32_t *labels_out, uint32_t *truth_out,
+                         pchase_stream_t stream);
+
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8; `step` counts from 0)
+ * on the mean cross-entropy of the four heads over a batch of B <= max_batch
+ * traces (device x, B x 512 FP32; labels B x 4).  The batch's mean loss is
+ * added to *loss_accum (device float). */
+int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work, const float *x,
+                              const uint32_t *labels, uint32_t B, float lr, uint32_t step,
+                              float *loss_accum, pchase_stream_t stream);
+
+/* Forward pass over n traces (device x, n x 512) in max_batch chunks:
+ * pred_out n x 4 class indices, conf_out n (product of the heads' top softmax
+ * probabilities), logits_out n x 31 FP32 (may be NULL). */
+int pchase_inverse_infer(const pchase_inverse *h, const void *params, void *work, const float *x,
+                         uint32_t n, uint32_t *pred_out, float *conf_out, float *logits_out,
+                         pchase_stream_t stream);
+
+/*
+ * Exhaustive least-squares matcher (FP32): for each trace y (device, n x 512)
+ * keep the points at or below its 507th smallest value (the 5 largest are the
+ * spike allowance), fit y ~ alpha + beta * r_g for every geometry g (device
+ * rates, n_geoms x 512) over the kept points, and take the smallest residual
+ * (the plain variance of y when the fitted slope is not positive); equal
+ * residuals go to the lower geometry index, so callers order the table
+ * canonically.  best_out n indices, resid_out n residuals (may be NULL).
+ * Work buffer (device): pchase_lsq_work_bytes(n).
+ */
+size_t pchase_lsq_work_bytes(uint32_t n);
+int pchase_lsq_match(const float *rates, uint32_t n_geoms, const float *y, uint32_t n,
+                     uint32_t *best_out, float *resid_out, void *work, pchase_stream_t stream);
+
+/*
+ * Learned prediction with fallback, all on the device: infer, map each
+ * trace's four labels through label_to_cand (17*4*7*3 uint32, index
+ * ((c*4 + b)*7 + w)*3 + p, 0xFFFFFFFF = no such geometry) to a geometry
+ * index; traces whose confidence is below conf_thresh or whose labels name no
+ * geometry are listed in fallback_list (count in *n_fallback) and resolved by
+ * pchase_lsq_match.  cand_out n geometry indices.  Scratch (device):
+ * pred_scratch n x 4, conf_out n, fallback_list n, fb_rows n x 512 FP32,
+ * fb_idx n, lsq_work pchase_lsq_work_bytes(n).
+ */
+int pchase_inverse_classify(const pchase_inverse *h, const void *params, void *work,
+                            const float *x, uint32_t n, const uint32_t *label_to_cand,
+                            const float *rates, uint32_t n_geoms, float conf_thresh,
+                            uint32_t *pred_scratch, float *conf_out, uint32_t *cand_out,
+                            uint32_t *fallback_list, uint32_t *n_fallback, float *fb_rows,
+                            uint32_t *fb_idx, void *lsq_work, pchase_stream_t stream);
+
+/* Last host-side failure of the S7 calls on this thread. */
+const char *pchase_inverse_last_error(void);
+
 /* ------------------------------------------------------------- library */
 
 const char *pchase_last_error_string(void);

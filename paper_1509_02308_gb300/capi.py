@@ -74,6 +74,23 @@ SIGNATURES = {
     "pchase_probe_global_throughput": (ctypes.c_int, [ctypes.c_int, _c_u32, _c_u32, _c_u32,
                                                       _c_u32, _c_p, _c_p, _c_u64, _c_u32,
                                                       ctypes.POINTER(ctypes.c_double), _c_p]),
+    "pchase_inverse_create": (ctypes.c_int, [_c_u32, ctypes.POINTER(_c_p)]),
+    "pchase_inverse_destroy": (None, [_c_p]),
+    "pchase_inverse_param_count": (_c_u64, [_c_p]),
+    "pchase_inverse_param_bytes": (ctypes.c_size_t, [_c_p]),
+    "pchase_inverse_work_bytes": (ctypes.c_size_t, [_c_p]),
+    "pchase_inverse_init": (ctypes.c_int, [_c_p, _c_p, _c_u64, _c_p]),
+    "pchase_inverse_synth": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_u64, _c_u64, _c_u32, _c_p,
+                                            _c_p, _c_p, _c_p, _c_p]),
+    "pchase_inverse_train_step": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_u32,
+                                                 ctypes.c_float, _c_u32, _c_p, _c_p]),
+    "pchase_inverse_infer": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_u32, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_lsq_work_bytes": (ctypes.c_size_t, [_c_u32]),
+    "pchase_lsq_match": (ctypes.c_int, [_c_p, _c_u32, _c_p, _c_u32, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_inverse_classify": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_u32, _c_p, _c_p, _c_u32,
+                                               ctypes.c_float, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
+                                               _c_p, _c_p, _c_p]),
+    "pchase_inverse_last_error": (ctypes.c_char_p, []),
     "pchase_last_error_string": (ctypes.c_char_p, []),
     "pchase_version": (ctypes.c_char_p, []),
     "pchase_device_sm_count": (ctypes.c_int, []),

@@ -1,0 +1,959 @@
+// S7: the learned inverse.  A small 1-D convolutional network reads a
+// normalised mean-latency trace over the 512 points of the plan and predicts
+// (capacity, line size, ways, policy); an exhaustive least-squares matcher over
+// the simulator's miss-rate table is its fallback and its judge.
+//
+// Network (per trace, channel-last activations [L, C]):
+//   4 x [conv1d k=5, stride 2, pad 2, 64 channels, GELU]: 512x1 -> 256 -> 128 -> 64 -> 32
+//   flatten 32*64 = 2048 -> FC 256 -> GELU -> FC 31 = heads of 17 + 4 + 7 + 3 logits
+// Convolutions run as im2col + GEMM.  All GEMMs use BF16 operands and FP32
+// accumulation on the tensor cores (mma.sync m16n8k16); master weights, Adam
+// moments and gradients stay FP32.
+//
+// The synthetic traces follow Sec. 4.1's mean-latency model t = t0 + t_m r
+// with r the miss rate the simulator reports for each plan point.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "pchase_internal.cuh"
+
+namespace pchase {
+
+namespace {
+
+// ------------------------------------------------------------------ GEMM
+// C[M,N] = sum_k A(m,k) B(k,n).  A is row-major (A[m*lda+k]) or column-major
+// (A[k*lda+m]); B is row-major (B[k*ldb+n]) or column-major (B[n*ldb+k]).
+// Tiles 128x128x32, 256 threads (8 warps of 64x32), BF16 tiles in shared
+// memory with k contiguous, fragments by ldmatrix, FP32 accumulators.
+// Epilogue: + bias[n] (optional), then GELU (optional); writes FP32 and/or
+// BF16 copies; `pre` (optional, FP32) receives the value before GELU.
+constexpr int GBM = 128, GBN = 128, GBK = 32, GPAD = 8;
+
+struct GemmArgs {
+    const __nv_bfloat16 *A;
+    const __nv_bfloat16 *B;
+    int M, N, K, lda, ldb;
+    const float *bias;
+    float *Cf;
+    __nv_bfloat16 *Cb;
+    float *pre;
+    int ldc;
+    int gelu;
+};
+
+__device__ __forceinline__ float gelu_f(float x) {
+    // tanh form of GELU (Hendrycks & Gimpel 2016)
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
+}
+
+__device__ __forceinline__ float gelu_grad(float x) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    const float u = k0 * (x + k1 * x * x * x);
+    const float t = tanhf(u);
+    return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * x * x);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                        uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float *c, uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <bool A_COL, bool B_ROW>
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g) {
+    __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    for (int k0 = 0; k0 < g.K; k0 += GBK) {
+        // ---- tiles into shared memory, k contiguous
+        for (int e = tid; e < GBM * GBK; e += 256) {
+            int r, c;
+            if (A_COL) { c = e / GBM; r = e % GBM; } else { r = e / GBK; c = e % GBK; }
+            const int m = m0 + r, k = k0 + c;
+            __nv_bfloat16 v = zero;
+            if (m < g.M && k < g.K) v = A_COL ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
+            As[r][c] = v;
+        }
+        for (int e = tid; e < GBN * GBK; e += 256) {
+            int r, c;
+            if (B_ROW) { c = e / GBN; r = e % GBN; } else { r = e / GBK; c = e % GBK; }
+            const int n = n0 + r, k = k0 + c;
+            __nv_bfloat16 v = zero;
+            if (n < g.N && k < g.K) v = B_ROW ? g.B[(size_t)k * g.ldb + n] : g.B[(size_t)n * g.ldb + k];
+            Bs[r][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; kk += 16) {
+            uint32_t af[4][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int row = wm + i * 16 + (lane & 15);
+                const int col = kk + ((lane >> 4) << 3);
+                ldsm_x4((uint32_t)__cvta_generic_to_shared(&As[row][col]), af[i][0], af[i][1],
+                        af[i][2], af[i][3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j += 2) {
+                // two n8 tiles per x4: matrices (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, ...)
+                const int row = wn + j * 8 + (lane & 7) + ((lane >> 4) << 3);
+                const int col = kk + (((lane >> 3) & 1) << 3);
+                uint32_t r0, r1, r2, r3;
+                ldsm_x4((uint32_t)__cvta_generic_to_shared(&Bs[row][col]), r0, r1, r2, r3);
+                bfr[j][0] = r0;
+                bfr[j][1] = r1;
+                bfr[j + 1][0] = r2;
+                bfr[j + 1][1] = r3;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_bf16(acc[i][j], af[i][0], af[i][1], af[i][2], af[i][3], bfr[j][0], bfr[j][1]);
+        }
+        __syncthreads();
+    }
+    // ---- epilogue
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = m0 + wm + i * 16 + (lane >> 2) + ((q >> 1) << 3);
+                const int n = n0 + wn + j * 8 + ((lane & 3) << 1) + (q & 1);
+                if (m >= g.M || n >= g.N) continue;
+                float v = acc[i][j][q];
+                if (g.bias) v += g.bias[n];
+                const size_t o = (size_t)m * g.ldc + n;
+                if (g.pre) g.pre[o] = v;
+                if (g.gelu) v = gelu_f(v);
+                if (g.Cf) g.Cf[o] = v;
+                if (g.Cb) g.Cb[o] = __float2bfloat16(v);
+            }
+}
+
+cudaError_t gemm(bool a_col, bool b_row, const GemmArgs &g, cudaStream_t st) {
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM);
+    if (!a_col && !b_row) gemm_kernel<false, false><<<grid, 256, 0, st>>>(g);
+    else if (!a_col && b_row) gemm_kernel<false, true><<<grid, 256, 0, st>>>(g);
+    else if (a_col && !b_row) gemm_kernel<true, false><<<grid, 256, 0, st>>>(g);
+    else gemm_kernel<true, true><<<grid, 256, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------- network plumbing
+constexpr int kPoints = 512;
+constexpr int kCh = 64;
+constexpr int kKer = 5;
+constexpr int kHidden = 256;
+constexpr int kFlat = 32 * kCh;
+constexpr int kLogits = 31;
+__constant__ int c_head_off[5] = {0, 17, 21, 28, 31};
+
+// im2col for a stride-2, pad-2, k=5 convolution over channel-last input
+// x[b][li][ci] (li < lin) -> cols[b*lout + lo][kk*cin + ci]
+__global__ void im2col_kernel(const __nv_bfloat16 *x, int nb, int lin, int cin,
+                              __nv_bfloat16 *cols) {
+    const int lout = lin / 2;
+    const size_t total = (size_t)nb * lout * kKer * cin;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(e % cin);
+        size_t r = e / cin;
+        const int kk = (int)(r % kKer);
+        r /= kKer;
+        const int lo = (int)(r % lout);
+        const int b = (int)(r / lout);
+        const int li = 2 * lo + kk - 2;
+        __nv_bfloat16 v = __float2bfloat16(0.0f);
+        if (li >= 0 && li < lin) v = x[((size_t)b * lin + li) * cin + ci];
+        cols[e] = v;
+    }
+}
+
+// gather-form col2im: dx[b][li][ci] = sum over (lo, kk) with 2 lo + kk - 2 = li
+__global__ void col2im_kernel(const float *dcols, int nb, int lin, int cin, float *dx) {
+    const int lout = lin / 2;
+    const size_t total = (size_t)nb * lin * cin;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(e % cin);
+        const size_t r = e / cin;
+        const int li = (int)(r % lin);
+        const int b = (int)(r / lin);
+        float s = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < kKer; ++kk) {
+            const int t = li + 2 - kk;
+            if (t < 0 || (t & 1)) continue;
+            const int lo = t >> 1;
+            if (lo >= lout) continue;
+            s += dcols[((size_t)b * lout + lo) * (kKer * cin) + kk * cin + ci];
+        }
+        dx[e] = s;
+    }
+}
+
+// dz = dy * gelu'(pre) (FP32 in, BF16 out for the next GEMMs)
+__global__ void gelu_back_kernel(const float *dy, const float *pre, size_t n, float *dzf,
+                                 __nv_bfloat16 *dzb) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float v = dy[i] * gelu_grad(pre[i]);
+        if (dzf) dzf[i] = v;
+        dzb[i] = __float2bfloat16(v);
+    }
+}
+
+// column sums of a row-major [rows, cols] FP32 matrix (bias gradients)
+__global__ void colsum_kernel(const float *x, int rows, int cols, float *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.0f;
+    for (int r = 0; r < rows; ++r) s += x[(size_t)r * cols + c];
+    out[c] = s;
+}
+
+// softmax cross-entropy over the four heads; loss (mean over the batch and
+// heads) accumulated into *loss; dlogits = (softmax - onehot) / (4 batch)
+__global__ void xent_kernel(const float *logits, const uint32_t *labels, int nb, float *dlog,
+                            __nv_bfloat16 *dlogb, float *loss) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    float l = 0.0f;
+    const float inv = 1.0f / (4.0f * nb);
+    for (int h = 0; h < 4; ++h) {
+        const int o0 = c_head_off[h], o1 = c_head_off[h + 1];
+        const float *z = logits + (size_t)b * kLogits;
+        float mx = -INFINITY;
+        for (int i = o0; i < o1; ++i) mx = fmaxf(mx, z[i]);
+        float se = 0.0f;
+        for (int i = o0; i < o1; ++i) se += expf(z[i] - mx);
+        const uint32_t y = labels[(size_t)b * 4 + h];
+        l += logf(se) + mx - z[o0 + y];
+        for (int i = o0; i < o1; ++i) {
+            const float p = expf(z[i] - mx) / se;
+            const float d = (p - (i == (int)(o0 + y) ? 1.0f : 0.0f)) * inv;
+            dlog[(size_t)b * kLogits + i] = d;
+            dlogb[(size_t)b * kLogits + i] = __float2bfloat16(d);
+        }
+    }
+    atomicAdd(loss, l * inv);
+}
+
+// Adam (Kingma & Ba 2015) on FP32 master weights; refreshes BF16 copies
+__global__ void adam_kernel(float *w, const float *gr, float *m, float *v, __nv_bfloat16 *wb,
+                            size_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float g = gr[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * g;
+        const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        wb[i] = __float2bfloat16(wi);
+    }
+}
+
+__device__ __forceinline__ uint64_t smix(uint64_t x) { return splitmix64(x); }
+__device__ __forceinline__ float unit_f(uint64_t h) { return (float)(h >> 40) * (1.0f / 16777216.0f); }
+
+// Uniform init in +-scale per parameter segment, counter-based (SplitMix64
+// keyed on seed and index); biases start at 0 (scale 0).
+struct InitSegs {
+    unsigned long long end[12];
+    float scale[12];
+    int n;
+};
+
+__global__ void init_kernel(float *w, __nv_bfloat16 *wb, size_t n, const InitSegs segs,
+                            uint64_t seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int s = 0;
+        while (s < segs.n - 1 && i >= segs.end[s]) ++s;
+        const float u = unit_f(smix(seed ^ (i * 0x9E3779B97F4A7C15ull)));
+        const float v = (2.0f * u - 1.0f) * segs.scale[s];
+        w[i] = v;
+        wb[i] = __float2bfloat16(v);
+    }
+}
+
+// Synthetic traces: sample i picks a geometry, a (t0, t1) pair, per-point
+// jitter and spikes, all from SplitMix64 keyed on (seed, i, point), then
+// min-max normalises.  Box-Muller turns two uniforms into a Gaussian.
+__global__ void synth_kernel(const float *rates, const uint32_t *targets, uint32_t n_geoms,
+                             uint64_t seed, uint64_t first, uint32_t n, float t0_lo, float t0_hi,
+                             float lr_lo, float lr_hi, float sigma, float spike_p, float sp_lo,
+                             float sp_hi, float *xf, __nv_bfloat16 *xb, uint32_t *labels,
+                             uint32_t *truth) {
+    const uint32_t s = blockIdx.x;
+    if (s >= n) return;
+    __shared__ float y[kPoints];
+    __shared__ float red[2][32];
+    const uint64_t id = first + s;
+    const uint64_t base = smix(seed ^ (id * 0xD1B54A32D192ED03ull));
+    const uint32_t g = (uint32_t)(((smix(base ^ 1) >> 32) * (uint64_t)n_geoms) >> 32);
+    const float t0 = t0_lo + (t0_hi - t0_lo) * unit_f(smix(base ^ 2));
+    const float rho = expf(lr_lo + (lr_hi - lr_lo) * unit_f(smix(base ^ 3)));
+    const float tm = t0 * (rho - 1.0f);
+    float mn = INFINITY, mx = -INFINITY;
+    for (int p = threadIdx.x; p < kPoints; p += blockDim.x) {
+        const uint64_t hp = smix(base ^ (((uint64_t)p + 16) << 20));
+        const float u1 = fmaxf(unit_f(smix(hp ^ 1)), 1e-7f), u2 = unit_f(smix(hp ^ 2));
+        const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+        float v = (t0 + tm * rates[(size_t)g * kPoints + p]) * (1.0f + sigma * z);
+        if (unit_f(smix(hp ^ 3)) < spike_p) v *= sp_lo + (sp_hi - sp_lo) * unit_f(smix(hp ^ 4));
+        y[p] = v;
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+    }
+    for (int o = 16; o; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(kFull, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = mn;
+        red[1][threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    mn = red[0][0];
+    mx = red[1][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        mn = fminf(mn, red[0][w]);
+        mx = fmaxf(mx, red[1][w]);
+    }
+    const float sc = mx > mn ? 1.0f / (mx - mn) : 0.0f;
+    for (int p = threadIdx.x; p < kPoints; p += blockDim.x) {
+        const float v = (y[p] - mn) * sc;
+        if (xf) xf[(size_t)s * kPoints + p] = v;
+        if (xb) xb[(size_t)s * kPoints + p] = __float2bfloat16(v);
+    }
+    if (threadIdx.x < 4) labels[(size_t)s * 4 + threadIdx.x] = targets[(size_t)g * 4 + threadIdx.x];
+    if (threadIdx.x == 0 && truth) truth[s] = g;
+}
+
+// argmax and confidence (product of the heads' top probabilities)
+__global__ void predict_kernel(const float *logits, int nb, uint32_t *pred, float *conf) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    float c = 1.0f;
+    for (int h = 0; h < 4; ++h) {
+        const int o0 = c_head_off[h], o1 = c_head_off[h + 1];
+        const float *z = logits + (size_t)b * kLogits;
+        int best = o0;
+        for (int i = o0 + 1; i < o1; ++i)
+            if (z[i] > z[best]) best = i;
+        float se = 0.0f;
+        for (int i = o0; i < o1; ++i) se += expf(z[i] - z[best]);
+        c *= 1.0f / se;
+        pred[(size_t)b * 4 + h] = (uint32_t)(best - o0);
+    }
+    conf[b] = c;
+}
+
+// column sums with atomics (out zeroed by the caller)
+__global__ void colsum_atomic_kernel(const float *x, int rows, int cols, int rows_per_block,
+                                     float *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    const int r0 = blockIdx.y * rows_per_block;
+    const int r1 = min(rows, r0 + rows_per_block);
+    float s = 0.0f;
+    for (int r = r0; r < r1; ++r) s += x[(size_t)r * cols + c];
+    atomicAdd(out + c, s);
+}
+
+__global__ void f2b_kernel(const float *x, size_t n, __nv_bfloat16 *y) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16(x[i]);
+}
+
+// ---- exhaustive least-squares matcher (FP32)
+// Per trace: keep the points at or below its 507th smallest value (drops the
+// 5 largest of 512, the spike allowance); mask m_p.  For candidate g with
+// miss rates r_gp the best affine fit y ~ alpha + beta r_g over kept points
+// leaves residual Var_y - Cov^2 / Var_r (Var_y when Var_r is 0 or the slope is
+// not positive).  The smallest residual wins; equal residuals go to the lower
+// candidate index.
+constexpr int kKeep = kPoints - 5;
+
+__global__ void lsq_prep_kernel(const float *y, uint32_t n, float *ym, float *mask, float *stats) {
+    __shared__ float v[kPoints];
+    const uint32_t i = blockIdx.x;
+    if (i >= n) return;
+    for (int p = threadIdx.x; p < kPoints; p += blockDim.x) v[p] = y[(size_t)i * kPoints + p];
+    __syncthreads();
+    // bitonic sort of a copy in shared memory (ascending)
+    __shared__ float sv[kPoints];
+    for (int p = threadIdx.x; p < kPoints; p += blockDim.x) sv[p] = v[p];
+    __syncthreads();
+    for (int k = 2; k <= kPoints; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < kPoints; p += blockDim.x) {
+                const int q = p ^ j;
+                if (q > p) {
+                    const bool up = (p & k) == 0;
+                    const float a = sv[p], b = sv[q];
+                    if ((a > b) == up) { sv[p] = b; sv[q] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    const float thr = sv[kKeep - 1];
+    __shared__ float acc[3];
+    if (threadIdx.x < 3) acc[threadIdx.x] = 0.0f;
+    __syncthreads();
+    float c = 0.0f, sy = 0.0f, syy = 0.0f;
+    for (int p = threadIdx.x; p < kPoints; p += blockDim.x) {
+        const float m = v[p] <= thr ? 1.0f : 0.0f;
+        mask[(size_t)i * kPoints + p] = m;
+        ym[(size_t)i * kPoints + p] = m * v[p];
+        c += m;
+        sy += m * v[p];
+        syy += m * v[p] * v[p];
+    }
+    atomicAdd(&acc[0], c);
+    atomicAdd(&acc[1], sy);
+    atomicAdd(&acc[2], syy);
+    __syncthreads();
+    if (threadIdx.x < 3) stats[(size_t)i * 3 + threadIdx.x] = acc[threadIdx.x];
+}
+
+// 64 traces x 64 candidates per block, 256 threads with 4 x 4 outputs each
+__global__ void __launch_bounds__(256) lsq_kernel(const float *ym, const float *mask,
+                                                  const float *stats, uint32_t n,
+                                                  const float *rates, uint32_t G,
+                                                  unsigned long long *best) {
+    __shared__ float sY[32][65], sM[32][65], sR[32][65];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const uint32_t i0 = blockIdx.y * 64, g0 = blockIdx.x * 64;
+    float dyr[4][4], dr[4][4], drr[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dyr[a][b] = dr[a][b] = drr[a][b] = 0.0f;
+    for (int k0 = 0; k0 < kPoints; k0 += 32) {
+        for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+            const int kk = e & 31, r = e >> 5;
+            const uint32_t ti = i0 + r, gi = g0 + r;
+            sY[kk][r] = ti < n ? ym[(size_t)ti * kPoints + k0 + kk] : 0.0f;
+            sM[kk][r] = ti < n ? mask[(size_t)ti * kPoints + k0 + kk] : 0.0f;
+            sR[kk][r] = gi < G ? rates[(size_t)gi * kPoints + k0 + kk] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            float yv[4], mv[4], rv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                yv[a] = sY[kk][ty * 4 + a];
+                mv[a] = sM[kk][ty * 4 + a];
+                rv[a] = sR[kk][tx * 4 + a];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    dyr[a][b] = fmaf(yv[a], rv[b], dyr[a][b]);
+                    dr[a][b] = fmaf(mv[a], rv[b], dr[a][b]);
+                    drr[a][b] = fmaf(mv[a], rv[b] * rv[b], drr[a][b]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const uint32_t ti = i0 + ty * 4 + a;
+        if (ti >= n) continue;
+        const float cnt = stats[ti * 3], sy = stats[ti * 3 + 1], syy = stats[ti * 3 + 2];
+        const float var_y = syy - sy * sy / cnt;
+        unsigned long long b_best = ~0ull;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t gi = g0 + tx * 4 + b;
+            if (gi >= G) continue;
+            const float cov = dyr[a][b] - sy * dr[a][b] / cnt;
+            const float var_r = drr[a][b] - dr[a][b] * dr[a][b] / cnt;
+            float res = var_y;
+            if (var_r > 1e-12f && cov > 0.0f) res = var_y - cov * cov / var_r;
+            res = fmaxf(res, 0.0f);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(res) << 32) | gi;
+            b_best = key < b_best ? key : b_best;
+        }
+        if (b_best != ~0ull) atomicMin(best + ti, b_best);
+    }
+}
+
+__global__ void fill_u64_kernel(unsigned long long *p, size_t n, unsigned long long v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void lsq_unpack_kernel(const unsigned long long *best, uint32_t n, uint32_t *idx,
+                                  float *res) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    idx[i] = (uint32_t)(best[i] & 0xFFFFFFFFull);
+    if (res) res[i] = __uint_as_float((uint32_t)(best[i] >> 32));
+}
+
+// learned predictions -> candidate index through a label table; low
+// confidence or an unknown label combination marks the trace for fallback
+__global__ void route_kernel(const uint32_t *pred, const float *conf, uint32_t n,
+                             const uint32_t *label_to_cand, float thresh, uint32_t *cand_out,
+                             uint32_t *fallback_list, uint32_t *n_fallback) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t *p = pred + (size_t)i * 4;
+    const uint32_t key = ((p[0] * 4 + p[1]) * 7 + p[2]) * 3 + p[3];
+    const uint32_t c = label_to_cand[key];
+    if (conf[i] < thresh || c == 0xFFFFFFFFu) {
+        const uint32_t k = atomicAdd(n_fallback, 1u);
+        fallback_list[k] = i;
+        cand_out[i] = 0xFFFFFFFFu;
+    } else {
+        cand_out[i] = c;
+    }
+}
+
+__global__ void gather_rows_kernel(const float *x, const uint32_t *rows, const uint32_t *n_rows,
+                                   float *out) {
+    const uint32_t r = blockIdx.x;
+    if (r >= *n_rows) return;
+    const float *src = x + (size_t)rows[r] * kPoints;
+    for (int p = threadIdx.x; p < kPoints; p += blockDim.x) out[(size_t)r * kPoints + p] = src[p];
+}
+
+__global__ void scatter_fallback_kernel(const uint32_t *rows, const uint32_t *n_rows,
+                                        const uint32_t *idx, uint32_t *cand_out) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= *n_rows) return;
+    cand_out[rows[r]] = idx[r];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side
+struct InverseLayout {
+    // parameter segments (FP32 master / BF16 copy / grads / Adam moments share offsets)
+    size_t w[6], b[6], n_params;
+    int cin[4], lin[4];
+};
+
+InverseLayout inverse_layout() {
+    InverseLayout L{};
+    size_t off = 0;
+    const int cins[4] = {1, kCh, kCh, kCh};
+    const int lins[4] = {kPoints, kPoints / 2, kPoints / 4, kPoints / 8};
+    for (int l = 0; l < 4; ++l) {
+        L.cin[l] = cins[l];
+        L.lin[l] = lins[l];
+        L.w[l] = off;
+        off += (size_t)kCh * kKer * cins[l];
+        L.b[l] = off;
+        off += kCh;
+    }
+    L.w[4] = off;
+    off += (size_t)kHidden * kFlat;
+    L.b[4] = off;
+    off += kHidden;
+    L.w[5] = off;
+    off += (size_t)kLogits * kHidden;
+    L.b[5] = off;
+    off += kLogits;
+    L.n_params = off;
+    return L;
+}
+
+
+namespace {
+
+int grid_for(size_t n, int threads = 256) {
+    size_t b = (n + threads - 1) / threads;
+    if (b > 8192) b = 8192;
+    return (int)(b ? b : 1);
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+}  // namespace pchase
+
+using namespace pchase;
+
+struct pchase_inverse {
+    InverseLayout L;
+    uint32_t max_batch;
+    size_t p_w, p_wb, p_g, p_m, p_v, p_bytes;
+    size_t xb, cols[4], pre[4], act[4], pre4, h4, logits, dlog, dlogb, dh, dzf, dzb, dbig, dsmall,
+        work_bytes;
+};
+
+namespace {
+thread_local std::string g_inv_err;
+int inv_fail(int code, const char *m) {
+    g_inv_err = m;
+    return code;
+}
+#define INV_CUDA(call)                                       \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return inv_fail(PCHASE_ECUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+T *at(void *base, size_t off) {
+    return reinterpret_cast<T *>(static_cast<uint8_t *>(base) + off);
+}
+template <typename T>
+const T *at(const void *base, size_t off) {
+    return reinterpret_cast<const T *>(static_cast<const uint8_t *>(base) + off);
+}
+
+int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B, cudaStream_t st) {
+    const InverseLayout &L = h->L;
+    const __nv_bfloat16 *wb = at<__nv_bfloat16>(params, h->p_wb);
+    const float *wf = at<float>(params, h->p_w);
+    const __nv_bfloat16 *in = at<__nv_bfloat16>(work, h->xb);
+    for (int l = 0; l < 4; ++l) {
+        const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
+        __nv_bfloat16 *cols = at<__nv_bfloat16>(work, h->cols[l]);
+        const size_t nc = (size_t)B * lout * kKer * cin;
+        im2col_kernel<<<grid_for(nc), 256, 0, st>>>(in, (int)B, lin, cin, cols);
+        GemmArgs g{};
+        g.A = cols;
+        g.B = wb + L.w[l];
+        g.M = (int)(B * lout);
+        g.N = kCh;
+        g.K = kKer * cin;
+        g.lda = kKer * cin;
+        g.ldb = kKer * cin;
+        g.bias = wf + L.b[l];
+        g.pre = at<float>(work, h->pre[l]);
+        g.Cb = at<__nv_bfloat16>(work, h->act[l]);
+        g.ldc = kCh;
+        g.gelu = 1;
+        INV_CUDA(gemm(false, false, g, st));
+        in = g.Cb;
+    }
+    GemmArgs f{};
+    f.A = in;
+    f.B = wb + L.w[4];
+    f.M = (int)B;
+    f.N = kHidden;
+    f.K = kFlat;
+    f.lda = kFlat;
+    f.ldb = kFlat;
+    f.bias = wf + L.b[4];
+    f.pre = at<float>(work, h->pre4);
+    f.Cb = at<__nv_bfloat16>(work, h->h4);
+    f.ldc = kHidden;
+    f.gelu = 1;
+    INV_CUDA(gemm(false, false, f, st));
+    GemmArgs o{};
+    o.A = f.Cb;
+    o.B = wb + L.w[5];
+    o.M = (int)B;
+    o.N = kLogits;
+    o.K = kHidden;
+    o.lda = kHidden;
+    o.ldb = kHidden;
+    o.bias = wf + L.b[5];
+    o.Cf = at<float>(work, h->logits);
+    o.ldc = kLogits;
+    INV_CUDA(gemm(false, false, o, st));
+    return PCHASE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pchase_inverse_last_error(void) { return g_inv_err.c_str(); }
+
+int pchase_inverse_create(uint32_t max_batch, pchase_inverse **out) {
+    if (!out || max_batch == 0 || max_batch > (1u << 16))
+        return inv_fail(PCHASE_EINVAL, "max_batch must be in [1, 65536]");
+    auto *h = new (std::nothrow) pchase_inverse();
+    if (!h) return inv_fail(PCHASE_ENOMEM, "allocation");
+    h->L = inverse_layout();
+    h->max_batch = max_batch;
+    const size_t n = h->L.n_params;
+    size_t o = 0;
+    h->p_w = o; o = a256(o + 4 * n);
+    h->p_wb = o; o = a256(o + 2 * n);
+    h->p_g = o; o = a256(o + 4 * n);
+    h->p_m = o; o = a256(o + 4 * n);
+    h->p_v = o; o = a256(o + 4 * n);
+    h->p_bytes = o;
+    const size_t B = max_batch;
+    o = 0;
+    h->xb = o; o = a256(o + 2 * B * kPoints);
+    size_t big = B * kFlat;  // largest per-layer fp32 gradient
+    for (int l = 0; l < 4; ++l) {
+        const size_t lout = h->L.lin[l] / 2, cin = h->L.cin[l];
+        h->cols[l] = o; o = a256(o + 2 * B * lout * kKer * cin);
+        h->pre[l] = o; o = a256(o + 4 * B * lout * kCh);
+        h->act[l] = o; o = a256(o + 2 * B * lout * kCh);
+        big = std::max(big, B * lout * kKer * cin);
+        big = std::max(big, B * lout * kCh);
+        big = std::max(big, B * (size_t)h->L.lin[l] * cin);
+    }
+    h->pre4 = o; o = a256(o + 4 * B * kHidden);
+    h->h4 = o; o = a256(o + 2 * B * kHidden);
+    h->logits = o; o = a256(o + 4 * B * kLogits);
+    h->dlog = o; o = a256(o + 4 * B * kLogits);
+    h->dlogb = o; o = a256(o + 2 * B * kLogits);
+    h->dh = o; o = a256(o + 4 * B * kHidden);
+    h->dzf = o; o = a256(o + 4 * big);
+    h->dzb = o; o = a256(o + 2 * big);
+    h->dbig = o; o = a256(o + 4 * big);
+    h->dsmall = o; o = a256(o + 4 * big);
+    h->work_bytes = o;
+    *out = h;
+    return PCHASE_OK;
+}
+
+void pchase_inverse_destroy(pchase_inverse *h) { delete h; }
+uint64_t pchase_inverse_param_count(const pchase_inverse *h) { return h ? h->L.n_params : 0; }
+size_t pchase_inverse_param_bytes(const pchase_inverse *h) { return h ? h->p_bytes : 0; }
+size_t pchase_inverse_work_bytes(const pchase_inverse *h) { return h ? h->work_bytes : 0; }
+
+int pchase_inverse_init(const pchase_inverse *h, void *params, uint64_t seed,
+                        pchase_stream_t stream) {
+    if (!h || !params) return inv_fail(PCHASE_EINVAL, "NULL argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const InverseLayout &L = h->L;
+    InitSegs s{};
+    int k = 0;
+    for (int l = 0; l < 6; ++l) {
+        const size_t fan_in = l < 4 ? (size_t)kKer * L.cin[l] : (l == 4 ? kFlat : kHidden);
+        s.end[k] = L.b[l];
+        s.scale[k++] = sqrtf(6.0f / (float)fan_in) * (l == 5 ? 0.5f : 1.0f);
+        s.end[k] = l < 5 ? L.w[l + 1] : L.n_params;
+        s.scale[k++] = 0.0f;
+    }
+    s.n = k;
+    const size_t n = L.n_params;
+    init_kernel<<<grid_for(n), 256, 0, st>>>(at<float>(params, h->p_w),
+                                               at<__nv_bfloat16>(params, h->p_wb), n, s, seed);
+    INV_CUDA(cudaMemsetAsync(at<float>(params, h->p_m), 0, 4 * n, st));
+    INV_CUDA(cudaMemsetAsync(at<float>(params, h->p_v), 0, 4 * n, st));
+    INV_CUDA(cudaGetLastError());
+    return PCHASE_OK;
+}
+
+int pchase_inverse_synth(const float *rates, const uint32_t *targets, uint32_t n_geoms,
+                         uint64_t seed, uint64_t first, uint32_t n, const float *noise,
+                         float *x_out, uint32_t *labels_out, uint32_t *truth_out,
+                         pchase_stream_t stream) {
+    if (!rates || !targets || !x_out || !labels_out || !noise || n_geoms == 0)
+        return inv_fail(PCHASE_EINVAL, "NULL argument or no geometries");
+    if (n == 0) return PCHASE_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    synth_kernel<<<n, 128, 0, st>>>(rates, targets, n_geoms, seed, first, n, noise[0], noise[1],
+                                    logf(noise[2]), logf(noise[3]), noise[4], noise[5], noise[6],
+                                    noise[7], x_out, nullptr, labels_out, truth_out);
+    INV_CUDA(cudaGetLastError());
+    return PCHASE_OK;
+}
+
+int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work, const float *x,
+                              const uint32_t *labels, uint32_t B, float lr, uint32_t step,
+                              float *loss_accum, pchase_stream_t stream) {
+    if (!h || !params || !work || !x || !labels || !loss_accum)
+        return inv_fail(PCHASE_EINVAL, "NULL argument");
+    if (B == 0 || B > h->max_batch) return inv_fail(PCHASE_ERANGE, "batch above max_batch");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const InverseLayout &L = h->L;
+    f2b_kernel<<<grid_for((size_t)B * kPoints), 256, 0, st>>>(x, (size_t)B * kPoints,
+                                                               at<__nv_bfloat16>(work, h->xb));
+    int rc = forward(h, params, work, B, st);
+    if (rc) return rc;
+    const size_t n = L.n_params;
+    float *grad = at<float>(params, h->p_g);
+    const __nv_bfloat16 *wb = at<__nv_bfloat16>(params, h->p_wb);
+    INV_CUDA(cudaMemsetAsync(grad, 0, 4 * n, st));
+    float *dlog = at<float>(work, h->dlog);
+    __nv_bfloat16 *dlogb = at<__nv_bfloat16>(work, h->dlogb);
+    xent_kernel<<<(B + 127) / 128, 128, 0, st>>>(at<float>(work, h->logits), labels, (int)B, dlog,
+                                                 dlogb, loss_accum);
+    // heads
+    {
+        GemmArgs g{};
+        g.A = dlogb; g.B = at<__nv_bfloat16>(work, h->h4);
+        g.M = kLogits; g.N = kHidden; g.K = (int)B; g.lda = kLogits; g.ldb = kHidden;
+        g.Cf = grad + L.w[5]; g.ldc = kHidden;
+        INV_CUDA(gemm(true, true, g, st));
+        colsum_atomic_kernel<<<dim3(1, (B + 255) / 256), 32, 0, st>>>(dlog, (int)B, kLogits, 256,
+                                                                       grad + L.b[5]);
+        GemmArgs d{};
+        d.A = dlogb; d.B = wb + L.w[5];
+        d.M = (int)B; d.N = kHidden; d.K = kLogits; d.lda = kLogits; d.ldb = kHidden;
+        d.Cf = at<float>(work, h->dh); d.ldc = kHidden;
+        INV_CUDA(gemm(false, true, d, st));
+    }
+    // FC
+    float *dzf = at<float>(work, h->dzf);
+    __nv_bfloat16 *dzb = at<__nv_bfloat16>(work, h->dzb);
+    float *dbig = at<float>(work, h->dbig);
+    float *dsmall = at<float>(work, h->dsmall);
+    {
+        const size_t m = (size_t)B * kHidden;
+        gelu_back_kernel<<<grid_for(m), 256, 0, st>>>(at<float>(work, h->dh),
+                                                      at<float>(work, h->pre4), m, dzf, dzb);
+        GemmArgs g{};
+        g.A = dzb; g.B = at<__nv_bfloat16>(work, h->act[3]);
+        g.M = kHidden; g.N = kFlat; g.K = (int)B; g.lda = kHidden; g.ldb = kFlat;
+        g.Cf = grad + L.w[4]; g.ldc = kFlat;
+        INV_CUDA(gemm(true, true, g, st));
+        colsum_atomic_kernel<<<dim3((kHidden + 127) / 128, (B + 255) / 256), 128, 0, st>>>(
+            dzf, (int)B, kHidden, 256, grad + L.b[4]);
+        GemmArgs d{};
+        d.A = dzb; d.B = wb + L.w[4];
+        d.M = (int)B; d.N = kFlat; d.K = kHidden; d.lda = kHidden; d.ldb = kFlat;
+        d.Cf = dbig; d.ldc = kFlat;  // d(act3) [B, 32, 64]
+        INV_CUDA(gemm(false, true, d, st));
+    }
+    // convolutions, last to first
+    for (int l = 3; l >= 0; --l) {
+        const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
+        const size_t rows = (size_t)B * lout, m = rows * kCh;
+        gelu_back_kernel<<<grid_for(m), 256, 0, st>>>(dbig, at<float>(work, h->pre[l]), m, dzf, dzb);
+        GemmArgs g{};
+        g.A = dzb; g.B = at<__nv_bfloat16>(work, h->cols[l]);
+        g.M = kCh; g.N = kKer * cin; g.K = (int)rows; g.lda = kCh; g.ldb = kKer * cin;
+        g.Cf = grad + L.w[l]; g.ldc = kKer * cin;
+        INV_CUDA(gemm(true, true, g, st));
+        colsum_atomic_kernel<<<dim3(1, (unsigned)((rows + 1023) / 1024)), 64, 0, st>>>(
+            dzf, (int)rows, kCh, 1024, grad + L.b[l]);
+        if (l > 0) {
+            GemmArgs d{};
+            d.A = dzb; d.B = wb + L.w[l];
+            d.M = (int)rows; d.N = kKer * cin; d.K = kCh; d.lda = kCh; d.ldb = kKer * cin;
+            d.Cf = dsmall; d.ldc = kKer * cin;
+            INV_CUDA(gemm(false, true, d, st));
+            const size_t nx = (size_t)B * lin * cin;
+            col2im_kernel<<<grid_for(nx), 256, 0, st>>>(dsmall, (int)B, lin, cin, dbig);
+        }
+    }
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)step + 1.0f), c2 = 1.0f - powf(b2, (float)step + 1.0f);
+    adam_kernel<<<grid_for(n), 256, 0, st>>>(at<float>(params, h->p_w), grad,
+                                              at<float>(params, h->p_m), at<float>(params, h->p_v),
+                                              at<__nv_bfloat16>(params, h->p_wb), n, lr, b1, b2,
+                                              1e-8f, c1, c2);
+    INV_CUDA(cudaGetLastError());
+    return PCHASE_OK;
+}
+
+int pchase_inverse_infer(const pchase_inverse *h, const void *params, void *work, const float *x,
+                         uint32_t n, uint32_t *pred_out, float *conf_out, float *logits_out,
+                         pchase_stream_t stream) {
+    if (!h || !params || !work || !x || !pred_out || !conf_out)
+        return inv_fail(PCHASE_EINVAL, "NULL argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (uint32_t b0 = 0; b0 < n; b0 += h->max_batch) {
+        const uint32_t B = std::min(h->max_batch, n - b0);
+        f2b_kernel<<<grid_for((size_t)B * kPoints), 256, 0, st>>>(
+            x + (size_t)b0 * kPoints, (size_t)B * kPoints, at<__nv_bfloat16>(work, h->xb));
+        int rc = forward(h, params, work, B, st);
+        if (rc) return rc;
+        const float *lg = at<float>(work, h->logits);
+        predict_kernel<<<(B + 127) / 128, 128, 0, st>>>(lg, (int)B, pred_out + (size_t)b0 * 4,
+                                                        conf_out + b0);
+        if (logits_out)
+            INV_CUDA(cudaMemcpyAsync(logits_out + (size_t)b0 * kLogits, lg,
+                                     (size_t)B * kLogits * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    INV_CUDA(cudaGetLastError());
+    return PCHASE_OK;
+}
+
+size_t pchase_lsq_work_bytes(uint32_t n) {
+    return a256((size_t)n * kPoints * 4) * 2 + a256((size_t)n * 12) + a256((size_t)n * 8);
+}
+
+int pchase_lsq_match(const float *rates, uint32_t n_geoms, const float *y, uint32_t n,
+                     uint32_t *best_out, float *resid_out, void *work, pchase_stream_t stream) {
+    if (!rates || !y || !best_out || !work || n_geoms == 0)
+        return inv_fail(PCHASE_EINVAL, "NULL argument or no geometries");
+    if (n == 0) return PCHASE_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    float *ym = at<float>(work, 0);
+    float *mask = at<float>(work, a256((size_t)n * kPoints * 4));
+    float *stats = at<float>(work, 2 * a256((size_t)n * kPoints * 4));
+    unsigned long long *best = at<unsigned long long>(
+        work, 2 * a256((size_t)n * kPoints * 4) + a256((size_t)n * 12));
+    lsq_prep_kernel<<<n, 256, 0, st>>>(y, n, ym, mask, stats);
+    fill_u64_kernel<<<grid_for(n), 256, 0, st>>>(best, n, ~0ull);
+    dim3 grid((n_geoms + 63) / 64, (n + 63) / 64);
+    lsq_kernel<<<grid, 256, 0, st>>>(ym, mask, stats, n, rates, n_geoms, best);
+    lsq_unpack_kernel<<<(n + 255) / 256, 256, 0, st>>>(best, n, best_out, resid_out);
+    INV_CUDA(cudaGetLastError());
+    return PCHASE_OK;
+}
+
+int pchase_inverse_classify(const pchase_inverse *h, const void *params, void *work,
+                            const float *x, uint32_t n, const uint32_t *label_to_cand,
+                            const float *rates, uint32_t n_geoms, float conf_thresh,
+                            uint32_t *pred_scratch, float *conf_out, uint32_t *cand_out,
+                            uint32_t *fallback_list, uint32_t *n_fallback, float *fb_rows,
+                            uint32_t *fb_idx, void *lsq_work, pchase_stream_t stream) {
+    if (!h || !params || !work || !x || !label_to_cand || !rates || !pred_scratch || !conf_out ||
+        !cand_out || !fallback_list || !n_fallback || !fb_rows || !fb_idx || !lsq_work)
+        return inv_fail(PCHASE_EINVAL, "NULL argument");
+    if (n == 0) return PCHASE_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = pchase_inverse_infer(h, params, work, x, n, pred_scratch, conf_out, nullptr, stream);
+    if (rc) return rc;
+    INV_CUDA(cudaMemsetAsync(n_fallback, 0, 4, st));
+    route_kernel<<<(n + 255) / 256, 256, 0, st>>>(pred_scratch, conf_out, n, label_to_cand,
+                                                  conf_thresh, cand_out, fallback_list, n_fallback);
+    // the fallback runs over a compacted copy; its size is known only on the
+    // device, so the matcher covers the worst case n rows and rows past the
+    // count are left out by the scatter
+    gather_rows_kernel<<<n, 128, 0, st>>>(x, fallback_list, n_fallback, fb_rows);
+    rc = pchase_lsq_match(rates, n_geoms, fb_rows, n, fb_idx, nullptr, lsq_work, stream);
+    if (rc) return rc;
+    scatter_fallback_kernel<<<(n + 255) / 256, 256, 0, st>>>(fallback_list, n_fallback, fb_idx,
+                                                             cand_out);
+    INV_CUDA(cudaGetLastError());
+    return PCHASE_OK;
+}
+
+}  // extern "C"

@@ -211,10 +211,12 @@ struct RoundResolver {
         const uint32_t key = head ? set : (0x80000000u | (uint32_t)lane);
         const uint32_t peers = __match_any_sync(kFull, key);
         const uint32_t rank = __popc(peers & lt);
-        const uint32_t rounds = __reduce_max_sync(kFull, head ? rank + 1 : 0u);
-        bool miss = false;
-        for (uint32_t r = 0; r < rounds; ++r) {
-            if (head && rank == r) miss = S.access(set, line, t);
+        bool miss = false, pending = head;
+        for (uint32_t r = 0; __any_sync(kFull, pending); ++r) {
+            if (pending && rank == r) {
+                miss = S.access(set, line, t);
+                pending = false;
+            }
             __syncwarp();
         }
         return miss;
@@ -670,9 +672,11 @@ __device__ __forceinline__ void run_item(const SimItem it, Res &R, const SimOut 
             const uint32_t ln = j >> lsh;
             line[u] = ln;
             set[u] = ln - div_q(ln, mm, s1, s2) * sets;
-            uint32_t prev = __shfl_up_sync(kFull, ln, 1);
-            if (lane == 0) prev = carry;
-            carry = __shfl_sync(kFull, ln, 31);
+            // one rotate: lane i gets lane i-1's line; lane 0 gets lane 31's,
+            // which is the previous access for the next step's lane 0
+            const uint32_t rot = __shfl_sync(kFull, ln, (lane + 31) & 31);
+            const uint32_t prev = lane == 0 ? carry : rot;
+            carry = rot;
             head[u] = active && ln != prev;
         }
         // ---- state updates in trace order, then the step's miss word

@@ -1,0 +1,192 @@
+"""Learned inverse (S7) driver: argument marshalling and the training loop's
+sequencing over the C ABI.  Every computation (simulation, synthesis, the
+network, the least-squares matcher) runs in the CUDA library."""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+
+import numpy as np
+import torch
+
+from . import capi as C
+from . import workloads as W
+from .api import SimPlan
+
+DEV = "cuda"
+N_LABELS = 17 * 4 * 7 * 3
+
+
+def _check(rc):
+    if rc != C.OK:
+        L = C.load()
+        raise C.PchaseError(rc, L.pchase_inverse_last_error().decode() or
+                            L.pchase_last_error_string().decode())
+
+
+def canonical_key(g: W.Geom):
+    """Identifiability order (policy LRU < FIFO < RANDOM, larger b, fewer ways,
+    smaller C) used to pick one representative of geometries a plan cannot
+    separate."""
+    return (g.policy, -g.b, g.ways, g.C)
+
+
+def candidate_table(seed_base: int = 0x5EED):
+    """Every grid geometry under every policy, in canonical order."""
+    cands = [W.Geom(C_, b, a, T, p, seed_base + i)
+             for i, (C_, b, a, T) in enumerate(W.geometry_grid()) for p in (0, 1, 2)]
+    return sorted(cands, key=canonical_key)
+
+
+def plan_traces():
+    """The 512 plan points as simulator trace descriptors (explicit traces on
+    the device for the hot re-touch points)."""
+    pts = W.p512_plan()
+    traces, keep = [], []
+    for run, tr in pts:
+        if tr is None:
+            traces.append((None, run.length, run.warmup, run.n_elems, run.stride))
+        else:
+            t = torch.from_numpy(tr.view(np.int32)).to(DEV)
+            keep.append(t)
+            traces.append((t, run.length, run.warmup, run.n_elems, 1))
+    return pts, traces, keep
+
+
+def rate_table(cands, tune=None):
+    """Miss rate after warm-up of every candidate at every plan point
+    (FP32 [G, 512]), by one simulator plan over candidates x points."""
+    pts, traces, keep = plan_traces()
+    plan = SimPlan(cands, traces, tune=tune)
+    _, counts = plan.run(want_bitmaps=False)
+    torch.cuda.synchronize()
+    c = counts.view(-1, 2)[:, 1].view(len(cands), len(pts)).double()
+    meas = torch.tensor([r.length - r.warmup for r, _ in pts], dtype=torch.float64, device=DEV)
+    rates = (c / meas).float().contiguous()
+    return rates, counts.view(len(cands), len(pts), 2)
+
+
+def classes_from_rates(cands, rates: torch.Tensor):
+    """Candidates with identical rate rows form one class; returns per
+    candidate its class id and its class representative (the first member in
+    canonical order), the targets (labels of the representative) and the
+    label -> candidate table."""
+    r = rates.cpu().numpy()
+    rep = {}
+    rep_of = np.zeros(len(cands), dtype=np.int64)
+    for i in range(len(cands)):
+        h = hashlib.sha1(r[i].tobytes()).hexdigest()
+        if h not in rep:
+            rep[h] = i
+        rep_of[i] = rep[h]
+    targets = np.array([W.geometry_label(cands[rep_of[i]]) for i in range(len(cands))],
+                       dtype=np.uint32)
+    l2c = np.full(N_LABELS, 0xFFFFFFFF, dtype=np.uint32)
+    for i, g in enumerate(cands):
+        c, b, w, p = W.geometry_label(g)
+        l2c[((c * 4 + b) * 7 + w) * 3 + p] = rep_of[i]
+    return rep_of, targets, l2c
+
+
+class LearnedInverse:
+    def __init__(self, max_batch: int = 4096):
+        self.L = C.load()
+        h = ctypes.c_void_p()
+        _check(self.L.pchase_inverse_create(max_batch, ctypes.byref(h)))
+        self.h = h
+        self.max_batch = max_batch
+        self.n_params = int(self.L.pchase_inverse_param_count(h))
+        self.params = torch.empty(int(self.L.pchase_inverse_param_bytes(h)) + 256,
+                                  dtype=torch.uint8, device=DEV)
+        self.work = torch.empty(int(self.L.pchase_inverse_work_bytes(h)) + 256,
+                                dtype=torch.uint8, device=DEV)
+        self._p = (C.ptr(self.params) + 255) & ~255
+        self._w = (C.ptr(self.work) + 255) & ~255
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.L.pchase_inverse_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def weights(self) -> torch.Tensor:
+        """FP32 master weights (a view into the parameter buffer)."""
+        off = self._p - C.ptr(self.params)
+        return self.params[off:off + 4 * self.n_params].view(torch.float32)
+
+    def init(self, seed: int = 1):
+        _check(self.L.pchase_inverse_init(self.h, self._p, seed, C.stream_handle()))
+
+    @staticmethod
+    def synth(rates: torch.Tensor, targets: torch.Tensor, n: int, seed: int, first: int = 0,
+              noise: dict | None = None):
+        L = C.load()
+        nz = noise or W.latency_noise_params()
+        arr = (ctypes.c_float * 8)(nz["t0_lo"], nz["t0_hi"], nz["rho_lo"], nz["rho_hi"],
+                                   nz["sigma"], nz["spike_p"], nz["spike_lo"], nz["spike_hi"])
+        x = torch.empty(n, W.PLAN_POINTS, dtype=torch.float32, device=DEV)
+        lab = torch.empty(n, 4, dtype=torch.int32, device=DEV)
+        truth = torch.empty(max(1, n), dtype=torch.int32, device=DEV)
+        _check(L.pchase_inverse_synth(C.ptr(rates), C.ptr(targets), rates.shape[0], seed, first, n,
+                                      ctypes.addressof(arr), C.ptr(x), C.ptr(lab), C.ptr(truth),
+                                      C.stream_handle()))
+        return x, lab, truth[:n]
+
+    def train(self, rates, targets, steps: int, batch: int, lr: float = 2e-3, seed: int = 0x5EED0004,
+              log_every: int = 0):
+        """Adam with a cosine schedule on freshly synthesised batches."""
+        loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+        hist = []
+        for s in range(steps):
+            x, lab, _ = self.synth(rates, targets, batch, seed, first=s * batch)
+            lr_s = lr * 0.5 * (1.0 + np.cos(np.pi * s / max(1, steps)))
+            loss.zero_()
+            _check(self.L.pchase_inverse_train_step(self.h, self._p, self._w, C.ptr(x), C.ptr(lab),
+                                                    batch, lr_s, s, C.ptr(loss),
+                                                    C.stream_handle()))
+            if log_every and (s % log_every == 0 or s == steps - 1):
+                hist.append((s, float(loss.item())))
+        return hist
+
+    def infer(self, x: torch.Tensor, want_logits: bool = False):
+        n = x.shape[0]
+        pred = torch.empty(max(1, n), 4, dtype=torch.int32, device=DEV)
+        conf = torch.empty(max(1, n), dtype=torch.float32, device=DEV)
+        lg = torch.empty(max(1, n), 31, dtype=torch.float32, device=DEV) if want_logits else None
+        _check(self.L.pchase_inverse_infer(self.h, self._p, self._w, C.ptr(x), n, C.ptr(pred),
+                                           C.ptr(conf), C.ptr(lg), C.stream_handle()))
+        return pred[:n], conf[:n], (lg[:n] if lg is not None else None)
+
+    def classify(self, x: torch.Tensor, l2c: torch.Tensor, rates: torch.Tensor,
+                 conf_thresh: float = 0.9):
+        """Learned answer with least-squares fallback: (candidate index per
+        trace, number of fallbacks)."""
+        n = x.shape[0]
+        pred = torch.empty(max(1, n), 4, dtype=torch.int32, device=DEV)
+        conf = torch.empty(max(1, n), dtype=torch.float32, device=DEV)
+        cand = torch.empty(max(1, n), dtype=torch.int32, device=DEV)
+        fl = torch.empty(max(1, n), dtype=torch.int32, device=DEV)
+        nf = torch.zeros(1, dtype=torch.int32, device=DEV)
+        rows = torch.empty(max(1, n), W.PLAN_POINTS, dtype=torch.float32, device=DEV)
+        idx = torch.empty(max(1, n), dtype=torch.int32, device=DEV)
+        lw = torch.empty(int(self.L.pchase_lsq_work_bytes(n)) + 256, dtype=torch.uint8, device=DEV)
+        _check(self.L.pchase_inverse_classify(self.h, self._p, self._w, C.ptr(x), n, C.ptr(l2c),
+                                              C.ptr(rates), rates.shape[0], conf_thresh,
+                                              C.ptr(pred), C.ptr(conf), C.ptr(cand), C.ptr(fl),
+                                              C.ptr(nf), C.ptr(rows), C.ptr(idx),
+                                              (C.ptr(lw) + 255) & ~255, C.stream_handle()))
+        return cand[:n], nf
+
+
+def lsq_match(rates: torch.Tensor, y: torch.Tensor):
+    """Exhaustive least-squares matcher: (best candidate index, residual)."""
+    L = C.load()
+    n = y.shape[0]
+    best = torch.empty(max(1, n), dtype=torch.int32, device=DEV)
+    res = torch.empty(max(1, n), dtype=torch.float32, device=DEV)
+    lw = torch.empty(int(L.pchase_lsq_work_bytes(n)) + 256, dtype=torch.uint8, device=DEV)
+    _check(L.pchase_lsq_match(C.ptr(rates), rates.shape[0], C.ptr(y), n, C.ptr(best), C.ptr(res),
+                              (C.ptr(lw) + 255) & ~255, C.stream_handle()))
+    return best[:n], res[:n]

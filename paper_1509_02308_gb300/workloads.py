@@ -189,3 +189,85 @@ def describe_config2(geoms, runs) -> dict:
 
 def log2i(x: int) -> int:
     return int(math.log2(x))
+
+
+# ------------------------------------------------------- learned inverse (S7)
+PLAN_POINTS = 512
+WAY_LABELS = (1, 2, 4, 8, 16, 32)  # label 6: any other associativity (full)
+
+
+def geometry_label(g) -> tuple:
+    """(capacity index, line-size index, ways index, policy) of a grid geometry."""
+    ci = CAPACITIES.index(g.C)
+    bi = LINE_SIZES.index(g.b)
+    wi = WAY_LABELS.index(g.ways) if g.ways in WAY_LABELS else 6
+    return ci, bi, wi, g.policy
+
+
+def _logspace_bytes(lo: int, hi: int, n: int, mult: int):
+    out = []
+    for k in range(n):
+        v = lo * (hi / lo) ** (k / (n - 1))
+        out.append(max(mult, int(round(v / mult)) * mult))
+    return out
+
+
+def hot_retouch_trace(n_bytes: int, stream_stride: int = 64, words: int = 8,
+                      max_len: int = 1 << 15) -> np.ndarray:
+    """Accesses alternate between a hot 32-byte line (its `words` words in
+    turn, as a chain through distinct elements would) and a uniform stream
+    over [stream_stride, n_bytes), in the style of the non-uniform chains of
+    Fig. 10.  Returns element indices, two passes of the stream or max_len."""
+    stream = np.arange(stream_stride, n_bytes, stream_stride, dtype=np.int64) // 4
+    if stream.size == 0:
+        stream = np.array([stream_stride // 4], dtype=np.int64)
+    L = min(max_len, 4 * stream.size)
+    k = np.arange(L)
+    hot = (k // 2) % words
+    st = stream[(k // 2) % stream.size]
+    return np.where(k % 2 == 0, hot, st).astype(np.uint32)
+
+
+def p512_plan():
+    """The 512-point plan of the learned inverse: list of (Run, explicit
+    trace or None).  Points: 176 with s = 4 B and 176 with s = 32 B over array
+    sizes log-spaced from 512 B to 512 KB; 61 with s = 128 B over 1-512 KB;
+    35 Saavedra stride sweeps (N = 512 KB and 1 MB, s = 4 B * 2^j); 64 hot
+    re-touch traces over 1-512 KB.  Each uniform point runs one warm-up pass
+    (at most 2^17 accesses) and then at most 2^15 measured accesses."""
+    pts = []
+
+    def uni(nb, sb):
+        n, s = nb // 4, sb // 4
+        per = n // math.gcd(n, s)
+        warm = min(per, 1 << 17)
+        meas = min(per, 1 << 15)
+        pts.append((Run(n, s, warm + meas, warm), None))
+
+    for nb in _logspace_bytes(512, 512 << 10, 176, 4):
+        uni(nb, 4)
+    for nb in _logspace_bytes(512, 512 << 10, 176, 32):
+        uni(nb, 32)
+    for nb in _logspace_bytes(1024, 512 << 10, 61, 128):
+        uni(nb, 128)
+    for nb, jmax in ((512 << 10, 17), (1 << 20, 18)):
+        for j in range(jmax):
+            uni(nb, 4 << j)
+    for nb in _logspace_bytes(1024, 512 << 10, 64, 64):
+        tr = hot_retouch_trace(nb)
+        n = int(tr.max()) + 1
+        warm = tr.size // 2
+        pts.append((Run(n, 1, tr.size, warm), tr))
+    assert len(pts) == PLAN_POINTS, len(pts)
+    return pts
+
+
+def latency_noise_params():
+    """Synthetic timing model of the learned-inverse traces (seeded on the
+    device): per trace t0 ~ U[20, 400] cycles and t1 = t0 * rho with
+    log(rho) ~ U[log 1.1, log 30] (the span of Fig. 11's latency spectrum);
+    per point latency t0 + (t1 - t0) * r, Gaussian relative jitter sigma
+    2 %, spikes on 0.5 % of points scaled by U[2, 10]; then min-max
+    normalisation to [0, 1]."""
+    return {"t0_lo": 20.0, "t0_hi": 400.0, "rho_lo": 1.5, "rho_hi": 30.0, "sigma": 0.02,
+            "spike_p": 0.005, "spike_lo": 2.0, "spike_hi": 10.0}
