@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--items", type=int, default=4096)
+    p.add_argument("--max-len", type=int, default=1 << 20,
+                   help="longest trace of the batch (smaller for profiler captures)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-infer", action="store_true")
@@ -185,7 +187,8 @@ def ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    geoms, runs = W.config2(n_items=args.items, seed_base=0x5EED0002 + rank * args.items)
+    geoms, runs = W.config2(n_items=args.items, seed_base=0x5EED0002 + rank * args.items,
+                            max_len=args.max_len)
     total_acc = W.total_accesses(runs)
     offs = np.zeros(len(runs) + 1, dtype=np.uint64)
     offs[1:] = np.cumsum([r.length for r in runs])

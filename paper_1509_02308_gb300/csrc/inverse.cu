@@ -44,6 +44,8 @@ struct GemmArgs {
     float *pre;
     int ldc;
     int gelu;
+    int splitk;  // > 1: blockIdx.z takes a K slice and atomically adds into Cf
+    int vec_a, vec_b;  // 16-byte loads allowed along the contiguous dimension
 };
 
 __device__ __forceinline__ float gelu_f(float x) {
@@ -90,23 +92,84 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
     const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = 0; k0 < g.K; k0 += GBK) {
+    // K slice of this block (split-K)
+    const int kchunk = ((g.K + g.splitk - 1) / g.splitk + GBK - 1) / GBK * GBK;
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(g.K, kbeg + kchunk);
+    for (int k0 = kbeg; k0 < kend; k0 += GBK) {
         // ---- tiles into shared memory, k contiguous
-        for (int e = tid; e < GBM * GBK; e += 256) {
-            int r, c;
-            if (A_COL) { c = e / GBM; r = e % GBM; } else { r = e / GBK; c = e % GBK; }
-            const int m = m0 + r, k = k0 + c;
-            __nv_bfloat16 v = zero;
-            if (m < g.M && k < g.K) v = A_COL ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
-            As[r][c] = v;
+        if (g.vec_a) {
+            // 8 consecutive elements along the contiguous dimension per load
+            for (int e = tid; e < GBM * GBK / 8; e += 256) {
+                int r, c;
+                if (A_COL) { c = e / (GBM / 8); r = (e % (GBM / 8)) * 8; } else { r = e / (GBK / 8); c = (e % (GBK / 8)) * 8; }
+                const int m = m0 + r, k = k0 + c;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (A_COL) {
+                    if (k < kend && m + 7 < g.M) v = *reinterpret_cast<const uint4 *>(g.A + (size_t)k * g.lda + m);
+                    else if (k < kend) {
+                        __nv_bfloat16 t[8];
+                        for (int q = 0; q < 8; ++q) t[q] = m + q < g.M ? g.A[(size_t)k * g.lda + m + q] : zero;
+                        v = *reinterpret_cast<uint4 *>(t);
+                    }
+                    const __nv_bfloat16 *t = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) As[r + q][c] = t[q];
+                } else {
+                    if (m < g.M && k + 7 < kend) v = *reinterpret_cast<const uint4 *>(g.A + (size_t)m * g.lda + k);
+                    else if (m < g.M) {
+                        __nv_bfloat16 t[8];
+                        for (int q = 0; q < 8; ++q) t[q] = k + q < kend ? g.A[(size_t)m * g.lda + k + q] : zero;
+                        v = *reinterpret_cast<uint4 *>(t);
+                    }
+                    *reinterpret_cast<uint4 *>(&As[r][c]) = v;
+                }
+            }
+        } else {
+            for (int e = tid; e < GBM * GBK; e += 256) {
+                int r, c;
+                if (A_COL) { c = e / GBM; r = e % GBM; } else { r = e / GBK; c = e % GBK; }
+                const int m = m0 + r, k = k0 + c;
+                __nv_bfloat16 v = zero;
+                if (m < g.M && k < kend) v = A_COL ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
+                As[r][c] = v;
+            }
         }
-        for (int e = tid; e < GBN * GBK; e += 256) {
-            int r, c;
-            if (B_ROW) { c = e / GBN; r = e % GBN; } else { r = e / GBK; c = e % GBK; }
-            const int n = n0 + r, k = k0 + c;
-            __nv_bfloat16 v = zero;
-            if (n < g.N && k < g.K) v = B_ROW ? g.B[(size_t)k * g.ldb + n] : g.B[(size_t)n * g.ldb + k];
-            Bs[r][c] = v;
+        if (g.vec_b) {
+            for (int e = tid; e < GBN * GBK / 8; e += 256) {
+                int r, c;
+                if (B_ROW) { c = e / (GBN / 8); r = (e % (GBN / 8)) * 8; } else { r = e / (GBK / 8); c = (e % (GBK / 8)) * 8; }
+                const int n = n0 + r, k = k0 + c;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (B_ROW) {
+                    if (k < kend && n + 7 < g.N) v = *reinterpret_cast<const uint4 *>(g.B + (size_t)k * g.ldb + n);
+                    else if (k < kend) {
+                        __nv_bfloat16 t[8];
+                        for (int q = 0; q < 8; ++q) t[q] = n + q < g.N ? g.B[(size_t)k * g.ldb + n + q] : zero;
+                        v = *reinterpret_cast<uint4 *>(t);
+                    }
+                    const __nv_bfloat16 *t = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) Bs[r + q][c] = t[q];
+                } else {
+                    if (n < g.N && k + 7 < kend) v = *reinterpret_cast<const uint4 *>(g.B + (size_t)n * g.ldb + k);
+                    else if (n < g.N) {
+                        __nv_bfloat16 t[8];
+                        for (int q = 0; q < 8; ++q) t[q] = k + q < kend ? g.B[(size_t)n * g.ldb + k + q] : zero;
+                        v = *reinterpret_cast<uint4 *>(t);
+                    }
+                    *reinterpret_cast<uint4 *>(&Bs[r][c]) = v;
+                }
+            }
+        } else {
+            for (int e = tid; e < GBN * GBK; e += 256) {
+                int r, c;
+                if (B_ROW) { c = e / GBN; r = e % GBN; } else { r = e / GBK; c = e % GBK; }
+                const int n = n0 + r, k = k0 + c;
+                __nv_bfloat16 v = zero;
+                if (n < g.N && k < kend) v = B_ROW ? g.B[(size_t)k * g.ldb + n] : g.B[(size_t)n * g.ldb + k];
+                Bs[r][c] = v;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -150,8 +213,12 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g) {
                 const int n = n0 + wn + j * 8 + ((lane & 3) << 1) + (q & 1);
                 if (m >= g.M || n >= g.N) continue;
                 float v = acc[i][j][q];
-                if (g.bias) v += g.bias[n];
                 const size_t o = (size_t)m * g.ldc + n;
+                if (g.splitk > 1) {
+                    atomicAdd(g.Cf + o, v);
+                    continue;
+                }
+                if (g.bias) v += g.bias[n];
                 if (g.pre) g.pre[o] = v;
                 if (g.gelu) v = gelu_f(v);
                 if (g.Cf) g.Cf[o] = v;
@@ -159,9 +226,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g) {
             }
 }
 
-cudaError_t gemm(bool a_col, bool b_row, const GemmArgs &g, cudaStream_t st) {
-    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-    dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM);
+cudaError_t gemm(bool a_col, bool b_row, const GemmArgs &g0, cudaStream_t st) {
+    if (g0.M <= 0 || g0.N <= 0) return cudaSuccess;
+    GemmArgs g = g0;
+    if (g.splitk < 1) g.splitk = 1;
+    // 16-byte loads need an 8-element-aligned leading dimension and base
+    g.vec_a = (g.lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0);
+    g.vec_b = (g.ldb % 8 == 0) && ((reinterpret_cast<uintptr_t>(g.B) & 15) == 0);
+    dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, g.splitk);
     if (!a_col && !b_row) gemm_kernel<false, false><<<grid, 256, 0, st>>>(g);
     else if (!a_col && b_row) gemm_kernel<false, true><<<grid, 256, 0, st>>>(g);
     else if (a_col && !b_row) gemm_kernel<true, false><<<grid, 256, 0, st>>>(g);
@@ -601,6 +673,14 @@ InverseLayout inverse_layout() {
 
 namespace {
 
+// enough K slices to give every SM a few tiles, each slice >= 512 deep
+int splitk_for(int M, int N, int K) {
+    const int tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
+    int s = (4 * 152 + tiles - 1) / tiles;
+    s = std::min(s, std::max(1, K / 512));
+    return std::max(1, s);
+}
+
 int grid_for(size_t n, int threads = 256) {
     size_t b = (n + threads - 1) / threads;
     if (b > 8192) b = 8192;
@@ -817,7 +897,7 @@ int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work,
         GemmArgs g{};
         g.A = dlogb; g.B = at<__nv_bfloat16>(work, h->h4);
         g.M = kLogits; g.N = kHidden; g.K = (int)B; g.lda = kLogits; g.ldb = kHidden;
-        g.Cf = grad + L.w[5]; g.ldc = kHidden;
+        g.Cf = grad + L.w[5]; g.ldc = kHidden; g.splitk = splitk_for(g.M, g.N, g.K);
         INV_CUDA(gemm(true, true, g, st));
         colsum_atomic_kernel<<<dim3(1, (B + 255) / 256), 32, 0, st>>>(dlog, (int)B, kLogits, 256,
                                                                        grad + L.b[5]);
@@ -839,7 +919,7 @@ int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work,
         GemmArgs g{};
         g.A = dzb; g.B = at<__nv_bfloat16>(work, h->act[3]);
         g.M = kHidden; g.N = kFlat; g.K = (int)B; g.lda = kHidden; g.ldb = kFlat;
-        g.Cf = grad + L.w[4]; g.ldc = kFlat;
+        g.Cf = grad + L.w[4]; g.ldc = kFlat; g.splitk = splitk_for(g.M, g.N, g.K);
         INV_CUDA(gemm(true, true, g, st));
         colsum_atomic_kernel<<<dim3((kHidden + 127) / 128, (B + 255) / 256), 128, 0, st>>>(
             dzf, (int)B, kHidden, 256, grad + L.b[4]);
@@ -857,7 +937,7 @@ int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work,
         GemmArgs g{};
         g.A = dzb; g.B = at<__nv_bfloat16>(work, h->cols[l]);
         g.M = kCh; g.N = kKer * cin; g.K = (int)rows; g.lda = kCh; g.ldb = kKer * cin;
-        g.Cf = grad + L.w[l]; g.ldc = kKer * cin;
+        g.Cf = grad + L.w[l]; g.ldc = kKer * cin; g.splitk = splitk_for(g.M, g.N, g.K);
         INV_CUDA(gemm(true, true, g, st));
         colsum_atomic_kernel<<<dim3(1, (unsigned)((rows + 1023) / 1024)), 64, 0, st>>>(
             dzf, (int)rows, kCh, 1024, grad + L.b[l]);

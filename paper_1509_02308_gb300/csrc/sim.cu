@@ -483,126 +483,159 @@ struct BatchLRU {
         return m;
     }
 
+    // All set groups at once.  A group of g heads can push out at most g
+    // resident lines, so a line whose rank (live entries older than it) is g
+    // or more is a sure hit, and the g oldest live entries of the set (its
+    // window) are all that is needed: the group's own lanes read the ring g
+    // positions at a time until g live entries are seen or the ring ends.
     __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t,
                                             int lane, uint32_t lt, uint32_t) {
         if (__ballot_sync(kFull, head) == 0) return false;
         const Grouped g = group_heads(line, set, head, lane, lt, perm);
         const uint32_t a = ways;
+        const uint32_t gm = g.gmask;
+        const uint32_t gs = g.act ? (uint32_t)__popc(gm) : 0u;
+        const uint32_t j = (uint32_t)lane - g.gb;
         const uint32_t lm = __match_any_sync(kFull, g.act ? g.x : (0x80000000u | (uint32_t)lane));
         const uint32_t pm = lm & lt;
         const int prev = pm ? 31 - __clz(pm) : -1;
         const bool first = g.act && prev < 0;
         const bool lastocc = g.act && (lm & ~(lt | (1u << lane))) == 0;
-        bool miss = false;
-        uint32_t leaders = __ballot_sync(kFull, g.act && (uint32_t)lane == g.gb);
-        while (leaders) {
-            const uint32_t gl = __ffs(leaders) - 1;
-            leaders &= leaders - 1;
+        uint32_t *rg = ring + (size_t)(g.act ? g.set : 0) * R;
+        uint4 m = g.act ? meta[g.set] : make_uint4(0, 0, 0, 0);
+        // compaction of nearly full rings (one set at a time, rare)
+        uint32_t need = __ballot_sync(kFull, g.act && lane == (int)g.gb && m.y - m.x > R - 64);
+        while (need) {
+            const uint32_t gl = __ffs(need) - 1;
+            need &= need - 1;
             const uint32_t s = __shfl_sync(kFull, g.set, gl);
-            const uint32_t gm = __shfl_sync(kFull, g.gmask, gl);
-            const bool mine = (gm >> lane) & 1u;
-            uint32_t *rg = ring + (size_t)s * R;
-            uint4 m = meta[s];
-            if (m.y - m.x > R - 64) m = compact(s, m, lane, lt);
-            // tail window: chunks of 32 positions until 32 live entries
-            uint32_t nlive = 0, nch = 0;
-            for (int pass = 0; pass < 2; ++pass) {
-                nlive = 0;
-                nch = 0;
-                for (uint32_t c = 0; c < 8; ++c) {
-                    const uint32_t p = m.x + 32 * c + (uint32_t)lane;
-                    const uint32_t e = p < m.y ? rg[p & rmask] : kStale;
-                    const uint32_t bal = __ballot_sync(kFull, e != kStale);
-                    if (lane == 0) {
-                        wsc[c] = bal;
-                        wsc[8 + c] = nlive;
-                    }
-                    nlive += __popc(bal);
-                    nch = c + 1;
-                    if (nlive >= 32 || m.x + 32 * (c + 1) >= m.y) break;
-                }
-                if (nlive >= 32 || m.x + 32 * nch >= m.y) break;
-                m = compact(s, m, lane, lt);  // stale entries hid the window
-            }
-            __syncwarp();
-            // depth of each head's line
-            const uint32_t w1 = mine ? tab[g.x] : 0u;
-            uint32_t rank = 32;  // 32: resident above the window (sure hit)
-            if (w1) {
-                const uint32_t off = (w1 - 1 - m.x) & rmask;
-                const uint32_t c = off >> 5;
-                if (c < nch) {
-                    const uint32_t rk = wsc[8 + c] + __popc(wsc[c] & ((1u << (off & 31)) - 1u));
-                    if (rk < 32) rank = rk;
-                }
-            }
-            // lines older than this one or new, first used earlier in the step
-            const uint32_t key = (mine && first) ? (w1 == 0 ? 0u : rank + 1) : 63u;
-            const uint32_t older = lanes_below(key, rank + 1) & gm & lt;
-            // distinct lines strictly between a repeat and its previous use
-            const uint32_t pkey = mine ? (uint32_t)(prev + 1) : 63u;
-            const uint32_t pthr = prev < 0 ? 0u : (uint32_t)prev + 1;
-            const uint32_t between = lanes_below(pkey, pthr) & gm & lt &
-                                     ~((prev < 0) ? 0u : ((2u << prev) - 1u));
-            if (mine) {
-                if (first) {
-                    if (w1 == 0) miss = true;
-                    else if (rank < 32) miss = (m.z - 1 - rank) + __popc(older) >= a;
-                } else {
-                    miss = (uint32_t)__popc(between) >= a;
-                }
-            }
-            // ----- update this set
-            const uint32_t D = __popc(__ballot_sync(kFull, mine && lastocc));
-            const uint32_t Rb = __popc(__ballot_sync(kFull, mine && first && w1 != 0));
-            if (mine && first && w1) rg[w1 - 1] = kStale;
-            __syncwarp();
-            const uint32_t keep_old = D <= a ? a - D : 0u;
-            const uint32_t old_live = m.z - Rb;
-            const uint32_t E = old_live > keep_old ? old_live - keep_old : 0u;
-            uint32_t done = 0;
-            uint32_t new_tail = m.x + 32 * nch < m.y ? m.x + 32 * nch : m.y;
-            bool tail_set = false;
-            for (uint32_t c = 0; c < nch; ++c) {
-                const uint32_t p = m.x + 32 * c + (uint32_t)lane;
-                const uint32_t e = p < m.y ? rg[p & rmask] : kStale;
-                const bool live = e != kStale;
-                const uint32_t bal = __ballot_sync(kFull, live);
-                const uint32_t rk = done + __popc(bal & lt);
-                const bool ev = live && rk < E;
-                if (ev) {
-                    tab[e] = 0;
-                    rg[p & rmask] = kStale;
-                }
-                const uint32_t keep = __ballot_sync(kFull, live && !ev);
-                if (!tail_set && keep) {
-                    new_tail = m.x + 32 * c + (__ffs(keep) - 1);
-                    tail_set = true;
-                }
-                done += __popc(bal);
-            }
-            // append the step's lines in last-use order
-            const uint32_t q = __popc(__ballot_sync(kFull, mine && lastocc) & lt);
-            if (mine && lastocc) {
-                const uint32_t p = (m.y + q) & rmask;
-                if (D > a && q < D - a) {
-                    rg[p] = kStale;
-                    tab[g.x] = 0;
-                } else {
-                    rg[p] = g.x;
-                    tab[g.x] = (uint16_t)(p + 1);
-                }
-            }
-            if (lane == 0) {
-                uint4 n;
-                n.x = new_tail;
-                n.y = m.y + D;
-                n.z = D <= a ? old_live - E + D : a;
-                n.w = 0;
-                meta[s] = n;
-            }
-            __syncwarp();
+            uint4 ms = meta[s];
+            ms = compact(s, ms, lane, lt);
+            if (g.act && g.set == s) m = ms;
         }
+        // windows: up to kWin rounds of g positions per group
+        constexpr int kWin = 8;
+        uint32_t wbal[kWin];
+        uint32_t wlive = 0, nround = 0;
+        bool done = !g.act;
+#pragma unroll
+        for (int r = 0; r < kWin; ++r) {
+            const uint32_t p = m.x + (uint32_t)r * gs + j;
+            const uint32_t e = (!done && p < m.y) ? rg[p & rmask] : kStale;
+            wbal[r] = __ballot_sync(kFull, e != kStale) & gm;
+            if (!done) {
+                wlive += __popc(wbal[r]);
+                nround = (uint32_t)r + 1;
+                if (wlive >= gs || m.x + (uint32_t)(r + 1) * gs >= m.y) done = true;
+            }
+            if (__all_sync(kFull, done)) break;
+        }
+        // a group whose window is still short (stale entries in the way) is
+        // compacted and scanned again in one round
+        uint32_t redo = __ballot_sync(kFull, !done && lane == (int)g.gb);
+        if (redo) {
+            while (redo) {
+                const uint32_t gl = __ffs(redo) - 1;
+                redo &= redo - 1;
+                const uint32_t s = __shfl_sync(kFull, g.set, gl);
+                uint4 ms = compact(s, meta[s], lane, lt);
+                if (g.act && g.set == s) m = ms;
+            }
+            const bool again = !done;
+            const uint32_t p = m.x + j;
+            const uint32_t e = (again && p < m.y) ? rg[p & rmask] : kStale;
+            const uint32_t bal = __ballot_sync(kFull, e != kStale) & gm;
+            if (again) {
+                wbal[0] = bal;
+                wlive = __popc(bal);
+                nround = 1;
+            }
+        }
+        __syncwarp();
+        // rank of each head's resident line among the window's live entries
+        const uint32_t w1 = g.act ? tab[g.x] : 0u;
+        uint32_t rank = 32;
+        if (w1) {
+            const uint32_t off = (w1 - 1 - m.x) & rmask;
+            if (off < nround * gs) {
+                const uint32_t r0 = off / gs, j0 = off - r0 * gs;
+                uint32_t rk = 0;
+#pragma unroll
+                for (int r = 0; r < kWin; ++r) {
+                    if ((uint32_t)r < r0) rk += __popc(wbal[r]);
+                    else if ((uint32_t)r == r0) rk += __popc(wbal[r] & ((1u << (g.gb + j0)) - 1u));
+                }
+                if (rk < gs) rank = rk;
+            }
+        }
+        // lines older than this one or new, first used earlier in the group
+        const uint32_t key = first ? (w1 == 0 ? 0u : rank + 1) : 63u;
+        const uint32_t older = lanes_below(key, rank + 1) & gm & lt;
+        // distinct lines strictly between a repeat and its previous use
+        const uint32_t pkey = g.act ? (uint32_t)(prev + 1) : 63u;
+        const uint32_t pthr = prev < 0 ? 0u : (uint32_t)prev + 1;
+        const uint32_t between = lanes_below(pkey, pthr) & gm & lt &
+                                 ~((prev < 0) ? 0u : ((2u << prev) - 1u));
+        bool miss = false;
+        if (g.act) {
+            if (first) {
+                if (w1 == 0) miss = true;
+                else if (rank < 32) miss = (m.z - 1 - rank) + __popc(older) >= a;
+            } else {
+                miss = (uint32_t)__popc(between) >= a;
+            }
+        }
+        // ----- updates, every group at once
+        const uint32_t lastbal = __ballot_sync(kFull, lastocc);
+        const uint32_t D = __popc(lastbal & gm);
+        const uint32_t Rb = __popc(__ballot_sync(kFull, first && w1 != 0) & gm);
+        if (first && w1) rg[w1 - 1] = kStale;
+        __syncwarp();
+        const uint32_t keep_old = D <= a ? a - D : 0u;
+        const uint32_t old_live = m.z - Rb;
+        const uint32_t E = old_live > keep_old ? old_live - keep_old : 0u;
+        uint32_t evd = 0, new_tail = m.x + nround * gs < m.y ? m.x + nround * gs : m.y;
+        bool tail_set = false;
+        for (uint32_t r = 0; r < (uint32_t)kWin; ++r) {
+            const bool in = g.act && r < nround;
+            const uint32_t p = m.x + r * gs + j;
+            const uint32_t e = (in && p < m.y) ? rg[p & rmask] : kStale;
+            const bool live = e != kStale;
+            const uint32_t bal = __ballot_sync(kFull, live) & gm;
+            const bool ev = live && evd + __popc(bal & lt) < E;
+            if (ev) {
+                tab[e] = 0;
+                rg[p & rmask] = kStale;
+            }
+            const uint32_t keep = __ballot_sync(kFull, live && !ev) & gm;
+            if (in && !tail_set && keep) {
+                new_tail = m.x + r * gs + (__ffs(keep) - 1 - g.gb);
+                tail_set = true;
+            }
+            evd += __popc(bal);
+            if (__all_sync(kFull, !in || r + 1 >= nround)) break;
+        }
+        // append the group's lines in last-use order
+        if (lastocc) {
+            const uint32_t q = __popc(lastbal & gm & lt);
+            const uint32_t p = (m.y + q) & rmask;
+            if (D > a && q < D - a) {
+                rg[p] = kStale;
+                tab[g.x] = 0;
+            } else {
+                rg[p] = g.x;
+                tab[g.x] = (uint16_t)(p + 1);
+            }
+        }
+        if (g.act && (uint32_t)lane == g.gb) {
+            uint4 n;
+            n.x = new_tail;
+            n.y = m.y + D;
+            n.z = D <= a ? old_live - E + D : a;
+            n.w = 0;
+            meta[g.set] = n;
+        }
+        __syncwarp();
         return __shfl_sync(kFull, miss ? 1u : 0u, head ? g.dest : (uint32_t)lane) != 0 && head;
     }
 };
