@@ -242,6 +242,31 @@ int pchase_classify(const float *lat, const uint64_t *offsets, uint32_t n_obs,
                     float *thresh_out, void *workspace, pchase_stream_t stream);
 
 /*
+ * pchase_classify without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory, for
+ * example a measurement loop that classifies probe latencies between probe
+ * runs, where a cudaMalloc would synchronise the device and disturb the very
+ * timings being taken, or a process whose device memory is owned entirely by
+ * another allocator.  Same inputs, outputs and reading as pchase_classify; its
+ * scratch is a fixed 8 MiB array inside the library (every GPU that loads the
+ * library holds it until the process exits), so the request must satisfy
+ * 16 * n_obs * (max_len + 1) bytes (rounded up to 256) <= 8 MiB, else the call
+ * returns PCHASE_ERANGE without queuing anything.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and should come
+ * before any stream capture.  Every call on a device shares the one array:
+ * calls whose work overlaps on the GPU (different streams, or another thread)
+ * race on it; calls queued on one stream are ordered.  The kernels initialise
+ * everything they read, so contents left by an earlier call are never used.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+int pchase_classify_noalloc(const float *lat, const uint64_t *offsets, uint32_t n_obs,
+                            uint64_t max_len, uint32_t *bits_out,
+                            const uint64_t *bit_word_offsets, float *thresh_out,
+                            pchase_stream_t stream);
+/* Size in bytes of the static scratch of pchase_classify_noalloc (8 MiB). */
+size_t pchase_classify_noalloc_limit_bytes(void);
+
+/*
  * Exhaustive matcher (S5), the mechanised form of Fig. 6 (Sec. 4.2): every
  * plan item (candidate g, plan trace t) is replayed and compared with the
  * observed miss bits of trace t (observed + obs_word_offsets[t], device); the

@@ -64,6 +64,8 @@ SIGNATURES = {
                                        _c_p, _c_p, ctypes.POINTER(ctypes.c_size_t), _c_p]),
     "pchase_classify_workspace_bytes": (ctypes.c_size_t, [_c_u32, _c_u64]),
     "pchase_classify": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_u64, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_classify_noalloc": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_u64, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_classify_noalloc_limit_bytes": (ctypes.c_size_t, []),
     "pchase_match_run": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_u64, _c_p, _c_p, _c_p]),
     "pchase_canonical_pick": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_p, _c_p]),
     "pchase_infer_scratch_bytes": (ctypes.c_size_t, [_c_p]),

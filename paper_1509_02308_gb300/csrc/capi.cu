@@ -123,6 +123,8 @@ int check_trace(const pchase_trace &t, uint32_t i) {
 
 }  // namespace
 
+int pchase::set_last_error(int code, const char *msg) { return fail(code, msg); }
+
 struct pchase_sim_plan {
     std::vector<SimItem> items;
     SlotLayout layout{};

@@ -16,6 +16,8 @@
 //      buckets, and is computed from the same two floats as a sort would give;
 //   3. a block scans the buckets in order (first maximum wins) and a grid
 //      writes the miss bits with __ballot_sync.
+#include <mutex>
+
 #include "pchase_internal.cuh"
 
 namespace pchase {
@@ -283,4 +285,75 @@ cudaError_t canonical_pick(const pchase_geom *geoms, const uint64_t *dist, uint3
     return cudaGetLastError();
 }
 
+// ------------------------------------------------ classification without allocation
+// Scratch of pchase_classify_noalloc: a fixed array in the library's own
+// device memory, shared by every call on a device and kept until the process
+// exits.  Host code cannot use the name g_noalloc_scratch as an address: it
+// names a host-side stand-in, so the device address is looked up once per
+// device with cudaGetSymbolAddress.
+constexpr size_t kNoallocScratchBytes = 8u << 20;
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices];
+
+// Device address of the scratch array for the current device (set up on the
+// first call per device).
+cudaError_t noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
 }  // namespace pchase
+
+extern "C" size_t pchase_classify_noalloc_limit_bytes(void) {
+    return pchase::kNoallocScratchBytes;
+}
+
+extern "C" int pchase_classify_noalloc(const float *lat, const uint64_t *offsets, uint32_t n_obs,
+                                       uint64_t max_len, uint32_t *bits_out,
+                                       const uint64_t *bit_word_offsets, float *thresh_out,
+                                       pchase_stream_t stream) {
+    using namespace pchase;
+    if (n_obs == 0) return PCHASE_OK;
+    if (!lat || !offsets || !bits_out || !bit_word_offsets)
+        return set_last_error(PCHASE_EINVAL, "pchase_classify_noalloc: NULL argument");
+    const size_t meta = classify_meta_bytes(n_obs);
+    const size_t bk = (classify_bucket_bytes(n_obs, max_len) + 255) & ~size_t(255);
+    if (max_len > (kNoallocScratchBytes >> 4) || n_obs > (kNoallocScratchBytes >> 4) ||
+        meta + bk > kNoallocScratchBytes)
+        return set_last_error(PCHASE_ERANGE,
+                              "pchase_classify_noalloc: n_obs * max_len too large for the "
+                              "8 MiB static scratch (need 16 * n_obs * (max_len + 1) bytes, "
+                              "rounded up); use pchase_classify with a workspace");
+    void *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess)
+        return set_last_error(PCHASE_ECUDA, "pchase_classify_noalloc: cudaGetSymbolAddress failed");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint8_t *w = static_cast<uint8_t *>(scratch);
+    // the kernels write every metadata entry and initialise every bucket they
+    // read, so nothing left by an earlier call is consumed
+    e = classify_thresholds(lat, offsets, n_obs, max_len, w, w + meta, thresh_out, st, sms);
+    if (e == cudaSuccess)
+        e = classify_bits(lat, offsets, 1, n_obs, max_len, w, bits_out, bit_word_offsets, st, sms);
+    if (e != cudaSuccess) return set_last_error(PCHASE_ECUDA, cudaGetErrorString(e));
+    return PCHASE_OK;
+}

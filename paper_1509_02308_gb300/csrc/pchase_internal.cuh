@@ -116,6 +116,10 @@ struct SimOut {
     uint64_t *timeline;
 };
 
+// Records the text pchase_last_error_string() returns on this thread and
+// passes `code` through (capi.cu).
+int set_last_error(int code, const char *msg);
+
 // Kernel launchers (sim.cu)
 cudaError_t launch_sim(const SimItem *items, const SlotLayout &layout, uint32_t *queues, int grid,
                        const SimOut &out, cudaStream_t st);
