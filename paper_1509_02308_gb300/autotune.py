@@ -19,7 +19,7 @@ import torch
 from .api import SimPlan
 
 KNOBS = {
-    "batch_max_sets": [0xFFFFFFFF, 1, 2, 4, 8, 16],
+    "batch_max_sets": [0xFFFFFFFF, 2, 4, 8, 16, 32, 64, 1 << 30],
     "scan_max_ways": [4, 8, 16, 32],
     "max_warps_per_cta": [8, 12, 16],
     "smem_budget_bytes": [160 * 1024, 200 * 1024, 220 * 1024],
