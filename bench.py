@@ -81,6 +81,25 @@ def dist_env():
     return rank, world, local
 
 
+# ------------------------------------------------------------ multi-GPU
+def rank_workload(rank: int, items: int, max_len: int):
+    """Rank r's own batch: the same recipe with its own seed range (items
+    r*items .. (r+1)*items - 1 of the seed sequence), so ranks share no item."""
+    from paper_1509_02308_gb300 import workloads as W
+    return W.config2(n_items=items, seed_base=0x5EED0002 + rank * items, max_len=max_len)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (all_reduce MAX); the value itself when alone."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
@@ -192,8 +211,7 @@ def ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    geoms, runs = W.config2(n_items=args.items, seed_base=0x5EED0002 + rank * args.items,
-                            max_len=args.max_len)
+    geoms, runs = rank_workload(rank, args.items, args.max_len)
     total_acc = W.total_accesses(runs)
     offs = np.zeros(len(runs) + 1, dtype=np.uint64)
     offs[1:] = np.cumsum([r.length for r in runs])
@@ -297,12 +315,7 @@ def ours(args):
     clk = clocks.stop()
 
     # max over ranks
-    t_step = ms / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(ms / args.steps, world, dev)
     value = total_acc * world / (t_step * 1e-3)
 
     peaks, peak_kind = measured_peaks()

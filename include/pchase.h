@@ -133,11 +133,11 @@ int pchase_build_batch(const pchase_trace *traces, uint32_t n, uint32_t *trace_o
  * defaults (pass NULL).  See pchase_sim_plan_create.
  */
 typedef struct {
-    uint32_t scan_max_ways;      /* a <= this: way-scan sets; above: line-table sets (default 8) */
-    uint32_t smem_budget_bytes;  /* shared memory per CTA (default 96 KB) */
+    uint32_t scan_max_ways;      /* a <= this: way-scan sets; above: line-table sets (default 4) */
+    uint32_t smem_budget_bytes;  /* shared memory per CTA for the slot mix (default 220 KB) */
     uint32_t max_warps_per_cta;  /* (default 16) */
     uint32_t ctas_per_sm_cap;    /* 0 = as many as fit */
-    uint32_t batch_max_sets;     /* T <= this: whole-step batch resolution per set (default 8;
+    uint32_t batch_max_sets;     /* T <= this: whole-step batch resolution per set (default 64;
                                     0 keeps the default, 0xFFFFFFFF disables batch mode) */
 } pchase_tune;
 

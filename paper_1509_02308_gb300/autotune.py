@@ -24,7 +24,7 @@ KNOBS = {
     "max_warps_per_cta": [8, 12, 16],
     "smem_budget_bytes": [160 * 1024, 200 * 1024, 220 * 1024],
 }
-DEFAULT = {"batch_max_sets": 8, "scan_max_ways": 8, "max_warps_per_cta": 16,
+DEFAULT = {"batch_max_sets": 64, "scan_max_ways": 4, "max_warps_per_cta": 16,
            "smem_budget_bytes": 220 * 1024}
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 

@@ -251,7 +251,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     *plan_out = nullptr;
     if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
         return fail(PCHASE_EINVAL, "NULL descriptor array");
-    pchase_tune tn{8, 220 * 1024, 16, 0, 8};
+    pchase_tune tn{4, 220 * 1024, 16, 0, 64};
     if (tune) {
         if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
