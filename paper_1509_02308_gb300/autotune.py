@@ -22,7 +22,7 @@ KNOBS = {
     "batch_max_sets": [0xFFFFFFFF, 2, 4, 8, 16, 32, 64, 1 << 30],
     "scan_max_ways": [4, 8, 16, 32],
     "max_warps_per_cta": [8, 12, 16],
-    "smem_budget_bytes": [160 * 1024, 200 * 1024, 220 * 1024],
+    "smem_budget_bytes": [64 * 1024, 96 * 1024, 128 * 1024, 160 * 1024, 200 * 1024, 220 * 1024],
 }
 DEFAULT = {"batch_max_sets": 64, "scan_max_ways": 4, "max_warps_per_cta": 16,
            "smem_budget_bytes": 220 * 1024}

@@ -241,6 +241,123 @@ cudaError_t gemm(bool a_col, bool b_row, const GemmArgs &g0, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------- convolution as implicit GEMM
+// out[(b, lo), co] = bias[co] + sum_{kk, ci} W[co][kk*64 + ci] * x[b][2 lo + kk - 2][ci]
+// for 64 input and 64 output channels, x channel-last BF16.  The A tile
+// (128 output positions x 32 reduction entries, i.e. half the channels of
+// one tap) is gathered straight from x with 16-byte cp.async copies (zero
+// fill outside the sequence); W tiles likewise; two stages in flight.
+constexpr int CBM = 128, CBN = 64, CBK = 32, CPAD = 8;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(256) conv64_kernel(const __nv_bfloat16 *__restrict__ x, int nb,
+                                                     int lin, const __nv_bfloat16 *__restrict__ W,
+                                                     const float *__restrict__ bias,
+                                                     __nv_bfloat16 *__restrict__ out,
+                                                     float *__restrict__ pre) {
+    constexpr int CIN = 64, KTOT = 5 * CIN, NKT = KTOT / CBK;
+    __shared__ __align__(16) __nv_bfloat16 As[2][CBM][CBK + CPAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][CBN][CBK + CPAD];
+    const int lout = lin / 2;
+    const int M = nb * lout;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * CBM;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+    auto load = [&](int stage, int kt) {
+        const int kk = kt >> 1, ci0 = (kt & 1) * 32;
+        for (int e = tid; e < CBM * 4; e += 256) {
+            const int r = e >> 2, c = (e & 3) * 8;
+            const int m = m0 + r;
+            const int b = m / lout, lo = m - b * lout;
+            const int li = 2 * lo + kk - 2;
+            const bool ok = m < M && li >= 0 && li < lin;
+            const __nv_bfloat16 *src = ok ? x + ((size_t)b * lin + li) * CIN + ci0 + c : x;
+            cp_async16((uint32_t)__cvta_generic_to_shared(&As[stage][r][c]), src, ok);
+        }
+        {
+            const int r = tid >> 2, c = (tid & 3) * 8;
+            cp_async16((uint32_t)__cvta_generic_to_shared(&Bs[stage][r][c]),
+                       W + (size_t)r * KTOT + kt * CBK + c, true);
+        }
+        cp_async_commit();
+    };
+    load(0, 0);
+    for (int kt = 0; kt < NKT; ++kt) {
+        const int st = kt & 1;
+        if (kt + 1 < NKT) {
+            load(st ^ 1, kt + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < CBK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int row = wm + i * 16 + (lane & 15);
+                const int col = kk + ((lane >> 4) << 3);
+                ldsm_x4((uint32_t)__cvta_generic_to_shared(&As[st][row][col]), af[i][0], af[i][1],
+                        af[i][2], af[i][3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j += 2) {
+                const int row = wn + j * 8 + (lane & 7) + ((lane >> 4) << 3);
+                const int col = kk + (((lane >> 3) & 1) << 3);
+                uint32_t r0, r1, r2, r3;
+                ldsm_x4((uint32_t)__cvta_generic_to_shared(&Bs[st][row][col]), r0, r1, r2, r3);
+                bfr[j][0] = r0;
+                bfr[j][1] = r1;
+                bfr[j + 1][0] = r2;
+                bfr[j + 1][1] = r3;
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_bf16(acc[i][j], af[i][0], af[i][1], af[i][2], af[i][3], bfr[j][0], bfr[j][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm + i * 16 + (lane >> 2) + h * 8;
+                const int n = wn + j * 8 + ((lane & 3) << 1);
+                if (m >= M) continue;
+                const float v0 = acc[i][j][2 * h] + bias[n];
+                const float v1 = acc[i][j][2 * h + 1] + bias[n + 1];
+                const size_t o = (size_t)m * CBN + n;
+                if (pre) {
+                    pre[o] = v0;
+                    pre[o + 1] = v1;
+                }
+                __nv_bfloat162 pk;
+                pk.x = __float2bfloat16(gelu_f(v0));
+                pk.y = __float2bfloat16(gelu_f(v1));
+                *reinterpret_cast<__nv_bfloat162 *>(out + o) = pk;
+            }
+}
+
 // --------------------------------------------------------- network plumbing
 constexpr int kPoints = 512;
 constexpr int kCh = 64;
@@ -481,9 +598,11 @@ __global__ void f2b_kernel(const float *x, size_t n, __nv_bfloat16 *y) {
 // candidate index.
 constexpr int kKeep = kPoints - 5;
 
-__global__ void lsq_prep_kernel(const float *y, uint32_t n, float *ym, float *mask, float *stats) {
+__global__ void lsq_prep_kernel(const float *y, uint32_t n, const uint32_t *n_dev, float *ym,
+                                float *mask, float *stats) {
     __shared__ float v[kPoints];
     const uint32_t i = blockIdx.x;
+    if (n_dev && *n_dev < n) n = *n_dev;
     if (i >= n) return;
     for (int p = threadIdx.x; p < kPoints; p += blockDim.x) v[p] = y[(size_t)i * kPoints + p];
     __syncthreads();
@@ -526,11 +645,13 @@ __global__ void lsq_prep_kernel(const float *y, uint32_t n, float *ym, float *ma
 // 64 traces x 64 candidates per block, 256 threads with 4 x 4 outputs each
 __global__ void __launch_bounds__(256) lsq_kernel(const float *ym, const float *mask,
                                                   const float *stats, uint32_t n,
-                                                  const float *rates, uint32_t G,
-                                                  unsigned long long *best) {
+                                                  const uint32_t *n_dev, const float *rates,
+                                                  uint32_t G, unsigned long long *best) {
     __shared__ float sY[32][65], sM[32][65], sR[32][65];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const uint32_t i0 = blockIdx.y * 64, g0 = blockIdx.x * 64;
+    if (n_dev && *n_dev < n) n = *n_dev;
+    if (i0 >= n) return;  // rows beyond the device-side count: nothing to do
     float dyr[4][4], dr[4][4], drr[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -594,9 +715,10 @@ __global__ void fill_u64_kernel(unsigned long long *p, size_t n, unsigned long l
         p[i] = v;
 }
 
-__global__ void lsq_unpack_kernel(const unsigned long long *best, uint32_t n, uint32_t *idx,
-                                  float *res) {
+__global__ void lsq_unpack_kernel(const unsigned long long *best, uint32_t n, const uint32_t *n_dev,
+                                  uint32_t *idx, float *res) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n_dev && *n_dev < n) n = *n_dev;
     if (i >= n) return;
     idx[i] = (uint32_t)(best[i] & 0xFFFFFFFFull);
     if (res) res[i] = __uint_as_float((uint32_t)(best[i] >> 32));
@@ -724,13 +846,29 @@ const T *at(const void *base, size_t off) {
     return reinterpret_cast<const T *>(static_cast<const uint8_t *>(base) + off);
 }
 
-int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B, cudaStream_t st) {
+int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B, cudaStream_t st,
+            bool train) {
     const InverseLayout &L = h->L;
     const __nv_bfloat16 *wb = at<__nv_bfloat16>(params, h->p_wb);
     const float *wf = at<float>(params, h->p_w);
     const __nv_bfloat16 *in = at<__nv_bfloat16>(work, h->xb);
     for (int l = 0; l < 4; ++l) {
         const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
+        if (cin == kCh) {
+            // implicit im2col; training also keeps the explicit columns for dW
+            if (train) {
+                __nv_bfloat16 *cols = at<__nv_bfloat16>(work, h->cols[l]);
+                const size_t nc = (size_t)B * lout * kKer * cin;
+                im2col_kernel<<<grid_for(nc), 256, 0, st>>>(in, (int)B, lin, cin, cols);
+            }
+            __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
+            const int M = (int)(B * lout);
+            conv64_kernel<<<(M + CBM - 1) / CBM, 256, 0, st>>>(
+                in, (int)B, lin, wb + L.w[l], wf + L.b[l], o, train ? at<float>(work, h->pre[l]) : nullptr);
+            INV_CUDA(cudaGetLastError());
+            in = o;
+            continue;
+        }
         __nv_bfloat16 *cols = at<__nv_bfloat16>(work, h->cols[l]);
         const size_t nc = (size_t)B * lout * kKer * cin;
         im2col_kernel<<<grid_for(nc), 256, 0, st>>>(in, (int)B, lin, cin, cols);
@@ -743,7 +881,7 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
         g.lda = kKer * cin;
         g.ldb = kKer * cin;
         g.bias = wf + L.b[l];
-        g.pre = at<float>(work, h->pre[l]);
+        g.pre = train ? at<float>(work, h->pre[l]) : nullptr;
         g.Cb = at<__nv_bfloat16>(work, h->act[l]);
         g.ldc = kCh;
         g.gelu = 1;
@@ -759,7 +897,7 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
     f.lda = kFlat;
     f.ldb = kFlat;
     f.bias = wf + L.b[4];
-    f.pre = at<float>(work, h->pre4);
+    f.pre = train ? at<float>(work, h->pre4) : nullptr;
     f.Cb = at<__nv_bfloat16>(work, h->h4);
     f.ldc = kHidden;
     f.gelu = 1;
@@ -882,7 +1020,7 @@ int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work,
     const InverseLayout &L = h->L;
     f2b_kernel<<<grid_for((size_t)B * kPoints), 256, 0, st>>>(x, (size_t)B * kPoints,
                                                                at<__nv_bfloat16>(work, h->xb));
-    int rc = forward(h, params, work, B, st);
+    int rc = forward(h, params, work, B, st, true);
     if (rc) return rc;
     const size_t n = L.n_params;
     float *grad = at<float>(params, h->p_g);
@@ -971,7 +1109,7 @@ int pchase_inverse_infer(const pchase_inverse *h, const void *params, void *work
         const uint32_t B = std::min(h->max_batch, n - b0);
         f2b_kernel<<<grid_for((size_t)B * kPoints), 256, 0, st>>>(
             x + (size_t)b0 * kPoints, (size_t)B * kPoints, at<__nv_bfloat16>(work, h->xb));
-        int rc = forward(h, params, work, B, st);
+        int rc = forward(h, params, work, B, st, false);
         if (rc) return rc;
         const float *lg = at<float>(work, h->logits);
         predict_kernel<<<(B + 127) / 128, 128, 0, st>>>(lg, (int)B, pred_out + (size_t)b0 * 4,
@@ -984,6 +1122,10 @@ int pchase_inverse_infer(const pchase_inverse *h, const void *params, void *work
     return PCHASE_OK;
 }
 
+static int lsq_run(const float *rates, uint32_t n_geoms, const float *y, uint32_t n,
+                   const uint32_t *n_dev, uint32_t *best_out, float *resid_out, void *work,
+                   cudaStream_t st);
+
 size_t pchase_lsq_work_bytes(uint32_t n) {
     return a256((size_t)n * kPoints * 4) * 2 + a256((size_t)n * 12) + a256((size_t)n * 8);
 }
@@ -993,20 +1135,32 @@ int pchase_lsq_match(const float *rates, uint32_t n_geoms, const float *y, uint3
     if (!rates || !y || !best_out || !work || n_geoms == 0)
         return inv_fail(PCHASE_EINVAL, "NULL argument or no geometries");
     if (n == 0) return PCHASE_OK;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return lsq_run(rates, n_geoms, y, n, nullptr, best_out, resid_out, work,
+                   reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+// The least-squares matcher over the first min(n, *n_dev) rows (n_dev NULL:
+// all n); grids cover n rows and blocks past the device-side count return.
+static int lsq_run(const float *rates, uint32_t n_geoms, const float *y, uint32_t n,
+                   const uint32_t *n_dev, uint32_t *best_out, float *resid_out, void *work,
+                   cudaStream_t st) {
     float *ym = at<float>(work, 0);
     float *mask = at<float>(work, a256((size_t)n * kPoints * 4));
     float *stats = at<float>(work, 2 * a256((size_t)n * kPoints * 4));
     unsigned long long *best = at<unsigned long long>(
         work, 2 * a256((size_t)n * kPoints * 4) + a256((size_t)n * 12));
-    lsq_prep_kernel<<<n, 256, 0, st>>>(y, n, ym, mask, stats);
+    lsq_prep_kernel<<<n, 256, 0, st>>>(y, n, n_dev, ym, mask, stats);
     fill_u64_kernel<<<grid_for(n), 256, 0, st>>>(best, n, ~0ull);
     dim3 grid((n_geoms + 63) / 64, (n + 63) / 64);
-    lsq_kernel<<<grid, 256, 0, st>>>(ym, mask, stats, n, rates, n_geoms, best);
-    lsq_unpack_kernel<<<(n + 255) / 256, 256, 0, st>>>(best, n, best_out, resid_out);
+    lsq_kernel<<<grid, 256, 0, st>>>(ym, mask, stats, n, n_dev, rates, n_geoms, best);
+    lsq_unpack_kernel<<<(n + 255) / 256, 256, 0, st>>>(best, n, n_dev, best_out, resid_out);
     INV_CUDA(cudaGetLastError());
     return PCHASE_OK;
 }
+
+extern "C" {
 
 int pchase_inverse_classify(const pchase_inverse *h, const void *params, void *work,
                             const float *x, uint32_t n, const uint32_t *label_to_cand,
@@ -1024,11 +1178,10 @@ int pchase_inverse_classify(const pchase_inverse *h, const void *params, void *w
     INV_CUDA(cudaMemsetAsync(n_fallback, 0, 4, st));
     route_kernel<<<(n + 255) / 256, 256, 0, st>>>(pred_scratch, conf_out, n, label_to_cand,
                                                   conf_thresh, cand_out, fallback_list, n_fallback);
-    // the fallback runs over a compacted copy; its size is known only on the
-    // device, so the matcher covers the worst case n rows and rows past the
-    // count are left out by the scatter
+    // the fallback runs over a compacted copy whose size is known only on the
+    // device: the matcher's grids cover n rows and its blocks stop at the count
     gather_rows_kernel<<<n, 128, 0, st>>>(x, fallback_list, n_fallback, fb_rows);
-    rc = pchase_lsq_match(rates, n_geoms, fb_rows, n, fb_idx, nullptr, lsq_work, stream);
+    rc = lsq_run(rates, n_geoms, fb_rows, n, n_fallback, fb_idx, nullptr, lsq_work, st);
     if (rc) return rc;
     scatter_fallback_kernel<<<(n + 255) / 256, 256, 0, st>>>(fallback_list, n_fallback, fb_idx,
                                                              cand_out);
