@@ -139,6 +139,10 @@ typedef struct {
     uint32_t ctas_per_sm_cap;    /* 0 = as many as fit */
     uint32_t batch_max_sets;     /* T <= this: whole-step batch resolution per set (default 64;
                                     0 keeps the default, 0xFFFFFFFF disables batch mode) */
+    uint32_t max_split;          /* most parts a long item's sets are split into (power of two,
+                                    default 32; 1 = never split) */
+    uint32_t split_cost_ns;      /* split items whose estimated warp time is above this
+                                    (0 = automatic, from the whole plan's estimated work) */
 } pchase_tune;
 
 typedef struct pchase_sim_plan pchase_sim_plan;
@@ -148,8 +152,11 @@ typedef struct pchase_sim_plan pchase_sim_plan;
  * pairs[i]; pairs == NULL means all n_geom x n_trace combinations, item
  * g * n_trace + t.  geoms, traces and pairs are host arrays; the trace index
  * pointers inside `traces` are device pointers used later by pchase_sim_run.
- * The plan sorts items longest first into shared-memory size classes, one
- * persistent kernel per class (S6).  Errors: EINVAL for a bad geometry,
+ * Items whose estimated work dominates the batch are split by sets into
+ * independent units (sets never interact, so the result is unchanged); units
+ * are sorted costliest first into shared-memory size classes served by one
+ * persistent launch with a per-CTA mix of arenas (S6); units too large for
+ * that mix get a second launch on a side stream.  Errors: EINVAL for a bad geometry,
  * pair or trace; ERANGE if a geometry is too large for any class
  * (more than 65535 lines, or state above the workspace limits).
  */
@@ -164,7 +171,9 @@ size_t pchase_sim_plan_workspace_bytes(const pchase_sim_plan *plan);
 /* Number of items, and of bitmap words when the plan lays bitmaps out itself. */
 uint64_t pchase_sim_plan_items(const pchase_sim_plan *plan);
 uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);
-/* Kernel launches one pchase_sim_run (or pchase_match_run) queues. */
+/* Kernel launches one pchase_sim_run queues (the output clear, the slot-mix
+ * launch and, when the plan has jumbo units, the side launch);
+ * pchase_match_run queues one fewer (no output clear). */
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
 /*
  * Writes a one-line text description of the plan (items per set mode, size

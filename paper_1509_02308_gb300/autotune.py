@@ -3,7 +3,7 @@ the CTA shape by timing the caller's own workload on the device.
 
 Coordinate descent over the knobs of pchase_tune: for each knob in turn every
 candidate value is timed (median of `reps` CUDA-event-timed runs of the whole
-planned batch) with the other knobs at their best so far; two sweeps.  The
+planned batch, bitmaps and counts written) with the other knobs at their best so far; two sweeps.  The
 winner is cached as JSON, keyed by the device name and a signature of the
 workload (geometry and trace shapes), so later runs reuse it.
 """
@@ -23,9 +23,10 @@ KNOBS = {
     "scan_max_ways": [4, 8, 16, 32],
     "max_warps_per_cta": [8, 12, 16],
     "smem_budget_bytes": [64 * 1024, 96 * 1024, 128 * 1024, 160 * 1024, 200 * 1024, 220 * 1024],
+    "max_split": [1, 8, 32],
 }
 DEFAULT = {"batch_max_sets": 64, "scan_max_ways": 4, "max_warps_per_cta": 16,
-           "smem_budget_bytes": 220 * 1024}
+           "smem_budget_bytes": 220 * 1024, "max_split": 32}
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -41,13 +42,13 @@ def signature(geoms, traces, pairs) -> str:
 
 def _time(geoms, traces, pairs, tune, reps):
     plan = SimPlan(geoms, traces, pairs=pairs, tune=tune)
-    plan.run(want_bitmaps=False)
+    bitmaps, counts = plan.run()
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        plan.run(want_bitmaps=False)
+        plan.run(bitmaps=bitmaps, counts=counts)
         b.record()
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b))

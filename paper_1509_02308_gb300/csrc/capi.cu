@@ -1,6 +1,7 @@
 // C ABI entry points (include/pchase.h): argument checks, the simulation
 // planner, workspace layout, and launches.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -77,9 +78,127 @@ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 constexpr uint32_t kMaxLines = 65535;
 constexpr uint32_t kMaxArena = 232448;  // 227 KB, one warp per CTA
-const uint32_t kCaps[] = {512,   1024,  2048,  3072,   4096,   6144,   8192,   12288,
-                          16384, 24576, 32768, 49152,  65536,  98304,  131072, 163840,
-                          196608, kMaxArena};
+// size classes of unit arenas (bytes; queued units add their queue and staging ring)
+const uint32_t kCaps[] = {1024,  2560,  3072,  4096,   5120,   6144,   8192,   10240,  12288,
+                          16384, 20480, 24576, 32768,  40960,  49152,  65536,  81920,
+                          98304, 112640, 131072, 163840, 196608, kMaxArena};
+
+// Planner cost model (ns of one warp, measured on GB300): a step of 32 heads
+// in each set mode, plus the gather of every 32 trace accesses a unit reads.
+constexpr double kStepBatchNs = 1500.0;
+constexpr double kStepScanNs = 600.0;
+constexpr double kStepTableNs = 700.0;
+constexpr double kRoundNs = 170.0;     // each extra round of same-set heads
+constexpr double kGatherNs = 50.0;
+constexpr double kBatchRounds = 6.0;   // this many rounds: batch mode whatever T'
+constexpr double kPlanSms = 152.0;     // SMs the automatic split target assumes
+
+// What the planner assumes about an item's access stream, from its trace's
+// stride (exact for uniform chains, a hint for explicit traces).
+struct ItemShape {
+    double heads = 0.0;    // expected run heads (accesses that change line)
+    double visited = 1.0;  // sets the stream visits
+    uint32_t psh = 0;      // visited sets are multiples of 2^psh
+    uint32_t t2sh = 0;     // 2^t2sh: largest power of two dividing T
+    double cost = 0.0;
+};
+
+struct UnitShape {
+    bool direct = false;  // steps over consecutive accesses, no queue
+    uint32_t mode = 0, sets = 0, table_n = 0, ring = 0;
+    uint64_t arena = 0;
+    double cost = 0.0;
+};
+
+uint64_t gcd64(uint64_t a, uint64_t b) {
+    while (b) {
+        const uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
+    const uint64_t sb = 4ull * (Tr.stride % Tr.n_elems);  // bytes between accesses
+    const uint64_t b = G.line_bytes;
+    double density = 1.0;
+    uint64_t delta = 1;  // lines between consecutive heads
+    if (sb && sb < b) density = (double)sb / (double)b;
+    else if (sb >= b && sb % b == 0) delta = sb / b;
+    sh.heads = std::max(1.0, (double)Tr.len * density);
+    const uint64_t T = G.sets;
+    const uint64_t gfull = gcd64(delta % T ? delta % T : T, T);
+    sh.visited = (double)(T / gfull);
+    const uint64_t t2 = T & (~T + 1);
+    const uint64_t g2 = gfull & (~gfull + 1);
+    sh.t2sh = ilog2((uint32_t)t2);
+    sh.psh = ilog2((uint32_t)std::min(g2, t2));
+}
+
+// Set mode, arena and cost of one unit of a 2^ksh-way split (ksh = 0: whole).
+bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t psh, uint32_t ksh,
+                const ItemShape &sh, const pchase_tune &tn, UnitShape &u) {
+    (void)psh;
+    const uint32_t T = G.sets, a = G.ways;
+    const uint32_t Tl = T >> ksh;
+    const uint64_t lines = (uint64_t)Tl * a;
+    const uint32_t top = (it.n_elems - 1) >> it.lsh;  // largest line
+    const uint64_t table_n = ksh ? (uint64_t)Tl * (top / T + 1) : (uint64_t)top + 1;
+    const double parts = (double)(1u << ksh);
+    const double vis = std::max(1.0, sh.visited / parts);
+    const double rounds = std::ceil(32.0 / std::min(32.0, vis));
+    const double steps = std::ceil(sh.heads / parts / 32.0);
+    uint32_t ring = 256;
+    while (ring < a + 128) ring <<= 1;
+    uint64_t batch = 256 + 16ull * Tl + 2ull * table_n;
+    if (G.policy == PCHASE_LRU) batch += 4ull * Tl * ring;
+    else batch += ((4 * lines + 15) & ~15ull) + (G.policy == PCHASE_RANDOM ? 8 * lines : 0);
+    batch = align16(batch);
+    u.sets = Tl;
+    u.table_n = (uint32_t)std::min<uint64_t>(table_n, 0xFFFFFFFFull);
+    u.ring = 0;
+    double step_ns;
+    // many same-set heads per step favour batch mode even above batch_max_sets,
+    // as long as the unit still fits the shared slot mix
+    const bool many_rounds =
+        rounds >= kBatchRounds && 2 * (kStageBytes + batch) <= tn.smem_budget_bytes;
+    if (tn.batch_max_sets && (Tl <= tn.batch_max_sets || many_rounds) &&
+        kStageBytes + batch <= kMaxArena && ring <= 32768) {
+        u.mode = kModeBatch;
+        u.ring = ring;
+        u.arena = batch;
+        step_ns = kStepBatchNs;
+    } else if (a <= tn.scan_max_ways) {
+        u.mode = kModeScan;
+        u.arena = 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * Tl : 0);
+        step_ns = kStepScanNs + kRoundNs * (rounds - 1.0);
+    } else {
+        u.mode = kModeTable;
+        u.arena = 8ull * Tl + 4 * lines + (G.policy == PCHASE_LRU ? 4 * lines : 0) + 2ull * table_n;
+        step_ns = kStepTableNs + kRoundNs * (rounds - 1.0);
+    }
+    // a whole item whose accesses are mostly heads steps over them as they
+    // come; the others queue their heads (and a split part gathers its own)
+    u.direct = ksh == 0 && sh.heads >= 0.5 * (double)it.len;
+    const double chunks = std::ceil((double)it.len / 32.0);
+    u.arena = align16(u.arena) + (u.direct ? 0u : kStageBytes);
+    u.cost = u.direct ? chunks * step_ns : steps * step_ns + chunks * kGatherNs;
+    return u.arena <= kMaxArena;
+}
+
+void apply_unit(SimItem &it, const UnitShape &u) {
+    it.direct = u.direct ? 1 : 0;
+    it.mode = (uint8_t)u.mode;
+    it.sets = u.sets;
+    const DivMagic dm = make_div_magic(u.sets);
+    it.magic_m = dm.m;
+    it.s1 = (uint8_t)dm.s1;
+    it.s2 = (uint8_t)dm.s2;
+    it.table_n = u.table_n;
+    it.ring = u.ring;
+    it.arena_bytes = (uint32_t)u.arena;
+}
 
 int check_geom(const pchase_geom &g, uint32_t i) {
     char buf[160];
@@ -132,7 +251,8 @@ struct pchase_sim_plan {
     uint32_t jumbo_first_class = 0;
     uint64_t n_jumbo = 0;
     uint64_t bitmap_words = 0;
-    uint64_t n_items = 0;
+    uint64_t n_items = 0;  // caller's items
+    uint64_t n_units = 0;  // units (items, or parts of split items)
     size_t ws_bytes = 0, off_items = 0, off_geoms = 0, off_seg = 0, off_obs_words = 0,
            off_pool = 0;
     bool cross = false;
@@ -168,7 +288,7 @@ int plan_runtime(pchase_sim_plan *p) {
         const int per = sim_max_ctas_per_sm(p->layout);
         if (per <= 0) return fail(PCHASE_ECUDA, "simulator kernel cannot be resident");
         p->grid = (int)std::max<uint64_t>(
-            1, std::min<uint64_t>((uint64_t)per * p->sms, p->n_items - p->n_jumbo));
+            1, std::min<uint64_t>((uint64_t)per * p->sms, p->n_units - p->n_jumbo));
     }
     if (p->jumbo.nwarps) {
         const int per = sim_max_ctas_per_sm(p->jumbo);
@@ -191,6 +311,7 @@ int plan_launch(pchase_sim_plan *p, void *ws, const SimOut &out, cudaStream_t st
     if (!o.status) o.status = reinterpret_cast<uint32_t *>(w + 128);
     const SimItem *items = reinterpret_cast<const SimItem *>(w + p->off_items);
     uint32_t *queues = reinterpret_cast<uint32_t *>(w);
+    PCHASE_CUDA(launch_sim_zero(items, p->n_units, p->sms, o, st), "output clear");
     if (p->jumbo.nwarps) {
         // jumbo items first, on a side stream joined back before returning
         PCHASE_CUDA(cudaEventRecord(p->fork, st), "cudaEventRecord");
@@ -251,7 +372,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     *plan_out = nullptr;
     if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
         return fail(PCHASE_EINVAL, "NULL descriptor array");
-    pchase_tune tn{4, 220 * 1024, 16, 0, 64};
+    pchase_tune tn{4, 220 * 1024, 16, 0, 64, 32, 0};
     if (tune) {
         if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
@@ -259,6 +380,8 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         if (tune->max_warps_per_cta)
             tn.max_warps_per_cta = std::min<uint32_t>(tune->max_warps_per_cta, kMaxWarpsPerCta);
         tn.ctas_per_sm_cap = tune->ctas_per_sm_cap;
+        if (tune->max_split) tn.max_split = std::min<uint32_t>(tune->max_split, 256);
+        tn.split_cost_ns = tune->split_cost_ns;
     }
     for (uint32_t i = 0; i < n_geom; ++i) {
         int rc = check_geom(geoms[i], i);
@@ -291,14 +414,19 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     }
     p->total_len = p->seg_offsets[n_trace];
 
-    std::vector<SimItem> items;
+    // ---- items -> units.  Each item gets a base unit; a long one is split
+    // by sets into 2^ksh units (see SimItem) so no unit dominates the launch.
+    std::vector<SimItem> base;
+    std::vector<ItemShape> shape;
     try {
-        items.resize(n_items);
+        base.resize(n_items);
+        shape.resize(n_items);
     } catch (...) {
         delete p;
         return fail(PCHASE_ENOMEM, "item table allocation");
     }
     uint64_t word = 0;
+    double total = 0.0;
     for (uint64_t i = 0; i < n_items; ++i) {
         uint32_t g, t;
         if (p->cross) {
@@ -314,7 +442,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         }
         const pchase_geom &G = geoms[g];
         const pchase_trace &Tr = traces[t];
-        SimItem &it = items[i];
+        SimItem &it = base[i];
         memset(&it, 0, sizeof it);
         it.idx = Tr.idx;
         it.len = (uint32_t)Tr.len;
@@ -322,11 +450,6 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         it.n_elems = Tr.n_elems;
         it.stride = Tr.stride % Tr.n_elems;
         it.ways = G.ways;
-        it.sets = G.sets;
-        const DivMagic dm = make_div_magic(G.sets);
-        it.magic_m = dm.m;
-        it.s1 = (uint8_t)dm.s1;
-        it.s2 = (uint8_t)dm.s2;
         it.policy = (uint8_t)G.policy;
         it.lsh = ilog2(G.line_bytes) - 2;
         it.seed = G.seed;
@@ -335,69 +458,103 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         it.out_item = (uint32_t)i;
         it.cand = g;
         it.obs = t;
-        const uint64_t lines = (uint64_t)G.sets * G.ways;
-        uint64_t arena;
-        uint32_t ring = 256;
-        while (ring < G.ways + 128) ring <<= 1;
-        const uint32_t table_n = ((Tr.n_elems - 1) >> it.lsh) + 1;
-        uint64_t batch_arena = 256 + 16ull * G.sets + 2ull * table_n;
-        if (G.policy == PCHASE_LRU) batch_arena += 4ull * G.sets * ring;
-        else batch_arena += ((4 * lines + 15) & ~15ull) + (G.policy == PCHASE_RANDOM ? 8 * lines : 0);
-        batch_arena = align16(batch_arena);
-        if (G.sets <= tn.batch_max_sets && batch_arena <= kMaxArena && ring <= 32768) {
-            it.mode = kModeBatch;
-            it.table_n = table_n;
-            it.ring = ring;
-            arena = batch_arena;
-        } else if (G.ways <= tn.scan_max_ways) {
-            it.mode = kModeScan;
-            arena = 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * G.sets : 0);
-        } else {
-            it.mode = kModeTable;
-            it.table_n = ((Tr.n_elems - 1) >> it.lsh) + 1;
-            arena = 8ull * G.sets + 4 * lines + (G.policy == PCHASE_LRU ? 4 * lines : 0) +
-                    2ull * it.table_n;
-        }
-        arena = align16(arena);
-        if (arena > kMaxArena) {
+        it.gsets = G.sets;
+        const DivMagic gdm = make_div_magic(G.sets);
+        it.gmagic = gdm.m;
+        it.gs1 = (uint8_t)gdm.s1;
+        it.gs2 = (uint8_t)gdm.s2;
+        it.lead = 1;
+        ItemShape &sh = shape[i];
+        item_shape(G, Tr, sh);
+        UnitShape u;
+        if (!unit_shape(G, it, 0, 0, sh, tn, u)) {
             delete p;
             char buf[200];
             snprintf(buf, sizeof buf,
                      "item %llu needs %llu bytes of set state, above the %u-byte limit",
-                     (unsigned long long)i, (unsigned long long)arena, kMaxArena);
+                     (unsigned long long)i, (unsigned long long)u.arena, kMaxArena);
             return fail(PCHASE_ERANGE, buf);
         }
-        it.arena_bytes = (uint32_t)arena;
+        sh.cost = u.cost;
+        total += u.cost;
     }
     p->bitmap_words = word;
-
-    // size classes, longest items first inside each class
-    std::vector<int> cls(n_items);
-    const int ncap = (int)(sizeof kCaps / sizeof kCaps[0]);
+    const uint32_t max_split = std::max<uint32_t>(1, tn.max_split);
+    // Split target: no unit above the plan's share per warp slot, but no
+    // split below what the longest unsplittable work takes anyway (splitting
+    // costs a gather pass per part and only the critical path gains).
+    auto best_split = [&](uint64_t i, double target, uint32_t &k_out, UnitShape &u_out) {
+        const pchase_geom &G = geoms[base[i].cand];
+        const ItemShape &sh = shape[i];
+        k_out = 0;
+        unit_shape(G, base[i], 0, 0, sh, tn, u_out);
+        if (u_out.cost <= target) return;
+        for (uint32_t ksh = 1; (1u << ksh) <= max_split && sh.psh + ksh <= sh.t2sh; ++ksh) {
+            UnitShape u;
+            if (!unit_shape(G, base[i], sh.psh, ksh, sh, tn, u)) continue;
+            if (u.cost < u_out.cost * 0.97) {
+                u_out = u;
+                k_out = ksh;
+            }
+            if (u_out.cost <= target) break;
+        }
+    };
+    double critical = 0.0;
     for (uint64_t i = 0; i < n_items; ++i) {
+        uint32_t k;
+        UnitShape u;
+        best_split(i, 0.0, k, u);
+        critical = std::max(critical, u.cost);
+    }
+    const double target = tn.split_cost_ns ? (double)tn.split_cost_ns
+                                           : std::max({total / (kPlanSms * 36.0), critical, 2.0e5});
+    std::vector<SimItem> items;
+    std::vector<double> cost;
+    try {
+        items.reserve(n_items);
+        cost.reserve(n_items);
+        for (uint64_t i = 0; i < n_items; ++i) {
+            const pchase_geom &G = geoms[base[i].cand];
+            const ItemShape &sh = shape[i];
+            // smallest split that meets the target, else the cheapest one
+            uint32_t best_k;
+            UnitShape best;
+            best_split(i, target, best_k, best);
+            for (uint32_t r = 0; r < (1u << best_k); ++r) {
+                SimItem it = base[i];
+                it.psh = (uint8_t)(best_k ? sh.psh : 0);
+                it.ksh = (uint8_t)best_k;
+                it.kres = r;
+                it.lead = r == 0;
+                apply_unit(it, best);
+                it.cost = (float)best.cost;
+                items.push_back(it);
+                cost.push_back(best.cost);
+            }
+        }
+    } catch (...) {
+        delete p;
+        return fail(PCHASE_ENOMEM, "unit table allocation");
+    }
+    const uint64_t n_units = items.size();
+    p->n_units = n_units;
+
+    // size classes, costliest units first inside each class
+    std::vector<int> cls(n_units);
+    const int ncap = (int)(sizeof kCaps / sizeof kCaps[0]);
+    for (uint64_t i = 0; i < n_units; ++i) {
         int c = 0;
         while (kCaps[c] < items[i].arena_bytes) ++c;
         cls[i] = c;
     }
-    std::vector<uint64_t> order(n_items);
-    for (uint64_t i = 0; i < n_items; ++i) order[i] = i;
-    // expected cost: steps x rounds a step needs (heads of one set act in turn
-    // in scan and table mode; batch mode resolves a set's heads together)
-    std::vector<double> cost(n_items);
-    for (uint64_t i = 0; i < n_items; ++i) {
-        const SimItem &x = items[i];
-        const double steps = (x.len + 31) / 32;
-        double rounds = 1.0;
-        if (x.mode != kModeBatch) rounds = std::max(1.0, 32.0 / std::max(1u, x.sets));
-        else rounds = 1.5 + 0.25 * x.sets;
-        cost[i] = steps * (1.0 + 0.5 * rounds) * (x.mode == kModeTable ? 1.5 : 1.0);
-    }
+    std::vector<uint64_t> order(n_units);
+    for (uint64_t i = 0; i < n_units; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
         if (cls[x] != cls[y]) return cls[x] > cls[y];
         return cost[x] > cost[y];
     });
-    p->items.reserve(n_items);
-    for (uint64_t k = 0; k < n_items; ++k) p->items.push_back(items[order[k]]);
+    p->items.reserve(n_units);
+    for (uint64_t k = 0; k < n_units; ++k) p->items.push_back(items[order[k]]);
     // queues: one per size class, smallest class first
     SlotLayout &L = p->layout;
     memset(&L, 0, sizeof L);
@@ -409,7 +566,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         std::vector<int> present;
         for (int c = 0; c < ncap; ++c) {
             bool any = false;
-            for (uint64_t i = 0; i < n_items && !any; ++i) any = cls[i] == c;
+            for (uint64_t i = 0; i < n_units && !any; ++i) any = cls[i] == c;
             if (any) present.push_back(c);
         }
         nclass = (uint32_t)present.size();
@@ -420,10 +577,10 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         // sorted table is class-descending: find each class's run
         for (uint32_t q = 0; q < nclass; ++q) {
             const int c = present[q];
-            uint64_t first = n_items, count = 0;
-            for (uint64_t k = 0; k < n_items; ++k)
+            uint64_t first = n_units, count = 0;
+            for (uint64_t k = 0; k < n_units; ++k)
                 if (cls[order[k]] == c) {
-                    if (first == n_items) first = k;
+                    if (first == n_units) first = k;
                     ++count;
                     work[q] += cost[order[k]];
                 }
@@ -514,7 +671,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     // workspace: [queues + status: 256][items][geoms][seg offsets][obs word offsets][pool]
     size_t off = 256;
     p->off_items = off;
-    off = align256(off + n_items * sizeof(SimItem));
+    off = align256(off + n_units * sizeof(SimItem));
     p->off_geoms = off;
     off = align256(off + (size_t)n_geom * sizeof(pchase_geom));
     p->off_seg = off;
@@ -539,18 +696,25 @@ uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan) {
 }
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
     if (!plan) return 0;
-    return (plan->layout.nwarps ? 1u : 0u) + (plan->jumbo.nwarps ? 1u : 0u);
+    // output clear + main slot-mix launch + side launch of jumbo units
+    return (plan->n_units ? 1u : 0u) + (plan->layout.nwarps ? 1u : 0u) +
+           (plan->jumbo.nwarps ? 1u : 0u);
 }
 
 size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes) {
     std::string d;
     if (plan) {
-        uint64_t modes[3] = {0, 0, 0};
-        for (const SimItem &it : plan->items) modes[it.mode < 3 ? it.mode : 0]++;
+        uint64_t modes[3] = {0, 0, 0}, split = 0;
+        for (const SimItem &it : plan->items) {
+            modes[it.mode < 3 ? it.mode : 0]++;
+            split += it.ksh && it.lead;
+        }
         char tmp[256];
         snprintf(tmp, sizeof tmp,
-                 "items=%llu scan=%llu table=%llu batch=%llu jumbo=%llu classes=%u warps=%u smem=%u slots=",
-                 (unsigned long long)plan->n_items, (unsigned long long)modes[0],
+                 "items=%llu units=%llu split=%llu scan=%llu table=%llu batch=%llu jumbo=%llu "
+                 "classes=%u warps=%u smem=%u slots=",
+                 (unsigned long long)plan->n_items, (unsigned long long)plan->n_units,
+                 (unsigned long long)split, (unsigned long long)modes[0],
                  (unsigned long long)modes[1], (unsigned long long)modes[2],
                  (unsigned long long)plan->n_jumbo, plan->layout.nclasses, plan->layout.nwarps,
                  plan->layout.smem_bytes);

@@ -62,7 +62,11 @@ __device__ __forceinline__ uint32_t random_way(uint64_t seed, uint32_t set, uint
 // ------------------------------------------------------------ plan items
 enum SetMode : uint8_t { kModeScan = 0, kModeTable = 1, kModeBatch = 2 };
 
-// One simulation item as the kernels read it (64-bit aligned, 88 bytes).
+// One simulation unit as the kernels read it (64-bit aligned, 112 bytes).
+// A caller's item is one unit, or several when its sets are split: unit r of
+// a split owns the sets whose index s has ((s >> psh) & (2^ksh - 1)) == kres,
+// renumbered locally as ((s >> (psh + ksh)) << psh) | (s & (2^psh - 1)), and
+// sees each line as the local line  local set + T' * (line div T).
 struct SimItem {
     const uint32_t *idx;  // NULL: analytic uniform chain
     uint32_t len;
@@ -70,24 +74,49 @@ struct SimItem {
     uint32_t n_elems;
     uint32_t stride;      // analytic chains, already reduced mod n_elems
     uint32_t ways;
-    uint32_t sets;
-    uint32_t magic_m;     // set = line mod sets, by DivMagic of `sets`
+    uint32_t sets;        // local sets T' = T >> ksh
+    uint32_t magic_m;     // local set = local line mod T', by DivMagic of T'
     uint8_t s1, s2, policy, mode;
     uint32_t lsh;         // line = index >> lsh  (b = 4 << lsh)
-    uint32_t table_n;     // line-table entries (kModeTable)
+    uint32_t table_n;     // line-table entries (local lines)
     uint64_t seed;
     uint64_t word_off;    // plan-owned bitmap layout
     uint32_t out_item;    // caller's item number
     uint32_t cand;        // matcher: candidate
     uint32_t obs;         // matcher: observed trace
-    uint32_t arena_bytes; // state bytes this item needs
+    uint32_t arena_bytes; // shared memory this unit needs (queue + set state)
     uint32_t ring;        // batch-mode LRU: recency ring entries per set (power of two)
-    uint32_t pad;
+    uint32_t gsets;       // the geometry's T
+    uint32_t gmagic;      // DivMagic of T
+    uint8_t gs1, gs2, psh, ksh;
+    uint32_t kres;        // this unit's residue (0 when not split)
+    uint8_t lead;         // 1 on exactly one unit of each caller item
+    uint8_t direct;       // step over consecutive accesses (dense, unsplit), no queue
+    uint8_t pad8[2];
+    float cost;           // planner's estimate of the unit's warp time (ns)
+    uint32_t pad32;
 };
 
-// One launch serves every item.  Each CTA holds the same mix of per-warp
-// shared-memory arenas ("slots"); warp w serves size class warp_class[w]
-// first and then takes items of smaller classes.
+static_assert(sizeof(SimItem) == 112, "SimItem layout");
+
+// Global set index of local set `local` of a unit (see SimItem).
+__host__ __device__ __forceinline__ uint32_t global_set(uint32_t local, uint32_t psh, uint32_t ksh,
+                                                        uint32_t kres) {
+    return ((((local >> psh) << ksh) | kres) << psh) | (local & ((1u << psh) - 1u));
+}
+
+// Staging at the start of a queued unit's arena: the compaction queue (run
+// heads of the unit's sets wait here, in trace order, until a full step of 32
+// is ready), then the ring the trace streams into ahead of use.
+constexpr uint32_t kQueueEntries = 64;   // uint2 {local line, position | observed bit << 31}
+constexpr uint32_t kQueueBytes = kQueueEntries * 8;
+constexpr uint32_t kRing = 16;           // chunks of 32 accesses (+ observed words)
+constexpr uint32_t kStageBytes = kQueueBytes + kRing * 32 * 4 + kRing * 4;
+
+// One launch serves every unit.  Each CTA holds the same mix of per-warp
+// shared-memory arenas ("slots"); a free warp takes, among the classes its
+// slot can hold (pad .. warp_class[w]), the next unit of the class whose next
+// unit has the highest estimated cost (each class queue is costliest first).
 constexpr int kMaxWarpsPerCta = 16;
 constexpr int kMaxClasses = 24;
 struct SlotLayout {
@@ -123,6 +152,10 @@ int set_last_error(int code, const char *msg);
 // Kernel launchers (sim.cu)
 cudaError_t launch_sim(const SimItem *items, const SlotLayout &layout, uint32_t *queues, int grid,
                        const SimOut &out, cudaStream_t st);
+// Zeroes the outputs the units accumulate into (bitmap words, miss counts,
+// timeline) for every caller item of the plan.
+cudaError_t launch_sim_zero(const SimItem *items, uint64_t n_units, int sms, const SimOut &out,
+                            cudaStream_t st);
 int sim_max_ctas_per_sm(const SlotLayout &layout);
 
 }  // namespace pchase

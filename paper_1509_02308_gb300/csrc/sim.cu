@@ -7,15 +7,17 @@
 // fill) or RANDOM (SplitMix64-keyed way).
 //
 // Mapping onto the GPU:
-//   * one warp per item (geometry x trace), pulled from a per-class atomic
-//     queue by persistent CTAs; the item's whole cache state lives in the
-//     warp's slice of shared memory;
-//   * the warp streams the trace 32 consecutive accesses per step (coalesced
-//     128-byte loads issued six steps ahead; analytic uniform chains are
-//     generated in registers instead), decodes set and line in registers, and
-//     marks accesses that repeat the previous access's line: such an access
-//     hits under every policy and changes no replacement order, so only run
-//     heads touch set state;
+//   * one warp per unit, pulled from a per-class atomic queue by persistent
+//     CTAs; a unit is an item (geometry x trace) or, for long items, one part
+//     of a split of its sets (sets never interact, so each part replays the
+//     whole trace but keeps only its own sets' accesses); the unit's cache
+//     state lives in the warp's slice of shared memory;
+//   * the warp reads the trace 32 accesses at a time (coalesced loads issued
+//     128 accesses ahead; analytic uniform chains are generated in registers)
+//     and drops every access that repeats the previous access's line: it hits
+//     under every policy and changes no replacement order.  The remaining run
+//     heads of the unit's sets are compacted, in trace order, into a queue in
+//     shared memory, and the cache steps over full groups of 32 of them;
 //   * heads in different sets are independent; heads in one set must act in
 //     trace order.  Three set modes:
 //       scan  (few ways, many sets): a head of rank r among the step's heads
@@ -26,8 +28,11 @@
 //             FIFO order as a ring pointer;
 //       batch (few sets): all heads of a set are resolved together, one lane
 //             each, without rounds (see the batch section below);
-//   * miss bits come from __ballot_sync; 32 steps are buffered one word per
-//     lane and stored as one coalesced 128-byte write.
+//   * miss bits are OR-ed into bitmap words zeroed beforehand (one reduction
+//     per word touched by a step), counts are added atomically, so the units
+//     of a split item need no coordination.
+#include <algorithm>
+
 #include "pchase_internal.cuh"
 
 namespace pchase {
@@ -52,26 +57,33 @@ constexpr uint32_t kStale = 0xFFFFFFFFu;
 // Stamps: an invalid way w holds stamp w (< a), a filled way t + a, where t
 // is the access time of its last use (LRU) or of its fill (FIFO, RANDOM), so
 // the smallest stamp is the lowest invalid way if any, else the victim.
-template <int POLICY, int A>
+template <int POLICY>
 struct ScanSets {
     uint2 *slot;
     uint32_t *evict;
     uint32_t ways;
     uint64_t seed;
+    uint32_t psh, ksh, kres;  // local -> global set (RANDOM's key)
 
-    __device__ __forceinline__ void init(uint8_t *arena, const SimItem &it, int lane) {
-        ways = A ? A : it.ways;
+    __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
+        ways = it.ways;
         seed = it.seed;
+        psh = it.psh;
+        ksh = it.ksh;
+        kres = it.kres;
         slot = reinterpret_cast<uint2 *>(arena);
+        evict = reinterpret_cast<uint32_t *>(arena + 8ull * it.sets * ways);
+    }
+
+    __device__ __forceinline__ void clear(const SimItem &it, int lane) {
         const uint32_t n = it.sets * ways;
-        evict = reinterpret_cast<uint32_t *>(arena + 8ull * n);
         for (uint32_t i = lane; i < n; i += 32) slot[i] = make_uint2(kInvalidLine, i % ways);
         if (POLICY == PCHASE_RANDOM)
             for (uint32_t i = lane; i < it.sets; i += 32) evict[i] = 0;
     }
 
     __device__ __forceinline__ bool access(uint32_t set, uint32_t line, uint32_t t) {
-        const uint32_t a = A ? A : ways;
+        const uint32_t a = ways;
         uint2 *s = slot + set * a;
         int hit = -1;
         uint32_t best = 0xFFFFFFFFu;
@@ -89,7 +101,7 @@ struct ScanSets {
         if (POLICY == PCHASE_RANDOM && best >= a) {
             const uint32_t k = evict[set];
             evict[set] = k + 1;
-            v = random_way(seed, set, k, a);
+            v = random_way(seed, global_set(set, psh, ksh, kres), k, a);
         }
         s[v] = make_uint2(line, t + a);
         return true;
@@ -108,10 +120,14 @@ struct TableSets {
     uint16_t *prv, *nxt, *tab;
     uint32_t ways;
     uint64_t seed;
+    uint32_t psh, ksh, kres;
 
-    __device__ __forceinline__ void init(uint8_t *arena, const SimItem &it, int lane) {
+    __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         seed = it.seed;
+        psh = it.psh;
+        ksh = it.ksh;
+        kres = it.kres;
         const uint32_t n = it.sets * ways;
         size_t off = 0;
         meta = reinterpret_cast<uint2 *>(arena);
@@ -125,6 +141,10 @@ struct TableSets {
             off += 2ull * n;
         }
         tab = reinterpret_cast<uint16_t *>(arena + off);
+    }
+
+    __device__ __forceinline__ void clear(const SimItem &it, int lane) {
+        const uint32_t n = it.sets * ways;
         const uint2 m0 = POLICY == PCHASE_LRU ? make_uint2(0xFFFFFFFFu, 0) : make_uint2(0, 0);
         for (uint32_t i = lane; i < it.sets; i += 32) meta[i] = m0;
         for (uint32_t i = lane; i < n; i += 32) sline[i] = kInvalidLine;
@@ -189,7 +209,7 @@ struct TableSets {
                 v = m.x;
                 m.x += 1;
             } else {
-                v = random_way(seed, set, m.y, a);
+                v = random_way(seed, global_set(set, psh, ksh, kres), m.y, a);
                 m.y += 1;
                 tab[sline[base + v]] = 0;
             }
@@ -257,6 +277,20 @@ struct Grouped {
 
 __device__ __forceinline__ Grouped group_heads(uint32_t line, uint32_t set, bool head, int lane,
                                                uint32_t lt, uint32_t *perm) {
+    // common case (compacted steps, single-set units): the heads fill lanes
+    // 0..n-1 and share one set, so they already form one group in order
+    const uint32_t hb = __ballot_sync(kFull, head);
+    const uint32_t s0 = __shfl_sync(kFull, set, 0);
+    if ((hb & (hb + 1u)) == 0 && __all_sync(kFull, !head || set == s0)) {
+        Grouped g;
+        g.x = line;
+        g.set = set;
+        g.act = head;
+        g.gmask = hb;
+        g.gb = 0;
+        g.dest = (uint32_t)lane;
+        return g;
+    }
     const uint32_t key = head ? set : (0x80000000u | (uint32_t)lane);
     const uint32_t gm = __match_any_sync(kFull, key);
     const bool leader = head && (gm & lt) == 0;
@@ -269,7 +303,7 @@ __device__ __forceinline__ Grouped group_heads(uint32_t line, uint32_t set, bool
     }
     const uint32_t base = __shfl_sync(kFull, inc - size, __ffs(gm) - 1);
     const uint32_t dest = base + __popc(gm & lt);
-    const uint32_t nh = __popc(__ballot_sync(kFull, head));
+    const uint32_t nh = __popc(hb);
     if (head) perm[dest] = (uint32_t)lane;
     __syncwarp();
     const bool act = (uint32_t)lane < nh;
@@ -312,10 +346,14 @@ struct BatchFR {
     uint32_t *perm;
     uint32_t ways;
     uint64_t seed;
+    uint32_t psh, ksh, kres;
 
-    __device__ __forceinline__ void init(uint8_t *arena, const SimItem &it, int lane) {
+    __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         seed = it.seed;
+        psh = it.psh;
+        ksh = it.ksh;
+        kres = it.kres;
         const uint32_t n = it.sets * ways;
         size_t off = 0;
         perm = reinterpret_cast<uint32_t *>(arena);
@@ -329,6 +367,10 @@ struct BatchFR {
             off += 8ull * n;
         }
         tab = reinterpret_cast<uint16_t *>(arena + off);
+    }
+
+    __device__ __forceinline__ void clear(const SimItem &it, int lane) {
+        const uint32_t n = it.sets * ways;
         for (uint32_t i = lane; i < it.sets; i += 32) meta[i] = make_uint4(0, 0, 0, 0);
         for (uint32_t i = lane; i < n; i += 32) sline[i] = kInvalidLine;
         if (POLICY == PCHASE_RANDOM)
@@ -358,7 +400,8 @@ struct BatchFR {
         } else {
             const uint32_t k = m.x + r;
             evicts = k >= a;
-            insw = evicts ? random_way(seed, g.set, m.y + (k - a), a) : k;
+            insw = evicts ? random_way(seed, global_set(g.set, psh, ksh, kres), m.y + (k - a), a)
+                          : k;
         }
         // next group rank with the same way
         const uint32_t sw = __match_any_sync(kFull, g.act ? g.set * a + insw
@@ -431,29 +474,31 @@ struct BatchFR {
     }
 };
 
-// LRU.  Arena: uint32 perm[32] + window scratch[16]; uint4 meta[T] =
+// LRU.  Arena: uint32 perm[32] (+ pad to 256 B); uint4 meta[T] =
 // {tail, head, live, -} (monotone ring positions); uint32 ring[T*R];
 // uint16 tab[table_n] (ring index + 1).
 struct BatchLRU {
     uint4 *meta;
     uint32_t *ring;
     uint16_t *tab;
-    uint32_t *perm, *wsc;
+    uint32_t *perm;
     uint32_t ways, R, rmask;
 
-    __device__ __forceinline__ void init(uint8_t *arena, const SimItem &it, int lane) {
+    __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         R = it.ring;
         rmask = R - 1;
         size_t off = 0;
         perm = reinterpret_cast<uint32_t *>(arena);
-        wsc = perm + 32;
         off += 256;
         meta = reinterpret_cast<uint4 *>(arena + off);
         off += 16ull * it.sets;
         ring = reinterpret_cast<uint32_t *>(arena + off);
         off += 4ull * it.sets * R;
         tab = reinterpret_cast<uint16_t *>(arena + off);
+    }
+
+    __device__ __forceinline__ void clear(const SimItem &it, int lane) {
         for (uint32_t i = lane; i < it.sets; i += 32) meta[i] = make_uint4(0, 0, 0, 0);
         uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
         for (uint32_t i = lane; i < (it.table_n + 1) / 2; i += 32) t32[i] = 0;
@@ -640,29 +685,137 @@ struct BatchLRU {
     }
 };
 
-// --------------------------------------------------------------- item loop
-// One step (32 accesses) per trip.  The code is kept small on purpose: warps
-// of many different items (policies, set modes) share each SM, and a larger
-// loop body multiplied by every variant stops fitting the instruction cache.
-constexpr uint32_t kUnroll = 1;
+// --------------------------------------------------------------- unit loop
+// cp.async (Ampere-style asynchronous global -> shared copies, 4 bytes a lane)
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
-template <typename Res>
-__device__ __forceinline__ void run_item(const SimItem it, Res &R, const SimOut out, int lane) {
+// ORs one step's miss bits into the unit's bitmap (words zeroed beforehand):
+// lanes hold increasing positions, so lanes sharing a word are consecutive;
+// each run of them is OR-reduced and its first lane issues one reduction.
+__device__ __forceinline__ void emit_bits(uint32_t *bm, uint32_t pos, bool miss, bool act,
+                                          int lane) {
+    const uint32_t p0 = __shfl_sync(kFull, pos, 0);
+    if (__all_sync(kFull, act && pos == p0 + (uint32_t)lane)) {
+        // 32 consecutive positions: at most two words
+        const uint32_t bits = __ballot_sync(kFull, miss);
+        if (lane == 0) {
+            const uint32_t sh = p0 & 31u;
+            atomicOr(bm + (p0 >> 5), bits << sh);
+            if (sh && (bits >> (32u - sh))) atomicOr(bm + (p0 >> 5) + 1, bits >> (32u - sh));
+        }
+        return;
+    }
+    const uint32_t w = act ? pos >> 5 : 0xFFFFFFFFu;
+    uint32_t b = miss ? 1u << (pos & 31u) : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t vb = __shfl_down_sync(kFull, b, o);
+        const uint32_t vw = __shfl_down_sync(kFull, w, o);
+        if (lane + o < 32 && vw == w) b |= vb;
+    }
+    const uint32_t wp = __shfl_up_sync(kFull, w, 1);
+    if (act && b && (lane == 0 || wp != w)) atomicOr(bm + w, b);
+}
+
+// Kinds of set state: mode * 3 + policy.
+enum : uint32_t {
+    kScanLru = kModeScan * 3 + PCHASE_LRU,
+    kScanFifo = kModeScan * 3 + PCHASE_FIFO,
+    kScanRandom = kModeScan * 3 + PCHASE_RANDOM,
+    kTableLru = kModeTable * 3 + PCHASE_LRU,
+    kTableFifo = kModeTable * 3 + PCHASE_FIFO,
+    kTableRandom = kModeTable * 3 + PCHASE_RANDOM,
+    kBatchLru = kModeBatch * 3 + PCHASE_LRU,
+    kBatchFifo = kModeBatch * 3 + PCHASE_FIFO,
+    kBatchRandom = kModeBatch * 3 + PCHASE_RANDOM,
+};
+
+// One step of heads through the unit's set state.  The state's views are
+// rebuilt from the arena each step (a few integer ops), so that this is the
+// only copy of every mode's code: all modes share one unit loop, which keeps
+// the simulator's hot code within the instruction cache while warps of many
+// different units share an SM.
+__device__ __forceinline__ bool resolve_step(uint32_t kind, uint8_t *st, const SimItem &it,
+                                             uint32_t line, uint32_t set, bool head, uint32_t pos,
+                                             int lane, uint32_t lt, uint32_t step) {
+    switch (kind) {
+    case kScanLru: { RoundResolver<ScanSets<PCHASE_LRU>> R; R.S.bind(st, it);
+                     return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kScanFifo: { RoundResolver<ScanSets<PCHASE_FIFO>> R; R.S.bind(st, it);
+                      return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kScanRandom: { RoundResolver<ScanSets<PCHASE_RANDOM>> R; R.S.bind(st, it);
+                        return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kTableLru: { RoundResolver<TableSets<PCHASE_LRU>> R; R.S.bind(st, it);
+                      return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kTableFifo: { RoundResolver<TableSets<PCHASE_FIFO>> R; R.S.bind(st, it);
+                       return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kTableRandom: { RoundResolver<TableSets<PCHASE_RANDOM>> R; R.S.bind(st, it);
+                         return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kBatchLru: { BatchLRU R; R.bind(st, it);
+                      return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kBatchFifo: { BatchFR<PCHASE_FIFO> R; R.bind(st, it);
+                       return R.resolve(line, set, head, pos, lane, lt, step); }
+    default: { BatchFR<PCHASE_RANDOM> R; R.bind(st, it);
+               return R.resolve(line, set, head, pos, lane, lt, step); }
+    }
+}
+
+__device__ __forceinline__ void clear_state(uint32_t kind, uint8_t *st, const SimItem &it,
+                                            int lane) {
+    switch (kind) {
+    case kScanLru: { ScanSets<PCHASE_LRU> S; S.bind(st, it); S.clear(it, lane); break; }
+    case kScanFifo: { ScanSets<PCHASE_FIFO> S; S.bind(st, it); S.clear(it, lane); break; }
+    case kScanRandom: { ScanSets<PCHASE_RANDOM> S; S.bind(st, it); S.clear(it, lane); break; }
+    case kTableLru: { TableSets<PCHASE_LRU> S; S.bind(st, it); S.clear(it, lane); break; }
+    case kTableFifo: { TableSets<PCHASE_FIFO> S; S.bind(st, it); S.clear(it, lane); break; }
+    case kTableRandom: { TableSets<PCHASE_RANDOM> S; S.bind(st, it); S.clear(it, lane); break; }
+    case kBatchLru: { BatchLRU S; S.bind(st, it); S.clear(it, lane); break; }
+    case kBatchFifo: { BatchFR<PCHASE_FIFO> S; S.bind(st, it); S.clear(it, lane); break; }
+    default: { BatchFR<PCHASE_RANDOM> S; S.bind(st, it); S.clear(it, lane); break; }
+    }
+}
+
+// One unit: gather trips fill the queue with the unit's run heads, and each
+// step hands the next 32 of them to the unit's set state in trace order.
+__device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, const SimOut &out,
+                                         int lane) {
+    // arena: [queue + staging ring (units that compact their heads)][set state]
+    uint2 *const queue = reinterpret_cast<uint2 *>(g_smem + arena);
+    uint8_t *const st = g_smem + arena + (it.direct ? 0u : kStageBytes);
+    const uint32_t kind = (uint32_t)it.mode * 3u + it.policy;
+    clear_state(kind, st, it, lane);
+    __syncwarp();
     const uint32_t len = it.len;
     const uint32_t *__restrict__ idxp = it.idx;
     const uint32_t N = it.n_elems;
     const uint32_t lsh = it.lsh, sets = it.sets, mm = it.magic_m, s1 = it.s1, s2 = it.s2;
+    const bool split = it.ksh != 0;
+    const uint32_t gT = it.gsets, gm = it.gmagic, gs1 = it.gs1, gs2 = it.gs2;
+    const uint32_t psh = it.psh, ksh = it.ksh, kres = it.kres;
+    const uint32_t pmask = (1u << psh) - 1u, kmask = (1u << ksh) - 1u;
     const uint32_t warmup = it.warmup;
     const uint32_t lt = lanemask_lt();
     const bool ham = out.dist != nullptr;
-    uint32_t *const bitmaps = out.bitmaps;
     const uint32_t *const observed = out.observed;
     const uint64_t stop_above = out.stop_above;
-    const uint64_t wbase = out.word_offsets ? out.word_offsets[it.out_item] : it.word_off;
+    uint32_t *const bm = out.bitmaps
+        ? out.bitmaps + (out.word_offsets ? out.word_offsets[it.out_item] : it.word_off)
+        : nullptr;
     const uint64_t obase = ham ? out.obs_word_offsets[it.obs] : 0;
 
-    uint32_t carry = kInvalidLine;
-    uint32_t myword = 0;
     uint32_t tot = 0, aft = 0, bad = 0;
     uint64_t dsum = 0;  // Hamming distance so far (warp-uniform)
 
@@ -672,28 +825,21 @@ __device__ __forceinline__ void run_item(const SimItem it, Res &R, const SimOut 
         aj = (uint32_t)(((uint64_t)lane * it.stride) % N);
         ainc = (uint32_t)((32ull * it.stride) % N);
     }
-    const uint32_t nsteps = (len + 31) >> 5;
-    // explicit traces: the next block's loads are issued one block ahead
-    uint32_t pf[kUnroll];
-#pragma unroll
-    for (uint32_t u = 0; u < kUnroll; ++u) {
-        const uint32_t t = (u << 5) + (uint32_t)lane;
-        pf[u] = (idxp && t < len) ? idxp[t] : 0u;
-    }
-
-    for (uint32_t st0 = 0; st0 < nsteps; st0 += kUnroll) {
-        uint32_t line[kUnroll], set[kUnroll];
-        bool head[kUnroll];
-        // ---- decode four steps (no cache state involved)
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll; ++u) {
-            const uint32_t t = ((st0 + u) << 5) + (uint32_t)lane;
+    if (it.direct) {
+        // ---- direct: nearly every access is a head, so each step takes 32
+        // consecutive accesses as they come (repeats ride along as hits) and
+        // the unit, sole writer of its words, stores 32 steps' words at once
+        const uint32_t nsteps = (len + 31) >> 5;
+        uint32_t carry = kInvalidLine, myword = 0;
+        uint32_t pf = (idxp && (uint32_t)lane < len) ? idxp[lane] : 0u;
+        for (uint32_t s0 = 0; s0 < nsteps; ++s0) {
+            const uint32_t t = (s0 << 5) + (uint32_t)lane;
             bool active = t < len;
             uint32_t j;
             if (idxp) {
-                j = pf[u];
-                const uint32_t tn = t + (kUnroll << 5);
-                pf[u] = tn < len ? idxp[tn] : 0u;
+                j = pf;
+                const uint32_t tn = t + 32;
+                pf = tn < len ? idxp[tn] : 0u;
             } else {
                 j = aj;
                 aj = (aj >= N - ainc) ? aj - (N - ainc) : aj + ainc;
@@ -703,93 +849,151 @@ __device__ __forceinline__ void run_item(const SimItem it, Res &R, const SimOut 
                 active = false;
             }
             const uint32_t ln = j >> lsh;
-            line[u] = ln;
-            set[u] = ln - div_q(ln, mm, s1, s2) * sets;
-            // one rotate: lane i gets lane i-1's line; lane 0 gets lane 31's,
-            // which is the previous access for the next step's lane 0
+            const uint32_t set = ln - div_q(ln, mm, s1, s2) * sets;
             const uint32_t rot = __shfl_sync(kFull, ln, (lane + 31) & 31);
             const uint32_t prev = lane == 0 ? carry : rot;
             carry = rot;
-            head[u] = active && ln != prev;
-        }
-        // ---- state updates in trace order, then the step's miss word
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll; ++u) {
-            const uint32_t st = st0 + u;
-            const uint32_t t = (st << 5) + (uint32_t)lane;
-            const bool miss = R.resolve(line[u], set[u], head[u], t, lane, lt, st + 1);
+            const bool head = active && ln != prev;
+            const bool miss = resolve_step(kind, st, it, ln, set, head, t, lane, lt, s0 + 1);
             const uint32_t bits = __ballot_sync(kFull, miss);
-            // accesses at or after the warm-up within this step
-            const uint32_t base = st << 5;
+            const uint32_t base = s0 << 5;
             const uint32_t after = base >= warmup ? kFull
                                  : (warmup - base >= 32 ? 0u : ~((1u << (warmup - base)) - 1u));
             tot += __popc(bits);
             aft += __popc(bits & after);
-            const uint32_t slot = st & 31;
+            const uint32_t slot = s0 & 31;
             if ((uint32_t)lane == slot) myword = bits;
-            if (st < nsteps && (slot == 31 || st + 1 == nsteps)) {
-                const uint64_t w0 = (uint64_t)(st & ~31u);
+            if (slot == 31 || s0 + 1 == nsteps) {
+                const uint32_t w0 = s0 & ~31u;
                 uint32_t dl = 0;
                 if ((uint32_t)lane <= slot) {
                     if (ham) dl = __popc(observed[obase + w0 + lane] ^ myword);
-                    else if (bitmaps) bitmaps[wbase + w0 + lane] = myword;
+                    else if (bm) bm[w0 + lane] = myword;
                 }
                 myword = 0;
-                if (ham) dsum += __reduce_add_sync(kFull, dl);
+                if (ham) {
+                    dsum += __reduce_add_sync(kFull, dl);
+                    if (dsum > stop_above) break;
+                }
             }
         }
-        if (ham && dsum > stop_above) break;
+    } else {
+        uint32_t qw = 0, qr = 0;         // queue entries written / read (warp-uniform)
+        uint32_t ocarry = kInvalidLine;  // line of the access before the next chunk
+        uint32_t ccarry = kInvalidLine;  // local line of the last head handed out
+        uint32_t step = 0;
+        // staging ring: chunk c (32 accesses) lands in ring[c % kRing][lane],
+        // its observed word in oring[c % kRing]; kRing - 1 chunks in flight.
+        // Each lane reads back only what it copied itself.
+        uint32_t *const ring = reinterpret_cast<uint32_t *>(g_smem + arena + kQueueBytes);
+        uint32_t *const oring = ring + kRing * 32;
+        const uint32_t nchunks = (len + 31) >> 5;
+        auto issue = [&](uint32_t c) {
+            if (c < nchunks) {
+                const uint32_t t = (c << 5) + (uint32_t)lane;
+                if (idxp && t < len) cp_async4(ring + (c % kRing) * 32 + lane, idxp + t);
+                if (ham && lane == 0) cp_async4(oring + (c % kRing), observed + obase + c);
+            }
+            cp_async_commit();
+        };
+        for (uint32_t c = 0; c + 1 < kRing; ++c) issue(c);
+        uint32_t cin = 0;  // next chunk to gather
+
+        for (;;) {
+            if (qw - qr < 32 && cin < nchunks) {
+                // ---- gather one chunk (at most 31 + 32 entries queued)
+                issue(cin + kRing - 1);
+                cp_async_wait<kRing - 1>();
+                const uint32_t t = (cin << 5) + (uint32_t)lane;
+                bool valid = t < len;
+                uint32_t j;
+                if (idxp) {
+                    j = ring[(cin % kRing) * 32 + lane];
+                } else {
+                    j = aj;
+                    aj = (aj >= N - ainc) ? aj - (N - ainc) : aj + ainc;
+                }
+                const uint32_t ow =
+                    ham ? __shfl_sync(kFull, lane == 0 ? oring[cin % kRing] : 0u, 0) : 0u;
+                if (valid && j >= N) {
+                    bad = 1;
+                    valid = false;
+                }
+                const uint32_t ln = j >> lsh;
+                // one rotate: lane i gets lane i-1's line; lane 0 gets lane
+                // 31's, the previous access of the next chunk's lane 0
+                const uint32_t rot = __shfl_sync(kFull, ln, (lane + 31) & 31);
+                const uint32_t prevl = lane == 0 ? ocarry : rot;
+                ocarry = rot;
+                bool mine = valid;
+                uint32_t lp = ln;
+                if (split) {
+                    const uint32_t q = div_q(ln, gm, gs1, gs2);
+                    const uint32_t set = ln - q * gT;
+                    const uint32_t sg = set >> psh;
+                    mine = valid && (sg & kmask) == kres;
+                    lp = ((((sg >> ksh) << psh) | (set & pmask))) + q * sets;
+                }
+                const bool take = mine && ln != prevl;
+                const uint32_t bal = __ballot_sync(kFull, take);
+                if (take) {
+                    const uint32_t pv = ham ? (t | (((ow >> lane) & 1u) << 31)) : t;
+                    queue[(qw + __popc(bal & lt)) & (kQueueEntries - 1)] = make_uint2(lp, pv);
+                }
+                qw += __popc(bal);
+                if (ham) {
+                    // dropped repeats hit: they differ where a miss was observed
+                    const uint32_t rep = __ballot_sync(kFull, mine && !take);
+                    dsum += __popc(rep & ow);
+                }
+                ++cin;
+                continue;
+            }
+            const uint32_t avail = qw - qr;
+            if (avail == 0) break;
+            // ---- one step over the next (up to) 32 heads
+            __syncwarp();
+            const bool act = (uint32_t)lane < avail;
+            const uint2 e = act ? queue[(qr + (uint32_t)lane) & (kQueueEntries - 1)]
+                                : make_uint2(kInvalidLine, 0u);
+            qr += avail < 32 ? avail : 32u;
+            __syncwarp();
+            const uint32_t line = e.x;
+            const uint32_t pos = e.y & 0x7FFFFFFFu;
+            const uint32_t set = line - div_q(line, mm, s1, s2) * sets;
+            const uint32_t rot = __shfl_sync(kFull, line, (lane + 31) & 31);
+            const uint32_t prev = lane == 0 ? ccarry : rot;
+            ccarry = rot;
+            const bool head = act && line != prev;
+            ++step;
+            const bool miss = resolve_step(kind, st, it, line, set, head, pos, lane, lt, step);
+            const uint32_t bits = __ballot_sync(kFull, miss);
+            tot += __popc(bits);
+            aft += __popc(__ballot_sync(kFull, miss && pos >= warmup));
+            if (ham) {
+                dsum += __popc(__ballot_sync(kFull, act && miss != ((e.y >> 31) != 0)));
+                if (dsum > stop_above) break;
+            } else if (bm && bits) {
+                emit_bits(bm, pos, miss, act, lane);
+            }
+        }
+        // copies still in flight (an early stop) must land before the arena
+        // is handed to the next unit
+        cp_async_wait_all();
     }
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(out.status, PCHASE_DEV_INDEX_RANGE);
-    if (ham) {
-        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(out.dist + it.cand),
-                                 (unsigned long long)dsum);
-    } else if (lane == 0 && out.miss_counts) {
-        out.miss_counts[2ull * it.out_item] = tot;
-        out.miss_counts[2ull * it.out_item + 1] = aft;
+    if (lane == 0) {
+        if (ham) {
+            if (dsum)
+                atomicAdd(reinterpret_cast<unsigned long long *>(out.dist + it.cand),
+                          (unsigned long long)dsum);
+        } else if (out.miss_counts) {
+            unsigned long long *mc =
+                reinterpret_cast<unsigned long long *>(out.miss_counts + 2ull * it.out_item);
+            if (tot) atomicAdd(mc, (unsigned long long)tot);
+            if (aft) atomicAdd(mc + 1, (unsigned long long)aft);
+        }
     }
-}
-
-template <int POLICY, int A>
-__device__ __forceinline__ void run_scan(const SimItem it, uint32_t arena, const SimOut out,
-                                         int lane) {
-    RoundResolver<ScanSets<POLICY, A>> R;
-    R.S.init(g_smem + arena, it, lane);
-    __syncwarp();
-    run_item(it, R, out, lane);
-}
-
-template <int POLICY>
-__device__ __noinline__ void run_scan_any(const SimItem it, uint32_t arena, const SimOut out,
-                                          int lane) {
-    if (it.ways == 1) run_scan<POLICY, 1>(it, arena, out, lane);
-    else run_scan<POLICY, 0>(it, arena, out, lane);
-}
-
-template <int POLICY>
-__device__ __noinline__ void run_table(const SimItem it, uint32_t arena, const SimOut out,
-                                       int lane) {
-    RoundResolver<TableSets<POLICY>> R;
-    R.S.init(g_smem + arena, it, lane);
-    __syncwarp();
-    run_item(it, R, out, lane);
-}
-
-template <int POLICY>
-__device__ __noinline__ void run_batch_fr(const SimItem it, uint32_t arena, const SimOut out,
-                                          int lane) {
-    BatchFR<POLICY> R;
-    R.init(g_smem + arena, it, lane);
-    __syncwarp();
-    run_item(it, R, out, lane);
-}
-
-__device__ __noinline__ void run_batch_lru(const SimItem it, uint32_t arena, const SimOut out,
-                                           int lane) {
-    BatchLRU R;
-    R.init(g_smem + arena, it, lane);
-    __syncwarp();
-    run_item(it, R, out, lane);
 }
 
 __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ items,
@@ -798,42 +1002,69 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t arena = L.warp_off[warp];
-    for (int c = (int)L.warp_class[warp]; c >= (int)L.pad; --c) {
-        for (;;) {
-            uint32_t k = 0;
-            if (lane == 0) k = atomicAdd(queues + c, 1u);
-            k = __shfl_sync(kFull, k, 0);
-            if (k >= L.cls_count[c]) break;
+    const uint32_t top = L.warp_class[warp];
+    // class this lane watches (pad + lane <= top)
+    const uint32_t wc = L.pad + (uint32_t)lane;
+    const bool watch = wc <= top && wc < L.nclasses;
+    const uint32_t cnt = watch ? L.cls_count[wc] : 0u;
+    const uint32_t first = watch ? L.cls_first[wc] : 0u;
+    for (;;) {
+        // longest first: the class whose next unit costs most
+        uint32_t key = 0;
+        if (watch) {
+            const uint32_t h = *reinterpret_cast<volatile uint32_t *>(queues + wc);
+            if (h < cnt) key = __float_as_uint(fmaxf(items[first + h].cost, 1.0f));
+        }
+        const uint32_t kmax = __reduce_max_sync(kFull, key);
+        if (kmax == 0) break;  // every class this slot can hold is done
+        const int src = __ffs(__ballot_sync(kFull, key == kmax)) - 1;
+        const uint32_t c = L.pad + (uint32_t)src;
+        uint32_t k = 0;
+        if (lane == src) k = atomicAdd(queues + c, 1u);
+        k = __shfl_sync(kFull, k, src);
+        if (k >= L.cls_count[c]) continue;  // taken meanwhile: look again
+        {
             const SimItem it = items[L.cls_first[c] + k];
             uint64_t t_start = 0;
             if (out.timeline) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
-            if (it.mode == kModeScan) {
-                if (it.policy == PCHASE_LRU) run_scan_any<PCHASE_LRU>(it, arena, out, lane);
-                else if (it.policy == PCHASE_FIFO) run_scan_any<PCHASE_FIFO>(it, arena, out, lane);
-                else run_scan_any<PCHASE_RANDOM>(it, arena, out, lane);
-            } else if (it.mode == kModeTable) {
-                if (it.policy == PCHASE_LRU) run_table<PCHASE_LRU>(it, arena, out, lane);
-                else if (it.policy == PCHASE_FIFO) run_table<PCHASE_FIFO>(it, arena, out, lane);
-                else run_table<PCHASE_RANDOM>(it, arena, out, lane);
-            } else {
-                if (it.policy == PCHASE_LRU) run_batch_lru(it, arena, out, lane);
-                else if (it.policy == PCHASE_FIFO) run_batch_fr<PCHASE_FIFO>(it, arena, out, lane);
-                else run_batch_fr<PCHASE_RANDOM>(it, arena, out, lane);
-            }
+            run_unit(it, arena, out, lane);
             __syncwarp();
             if (out.timeline && lane == 0) {
-                uint64_t t_end, sm;
+                // units of a split item share the entry: first start, last end
+                uint64_t t_end;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
                 uint32_t smid;
                 asm("mov.u32 %0, %%smid;" : "=r"(smid));
-                sm = smid;
-                uint64_t *tl = out.timeline + 4ull * it.out_item;
-                tl[0] = t_start;
-                tl[1] = t_end;
-                tl[2] = sm;
-                tl[3] = (uint64_t)warp;
+                unsigned long long *tl =
+                    reinterpret_cast<unsigned long long *>(out.timeline + 4ull * it.out_item);
+                atomicMin(tl, (unsigned long long)t_start);
+                const unsigned long long prev_end = atomicMax(tl + 1, (unsigned long long)t_end);
+                if (prev_end <= t_end) {
+                    tl[2] = smid;
+                    tl[3] = (unsigned long long)warp;
+                }
             }
         }
+    }
+}
+
+// One warp per unit; the lead unit of each caller item clears its outputs.
+__global__ void __launch_bounds__(256) sim_zero_kernel(const SimItem *__restrict__ items,
+                                                       uint64_t n_units, SimOut out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_units;
+         i += nw) {
+        const SimItem &it = items[i];
+        if (!it.lead) continue;
+        const uint32_t item = it.out_item;
+        if (out.bitmaps) {
+            uint32_t *bm = out.bitmaps + (out.word_offsets ? out.word_offsets[item] : it.word_off);
+            const uint32_t nwords = (it.len + 31) >> 5;
+            for (uint32_t k = (uint32_t)lane; k < nwords; k += 32) bm[k] = 0;
+        }
+        if (out.miss_counts && lane < 2) out.miss_counts[2ull * item + lane] = 0;
+        if (out.timeline && lane < 4) out.timeline[4ull * item + lane] = lane == 0 ? ~0ull : 0ull;
     }
 }
 
@@ -845,6 +1076,14 @@ cudaError_t launch_sim(const SimItem *items, const SlotLayout &layout, uint32_t 
                                          (int)layout.smem_bytes);
     if (e != cudaSuccess) return e;
     sim_kernel<<<grid, layout.nwarps * 32, layout.smem_bytes, st>>>(items, layout, queues, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sim_zero(const SimItem *items, uint64_t n_units, int sms, const SimOut &out,
+                            cudaStream_t st) {
+    if (!n_units || !(out.bitmaps || out.miss_counts || out.timeline)) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((n_units + 7) / 8, (uint64_t)std::max(sms, 1) * 8);
+    sim_zero_kernel<<<(unsigned)blocks, 256, 0, st>>>(items, n_units, out);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,9 @@ def test_match_distances_equal_oracle():
     traces = [(torch.from_numpy(t.view(np.int32)).cuda(), r.length, r.warmup, r.n_elems, r.stride)
               for t, r in zip(host, runs)]
     plan = api.SimPlan(cands, traces)
+    # the same candidates with every item split into set-parts
+    split = api.SimPlan(cands, traces, tune={"max_split": 4, "split_cost_ns": 1})
+    assert " split=0 " not in split.description
     words, offs = [], [0]
     for o in obs_host:
         wv = np.packbits(o, bitorder="little")
@@ -95,11 +98,15 @@ def test_match_distances_equal_oracle():
     seeds = np.array([g.seed for g in cands], dtype=np.uint64)
     want = oracle.match(rows, seeds, host, obs_host)
     assert np.array_equal(dist, want)
+    assert np.array_equal(split.match(obs, owo).cpu().numpy().astype(np.uint64), want)
     # early stop keeps every candidate at or under the bound exact
     bound = int(np.sort(want)[5])
     d2 = plan.match(obs, owo, stop_above=bound).cpu().numpy().astype(np.uint64)
     assert np.array_equal(d2[want <= bound], want[want <= bound])
     assert (d2[want > bound] > bound).all()
+    d3 = split.match(obs, owo, stop_above=bound).cpu().numpy().astype(np.uint64)
+    assert np.array_equal(d3[want <= bound], want[want <= bound])
+    assert (d3[want > bound] > bound).all()
     # canonical pick
     pick = api.pchase_canonical_pick(cands, torch.from_numpy(want.astype(np.int64)).cuda())
     pi, nb = oracle.canonical_pick(rows, want)

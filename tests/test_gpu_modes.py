@@ -16,12 +16,19 @@ pytestmark = pytest.mark.gpu
 if torch.cuda.is_available():
     from paper_1509_02308_gb300 import api
 
+# split_*: every item whose T has a power-of-two factor is split into as many
+# set-parts as that allows (up to 8), each part on its own warp
+SPLIT = {"max_split": 8, "split_cost_ns": 1}
 TUNES = {
     "batch_all": {"batch_max_sets": 1 << 30},
     "no_batch_scan8": {"batch_max_sets": 0xFFFFFFFF, "scan_max_ways": 8},
     "no_batch_scan32": {"batch_max_sets": 0xFFFFFFFF, "scan_max_ways": 32},
-    "no_batch_table": {"batch_max_sets": 0xFFFFFFFF, "scan_max_ways": 0xFFFFFFFF},
+    "no_batch_table": {"batch_max_sets": 0xFFFFFFFF, "scan_max_ways": 1},
     "default": None,
+    "split_batch": {**SPLIT, "batch_max_sets": 1 << 30},
+    "split_scan": {**SPLIT, "batch_max_sets": 0xFFFFFFFF, "scan_max_ways": 32},
+    "split_table": {**SPLIT, "batch_max_sets": 0xFFFFFFFF, "scan_max_ways": 1},
+    "split_default": SPLIT,
 }
 
 
@@ -67,6 +74,8 @@ def test_modes_match_oracle(tune_name):
     dev = [torch.from_numpy(t.view(np.int32)).cuda() for t in host]
     traces = [(d, t.size, min(t.size, 50), n, 1) for d, t, n in zip(dev, host, n_el)]
     plan = api.SimPlan(geoms, traces, tune=TUNES[tune_name])
+    if tune_name.startswith("split"):
+        assert " split=0 " not in plan.description, plan.description
     bitmaps, counts = plan.run()
     torch.cuda.synchronize()
     b = bitmaps.cpu().numpy().view(np.uint32)

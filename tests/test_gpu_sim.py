@@ -189,6 +189,7 @@ def test_config2_full_size_sampled():
     traces = [(flat[int(offs[i]):int(offs[i + 1])], r.length, r.warmup, r.n_elems, r.stride)
               for i, r in enumerate(runs)]
     plan = SimPlan(geoms, traces, pairs=[(i, i) for i in range(len(runs))])
+    assert " split=0 " not in plan.description  # the longest items run as set-parts
     bitmaps, counts = plan.run()
     torch.cuda.synchronize()
     counts = counts.view(-1, 2).cpu().numpy()
@@ -197,7 +198,11 @@ def test_config2_full_size_sampled():
     # sample: cheap items of every policy and set mode, plus the first and last
     cand = [i for i in range(len(runs)) if runs[i].length <= 60000 and geoms[i].ways <= 512]
     rng = np.random.Generator(np.random.PCG64(7))
-    sample = sorted(set(rng.choice(cand, size=40, replace=False).tolist()))
+    sample = set(rng.choice(cand, size=40, replace=False).tolist())
+    # and the longest items of modest associativity (split into set-parts)
+    longest = sorted((i for i in range(len(runs)) if geoms[i].ways <= 64),
+                     key=lambda i: -runs[i].length)
+    sample = sorted(sample | set(longest[:6]))
     for i in sample:
         g, r = geoms[i], runs[i]
         want = oracle_bits(g, oracle.pchase_trace(r.n_elems, r.stride, r.length))
