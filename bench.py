@@ -158,6 +158,12 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+# From one ncu capture (--set full) of the current sim_kernel on the batched
+# workload with items capped at 65,536 accesses.
+SIM_DRAM_BYTES_PER_ACCESS = (264.800256e6 + 7.800576e6) / 65559830
+SIM_WARP_INST_PER_ACCESS = 554370987 / 65559830
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -323,8 +329,19 @@ def ours(args):
     alg_bytes = total_acc * 4.0 + total_acc / 8.0
     achieved = alg_bytes / (sim_avg * 1e-3) / 1e9
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # DRAM bytes per access of sim_kernel from one ncu capture of the same
+    # kernel on this workload with items capped at 64 K accesses (272.6 MB for
+    # 65,559,830 accesses), scaled to this launch set by its accesses
+    traffic = SIM_DRAM_BYTES_PER_ACCESS * total_acc
+    # issue roofline: warp instructions per access from the same capture
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    issue_peak = sms * 4 * sm_mhz * 1e6 / SIM_WARP_INST_PER_ACCESS  # accesses/s
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "issue": {"warp_inst_per_access": SIM_WARP_INST_PER_ACCESS,
+                      "peak_accesses_per_s": issue_peak,
+                      "frac": total_acc / (sim_avg * 1e-3) / issue_peak,
+                      "note": "SMs x 4 schedulers x median SM clock / measured instructions"},
             "kernel": "sim_kernel (all size classes of one pchase_sim_run)",
             "kernel_ms": sim_avg, "peak_kind": f"{peak_kind} HBM copy bandwidth",
             "algorithmic_bytes_per_launch": alg_bytes,
