@@ -265,7 +265,7 @@ def p512_plan():
 def latency_noise_params():
     """Synthetic timing model of the learned-inverse traces (seeded on the
     device): per trace t0 ~ U[20, 400] cycles and t1 = t0 * rho with
-    log(rho) ~ U[log 1.1, log 30] (the span of Fig. 11's latency spectrum);
+    log(rho) ~ U[log 1.5, log 30] (within the span of Fig. 11's latency spectrum);
     per point latency t0 + (t1 - t0) * r, Gaussian relative jitter sigma
     2 %, spikes on 0.5 % of points scaled by U[2, 10]; then min-max
     normalisation to [0, 1]."""

@@ -32,15 +32,24 @@ def test_version_string():
     assert b"sm_103a" in C.load().pchase_version()
 
 
-def _plan(geoms, traces, pairs=None):
+def _plan(geoms, traces, pairs=None, tune=None):
     L = C.load()
     ga, ta = C.geom_array(geoms), C.trace_array(traces)
     pa = C.pair_array(pairs) if pairs is not None else None
+    tn = C.Tune(*[tune.get(f, 0) for f, _ in C.Tune._fields_]) if tune else None
     h = ctypes.c_void_p()
     rc = L.pchase_sim_plan_create(ctypes.addressof(ga), len(geoms), ctypes.addressof(ta),
                                   len(traces), ctypes.addressof(pa) if pa is not None else None,
-                                  len(pairs) if pairs else 0, None, ctypes.byref(h))
+                                  len(pairs) if pairs else 0,
+                                  ctypes.addressof(tn) if tn is not None else None, ctypes.byref(h))
     return rc, h
+
+
+def _describe(h) -> dict:
+    L = C.load()
+    buf = ctypes.create_string_buffer(4096)
+    L.pchase_sim_plan_describe(h, buf, len(buf))
+    return dict(kv.split("=", 1) for kv in buf.value.decode().split())
 
 
 @pytest.mark.parametrize("geom,code", [
@@ -77,6 +86,40 @@ def test_plan_sizes_and_layout():
         assert L.pchase_sim_plan_items(h) == 6
         assert L.pchase_sim_plan_bitmap_words(h) == 2 * (4 + 2 + 0)
         assert L.pchase_sim_plan_workspace_bytes(h) >= 256 + 6 * 80
+    finally:
+        L.pchase_sim_plan_destroy(h)
+
+
+def test_planner_splits_only_what_can_gain():
+    """Host-side split rules: a split part owns a power-of-two share of the
+    sets the trace actually visits; fully associative caches and traces whose
+    stride keeps them in one set stay whole; splitting is off at max_split 1."""
+    L = C.load()
+    geoms = [W.Geom(64 * 8 * 64, 64, 8, 64),   # T = 64
+             W.Geom(8 * 64, 64, 8, 1),          # fully associative
+             W.Geom(96 * 2 * 64, 64, 2, 96)]    # T = 3 * 32
+    n = 1 << 16
+    traces = [(None, 1 << 20, 0, n, 16),        # 64 B stride: one line per access, all sets
+              (None, 1 << 20, 0, n, 64 * 16)]   # 4 KB stride: 64 lines apart
+    force = {"max_split": 8, "split_cost_ns": 1}
+    rc, h = _plan(geoms, traces, tune=force)
+    assert rc == C.OK
+    try:
+        d = _describe(h)
+        # T=64: 8 parts with the dense trace; the 4 KB stride visits set 0 only
+        # (64 lines apart, T = 64), so it stays whole.  Fully associative: whole.
+        # T=96 with the dense trace: 8 parts (power-of-two factor 32); with the
+        # 4 KB stride the visited sets are multiples of 32, i.e. 3 of them and
+        # no power-of-two share to split.
+        assert int(d["items"]) == 6
+        assert int(d["split"]) == 2 and int(d["units"]) == 6 - 2 + 16
+    finally:
+        L.pchase_sim_plan_destroy(h)
+    rc, h = _plan(geoms, traces, tune={"max_split": 1, "split_cost_ns": 1})
+    assert rc == C.OK
+    try:
+        d = _describe(h)
+        assert int(d["split"]) == 0 and int(d["units"]) == 6
     finally:
         L.pchase_sim_plan_destroy(h)
 
