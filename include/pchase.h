@@ -53,7 +53,7 @@ typedef enum {
 /* Bits a kernel ORs into the caller's device status word (uint32). */
 #define PCHASE_DEV_INDEX_RANGE 1u   /* a trace index was >= n_elems; the access was skipped */
 #define PCHASE_DEV_CHAIN_RANGE 2u   /* a chain pointed outside its array; the walk stopped */
-#define PCHASE_DEV_TIMEOUT 4u       /* a probe's iteration cap ended a loop */
+#define PCHASE_DEV_TIMEOUT 4u       /* a probe's iteration cap, or a bounded wait, ended a loop */
 
 typedef enum { PCHASE_LRU = 0, PCHASE_FIFO = 1, PCHASE_RANDOM = 2 } pchase_policy;
 
@@ -379,7 +379,9 @@ int pchase_probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas,
  * Network: 4 x [conv1d k=5, stride 2, pad 2, 64 channels, GELU] (512 -> 32
  * positions), flatten 2048 -> FC 256 + GELU -> FC 31 logits, read as heads of
  * 17 (capacity), 4 (line size), 7 (ways), 3 (policy).  BF16 GEMM operands,
- * FP32 accumulation; FP32 master weights, Adam moments and gradients.
+ * FP32 accumulation; FP32 master weights, Adam moments and gradients.  At
+ * inference the 64-channel convolutions run on the tcgen05 tensor cores with
+ * TMEM accumulators.
  *
  * Buffers: the caller allocates `params` (pchase_inverse_param_bytes; its
  * first 4 * param_count bytes are the FP32 weights in layer order, each
@@ -397,6 +399,15 @@ void pchase_inverse_destroy(pchase_inverse *h);
 uint64_t pchase_inverse_param_count(const pchase_inverse *h);
 size_t pchase_inverse_param_bytes(const pchase_inverse *h);
 size_t pchase_inverse_work_bytes(const pchase_inverse *h);
+
+/* Byte offset in `work` of a device uint32 status word: pchase_inverse_infer,
+ * _classify and _train_step clear it when called, and a tensor-core
+ * completion wait that gives up (after 2 s) ORs PCHASE_DEV_TIMEOUT into it. */
+size_t pchase_inverse_status_offset(const pchase_inverse *h);
+/* Byte offset in `work` of convolution layer `layer`'s (0..3) BF16 output,
+ * [B][positions][64] for the last chunk of the last forward pass; 0 for a
+ * layer out of range.  For inspection and tests. */
+size_t pchase_inverse_activation_offset(const pchase_inverse *h, uint32_t layer);
 
 /* Uniform init of every weight in +-sqrt(6 / fan_in) (SplitMix64 keyed on
  * seed and index), biases 0, Adam moments 0. */

@@ -1,0 +1,314 @@
+// Tensor-core convolution of the learned inverse's 64-channel layers
+// (kernel 5, stride 2, zero padding 2; S7) on sm_103a's fifth-generation
+// tensor cores: tcgen05.mma with both operands in shared memory and the FP32
+// accumulator in tensor memory (TMEM), implicit im2col.
+//
+// out[b][p][co] = GELU(bias[co] + sum_k sum_ci W[co][k*64 + ci] * x[b][2p + k - 2][ci])
+//
+// One tile is 128 consecutive output rows (b, p) x 64 output channels, i.e.
+// one M=128, N=64 accumulator, computed as 5 taps x 4 K-slices of 16 channels
+// (20 MMAs, issued by one thread).  The A operand of tap k would be the input
+// rows 2p + k - 2: rows two apart, which no shared-memory matrix descriptor
+// can address.  So the tile's rows are taken in a transposed order, TMEM lane
+// r = 8g + i holding output row o = 16i + g of the tile, and the input slab is
+// staged as two planes (even and odd input offsets) whose row 8G + i holds
+// input position 2*p(16i) + 2(G - 1) + plane.  Tap k then reads plane k % 2 from
+// row group k / 2 on: 128 consecutive rows of 128 bytes (64 BF16 channels), a
+// canonical K-major operand with the 128-byte swizzle, every tap starting on
+// a 1024-byte swizzle-atom boundary.  The weights are five such N=64 x K=64
+// tiles, loaded once per CTA.
+//
+// Each persistent CTA (256 threads) loops over tiles: slabs stream in by
+// cp.async two tiles ahead (three buffers), the MMAs of tile j run while the
+// epilogue of tile j-1 (tcgen05.ld from the other TMEM accumulator, bias,
+// GELU, BF16 store) runs on all eight warps: warp w reads TMEM lanes
+// 32 (w % 4) .. +31 (the lanes its quarter of the CTA may access) and
+// columns 32 (w / 4) .. +31.  Completion waits on an mbarrier
+// give up after 2 s of %globaltimer: the kernel then ORs PCHASE_DEV_TIMEOUT
+// into *status, stops, waits for its own copies, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "conv_tc.cuh"
+
+namespace pchase {
+namespace {
+
+constexpr int kCh = 64;
+constexpr int kTaps = 5;
+constexpr int kTileRows = 128;
+constexpr int kGroups = 18;                           // 8-row groups per slab plane
+constexpr uint32_t kPlaneBytes = kGroups * 8 * 128;   // 18 KB
+constexpr uint32_t kSlabBytes = 2 * kPlaneBytes;      // 36 KB
+constexpr int kSlabs = 3;
+constexpr uint32_t kWBytes = kTaps * kCh * 128;       // 40 KB
+constexpr uint32_t kTmemCols = 128;                   // two 64-column accumulators
+constexpr uint32_t kSmemBytes = 1024 + kWBytes + kSlabs * kSlabBytes + 64;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// Instruction descriptor of tcgen05.mma .kind::f16: FP32 accumulator (bits
+// 4-5 = 1), BF16 A and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 =
+// 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                            ((uint32_t)(kTileRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
+// bytes in 8-row atoms of 1024 bytes (stride byte offset 1024), descriptor
+// version 1 (bits 46-47), layout type 2 = SWIZZLE_128B (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(16u >> 4) << 16) |
+           ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    const int n = valid ? 16 : 0;  // 0: zero-fill (padding, rows past the end)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+// tanh form of GELU (Hendrycks & Gimpel 2016) with the hardware tanh
+// (tanh.approx.f32, relative error about 2^-11, below the BF16 output's 2^-8)
+__device__ __forceinline__ float gelu_fast(float x) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(k0 * (x + k1 * x * x * x)));
+    return 0.5f * x * (1.0f + t);
+}
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_kernel(const __nv_bfloat16 *__restrict__ x, int nb, int lin,
+                   const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
+                   __nv_bfloat16 *__restrict__ out, float *__restrict__ pre,
+                   uint32_t *__restrict__ status) {
+    extern __shared__ uint8_t dsm[];
+    const uint32_t raw = smem_u32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
+    uint8_t *const gbase = dsm + (base - raw);
+    const uint32_t sW = base;
+    const uint32_t sSlab = base + kWBytes;
+    const uint32_t sBar = base + kWBytes + kSlabs * kSlabBytes;  // two mbarriers
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + kWBytes + kSlabs * kSlabBytes + 16);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lout = lin >> 1;
+    const int M = nb * lout;
+    const int ntiles = (M + kTileRows - 1) / kTileRows;
+
+    // weights: tap k is W[:, 64k .. 64k+63], 64 rows of 128 bytes, swizzled
+    for (int e = tid; e < kTaps * kCh * 8; e += kThreads) {
+        const int k = e >> 9, co = (e >> 3) & 63, c = e & 7;
+        cp_async16(sW + k * 8192 + co * 128 + ((c ^ (co & 7)) << 4),
+                   W + (size_t)co * (kTaps * kCh) + k * kCh + c * 8, true);
+    }
+    cp_async_commit();
+
+    auto load_slab = [&](int buf, int tile) {
+        if (tile < ntiles) {
+            const uint32_t slab = sSlab + buf * kSlabBytes;
+            const int m0 = tile * kTileRows;
+            for (int e = tid; e < 2 * kGroups * 8 * 8; e += kThreads) {
+                const int pl = e >= kGroups * 64 ? 1 : 0;
+                const int rem = e - pl * kGroups * 64;
+                const int R = rem >> 3, c = rem & 7;
+                const int G = R >> 3, i = R & 7;
+                const int mi = m0 + 16 * i;  // first of the 16 output rows of group i
+                const int b = mi / lout, p0 = mi - b * lout;
+                const int q = 2 * p0 + 2 * (G - 1) + pl;
+                const bool ok = mi < M && q >= 0 && q < lin;
+                const __nv_bfloat16 *src = ok ? x + ((size_t)b * lin + q) * kCh + c * 8 : x;
+                cp_async16(slab + pl * kPlaneBytes + R * 128 + ((c ^ i) << 4), src, ok);
+            }
+        }
+        cp_async_commit();  // one group per call, empty or not
+    };
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    load_slab(0, blockIdx.x);
+    load_slab(1, blockIdx.x + gridDim.x);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    // epilogue of the tile whose MMAs went to accumulator acc
+    auto epilogue = [&](int tile, int j) -> bool {
+        const int acc = j & 1;
+        const bool got = mbar_wait(sBar + 8 * acc, (uint32_t)(j >> 1) & 1u);
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
+            return false;
+        }
+        tc_fence_after();
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t taddr = tmem + (uint32_t)acc * 64u + (uint32_t)half * 32u +
+                               ((uint32_t)(quarter * 32) << 16);
+        uint32_t v[2][16];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) tmem_ld16(taddr + q * 16, v[q]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int r = quarter * 32 + lane;
+        const int m = tile * kTileRows + 16 * (r & 7) + (r >> 3);
+        if (m < M) {
+            float *pr = pre ? pre + (size_t)m * kCh + half * 32 : nullptr;
+            uint4 *o4 = reinterpret_cast<uint4 *>(out + (size_t)m * kCh + half * 32);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int e = 0; e < 16; e += 2) {
+                    const int n = half * 32 + q * 16 + e;
+                    const float a0 = __uint_as_float(v[q][e]) + __ldg(bias + n);
+                    const float a1 = __uint_as_float(v[q][e + 1]) + __ldg(bias + n + 1);
+                    if (pr) {
+                        pr[q * 16 + e] = a0;
+                        pr[q * 16 + e + 1] = a1;
+                    }
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(gelu_fast(a0), gelu_fast(a1));
+                    pk[e >> 1] = *reinterpret_cast<const uint32_t *>(&h);
+                }
+                o4[2 * q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                o4[2 * q + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+        tc_fence_before();
+        return true;
+    };
+
+    int j = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+        // slab j (and the weights) in shared memory, visible to the tensor cores
+        cp_async_wait1();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t d = tmem + (uint32_t)(j & 1) * 64u;
+            const uint32_t slab = sSlab + (uint32_t)(j % kSlabs) * kSlabBytes;
+#pragma unroll
+            for (int k = 0; k < kTaps; ++k) {
+                const uint32_t a0 = slab + (uint32_t)(k & 1) * kPlaneBytes + (uint32_t)(k >> 1) * 1024u;
+                const uint32_t b0 = sW + (uint32_t)k * 8192u;
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    mma_bf16(d, sw128_desc(a0 + 32u * s), sw128_desc(b0 + 32u * s),
+                             (k | s) != 0 ? 1u : 0u);
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    sBar + 8u * (uint32_t)(j & 1))
+                : "memory");
+        }
+        if (j > 0 && !epilogue(t - (int)gridDim.x, j - 1)) {
+            ok = false;
+            break;
+        }
+        // the buffer of tile j - 1 is free once its MMAs completed
+        load_slab((j + 2) % kSlabs, t + 2 * (int)gridDim.x);
+    }
+    if (ok && j > 0) epilogue(blockIdx.x + (j - 1) * (int)gridDim.x, j - 1);
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+}
+
+}  // namespace
+
+cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16 *W,
+                    const float *bias, __nv_bfloat16 *out, float *pre, uint32_t *status,
+                    int sms, cudaStream_t st) {
+    const int lout = lin / 2;
+    if (nb <= 0) return cudaSuccess;
+    if (lin % 2 || lout % 16 || !(lout >= kTileRows ? lout % kTileRows == 0 : kTileRows % lout == 0))
+        return cudaErrorInvalidValue;
+    if (!status) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = ((long long)nb * lout + kTileRows - 1) / kTileRows;
+    const int grid = (int)std::min<long long>(ntiles, std::max(1, sms));
+    conv_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, nb, lin, W, bias, out, pre, status);
+    return cudaGetLastError();
+}
+
+}  // namespace pchase

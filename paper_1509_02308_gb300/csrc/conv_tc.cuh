@@ -1,0 +1,22 @@
+// Tensor-core (tcgen05) convolution of the learned inverse (conv_tc.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "pchase.h"
+
+namespace pchase {
+
+// out[b][p][:] = GELU(bias + conv(x)[b][p][:]) for x [nb][lin][64] BF16 (row
+// of 64 channels per position), W [64][5*64] BF16 (column k*64 + ci), lout =
+// lin / 2 output positions; pre (may be NULL) receives the FP32 values before
+// GELU.  lout must be a multiple of 16 that divides 128 or is a multiple of
+// it.  A tensor-core completion wait that gives up ORs PCHASE_DEV_TIMEOUT into
+// *status (device).  Returns cudaErrorInvalidValue for unsupported shapes.
+cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16 *W,
+                    const float *bias, __nv_bfloat16 *out, float *pre, uint32_t *status,
+                    int sms, cudaStream_t st);
+
+}  // namespace pchase

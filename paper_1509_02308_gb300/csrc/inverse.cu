@@ -19,6 +19,7 @@
 
 #include <cuda_bf16.h>
 
+#include "conv_tc.cuh"
 #include "pchase_internal.cuh"
 
 namespace pchase {
@@ -583,6 +584,65 @@ __global__ void colsum_atomic_kernel(const float *x, int rows, int cols, int row
     atomicAdd(out + c, s);
 }
 
+// First convolution (1 input channel): out[b][p][co] = GELU(bias[co] +
+// sum_k W[co][k] * x[b][2p + k - 2]) with BF16 operands and FP32 sums, the
+// same products as the GEMM form.  One thread (grid-stride) per (trace,
+// position, group of 8 output channels), one 16-byte store; HBM-bound on the
+// 64-channel output.
+__global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restrict__ x, int nb,
+                                                    const __nv_bfloat16 *__restrict__ W,
+                                                    const float *__restrict__ bias,
+                                                    __nv_bfloat16 *__restrict__ out,
+                                                    float *__restrict__ pre) {
+    __shared__ float ws[kCh * kKer], bs[kCh];
+    for (int i = threadIdx.x; i < kCh * kKer; i += blockDim.x) ws[i] = __bfloat162float(W[i]);
+    for (int i = threadIdx.x; i < kCh; i += blockDim.x) bs[i] = bias[i];
+    __syncthreads();
+    constexpr int lout = kPoints / 2;
+    const size_t total = (size_t)nb * lout * 8;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(idx & 7);
+        const size_t bp = idx >> 3;
+        const int p = (int)(bp % lout);
+        const size_t b = bp / lout;
+        float xin[kKer];
+#pragma unroll
+        for (int k = 0; k < kKer; ++k) {
+            const int q = 2 * p + k - 2;
+            xin[k] = (q >= 0 && q < kPoints) ? __bfloat162float(x[b * kPoints + q]) : 0.0f;
+        }
+        uint32_t pk[4];
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int co = g * 8 + c + h;
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < kKer; ++k) acc = fmaf(ws[co * kKer + k], xin[k], acc);
+                v[h] = acc + bs[co];
+                if (pre) pre[bp * kCh + co] = v[h];
+            }
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_f(v[0]), gelu_f(v[1]));
+            pk[c >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
+        }
+        *reinterpret_cast<uint4 *>(out + bp * kCh + g * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+// acc (split-K sums, M x N FP32) += bias; out = BF16(GELU(acc)).
+__global__ void bias_gelu_kernel(float *acc, const float *bias, int M, int N,
+                                 __nv_bfloat16 *out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)M * N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float v = acc[i] + bias[i % N];
+        acc[i] = v;
+        out[i] = __float2bfloat16(gelu_f(v));
+    }
+}
+
 __global__ void f2b_kernel(const float *x, size_t n, __nv_bfloat16 *y) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
@@ -821,8 +881,8 @@ struct pchase_inverse {
     InverseLayout L;
     uint32_t max_batch;
     size_t p_w, p_wb, p_g, p_m, p_v, p_bytes;
-    size_t xb, cols[4], pre[4], act[4], pre4, h4, logits, dlog, dlogb, dh, dzf, dzb, dbig, dsmall,
-        work_bytes;
+    size_t status, xb, cols[4], pre[4], act[4], pre4, h4, logits, dlog, dlogb, dh, dzf, dzb, dbig,
+        dsmall, work_bytes;
 };
 
 namespace {
@@ -846,6 +906,13 @@ const T *at(const void *base, size_t off) {
     return reinterpret_cast<const T *>(static_cast<const uint8_t *>(base) + off);
 }
 
+int device_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n;
+}
+
 int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B, cudaStream_t st,
             bool train) {
     const InverseLayout &L = h->L;
@@ -854,6 +921,14 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
     const __nv_bfloat16 *in = at<__nv_bfloat16>(work, h->xb);
     for (int l = 0; l < 4; ++l) {
         const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
+        if (cin == kCh && !train) {
+            // inference: tcgen05 tensor cores, TMEM accumulators, implicit im2col
+            __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
+            INV_CUDA(conv_tc(in, (int)B, lin, wb + L.w[l], wf + L.b[l], o, nullptr,
+                             at<uint32_t>(work, h->status), device_sms(), st));
+            in = o;
+            continue;
+        }
         if (cin == kCh) {
             // implicit im2col; training also keeps the explicit columns for dW
             if (train) {
@@ -869,25 +944,23 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
             in = o;
             continue;
         }
-        __nv_bfloat16 *cols = at<__nv_bfloat16>(work, h->cols[l]);
-        const size_t nc = (size_t)B * lout * kKer * cin;
-        im2col_kernel<<<grid_for(nc), 256, 0, st>>>(in, (int)B, lin, cin, cols);
-        GemmArgs g{};
-        g.A = cols;
-        g.B = wb + L.w[l];
-        g.M = (int)(B * lout);
-        g.N = kCh;
-        g.K = kKer * cin;
-        g.lda = kKer * cin;
-        g.ldb = kKer * cin;
-        g.bias = wf + L.b[l];
-        g.pre = train ? at<float>(work, h->pre[l]) : nullptr;
-        g.Cb = at<__nv_bfloat16>(work, h->act[l]);
-        g.ldc = kCh;
-        g.gelu = 1;
-        INV_CUDA(gemm(false, false, g, st));
-        in = g.Cb;
+        // first layer (one input channel): direct; training keeps the
+        // explicit columns for its weight gradient
+        if (train) {
+            __nv_bfloat16 *cols = at<__nv_bfloat16>(work, h->cols[l]);
+            const size_t nc = (size_t)B * lout * kKer * cin;
+            im2col_kernel<<<grid_for(nc), 256, 0, st>>>(in, (int)B, lin, cin, cols);
+        }
+        __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
+        conv1_kernel<<<grid_for((size_t)B * lout * 8), 256, 0, st>>>(
+            in, (int)B, wb + L.w[l], wf + L.b[l], o, train ? at<float>(work, h->pre[l]) : nullptr);
+        INV_CUDA(cudaGetLastError());
+        in = o;
     }
+    // FC 2048 -> 256: split-K into FP32 sums (B x 256 is too few 128 x 128
+    // tiles to fill the GPU over K = 2048), then bias + GELU
+    float *acc4 = at<float>(work, h->pre4);
+    INV_CUDA(cudaMemsetAsync(acc4, 0, (size_t)B * kHidden * sizeof(float), st));
     GemmArgs f{};
     f.A = in;
     f.B = wb + L.w[4];
@@ -896,12 +969,14 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
     f.K = kFlat;
     f.lda = kFlat;
     f.ldb = kFlat;
-    f.bias = wf + L.b[4];
-    f.pre = train ? at<float>(work, h->pre4) : nullptr;
-    f.Cb = at<__nv_bfloat16>(work, h->h4);
+    f.Cf = acc4;
     f.ldc = kHidden;
-    f.gelu = 1;
+    f.splitk = 8;
     INV_CUDA(gemm(false, false, f, st));
+    bias_gelu_kernel<<<grid_for((size_t)B * kHidden), 256, 0, st>>>(
+        acc4, wf + L.b[4], (int)B, kHidden, at<__nv_bfloat16>(work, h->h4));
+    INV_CUDA(cudaGetLastError());
+    f.Cb = at<__nv_bfloat16>(work, h->h4);
     GemmArgs o{};
     o.A = f.Cb;
     o.B = wb + L.w[5];
@@ -940,6 +1015,7 @@ int pchase_inverse_create(uint32_t max_batch, pchase_inverse **out) {
     h->p_bytes = o;
     const size_t B = max_batch;
     o = 0;
+    h->status = o; o = a256(o + 4);
     h->xb = o; o = a256(o + 2 * B * kPoints);
     size_t big = B * kFlat;  // largest per-layer fp32 gradient
     for (int l = 0; l < 4; ++l) {
@@ -970,6 +1046,10 @@ void pchase_inverse_destroy(pchase_inverse *h) { delete h; }
 uint64_t pchase_inverse_param_count(const pchase_inverse *h) { return h ? h->L.n_params : 0; }
 size_t pchase_inverse_param_bytes(const pchase_inverse *h) { return h ? h->p_bytes : 0; }
 size_t pchase_inverse_work_bytes(const pchase_inverse *h) { return h ? h->work_bytes : 0; }
+size_t pchase_inverse_status_offset(const pchase_inverse *h) { return h ? h->status : 0; }
+size_t pchase_inverse_activation_offset(const pchase_inverse *h, uint32_t layer) {
+    return h && layer < 4 ? h->act[layer] : 0;
+}
 
 int pchase_inverse_init(const pchase_inverse *h, void *params, uint64_t seed,
                         pchase_stream_t stream) {
@@ -1018,6 +1098,7 @@ int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work,
     if (B == 0 || B > h->max_batch) return inv_fail(PCHASE_ERANGE, "batch above max_batch");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const InverseLayout &L = h->L;
+    INV_CUDA(cudaMemsetAsync(at<uint32_t>(work, h->status), 0, 4, st));
     f2b_kernel<<<grid_for((size_t)B * kPoints), 256, 0, st>>>(x, (size_t)B * kPoints,
                                                                at<__nv_bfloat16>(work, h->xb));
     int rc = forward(h, params, work, B, st, true);
@@ -1105,6 +1186,7 @@ int pchase_inverse_infer(const pchase_inverse *h, const void *params, void *work
     if (!h || !params || !work || !x || !pred_out || !conf_out)
         return inv_fail(PCHASE_EINVAL, "NULL argument");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    INV_CUDA(cudaMemsetAsync(at<uint32_t>(work, h->status), 0, 4, st));
     for (uint32_t b0 = 0; b0 < n; b0 += h->max_batch) {
         const uint32_t B = std::min(h->max_batch, n - b0);
         f2b_kernel<<<grid_for((size_t)B * kPoints), 256, 0, st>>>(

@@ -116,6 +116,24 @@ class LearnedInverse:
         off = self._p - C.ptr(self.params)
         return self.params[off:off + 4 * self.n_params].view(torch.float32)
 
+    def status(self) -> int:
+        """Device status word (PCHASE_DEV_* bits) of the last infer, classify
+        or train call; reading it synchronises with the device."""
+        off = (self._w - C.ptr(self.work)) + int(self.L.pchase_inverse_status_offset(self.h))
+        return int(self.work[off:off + 4].view(torch.int32).item())
+
+    def activations(self, B: int):
+        """Host copies of the four convolution outputs of the last forward
+        chunk (B traces): float32 [B, positions, 64] per layer."""
+        out = []
+        for l in range(4):
+            off = (self._w - C.ptr(self.work)) + int(
+                self.L.pchase_inverse_activation_offset(self.h, l))
+            n = B * (W.PLAN_POINTS >> (l + 1)) * 64
+            a = self.work[off:off + 2 * n].view(torch.bfloat16).float().cpu().numpy()
+            out.append(a.reshape(B, W.PLAN_POINTS >> (l + 1), 64))
+        return out
+
     def init(self, seed: int = 1):
         _check(self.L.pchase_inverse_init(self.h, self._p, seed, C.stream_handle()))
 

@@ -21,6 +21,7 @@ def test_forward_matches_oracle():
     rng = np.random.Generator(np.random.PCG64(5))
     x = rng.random((37, R.POINTS)).astype(np.float32)  # 37: ragged against the 128-row tiles
     pred, conf, lg = net.infer(torch.from_numpy(x).cuda(), want_logits=True)
+    assert net.status() == 0  # no tensor-core wait gave up
     w = net.weights().cpu().numpy().copy()
     want = R.forward(w, x, round_bf16=True)
     got = lg.cpu().numpy()
@@ -34,6 +35,53 @@ def test_forward_matches_oracle():
     _, _, lg2 = net.infer(torch.from_numpy(x2).cuda(), want_logits=True)
     want2 = R.forward(w, x2[130:], round_bf16=True)
     assert np.abs(lg2.cpu().numpy()[130:] - want2).max() <= 2e-2 * np.abs(want2).max() + 1e-3
+    assert net.status() == 0
+
+
+def test_tensor_core_convolution_matches_oracle_layer_by_layer():
+    """The tcgen05 convolution (inference path) against the oracle's
+    convolution on the same BF16 operands, for each 64-channel layer shape
+    (output positions 128, 64, 32: one, two and four traces per 128-row tile)
+    and a batch whose last tile is partial."""
+    net = INV.LearnedInverse(max_batch=48)
+    net.init(seed=21)
+    rng = np.random.Generator(np.random.PCG64(12))
+    x = rng.random((37, R.POINTS)).astype(np.float32)
+    _, _, lg = net.infer(torch.from_numpy(x).cuda(), want_logits=True)
+    assert net.status() == 0
+    w = net.weights().cpu().numpy().copy()
+    layers = R.unpack(w)
+    # replay the network layer by layer on the oracle, comparing the device's
+    # activations after every convolution (work buffer views)
+    acts = net.activations(37)
+    h = R.bf16(x).reshape(37, R.POINTS, 1)
+    for l in range(4):
+        Wl, bl = layers[l]
+        want = R.gelu(R.conv1d_s2(h, R.bf16(Wl), bl))
+        got = acts[l].astype(np.float64)
+        assert got.shape == want.shape, (l, got.shape, want.shape)
+        err = np.abs(got - want)
+        # BF16 output rounding (2^-8 relative) plus FP32 accumulation order
+        assert (err <= 8e-3 * np.abs(want) + 2e-3).all(), (l, float(err.max()))
+        h = R.bf16(got.astype(np.float32))
+
+
+def test_forward_large_batch_sampled_rows():
+    """A 3000-trace batch: every elementwise and GEMM launch of the forward
+    pass needs several grid-stride rounds or many tiles; sampled rows, the
+    last rows included, against the oracle."""
+    net = INV.LearnedInverse(max_batch=4096)
+    net.init(seed=13)
+    rng = np.random.Generator(np.random.PCG64(14))
+    x = rng.random((3000, R.POINTS)).astype(np.float32)
+    _, _, lg = net.infer(torch.from_numpy(x).cuda(), want_logits=True)
+    assert net.status() == 0
+    got = lg.cpu().numpy()
+    w = net.weights().cpu().numpy().copy()
+    rows = np.concatenate([rng.choice(2990, size=10, replace=False), np.arange(2990, 3000)])
+    want = R.forward(w, x[rows], round_bf16=True)
+    scale = np.abs(want).max()
+    assert np.abs(got[rows] - want).max() <= 2e-2 * scale + 1e-3, np.abs(got[rows] - want).max()
 
 
 def test_synth_matches_oracle():
