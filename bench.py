@@ -548,7 +548,7 @@ def learned_bench(args, dev):
     net.classify(x[:1024], l2c_t, rates, 0.9)
     INV.lsq_match(rates, x[:1024])
     out = {}
-    for thr in (0.5, 0.9):
+    for thr in (0.5, 0.7, 0.8, 0.9, 0.97):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cand, nf = net.classify(x, l2c_t, rates, thr)
@@ -565,19 +565,30 @@ def learned_bench(args, dev):
     net.infer(x)
     torch.cuda.synchronize()
     t_net = time.perf_counter() - t0
+    rep_exact, _, _ = INV.classes_from_rates(cands, rates, tol=0.0)
     res = {"candidates": len(cands), "classes": int(len(set(rep_of.tolist()))),
+           "class_tolerance": INV.CLASS_TOLERANCE,
+           "classes_identical_rows": int(len(set(rep_exact.tolist()))),
            "plan_points": 512, "rate_table_s": t_rates,
            "train_samples": args.inverse_steps * 4096, "train_s": t_train,
            "train_ms_per_step": t_train / max(1, args.inverse_steps) * 1e3,
            "loss_history": hist, "eval_traces": n,
            "judge_traces_per_s": n / t_lsq,
            "judge_accuracy_vs_truth": float((judge == rep_of[truth]).mean()),
+           "judge_accuracy_identical_rows": float(
+               (rep_exact[best.cpu().numpy()] == rep_exact[truth]).mean()),
            "network_only_traces_per_s": n / t_net}
+    pick = None
     for thr, (dt, cand, nf) in out.items():
+        acc = float((rep_of[cand] == rep_of[truth]).mean())
         res[f"thr{thr}"] = {"traces_per_s": n / dt, "fallback": nf,
                             "agreement_with_judge": float((rep_of[cand] == judge).mean()),
-                            "accuracy_vs_truth": float((rep_of[cand] == rep_of[truth]).mean()),
+                            "accuracy_vs_truth": acc,
                             "speedup_vs_judge": (n / dt) / (n / t_lsq)}
+        if acc >= 0.99 and (pick is None or n / dt > res[f"thr{pick}"]["traces_per_s"]):
+            pick = thr
+    res["at_99pct"] = ({"threshold": pick, **res[f"thr{pick}"]} if pick is not None
+                       else {"threshold": None, "note": "no threshold reached 99 % accuracy"})
     return res
 
 

@@ -164,21 +164,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     cp_async_commit();
 
+    // slab loader: thread (plane, i, c, half) copies 16-byte chunk c of rows
+    // 8G + i, G in its half of 0..17: nine copies two input positions apart
+    const int ld_c = tid & 7, ld_i = (tid >> 3) & 7, ld_pl = (tid >> 6) & 1, ld_h = tid >> 7;
+    const int ld_g0 = ld_h * (kGroups / 2);
     auto load_slab = [&](int buf, int tile) {
         if (tile < ntiles) {
-            const uint32_t slab = sSlab + buf * kSlabBytes;
-            const int m0 = tile * kTileRows;
-            for (int e = tid; e < 2 * kGroups * 8 * 8; e += kThreads) {
-                const int pl = e >= kGroups * 64 ? 1 : 0;
-                const int rem = e - pl * kGroups * 64;
-                const int R = rem >> 3, c = rem & 7;
-                const int G = R >> 3, i = R & 7;
-                const int mi = m0 + 16 * i;  // first of the 16 output rows of group i
-                const int b = mi / lout, p0 = mi - b * lout;
-                const int q = 2 * p0 + 2 * (G - 1) + pl;
-                const bool ok = mi < M && q >= 0 && q < lin;
-                const __nv_bfloat16 *src = ok ? x + ((size_t)b * lin + q) * kCh + c * 8 : x;
-                cp_async16(slab + pl * kPlaneBytes + R * 128 + ((c ^ i) << 4), src, ok);
+            const int mi = tile * kTileRows + 16 * ld_i;  // first of the 16 output rows of group i
+            const int b = mi / lout, p0 = mi - b * lout;
+            const bool row_ok = mi < M;
+            const int q0 = 2 * p0 + 2 * (ld_g0 - 1) + ld_pl;
+            const __nv_bfloat16 *src = x + ((size_t)(row_ok ? b : 0) * lin) * kCh + ld_c * 8;
+            const uint32_t dst = sSlab + buf * kSlabBytes + ld_pl * kPlaneBytes +
+                                 (8 * ld_g0 + ld_i) * 128 + ((ld_c ^ ld_i) << 4);
+#pragma unroll
+            for (int gg = 0; gg < kGroups / 2; ++gg) {
+                const int q = q0 + 2 * gg;
+                const bool ok = row_ok && q >= 0 && q < lin;
+                cp_async16(dst + gg * 1024, ok ? src + (size_t)q * kCh : x, ok);
             }
         }
         cp_async_commit();  // one group per call, empty or not

@@ -55,6 +55,16 @@ __device__ __forceinline__ float gelu_f(float x) {
     return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
 }
 
+// GELU with the hardware tanh (tanh.approx.f32, relative error about 2^-11,
+// below the BF16 rounding of every activation): inference only, so training's
+// forward and backward keep the same tanhf.
+__device__ __forceinline__ float gelu_fast(float x) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(k0 * (x + k1 * x * x * x)));
+    return 0.5f * x * (1.0f + t);
+}
+
 __device__ __forceinline__ float gelu_grad(float x) {
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
     const float u = k0 * (x + k1 * x * x * x);
@@ -594,15 +604,19 @@ __global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restr
                                                     const float *__restrict__ bias,
                                                     __nv_bfloat16 *__restrict__ out,
                                                     float *__restrict__ pre) {
-    __shared__ float ws[kCh * kKer], bs[kCh];
-    for (int i = threadIdx.x; i < kCh * kKer; i += blockDim.x) ws[i] = __bfloat162float(W[i]);
-    for (int i = threadIdx.x; i < kCh; i += blockDim.x) bs[i] = bias[i];
-    __syncthreads();
     constexpr int lout = kPoints / 2;
     const size_t total = (size_t)nb * lout * 8;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int g = (int)(idx & 7);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;  // a multiple of 8: g stays fixed
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = (int)(idx & 7);
+    float w[8][kKer], bs[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        bs[c] = bias[g * 8 + c];
+#pragma unroll
+        for (int k = 0; k < kKer; ++k) w[c][k] = __bfloat162float(W[(g * 8 + c) * kKer + k]);
+    }
+    for (; idx < total; idx += stride) {
         const size_t bp = idx >> 3;
         const int p = (int)(bp % lout);
         const size_t b = bp / lout;
@@ -618,14 +632,15 @@ __global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restr
             float v[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int co = g * 8 + c + h;
                 float acc = 0.0f;
 #pragma unroll
-                for (int k = 0; k < kKer; ++k) acc = fmaf(ws[co * kKer + k], xin[k], acc);
-                v[h] = acc + bs[co];
-                if (pre) pre[bp * kCh + co] = v[h];
+                for (int k = 0; k < kKer; ++k) acc = fmaf(w[c + h][k], xin[k], acc);
+                v[h] = acc + bs[c + h];
+                if (pre) pre[bp * kCh + g * 8 + c + h] = v[h];
             }
-            const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_f(v[0]), gelu_f(v[1]));
+            const __nv_bfloat162 hv =
+                pre ? __floats2bfloat162_rn(gelu_f(v[0]), gelu_f(v[1]))
+                    : __floats2bfloat162_rn(gelu_fast(v[0]), gelu_fast(v[1]));
             pk[c >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
         }
         *reinterpret_cast<uint4 *>(out + bp * kCh + g * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);

@@ -4,7 +4,6 @@ network, the least-squares matcher) runs in the CUDA library."""
 from __future__ import annotations
 
 import ctypes
-import hashlib
 
 import numpy as np
 import torch
@@ -66,21 +65,36 @@ def rate_table(cands, tune=None):
     return rates, counts.view(len(cands), len(pts), 2)
 
 
-def classes_from_rates(cands, rates: torch.Tensor):
-    """Candidates with identical rate rows form one class; returns per
-    candidate its class id and its class representative (the first member in
-    canonical order), the targets (labels of the representative) and the
+# Two geometries whose miss rates differ by at most this much at every plan
+# point are one answer class: under the timing noise of the synthetic traces
+# (2 % jitter) no matcher separates them.
+CLASS_TOLERANCE = 0.01
+
+
+def classes_from_rates(cands, rates: torch.Tensor, tol: float = CLASS_TOLERANCE):
+    """Answer classes of the candidates under the plan: single-linkage groups
+    of rate rows within `tol` of each other at every point (tol = 0: identical
+    rows).  Returns per candidate its class representative (the first member
+    in canonical order), the targets (labels of the representative) and the
     label -> candidate table."""
-    r = rates.cpu().numpy()
-    rep = {}
-    rep_of = np.zeros(len(cands), dtype=np.int64)
-    for i in range(len(cands)):
-        h = hashlib.sha1(r[i].tobytes()).hexdigest()
-        if h not in rep:
-            rep[h] = i
-        rep_of[i] = rep[h]
-    targets = np.array([W.geometry_label(cands[rep_of[i]]) for i in range(len(cands))],
-                       dtype=np.uint32)
+    r = rates.cpu().numpy().astype(np.float64)
+    n = len(cands)
+    parent = np.arange(n)
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for i in range(n):
+        close = np.nonzero(np.abs(r[i + 1:] - r[i]).max(axis=1) <= tol)[0] + i + 1
+        for j in close:
+            a, b = find(i), find(int(j))
+            if a != b:
+                parent[max(a, b)] = min(a, b)  # the lower index (canonical order) leads
+    rep_of = np.array([find(i) for i in range(n)], dtype=np.int64)
+    targets = np.array([W.geometry_label(cands[rep_of[i]]) for i in range(n)], dtype=np.uint32)
     l2c = np.full(N_LABELS, 0xFFFFFFFF, dtype=np.uint32)
     for i, g in enumerate(cands):
         c, b, w, p = W.geometry_label(g)
