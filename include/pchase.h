@@ -282,8 +282,10 @@ size_t pchase_classify_noalloc_limit_bytes(void);
  * Hamming distance summed over the candidate's traces goes to dist_out[g]
  * (device uint64, zeroed by the call).  `plan` must have been created with
  * pairs == NULL over (candidates x plan traces); `stop_above`: an item stops
- * once its own distance exceeds it (UINT64_MAX: never), which keeps exact
- * answers for every candidate whose distance stays <= stop_above.
+ * once its candidate's distance (the other items' sums so far plus its own)
+ * exceeds it, and an item of a candidate already above it is skipped
+ * (UINT64_MAX: never).  Every candidate whose distance is <= stop_above gets
+ * its exact distance; any other gets some value above stop_above.
  */
 int pchase_match_run(const pchase_sim_plan *plan, void *workspace, const uint32_t *observed,
                      const uint64_t *obs_word_offsets, uint64_t stop_above, uint64_t *dist_out,

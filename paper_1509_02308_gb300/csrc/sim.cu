@@ -788,6 +788,19 @@ __device__ __forceinline__ void clear_state(uint32_t kind, uint8_t *st, const Si
     }
 }
 
+// Matcher: true when the candidate's distance, summed atomically by its other
+// units, plus this unit's own part is already above the bound.  Distances at
+// or under the bound are never cut short, so they stay exact; one above it is
+// only known to be above it.
+__device__ __forceinline__ bool over_bound(const SimOut &out, uint32_t cand, uint64_t own,
+                                           int lane) {
+    if (out.stop_above == ~0ull) return false;
+    unsigned long long d = 0;
+    if (lane == 0) d = *reinterpret_cast<volatile const unsigned long long *>(out.dist + cand);
+    d = __shfl_sync(kFull, d, 0);
+    return d + own > out.stop_above;
+}
+
 // One unit: gather trips fill the queue with the unit's run heads, and each
 // step hands the next 32 of them to the unit's set state in trace order.
 __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, const SimOut &out,
@@ -796,6 +809,8 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     uint2 *const queue = reinterpret_cast<uint2 *>(g_smem + arena);
     uint8_t *const st = g_smem + arena + (it.direct ? 0u : kStageBytes);
     const uint32_t kind = (uint32_t)it.mode * 3u + it.policy;
+    // matcher: a candidate whose other units already exceed the bound is out
+    if (out.dist && over_bound(out, it.cand, 0, lane)) return;
     clear_state(kind, st, it, lane);
     __syncwarp();
     const uint32_t len = it.len;
@@ -832,6 +847,8 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
         const uint32_t nsteps = (len + 31) >> 5;
         uint32_t carry = kInvalidLine, myword = 0;
         uint32_t pf = (idxp && (uint32_t)lane < len) ? idxp[lane] : 0u;
+        // matcher: the observed word of the step, loaded one step ahead
+        uint32_t pw = (ham && len) ? observed[obase] : 0u;
         for (uint32_t s0 = 0; s0 < nsteps; ++s0) {
             const uint32_t t = (s0 << 5) + (uint32_t)lane;
             bool active = t < len;
@@ -861,20 +878,22 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
                                  : (warmup - base >= 32 ? 0u : ~((1u << (warmup - base)) - 1u));
             tot += __popc(bits);
             aft += __popc(bits & after);
+            if (ham) {
+                // every step: its 32 outcomes against the observed word
+                const uint32_t ow = pw;
+                pw = s0 + 1 < nsteps ? observed[obase + s0 + 1] : 0u;
+                const uint32_t valid = len - base >= 32 ? kFull : ((1u << (len - base)) - 1u);
+                dsum += __popc((bits ^ ow) & valid);
+                if (dsum > stop_above) break;
+                if ((s0 & 31) == 31 && over_bound(out, it.cand, dsum, lane)) break;
+                continue;
+            }
             const uint32_t slot = s0 & 31;
             if ((uint32_t)lane == slot) myword = bits;
             if (slot == 31 || s0 + 1 == nsteps) {
                 const uint32_t w0 = s0 & ~31u;
-                uint32_t dl = 0;
-                if ((uint32_t)lane <= slot) {
-                    if (ham) dl = __popc(observed[obase + w0 + lane] ^ myword);
-                    else if (bm) bm[w0 + lane] = myword;
-                }
+                if ((uint32_t)lane <= slot && bm) bm[w0 + lane] = myword;
                 myword = 0;
-                if (ham) {
-                    dsum += __reduce_add_sync(kFull, dl);
-                    if (dsum > stop_above) break;
-                }
             }
         }
     } else {
@@ -973,6 +992,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             if (ham) {
                 dsum += __popc(__ballot_sync(kFull, act && miss != ((e.y >> 31) != 0)));
                 if (dsum > stop_above) break;
+                if ((step & 31) == 0 && over_bound(out, it.cand, dsum, lane)) break;
             } else if (bm && bits) {
                 emit_bits(bm, pos, miss, act, lane);
             }
