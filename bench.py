@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=512, help="items in the oracle sample")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner (default knobs)")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-inverse section")
+    p.add_argument("--no-probes", action="store_true", help="skip the on-device probe section")
     p.add_argument("--inverse-steps", type=int, default=600,
                    help="training steps of 4096 synthetic traces for the learned inverse")
     p.add_argument("--inverse-eval", type=int, default=100000)
@@ -373,6 +374,11 @@ def ours(args):
         except Exception as ex:  # reported, never hidden
             result["inference"] = {"error": repr(ex)}
 
+    if not args.no_probes and rank == 0:
+        try:
+            result["probes"] = probe_bench(dev)
+        except Exception as ex:  # report, never mask the main number
+            result["probes"] = {"error": repr(ex)}
     if not args.no_learned and rank == 0:
         try:
             result["learned_inverse"] = learned_bench(args, dev)
@@ -506,13 +512,87 @@ def infer_bench(dev):
     exact = sum(1 for p in full_picks if p == truth_idx) / n_obs
     exact_fast = sum(1 for p in fast_picks if p == truth_idx) / n_obs
     sim_acc = len(cands) * int(offs[-1])
+    # batched: many observations per call, each with its own noise
+    n_batch = 256
+    lat_b = torch.from_numpy(np.stack([
+        ((100.0 + 300.0 * miss) * (1.0 + 0.02 * rng.standard_normal(miss.size))).astype(np.float32)
+        for _ in range(n_batch)])).to(dev)
+    batch = {}
+    for stop, name in ((2**64 - 1, "unbounded"), (0, "stop0")):
+        api.infer_batch(plan, lat_b[:8], stop_above=stop)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, pk = api.infer_batch(plan, lat_b, stop_above=stop)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        pk = pk.cpu().numpy()
+        batch[name] = {"traces_inferred_per_s": n_batch / dt,
+                       "exact_recovery": float((pk[:, 0] == truth_idx).mean()),
+                       "observations_per_call": n_batch}
     return {"traces_inferred_per_s": 1.0 / full_dt, "exact_recovery": exact,
             "traces_inferred_per_s_stop0": 1.0 / fast_dt, "exact_recovery_stop0": exact_fast,
+            "batched": batch,
             "candidates": len(cands), "plan_traces": len(runs), "plan_accesses": int(offs[-1]),
             "simulated_accesses_per_inference": sim_acc,
             "matcher_accesses_per_s": sim_acc / full_dt,
             "note": "one observation = latencies of all plan traces (2% jitter); stop0 = "
-                    "distance bound 0, exact whenever a candidate matches perfectly"}
+                    "distance bound 0, exact whenever a candidate matches perfectly; batched = "
+                    "infer_geometry_batch over 256 observations per call"}
+
+
+def probe_bench(dev):
+    """The sm_103a probes on this GPU (S8-S10): P-chase latency plateaus,
+    the shared-memory bank sweep, and global read/write/copy throughput over
+    1 GB against the measured HBM copy bandwidth, swept over CTAs per SM and
+    loads in flight per thread."""
+    import math
+
+    import torch
+
+    from paper_1509_02308_gb300 import api
+
+    out = {}
+    # latency regimes (medians of 2048 timed accesses, cycles, overhead removed)
+    lat = {}
+    for name, nbytes, sb, mode in (("l1_16KB_s128B", 16 << 10, 128, 0),
+                                   ("l2_4MB_s128B", 4 << 20, 128, 1),
+                                   ("hbm_512MB_s4KB", 512 << 20, 4096, 1)):
+        n = nbytes // 4
+        _, arr = api.pchase_build(n, sb // 4, 1, with_array=True)
+        l, _, _, st = api.pchase_probe_latency(arr, n, iters=2048, warmup=n // (sb // 4) if
+                                               nbytes <= (4 << 20) else 0, cache_mode=mode)
+        torch.cuda.synchronize()
+        lat[name] = float(np.median(l.cpu().numpy().view(np.uint32)))
+        del arr
+    out["latency_cycles"] = lat
+    cyc, deg = api.pchase_probe_smem_bank(64, repeats=9)
+    cyc, deg = cyc.cpu().numpy(), deg.cpu().numpy()
+    out["smem_bank"] = {"cycles_by_degree": {int(d): float(np.median(cyc[deg == d]))
+                                             for d in (1, 2, 4, 8, 16, 32)},
+                        "degree_is_gcd_s_32": bool(all(deg[s - 1] == math.gcd(s, 32)
+                                                       for s in range(1, 65)))}
+    nbytes = 1 << 30
+    a = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    b = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, peak_kind = measured_peaks()
+    thr = {}
+    for kind, name in ((0, "read"), (1, "write"), (2, "copy")):
+        best, cfg = 0.0, None
+        for per_sm in (2, 4, 8):
+            for ilp in (1, 2, 4, 8):
+                g = api.pchase_probe_global_throughput(kind, 16, sms * per_sm, 256, ilp, a, b,
+                                                       nbytes, reps=5)
+                if g > best:
+                    best, cfg = g, {"ctas_per_sm": per_sm, "threads": 256, "ilp": ilp,
+                                    "vector_bytes": 16}
+        thr[name] = {"gbs": best, "frac_of_measured": best / peaks["hbm_gbs"],
+                     "frac_of_nominal_8TBs": best / 8000.0, "best_config": cfg}
+    out["global_throughput_1GB"] = thr
+    out["peak_kind"] = f"{peak_kind} HBM copy bandwidth {peaks['hbm_gbs']} GB/s"
+    del a, b
+    torch.cuda.empty_cache()
+    return out
 
 
 def learned_bench(args, dev):

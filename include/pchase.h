@@ -318,6 +318,22 @@ int infer_geometry(const pchase_sim_plan *plan, void *workspace, const float *la
                    void *scratch, uint64_t stop_above, uint64_t *dist_out, uint32_t *pick_out,
                    uint32_t *dev_status, pchase_stream_t stream);
 
+/*
+ * infer_geometry over n_obs observations in one call (batched inference):
+ * lat (device) holds n_obs observations back to back, each the plan's
+ * traces' latencies in trace order (total length L = sum of trace lengths).
+ * Every observation gets its own pooled threshold (R9), its own distances
+ * dist_out[o * n_candidates + g] and its own canonical pick
+ * pick_out[2o], pick_out[2o + 1].  The candidates' items run once per
+ * observation inside the same launches.  Scratch (device, 256-byte aligned):
+ * pchase_infer_batch_scratch_bytes(plan, n_obs).  Errors: EINVAL as
+ * infer_geometry; ERANGE when n_obs > 1024 or n_obs x plan traces > 65535.
+ */
+size_t pchase_infer_batch_scratch_bytes(const pchase_sim_plan *plan, uint32_t n_obs);
+int infer_geometry_batch(const pchase_sim_plan *plan, void *workspace, const float *lat,
+                         uint32_t n_obs, void *scratch, uint64_t stop_above, uint64_t *dist_out,
+                         uint32_t *pick_out, uint32_t *dev_status, pchase_stream_t stream);
+
 /* --------------------------------------------------------------- S8-S10 */
 
 /*

@@ -148,6 +148,23 @@ class SimPlan:
         return dist, pick
 
 
+def infer_batch(plan: "SimPlan", lats: torch.Tensor, stop_above: int = 2**64 - 1, status=None,
+                stream=None):
+    """Batched inference: lats [n_obs, L] FP32 (each row one observation of
+    every plan trace) -> (dist [n_obs, n_candidates], pick [n_obs, 2])."""
+    L = plan.L
+    n_obs = int(lats.shape[0])
+    scratch_b = int(L.pchase_infer_batch_scratch_bytes(plan.h, n_obs))
+    scratch = torch.empty(scratch_b + 256, dtype=torch.uint8, device=DEV)
+    sp = (C.ptr(scratch) + 255) & ~255
+    dist = torch.empty(n_obs, max(1, len(plan.geoms)), dtype=torch.int64, device=DEV)
+    pick = torch.empty(n_obs, 2, dtype=torch.int32, device=DEV)
+    C.check(L.infer_geometry_batch(plan.h, plan._ws, C.ptr(lats), n_obs, sp, stop_above,
+                                   C.ptr(dist), C.ptr(pick), C.ptr(status),
+                                   C.stream_handle(stream)))
+    return dist, pick
+
+
 def cache_sim_batch(geoms: list[Geom], traces, pairs=None, stream=None):
     """One-shot simulation: (bitmaps int32 tensor, counts int64 [items, 2],
     word offsets numpy)."""

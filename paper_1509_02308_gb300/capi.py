@@ -70,6 +70,9 @@ SIGNATURES = {
     "pchase_canonical_pick": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_p, _c_p]),
     "pchase_infer_scratch_bytes": (ctypes.c_size_t, [_c_p]),
     "infer_geometry": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_u64, _c_p, _c_p, _c_p, _c_p]),
+    "pchase_infer_batch_scratch_bytes": (ctypes.c_size_t, [_c_p, _c_u32]),
+    "infer_geometry_batch": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_u32, _c_p, _c_u64, _c_p, _c_p,
+                                            _c_p, _c_p]),
     "pchase_probe_latency": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.c_int,
                                             _c_p, _c_p, _c_p, _c_p, _c_p]),
     "pchase_probe_smem_bank": (ctypes.c_int, [_c_u32, _c_u32, _c_p, _c_p, _c_p]),

@@ -25,7 +25,10 @@ cudaError_t classify_bits(const float *lat, const uint64_t *seg_offsets, int per
                           uint32_t n_seg, uint64_t max_seg_len, const void *meta_mem,
                           uint32_t *bits, const uint64_t *word_offsets, cudaStream_t st, int sms);
 cudaError_t canonical_pick(const pchase_geom *geoms, const uint64_t *dist, uint32_t n,
-                           uint32_t *pick, cudaStream_t st);
+                           uint32_t *pick, cudaStream_t st, uint32_t n_obs = 1);
+cudaError_t batch_offsets(const uint64_t *seg, const uint64_t *owo, uint32_t T, uint32_t n_obs,
+                          uint64_t L, uint64_t obs_words, uint64_t *obs_off, uint64_t *seg_out,
+                          uint64_t *wo_out, cudaStream_t st);
 cudaError_t probe_latency(const uint32_t *A, uint32_t n, uint32_t start, uint32_t warmup,
                           uint32_t iters, int mode, uint32_t *lat, uint32_t *idx, uint32_t *ovh,
                           uint32_t *status, cudaStream_t st);
@@ -77,6 +80,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 constexpr uint32_t kMaxLines = 65535;
+constexpr uint32_t kMaxBatchObs = 1024;  // observations per infer_geometry_batch call
 constexpr uint32_t kMaxArena = 232448;  // 227 KB, one warp per CTA
 // size classes of unit arenas (bytes; queued units add their queue and staging ring)
 const uint32_t kCaps[] = {1024,  2560,  3072,  4096,   5120,   6144,   8192,   10240,  12288,
@@ -902,6 +906,69 @@ int infer_geometry(const pchase_sim_plan *plan, void *workspace, const float *la
     if (rc) return rc;
     PCHASE_CUDA(canonical_pick(reinterpret_cast<const pchase_geom *>(w + plan->off_geoms), dist_out,
                                plan->n_geom, pick_out, st),
+                "canonical pick");
+    return PCHASE_OK;
+}
+
+size_t pchase_infer_batch_scratch_bytes(const pchase_sim_plan *plan, uint32_t n_obs) {
+    if (!plan || n_obs == 0) return 0;
+    const uint64_t T = plan->n_trace;
+    return classify_meta_bytes(n_obs) + align256(classify_bucket_bytes(n_obs, plan->total_len)) +
+           align256((n_obs + 1ull) * 8) + align256((n_obs * T + 1) * 8) +
+           align256(n_obs * T * 8) + align256(n_obs * plan->obs_words * 4 + 4);
+}
+
+int infer_geometry_batch(const pchase_sim_plan *plan, void *workspace, const float *lat,
+                         uint32_t n_obs, void *scratch, uint64_t stop_above, uint64_t *dist_out,
+                         uint32_t *pick_out, uint32_t *dev_status, pchase_stream_t stream) {
+    if (!plan || !workspace || !lat || !scratch || !dist_out || !pick_out)
+        return fail(PCHASE_EINVAL, "infer_geometry_batch: NULL argument");
+    if (!plan->cross) return fail(PCHASE_EINVAL, "infer_geometry_batch needs a candidates x traces plan");
+    if (n_obs == 0) return PCHASE_OK;
+    if ((uint64_t)n_obs * plan->n_trace > 65535 || n_obs > kMaxBatchObs)
+        return fail(PCHASE_ERANGE, "infer_geometry_batch: too many observations for one call");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *w = static_cast<uint8_t *>(workspace);
+    uint8_t *s = static_cast<uint8_t *>(scratch);
+    const uint64_t T = plan->n_trace, L = plan->total_len;
+    size_t off = 0;
+    void *meta = s;
+    off += classify_meta_bytes(n_obs);
+    void *bk = s + off;
+    off += align256(classify_bucket_bytes(n_obs, L));
+    uint64_t *obs_off = reinterpret_cast<uint64_t *>(s + off);
+    off += align256((n_obs + 1ull) * 8);
+    uint64_t *seg_b = reinterpret_cast<uint64_t *>(s + off);
+    off += align256((n_obs * T + 1) * 8);
+    uint64_t *wo_b = reinterpret_cast<uint64_t *>(s + off);
+    off += align256(n_obs * T * 8);
+    uint32_t *bits = reinterpret_cast<uint32_t *>(s + off);
+    const uint64_t *seg = reinterpret_cast<const uint64_t *>(w + plan->off_seg);
+    const uint64_t *owo = reinterpret_cast<const uint64_t *>(w + plan->off_obs_words);
+    const int sms = sm_count();
+    PCHASE_CUDA(batch_offsets(seg, owo, (uint32_t)T, n_obs, L, plan->obs_words, obs_off, seg_b,
+                              wo_b, st),
+                "batch offsets");
+    PCHASE_CUDA(classify_thresholds(lat, obs_off, n_obs, L, meta, bk, nullptr, st, sms),
+                "classify thresholds");
+    PCHASE_CUDA(classify_bits(lat, seg_b, (int)T, n_obs * (uint32_t)T, plan->max_trace_len, meta,
+                              bits, wo_b, st, sms),
+                "classify bits");
+    PCHASE_CUDA(cudaMemsetAsync(dist_out, 0, (size_t)n_obs * plan->n_geom * sizeof(uint64_t), st),
+                "cudaMemsetAsync(dist)");
+    SimOut out{};
+    out.status = dev_status;
+    out.observed = bits;
+    out.obs_word_offsets = owo;
+    out.stop_above = stop_above;
+    out.dist = dist_out;
+    out.n_rep = n_obs;
+    out.rep_dist_stride = plan->n_geom;
+    out.rep_obs_stride = plan->obs_words;
+    int rc = plan_launch(const_cast<pchase_sim_plan *>(plan), workspace, out, st);
+    if (rc) return rc;
+    PCHASE_CUDA(canonical_pick(reinterpret_cast<const pchase_geom *>(w + plan->off_geoms), dist_out,
+                               plan->n_geom, pick_out, st, n_obs),
                 "canonical pick");
     return PCHASE_OK;
 }

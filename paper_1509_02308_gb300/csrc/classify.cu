@@ -18,6 +18,8 @@
 //      writes the miss bits with __ballot_sync.
 #include <mutex>
 
+#include <algorithm>
+
 #include "pchase_internal.cuh"
 
 namespace pchase {
@@ -67,10 +69,19 @@ __global__ void __launch_bounds__(1024) select_cut_kernel(const float *lat,
         __syncthreads();
         const uint32_t prefix = s_prefix, mask = s_mask;
         uint32_t mn = 0xFFFFFFFFu;
-        for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t k = fkey(x[i]);
-            if (pass == 0) mn = min(mn, k);
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        // latencies crowd into a few digits, so lanes with the same digit add
+        // their count with one atomic (warp-aggregated)
+        for (uint64_t i0 = 0; i0 < n; i0 += blockDim.x) {
+            const uint64_t i = i0 + threadIdx.x;
+            uint32_t d = 0xFFFFFFFFu;
+            if (i < n) {
+                const uint32_t k = fkey(x[i]);
+                if (pass == 0) mn = min(mn, k);
+                if ((k & mask) == prefix) d = (k >> shift) & 255u;
+            }
+            const uint32_t peers = __match_any_sync(kFull, d);
+            if (d != 0xFFFFFFFFu && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0)
+                atomicAdd(&hist[d], (uint32_t)__popc(peers));
         }
         if (pass == 0) {
             mn = __reduce_min_sync(kFull, mn);
@@ -178,13 +189,14 @@ __global__ void __launch_bounds__(1024) gap_kernel(uint64_t max_len, ObsMeta *me
     }
 }
 
-// Miss bits of segment s against the threshold of observation s (per_seg)
+// Miss bits of segment s against the threshold of observation s / per_seg
+// (per_seg segments per observation; 0: one pooled threshold)
 // or of observation 0 (every segment pooled into one observation).
 __global__ void bits_kernel(const float *lat, const uint64_t *seg_offsets, int per_seg,
                             uint32_t n_seg, const ObsMeta *meta, uint32_t *bits,
                             const uint64_t *word_offsets) {
     const uint32_t s = blockIdx.y;
-    const float thr = meta[per_seg ? s : 0].thr;
+    const float thr = meta[per_seg ? s / (uint32_t)per_seg : 0].thr;
     const uint64_t b0 = seg_offsets[s], n = seg_offsets[s + 1] - b0;
     const uint64_t words = (n + 31) / 32;
     const uint64_t wo = word_offsets[s];
@@ -213,6 +225,9 @@ __device__ __forceinline__ bool better(const pchase_geom *g, const uint64_t *d, 
 
 __global__ void __launch_bounds__(1024) pick_kernel(const pchase_geom *geoms, const uint64_t *dist,
                                                     uint32_t n, uint32_t *pick) {
+    // block o picks for observation o: distances dist + o * n
+    dist += (size_t)blockIdx.x * n;
+    pick += 2ull * blockIdx.x;
     __shared__ uint32_t best[1024];
     __shared__ uint32_t count;
     uint32_t b = 0xFFFFFFFFu;
@@ -280,8 +295,37 @@ cudaError_t classify_bits(const float *lat, const uint64_t *seg_offsets, int per
 }
 
 cudaError_t canonical_pick(const pchase_geom *geoms, const uint64_t *dist, uint32_t n,
-                           uint32_t *pick, cudaStream_t st) {
-    pick_kernel<<<1, 1024, 0, st>>>(geoms, dist, n, pick);
+                           uint32_t *pick, cudaStream_t st, uint32_t n_obs) {
+    pick_kernel<<<n_obs ? n_obs : 1, 1024, 0, st>>>(geoms, dist, n, pick);
+    return cudaGetLastError();
+}
+
+// Segment and word offsets of n_obs observations laid out back to back, each
+// L latencies in plan-trace order (T traces, seg[T + 1], owo[T]).
+__global__ void batch_offsets_kernel(const uint64_t *seg, const uint64_t *owo, uint32_t T,
+                                     uint32_t n_obs, uint64_t L, uint64_t obs_words,
+                                     uint64_t *obs_off, uint64_t *seg_out, uint64_t *wo_out) {
+    const uint64_t n = (uint64_t)n_obs * T;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t o = i / T, t = i % T;
+        if (i == n) {
+            seg_out[n] = n_obs * L;
+        } else {
+            seg_out[i] = o * L + seg[t];
+            wo_out[i] = o * obs_words + owo[t];
+        }
+        if (i <= n_obs) obs_off[i] = i * L;
+    }
+}
+
+cudaError_t batch_offsets(const uint64_t *seg, const uint64_t *owo, uint32_t T, uint32_t n_obs,
+                          uint64_t L, uint64_t obs_words, uint64_t *obs_off, uint64_t *seg_out,
+                          uint64_t *wo_out, cudaStream_t st) {
+    const uint64_t n = (uint64_t)n_obs * T + 1;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((n + 255) / 256, 1024);
+    batch_offsets_kernel<<<blocks, 256, 0, st>>>(seg, owo, T, n_obs, L, obs_words, obs_off,
+                                                 seg_out, wo_out);
     return cudaGetLastError();
 }
 

@@ -143,6 +143,12 @@ struct SimOut {
     uint64_t *dist;
     // optional per-item timeline (4 uint64 per item)
     uint64_t *timeline;
+    // matcher over several observations: every unit runs once per
+    // observation r < n_rep (0 = 1), with dist + r * rep_dist_stride and
+    // observed + r * rep_obs_stride
+    uint32_t n_rep;
+    uint64_t rep_dist_stride;
+    uint64_t rep_obs_stride;
 };
 
 // Records the text pchase_last_error_string() returns on this thread and

@@ -1026,14 +1026,15 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
     // class this lane watches (pad + lane <= top)
     const uint32_t wc = L.pad + (uint32_t)lane;
     const bool watch = wc <= top && wc < L.nclasses;
-    const uint32_t cnt = watch ? L.cls_count[wc] : 0u;
+    const uint32_t nrep = out.n_rep ? out.n_rep : 1u;
+    const uint32_t cnt = (watch ? L.cls_count[wc] : 0u) * nrep;
     const uint32_t first = watch ? L.cls_first[wc] : 0u;
     for (;;) {
         // longest first: the class whose next unit costs most
         uint32_t key = 0;
         if (watch) {
             const uint32_t h = *reinterpret_cast<volatile uint32_t *>(queues + wc);
-            if (h < cnt) key = __float_as_uint(fmaxf(items[first + h].cost, 1.0f));
+            if (h < cnt) key = __float_as_uint(fmaxf(items[first + h / nrep].cost, 1.0f));
         }
         const uint32_t kmax = __reduce_max_sync(kFull, key);
         if (kmax == 0) break;  // every class this slot can hold is done
@@ -1042,12 +1043,21 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
         uint32_t k = 0;
         if (lane == src) k = atomicAdd(queues + c, 1u);
         k = __shfl_sync(kFull, k, src);
-        if (k >= L.cls_count[c]) continue;  // taken meanwhile: look again
+        const uint32_t cper = L.cls_count[c];
+        if (k >= cper * nrep) continue;  // taken meanwhile: look again
         {
-            const SimItem it = items[L.cls_first[c] + k];
+            // unit-major: each unit runs for every observation in turn, so the
+            // costliest (most discriminating) units come first for all of them
+            const uint32_t u = k / nrep, rep = k - u * nrep;
+            const SimItem it = items[L.cls_first[c] + u];
+            SimOut o = out;
+            if (rep) {
+                o.dist += rep * out.rep_dist_stride;
+                o.observed += rep * out.rep_obs_stride;
+            }
             uint64_t t_start = 0;
             if (out.timeline) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
-            run_unit(it, arena, out, lane);
+            run_unit(it, arena, o, lane);
             __syncwarp();
             if (out.timeline && lane == 0) {
                 // units of a split item share the entry: first start, last end

@@ -147,3 +147,44 @@ def test_infer_geometry_round_trip():
                 oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, t, seed=g.seed),
                 oracle.cache_sim(truth.C, truth.b, truth.ways, truth.sets, truth.policy, t,
                                  seed=truth.seed))
+
+
+def test_batched_inference_equals_one_by_one():
+    """infer_geometry_batch over several observations (different truths,
+    noise and spikes) returns, per observation, the distances and pick of
+    infer_geometry on that observation alone; with a distance bound the
+    candidates within it keep exact distances."""
+    cands = small_candidates()
+    runs = small_plan()
+    host = [oracle.pchase_trace(r.n_elems, r.stride, r.length) for r in runs]
+    traces = [(torch.from_numpy(t.view(np.int32)).cuda(), r.length, r.warmup, r.n_elems, r.stride)
+              for t, r in zip(host, runs)]
+    plan = api.SimPlan(cands, traces)
+    truths = [cands[i] for i in (3, 10, 37, 58, 90, len(cands) - 5, len(cands) - 1)]
+    lats = []
+    for ti, truth in enumerate(truths):
+        miss = [oracle.cache_sim(truth.C, truth.b, truth.ways, truth.sets, truth.policy, t,
+                                 seed=truth.seed) for t in host]
+        lats.append(np.concatenate([synth_latency(m, 500 + ti * 11 + k, spikes=0.002 * (ti % 2))
+                                    for k, m in enumerate(miss)]))
+    lat_t = torch.from_numpy(np.stack(lats)).cuda()
+    for stop in (2**64 - 1, 0, 3):
+        dist_b, pick_b = api.infer_batch(plan, lat_t, stop_above=stop)
+        torch.cuda.synchronize()
+        dist_b = dist_b.cpu().numpy().astype(np.uint64)
+        pick_b = pick_b.cpu().numpy()
+        for o in range(len(truths)):
+            d1, p1 = plan.infer(lat_t[o].contiguous(), stop_above=stop)
+            d1 = d1.cpu().numpy().astype(np.uint64)
+            if stop == 2**64 - 1:
+                assert np.array_equal(dist_b[o], d1)
+            else:
+                keep = d1 <= stop
+                assert np.array_equal(dist_b[o][keep], d1[keep])
+                assert (dist_b[o][~keep] > stop).all()
+            if d1[int(p1[0])] <= stop:
+                # an answer within the bound is exact, hence the same pick
+                assert int(pick_b[o, 0]) == int(p1[0]) and int(pick_b[o, 1]) == int(p1[1])
+            else:
+                # nothing within the bound: both say so
+                assert dist_b[o][int(pick_b[o, 0])] > stop
