@@ -294,6 +294,206 @@ __global__ void __launch_bounds__(kThreads, 1)
                      : "memory");
 }
 
+// ------------------------------------------------------------ FC + heads
+// logits[m][h] = bias5[h] + sum_n bf16(GELU(bias4[n] + sum_k act[m][k] W4[n][k])) W5[h][n]
+// act [B][2048] BF16, W4 [256][2048] BF16, W5 [31][256] BF16.  CTA (s, t)
+// takes rows 128t .. 128t+127 and hidden units 64s .. 64s+63:
+//   * FC on the tensor cores: M128 N64, K = 2048 in 32 blocks of 64 through a
+//     6-buffer cp.async ring loaded 3 blocks ahead; an mbarrier per buffer
+//     frees it once that block's MMAs are done;
+//   * epilogue: bias, GELU, BF16 rounding of the 128 x 64 hidden slice into a
+//     swizzled shared tile, then the heads as a second MMA (M128 N32 K64 with
+//     W5's slice padded to 32 rows) into 32 more TMEM columns;
+//   * the 31 head partial sums per row are added atomically into logits
+//     (zeroed by the launcher; slice 0 adds bias5).
+constexpr int kFcK = 2048, kFcN = 256, kHeads = 31, kFcSlice = 64, kHeadsPad = 32;
+constexpr int kFcStages = 6;   // ring buffers
+constexpr int kFcAhead = 3;    // blocks loaded ahead; a buffer is refilled once the
+                               // MMAs of the block kFcStages back are done (2 blocks of slack)
+constexpr uint32_t kFcABytes = kTileRows * 128, kFcBBytes = kFcSlice * 128;
+constexpr uint32_t kFcStageBytes = kFcABytes + kFcBBytes;  // 24 KB
+constexpr uint32_t kW5Bytes = kHeadsPad * 128;             // 32 rows x 64 BF16, swizzled
+constexpr uint32_t kFcSmemBytes =
+    1024 + kFcStages * kFcStageBytes + kW5Bytes + 8 * (kFcStages + 1) + 16;
+constexpr uint32_t kIdescHeads = (1u << 4) | (1u << 7) | (1u << 10) |
+                                 ((uint32_t)(kHeadsPad >> 3) << 17) |
+                                 ((uint32_t)(kTileRows >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_n32(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                             uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdescHeads), "r"(acc)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    fc_heads_tc_kernel(const __nv_bfloat16 *__restrict__ act, int nb,
+                       const __nv_bfloat16 *__restrict__ W4, const float *__restrict__ bias4,
+                       const __nv_bfloat16 *__restrict__ W5, const float *__restrict__ bias5,
+                       float *__restrict__ logits, uint32_t *__restrict__ status) {
+    extern __shared__ uint8_t dsm[];
+    const uint32_t raw = smem_u32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *const gbase = dsm + (base - raw);
+    const uint32_t sStage = base;
+    const uint32_t sW5 = base + kFcStages * kFcStageBytes;  // 1024-aligned
+    const uint32_t sBar = sW5 + kW5Bytes;  // kFcStages ring mbarriers + 1 for the heads
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(
+        gbase + kFcStages * kFcStageBytes + kW5Bytes + 8 * (kFcStages + 1));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * kFcSlice;
+    const int m0 = blockIdx.y * kTileRows;
+    constexpr int kBlocks = kFcK / 64;
+
+    // W5 columns n0 .. n0+63 as a B operand: 32 rows (row 31 zero) x 128 B, swizzled
+    for (int e = tid; e < kHeadsPad * 8; e += 128) {
+        const int h = e >> 3, c = e & 7;
+        const bool ok = h < kHeads;
+        cp_async16(sW5 + h * 128 + ((c ^ (h & 7)) << 4),
+                   ok ? W5 + (size_t)h * kFcN + n0 + c * 8 : W5, ok);
+    }
+    auto load = [&](int kb) {
+        if (kb < kBlocks) {
+            const uint32_t st = sStage + (kb % kFcStages) * kFcStageBytes;
+            const int k0 = kb * 64;
+            // A: 128 rows x 8 chunks; B: 64 rows x 8 chunks; 128-byte swizzle
+            for (int e = tid; e < (kTileRows + kFcSlice) * 8; e += 128) {
+                const int r = e >> 3, c = e & 7;
+                if (r < kTileRows) {
+                    const int m = m0 + r;
+                    const bool ok = m < nb;
+                    cp_async16(st + r * 128 + ((c ^ (r & 7)) << 4),
+                               ok ? act + (size_t)m * kFcK + k0 + c * 8 : act, ok);
+                } else {
+                    const int rn = r - kTileRows;
+                    cp_async16(st + kFcABytes + rn * 128 + ((c ^ (rn & 7)) << 4),
+                               W4 + (size_t)(n0 + rn) * kFcK + k0 + c * 8, true);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    if (tid == 0) {
+        for (int q = 0; q <= kFcStages; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8 * q) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int kb = 0; kb < kFcAhead; ++kb) load(kb);  // W5 rides in the first group
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;  // columns 0..63: FC; 64..95: heads
+
+    bool ok = true;
+    for (int kb = 0; kb < kBlocks; ++kb) {
+        // block kb + kFcAhead refills the buffer of block kb + kFcAhead - kFcStages
+        const int pb = kb + kFcAhead - kFcStages;
+        if (pb >= 0) {
+            const bool got = mbar_wait(sBar + 8 * (pb % kFcStages), (uint32_t)(pb / kFcStages) & 1u);
+            if (!__syncthreads_and(got)) {
+                ok = false;
+                break;
+            }
+        }
+        load(kb + kFcAhead);
+        asm volatile("cp.async.wait_group %0;" ::"n"(kFcAhead) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t st = sStage + (kb % kFcStages) * kFcStageBytes;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem, sw128_desc(st + 32u * s), sw128_desc(st + kFcABytes + 32u * s),
+                         (kb | s) != 0 ? 1u : 0u);
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    sBar + 8u * (uint32_t)(kb % kFcStages))
+                : "memory");
+        }
+    }
+    if (ok) {
+        const int lb = kBlocks - 1;  // the last commit covers every earlier MMA
+        const bool got = mbar_wait(sBar + 8 * (lb % kFcStages), (uint32_t)(lb / kFcStages) & 1u);
+        ok = __syncthreads_and(got);
+    }
+    const int r = warp * 32 + lane;  // TMEM lane = tile row
+    if (ok) {
+        // hidden slice -> BF16 A tile of the heads MMA (buffer 0 is free now)
+        tc_fence_after();
+        const uint32_t hA = sStage;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t v[16];
+            tmem_ld16(taddr + q * 16, v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            uint32_t pk[8];
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                const int n = n0 + q * 16 + e;
+                const float z0 = __uint_as_float(v[e]) + __ldg(bias4 + n);
+                const float z1 = __uint_as_float(v[e + 1]) + __ldg(bias4 + n + 1);
+                const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_fast(z0), gelu_fast(z1));
+                pk[e >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
+            }
+            // 16 columns = chunks 2q, 2q+1 of row r
+            uint4 *row = reinterpret_cast<uint4 *>(gbase + (hA - base) + r * 128);
+            row[(2 * q) ^ (r & 7)] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            row[(2 * q + 1) ^ (r & 7)] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16_n32(tmem + 64u, sw128_desc(hA + 32u * s), sw128_desc(sW5 + 32u * s),
+                             s != 0 ? 1u : 0u);
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    sBar + 8u * kFcStages)
+                : "memory");
+        }
+        const bool got = mbar_wait(sBar + 8 * kFcStages, 0u);
+        ok = __syncthreads_and(got);
+        if (ok) {
+            tc_fence_after();
+            uint32_t v[2][16];
+            tmem_ld16(taddr + 64, v[0]);
+            tmem_ld16(taddr + 80, v[1]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int m = m0 + r;
+            if (m < nb) {
+#pragma unroll
+                for (int h = 0; h < kHeads; ++h)
+                    atomicAdd(logits + (size_t)m * kHeads + h,
+                              __uint_as_float(v[h >> 4][h & 15]) +
+                                  (blockIdx.x == 0 ? __ldg(bias5 + h) : 0.0f));
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
+                     : "memory");
+}
+
 }  // namespace
 
 cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16 *W,
@@ -311,6 +511,23 @@ cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16
     const long long ntiles = ((long long)nb * lout + kTileRows - 1) / kTileRows;
     const int grid = (int)std::min<long long>(ntiles, std::max(1, sms));
     conv_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, nb, lin, W, bias, out, pre, status);
+    return cudaGetLastError();
+}
+
+cudaError_t fc_heads_tc(const __nv_bfloat16 *act, int nb, const __nv_bfloat16 *W4,
+                        const float *bias4, const __nv_bfloat16 *W5, const float *bias5,
+                        float *logits, uint32_t *status, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    if (!status) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fc_heads_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kFcSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(logits, 0, (size_t)nb * kHeads * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    dim3 grid(kFcN / kFcSlice, (nb + kTileRows - 1) / kTileRows);
+    fc_heads_tc_kernel<<<grid, 128, kFcSmemBytes, st>>>(act, nb, W4, bias4, W5, bias5, logits,
+                                                        status);
     return cudaGetLastError();
 }
 

@@ -19,4 +19,14 @@ cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16
                     const float *bias, __nv_bfloat16 *out, float *pre, uint32_t *status,
                     int sms, cudaStream_t st);
 
+// logits [nb][31] FP32 = heads(GELU(FC(act))) for act [nb][2048] BF16 (the
+// flattened last convolution), W4 [256][2048] BF16 + bias4, W5 [31][256] BF16
+// + bias5; hidden activations rounded to BF16 as the heads' operands.  The
+// FC runs on tcgen05 tensor cores (4 slices of 64 hidden units per 128 rows),
+// the heads on CUDA cores in its epilogue.  Zeroes logits first.  A wait that
+// gives up ORs PCHASE_DEV_TIMEOUT into *status.
+cudaError_t fc_heads_tc(const __nv_bfloat16 *act, int nb, const __nv_bfloat16 *W4,
+                        const float *bias4, const __nv_bfloat16 *W5, const float *bias5,
+                        float *logits, uint32_t *status, cudaStream_t st);
+
 }  // namespace pchase

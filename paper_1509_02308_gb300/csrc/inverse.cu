@@ -972,6 +972,12 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
         INV_CUDA(cudaGetLastError());
         in = o;
     }
+    if (!train) {
+        // inference: FC on the tcgen05 tensor cores, heads in its epilogue
+        INV_CUDA(fc_heads_tc(in, (int)B, wb + L.w[4], wf + L.b[4], wb + L.w[5], wf + L.b[5],
+                             at<float>(work, h->logits), at<uint32_t>(work, h->status), st));
+        return PCHASE_OK;
+    }
     // FC 2048 -> 256: split-K into FP32 sums (B x 256 is too few 128 x 128
     // tiles to fill the GPU over K = 2048), then bias + GELU
     float *acc4 = at<float>(work, h->pre4);
