@@ -161,8 +161,8 @@ class ClockSampler:
 
 # From one ncu capture (--set full) of the current sim_kernel on the batched
 # workload with items capped at 65,536 accesses.
-SIM_DRAM_BYTES_PER_ACCESS = (264.800256e6 + 7.800576e6) / 65559830
-SIM_WARP_INST_PER_ACCESS = 554370987 / 65559830
+SIM_DRAM_BYTES_PER_ACCESS = (265.340672e6 + 7.8336e6) / 65559830
+SIM_WARP_INST_PER_ACCESS = 558339136 / 65559830
 
 
 def measured_peaks():
@@ -331,7 +331,7 @@ def ours(args):
     achieved = alg_bytes / (sim_avg * 1e-3) / 1e9
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     # DRAM bytes per access of sim_kernel from one ncu capture of the same
-    # kernel on this workload with items capped at 64 K accesses (272.6 MB for
+    # kernel on this workload with items capped at 64 K accesses (273.2 MB for
     # 65,559,830 accesses), scaled to this launch set by its accesses
     traffic = SIM_DRAM_BYTES_PER_ACCESS * total_acc
     # issue roofline: warp instructions per access from the same capture
