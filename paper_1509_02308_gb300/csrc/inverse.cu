@@ -596,19 +596,18 @@ __global__ void colsum_atomic_kernel(const float *x, int rows, int cols, int row
 
 // First convolution (1 input channel): out[b][p][co] = GELU(bias[co] +
 // sum_k W[co][k] * x[b][2p + k - 2]) with BF16 operands and FP32 sums, the
-// same products as the GEMM form.  One thread (grid-stride) per (trace,
-// position, group of 8 output channels), one 16-byte store; HBM-bound on the
-// 64-channel output.
+// same products as the GEMM form.  One block per trace: the 512 inputs are
+// staged in shared memory (zero padding around them); thread t computes
+// channels 8 (t % 8) .. +7 at positions 8 (t / 8) .. +7, one 16-byte store per
+// position.  HBM-bound on the 32 KB output per trace.
 __global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restrict__ x, int nb,
                                                     const __nv_bfloat16 *__restrict__ W,
                                                     const float *__restrict__ bias,
                                                     __nv_bfloat16 *__restrict__ out,
                                                     float *__restrict__ pre) {
     constexpr int lout = kPoints / 2;
-    const size_t total = (size_t)nb * lout * 8;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;  // a multiple of 8: g stays fixed
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int g = (int)(idx & 7);
+    __shared__ float xs[kPoints + 8];  // xs[q + 2] = x[q], zeros outside
+    const int t = threadIdx.x, g = t & 7, p0 = (t >> 3) * 8;
     float w[8][kKer], bs[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -616,34 +615,41 @@ __global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restr
 #pragma unroll
         for (int k = 0; k < kKer; ++k) w[c][k] = __bfloat162float(W[(g * 8 + c) * kKer + k]);
     }
-    for (; idx < total; idx += stride) {
-        const size_t bp = idx >> 3;
-        const int p = (int)(bp % lout);
-        const size_t b = bp / lout;
-        float xin[kKer];
-#pragma unroll
-        for (int k = 0; k < kKer; ++k) {
-            const int q = 2 * p + k - 2;
-            xin[k] = (q >= 0 && q < kPoints) ? __bfloat162float(x[b * kPoints + q]) : 0.0f;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        __syncthreads();  // the previous trace's reads are done
+        for (int q = t; q < kPoints + 8; q += blockDim.x) {
+            const int src = q - 2;
+            xs[q] = (src >= 0 && src < kPoints) ? __bfloat162float(x[(size_t)b * kPoints + src])
+                                                : 0.0f;
         }
-        uint32_t pk[4];
+        __syncthreads();
+#pragma unroll 2
+        for (int i = 0; i < 8; ++i) {
+            const int p = p0 + i;
+            float xin[kKer];
 #pragma unroll
-        for (int c = 0; c < 8; c += 2) {
-            float v[2];
+            for (int k = 0; k < kKer; ++k) xin[k] = xs[2 * p + k];  // x[2p + k - 2]
+            const size_t row = (size_t)b * lout + p;
+            uint32_t pk[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float acc = 0.0f;
+            for (int c = 0; c < 8; c += 2) {
+                float v[2];
 #pragma unroll
-                for (int k = 0; k < kKer; ++k) acc = fmaf(w[c + h][k], xin[k], acc);
-                v[h] = acc + bs[c + h];
-                if (pre) pre[bp * kCh + g * 8 + c + h] = v[h];
+                for (int h = 0; h < 2; ++h) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < kKer; ++k) acc = fmaf(w[c + h][k], xin[k], acc);
+                    v[h] = acc + bs[c + h];
+                    if (pre) pre[row * kCh + g * 8 + c + h] = v[h];
+                }
+                const __nv_bfloat162 hv =
+                    pre ? __floats2bfloat162_rn(gelu_f(v[0]), gelu_f(v[1]))
+                        : __floats2bfloat162_rn(gelu_fast(v[0]), gelu_fast(v[1]));
+                pk[c >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
             }
-            const __nv_bfloat162 hv =
-                pre ? __floats2bfloat162_rn(gelu_f(v[0]), gelu_f(v[1]))
-                    : __floats2bfloat162_rn(gelu_fast(v[0]), gelu_fast(v[1]));
-            pk[c >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
+            *reinterpret_cast<uint4 *>(out + row * kCh + g * 8) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-        *reinterpret_cast<uint4 *>(out + bp * kCh + g * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
 }
 
@@ -967,7 +973,7 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
             im2col_kernel<<<grid_for(nc), 256, 0, st>>>(in, (int)B, lin, cin, cols);
         }
         __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
-        conv1_kernel<<<grid_for((size_t)B * lout * 8), 256, 0, st>>>(
+        conv1_kernel<<<std::min<uint32_t>(B, 152u * 8u), 256, 0, st>>>(
             in, (int)B, wb + L.w[l], wf + L.b[l], o, train ? at<float>(work, h->pre[l]) : nullptr);
         INV_CUDA(cudaGetLastError());
         in = o;
