@@ -1029,6 +1029,7 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
     const uint32_t nrep = out.n_rep ? out.n_rep : 1u;
     const uint32_t cnt = (watch ? L.cls_count[wc] : 0u) * nrep;
     const uint32_t first = watch ? L.cls_first[wc] : 0u;
+    const bool prune = out.dist != nullptr && out.stop_above != ~0ull;
     for (;;) {
         // longest first: the class whose next unit costs most
         uint32_t key = 0;
@@ -1040,12 +1041,33 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
         if (kmax == 0) break;  // every class this slot can hold is done
         const int src = __ffs(__ballot_sync(kFull, key == kmax)) - 1;
         const uint32_t c = L.pad + (uint32_t)src;
-        uint32_t k = 0;
-        if (lane == src) k = atomicAdd(queues + c, 1u);
-        k = __shfl_sync(kFull, k, src);
         const uint32_t cper = L.cls_count[c];
-        if (k >= cper * nrep) continue;  // taken meanwhile: look again
-        {
+        const uint32_t total = cper * nrep;
+        // matcher with a bound over several observations: take up to 32 queue
+        // entries at once (unit-major, so one unit for up to 32 observations),
+        // screen them against their candidates' distances in parallel and run
+        // only the survivors (most entries belong to candidates already out)
+        const uint32_t grab = prune ? (nrep < 32u ? nrep : 32u) : 1u;
+        uint32_t k0 = 0;
+        if (lane == src) k0 = atomicAdd(queues + c, grab);
+        k0 = __shfl_sync(kFull, k0, src);
+        if (k0 >= total) continue;  // taken meanwhile: look again
+        uint32_t todo = 1u;
+        if (prune) {
+            const uint32_t kk = k0 + (uint32_t)lane;
+            bool alive = false;
+            if (lane < (int)grab && kk < total) {
+                const uint32_t uu = kk / nrep, rr = kk - uu * nrep;
+                const uint32_t cand = items[L.cls_first[c] + uu].cand;
+                const unsigned long long d = *reinterpret_cast<volatile const unsigned long long *>(
+                    out.dist + rr * out.rep_dist_stride + cand);
+                alive = d <= out.stop_above;
+            }
+            todo = __ballot_sync(kFull, alive);
+        }
+        while (todo) {
+            const uint32_t k = k0 + (uint32_t)(__ffs(todo) - 1);
+            todo &= todo - 1;
             // unit-major: each unit runs for every observation in turn, so the
             // costliest (most discriminating) units come first for all of them
             const uint32_t u = k / nrep, rep = k - u * nrep;
