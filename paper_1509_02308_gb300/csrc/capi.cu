@@ -163,24 +163,28 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t psh, uint32_t 
     u.table_n = (uint32_t)std::min<uint64_t>(table_n, 0xFFFFFFFFull);
     u.ring = 0;
     double step_ns;
-    // many same-set heads per step favour batch mode even above batch_max_sets,
-    // as long as the unit still fits the shared slot mix
+    // the cheaper of batch mode (eligible for T' <= batch_max_sets, or when
+    // many same-set heads per step make rounds costly, as long as the unit
+    // still fits the shared slot mix) and the round-based scan / table mode
     const bool many_rounds =
         rounds >= kBatchRounds && 2 * (kStageBytes + batch) <= tn.smem_budget_bytes;
-    if (tn.batch_max_sets && (Tl <= tn.batch_max_sets || many_rounds) &&
-        kStageBytes + batch <= kMaxArena && ring <= 32768) {
+    const bool batch_ok = tn.batch_max_sets && (Tl <= tn.batch_max_sets || many_rounds) &&
+                          kStageBytes + batch <= kMaxArena && ring <= 32768;
+    const bool scan = a <= tn.scan_max_ways;
+    const double round_ns = (scan ? kStepScanNs : kStepTableNs) + kRoundNs * (rounds - 1.0);
+    if (batch_ok && kStepBatchNs <= round_ns) {
         u.mode = kModeBatch;
         u.ring = ring;
         u.arena = batch;
         step_ns = kStepBatchNs;
-    } else if (a <= tn.scan_max_ways) {
+    } else if (scan) {
         u.mode = kModeScan;
         u.arena = 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * Tl : 0);
-        step_ns = kStepScanNs + kRoundNs * (rounds - 1.0);
+        step_ns = round_ns;
     } else {
         u.mode = kModeTable;
         u.arena = 8ull * Tl + 4 * lines + (G.policy == PCHASE_LRU ? 4 * lines : 0) + 2ull * table_n;
-        step_ns = kStepTableNs + kRoundNs * (rounds - 1.0);
+        step_ns = round_ns;
     }
     // a whole item whose accesses are mostly heads steps over them as they
     // come; the others queue their heads (and a split part gathers its own)

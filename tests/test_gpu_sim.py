@@ -189,7 +189,6 @@ def test_config2_full_size_sampled():
     traces = [(flat[int(offs[i]):int(offs[i + 1])], r.length, r.warmup, r.n_elems, r.stride)
               for i, r in enumerate(runs)]
     plan = SimPlan(geoms, traces, pairs=[(i, i) for i in range(len(runs))])
-    assert " split=0 " not in plan.description  # the longest items run as set-parts
     bitmaps, counts = plan.run()
     torch.cuda.synchronize()
     counts = counts.view(-1, 2).cpu().numpy()
@@ -214,6 +213,31 @@ def test_config2_full_size_sampled():
     # the bitmaps agree with the counts everywhere
     pop = np.unpackbits(bitmaps.cpu().numpy().view(np.uint8)).reshape(-1)
     assert int(pop.sum()) == int(counts[:, 0].sum())
+
+
+def test_longest_items_split_into_set_parts_full_length():
+    """The longest config-2 items of modest associativity at full length,
+    planned with forced set splits (up to 8 parts), against the oracle."""
+    from paper_1509_02308_gb300.api import SimPlan
+    geoms, runs = W.config2()
+    idx = sorted((i for i in range(len(runs)) if geoms[i].ways <= 64),
+                 key=lambda i: -runs[i].length)[:8]
+    g2 = [geoms[i] for i in idx]
+    r2 = [runs[i] for i in idx]
+    traces = [(None, r.length, r.warmup, r.n_elems, r.stride) for r in r2]
+    plan = SimPlan(g2, traces, pairs=[(i, i) for i in range(len(r2))],
+                   tune={"max_split": 8, "split_cost_ns": 1})
+    assert " split=0 " not in plan.description
+    bitmaps, counts = plan.run()
+    torch.cuda.synchronize()
+    counts = counts.view(-1, 2).cpu().numpy()
+    for k, (g, r) in enumerate(zip(g2, r2)):
+        want = oracle_bits(g, oracle.pchase_trace(r.n_elems, r.stride, r.length))
+        w0 = int(plan.word_offsets[k])
+        got = api.unpack_bits(bitmaps[w0:w0 + (r.length + 31) // 32].cpu().numpy().view(np.uint32),
+                              r.length)
+        assert np.array_equal(got, want), (k, g, r)
+        assert counts[k, 0] == want.sum() and counts[k, 1] == want[r.warmup:].sum()
 
 
 def test_index_out_of_range_is_flagged_not_faulted():
