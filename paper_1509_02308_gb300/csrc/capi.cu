@@ -87,13 +87,17 @@ const uint32_t kCaps[] = {1024,  2560,  3072,  4096,   5120,   6144,   8192,   1
                           16384, 20480, 24576, 32768,  40960,  49152,  65536,  81920,
                           98304, 112640, 131072, 163840, 196608, kMaxArena};
 
-// Planner cost model (ns of one warp, measured on GB300): a step of 32 heads
-// in each set mode, plus the gather of every 32 trace accesses a unit reads.
-constexpr double kStepBatchNs = 1500.0;
-constexpr double kStepScanNs = 600.0;
-constexpr double kStepTableNs = 700.0;
-constexpr double kRoundNs = 170.0;     // each extra round of same-set heads
-constexpr double kGatherNs = 50.0;
+// Planner cost model: ns of one warp on GB300 with the SM fully loaded, fitted
+// to per-item times of the batched workload.  A step in each set mode (batch
+// by policy; scan and table plus a cost per extra round of same-set heads),
+// and the gather of every 32 trace accesses a queued unit reads.
+// per policy: LRU, FIFO, RANDOM
+constexpr double kStepBatchNs[3] = {1900.0, 1660.0, 1780.0};
+constexpr double kStepScanNs[3] = {860.0, 880.0, 980.0};
+constexpr double kRoundScanNs[3] = {190.0, 140.0, 310.0};
+constexpr double kStepTableNs[3] = {750.0, 670.0, 690.0};
+constexpr double kRoundTableNs[3] = {130.0, 100.0, 150.0};
+constexpr double kGatherNs = 350.0;
 constexpr double kBatchRounds = 6.0;   // this many rounds: batch mode whatever T'
 constexpr double kPlanSms = 152.0;     // SMs the automatic split target assumes
 
@@ -103,7 +107,7 @@ struct ItemShape {
     double heads = 0.0;    // expected run heads (accesses that change line)
     double visited = 1.0;  // sets the stream visits
     uint32_t psh = 0;      // visited sets are multiples of 2^psh
-    uint32_t t2sh = 0;     // 2^t2sh: largest power of two dividing T
+    uint32_t groups = 1;   // T >> psh: the set groups a split divides among its parts
     double cost = 0.0;
 };
 
@@ -136,20 +140,19 @@ void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
     sh.visited = (double)(T / gfull);
     const uint64_t t2 = T & (~T + 1);
     const uint64_t g2 = gfull & (~gfull + 1);
-    sh.t2sh = ilog2((uint32_t)t2);
     sh.psh = ilog2((uint32_t)std::min(g2, t2));
+    sh.groups = (uint32_t)(T >> sh.psh);
 }
 
-// Set mode, arena and cost of one unit of a 2^ksh-way split (ksh = 0: whole).
-bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t psh, uint32_t ksh,
-                const ItemShape &sh, const pchase_tune &tn, UnitShape &u) {
-    (void)psh;
+// Set mode, arena and cost of one unit of a K-way split (K = 1: whole).
+bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemShape &sh,
+                const pchase_tune &tn, UnitShape &u) {
     const uint32_t T = G.sets, a = G.ways;
-    const uint32_t Tl = T >> ksh;
+    const uint32_t Tl = T / K;
     const uint64_t lines = (uint64_t)Tl * a;
     const uint32_t top = (it.n_elems - 1) >> it.lsh;  // largest line
-    const uint64_t table_n = ksh ? (uint64_t)Tl * (top / T + 1) : (uint64_t)top + 1;
-    const double parts = (double)(1u << ksh);
+    const uint64_t table_n = K > 1 ? (uint64_t)Tl * (top / T + 1) : (uint64_t)top + 1;
+    const double parts = (double)K;
     const double vis = std::max(1.0, sh.visited / parts);
     const double rounds = std::ceil(32.0 / std::min(32.0, vis));
     const double steps = std::ceil(sh.heads / parts / 32.0);
@@ -171,12 +174,15 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t psh, uint32_t 
     const bool batch_ok = tn.batch_max_sets && (Tl <= tn.batch_max_sets || many_rounds) &&
                           kStageBytes + batch <= kMaxArena && ring <= 32768;
     const bool scan = a <= tn.scan_max_ways;
-    const double round_ns = (scan ? kStepScanNs : kStepTableNs) + kRoundNs * (rounds - 1.0);
-    if (batch_ok && kStepBatchNs <= round_ns) {
+    const int pol = G.policy < 3 ? G.policy : 0;
+    const double round_ns = scan ? kStepScanNs[pol] + kRoundScanNs[pol] * (rounds - 1.0)
+                                 : kStepTableNs[pol] + kRoundTableNs[pol] * (rounds - 1.0);
+    const double batch_ns = kStepBatchNs[pol];
+    if (batch_ok && batch_ns <= round_ns) {
         u.mode = kModeBatch;
         u.ring = ring;
         u.arena = batch;
-        step_ns = kStepBatchNs;
+        step_ns = batch_ns;
     } else if (scan) {
         u.mode = kModeScan;
         u.arena = 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * Tl : 0);
@@ -186,12 +192,15 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t psh, uint32_t 
         u.arena = 8ull * Tl + 4 * lines + (G.policy == PCHASE_LRU ? 4 * lines : 0) + 2ull * table_n;
         step_ns = round_ns;
     }
-    // a whole item whose accesses are mostly heads steps over them as they
-    // come; the others queue their heads (and a split part gathers its own)
-    u.direct = ksh == 0 && sh.heads >= 0.5 * (double)it.len;
+    // a whole item steps over its accesses as they come (direct) when that
+    // beats gathering and compacting its heads (queued); a split part always
+    // queues its own sets' heads
     const double chunks = std::ceil((double)it.len / 32.0);
+    const double direct_cost = chunks * step_ns;
+    const double queued_cost = steps * step_ns + chunks * kGatherNs;
+    u.direct = K == 1 && direct_cost <= queued_cost;
     u.arena = align16(u.arena) + (u.direct ? 0u : kStageBytes);
-    u.cost = u.direct ? chunks * step_ns : steps * step_ns + chunks * kGatherNs;
+    u.cost = u.direct ? direct_cost : queued_cost;
     return u.arena <= kMaxArena;
 }
 
@@ -388,7 +397,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         if (tune->max_warps_per_cta)
             tn.max_warps_per_cta = std::min<uint32_t>(tune->max_warps_per_cta, kMaxWarpsPerCta);
         tn.ctas_per_sm_cap = tune->ctas_per_sm_cap;
-        if (tune->max_split) tn.max_split = std::min<uint32_t>(tune->max_split, 256);
+        if (tune->max_split) tn.max_split = std::min<uint32_t>(tune->max_split, 192);
         tn.split_cost_ns = tune->split_cost_ns;
     }
     for (uint32_t i = 0; i < n_geom; ++i) {
@@ -472,10 +481,11 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         it.gs1 = (uint8_t)gdm.s1;
         it.gs2 = (uint8_t)gdm.s2;
         it.lead = 1;
+        it.kcnt = 1;
         ItemShape &sh = shape[i];
         item_shape(G, Tr, sh);
         UnitShape u;
-        if (!unit_shape(G, it, 0, 0, sh, tn, u)) {
+        if (!unit_shape(G, it, 1, sh, tn, u)) {
             delete p;
             char buf[200];
             snprintf(buf, sizeof buf,
@@ -491,18 +501,21 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     // Split target: no unit above the plan's share per warp slot, but no
     // split below what the longest unsplittable work takes anyway (splitting
     // costs a gather pass per part and only the critical path gains).
+    // parts of a split: K = 2^j or 3 * 2^j dividing the item's set groups
     auto best_split = [&](uint64_t i, double target, uint32_t &k_out, UnitShape &u_out) {
         const pchase_geom &G = geoms[base[i].cand];
         const ItemShape &sh = shape[i];
-        k_out = 0;
-        unit_shape(G, base[i], 0, 0, sh, tn, u_out);
+        k_out = 1;
+        unit_shape(G, base[i], 1, sh, tn, u_out);
         if (u_out.cost <= target) return;
-        for (uint32_t ksh = 1; (1u << ksh) <= max_split && sh.psh + ksh <= sh.t2sh; ++ksh) {
+        for (uint32_t K = 2; K <= max_split && K <= sh.groups; ++K) {
+            const uint32_t odd = K % 3 == 0 ? K / 3 : K;
+            if ((odd & (odd - 1)) != 0 || sh.groups % K != 0) continue;
             UnitShape u;
-            if (!unit_shape(G, base[i], sh.psh, ksh, sh, tn, u)) continue;
+            if (!unit_shape(G, base[i], K, sh, tn, u)) continue;
             if (u.cost < u_out.cost * 0.97) {
                 u_out = u;
-                k_out = ksh;
+                k_out = K;
             }
             if (u_out.cost <= target) break;
         }
@@ -528,10 +541,14 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             uint32_t best_k;
             UnitShape best;
             best_split(i, target, best_k, best);
-            for (uint32_t r = 0; r < (1u << best_k); ++r) {
+            const DivMagic kdm = make_div_magic(best_k);
+            for (uint32_t r = 0; r < best_k; ++r) {
                 SimItem it = base[i];
-                it.psh = (uint8_t)(best_k ? sh.psh : 0);
-                it.ksh = (uint8_t)best_k;
+                it.psh = (uint8_t)(best_k > 1 ? sh.psh : 0);
+                it.kcnt = (uint8_t)best_k;
+                it.kmagic = kdm.m;
+                it.ks1 = (uint8_t)kdm.s1;
+                it.ks2 = (uint8_t)kdm.s2;
                 it.kres = r;
                 it.lead = r == 0;
                 apply_unit(it, best);
@@ -715,7 +732,7 @@ size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t b
         uint64_t modes[3] = {0, 0, 0}, split = 0;
         for (const SimItem &it : plan->items) {
             modes[it.mode < 3 ? it.mode : 0]++;
-            split += it.ksh && it.lead;
+            split += it.kcnt > 1 && it.lead;
         }
         char tmp[256];
         snprintf(tmp, sizeof tmp,

@@ -63,10 +63,10 @@ __device__ __forceinline__ uint32_t random_way(uint64_t seed, uint32_t set, uint
 enum SetMode : uint8_t { kModeScan = 0, kModeTable = 1, kModeBatch = 2 };
 
 // One simulation unit as the kernels read it (64-bit aligned, 112 bytes).
-// A caller's item is one unit, or several when its sets are split: unit r of
-// a split owns the sets whose index s has ((s >> psh) & (2^ksh - 1)) == kres,
-// renumbered locally as ((s >> (psh + ksh)) << psh) | (s & (2^psh - 1)), and
-// sees each line as the local line  local set + T' * (line div T).
+// A caller's item is one unit, or K (a power of two or three times one) when
+// its sets are split: unit r owns the sets s with (s >> psh) mod K == r,
+// renumbered locally as (((s >> psh) div K) << psh) | (s & (2^psh - 1)), and
+// sees each line as the local line  local set + T' * (line div T), T' = T / K.
 struct SimItem {
     const uint32_t *idx;  // NULL: analytic uniform chain
     uint32_t len;
@@ -74,7 +74,7 @@ struct SimItem {
     uint32_t n_elems;
     uint32_t stride;      // analytic chains, already reduced mod n_elems
     uint32_t ways;
-    uint32_t sets;        // local sets T' = T >> ksh
+    uint32_t sets;        // local sets T' = T / K
     uint32_t magic_m;     // local set = local line mod T', by DivMagic of T'
     uint8_t s1, s2, policy, mode;
     uint32_t lsh;         // line = index >> lsh  (b = 4 << lsh)
@@ -88,21 +88,22 @@ struct SimItem {
     uint32_t ring;        // batch-mode LRU: recency ring entries per set (power of two)
     uint32_t gsets;       // the geometry's T
     uint32_t gmagic;      // DivMagic of T
-    uint8_t gs1, gs2, psh, ksh;
+    uint8_t gs1, gs2, psh, ks1;
     uint32_t kres;        // this unit's residue (0 when not split)
     uint8_t lead;         // 1 on exactly one unit of each caller item
     uint8_t direct;       // step over consecutive accesses (dense, unsplit), no queue
-    uint8_t pad8[2];
+    uint8_t kcnt;         // K: parts of the split (1: whole)
+    uint8_t ks2;
     float cost;           // planner's estimate of the unit's warp time (ns)
-    uint32_t pad32;
+    uint32_t kmagic;      // DivMagic of K (with ks1, ks2)
 };
 
 static_assert(sizeof(SimItem) == 112, "SimItem layout");
 
 // Global set index of local set `local` of a unit (see SimItem).
-__host__ __device__ __forceinline__ uint32_t global_set(uint32_t local, uint32_t psh, uint32_t ksh,
+__host__ __device__ __forceinline__ uint32_t global_set(uint32_t local, uint32_t psh, uint32_t K,
                                                         uint32_t kres) {
-    return ((((local >> psh) << ksh) | kres) << psh) | (local & ((1u << psh) - 1u));
+    return (((local >> psh) * K + kres) << psh) | (local & ((1u << psh) - 1u));
 }
 
 // Staging at the start of a queued unit's arena: the compaction queue (run

@@ -63,13 +63,13 @@ struct ScanSets {
     uint32_t *evict;
     uint32_t ways;
     uint64_t seed;
-    uint32_t psh, ksh, kres;  // local -> global set (RANDOM's key)
+    uint32_t psh, kcnt, kres;  // local -> global set (RANDOM's key)
 
     __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         seed = it.seed;
         psh = it.psh;
-        ksh = it.ksh;
+        kcnt = it.kcnt;
         kres = it.kres;
         slot = reinterpret_cast<uint2 *>(arena);
         evict = reinterpret_cast<uint32_t *>(arena + 8ull * it.sets * ways);
@@ -101,7 +101,7 @@ struct ScanSets {
         if (POLICY == PCHASE_RANDOM && best >= a) {
             const uint32_t k = evict[set];
             evict[set] = k + 1;
-            v = random_way(seed, global_set(set, psh, ksh, kres), k, a);
+            v = random_way(seed, global_set(set, psh, kcnt, kres), k, a);
         }
         s[v] = make_uint2(line, t + a);
         return true;
@@ -120,13 +120,13 @@ struct TableSets {
     uint16_t *prv, *nxt, *tab;
     uint32_t ways;
     uint64_t seed;
-    uint32_t psh, ksh, kres;
+    uint32_t psh, kcnt, kres;
 
     __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         seed = it.seed;
         psh = it.psh;
-        ksh = it.ksh;
+        kcnt = it.kcnt;
         kres = it.kres;
         const uint32_t n = it.sets * ways;
         size_t off = 0;
@@ -209,7 +209,7 @@ struct TableSets {
                 v = m.x;
                 m.x += 1;
             } else {
-                v = random_way(seed, global_set(set, psh, ksh, kres), m.y, a);
+                v = random_way(seed, global_set(set, psh, kcnt, kres), m.y, a);
                 m.y += 1;
                 tab[sline[base + v]] = 0;
             }
@@ -346,13 +346,13 @@ struct BatchFR {
     uint32_t *perm;
     uint32_t ways;
     uint64_t seed;
-    uint32_t psh, ksh, kres;
+    uint32_t psh, kcnt, kres;
 
     __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         seed = it.seed;
         psh = it.psh;
-        ksh = it.ksh;
+        kcnt = it.kcnt;
         kres = it.kres;
         const uint32_t n = it.sets * ways;
         size_t off = 0;
@@ -400,7 +400,7 @@ struct BatchFR {
         } else {
             const uint32_t k = m.x + r;
             evicts = k >= a;
-            insw = evicts ? random_way(seed, global_set(g.set, psh, ksh, kres), m.y + (k - a), a)
+            insw = evicts ? random_way(seed, global_set(g.set, psh, kcnt, kres), m.y + (k - a), a)
                           : k;
         }
         // next group rank with the same way
@@ -817,10 +817,11 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     const uint32_t *__restrict__ idxp = it.idx;
     const uint32_t N = it.n_elems;
     const uint32_t lsh = it.lsh, sets = it.sets, mm = it.magic_m, s1 = it.s1, s2 = it.s2;
-    const bool split = it.ksh != 0;
+    const bool split = it.kcnt > 1;
     const uint32_t gT = it.gsets, gm = it.gmagic, gs1 = it.gs1, gs2 = it.gs2;
-    const uint32_t psh = it.psh, ksh = it.ksh, kres = it.kres;
-    const uint32_t pmask = (1u << psh) - 1u, kmask = (1u << ksh) - 1u;
+    const uint32_t psh = it.psh, K = it.kcnt, kres = it.kres;
+    const uint32_t km = it.kmagic, ks1 = it.ks1, ks2 = it.ks2;
+    const uint32_t pmask = (1u << psh) - 1u;
     const uint32_t warmup = it.warmup;
     const uint32_t lt = lanemask_lt();
     const bool ham = out.dist != nullptr;
@@ -950,8 +951,9 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
                     const uint32_t q = div_q(ln, gm, gs1, gs2);
                     const uint32_t set = ln - q * gT;
                     const uint32_t sg = set >> psh;
-                    mine = valid && (sg & kmask) == kres;
-                    lp = ((((sg >> ksh) << psh) | (set & pmask))) + q * sets;
+                    const uint32_t kq = div_q(sg, km, ks1, ks2);
+                    mine = valid && sg - kq * K == kres;
+                    lp = ((kq << psh) | (set & pmask)) + q * sets;
                 }
                 const bool take = mine && ln != prevl;
                 const uint32_t bal = __ballot_sync(kFull, take);

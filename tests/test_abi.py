@@ -108,11 +108,13 @@ def test_planner_splits_only_what_can_gain():
         d = _describe(h)
         # T=64: 8 parts with the dense trace; the 4 KB stride visits set 0 only
         # (64 lines apart, T = 64), so it stays whole.  Fully associative: whole.
-        # T=96 with the dense trace: 8 parts (power-of-two factor 32); with the
-        # 4 KB stride the visited sets are multiples of 32, i.e. 3 of them and
-        # no power-of-two share to split.
+        # T=96 with the dense trace: up to 8 parts (K must divide the set groups
+        # and be 2^j or 3 * 2^j); with the 4 KB stride the visited sets are the
+        # multiples of 32, three set groups, so K = 3.
+        # (how many parts the dense items get depends on the cost model)
         assert int(d["items"]) == 6
-        assert int(d["split"]) == 2 and int(d["units"]) == 6 - 2 + 16
+        assert int(d["split"]) == 3
+        assert 3 + 3 + 2 + 2 <= int(d["units"]) <= 3 + 3 + 8 + 8
     finally:
         L.pchase_sim_plan_destroy(h)
     rc, h = _plan(geoms, traces, tune={"max_split": 1, "split_cost_ns": 1})
