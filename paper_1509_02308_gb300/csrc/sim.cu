@@ -597,37 +597,44 @@ struct BatchLRU {
             }
         }
         __syncwarp();
-        // rank of each head's resident line among the window's live entries
         const uint32_t w1 = g.act ? tab[g.x] : 0u;
-        uint32_t rank = 32;
-        if (w1) {
-            const uint32_t off = (w1 - 1 - m.x) & rmask;
-            if (off < nround * gs) {
-                const uint32_t r0 = off / gs, j0 = off - r0 * gs;
-                uint32_t rk = 0;
-#pragma unroll
-                for (int r = 0; r < kWin; ++r) {
-                    if ((uint32_t)r < r0) rk += __popc(wbal[r]);
-                    else if ((uint32_t)r == r0) rk += __popc(wbal[r] & ((1u << (g.gb + j0)) - 1u));
-                }
-                if (rk < gs) rank = rk;
-            }
-        }
-        // lines older than this one or new, first used earlier in the group
-        const uint32_t key = first ? (w1 == 0 ? 0u : rank + 1) : 63u;
-        const uint32_t older = lanes_below(key, rank + 1) & gm & lt;
-        // distinct lines strictly between a repeat and its previous use
-        const uint32_t pkey = g.act ? (uint32_t)(prev + 1) : 63u;
-        const uint32_t pthr = prev < 0 ? 0u : (uint32_t)prev + 1;
-        const uint32_t between = lanes_below(pkey, pthr) & gm & lt &
-                                 ~((prev < 0) ? 0u : ((2u << prev) - 1u));
         bool miss = false;
-        if (g.act) {
-            if (first) {
-                if (w1 == 0) miss = true;
-                else if (rank < 32) miss = (m.z - 1 - rank) + __popc(older) >= a;
-            } else {
-                miss = (uint32_t)__popc(between) >= a;
+        if (__all_sync(kFull, !g.act || (first && w1 == 0))) {
+            // every head is its line's first use in the step and the line is
+            // not held (a thrashing stream): all of them miss
+            miss = g.act;
+        } else {
+            // rank of each head's resident line among the window's live entries
+            uint32_t rank = 32;
+            if (w1) {
+                const uint32_t off = (w1 - 1 - m.x) & rmask;
+                if (off < nround * gs) {
+                    const uint32_t r0 = off / gs, j0 = off - r0 * gs;
+                    uint32_t rk = 0;
+#pragma unroll
+                    for (int r = 0; r < kWin; ++r) {
+                        if ((uint32_t)r < r0) rk += __popc(wbal[r]);
+                        else if ((uint32_t)r == r0)
+                            rk += __popc(wbal[r] & ((1u << (g.gb + j0)) - 1u));
+                    }
+                    if (rk < gs) rank = rk;
+                }
+            }
+            // lines older than this one or new, first used earlier in the group
+            const uint32_t key = first ? (w1 == 0 ? 0u : rank + 1) : 63u;
+            const uint32_t older = lanes_below(key, rank + 1) & gm & lt;
+            // distinct lines strictly between a repeat and its previous use
+            const uint32_t pkey = g.act ? (uint32_t)(prev + 1) : 63u;
+            const uint32_t pthr = prev < 0 ? 0u : (uint32_t)prev + 1;
+            const uint32_t between = lanes_below(pkey, pthr) & gm & lt &
+                                     ~((prev < 0) ? 0u : ((2u << prev) - 1u));
+            if (g.act) {
+                if (first) {
+                    if (w1 == 0) miss = true;
+                    else if (rank < 32) miss = (m.z - 1 - rank) + __popc(older) >= a;
+                } else {
+                    miss = (uint32_t)__popc(between) >= a;
+                }
             }
         }
         // ----- updates, every group at once
