@@ -177,8 +177,10 @@ uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
 /*
  * Writes a one-line text description of the plan (items per set mode, size
- * classes, the per-CTA slot mix) into buf (host, `bytes` long, always
- * NUL-terminated); returns the length the full text needs.
+ * classes, the per-CTA slot mix, and the cost model's estimates in ms of one
+ * warp: est_ms=<longest unsplittable unit>,<split target>,<longest unit>,<sum>)
+ * into buf (host, `bytes` long, always NUL-terminated); returns the length the
+ * full text needs.
  */
 size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes);
 

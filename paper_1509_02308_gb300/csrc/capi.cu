@@ -97,6 +97,14 @@ constexpr double kStepScanNs[3] = {860.0, 880.0, 980.0};
 constexpr double kRoundScanNs[3] = {190.0, 140.0, 310.0};
 constexpr double kStepTableNs[3] = {750.0, 670.0, 690.0};
 constexpr double kRoundTableNs[3] = {130.0, 100.0, 150.0};
+// A step whose heads are all held (every access hits): batch mode by policy,
+// and table mode for FIFO / RANDOM, where such a hit changes nothing.
+constexpr double kStepHeldBatchNs[3] = {300.0, 130.0, 130.0};
+constexpr double kStepHeldTableNs = 130.0;
+// A batch step whose sets are each all hits or all misses (LRU / FIFO over
+// cyclic streams): FIFO, and LRU plus a cost per set in the step.
+constexpr double kStepNoHitFifoNs = 350.0;
+constexpr double kStepNoHitLruNs = 250.0, kNoHitLruSetNs = 200.0;
 constexpr double kGatherNs = 350.0;
 constexpr double kBatchRounds = 6.0;   // this many rounds: batch mode whatever T'
 constexpr double kPlanSms = 152.0;     // SMs the automatic split target assumes
@@ -108,6 +116,9 @@ struct ItemShape {
     double visited = 1.0;  // sets the stream visits
     uint32_t psh = 0;      // visited sets are multiples of 2^psh
     uint32_t groups = 1;   // T >> psh: the set groups a split divides among its parts
+    bool held = false;     // no set ever receives more than a distinct lines
+    bool cyclic = false;   // each set cycles through its lines in a fixed order every pass
+    double cold = 0.0;     // accesses before every line has been touched
     double cost = 0.0;
 };
 
@@ -142,6 +153,43 @@ void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
     const uint64_t g2 = gfull & (~gfull + 1);
     sh.psh = ilog2((uint32_t)std::min(g2, t2));
     sh.groups = (uint32_t)(T >> sh.psh);
+    // Held steady state: when no set can receive more than a distinct lines,
+    // nothing is ever evicted and every access after a line's first touch
+    // hits.  Any trace touches lines 0..top only; a uniform chain touches the
+    // multiples of g = gcd(N, s) once per pass of N / g accesses.
+    // Cyclic: each pass visits every line of the stream once in the same
+    // order (or in one ascending sweep).  A set receiving more than a lines
+    // then has each line come back after at least a others of its set, so
+    // under LRU and FIFO all its accesses miss; every other set holds its
+    // lines.  Either way each set's heads are all hits or all misses.
+    const uint64_t N = Tr.n_elems;
+    const uint64_t top = (4ull * (N - 1)) / b;
+    uint64_t per_set = (top + T) / T;
+    uint64_t pass = N;
+    const uint64_t se = Tr.stride % N;
+    if (Tr.stride && !se) {
+        // the chain never leaves element 0
+        sh.heads = 1.0;
+        per_set = 1;
+        pass = 1;
+    } else if (se) {
+        const uint64_t g = gcd64(N, se);
+        const uint64_t P = N / g;
+        pass = P;
+        const uint64_t gb = 4 * g;
+        if (gb % b == 0) {
+            const uint64_t dl = gb / b;  // lines k * dl, k < P, each once a pass
+            const uint64_t V = T / gcd64(dl % T ? dl % T : T, T);
+            per_set = std::min(per_set, (P + V - 1) / V);
+            sh.cyclic = true;
+        } else if (b % gb == 0) {
+            const uint64_t n = (4 * (N - g)) / b + 1;  // lines 0 .. n-1
+            per_set = std::min(per_set, (n + T - 1) / T);
+            sh.cyclic = se == g;  // one ascending sweep a pass
+        }
+    }
+    sh.held = per_set <= G.ways;
+    sh.cold = std::min((double)Tr.len, (double)pass);
 }
 
 // Set mode, arena and cost of one unit of a K-way split (K = 1: whole).
@@ -195,9 +243,25 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     // a whole item steps over its accesses as they come (direct) when that
     // beats gathering and compacting its heads (queued); a split part always
     // queues its own sets' heads
+    // held items: steps after the first pass take the all-held path
+    double held_ns = step_ns;
+    if (sh.held && u.mode == kModeBatch) held_ns = kStepHeldBatchNs[pol];
+    if (sh.held && u.mode == kModeTable && pol != PCHASE_LRU) held_ns = kStepHeldTableNs;
+    // cyclic LRU / FIFO batch units that do not hold everything: every step
+    // takes the path for sets that all hit or all miss
+    if (sh.cyclic && !sh.held && u.mode == kModeBatch && pol != PCHASE_RANDOM) {
+        const double sets_per_step = std::min(32.0, vis);
+        if (pol == PCHASE_FIFO) step_ns = held_ns = kStepNoHitFifoNs;
+        else if (sets_per_step <= 8.0)
+            step_ns = held_ns = kStepNoHitLruNs + kNoHitLruSetNs * sets_per_step;
+    }
     const double chunks = std::ceil((double)it.len / 32.0);
-    const double direct_cost = chunks * step_ns;
-    const double queued_cost = steps * step_ns + chunks * kGatherNs;
+    const double cold_chunks = std::min(chunks, std::ceil(sh.cold / 32.0) + 1.0);
+    const double cold_frac = it.len ? std::min(1.0, sh.cold / (double)it.len) : 1.0;
+    const double cold_steps = std::min(steps, std::ceil(steps * cold_frac) + 1.0);
+    const double direct_cost = cold_chunks * step_ns + (chunks - cold_chunks) * held_ns;
+    const double queued_cost =
+        cold_steps * step_ns + (steps - cold_steps) * held_ns + chunks * kGatherNs;
     u.direct = K == 1 && direct_cost <= queued_cost;
     u.arena = align16(u.arena) + (u.direct ? 0u : kStageBytes);
     u.cost = u.direct ? direct_cost : queued_cost;
@@ -278,6 +342,9 @@ struct pchase_sim_plan {
     std::vector<uint64_t> seg_offsets;     // n_trace + 1 (element offsets of trace latencies)
     std::vector<uint64_t> obs_word_offsets;  // n_trace
     uint64_t obs_words = 0, total_len = 0, max_trace_len = 0;
+    // planner estimates (ns of one warp): all units, the longest unit that
+    // cannot split further, the split target, the longest unit planned
+    double est_sum = 0.0, est_critical = 0.0, est_target = 0.0, est_max_unit = 0.0;
     // runtime state, set on the first run
     int device = -1, sms = 0, grid = 0, jgrid = 0;
     cudaStream_t side = nullptr;
@@ -529,6 +596,8 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     }
     const double target = tn.split_cost_ns ? (double)tn.split_cost_ns
                                            : std::max({total / (kPlanSms * 36.0), critical, 2.0e5});
+    p->est_critical = critical;
+    p->est_target = target;
     std::vector<SimItem> items;
     std::vector<double> cost;
     try {
@@ -555,6 +624,8 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                 it.cost = (float)best.cost;
                 items.push_back(it);
                 cost.push_back(best.cost);
+                p->est_sum += best.cost;
+                p->est_max_unit = std::max(p->est_max_unit, best.cost);
             }
         }
     } catch (...) {
@@ -755,6 +826,9 @@ size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t b
             snprintf(tmp, sizeof tmp, "%s%u", q ? "," : "", plan->layout.cls_count[q]);
             d += tmp;
         }
+        snprintf(tmp, sizeof tmp, " est_ms=%.2f,%.2f,%.2f,%.1f", plan->est_critical * 1e-6,
+                 plan->est_target * 1e-6, plan->est_max_unit * 1e-6, plan->est_sum * 1e-6);
+        d += tmp;
     }
     if (buf && bytes) {
         const size_t n = d.size() < bytes - 1 ? d.size() : bytes - 1;

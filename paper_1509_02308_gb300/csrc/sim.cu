@@ -59,6 +59,7 @@ constexpr uint32_t kStale = 0xFFFFFFFFu;
 // the smallest stamp is the lowest invalid way if any, else the victim.
 template <int POLICY>
 struct ScanSets {
+    static constexpr bool kStaticHits = false;  // residency needs a scan
     uint2 *slot;
     uint32_t *evict;
     uint32_t ways;
@@ -115,6 +116,9 @@ struct ScanSets {
 //   RANDOM meta = {filled, evictions}.
 template <int POLICY>
 struct TableSets {
+    // FIFO and RANDOM hits change nothing, and residency is one table read
+    static constexpr bool kStaticHits = POLICY != PCHASE_LRU;
+    __device__ __forceinline__ bool held(uint32_t line) const { return tab[line] != 0; }
     uint2 *meta;
     uint32_t *sline;
     uint16_t *prv, *nxt, *tab;
@@ -228,6 +232,11 @@ struct RoundResolver {
     Sets S;
     __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t t,
                                             int lane, uint32_t lt, uint32_t) {
+        // only a miss evicts: when every head's line is held at the start of
+        // the step, all of them hit, and under FIFO / RANDOM nothing changes
+        if constexpr (Sets::kStaticHits) {
+            if (__all_sync(kFull, !head || S.held(line))) return false;
+        }
         const uint32_t key = head ? set : (0x80000000u | (uint32_t)lane);
         const uint32_t peers = __match_any_sync(kFull, key);
         const uint32_t rank = __popc(peers & lt);
@@ -379,9 +388,93 @@ struct BatchFR {
         for (uint32_t i = lane; i < (it.table_n + 1) / 2; i += 32) t32[i] = 0;
     }
 
+    // A step whose heads are all new lines, none held at its start: every
+    // head misses, the r-th miss of a set's group takes that group's r-th
+    // way, and the last writer of each way is what stays.
+    __device__ __forceinline__ bool fresh_step(uint32_t line, uint32_t set, bool head, int lane,
+                                               uint32_t lt, uint32_t sm) {
+        const uint32_t a = ways;
+        const uint32_t r = __popc(sm & lt);
+        const uint32_t M = __popc(sm);
+        const uint4 m = head ? meta[set] : make_uint4(0, 0, 0, 0);
+        uint32_t insw;
+        bool evicts;
+        if (POLICY == PCHASE_FIFO) {
+            evicts = m.y + r >= a;
+            insw = (m.x + m.y + r) % a;
+        } else {
+            const uint32_t k = m.x + r;
+            evicts = k >= a;
+            insw = evicts ? random_way(seed, global_set(set, psh, kcnt, kres), m.y + (k - a), a)
+                          : k;
+        }
+        const uint32_t sw = __match_any_sync(kFull, head ? set * a + insw
+                                                          : (0x80000000u | (uint32_t)lane));
+        // the first writer of a way that was in use evicts the line it held
+        // (a line of the step is written again only after its earlier way
+        // was taken over, so only last writers stay)
+        if (head && evicts && (sw & lt) == 0) tab[sline[set * a + insw]] = 0;
+        __syncwarp();
+        if (head && (sw & ~(lt | (1u << lane))) == 0) {
+            sline[set * a + insw] = line;
+            tab[line] = (uint16_t)(insw + 1);
+        }
+        if (head && r == 0) {
+            uint4 n = m;
+            if (POLICY == PCHASE_FIFO) {
+                const uint32_t tot = m.y + M;
+                n.y = tot < a ? tot : a;
+                n.x = (m.x + (tot > a ? tot - a : 0u)) % a;
+            } else {
+                const uint32_t tot = m.x + M;
+                n.x = tot < a ? tot : a;
+                n.y = m.y + (tot > a ? tot - a : 0u);
+            }
+            meta[set] = n;
+        }
+        __syncwarp();
+        return head;
+    }
+
     __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t,
                                             int lane, uint32_t lt, uint32_t stamp) {
         if (__ballot_sync(kFull, head) == 0) return false;
+        // Only a miss evicts: when every head's line is held at the start of
+        // the step, all of them hit and nothing changes.
+        const uint32_t w0 = head ? tab[line] : 1u;
+        if (__all_sync(kFull, w0 != 0u)) return false;
+        {
+            // Pure sets: in a group where no head can hit all miss; a group
+            // whose heads all hold their lines all hits.  If every earlier
+            // head of its group misses, a first use misses when its line is
+            // not held or (FIFO) is pushed out by those misses, and a repeat
+            // (FIFO) when at least a misses of its set came since its previous
+            // use.  RANDOM takes only groups of new lines not held.
+            const uint32_t lm0 =
+                __match_any_sync(kFull, head ? line : (0x80000000u | (uint32_t)lane));
+            const uint32_t sm0 =
+                __match_any_sync(kFull, head ? set : (0x80000000u | (uint32_t)lane));
+            const uint32_t pm0 = lm0 & lt;
+            bool nohit = w0 == 0u && pm0 == 0u;
+            if (POLICY == PCHASE_FIFO) {
+                if (pm0) {
+                    const uint32_t below = (2u << (31 - __clz(pm0))) - 1u;
+                    nohit = (uint32_t)__popc(sm0 & lt & ~below) >= ways;
+                } else if (w0) {
+                    // held in way w, rho lines inserted before it: it leaves at
+                    // the (a - L + rho + 1)-th miss of its set
+                    const uint4 mf = head ? meta[set] : make_uint4(0, 0, 0, 0);
+                    const uint32_t rho = (w0 - 1u + ways - mf.x) % ways;
+                    nohit = (uint32_t)__popc(sm0 & lt) >= ways - mf.y + rho + 1u;
+                }
+            }
+            // held groups hit and change nothing; the others all miss
+            const uint32_t hbal = __ballot_sync(kFull, head && w0 != 0u);
+            const uint32_t nbal = __ballot_sync(kFull, head && nohit);
+            const bool gheld = head && (hbal & sm0) == sm0;
+            if (__all_sync(kFull, !head || gheld || (nbal & sm0) == sm0))
+                return fresh_step(line, set, head && !gheld, lane, lt, sm0);
+        }
         const Grouped g = group_heads(line, set, head, lane, lt, perm);
         const uint32_t a = ways;
         const uint32_t ltg = g.gmask & lt;
@@ -475,7 +568,8 @@ struct BatchFR {
 };
 
 // LRU.  Arena: uint32 perm[32] (+ pad to 256 B); uint4 meta[T] =
-// {tail, head, live, -} (monotone ring positions); uint32 ring[T*R];
+// {tail, head, live, compact} (monotone ring positions; compact = 1 when no
+// stale entry lies between tail and head); uint32 ring[T*R];
 // uint16 tab[table_n] (ring index + 1).
 struct BatchLRU {
     uint4 *meta;
@@ -499,7 +593,7 @@ struct BatchLRU {
     }
 
     __device__ __forceinline__ void clear(const SimItem &it, int lane) {
-        for (uint32_t i = lane; i < it.sets; i += 32) meta[i] = make_uint4(0, 0, 0, 0);
+        for (uint32_t i = lane; i < it.sets; i += 32) meta[i] = make_uint4(0, 0, 0, 1);
         uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
         for (uint32_t i = lane; i < (it.table_n + 1) / 2; i += 32) t32[i] = 0;
     }
@@ -523,9 +617,63 @@ struct BatchLRU {
             done += __popc(bal);
         }
         m.y = m.x + done;
+        m.w = 1;
         if (lane == 0) meta[set] = m;
         __syncwarp();
         return m;
+    }
+
+    // Every head of set s in the step misses (`last` marks the last use of
+    // each of its lines): the D distinct lines go on top in last-use order
+    // (only the last a of them stay when D > a) and the oldest held lines
+    // leave until a lines are held.
+    __device__ __forceinline__ void nohit_step(uint32_t s, uint32_t line, bool last, int lane,
+                                               uint32_t lt) {
+        const uint32_t a = ways;
+        uint32_t *rg = ring + (size_t)s * R;
+        uint4 m = meta[s];
+        if (m.y - m.x > R - 64) m = compact(s, m, lane, lt);
+        const uint32_t lb = __ballot_sync(kFull, last);
+        const uint32_t D = __popc(lb);
+        const uint32_t keep_old = D <= a ? a - D : 0u;
+        const uint32_t E = m.z > keep_old ? m.z - keep_old : 0u;
+        // evict the E oldest held lines; the tail moves to the first kept one,
+        // or past the step's own lines that do not stay
+        uint32_t new_tail = m.y + (D > a ? D - a : 0u), evd = 0;
+        bool found = false;
+        for (uint32_t p0 = m.x; p0 < m.y && (evd < E || !found); p0 += 32) {
+            const uint32_t p = p0 + (uint32_t)lane;
+            const uint32_t e = p < m.y ? rg[p & rmask] : kStale;
+            const bool live = e != kStale;
+            const uint32_t bal = __ballot_sync(kFull, live);
+            const bool ev = live && evd + __popc(bal & lt) < E;
+            if (ev) {
+                tab[e] = 0;
+                rg[p & rmask] = kStale;
+            }
+            const uint32_t keep = __ballot_sync(kFull, live && !ev);
+            if (!found && keep) {
+                new_tail = p0 + (uint32_t)(__ffs(keep) - 1);
+                found = true;
+            }
+            evd += __popc(bal);
+        }
+        __syncwarp();
+        if (last) {
+            const uint32_t q = __popc(lb & lt);
+            const uint32_t p = (m.y + q) & rmask;
+            if (D > a && q < D - a) {
+                rg[p] = kStale;
+            } else {
+                rg[p] = line;
+                tab[line] = (uint16_t)(p + 1);
+            }
+        }
+        // a prefix of the held lines left: a compact ring stays compact, and
+        // one whose held lines all left becomes compact
+        const uint32_t cpt = (m.w || !found) ? 1u : 0u;
+        if (lane == 0) meta[s] = make_uint4(new_tail, m.y + D, D <= a ? m.z - E + D : a, cpt);
+        __syncwarp();
     }
 
     // All set groups at once.  A group of g heads can push out at most g
@@ -535,7 +683,68 @@ struct BatchLRU {
     // positions at a time until g live entries are seen or the ring ends.
     __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t,
                                             int lane, uint32_t lt, uint32_t) {
-        if (__ballot_sync(kFull, head) == 0) return false;
+        // Pure sets.  Only a miss evicts, so when every head of a set's group
+        // holds its line at the start of the step (a held group), all of them
+        // hit: their old entries go stale and the lines are appended in
+        // last-use order, the held count and the tail stay.  A group in which
+        // no head can hit (each first use of a line not held, each repeat
+        // after at least a other distinct lines of its set since its previous
+        // use, each of them a miss inserted above it) all misses.  Steps made
+        // of such groups (at most 8 of the second kind) skip the general path.
+        const uint32_t hb = __ballot_sync(kFull, head);
+        if (hb == 0) return false;
+        const uint32_t w0 = head ? tab[line] : 1u;
+        const uint32_t sm0 = __match_any_sync(kFull, head ? set : (0x80000000u | (uint32_t)lane));
+        const uint32_t lm0 = __match_any_sync(kFull, head ? line : (0x80000000u | (uint32_t)lane));
+        const uint4 m0 = head ? meta[set] : make_uint4(0, 0, 0, 0);
+        const uint32_t pm0 = lm0 & lt;
+        const bool last = head && (lm0 & ~(lt | (1u << lane))) == 0;
+        const uint32_t hbal = __ballot_sync(kFull, head && w0 != 0u);
+        const bool gheld = head && (hbal & sm0) == sm0;
+        bool pure = hbal == hb;
+        uint32_t nlead = 0;
+        if (!pure) {
+            const int prev = pm0 ? 31 - __clz(pm0) : -1;
+            const uint32_t pkey = head ? (uint32_t)(prev + 1) : 63u;
+            const uint32_t pthr = prev < 0 ? 0u : (uint32_t)prev + 1;
+            const uint32_t between = lanes_below(pkey, pthr) & sm0 & lt &
+                                     ~((prev < 0) ? 0u : ((2u << prev) - 1u));
+            // a held first use at depth d leaves once d plus the distinct
+            // lines before it in the step reach a (exact depth needs a
+            // compact ring)
+            const uint32_t fbal = __ballot_sync(kFull, head && prev < 0);
+            bool nohit;
+            if (prev >= 0) nohit = (uint32_t)__popc(between) >= ways;
+            else if (w0 == 0u) nohit = true;
+            else nohit = m0.w && ((m0.y - w0) & rmask) + __popc(fbal & sm0 & lt) >= ways;
+            nohit = nohit && head;
+            const uint32_t nbal = __ballot_sync(kFull, nohit);
+            const bool gnohit = head && !gheld && (nbal & sm0) == sm0;
+            nlead = __ballot_sync(kFull, gnohit && (sm0 & lt) == 0);
+            pure = __all_sync(kFull, !head || gheld || gnohit) && __popc(nlead) <= 8;
+        }
+        // room for 32 entries in every held group's ring (else compact first)
+        if (pure && __all_sync(kFull, !gheld || m0.y - m0.x <= R - 64)) {
+            const uint32_t lb = __ballot_sync(kFull, last && gheld);
+            uint32_t *rg0 = ring + (size_t)(gheld ? set : 0u) * R;
+            if (gheld && pm0 == 0) rg0[w0 - 1] = kStale;
+            __syncwarp();
+            if (last && gheld) {
+                const uint32_t p = (m0.y + __popc(lb & sm0 & lt)) & rmask;
+                rg0[p] = line;
+                tab[line] = (uint16_t)(p + 1);
+            }
+            if (gheld && (sm0 & ~(lt | (1u << lane))) == 0)
+                meta[set] = make_uint4(m0.x, m0.y + __popc(lb & sm0), m0.z, 0u);
+            __syncwarp();
+            for (uint32_t todo = nlead; todo; todo &= todo - 1) {
+                const int ld = __ffs(todo) - 1;
+                const uint32_t s0 = __shfl_sync(kFull, set, ld);
+                const uint32_t gmask = __shfl_sync(kFull, sm0, ld);
+                nohit_step(s0, line, last && ((gmask >> lane) & 1u), lane, lt);
+            }
+            return head && !gheld;
+        }
         const Grouped g = group_heads(line, set, head, lane, lt, perm);
         const uint32_t a = ways;
         const uint32_t gm = g.gmask;
@@ -680,11 +889,14 @@ struct BatchLRU {
             }
         }
         if (g.act && (uint32_t)lane == g.gb) {
+            // no old line stays: the ring is the step's own lines, whose live
+            // entries follow the D - a that do not stay
+            const bool fresh = old_live == E;
             uint4 n;
-            n.x = new_tail;
+            n.x = fresh ? m.y + (D > a ? D - a : 0u) : new_tail;
             n.y = m.y + D;
             n.z = D <= a ? old_live - E + D : a;
-            n.w = 0;
+            n.w = fresh ? 1u : 0u;
             meta[g.set] = n;
         }
         __syncwarp();

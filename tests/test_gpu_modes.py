@@ -115,3 +115,34 @@ def test_batch_mode_long_thrash_and_refill():
             want = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, t, seed=g.seed)
             got = api.unpack_bits(b[int(plan.word_offsets[i]):], t.size)
             assert np.array_equal(got, want), (g, ti, int(np.argmax(got != want)))
+
+
+@pytest.mark.parametrize("tune_name", ["batch_all", "default"])
+def test_cyclic_periods_around_the_ways(tune_name):
+    """Cyclic traces over m lines with m from 1 to 2a+1 and past 32, on 1-3
+    sets: steady states that all hit, that all miss with each line coming back
+    inside a 32-access step, and that mix; lines touched once or twice in a
+    row (dense and half-dense run heads)."""
+    geoms = [W.Geom(T * a * 32, 32, a, T, p, 0x5100 + 31 * a + T + 7 * p)
+             for T in (1, 2, 3) for a in (1, 2, 3, 4, 7, 8, 12, 16, 31) for p in (0, 1, 2)]
+    host = []
+    for m in (1, 2, 3, 4, 5, 6, 7, 8, 9, 11, 13, 15, 16, 17, 24, 25, 31, 32, 33, 34, 40, 47,
+              63, 64, 65):
+        cyc = (np.arange(m) * 8).astype(np.uint32)
+        host.append(np.tile(cyc, 4000 // m + 1)[:4000])
+        host.append(np.repeat(np.tile(cyc, 2000 // m + 1), 2)[:4000] + 1)
+    n_el = [int(t.max()) + 1 for t in host]
+    dev = [torch.from_numpy(t.view(np.int32)).cuda() for t in host]
+    traces = [(d, t.size, 40, n, 1) for d, t, n in zip(dev, host, n_el)]
+    plan = api.SimPlan(geoms, traces, tune=TUNES[tune_name])
+    bitmaps, counts = plan.run()
+    torch.cuda.synchronize()
+    b = bitmaps.cpu().numpy().view(np.uint32)
+    c = counts.view(-1, 2).cpu().numpy()
+    for gi, g in enumerate(geoms):
+        for ti, t in enumerate(host):
+            i = gi * len(host) + ti
+            want = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, t, seed=g.seed)
+            got = api.unpack_bits(b[int(plan.word_offsets[i]):], t.size)
+            assert np.array_equal(got, want), (tune_name, g, ti, int(np.argmax(got != want)))
+            assert c[i, 0] == want.sum() and c[i, 1] == want[40:].sum()
