@@ -176,8 +176,9 @@ uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);
  * pchase_match_run queues one fewer (no output clear). */
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
 /*
- * Writes a one-line text description of the plan (items per set mode, size
- * classes, the per-CTA slot mix, and the cost model's estimates in ms of one
+ * Writes a one-line text description of the plan (units per set mode, units
+ * that step over their accesses directly, size classes, the per-CTA slot mix,
+ * and the cost model's estimates in ms of one
  * warp: est_ms=<longest unsplittable unit>,<split target>,<longest unit>,<sum>)
  * into buf (host, `bytes` long, always NUL-terminated); returns the length the
  * full text needs.

@@ -93,18 +93,18 @@ const uint32_t kCaps[] = {1024,  2560,  3072,  4096,   5120,   6144,   8192,   1
 // and the gather of every 32 trace accesses a queued unit reads.
 // per policy: LRU, FIFO, RANDOM
 constexpr double kStepBatchNs[3] = {1900.0, 1660.0, 1780.0};
-constexpr double kStepScanNs[3] = {860.0, 880.0, 980.0};
-constexpr double kRoundScanNs[3] = {190.0, 140.0, 310.0};
-constexpr double kStepTableNs[3] = {750.0, 670.0, 690.0};
-constexpr double kRoundTableNs[3] = {130.0, 100.0, 150.0};
+constexpr double kStepScanNs[3] = {765.0, 770.0, 845.0};
+constexpr double kRoundScanNs[3] = {200.0, 200.0, 265.0};
+constexpr double kStepTableNs[3] = {690.0, 635.0, 730.0};
+constexpr double kRoundTableNs[3] = {130.0, 110.0, 160.0};
 // A step whose heads are all held (every access hits): batch mode by policy,
 // and table mode for FIFO / RANDOM, where such a hit changes nothing.
-constexpr double kStepHeldBatchNs[3] = {300.0, 130.0, 130.0};
-constexpr double kStepHeldTableNs = 130.0;
+constexpr double kStepHeldBatchNs[3] = {630.0, 445.0, 450.0};
+constexpr double kStepHeldTableNs = 435.0;
 // A batch step whose sets are each all hits or all misses (LRU / FIFO over
 // cyclic streams): FIFO, and LRU plus a cost per set in the step.
-constexpr double kStepNoHitFifoNs = 350.0;
-constexpr double kStepNoHitLruNs = 250.0, kNoHitLruSetNs = 200.0;
+constexpr double kStepNoHitFifoNs = 1060.0;
+constexpr double kStepNoHitLruNs = 600.0, kNoHitLruSetNs = 480.0;
 constexpr double kGatherNs = 350.0;
 constexpr double kBatchRounds = 6.0;   // this many rounds: batch mode whatever T'
 constexpr double kPlanSms = 152.0;     // SMs the automatic split target assumes
@@ -181,10 +181,12 @@ void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
             const uint64_t dl = gb / b;  // lines k * dl, k < P, each once a pass
             const uint64_t V = T / gcd64(dl % T ? dl % T : T, T);
             per_set = std::min(per_set, (P + V - 1) / V);
+            sh.visited = std::min(sh.visited, (double)std::min(V, P));
             sh.cyclic = true;
         } else if (b % gb == 0) {
             const uint64_t n = (4 * (N - g)) / b + 1;  // lines 0 .. n-1
             per_set = std::min(per_set, (n + T - 1) / T);
+            sh.visited = std::min(sh.visited, (double)std::min(T, n));
             sh.cyclic = se == g;  // one ascending sweep a pass
         }
     }
@@ -204,67 +206,87 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     const double vis = std::max(1.0, sh.visited / parts);
     const double rounds = std::ceil(32.0 / std::min(32.0, vis));
     const double steps = std::ceil(sh.heads / parts / 32.0);
-    uint32_t ring = 256;
-    while (ring < a + 128) ring <<= 1;
+    // LRU recency ring per set: compacted when more than R - 64 positions are
+    // in use, so it holds a lines plus a step's 32 appends for R >= a + 64;
+    // the slack above that sets how often it compacts (cyclic streams keep
+    // their rings compact and never do)
+    uint32_t ring = 128;
+    while (ring < a + 96) ring <<= 1;
     uint64_t batch = 256 + 16ull * Tl + 2ull * table_n;
     if (G.policy == PCHASE_LRU) batch += 4ull * Tl * ring;
     else batch += ((4 * lines + 15) & ~15ull) + (G.policy == PCHASE_RANDOM ? 8 * lines : 0);
     batch = align16(batch);
     u.sets = Tl;
     u.table_n = (uint32_t)std::min<uint64_t>(table_n, 0xFFFFFFFFull);
-    u.ring = 0;
-    double step_ns;
-    // the cheaper of batch mode (eligible for T' <= batch_max_sets, or when
-    // many same-set heads per step make rounds costly, as long as the unit
-    // still fits the shared slot mix) and the round-based scan / table mode
+    // candidates: batch mode (eligible for T' <= batch_max_sets, or when many
+    // same-set heads per step make rounds costly, as long as the unit still
+    // fits the shared slot mix) and the round-based scan / table mode; each
+    // with its cost per step while lines are first touched (cold) and after
     const bool many_rounds =
         rounds >= kBatchRounds && 2 * (kStageBytes + batch) <= tn.smem_budget_bytes;
     const bool batch_ok = tn.batch_max_sets && (Tl <= tn.batch_max_sets || many_rounds) &&
                           kStageBytes + batch <= kMaxArena && ring <= 32768;
     const bool scan = a <= tn.scan_max_ways;
     const int pol = G.policy < 3 ? G.policy : 0;
-    const double round_ns = scan ? kStepScanNs[pol] + kRoundScanNs[pol] * (rounds - 1.0)
-                                 : kStepTableNs[pol] + kRoundTableNs[pol] * (rounds - 1.0);
-    const double batch_ns = kStepBatchNs[pol];
-    if (batch_ok && batch_ns <= round_ns) {
-        u.mode = kModeBatch;
-        u.ring = ring;
-        u.arena = batch;
-        step_ns = batch_ns;
-    } else if (scan) {
-        u.mode = kModeScan;
-        u.arena = 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * Tl : 0);
-        step_ns = round_ns;
-    } else {
-        u.mode = kModeTable;
-        u.arena = 8ull * Tl + 4 * lines + (G.policy == PCHASE_LRU ? 4 * lines : 0) + 2ull * table_n;
-        step_ns = round_ns;
+    struct Option {
+        uint32_t mode, ring;
+        uint64_t arena;
+        double cold_ns, warm_ns;
+    } opt[2];
+    int n_opt = 0;
+    if (batch_ok) {
+        Option o{kModeBatch, ring, batch, kStepBatchNs[pol], kStepBatchNs[pol]};
+        // held streams: steps after the first pass take the all-held path;
+        // cyclic LRU / FIFO streams: every step takes the path for sets that
+        // all hit or all miss
+        if (sh.held) o.warm_ns = kStepHeldBatchNs[pol];
+        if (sh.cyclic && !sh.held && pol != PCHASE_RANDOM) {
+            const double sets_per_step = std::min(32.0, vis);
+            if (pol == PCHASE_FIFO) o.cold_ns = o.warm_ns = kStepNoHitFifoNs;
+            else if (sets_per_step <= 8.0)
+                o.cold_ns = o.warm_ns = kStepNoHitLruNs + kNoHitLruSetNs * sets_per_step;
+        }
+        opt[n_opt++] = o;
+    }
+    {
+        const double round_ns = scan ? kStepScanNs[pol] + kRoundScanNs[pol] * (rounds - 1.0)
+                                     : kStepTableNs[pol] + kRoundTableNs[pol] * (rounds - 1.0);
+        Option o{scan ? kModeScan : kModeTable, 0u,
+                 scan ? 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * Tl : 0)
+                      : 8ull * Tl + 4 * lines + (G.policy == PCHASE_LRU ? 4 * lines : 0) +
+                            2ull * table_n,
+                 round_ns, round_ns};
+        if (!scan && sh.held && pol != PCHASE_LRU) o.warm_ns = kStepHeldTableNs;
+        opt[n_opt++] = o;
     }
     // a whole item steps over its accesses as they come (direct) when that
     // beats gathering and compacting its heads (queued); a split part always
-    // queues its own sets' heads
-    // held items: steps after the first pass take the all-held path
-    double held_ns = step_ns;
-    if (sh.held && u.mode == kModeBatch) held_ns = kStepHeldBatchNs[pol];
-    if (sh.held && u.mode == kModeTable && pol != PCHASE_LRU) held_ns = kStepHeldTableNs;
-    // cyclic LRU / FIFO batch units that do not hold everything: every step
-    // takes the path for sets that all hit or all miss
-    if (sh.cyclic && !sh.held && u.mode == kModeBatch && pol != PCHASE_RANDOM) {
-        const double sets_per_step = std::min(32.0, vis);
-        if (pol == PCHASE_FIFO) step_ns = held_ns = kStepNoHitFifoNs;
-        else if (sets_per_step <= 8.0)
-            step_ns = held_ns = kStepNoHitLruNs + kNoHitLruSetNs * sets_per_step;
-    }
+    // queues its own sets' heads.  The cheapest option that fits is taken.
     const double chunks = std::ceil((double)it.len / 32.0);
     const double cold_chunks = std::min(chunks, std::ceil(sh.cold / 32.0) + 1.0);
     const double cold_frac = it.len ? std::min(1.0, sh.cold / (double)it.len) : 1.0;
     const double cold_steps = std::min(steps, std::ceil(steps * cold_frac) + 1.0);
-    const double direct_cost = cold_chunks * step_ns + (chunks - cold_chunks) * held_ns;
-    const double queued_cost =
-        cold_steps * step_ns + (steps - cold_steps) * held_ns + chunks * kGatherNs;
-    u.direct = K == 1 && direct_cost <= queued_cost;
-    u.arena = align16(u.arena) + (u.direct ? 0u : kStageBytes);
-    u.cost = u.direct ? direct_cost : queued_cost;
+    bool have = false;
+    for (int k = 0; k < n_opt; ++k) {
+        const Option &o = opt[k];
+        const double direct_cost = cold_chunks * o.cold_ns + (chunks - cold_chunks) * o.warm_ns;
+        const double queued_cost = cold_steps * o.cold_ns + (steps - cold_steps) * o.warm_ns +
+                                   chunks * kGatherNs;
+        const bool direct = K == 1 && direct_cost <= queued_cost;
+        const uint64_t arena = align16(o.arena) + (direct ? 0u : kStageBytes);
+        const double cost = direct ? direct_cost : queued_cost;
+        const bool fits = arena <= kMaxArena;
+        // prefer options that fit; among those (or among none), the cheapest
+        if (!have || (fits && u.arena > kMaxArena) ||
+            ((fits || u.arena > kMaxArena) && cost < u.cost)) {
+            u.mode = o.mode;
+            u.ring = o.ring;
+            u.direct = direct;
+            u.arena = arena;
+            u.cost = cost;
+            have = true;
+        }
+    }
     return u.arena <= kMaxArena;
 }
 
@@ -575,7 +597,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         k_out = 1;
         unit_shape(G, base[i], 1, sh, tn, u_out);
         if (u_out.cost <= target) return;
-        for (uint32_t K = 2; K <= max_split && K <= sh.groups; ++K) {
+        for (uint32_t K = 2; K <= max_split && K <= sh.groups && K <= sh.visited; ++K) {
             const uint32_t odd = K % 3 == 0 ? K / 3 : K;
             if ((odd & (odd - 1)) != 0 || sh.groups % K != 0) continue;
             UnitShape u;
@@ -800,18 +822,20 @@ uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
 size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes) {
     std::string d;
     if (plan) {
-        uint64_t modes[3] = {0, 0, 0}, split = 0;
+        uint64_t modes[3] = {0, 0, 0}, split = 0, direct = 0;
         for (const SimItem &it : plan->items) {
             modes[it.mode < 3 ? it.mode : 0]++;
             split += it.kcnt > 1 && it.lead;
+            direct += it.direct;
         }
         char tmp[256];
         snprintf(tmp, sizeof tmp,
-                 "items=%llu units=%llu split=%llu scan=%llu table=%llu batch=%llu jumbo=%llu "
-                 "classes=%u warps=%u smem=%u slots=",
+                 "items=%llu units=%llu split=%llu scan=%llu table=%llu batch=%llu direct=%llu "
+                 "jumbo=%llu classes=%u warps=%u smem=%u slots=",
                  (unsigned long long)plan->n_items, (unsigned long long)plan->n_units,
                  (unsigned long long)split, (unsigned long long)modes[0],
                  (unsigned long long)modes[1], (unsigned long long)modes[2],
+                 (unsigned long long)direct,
                  (unsigned long long)plan->n_jumbo, plan->layout.nclasses, plan->layout.nwarps,
                  plan->layout.smem_bytes);
         d = tmp;

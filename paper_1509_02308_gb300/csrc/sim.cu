@@ -726,6 +726,13 @@ struct BatchLRU {
         // room for 32 entries in every held group's ring (else compact first)
         if (pure && __all_sync(kFull, !gheld || m0.y - m0.x <= R - 64)) {
             const uint32_t lb = __ballot_sync(kFull, last && gheld);
+            // a held group that re-uses exactly its set's D oldest lines (a
+            // cyclic stream) leaves a stale prefix: the tail moves past it and
+            // a compact ring stays compact
+            const uint32_t D = __popc(lb & sm0);
+            const bool front = gheld && pm0 == 0 && ((w0 - 1u - m0.x) & rmask) < D;
+            const uint32_t fb = __ballot_sync(kFull, gheld && pm0 == 0);
+            const uint32_t ob = __ballot_sync(kFull, front);
             uint32_t *rg0 = ring + (size_t)(gheld ? set : 0u) * R;
             if (gheld && pm0 == 0) rg0[w0 - 1] = kStale;
             __syncwarp();
@@ -734,8 +741,10 @@ struct BatchLRU {
                 rg0[p] = line;
                 tab[line] = (uint16_t)(p + 1);
             }
-            if (gheld && (sm0 & ~(lt | (1u << lane))) == 0)
-                meta[set] = make_uint4(m0.x, m0.y + __popc(lb & sm0), m0.z, 0u);
+            if (gheld && (sm0 & ~(lt | (1u << lane))) == 0) {
+                const bool adv = m0.w && (ob & sm0) == (fb & sm0);
+                meta[set] = make_uint4(adv ? m0.x + D : m0.x, m0.y + D, m0.z, adv ? 1u : 0u);
+            }
             __syncwarp();
             for (uint32_t todo = nlead; todo; todo &= todo - 1) {
                 const int ld = __ffs(todo) - 1;
