@@ -161,8 +161,8 @@ class ClockSampler:
 
 # From one ncu capture (--set full) of the current sim_kernel on the batched
 # workload with items capped at 65,536 accesses.
-SIM_DRAM_BYTES_PER_ACCESS = (265.340672e6 + 7.8336e6) / 65559830
-SIM_WARP_INST_PER_ACCESS = 558339136 / 65559830
+SIM_DRAM_BYTES_PER_ACCESS = (265.908224e6 + 7.31008e6) / 65559830
+SIM_WARP_INST_PER_ACCESS = 359570620 / 65559830
 
 
 def measured_peaks():
