@@ -328,6 +328,16 @@ __device__ __forceinline__ Grouped group_heads(uint32_t line, uint32_t set, bool
     return g;
 }
 
+// x mod a for x < 4a (else the division)
+__device__ __forceinline__ uint32_t mod_ways(uint32_t x, uint32_t a) {
+    if (x < 4u * a) {
+        if (x >= 2u * a) x -= 2u * a;
+        if (x >= a) x -= a;
+        return x;
+    }
+    return x % a;
+}
+
 // mask of lanes whose key is below this lane's threshold (keys, thresholds < 64)
 __device__ __forceinline__ uint32_t lanes_below(uint32_t key, uint32_t thr) {
     uint32_t less = 0, eq = kFull;
@@ -401,7 +411,7 @@ struct BatchFR {
         bool evicts;
         if (POLICY == PCHASE_FIFO) {
             evicts = m.y + r >= a;
-            insw = (m.x + m.y + r) % a;
+            insw = mod_ways(m.x + m.y + r, a);
         } else {
             const uint32_t k = m.x + r;
             evicts = k >= a;
@@ -424,7 +434,7 @@ struct BatchFR {
             if (POLICY == PCHASE_FIFO) {
                 const uint32_t tot = m.y + M;
                 n.y = tot < a ? tot : a;
-                n.x = (m.x + (tot > a ? tot - a : 0u)) % a;
+                n.x = mod_ways(m.x + (tot > a ? tot - a : 0u), a);
             } else {
                 const uint32_t tot = m.x + M;
                 n.x = tot < a ? tot : a;
@@ -464,7 +474,7 @@ struct BatchFR {
                     // held in way w, rho lines inserted before it: it leaves at
                     // the (a - L + rho + 1)-th miss of its set
                     const uint4 mf = head ? meta[set] : make_uint4(0, 0, 0, 0);
-                    const uint32_t rho = (w0 - 1u + ways - mf.x) % ways;
+                    const uint32_t rho = mod_ways(w0 - 1u + ways - mf.x, ways);
                     nohit = (uint32_t)__popc(sm0 & lt) >= ways - mf.y + rho + 1u;
                 }
             }
@@ -489,7 +499,7 @@ struct BatchFR {
         bool evicts;
         if (POLICY == PCHASE_FIFO) {
             evicts = m.y + r >= a;
-            insw = (m.x + m.y + r) % a;
+            insw = mod_ways(m.x + m.y + r, a);
         } else {
             const uint32_t k = m.x + r;
             evicts = k >= a;
@@ -504,7 +514,7 @@ struct BatchFR {
         // eviction index of this line's way (first group rank targeting it)
         int32_t e0 = -1;
         if (POLICY == PCHASE_FIFO) {
-            if (w1) e0 = (int32_t)(((w1 - 1 + a - m.x) % a) + (a - m.y));
+            if (w1) e0 = (int32_t)(mod_ways(w1 - 1 + a - m.x, a) + (a - m.y));
         } else {
             if (g.act && (sw & lt) == 0) scr[g.set * a + insw] = make_uint2(stamp, r);
             __syncwarp();
@@ -554,7 +564,7 @@ struct BatchFR {
             if (POLICY == PCHASE_FIFO) {
                 const uint32_t tot = m.y + M;
                 n.y = tot < a ? tot : a;
-                n.x = (m.x + (tot > a ? tot - a : 0u)) % a;
+                n.x = mod_ways(m.x + (tot > a ? tot - a : 0u), a);
             } else {
                 const uint32_t tot = m.x + M;
                 n.x = tot < a ? tot : a;
@@ -693,10 +703,10 @@ struct BatchLRU {
         // of such groups (at most 8 of the second kind) skip the general path.
         const uint32_t hb = __ballot_sync(kFull, head);
         if (hb == 0) return false;
-        const uint32_t w0 = head ? tab[line] : 1u;
+        uint32_t w0 = head ? tab[line] : 1u;
         const uint32_t sm0 = __match_any_sync(kFull, head ? set : (0x80000000u | (uint32_t)lane));
         const uint32_t lm0 = __match_any_sync(kFull, head ? line : (0x80000000u | (uint32_t)lane));
-        const uint4 m0 = head ? meta[set] : make_uint4(0, 0, 0, 0);
+        uint4 m0 = head ? meta[set] : make_uint4(0, 0, 0, 0);
         const uint32_t pm0 = lm0 & lt;
         const bool last = head && (lm0 & ~(lt | (1u << lane))) == 0;
         const uint32_t hbal = __ballot_sync(kFull, head && w0 != 0u);
@@ -707,8 +717,12 @@ struct BatchLRU {
             const int prev = pm0 ? 31 - __clz(pm0) : -1;
             const uint32_t pkey = head ? (uint32_t)(prev + 1) : 63u;
             const uint32_t pthr = prev < 0 ? 0u : (uint32_t)prev + 1;
-            const uint32_t between = lanes_below(pkey, pthr) & sm0 & lt &
-                                     ~((prev < 0) ? 0u : ((2u << prev) - 1u));
+            // distinct lines between a repeat and its previous use (none
+            // needed when no line repeats inside the step)
+            uint32_t between = 0;
+            if (__any_sync(kFull, prev >= 0))
+                between = lanes_below(pkey, pthr) & sm0 & lt &
+                          ~((prev < 0) ? 0u : ((2u << prev) - 1u));
             // a held first use at depth d leaves once d plus the distinct
             // lines before it in the step reach a (exact depth needs a
             // compact ring)
@@ -723,8 +737,19 @@ struct BatchLRU {
             nlead = __ballot_sync(kFull, gnohit && (sm0 & lt) == 0);
             pure = __all_sync(kFull, !head || gheld || gnohit) && __popc(nlead) <= 8;
         }
-        // room for 32 entries in every held group's ring (else compact first)
-        if (pure && __all_sync(kFull, !gheld || m0.y - m0.x <= R - 64)) {
+        if (pure && __any_sync(kFull, gheld)) {
+            // room for 32 entries in every held group's ring: compact the ones
+            // nearly full (the lines keep their order; positions move)
+            const uint32_t full =
+                __ballot_sync(kFull, gheld && (sm0 & lt) == 0 && m0.y - m0.x > R - 64);
+            if (full) {
+                for (uint32_t todo = full; todo; todo &= todo - 1) {
+                    const uint32_t s0 = __shfl_sync(kFull, set, __ffs(todo) - 1);
+                    compact(s0, meta[s0], lane, lt);
+                }
+                w0 = head ? tab[line] : 1u;
+                m0 = head ? meta[set] : make_uint4(0, 0, 0, 0);
+            }
             const uint32_t lb = __ballot_sync(kFull, last && gheld);
             // a held group that re-uses exactly its set's D oldest lines (a
             // cyclic stream) leaves a stale prefix: the tail moves past it and
@@ -746,6 +771,8 @@ struct BatchLRU {
                 meta[set] = make_uint4(adv ? m0.x + D : m0.x, m0.y + D, m0.z, adv ? 1u : 0u);
             }
             __syncwarp();
+        }
+        if (pure) {
             for (uint32_t todo = nlead; todo; todo &= todo - 1) {
                 const int ld = __ffs(todo) - 1;
                 const uint32_t s0 = __shfl_sync(kFull, set, ld);
