@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LRU, FIFO, RANDOM, REPLAY = 0, 1, 2, 3
+LRU, FIFO, RANDOM, REPLAY, WEIGHTED = 0, 1, 2, 3, 4
 OK, EINVAL, ERANGE, ENOMEM = 0, 1, 2, 3
 
 _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
@@ -62,6 +62,14 @@ def lib():
             L.or_cache_sim.argtypes = [ctypes.c_uint32] * 4 + [
                 ctypes.c_int, ctypes.c_uint64, _u32p, ctypes.c_uint64,
                 ctypes.c_void_p, ctypes.c_uint64, _u8p, ctypes.c_void_p]
+            L.or_cache_sim_ext.argtypes = [ctypes.c_uint32] * 4 + [
+                ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, _u32p, ctypes.c_uint64,
+                ctypes.c_void_p, ctypes.c_uint64, _u8p, ctypes.c_void_p,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                ctypes.POINTER(ctypes.c_uint64)]
+            L.or_weighted_victim.argtypes = [ctypes.c_uint64, ctypes.c_uint32,
+                                             ctypes.c_uint64, ctypes.c_uint32]
+            L.or_weighted_victim.restype = ctypes.c_uint32
             L.or_cache_sim_counts.argtypes = [ctypes.c_uint32] * 4 + [
                 ctypes.c_int, ctypes.c_uint64, _u32p, ctypes.c_uint64, ctypes.c_uint64,
                 ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
@@ -117,10 +125,18 @@ def random_victim(seed: int, set_: int, k: int, ways: int) -> int:
     return int(lib().or_random_victim(seed & 0xFFFFFFFFFFFFFFFF, set_, k, ways))
 
 
+def weighted_victim(seed: int, set_: int, k: int, ways: int) -> int:
+    return int(lib().or_weighted_victim(seed & 0xFFFFFFFFFFFFFFFF, set_, k, ways))
+
+
 # ----------------------------------------------------------------------- cache
 def cache_sim(C: int, b: int, ways: int, T: int, policy: int, trace: np.ndarray,
-              seed: int = 0, victims=None, want_final: bool = False):
-    """Per-access miss flags (uint8, 1 = miss) of one replay; see or_cache_sim."""
+              seed: int = 0, victims=None, want_final: bool = False, mapping: int = 0,
+              want_evictions: bool = False):
+    """Per-access miss flags (uint8, 1 = miss) of one replay; see or_cache_sim_ext.
+
+    want_final adds the line held by each way (T*ways, 0xFFFFFFFF when invalid);
+    want_evictions adds (sets, ways) of every eviction in order."""
     trace = np.ascontiguousarray(trace, dtype=np.uint32)
     out = np.empty(trace.size, dtype=np.uint8)
     vic_p, nv = None, 0
@@ -128,11 +144,23 @@ def cache_sim(C: int, b: int, ways: int, T: int, policy: int, trace: np.ndarray,
         vic = np.ascontiguousarray(victims, dtype=np.uint32)
         vic_p, nv = vic.ctypes.data, vic.size
     fin = np.empty(T * ways, dtype=np.uint32) if want_final else None
-    rc = lib().or_cache_sim(C, b, ways, T, policy, seed & 0xFFFFFFFFFFFFFFFF, trace,
-                            trace.size, vic_p, nv, out,
-                            fin.ctypes.data if fin is not None else None)
+    cap = trace.size if want_evictions else 0
+    es = np.empty(max(cap, 1), dtype=np.uint32)
+    ew = np.empty(max(cap, 1), dtype=np.uint32)
+    n_ev = ctypes.c_uint64()
+    rc = lib().or_cache_sim_ext(C, b, ways, T, policy, seed & 0xFFFFFFFFFFFFFFFF, mapping,
+                                trace, trace.size, vic_p, nv, out,
+                                fin.ctypes.data if fin is not None else None,
+                                es.ctypes.data if cap else None,
+                                ew.ctypes.data if cap else None, cap, ctypes.byref(n_ev))
     _check(rc, "cache_sim")
-    return (out, fin) if want_final else out
+    res = [out]
+    if want_final:
+        res.append(fin)
+    if want_evictions:
+        n = int(n_ev.value)
+        res += [es[:n].copy(), ew[:n].copy()]
+    return tuple(res) if len(res) > 1 else out
 
 
 def cache_sim_counts(C, b, ways, T, policy, trace, warmup, seed=0):

@@ -28,6 +28,7 @@
 #define OR_FIFO 1
 #define OR_RANDOM 2
 #define OR_REPLAY 3
+#define OR_WEIGHTED 4
 
 /* ------------------------------------------------------------------------ */
 /* P-chase array and chain walk                                              */
@@ -87,6 +88,22 @@ uint32_t or_random_victim(uint64_t seed, uint32_t set, uint64_t k, uint32_t ways
     return (uint32_t)(((h >> 32) * (uint64_t)ways) >> 32);
 }
 
+/* Victim way of the k-th eviction (0-based) in set `set` under the weighted
+ * policy the paper measures on the Fermi L1 data cache (Sec. 4.5): way 2 is
+ * replaced once every two misses and is three times as likely to go as each
+ * other way (1/6, 1/2, 1/6, 1/6 on four ways).  The reading used here: the
+ * evictions k = 0, 2, 4, ... take way 2; the others take one of the remaining
+ * ways uniformly, keyed like RANDOM on (seed, set, k), the high 32 bits
+ * mapped onto [0, ways - 1) and stepped past way 2.  Needs ways >= 3. */
+uint32_t or_weighted_victim(uint64_t seed, uint32_t set, uint64_t k, uint32_t ways)
+{
+    if (k % 2 == 0) return 2;
+    uint64_t key = seed ^ ((uint64_t)set << 40) ^ k;
+    uint64_t h = or_splitmix64(key);
+    uint32_t r = (uint32_t)(((h >> 32) * (uint64_t)(ways - 1)) >> 32);
+    return r < 2 ? r : r + 1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Set-associative cache                                                     */
 /* ------------------------------------------------------------------------ */
@@ -108,47 +125,56 @@ static int or_geom_ok(uint32_t C, uint32_t b, uint32_t ways, uint32_t T)
  *
  * The model is the classical one of Sec. 4.1 (Assumptions 1-3, Fig. 2):
  *   byte address = 4 * index;  line = address / b;
- *   set = line mod T (the set bits sit right above the offset bits, which for
- *   T a power of two is Assumption 2 and for other T is its modular reading);
- *   tag = line / T.
- * An access hits when its tag is held by a valid way of its set.  On a miss
+ *   set = (line >> mapping) mod T;  a way holds a whole line number.
+ * mapping = 0: the set bits sit right above the offset bits, which for T a
+ * power of two is Assumption 2 and for other T is its modular reading.
+ * mapping = m > 0: the set bits sit m bits higher, as the paper finds for the
+ * texture L1 cache (Sec. 4.3: bits 7-8 with 32-byte lines, m = 2), so 2^m
+ * consecutive lines share a set.
+ * An access hits when its line is held by a valid way of its set.  On a miss
  * the line goes into the lowest-numbered invalid way; when the set is full a
  * victim is chosen:
- *   LRU    (Assumption 3): the way whose last use is oldest;
- *   FIFO   : the way whose fill is oldest;
- *   RANDOM : or_random_victim(seed, set, k), k = evictions so far in the set;
- *   REPLAY : victims[e], e = evictions so far in the whole cache (the way
- *            numbers a caller read off a transcript such as Fig. 9).
- * Only LRU records a use on a hit.
+ *   LRU      (Assumption 3): the way whose last use is oldest;
+ *   FIFO     : the way whose fill is oldest;
+ *   RANDOM   : or_random_victim(seed, set, k), k = evictions so far in the set;
+ *   WEIGHTED : or_weighted_victim(seed, set, k), k as for RANDOM;
+ *   REPLAY   : victims[e], e = evictions so far in the whole cache (the way
+ *              numbers a caller read off a transcript such as Fig. 9).
+ * Only LRU records a use on a hit.  When evict_set / evict_way are given, the
+ * set and way of the first `evict_cap` evictions are written there and the
+ * number of evictions to *n_evict.
  */
-int or_cache_sim(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int policy,
-                 uint64_t seed, const uint32_t *trace, uint64_t len,
-                 const uint32_t *victims, uint64_t n_victims,
-                 uint8_t *miss_out, uint32_t *final_tags /* T*ways or NULL */)
+int or_cache_sim_ext(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int policy,
+                     uint64_t seed, uint32_t mapping, const uint32_t *trace, uint64_t len,
+                     const uint32_t *victims, uint64_t n_victims,
+                     uint8_t *miss_out, uint32_t *final_lines /* T*ways or NULL */,
+                     uint32_t *evict_set, uint32_t *evict_way, uint64_t evict_cap,
+                     uint64_t *n_evict)
 {
     if (!or_geom_ok(C, b, ways, T)) return OR_EINVAL;
-    if (policy < OR_LRU || policy > OR_REPLAY) return OR_EINVAL;
+    if (policy < OR_LRU || policy > OR_WEIGHTED) return OR_EINVAL;
+    if (policy == OR_WEIGHTED && ways < 3) return OR_EINVAL;
+    if (mapping > 16) return OR_EINVAL;
     uint64_t nlines = (uint64_t)T * ways;
-    uint64_t *tag = (uint64_t *)malloc(nlines * sizeof(uint64_t));
+    uint64_t *held = (uint64_t *)malloc(nlines * sizeof(uint64_t));
     uint8_t *valid = (uint8_t *)calloc(nlines, 1);
     uint64_t *last_use = (uint64_t *)malloc(nlines * sizeof(uint64_t));
     uint64_t *filled_at = (uint64_t *)malloc(nlines * sizeof(uint64_t));
     uint64_t *evictions = (uint64_t *)calloc(T, sizeof(uint64_t));
-    if (!tag || !valid || !last_use || !filled_at || !evictions) {
-        free(tag); free(valid); free(last_use); free(filled_at); free(evictions);
+    if (!held || !valid || !last_use || !filled_at || !evictions) {
+        free(held); free(valid); free(last_use); free(filled_at); free(evictions);
         return OR_ENOMEM;
     }
-    uint64_t replay_next = 0;
+    uint64_t replay_next = 0, n_ev = 0;
     int rc = OR_OK;
     for (uint64_t t = 0; t < len; t++) {
         uint64_t addr = 4ull * trace[t];
         uint64_t line = addr / b;
-        uint32_t set = (uint32_t)(line % T);
-        uint64_t tg = line / T;
+        uint32_t set = (uint32_t)((line >> mapping) % T);
         uint64_t base = (uint64_t)set * ways;
         int hit_way = -1;
         for (uint32_t w = 0; w < ways; w++) {
-            if (valid[base + w] && tag[base + w] == tg) { hit_way = (int)w; break; }
+            if (valid[base + w] && held[base + w] == line) { hit_way = (int)w; break; }
         }
         if (hit_way >= 0) {
             miss_out[t] = 0;
@@ -171,27 +197,43 @@ int or_cache_sim(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int policy,
                     if (filled_at[base + w] < filled_at[base + victim]) victim = w;
             } else if (policy == OR_RANDOM) {
                 victim = or_random_victim(seed, set, evictions[set], ways);
+            } else if (policy == OR_WEIGHTED) {
+                victim = or_weighted_victim(seed, set, evictions[set], ways);
             } else {
                 if (replay_next >= n_victims) { rc = OR_ERANGE; break; }
                 victim = victims[replay_next++];
                 if ((uint64_t)victim >= ways) { rc = OR_ERANGE; break; }
             }
             evictions[set]++;
+            if (evict_set && evict_way && n_ev < evict_cap) {
+                evict_set[n_ev] = set;
+                evict_way[n_ev] = (uint32_t)victim;
+            }
+            n_ev++;
         }
-        tag[base + victim] = tg;
+        held[base + victim] = line;
         valid[base + victim] = 1;
         last_use[base + victim] = t;
         filled_at[base + victim] = t;
     }
-    if (final_tags) {
-        /* line numbers held by each way, 0xFFFFFFFF for an invalid way */
-        for (uint64_t i = 0; i < nlines; i++) {
-            uint32_t set = (uint32_t)(i / ways);
-            final_tags[i] = valid[i] ? (uint32_t)(tag[i] * T + set) : 0xFFFFFFFFu;
-        }
+    if (final_lines) {
+        /* line number held by each way, 0xFFFFFFFF for an invalid way */
+        for (uint64_t i = 0; i < nlines; i++)
+            final_lines[i] = valid[i] ? (uint32_t)held[i] : 0xFFFFFFFFu;
     }
-    free(tag); free(valid); free(last_use); free(filled_at); free(evictions);
+    if (n_evict) *n_evict = n_ev;
+    free(held); free(valid); free(last_use); free(filled_at); free(evictions);
     return rc;
+}
+
+/* The standard mapping (mapping = 0) without an eviction record. */
+int or_cache_sim(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int policy,
+                 uint64_t seed, const uint32_t *trace, uint64_t len,
+                 const uint32_t *victims, uint64_t n_victims,
+                 uint8_t *miss_out, uint32_t *final_tags /* T*ways or NULL */)
+{
+    return or_cache_sim_ext(C, b, ways, T, policy, seed, 0, trace, len, victims, n_victims,
+                            miss_out, final_tags, NULL, NULL, 0, NULL);
 }
 
 /* Miss counts of one replay: total, and after the first `warmup` accesses. */

@@ -147,6 +147,78 @@ def test_texture_l1_sweep_fig5_shape():
         prev = per[2]
 
 
+def test_texture_l1_bits_7_8_mapping_sweep():
+    """Sec. 4.3: the texture L1 cache (12 KB, 32 B lines, 4 sets of 96) takes its
+    set from address bits 7-8, so each 128-byte block (4 lines) sits in one set
+    (mapping = 2 line bits above the offset).  Under LRU a set cycling through
+    n > 96 lines misses on every access and any other set hits, so with
+    N = 12 KB + d lines (s = 32 B) set i holds 96 + clamp(d - 4i, 0, 4) lines."""
+    C, b, T, a = 12 * 1024, 32, 4, 96
+    for d in range(0, 17):
+        nb = C + d * b
+        n_elems = nb // 4
+        tr = oracle.pchase_trace(n_elems, b // 4, 3 * (nb // b))
+        m = oracle.cache_sim(C, b, a, T, oracle.LRU, tr, mapping=2)
+        per = nb // b
+        counts = [a + min(max(d - 4 * i, 0), 4) for i in range(T)]
+        want = sum(c for c in counts if c > a)
+        assert m[2 * per:].sum() == want, d
+        # the standard mapping spreads the same lines one per set instead
+        ms = oracle.cache_sim(C, b, a, T, oracle.LRU, tr)
+        want_std = 0 if d == 0 else (d * (a + 1) if d <= T else per)
+        assert ms[2 * per:].sum() == want_std, d
+    # read-only / texture cache: above 12.5 KB every access misses (Sec. 4.3)
+    for kb in (12.75, 16, 24, 60):
+        nb = int(kb * 1024)
+        tr = oracle.pchase_trace(nb // 4, b // 4, 3 * (nb // b))
+        m = oracle.cache_sim(C, b, a, T, oracle.LRU, tr, mapping=2)
+        assert m[nb // b:].all(), kb
+
+
+def test_mapping_zero_is_the_standard_mapping():
+    for g in W.random_small_geoms(30, seed=21, max_lines=32):
+        tr = W.random_index_trace(400, g.C // 4 * 3, seed=g.seed % 977)
+        a = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed)
+        b = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed, mapping=0)
+        assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------- weighted
+def test_weighted_policy_fermi_l1_properties():
+    """Sec. 4.5 (Fermi L1 data cache, 16 KB, 128 B lines, 4 ways, 32 sets): way 2
+    is replaced once every two misses, and the four ways go with probabilities
+    1/6, 1/2, 1/6, 1/6."""
+    from scipy.stats import chisquare
+    C, b, a, T = 16384, 128, 4, 32
+    for seed in (1, 7, 0xFE12):
+        n = 129 * b // 4  # 129 lines: one line over, all misses in one set
+        tr = oracle.pchase_trace(n, b // 4, 400 * 129)
+        m, es, ew = oracle.cache_sim(C, b, a, T, oracle.WEIGHTED, tr, seed=seed,
+                                     want_evictions=True)
+        assert set(es.tolist()) == {0}  # only the overflowing set evicts
+        assert (ew[0::2] == 2).all()    # every other eviction takes way 2
+        assert (ew[1::2] != 2).all()
+        cnt = np.bincount(ew[1::2], minlength=4)
+        assert chisquare(cnt[[0, 1, 3]]).pvalue > 1e-3
+        assert abs((ew == 2).mean() - 0.5) <= 1.0 / len(ew)
+        # the 129th line sometimes misses and sometimes hits (Fig. 9's text),
+        # and the set misses less often than under LRU, where all of its
+        # accesses miss
+        pos = np.arange(len(tr))
+        late = pos >= 2 * 129
+        is128 = (tr // (b // 4)) == 128
+        assert m[late & is128].any() and not m[late & is128].all()
+        ml = oracle.cache_sim(C, b, a, T, oracle.LRU, tr)
+        set0 = (tr // (b // 4)) % T == 0
+        assert ml[late & set0].all() and m[late & set0].mean() < 1.0
+
+
+def test_weighted_policy_needs_three_ways():
+    tr = np.arange(10, dtype=np.uint32)
+    with pytest.raises(oracle.OracleError):
+        oracle.cache_sim(64, 32, 2, 1, oracle.WEIGHTED, tr)
+
+
 # --------------------------------------------------------------- invariants
 def test_all_hits_after_warmup_when_array_fits():
     for g in W.random_small_geoms(40, seed=11, max_lines=32):
@@ -194,18 +266,18 @@ def test_direct_mapped_policies_agree():
 
 
 # ------------------------------------------------------ brute force vs lists
-def _list_model(C, b, a, T, policy, seed, trace):
+def _list_model(C, b, a, T, policy, seed, trace, mapping=0):
     """Sets as Python lists: LRU keeps recency order, FIFO insertion order,
-    RANDOM explicit way slots.  Written independently of the oracle's
-    stamp-based bookkeeping."""
+    RANDOM and WEIGHTED explicit way slots.  Written independently of the
+    oracle's stamp-based bookkeeping."""
     sets = [[] for _ in range(T)]
     slots = [[None] * a for _ in range(T)]
     ev = [0] * T
     out = []
     for idx in trace:
         line = (4 * int(idx)) // b
-        s = line % T
-        if policy == oracle.RANDOM:
+        s = (line >> mapping) % T
+        if policy in (oracle.RANDOM, oracle.WEIGHTED):
             if line in slots[s]:
                 out.append(0)
                 continue
@@ -213,7 +285,8 @@ def _list_model(C, b, a, T, policy, seed, trace):
             if None in slots[s]:
                 slots[s][slots[s].index(None)] = line
             else:
-                slots[s][oracle.random_victim(seed, s, ev[s], a)] = line
+                pick = oracle.random_victim if policy == oracle.RANDOM else oracle.weighted_victim
+                slots[s][pick(seed, s, ev[s], a)] = line
                 ev[s] += 1
             continue
         lst = sets[s]
@@ -245,6 +318,27 @@ def test_bruteforce_tiny_caches_random_traces():
                         got = oracle.cache_sim(lines * b, b, a, T, policy, tr, seed=77)
                         want = _list_model(lines * b, b, a, T, policy, 77, tr)
                         assert np.array_equal(got, want), (b, lines, a, policy, tr)
+                        n_checked += 1
+    assert n_checked > 1000
+
+
+def test_bruteforce_mappings_and_weighted_policy():
+    rng = np.random.Generator(np.random.PCG64(77))
+    n_checked = 0
+    for b in (4, 8):
+        for (a, T) in ((1, 4), (2, 2), (3, 2), (4, 1), (4, 3), (2, 6)):
+            for mapping in (0, 1, 2, 3):
+                for policy in (oracle.LRU, oracle.FIFO, oracle.RANDOM, oracle.WEIGHTED):
+                    if policy == oracle.WEIGHTED and a < 3:
+                        continue
+                    for _ in range(8):
+                        L = int(rng.integers(1, 60))
+                        n_lines = int(rng.integers(1, 4 * a * T * (1 << mapping) + 2))
+                        tr = rng.integers(0, n_lines * b // 4, size=L).astype(np.uint32)
+                        got = oracle.cache_sim(a * T * b, b, a, T, policy, tr, seed=5,
+                                               mapping=mapping)
+                        want = _list_model(a * T * b, b, a, T, policy, 5, tr, mapping)
+                        assert np.array_equal(got, want), (b, a, T, mapping, policy, tr)
                         n_checked += 1
     assert n_checked > 1000
 
