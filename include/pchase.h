@@ -55,18 +55,29 @@ typedef enum {
 #define PCHASE_DEV_CHAIN_RANGE 2u   /* a chain pointed outside its array; the walk stopped */
 #define PCHASE_DEV_TIMEOUT 4u       /* a probe's iteration cap, or a bounded wait, ended a loop */
 
-typedef enum { PCHASE_LRU = 0, PCHASE_FIFO = 1, PCHASE_RANDOM = 2 } pchase_policy;
+typedef enum {
+    PCHASE_LRU = 0,
+    PCHASE_FIFO = 1,
+    PCHASE_RANDOM = 2,
+    PCHASE_WEIGHTED = 3 /* the Fermi L1 data cache's policy (Sec. 4.5), see below */
+} pchase_policy;
 
 /*
  * Cache geometry (Assumption 1, Sec. 4.1): `sets` (T) sets of `ways` (a) lines
  * of `line_bytes` (b) bytes, C = T*a*b.  b must be a power of two >= 4.
- * Lines map to sets by set = line mod T with line = (4*index) / b (the
- * modular reading of Assumption 2; `mapping` must be 0).  Replacement:
- * LRU (Assumption 3), FIFO, or RANDOM, whose k-th eviction in set s takes way
+ * Lines map to sets by set = (line >> mapping) mod T with line = (4*index) / b:
+ * mapping 0 is the modular reading of Assumption 2; mapping m (at most 16)
+ * puts the set bits m bits higher, so 2^m consecutive lines share a set (the
+ * texture L1 cache of Sec. 4.3 is b = 32, T = 4, mapping 2: address bits 7-8).
+ * Replacement: LRU (Assumption 3), FIFO, RANDOM, whose k-th eviction in set s
+ * takes way
  *   floor(((h >> 32) * a) / 2^32),  h = SplitMix64(seed ^ (s << 40) ^ k),
  * SplitMix64 being the first output of Steele-Lea-Flood's generator whose
- * state is its argument.  A miss fills the lowest-numbered invalid way first.
- * 32 bytes.
+ * state is its argument, or WEIGHTED (a >= 3): evictions k = 0, 2, 4, ... of
+ * set s take way 2, the others way r or r + 1 (r < 2 or r >= 2), where
+ * r = floor(((h >> 32) * (a - 1)) / 2^32) with h as for RANDOM; on four ways
+ * that replaces way 2 half of the time and each other way a sixth.  A miss
+ * fills the lowest-numbered invalid way first.  32 bytes.
  */
 typedef struct {
     uint32_t C_bytes;
@@ -74,8 +85,8 @@ typedef struct {
     uint32_t ways;
     uint32_t sets;
     uint32_t policy;  /* pchase_policy */
-    uint32_t mapping; /* 0: set = line mod T */
-    uint64_t seed;    /* RANDOM only */
+    uint32_t mapping; /* set = (line >> mapping) mod T; 0: set = line mod T */
+    uint64_t seed;    /* RANDOM and WEIGHTED only */
 } pchase_geom;
 
 /*

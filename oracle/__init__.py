@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LRU, FIFO, RANDOM, REPLAY, WEIGHTED = 0, 1, 2, 3, 4
+LRU, FIFO, RANDOM, WEIGHTED, REPLAY = 0, 1, 2, 3, 4
 OK, EINVAL, ERANGE, ENOMEM = 0, 1, 2, 3
 
 _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")

@@ -27,8 +27,8 @@
 #define OR_LRU 0
 #define OR_FIFO 1
 #define OR_RANDOM 2
-#define OR_REPLAY 3
-#define OR_WEIGHTED 4
+#define OR_WEIGHTED 3
+#define OR_REPLAY 4   /* oracle only: victims read off a transcript */
 
 /* ------------------------------------------------------------------------ */
 /* P-chase array and chain walk                                              */
@@ -152,7 +152,7 @@ int or_cache_sim_ext(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int poli
                      uint64_t *n_evict)
 {
     if (!or_geom_ok(C, b, ways, T)) return OR_EINVAL;
-    if (policy < OR_LRU || policy > OR_WEIGHTED) return OR_EINVAL;
+    if (policy < OR_LRU || policy > OR_REPLAY) return OR_EINVAL;
     if (policy == OR_WEIGHTED && ways < 3) return OR_EINVAL;
     if (mapping > 16) return OR_EINVAL;
     uint64_t nlines = (uint64_t)T * ways;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpchase.so")
 
 OK, EINVAL, ERANGE, ENOMEM, ETIMEOUT, ECUDA = range(6)
 DEV_INDEX_RANGE, DEV_CHAIN_RANGE, DEV_TIMEOUT = 1, 2, 4
-LRU, FIFO, RANDOM = 0, 1, 2
+LRU, FIFO, RANDOM, WEIGHTED = 0, 1, 2, 3
 
 _c_u32, _c_u64, _c_p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
 
@@ -151,7 +151,8 @@ def stream_handle(stream=None) -> int | None:
 def geom_array(geoms) -> ctypes.Array:
     arr = (Geom * max(1, len(geoms)))()
     for i, g in enumerate(geoms):
-        arr[i] = Geom(g.C, g.b, g.ways, g.sets, g.policy, 0, g.seed & 0xFFFFFFFFFFFFFFFF)
+        arr[i] = Geom(g.C, g.b, g.ways, g.sets, g.policy, getattr(g, "mapping", 0),
+                      g.seed & 0xFFFFFFFFFFFFFFFF)
     return arr
 
 

@@ -138,6 +138,15 @@ uint64_t gcd64(uint64_t a, uint64_t b) {
     return a;
 }
 
+// Largest line id a unit sees: (n_elems - 1) >> lsh, renumbered when the
+// mapping takes the set from higher bits (id = ((hi << m) | lo) * T + set).
+uint64_t top_line(const pchase_geom &G, uint32_t n_elems) {
+    const uint64_t top = (uint64_t)(n_elems - 1) / (G.line_bytes / 4);
+    if (!G.mapping) return top;
+    const uint64_t T = G.sets;
+    return ((top >> G.mapping) / T + 1) * (T << G.mapping) - 1;
+}
+
 void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
     const uint64_t sb = 4ull * (Tr.stride % Tr.n_elems);  // bytes between accesses
     const uint64_t b = G.line_bytes;
@@ -190,6 +199,15 @@ void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
             sh.cyclic = se == g;  // one ascending sweep a pass
         }
     }
+    if (G.mapping) {
+        // sets from higher line bits: only the bound over all line ids holds
+        sh.visited = (double)T;
+        sh.psh = 0;
+        sh.groups = (uint32_t)T;
+        sh.cyclic = false;
+        per_set = (top_line(G, Tr.n_elems) + T) / T;
+        if (Tr.stride && !se) per_set = 1;
+    }
     sh.held = per_set <= G.ways;
     sh.cold = std::min((double)Tr.len, (double)pass);
 }
@@ -200,8 +218,8 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     const uint32_t T = G.sets, a = G.ways;
     const uint32_t Tl = T / K;
     const uint64_t lines = (uint64_t)Tl * a;
-    const uint32_t top = (it.n_elems - 1) >> it.lsh;  // largest line
-    const uint64_t table_n = K > 1 ? (uint64_t)Tl * (top / T + 1) : (uint64_t)top + 1;
+    const uint64_t top = top_line(G, it.n_elems);  // largest line id
+    const uint64_t table_n = K > 1 ? (uint64_t)Tl * (top / T + 1) : top + 1;
     const double parts = (double)K;
     const double vis = std::max(1.0, sh.visited / parts);
     const double rounds = std::ceil(32.0 / std::min(32.0, vis));
@@ -213,8 +231,10 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     uint32_t ring = 128;
     while (ring < a + 96) ring <<= 1;
     uint64_t batch = 256 + 16ull * Tl + 2ull * table_n;
+    // WEIGHTED runs the RANDOM code and costs like it
+    const bool randomish = G.policy == PCHASE_RANDOM || G.policy == PCHASE_WEIGHTED;
     if (G.policy == PCHASE_LRU) batch += 4ull * Tl * ring;
-    else batch += ((4 * lines + 15) & ~15ull) + (G.policy == PCHASE_RANDOM ? 8 * lines : 0);
+    else batch += ((4 * lines + 15) & ~15ull) + (randomish ? 8 * lines : 0);
     batch = align16(batch);
     u.sets = Tl;
     u.table_n = (uint32_t)std::min<uint64_t>(table_n, 0xFFFFFFFFull);
@@ -227,7 +247,7 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     const bool batch_ok = tn.batch_max_sets && (Tl <= tn.batch_max_sets || many_rounds) &&
                           kStageBytes + batch <= kMaxArena && ring <= 32768;
     const bool scan = a <= tn.scan_max_ways;
-    const int pol = G.policy < 3 ? G.policy : 0;
+    const int pol = randomish ? PCHASE_RANDOM : (int)G.policy;
     struct Option {
         uint32_t mode, ring;
         uint64_t arena;
@@ -252,7 +272,7 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
         const double round_ns = scan ? kStepScanNs[pol] + kRoundScanNs[pol] * (rounds - 1.0)
                                      : kStepTableNs[pol] + kRoundTableNs[pol] * (rounds - 1.0);
         Option o{scan ? kModeScan : kModeTable, 0u,
-                 scan ? 8 * lines + (G.policy == PCHASE_RANDOM ? 4ull * Tl : 0)
+                 scan ? 8 * lines + (randomish ? 4ull * Tl : 0)
                       : 8ull * Tl + 4 * lines + (G.policy == PCHASE_LRU ? 4 * lines : 0) +
                             2ull * table_n,
                  round_ns, round_ns};
@@ -316,8 +336,11 @@ int check_geom(const pchase_geom &g, uint32_t i) {
                  g.ways, g.line_bytes, g.C_bytes);
         return fail(PCHASE_EINVAL, buf);
     }
-    if (g.policy > PCHASE_RANDOM || g.mapping != 0) {
-        snprintf(buf, sizeof buf, "geometry %u: unknown policy %u or mapping %u", i, g.policy,
+    if (g.policy > PCHASE_WEIGHTED || g.mapping > 16 || (uint64_t)g.sets << g.mapping > (1ull << 30) ||
+        (g.policy == PCHASE_WEIGHTED && g.ways < 3)) {
+        snprintf(buf, sizeof buf,
+                 "geometry %u: unknown policy %u, mapping %u above 16 (or T << mapping above 2^30),"
+                 " or WEIGHTED with fewer than 3 ways", i, g.policy,
                  g.mapping);
         return fail(PCHASE_EINVAL, buf);
     }
@@ -557,7 +580,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         it.stride = Tr.stride % Tr.n_elems;
         it.ways = G.ways;
         it.policy = (uint8_t)G.policy;
-        it.lsh = ilog2(G.line_bytes) - 2;
+        it.lsh = (ilog2(G.line_bytes) - 2) | (G.mapping << 8);
         it.seed = G.seed;
         it.word_off = word;
         word += (Tr.len + 31) / 32;

@@ -52,11 +52,27 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-// Victim way of the k-th eviction of set `set` under the RANDOM policy.
+// Victim way of the k-th eviction of set `set` under the RANDOM policy, or
+// under WEIGHTED (the Fermi L1 data cache, Sec. 4.5): evictions 0, 2, 4, ...
+// take way 2, the others one of the remaining ways, seeded-uniform.
 __device__ __forceinline__ uint32_t random_way(uint64_t seed, uint32_t set, uint32_t k,
-                                               uint32_t ways) {
+                                               uint32_t ways, bool weighted) {
+    if (weighted && (k & 1u) == 0) return 2;
     uint64_t h = splitmix64(seed ^ ((uint64_t)set << 40) ^ (uint64_t)k);
-    return (uint32_t)(((h >> 32) * (uint64_t)ways) >> 32);
+    const uint32_t n = weighted ? ways - 1 : ways;
+    const uint32_t r = (uint32_t)(((h >> 32) * (uint64_t)n) >> 32);
+    return weighted && r >= 2 ? r + 1 : r;
+}
+
+// Line id under a mapping that takes the set from m line bits higher
+// (set = (line >> m) mod T): line = ((hi * T + set) << m) | lo becomes
+// ((hi << m) | lo) * T + set, a one-to-one renumbering under which
+// set = id mod T, so every set mode, table and split sees the usual form.
+__device__ __forceinline__ uint32_t remap_line(uint32_t ln, uint32_t m, uint32_t T, uint32_t tm,
+                                               uint32_t ts1, uint32_t ts2) {
+    const uint32_t u = ln >> m;
+    const uint32_t hi = div_q(u, tm, ts1, ts2);
+    return (((hi << m) | (ln & ((1u << m) - 1u))) * T) + (u - hi * T);
 }
 
 // ------------------------------------------------------------ plan items
@@ -77,7 +93,7 @@ struct SimItem {
     uint32_t sets;        // local sets T' = T / K
     uint32_t magic_m;     // local set = local line mod T', by DivMagic of T'
     uint8_t s1, s2, policy, mode;
-    uint32_t lsh;         // line = index >> lsh  (b = 4 << lsh)
+    uint32_t lsh;         // line = index >> (lsh & 255) (b = 4 << that); lsh >> 8: mapping m
     uint32_t table_n;     // line-table entries (local lines)
     uint64_t seed;
     uint64_t word_off;    // plan-owned bitmap layout

@@ -64,11 +64,13 @@ struct ScanSets {
     uint32_t *evict;
     uint32_t ways;
     uint64_t seed;
+    bool wtd;                  // WEIGHTED victims (RANDOM code path)
     uint32_t psh, kcnt, kres;  // local -> global set (RANDOM's key)
 
     __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         seed = it.seed;
+        wtd = it.policy == PCHASE_WEIGHTED;
         psh = it.psh;
         kcnt = it.kcnt;
         kres = it.kres;
@@ -102,7 +104,7 @@ struct ScanSets {
         if (POLICY == PCHASE_RANDOM && best >= a) {
             const uint32_t k = evict[set];
             evict[set] = k + 1;
-            v = random_way(seed, global_set(set, psh, kcnt, kres), k, a);
+            v = random_way(seed, global_set(set, psh, kcnt, kres), k, a, wtd);
         }
         s[v] = make_uint2(line, t + a);
         return true;
@@ -124,11 +126,13 @@ struct TableSets {
     uint16_t *prv, *nxt, *tab;
     uint32_t ways;
     uint64_t seed;
+    bool wtd;
     uint32_t psh, kcnt, kres;
 
     __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         seed = it.seed;
+        wtd = it.policy == PCHASE_WEIGHTED;
         psh = it.psh;
         kcnt = it.kcnt;
         kres = it.kres;
@@ -213,7 +217,7 @@ struct TableSets {
                 v = m.x;
                 m.x += 1;
             } else {
-                v = random_way(seed, global_set(set, psh, kcnt, kres), m.y, a);
+                v = random_way(seed, global_set(set, psh, kcnt, kres), m.y, a, wtd);
                 m.y += 1;
                 tab[sline[base + v]] = 0;
             }
@@ -365,11 +369,13 @@ struct BatchFR {
     uint32_t *perm;
     uint32_t ways;
     uint64_t seed;
+    bool wtd;
     uint32_t psh, kcnt, kres;
 
     __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
         seed = it.seed;
+        wtd = it.policy == PCHASE_WEIGHTED;
         psh = it.psh;
         kcnt = it.kcnt;
         kres = it.kres;
@@ -415,7 +421,7 @@ struct BatchFR {
         } else {
             const uint32_t k = m.x + r;
             evicts = k >= a;
-            insw = evicts ? random_way(seed, global_set(set, psh, kcnt, kres), m.y + (k - a), a)
+            insw = evicts ? random_way(seed, global_set(set, psh, kcnt, kres), m.y + (k - a), a, wtd)
                           : k;
         }
         const uint32_t sw = __match_any_sync(kFull, head ? set * a + insw
@@ -503,7 +509,7 @@ struct BatchFR {
         } else {
             const uint32_t k = m.x + r;
             evicts = k >= a;
-            insw = evicts ? random_way(seed, global_set(g.set, psh, kcnt, kres), m.y + (k - a), a)
+            insw = evicts ? random_way(seed, global_set(g.set, psh, kcnt, kres), m.y + (k - a), a, wtd)
                           : k;
         }
         // next group rank with the same way
@@ -1063,7 +1069,8 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     // arena: [queue + staging ring (units that compact their heads)][set state]
     uint2 *const queue = reinterpret_cast<uint2 *>(g_smem + arena);
     uint8_t *const st = g_smem + arena + (it.direct ? 0u : kStageBytes);
-    const uint32_t kind = (uint32_t)it.mode * 3u + it.policy;
+    // WEIGHTED runs the RANDOM code with its own victim ways
+    const uint32_t kind = (uint32_t)it.mode * 3u + (it.policy < 2u ? it.policy : 2u);
     // matcher: a candidate whose other units already exceed the bound is out
     if (out.dist && over_bound(out, it.cand, 0, lane)) return;
     clear_state(kind, st, it, lane);
@@ -1071,7 +1078,8 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     const uint32_t len = it.len;
     const uint32_t *__restrict__ idxp = it.idx;
     const uint32_t N = it.n_elems;
-    const uint32_t lsh = it.lsh, sets = it.sets, mm = it.magic_m, s1 = it.s1, s2 = it.s2;
+    const uint32_t lsh = it.lsh & 255u, mk = it.lsh >> 8;  // line shift, mapping
+    const uint32_t sets = it.sets, mm = it.magic_m, s1 = it.s1, s2 = it.s2;
     const bool split = it.kcnt > 1;
     const uint32_t gT = it.gsets, gm = it.gmagic, gs1 = it.gs1, gs2 = it.gs2;
     const uint32_t psh = it.psh, K = it.kcnt, kres = it.kres;
@@ -1121,7 +1129,8 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
                 bad = 1;
                 active = false;
             }
-            const uint32_t ln = j >> lsh;
+            uint32_t ln = j >> lsh;
+            if (mk) ln = remap_line(ln, mk, gT, gm, gs1, gs2);
             const uint32_t set = ln - div_q(ln, mm, s1, s2) * sets;
             const uint32_t rot = __shfl_sync(kFull, ln, (lane + 31) & 31);
             const uint32_t prev = lane == 0 ? carry : rot;
@@ -1194,7 +1203,8 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
                     bad = 1;
                     valid = false;
                 }
-                const uint32_t ln = j >> lsh;
+                uint32_t ln = j >> lsh;
+                if (mk) ln = remap_line(ln, mk, gT, gm, gs1, gs2);
                 // one rotate: lane i gets lane i-1's line; lane 0 gets lane
                 // 31's, the previous access of the next chunk's lane 0
                 const uint32_t rot = __shfl_sync(kFull, ln, (lane + 31) & 31);

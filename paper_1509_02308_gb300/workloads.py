@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-LRU, FIFO, RANDOM = 0, 1, 2
+LRU, FIFO, RANDOM, WEIGHTED = 0, 1, 2, 3
 POLICY_NAMES = ("LRU", "FIFO", "RANDOM")
 _M64 = 0xFFFFFFFFFFFFFFFF
 _GAMMA = 0x9E3779B97F4A7C15
@@ -52,6 +52,7 @@ class Geom:
     sets: int
     policy: int = LRU
     seed: int = 0
+    mapping: int = 0  # set = (line >> mapping) mod T
 
     def row(self):
         return (self.C, self.b, self.ways, self.sets, self.policy)

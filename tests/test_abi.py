@@ -59,11 +59,24 @@ def _describe(h) -> dict:
     (W.Geom(1024, 32, 0, 32), C.EINVAL),      # no ways
     (W.Geom(1 << 22, 32, 1 << 17, 1), C.ERANGE),  # 131072 lines
     (W.Geom(1024, 32, 4, 8, 7), C.EINVAL),    # unknown policy
+    (W.Geom(1024, 32, 2, 16, 3), C.EINVAL),   # WEIGHTED needs 3 ways
+    (W.Geom(1024, 32, 4, 8, 0, mapping=17), C.EINVAL),  # mapping above 16
+    (W.Geom(1 << 20, 4, 1, 1 << 18, 0, mapping=13), C.EINVAL),  # T << mapping above 2^30
 ])
 def test_plan_rejects_bad_geometry(geom, code):
     rc, h = _plan([geom], [(None, 10, 0, 100, 1)])
     assert rc == code
     assert C.load().pchase_last_error_string()
+
+
+def test_plan_accepts_mapping_and_weighted_policy():
+    gs = [W.Geom(12288, 32, 96, 4, 0, mapping=2), W.Geom(16384, 128, 4, 32, 3, 5),
+          W.Geom(768, 16, 3, 16, 3, 9, mapping=4)]
+    rc, h = _plan(gs, [(None, 1000, 0, 3200, 8)])
+    assert rc == C.OK
+    d = _describe(h)
+    assert int(d["items"]) == 3
+    C.load().pchase_sim_plan_destroy(h)
 
 
 def test_plan_rejects_bad_trace_and_pair():
