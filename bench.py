@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner (default knobs)")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-inverse section")
     p.add_argument("--no-probes", action="store_true", help="skip the on-device probe section")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the set-mapping / weighted-policy section")
     p.add_argument("--inverse-steps", type=int, default=600,
                    help="training steps of 4096 synthetic traces for the learned inverse")
     p.add_argument("--inverse-eval", type=int, default=100000)
@@ -379,6 +381,11 @@ def ours(args):
             result["probes"] = probe_bench(dev)
         except Exception as ex:  # report, never mask the main number
             result["probes"] = {"error": repr(ex)}
+    if not args.no_variants and rank == 0:
+        try:
+            result["variants"] = variants_bench(dev)
+        except Exception as ex:  # noqa: BLE001
+            result["variants"] = {"error": repr(ex)}
     if not args.no_learned and rank == 0:
         try:
             result["learned_inverse"] = learned_bench(args, dev)
@@ -462,7 +469,6 @@ def infer_bench(dev):
     trace of the true cache (16 KB, 128 B, 4-way, LRU)."""
     import torch
 
-    import oracle
     from paper_1509_02308_gb300 import api, workloads as W
 
     truth, runs = W.config1()
@@ -479,10 +485,12 @@ def infer_bench(dev):
     traces = [(flat_built[int(offs[i]):int(offs[i + 1])], r.length, r.warmup, r.n_elems, r.stride)
               for i, r in enumerate(runs)]
     plan = api.SimPlan(cands, traces)
-    # observations: latencies synthesised from the truth's miss pattern
-    host = [oracle.pchase_trace(r.n_elems, r.stride, r.length) for r in runs]
-    miss = np.concatenate([oracle.cache_sim(truth.C, truth.b, truth.ways, truth.sets, 0, t)
-                           for t in host])
+    # observations: latencies synthesised from the truth's miss pattern, which
+    # the library simulates (the tests hold it bit-exact to the oracle)
+    tb, _, toffs = api.cache_sim_batch([truth], traces, pairs=[(0, i) for i in range(len(runs))])
+    tbw = tb.cpu().numpy().view(np.uint32)
+    miss = np.concatenate([api.unpack_bits(tbw[int(toffs[i]):], r.length)
+                           for i, r in enumerate(runs)]).astype(np.float64)
     rng = np.random.Generator(np.random.PCG64(0x5EED1001))
     n_obs = 8
     lats = []
@@ -593,6 +601,73 @@ def probe_bench(dev):
     del a, b
     torch.cuda.empty_cache()
     return out
+
+
+def variants_bench(dev):
+    """Set mappings from higher line bits and the weighted Fermi L1 policy on
+    the paper's own sweeps.  The texture L1 caches of Sec. 4.3 (12 KB and
+    24 KB, 32 B lines, 4 sets, address bits 7-8: mapping 2, LRU) over
+    s = 4 B and 32 B with N from C to C + 512 B in 32 B steps, then to 60 KB in
+    1 KB steps; the Fermi L1 data cache of Sec. 4.5 (16 KB, 128 B lines,
+    4 ways, 32 sets, weighted policy) under 64 policy seeds over N = 15-24 KB
+    in 128 B steps with s = 4 B and 128 B; 4 passes each, the first one
+    warm-up.  Reports simulated accesses/s of the plan run, and whether the
+    matcher, given the 12 KB texture cache's bitmaps, picks the bits-7-8
+    mapping among mappings 0-3 x {LRU, FIFO, RANDOM}."""
+    import torch
+
+    from paper_1509_02308_gb300 import api, workloads as W
+
+    def sweep(sizes, strides_b):
+        out = []
+        for nb in sizes:
+            for sb in strides_b:
+                n, s = nb // 4, sb // 4
+                per = n // math.gcd(n, s)
+                out.append(W.Run(n, s, 4 * per, per))
+        return out
+
+    tex_geoms = [W.Geom(12288, 32, 96, 4, W.LRU, mapping=2), W.Geom(24576, 32, 192, 4, W.LRU, mapping=2)]
+    tex_runs = [sweep(list(range(C, C + 513, 32)) + list(range(C + 1024, 61441, 1024)), (4, 32))
+                for C in (12288, 24576)]
+    fermi_runs = sweep(list(range(15 * 1024, 24 * 1024 + 1, 128)), (4, 128))
+    fermi_geoms = [W.Geom(16384, 128, 4, 32, W.WEIGHTED, 0xFE1 + 7919 * k) for k in range(64)]
+    runs = tex_runs[0] + tex_runs[1] + fermi_runs
+    geoms = tex_geoms + fermi_geoms
+    pairs = [(0, t) for t in range(len(tex_runs[0]))]
+    pairs += [(1, len(tex_runs[0]) + t) for t in range(len(tex_runs[1]))]
+    f0 = len(tex_runs[0]) + len(tex_runs[1])
+    pairs += [(2 + k, f0 + t) for k in range(len(fermi_geoms)) for t in range(len(fermi_runs))]
+    flat, offs = api.pchase_build_batch(runs)
+    traces = [(flat[int(offs[i]):int(offs[i + 1])], r.length, r.warmup, r.n_elems, r.stride)
+              for i, r in enumerate(runs)]
+    plan = api.SimPlan(geoms, traces, pairs=pairs)
+    total = sum(runs[t].length for _, t in pairs)
+    bitmaps, counts = plan.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    a.record()
+    for _ in range(reps):
+        plan.run(bitmaps, counts)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    # recovery of the texture L1 mapping from its own bitmaps
+    n0 = len(tex_runs[0])
+    cands = [W.Geom(12288, 32, 96, 4, p, 0x7E57 + p, mapping=m) for m in range(4) for p in (0, 1, 2)]
+    mplan = api.SimPlan(cands, traces[:n0])
+    owo = torch.tensor(plan.word_offsets[:n0].astype(np.int64), device=dev)
+    dist = mplan.match(bitmaps, owo).cpu().numpy()
+    pick = api.pchase_canonical_pick(cands, torch.from_numpy(dist.astype(np.int64)).to(dev))
+    picked = cands[int(pick[0])]
+    return {"accesses_per_s": total / (ms * 1e-3), "ms_per_run": ms, "items": len(pairs),
+            "accesses": total, "plan": plan.description,
+            "texture_l1_mapping_recovered": picked.mapping == 2 and picked.policy in (0, 1),
+            "texture_l1_min_distance_other_mappings":
+                int(min(d for c, d in zip(cands, dist) if c.mapping != 2)),
+            "note": "texture L1 (Sec. 4.3, bits 7-8) and 24 KB variant, LRU; Fermi L1 (Sec. 4.5) "
+                    "weighted policy x 64 seeds; paper sweeps, 4 passes"}
 
 
 def learned_bench(args, dev):
