@@ -600,7 +600,86 @@ def probe_bench(dev):
     out["peak_kind"] = f"{peak_kind} HBM copy bandwidth {peaks['hbm_gbs']} GB/s"
     del a, b
     torch.cuda.empty_cache()
+    out["smem_throughput"] = smem_throughput_sweep(dev)
+    out["latency_spectrum"] = latency_spectrum(dev)
     return out
+
+
+def latency_spectrum(dev, reps: int = 5):
+    """Sec. 5.2's non-uniform-stride P-chase on this GPU (Fig. 11's P1-P6):
+    the chain of workloads.spectrum_chain() walked once, cold, with L1 on
+    (ld.global.ca) and off (ld.global.cg); per segment the median latency in
+    cycles over `reps` walks, each after writing 512 MB to clear the caches."""
+    import torch
+
+    from paper_1509_02308_gb300 import api, workloads as W
+
+    path, labels, n = W.spectrum_chain()
+    arr = torch.zeros(n, dtype=torch.int32, device=dev)
+    arr[torch.tensor(path, dtype=torch.int64, device=dev)] = torch.tensor(
+        path[1:] + path[:1], dtype=torch.int32, device=dev)
+    lab = np.array(labels)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    out = {"segments": {"B_new_page": "1 MB stride, first access to a 2 MB page: cache miss, TLB miss (P5)",
+                        "B_same_page": "1 MB stride, page of the previous access: cache miss, TLB hit (P4)",
+                        "A_32MB": "32 MB stride over 2 GB: cache miss, TLB miss (P5/P6)",
+                        "C_revisit": "B's lines again after A's sweep: cache hit, TLB miss (P2/P3)",
+                        "D_same_line": "one 128-byte line: cache hit, TLB hit (P1)"}}
+    for mode, name in ((0, "l1_on_ld_ca"), (1, "l1_off_ld_cg")):
+        per = {k: [] for k in out["segments"]}
+        for _ in range(reps):
+            flush.fill_(1)
+            lat, vis, _, st = api.pchase_probe_latency(arr, n, iters=len(path), warmup=0,
+                                                       start=path[0], cache_mode=mode)
+            torch.cuda.synchronize()
+            if int(st.item()) or not np.array_equal(vis.cpu().numpy().view(np.uint32),
+                                                    np.array(path, dtype=np.uint32)):
+                return {"error": "the probe left the constructed chain"}
+            l = lat.cpu().numpy().view(np.uint32)
+            for k in per:
+                per[k].append(float(np.median(l[lab == k])))
+        out[name] = {k: float(np.median(v)) for k, v in per.items()}
+    del arr, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def smem_throughput_sweep(dev):
+    """Sec. 6.1's grid on this GPU: CTA size {32 .. 1024} x CTAs per SM {1 .. 6}
+    x ILP {1, 2, 4, 6, 8}, where the CTAs fit on an SM together (threads and
+    shared memory).  Throughput per SM in bytes per SM cycle (read + write,
+    as the paper counts), against 32 banks x 4 B = 128 B per cycle."""
+    import torch
+
+    from paper_1509_02308_gb300 import api
+
+    prop = torch.cuda.get_device_properties(dev)
+    max_thr = getattr(prop, "max_threads_per_multi_processor", 2048)
+    smem_sm = getattr(prop, "shared_memory_per_multiprocessor", 228 * 1024)
+    peaks, _ = measured_peaks()
+    f_mhz = peaks.get("sm_max_mhz", 2070.0)
+    best, best_cfg, by_warps = 0.0, None, {}
+    for threads in (32, 64, 128, 256, 512, 1024):
+        for per_sm in range(1, 7):
+            for ilp in (1, 2, 4, 6, 8):
+                cta_smem = 8 * ilp * threads
+                if threads * per_sm > max_thr or (cta_smem + 1024) * per_sm > smem_sm:
+                    continue
+                r = api.pchase_probe_smem_throughput(per_sm, threads, ilp, iters=2048)
+                if r["ctas_per_sm_seen"] != [per_sm, per_sm]:
+                    continue
+                bpc = r["bytes_per_cycle"]
+                warps = threads // 32 * per_sm
+                if bpc > by_warps.get(warps, (0.0,))[0]:
+                    by_warps[warps] = (bpc, {"threads": threads, "ctas_per_sm": per_sm,
+                                             "ilp": ilp})
+                if bpc > best:
+                    best, best_cfg = bpc, {"threads": threads, "ctas_per_sm": per_sm, "ilp": ilp,
+                                           "active_warps": warps}
+    return {"peak_bytes_per_sm_cycle": best, "theoretical_bytes_per_sm_cycle": 128.0,
+            "efficiency": best / 128.0, "best_config": best_cfg,
+            "peak_gbs_per_sm_at_max_clock": best * f_mhz * 1e6 / 1e9, "sm_max_mhz": f_mhz,
+            "peak_by_active_warps": {str(w): round(v[0], 2) for w, v in sorted(by_warps.items())}}
 
 
 def variants_bench(dev):

@@ -399,6 +399,22 @@ int pchase_probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas,
                                    uint64_t bytes, uint32_t reps, double *gbs_out,
                                    pchase_stream_t stream);
 
+/*
+ * Shared-memory throughput probe (Sec. 6.1, Table 6): `ctas` CTAs of
+ * `threads` threads (a multiple of 32, <= 1024); every thread copies `ilp`
+ * (1, 2, 4, 6 or 8) 4-byte words from one shared region to another, `iters`
+ * (<= 2^20) times, so a CTA uses 8 * ilp * threads bytes of shared memory (at
+ * most 227 KB) and moves 8 * ilp * threads * iters bytes (read + write).
+ * Launch ctas = SMs x CTAs per SM to place that many CTAs on each SM.  For
+ * CTA i the device outputs hold the SM clock64 before and after its copy loop
+ * (each taken after a __syncthreads; uint64 t0_out[i], t1_out[i]) and its SM id
+ * (uint32 smid_out[i]): an SM's throughput is the bytes of its CTAs over its
+ * span max(t1) - min(t0) in SM cycles.  Asynchronous on `stream`.
+ */
+int pchase_probe_smem_throughput(uint32_t ctas, uint32_t threads, uint32_t ilp, uint32_t iters,
+                                 uint64_t *t0_out, uint64_t *t1_out, uint32_t *smid_out,
+                                 pchase_stream_t stream);
+
 /* ------------------------------------------------------------------ S7 */
 
 /*

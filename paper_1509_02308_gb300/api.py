@@ -251,6 +251,31 @@ def pchase_probe_smem_bank(max_stride: int = 64, repeats: int = 9, stream=None):
     return cyc, deg
 
 
+def pchase_probe_smem_throughput(ctas_per_sm: int, threads: int, ilp: int, iters: int = 4096,
+                                 stream=None) -> dict:
+    """Sec. 6.1's shared-memory copy on every SM: bytes per SM cycle (mean and
+    best over SMs that held exactly ctas_per_sm CTAs), and CTAs seen per SM."""
+    L = C.load()
+    sms = torch.cuda.get_device_properties(DEV).multi_processor_count
+    ctas = sms * ctas_per_sm
+    t0 = torch.empty(ctas, dtype=torch.int64, device=DEV)
+    t1 = torch.empty(ctas, dtype=torch.int64, device=DEV)
+    sid = torch.empty(ctas, dtype=torch.int32, device=DEV)
+    C.check(L.pchase_probe_smem_throughput(ctas, threads, ilp, iters, C.ptr(t0), C.ptr(t1),
+                                           C.ptr(sid), C.stream_handle(stream)))
+    torch.cuda.current_stream().synchronize()
+    a, b, s = t0.cpu().numpy(), t1.cpu().numpy(), sid.cpu().numpy().astype(np.int64)
+    per = []
+    count = np.bincount(s, minlength=sms)
+    for sm in np.nonzero(count == ctas_per_sm)[0]:
+        m = s == sm
+        span = int(b[m].max() - a[m].min())
+        per.append(8.0 * ilp * threads * iters * int(m.sum()) / max(1, span))
+    return {"bytes_per_cycle": float(np.mean(per)) if per else 0.0,
+            "bytes_per_cycle_max": float(np.max(per)) if per else 0.0,
+            "sms_measured": len(per), "ctas_per_sm_seen": [int(count.min()), int(count.max())]}
+
+
 def pchase_probe_global_throughput(kind: int, vec_bytes: int, ctas: int, threads: int, ilp: int,
                                    src: torch.Tensor | None, dst: torch.Tensor, nbytes: int,
                                    reps: int = 5, stream=None) -> float:

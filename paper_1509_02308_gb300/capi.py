@@ -76,6 +76,8 @@ SIGNATURES = {
     "pchase_probe_latency": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.c_int,
                                             _c_p, _c_p, _c_p, _c_p, _c_p]),
     "pchase_probe_smem_bank": (ctypes.c_int, [_c_u32, _c_u32, _c_p, _c_p, _c_p]),
+    "pchase_probe_smem_throughput": (ctypes.c_int, [_c_u32, _c_u32, _c_u32, _c_u32, _c_p, _c_p,
+                                                     _c_p, _c_p]),
     "pchase_probe_global_throughput": (ctypes.c_int, [ctypes.c_int, _c_u32, _c_u32, _c_u32,
                                                       _c_u32, _c_p, _c_p, _c_u64, _c_u32,
                                                       ctypes.POINTER(ctypes.c_double), _c_p]),

@@ -34,6 +34,9 @@ cudaError_t probe_latency(const uint32_t *A, uint32_t n, uint32_t start, uint32_
                           uint32_t *status, cudaStream_t st);
 cudaError_t probe_smem(uint32_t max_stride, uint32_t repeats, float *cycles, uint32_t *degree,
                        cudaStream_t st);
+cudaError_t probe_smem_copy(uint32_t ctas, uint32_t threads, uint32_t ilp, uint32_t iters,
+                            unsigned long long *t0, unsigned long long *t1, uint32_t *smid,
+                            cudaStream_t st);
 cudaError_t probe_gmem(int kind, uint32_t vec_bytes, uint32_t ctas, uint32_t threads,
                        uint32_t ilp, const void *src, void *dst, uint64_t bytes, uint32_t reps,
                        double *gbs, cudaStream_t st);
@@ -1136,6 +1139,23 @@ int pchase_probe_smem_bank(uint32_t max_stride, uint32_t repeats, float *cycles_
     PCHASE_CUDA(probe_smem(max_stride, repeats, cycles_out, degree_out,
                            reinterpret_cast<cudaStream_t>(stream)),
                 "smem probe");
+    return PCHASE_OK;
+}
+
+int pchase_probe_smem_throughput(uint32_t ctas, uint32_t threads, uint32_t ilp, uint32_t iters,
+                                 uint64_t *t0_out, uint64_t *t1_out, uint32_t *smid_out,
+                                 pchase_stream_t stream) {
+    if (ctas == 0 || ctas > (1u << 20) || threads == 0 || threads > 1024 || (threads & 31) ||
+        (ilp != 1 && ilp != 2 && ilp != 4 && ilp != 6 && ilp != 8) || iters == 0 ||
+        iters > (1u << 20) || !t0_out || !t1_out || !smid_out)
+        return fail(PCHASE_EINVAL, "pchase_probe_smem_throughput: bad argument");
+    if (8ull * ilp * threads > 227ull * 1024)
+        return fail(PCHASE_ERANGE, "pchase_probe_smem_throughput: 8 * ilp * threads above 227 KB");
+    PCHASE_CUDA(probe_smem_copy(ctas, threads, ilp, iters,
+                                reinterpret_cast<unsigned long long *>(t0_out),
+                                reinterpret_cast<unsigned long long *>(t1_out), smid_out,
+                                reinterpret_cast<cudaStream_t>(stream)),
+                "shared-memory throughput probe");
     return PCHASE_OK;
 }
 

@@ -9,7 +9,11 @@
 //     starting at word t*stride of a self-pointing array, 64 dependent reads;
 //   * global-memory read / write / copy throughput (Sec. 5.1) with 4- or
 //     16-byte vectors, a grid-stride loop and `ilp` independent vectors per
-//     thread per trip.
+//     thread per trip;
+//   * shared-memory throughput (Sec. 6.1): every thread copies `ilp` 4-byte
+//     words from one shared region to another, `iters` times; each CTA times
+//     its loop with its SM's clock64 between two __syncthreads and records
+//     its SM, so the host can sum bytes per SM over the SM's busy span.
 // Every loop is bounded by its caller-given count.
 #include <algorithm>
 #include <vector>
@@ -226,7 +230,63 @@ cudaError_t launch_gmem(int kind, uint32_t ilp, uint32_t ctas, uint32_t threads,
     return launch_gmem_ilp<V, 2>(ilp, ctas, threads, src, dst, n, st);
 }
 
+// Sec. 6.1's copy: per trip, `ILP` independent shared loads, then their
+// stores into the second region (the words a thread copies are ILP x 4 bytes
+// read and written).  Volatile keeps every trip's accesses.
+template <int ILP>
+__global__ void smem_copy_kernel(uint32_t iters, unsigned long long *t0_out,
+                                 unsigned long long *t1_out, uint32_t *smid_out) {
+    extern __shared__ uint32_t sm_words[];
+    volatile uint32_t *src = sm_words;
+    volatile uint32_t *dst = sm_words + ILP * blockDim.x;
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) src[k * nt + tid] = tid * 7u + (uint32_t)k;
+    __syncthreads();
+    const long long t0 = clk();
+    for (uint32_t it = 0; it < iters; ++it) {
+        uint32_t v[ILP];
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) v[k] = src[k * nt + tid];
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) dst[k * nt + tid] = v[k] + it;
+    }
+    __syncthreads();
+    const long long t1 = clk();
+    if (tid == 0) {
+        uint32_t smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        t0_out[blockIdx.x] = (unsigned long long)t0;
+        t1_out[blockIdx.x] = (unsigned long long)t1;
+        smid_out[blockIdx.x] = smid;
+    }
+}
+
 }  // namespace
+
+cudaError_t probe_smem_copy(uint32_t ctas, uint32_t threads, uint32_t ilp, uint32_t iters,
+                            unsigned long long *t0, unsigned long long *t1, uint32_t *smid,
+                            cudaStream_t st) {
+    const size_t bytes = 8ull * ilp * threads;
+    cudaError_t e = cudaSuccess;
+    switch (ilp) {
+#define PCHASE_SMEM_ILP(N)                                                                     \
+    case N:                                                                                    \
+        e = cudaFuncSetAttribute(smem_copy_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)bytes);                                                  \
+        if (e != cudaSuccess) return e;                                                        \
+        smem_copy_kernel<N><<<ctas, threads, bytes, st>>>(iters, t0, t1, smid);                \
+        break;
+        PCHASE_SMEM_ILP(1)
+        PCHASE_SMEM_ILP(2)
+        PCHASE_SMEM_ILP(4)
+        PCHASE_SMEM_ILP(6)
+        PCHASE_SMEM_ILP(8)
+#undef PCHASE_SMEM_ILP
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t probe_latency(const uint32_t *A, uint32_t n, uint32_t start, uint32_t warmup,
                           uint32_t iters, int mode, uint32_t *lat, uint32_t *idx, uint32_t *ovh,

@@ -272,3 +272,34 @@ def latency_noise_params():
     normalisation to [0, 1]."""
     return {"t0_lo": 20.0, "t0_hi": 400.0, "rho_lo": 1.5, "rho_hi": 30.0, "sigma": 0.02,
             "spike_p": 0.005, "spike_lo": 2.0, "spike_hi": 10.0}
+
+
+# --------------------------------------------------------- latency spectrum
+def spectrum_chain():
+    """The non-uniform-stride chain of Sec. 5.2 (Fig. 10(b)), as element
+    indices visited in order, with a segment label per access, over an array
+    of `n_elems` 4-byte elements (2.3 GB):
+
+      B  65 accesses 1 MB apart (cold: data-cache misses; each new 2 MB page
+         comes on an even access, the odd ones reuse the page of the previous);
+      A  64 accesses 32 MB apart over 2 GB (cache misses on new pages);
+      C  B's 65 lines again through their next element (a chase visits each
+         element once), 32 lines apart in turn (data cached, pages last
+         touched before A's sweep);
+      D  32 accesses to the 32 elements of one 128-byte line (hits).
+
+    No element repeats, so a chain A[path[i]] = path[i + 1] closing on itself
+    walks exactly this path.  Returns (path, labels, n_elems)."""
+    MB = (1 << 20) // 4
+    base_b = 2048 * MB + 64 * MB
+    b_lines = [base_b + k * MB for k in range(65)]
+    a_lines = [k * 32 * MB + 16 for k in range(64)]
+    c_order = [(k * 32) % 65 for k in range(65)]
+    c_lines = [b_lines[k] + 1 for k in c_order]
+    d_base = base_b + 70 * MB
+    d_lines = [d_base + k for k in range(32)]
+    path = b_lines + a_lines + c_lines + d_lines
+    labels = (["B_new_page" if k % 2 == 0 else "B_same_page" for k in range(65)] +
+              ["A_32MB"] * 64 + ["C_revisit"] * 65 + ["D_same_line"] * 32)
+    n_elems = d_base + 64
+    return path, labels, n_elems

@@ -71,3 +71,47 @@ def test_global_throughput_is_plausible():
         assert 500.0 < res[kind] < 8000.0 * 1.05, (kind, res[kind])
     small = api.pchase_probe_global_throughput(2, 4, 1, 32, 1, a, b, 1 << 20, reps=3)
     assert 0 < small < res[2]
+
+
+@pytest.mark.parametrize("threads,per_sm,ilp", [(32, 1, 1), (256, 2, 4), (1024, 1, 8), (128, 6, 6)])
+def test_smem_throughput_probe_bounded_by_banks(threads, per_sm, ilp):
+    """Sec. 6.1's copy: every SM holds the CTAs asked for, and no SM moves more
+    than its 32 banks x 4 bytes per cycle."""
+    r = api.pchase_probe_smem_throughput(per_sm, threads, ilp, iters=512)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert r["ctas_per_sm_seen"] == [per_sm, per_sm]
+    assert r["sms_measured"] == sms
+    assert 0.0 < r["bytes_per_cycle"] <= r["bytes_per_cycle_max"] <= 128.0 * 1.02
+
+
+def test_smem_throughput_probe_rejects_bad_shapes():
+    from paper_1509_02308_gb300 import capi as C
+    L = C.load()
+    buf = torch.empty(16, dtype=torch.int64, device="cuda")
+    p = C.ptr(buf)
+    assert L.pchase_probe_smem_throughput(4, 100, 1, 10, p, p, p, None) == C.EINVAL  # not x32
+    assert L.pchase_probe_smem_throughput(4, 64, 3, 10, p, p, p, None) == C.EINVAL   # ilp 3
+    assert L.pchase_probe_smem_throughput(4, 64, 1, 0, p, p, p, None) == C.EINVAL    # no trips
+
+
+def test_latency_spectrum_chain_walk():
+    """Sec. 5.2's non-uniform chain: the probe walks exactly the constructed
+    path (no element repeats), and hits inside one line are faster than the
+    32 MB jumps that miss every cache."""
+    from paper_1509_02308_gb300 import workloads as W
+    path, labels, n = W.spectrum_chain()
+    assert len(set(path)) == len(path) and max(path) < n
+    arr = torch.zeros(n, dtype=torch.int32, device="cuda")
+    arr[torch.tensor(path, dtype=torch.int64, device="cuda")] = torch.tensor(
+        path[1:] + path[:1], dtype=torch.int32, device="cuda")
+    lab = np.array(labels)
+    for mode in (0, 1):
+        lat, vis, _, st = api.pchase_probe_latency(arr, n, iters=len(path), start=path[0],
+                                                   cache_mode=mode)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        assert np.array_equal(vis.cpu().numpy().view(np.uint32), np.array(path, dtype=np.uint32))
+        l = lat.cpu().numpy().view(np.uint32)
+        assert np.median(l[lab == "D_same_line"]) < np.median(l[lab == "A_32MB"])
+    del arr
+    torch.cuda.empty_cache()
