@@ -64,7 +64,7 @@ def lib():
                 ctypes.c_void_p, ctypes.c_uint64, _u8p, ctypes.c_void_p]
             L.or_cache_sim_ext.argtypes = [ctypes.c_uint32] * 4 + [
                 ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, _u32p, ctypes.c_uint64,
-                ctypes.c_void_p, ctypes.c_uint64, _u8p, ctypes.c_void_p,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _u8p, ctypes.c_void_p,
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                 ctypes.POINTER(ctypes.c_uint64)]
             L.or_weighted_victim.argtypes = [ctypes.c_uint64, ctypes.c_uint32,
@@ -132,12 +132,19 @@ def weighted_victim(seed: int, set_: int, k: int, ways: int) -> int:
 # ----------------------------------------------------------------------- cache
 def cache_sim(C: int, b: int, ways: int, T: int, policy: int, trace: np.ndarray,
               seed: int = 0, victims=None, want_final: bool = False, mapping: int = 0,
-              want_evictions: bool = False):
+              want_evictions: bool = False, filter=None):
     """Per-access miss flags (uint8, 1 = miss) of one replay; see or_cache_sim_ext.
 
+    filter: per-access flags; the cache sees only the flagged accesses (a lower
+    level of the hierarchy fed by the misses of the level above).
     want_final adds the line held by each way (T*ways, 0xFFFFFFFF when invalid);
     want_evictions adds (sets, ways) of every eviction in order."""
     trace = np.ascontiguousarray(trace, dtype=np.uint32)
+    flt = None
+    if filter is not None:
+        flt = np.ascontiguousarray(filter, dtype=np.uint8)
+        if flt.size != trace.size:
+            raise ValueError("filter must flag every access")
     out = np.empty(trace.size, dtype=np.uint8)
     vic_p, nv = None, 0
     if victims is not None:
@@ -149,7 +156,8 @@ def cache_sim(C: int, b: int, ways: int, T: int, policy: int, trace: np.ndarray,
     ew = np.empty(max(cap, 1), dtype=np.uint32)
     n_ev = ctypes.c_uint64()
     rc = lib().or_cache_sim_ext(C, b, ways, T, policy, seed & 0xFFFFFFFFFFFFFFFF, mapping,
-                                trace, trace.size, vic_p, nv, out,
+                                trace, trace.size, flt.ctypes.data if flt is not None else None,
+                                vic_p, nv, out,
                                 fin.ctypes.data if fin is not None else None,
                                 es.ctypes.data if cap else None,
                                 ew.ctypes.data if cap else None, cap, ctypes.byref(n_ev))
@@ -161,6 +169,21 @@ def cache_sim(C: int, b: int, ways: int, T: int, policy: int, trace: np.ndarray,
         n = int(n_ev.value)
         res += [es[:n].copy(), ew[:n].copy()]
     return tuple(res) if len(res) > 1 else out
+
+
+def hierarchy(levels, trace):
+    """Miss flags of each level of a cascade: levels[0] sees every access,
+    levels[k] only the misses of levels[k-1] (Sec. 3's L1 -> L2 path; with
+    page-sized lines, an L1 TLB -> L2 TLB path).  levels: dicts with C, b,
+    ways, T, policy and optionally seed, mapping.  The level an access is
+    served from is the sum of its flags."""
+    out, flt = [], None
+    for g in levels:
+        m = cache_sim(g["C"], g["b"], g["ways"], g["T"], g["policy"], trace,
+                      seed=g.get("seed", 0), mapping=g.get("mapping", 0), filter=flt)
+        out.append(m)
+        flt = m
+    return out
 
 
 def cache_sim_counts(C, b, ways, T, policy, trace, warmup, seed=0):

@@ -143,9 +143,16 @@ static int or_geom_ok(uint32_t C, uint32_t b, uint32_t ways, uint32_t T)
  * Only LRU records a use on a hit.  When evict_set / evict_way are given, the
  * set and way of the first `evict_cap` evictions are written there and the
  * number of evictions to *n_evict.
+ *
+ * filter (NULL: every access): the cache sees only the accesses t with
+ * filter[t] != 0, in order; the others neither hit nor miss (miss_out 0).
+ * With filter = the misses of a level above, this is the next level of the
+ * hierarchy of Sec. 3 (an L1 miss goes to L2; an L1 hit never reaches it), and
+ * with pages for lines (b = page size) it is a TLB level (Sec. 4.4).
  */
 int or_cache_sim_ext(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int policy,
                      uint64_t seed, uint32_t mapping, const uint32_t *trace, uint64_t len,
+                     const uint8_t *filter,
                      const uint32_t *victims, uint64_t n_victims,
                      uint8_t *miss_out, uint32_t *final_lines /* T*ways or NULL */,
                      uint32_t *evict_set, uint32_t *evict_way, uint64_t evict_cap,
@@ -168,6 +175,11 @@ int or_cache_sim_ext(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int poli
     uint64_t replay_next = 0, n_ev = 0;
     int rc = OR_OK;
     for (uint64_t t = 0; t < len; t++) {
+        if (filter && !filter[t]) {
+            /* the access never reaches this cache */
+            miss_out[t] = 0;
+            continue;
+        }
         uint64_t addr = 4ull * trace[t];
         uint64_t line = addr / b;
         uint32_t set = (uint32_t)((line >> mapping) % T);
@@ -232,8 +244,8 @@ int or_cache_sim(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int policy,
                  const uint32_t *victims, uint64_t n_victims,
                  uint8_t *miss_out, uint32_t *final_tags /* T*ways or NULL */)
 {
-    return or_cache_sim_ext(C, b, ways, T, policy, seed, 0, trace, len, victims, n_victims,
-                            miss_out, final_tags, NULL, NULL, 0, NULL);
+    return or_cache_sim_ext(C, b, ways, T, policy, seed, 0, trace, len, NULL, victims,
+                            n_victims, miss_out, final_tags, NULL, NULL, 0, NULL);
 }
 
 /* Miss counts of one replay: total, and after the first `warmup` accesses. */

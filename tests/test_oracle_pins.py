@@ -219,6 +219,101 @@ def test_weighted_policy_needs_three_ways():
         oracle.cache_sim(64, 32, 2, 1, oracle.WEIGHTED, tr)
 
 
+# ------------------------------------------------------------ hierarchy
+def _lvl(C, b, ways, T, policy=oracle.LRU, seed=0):
+    return dict(C=C, b=b, ways=ways, T=T, policy=policy, seed=seed)
+
+
+def test_filter_all_ones_is_unfiltered_and_all_zeros_sees_nothing():
+    for g in W.random_small_geoms(20, seed=31, max_lines=32):
+        tr = W.random_index_trace(500, g.C // 4 * 3, seed=g.seed % 911)
+        a = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed)
+        b = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed,
+                             filter=np.ones(tr.size, np.uint8))
+        z = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed,
+                             filter=np.zeros(tr.size, np.uint8))
+        assert np.array_equal(a, b) and not z.any()
+
+
+def test_filtered_run_is_the_run_of_the_kept_accesses():
+    # a lower level sees exactly the subsequence the level above lets through
+    rng = np.random.Generator(np.random.PCG64(8))
+    for g in W.random_small_geoms(30, seed=32, max_lines=32):
+        tr = W.random_index_trace(700, g.C // 4 * 4, seed=g.seed % 977)
+        keep = (rng.random(tr.size) < 0.4).astype(np.uint8)
+        got = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed, filter=keep)
+        sub = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr[keep == 1], seed=g.seed)
+        want = np.zeros(tr.size, np.uint8)
+        want[keep == 1] = sub
+        assert np.array_equal(got, want)
+
+
+def test_l2_behind_a_fitting_l1_takes_only_compulsory_misses():
+    """N <= C1: the L1 misses each line once; an L2 with lines b2 = f * b1 then
+    misses once per L2 line of the array and hits the other f - 1 L1 lines."""
+    for (b1, f) in ((32, 1), (32, 2), (64, 4)):
+        l1 = _lvl(4096, b1, 4, 4096 // (4 * b1))
+        l2 = _lvl(65536, b1 * f, 8, 65536 // (8 * b1 * f))
+        for nb in (1024, 3000, 4096):
+            n = nb // 4
+            tr = oracle.pchase_trace(n, 1, 3 * n)
+            m1, m2 = oracle.hierarchy([l1, l2], tr)
+            lines1 = -(-nb // b1)
+            lines2 = -(-nb // (b1 * f))
+            assert m1.sum() == lines1 and m1[n:].sum() == 0
+            assert m2.sum() == lines2 and m2[n:].sum() == 0
+            assert not (m2 & (1 - m1)).any()  # L2 sees only L1 misses
+
+
+def test_tlb_cascade_behind_a_thrashing_l1_tlb():
+    """Sec. 4.4: the L1 TLB is 16-way fully associative with 2 MB pages.  A
+    chain at s = 2 MB over 16 + k pages cycles through more pages than it
+    holds, so under LRU every access misses it and the L2 TLB sees the whole
+    stream: it then behaves as a lone cache (here 7 sets x 8 ways, LRU: a set
+    cycling through more than 8 pages misses on every access)."""
+    page = 2 << 20
+    l1 = _lvl(16 * page, page, 16, 1)
+    l2 = _lvl(56 * page, page, 8, 7)
+    for n_pages in (17, 20, 40, 56, 57, 64, 70):
+        n = n_pages * page // 4
+        tr = oracle.pchase_trace(n, page // 4, 4 * n_pages)
+        m1, m2 = oracle.hierarchy([l1, l2], tr)
+        assert m1[n_pages:].all()
+        lone = oracle.cache_sim(l2["C"], l2["b"], 8, 7, oracle.LRU, tr)
+        assert np.array_equal(m2, lone)
+        per_set = [len(range(s, n_pages, 7)) for s in range(7)]
+        assert m2[n_pages:2 * n_pages].sum() == sum(c for c in per_set if c > 8)
+    # 16 pages or fewer: after one pass every access hits the L1 TLB and the
+    # L2 TLB sees only the first touches
+    for n_pages in (1, 8, 16):
+        n = n_pages * page // 4
+        tr = oracle.pchase_trace(n, page // 4, 4 * n_pages)
+        m1, m2 = oracle.hierarchy([l1, l2], tr)
+        assert m1[n_pages:].sum() == 0 and m2.sum() == n_pages
+
+
+def test_bruteforce_two_level_hierarchy():
+    rng = np.random.Generator(np.random.PCG64(99))
+    n = 0
+    for _ in range(300):
+        b1 = int(rng.choice([4, 8]))
+        a1, T1 = int(rng.integers(1, 4)), int(rng.integers(1, 4))
+        b2 = b1 * int(rng.choice([1, 2]))
+        a2, T2 = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+        p1, p2 = int(rng.integers(0, 3)), int(rng.integers(0, 3))
+        L = int(rng.integers(1, 60))
+        tr = rng.integers(0, 4 * a2 * T2 * b2 // 4 + 2, size=L).astype(np.uint32)
+        m1, m2 = oracle.hierarchy([_lvl(a1 * T1 * b1, b1, a1, T1, p1, 3),
+                                   _lvl(a2 * T2 * b2, b2, a2, T2, p2, 4)], tr)
+        w1 = _list_model(a1 * T1 * b1, b1, a1, T1, p1, 3, tr)
+        keep = w1 == 1
+        w2 = np.zeros(L, np.uint8)
+        w2[keep] = _list_model(a2 * T2 * b2, b2, a2, T2, p2, 4, tr[keep])
+        assert np.array_equal(m1, w1) and np.array_equal(m2, w2)
+        n += 1
+    assert n == 300
+
+
 # --------------------------------------------------------------- invariants
 def test_all_hits_after_warmup_when_array_fits():
     for g in W.random_small_geoms(40, seed=11, max_lines=32):
