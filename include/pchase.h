@@ -154,6 +154,9 @@ typedef struct {
                                     default 32; 1 = never split) */
     uint32_t split_cost_ns;      /* split items whose estimated warp time is above this
                                     (0 = automatic, from the whole plan's estimated work) */
+    uint32_t filtered;           /* 1: the plan is a lower level of a hierarchy; every unit
+                                    gathers its accesses, so pchase_sim_run_filtered can skip
+                                    the ones a filter bitmap leaves out (default 0) */
 } pchase_tune;
 
 typedef struct pchase_sim_plan pchase_sim_plan;
@@ -223,6 +226,21 @@ int pchase_sim_plan_upload(const pchase_sim_plan *plan, void *workspace, size_t 
 int pchase_sim_run(const pchase_sim_plan *plan, void *workspace, uint32_t *bitmaps,
                    const uint64_t *word_offsets, uint64_t *miss_counts, uint32_t *dev_status,
                    pchase_stream_t stream);
+
+/*
+ * The next level of a hierarchy (Sec. 3: an L1 miss goes to L2, an L1 hit never
+ * does; with page-sized lines, a TLB level of Sec. 4.4): like pchase_sim_run,
+ * but item i sees only the accesses whose bit is set in its filter bitmap,
+ * filter + filter_word_offsets[i] (device; packed like `bitmaps`, normally the
+ * miss bitmap of the level above for the same trace), in order.  The other
+ * accesses neither hit nor miss (bit 0).  The plan must have been created
+ * with pchase_tune.filtered = 1 (PCHASE_EINVAL otherwise).  The level an
+ * access is served from is the sum of its bits over the levels.
+ */
+int pchase_sim_run_filtered(const pchase_sim_plan *plan, void *workspace,
+                            const uint32_t *filter, const uint64_t *filter_word_offsets,
+                            uint32_t *bitmaps, const uint64_t *word_offsets,
+                            uint64_t *miss_counts, uint32_t *dev_status, pchase_stream_t stream);
 
 /*
  * pchase_sim_run that also records, per item i (in the caller's numbering),

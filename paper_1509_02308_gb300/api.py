@@ -72,7 +72,7 @@ class SimPlan:
             tn = C.Tune(tune.get("scan_max_ways", 0), tune.get("smem_budget_bytes", 0),
                         tune.get("max_warps_per_cta", 0), tune.get("ctas_per_sm_cap", 0),
                         tune.get("batch_max_sets", 0), tune.get("max_split", 0),
-                        tune.get("split_cost_ns", 0))
+                        tune.get("split_cost_ns", 0), tune.get("filtered", 0))
         h = ctypes.c_void_p()
         C.check(self.L.pchase_sim_plan_create(
             ctypes.addressof(ga), len(self.geoms), ctypes.addressof(ta), len(self.traces),
@@ -116,6 +116,21 @@ class SimPlan:
             counts = torch.empty(2 * max(1, self.n_items), dtype=torch.int64, device=DEV)
         C.check(self.L.pchase_sim_run(self.h, self._ws, C.ptr(bitmaps) if want_bitmaps else None,
                                       None, C.ptr(counts), C.ptr(status), C.stream_handle(stream)))
+        return bitmaps, counts
+
+    def run_filtered(self, filter_bitmaps: torch.Tensor, filter_word_offsets: torch.Tensor,
+                     bitmaps: torch.Tensor | None = None, counts: torch.Tensor | None = None,
+                     status: torch.Tensor | None = None, stream=None):
+        """A lower level of a hierarchy (plan made with tune filtered=1): item
+        i sees only the accesses set in filter_bitmaps + filter_word_offsets[i]."""
+        if bitmaps is None:
+            bitmaps = _u32(max(1, self.bitmap_words))
+        if counts is None:
+            counts = torch.empty(2 * max(1, self.n_items), dtype=torch.int64, device=DEV)
+        C.check(self.L.pchase_sim_run_filtered(self.h, self._ws, C.ptr(filter_bitmaps),
+                                               C.ptr(filter_word_offsets), C.ptr(bitmaps), None,
+                                               C.ptr(counts), C.ptr(status),
+                                               C.stream_handle(stream)))
         return bitmaps, counts
 
     def run_profiled(self, stream=None):
@@ -163,6 +178,31 @@ def infer_batch(plan: "SimPlan", lats: torch.Tensor, stop_above: int = 2**64 - 1
                                    C.ptr(dist), C.ptr(pick), C.ptr(status),
                                    C.stream_handle(stream)))
     return dist, pick
+
+
+class HierarchyPlan:
+    """A cascade of cache (or TLB) levels over the same traces: level 0 sees
+    every access, level k only the misses of level k-1 (Sec. 3's L1 -> L2
+    path; page-sized lines give Sec. 4.4's L1 -> L2 TLB path).  levels: one
+    list of geometries per level, item i of every level pairing geometry
+    levels[k][pairs[i][0]] with trace pairs[i][1] (all x all when None)."""
+
+    def __init__(self, levels: list[list[Geom]], traces, pairs=None, tune: dict | None = None):
+        self.plans = []
+        for k, geoms in enumerate(levels):
+            tn = dict(tune or {})
+            if k > 0:
+                tn["filtered"] = 1
+            self.plans.append(SimPlan(geoms, traces, pairs=pairs, tune=tn or None))
+        self.word_offsets = self.plans[0].word_offsets
+        self._wo = torch.from_numpy(self.word_offsets[:-1].astype(np.int64)).to(DEV)
+
+    def run(self, stream=None):
+        """(bitmaps, counts) per level; an access's level is the sum of its bits."""
+        out = [self.plans[0].run(stream=stream)]
+        for p in self.plans[1:]:
+            out.append(p.run_filtered(out[-1][0], self._wo, stream=stream))
+        return out
 
 
 def cache_sim_batch(geoms: list[Geom], traces, pairs=None, stream=None):

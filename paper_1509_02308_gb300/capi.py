@@ -40,7 +40,8 @@ class Pair(ctypes.Structure):
 class Tune(ctypes.Structure):
     _fields_ = [("scan_max_ways", _c_u32), ("smem_budget_bytes", _c_u32),
                 ("max_warps_per_cta", _c_u32), ("ctas_per_sm_cap", _c_u32),
-                ("batch_max_sets", _c_u32), ("max_split", _c_u32), ("split_cost_ns", _c_u32)]
+                ("batch_max_sets", _c_u32), ("max_split", _c_u32), ("split_cost_ns", _c_u32),
+                ("filtered", _c_u32)]
 
 
 assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32
@@ -76,6 +77,8 @@ SIGNATURES = {
     "pchase_probe_latency": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.c_int,
                                             _c_p, _c_p, _c_p, _c_p, _c_p]),
     "pchase_probe_smem_bank": (ctypes.c_int, [_c_u32, _c_u32, _c_p, _c_p, _c_p]),
+    "pchase_sim_run_filtered": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p,
+                                                _c_p]),
     "pchase_probe_smem_throughput": (ctypes.c_int, [_c_u32, _c_u32, _c_u32, _c_u32, _c_p, _c_p,
                                                      _c_p, _c_p]),
     "pchase_probe_global_throughput": (ctypes.c_int, [ctypes.c_int, _c_u32, _c_u32, _c_u32,

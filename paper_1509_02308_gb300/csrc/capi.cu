@@ -295,7 +295,7 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
         const double direct_cost = cold_chunks * o.cold_ns + (chunks - cold_chunks) * o.warm_ns;
         const double queued_cost = cold_steps * o.cold_ns + (steps - cold_steps) * o.warm_ns +
                                    chunks * kGatherNs;
-        const bool direct = K == 1 && direct_cost <= queued_cost;
+        const bool direct = K == 1 && direct_cost <= queued_cost && !tn.filtered;
         const uint64_t arena = align16(o.arena) + (direct ? 0u : kStageBytes);
         const double cost = direct ? direct_cost : queued_cost;
         const bool fits = arena <= kMaxArena;
@@ -393,6 +393,7 @@ struct pchase_sim_plan {
     // planner estimates (ns of one warp): all units, the longest unit that
     // cannot split further, the split target, the longest unit planned
     double est_sum = 0.0, est_critical = 0.0, est_target = 0.0, est_max_unit = 0.0;
+    bool filtered = false;  // every unit queued (pchase_sim_run_filtered)
     // runtime state, set on the first run
     int device = -1, sms = 0, grid = 0, jgrid = 0;
     cudaStream_t side = nullptr;
@@ -504,7 +505,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     *plan_out = nullptr;
     if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
         return fail(PCHASE_EINVAL, "NULL descriptor array");
-    pchase_tune tn{4, 220 * 1024, 16, 0, 64, 32, 0};
+    pchase_tune tn{4, 220 * 1024, 16, 0, 64, 32, 0, 0};
     if (tune) {
         if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
@@ -514,6 +515,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         tn.ctas_per_sm_cap = tune->ctas_per_sm_cap;
         if (tune->max_split) tn.max_split = std::min<uint32_t>(tune->max_split, 192);
         tn.split_cost_ns = tune->split_cost_ns;
+        tn.filtered = tune->filtered ? 1u : 0u;
     }
     for (uint32_t i = 0; i < n_geom; ++i) {
         int rc = check_geom(geoms[i], i);
@@ -612,6 +614,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         total += u.cost;
     }
     p->bitmap_words = word;
+    p->filtered = tn.filtered != 0;
     const uint32_t max_split = std::max<uint32_t>(1, tn.max_split);
     // Split target: no unit above the plan's share per warp slot, but no
     // split below what the longest unsplittable work takes anyway (splitting
@@ -930,6 +933,27 @@ int pchase_sim_run(const pchase_sim_plan *plan, void *workspace, uint32_t *bitma
     out.word_offsets = word_offsets;
     out.miss_counts = miss_counts;
     out.status = dev_status;
+    return plan_launch(const_cast<pchase_sim_plan *>(plan), workspace, out,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+int pchase_sim_run_filtered(const pchase_sim_plan *plan, void *workspace,
+                            const uint32_t *filter, const uint64_t *filter_word_offsets,
+                            uint32_t *bitmaps, const uint64_t *word_offsets,
+                            uint64_t *miss_counts, uint32_t *dev_status, pchase_stream_t stream) {
+    if (!plan || !workspace) return fail(PCHASE_EINVAL, "plan or workspace is NULL");
+    if (!plan->filtered)
+        return fail(PCHASE_EINVAL, "pchase_sim_run_filtered: plan not created with tune.filtered");
+    if (!filter || !filter_word_offsets)
+        return fail(PCHASE_EINVAL, "pchase_sim_run_filtered: filter or its offsets are NULL");
+    if (plan->n_items == 0) return PCHASE_OK;
+    SimOut out{};
+    out.bitmaps = bitmaps;
+    out.word_offsets = word_offsets;
+    out.miss_counts = miss_counts;
+    out.status = dev_status;
+    out.filter = filter;
+    out.filter_word_offsets = filter_word_offsets;
     return plan_launch(const_cast<pchase_sim_plan *>(plan), workspace, out,
                        reinterpret_cast<cudaStream_t>(stream));
 }

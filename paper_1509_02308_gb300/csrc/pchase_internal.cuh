@@ -166,6 +166,10 @@ struct SimOut {
     uint32_t n_rep;
     uint64_t rep_dist_stride;
     uint64_t rep_obs_stride;
+    // a lower level of a hierarchy: item i's unit sees only the accesses set
+    // in filter + filter_word_offsets[i] (queued units only; not with the matcher)
+    const uint32_t *filter;
+    const uint64_t *filter_word_offsets;
 };
 
 // Records the text pchase_last_error_string() returns on this thread and

@@ -1172,11 +1172,16 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
         uint32_t *const ring = reinterpret_cast<uint32_t *>(g_smem + arena + kQueueBytes);
         uint32_t *const oring = ring + kRing * 32;
         const uint32_t nchunks = (len + 31) >> 5;
+        // a lower level of a hierarchy: a filter word per chunk (in the slot
+        // the matcher uses for observed words; the two never meet)
+        const uint32_t *const fbits =
+            out.filter ? out.filter + out.filter_word_offsets[it.out_item] : nullptr;
         auto issue = [&](uint32_t c) {
             if (c < nchunks) {
                 const uint32_t t = (c << 5) + (uint32_t)lane;
                 if (idxp && t < len) cp_async4(ring + (c % kRing) * 32 + lane, idxp + t);
                 if (ham && lane == 0) cp_async4(oring + (c % kRing), observed + obase + c);
+                if (fbits && lane == 0) cp_async4(oring + (c % kRing), fbits + c);
             }
             cp_async_commit();
         };
@@ -1220,7 +1225,12 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
                     mine = valid && sg - kq * K == kres;
                     lp = ((kq << psh) | (set & pmask)) + q * sets;
                 }
-                const bool take = mine && ln != prevl;
+                // filtered: every kept access is queued (its predecessor in the
+                // kept stream is not known here; the step drops repeats itself)
+                const uint32_t fw =
+                    fbits ? __shfl_sync(kFull, lane == 0 ? oring[cin % kRing] : 0u, 0) : kFull;
+                const bool take =
+                    mine && ((fw >> lane) & 1u) && (fbits != nullptr || ln != prevl);
                 const uint32_t bal = __ballot_sync(kFull, take);
                 if (take) {
                     const uint32_t pv = ham ? (t | (((ow >> lane) & 1u) << 31)) : t;
