@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner (default knobs)")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-inverse section")
     p.add_argument("--no-probes", action="store_true", help="skip the on-device probe section")
+    p.add_argument("--no-hierarchy", action="store_true",
+                   help="skip the cache / TLB hierarchy section")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the set-mapping / weighted-policy section")
     p.add_argument("--inverse-steps", type=int, default=600,
@@ -381,6 +383,11 @@ def ours(args):
             result["probes"] = probe_bench(dev)
         except Exception as ex:  # report, never mask the main number
             result["probes"] = {"error": repr(ex)}
+    if not args.no_hierarchy and rank == 0:
+        try:
+            result["hierarchy"] = hierarchy_bench(dev)
+        except Exception as ex:  # noqa: BLE001
+            result["hierarchy"] = {"error": repr(ex)}
     if not args.no_variants and rank == 0:
         try:
             result["variants"] = variants_bench(dev)
@@ -747,6 +754,46 @@ def variants_bench(dev):
                 int(min(d for c, d in zip(cands, dist) if c.mapping != 2)),
             "note": "texture L1 (Sec. 4.3, bits 7-8) and 24 KB variant, LRU; Fermi L1 (Sec. 4.5) "
                     "weighted policy x 64 seeds; paper sweeps, 4 passes"}
+
+
+def hierarchy_bench(dev, reps: int = 3):
+    """Cache and TLB hierarchies (workloads.hierarchy_config: 1024 items, L1
+    16-256 KB -> L2 0.5-3 MB, and a 16-entry L1 TLB -> 8-way L2 TLB over 4 KB,
+    64 KB or 2 MB pages, 142 M trace accesses).  One step runs both cascades
+    (4 levels: L1, L2 on L1's misses, L1 TLB, L2 TLB on its misses).  Reports
+    trace accesses/s through both cascades, level accesses simulated per
+    second, and where the accesses were served."""
+    import torch
+
+    from paper_1509_02308_gb300 import api, workloads as W
+
+    l1, l2, t1, t2, runs = W.hierarchy_config()
+    flat, offs = api.pchase_build_batch(runs)
+    traces = [(flat[int(offs[i]):int(offs[i + 1])], r.length, r.warmup, r.n_elems, r.stride)
+              for i, r in enumerate(runs)]
+    pairs = [(i, i) for i in range(len(runs))]
+    data = api.HierarchyPlan([l1, l2], traces, pairs=pairs)
+    tlb = api.HierarchyPlan([t1, t2], traces, pairs=pairs)
+    out = data.run() + tlb.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        out = data.run() + tlb.run()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    total = sum(r.length for r in runs)
+    miss = [int(o[1].view(-1, 2)[:, 0].sum().item()) for o in out]  # L1, L2, TLB1, TLB2
+    level_accesses = 2 * total + miss[0] + miss[2]
+    return {"trace_accesses_per_s": total / (ms * 1e-3), "ms_per_step": ms,
+            "level_accesses_per_s": level_accesses / (ms * 1e-3), "items": len(runs),
+            "trace_accesses": total, "served_from": {
+                "l1": 1.0 - miss[0] / total, "l2": (miss[0] - miss[1]) / total,
+                "memory": miss[1] / total},
+            "translated_by": {"l1_tlb": 1.0 - miss[2] / total, "l2_tlb": (miss[2] - miss[3]) / total,
+                              "page_walk": miss[3] / total},
+            "plans": [p.description for p in data.plans + tlb.plans]}
 
 
 def learned_bench(args, dev):

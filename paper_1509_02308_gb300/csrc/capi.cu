@@ -255,7 +255,7 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
         uint32_t mode, ring;
         uint64_t arena;
         double cold_ns, warm_ns;
-    } opt[2];
+    } opt[3];
     int n_opt = 0;
     if (batch_ok) {
         Option o{kModeBatch, ring, batch, kStepBatchNs[pol], kStepBatchNs[pol]};
@@ -281,6 +281,14 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
                  round_ns, round_ns};
         if (!scan && sh.held && pol != PCHASE_LRU) o.warm_ns = kStepHeldTableNs;
         opt[n_opt++] = o;
+    }
+    if (!scan) {
+        // way scans keep no line table, so they fit streams over any line
+        // range: the fallback when the table modes do not fit (a scan costs
+        // in proportion to the ways past the ones the fit covers)
+        const double f = std::max(1.0, (double)a / std::max(1u, tn.scan_max_ways));
+        const double ns = (kStepScanNs[pol] + kRoundScanNs[pol] * (rounds - 1.0)) * f;
+        opt[n_opt++] = Option{kModeScan, 0u, 8 * lines + (randomish ? 4ull * Tl : 0), ns, ns};
     }
     // a whole item steps over its accesses as they come (direct) when that
     // beats gathering and compacting its heads (queued); a split part always
@@ -561,6 +569,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     }
     uint64_t word = 0;
     double total = 0.0;
+    const uint32_t max_split = std::max<uint32_t>(1, tn.max_split);
     for (uint64_t i = 0; i < n_items; ++i) {
         uint32_t g, t;
         if (p->cross) {
@@ -603,19 +612,33 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         item_shape(G, Tr, sh);
         UnitShape u;
         if (!unit_shape(G, it, 1, sh, tn, u)) {
-            delete p;
-            char buf[200];
-            snprintf(buf, sizeof buf,
-                     "item %llu needs %llu bytes of set state, above the %u-byte limit",
-                     (unsigned long long)i, (unsigned long long)u.arena, kMaxArena);
-            return fail(PCHASE_ERANGE, buf);
+            // too much set state for one warp: some split into set-parts must fit
+            uint64_t need = u.arena;
+            bool fits = false;
+            for (uint32_t K = 2; !fits && K <= max_split && K <= sh.groups && K <= sh.visited;
+                 ++K) {
+                const uint32_t odd = K % 3 == 0 ? K / 3 : K;
+                if ((odd & (odd - 1)) != 0 || sh.groups % K != 0) continue;
+                UnitShape uk;
+                fits = unit_shape(G, it, K, sh, tn, uk);
+                if (fits) u.cost = uk.cost * K;
+                need = std::min(need, (uint64_t)uk.arena);
+            }
+            if (!fits) {
+                delete p;
+                char buf[200];
+                snprintf(buf, sizeof buf,
+                         "item %llu needs %llu bytes of set state (in its smallest allowed part), "
+                         "above the %u-byte limit",
+                         (unsigned long long)i, (unsigned long long)need, kMaxArena);
+                return fail(PCHASE_ERANGE, buf);
+            }
         }
         sh.cost = u.cost;
         total += u.cost;
     }
     p->bitmap_words = word;
     p->filtered = tn.filtered != 0;
-    const uint32_t max_split = std::max<uint32_t>(1, tn.max_split);
     // Split target: no unit above the plan's share per warp slot, but no
     // split below what the longest unsplittable work takes anyway (splitting
     // costs a gather pass per part and only the critical path gains).
@@ -623,15 +646,18 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     auto best_split = [&](uint64_t i, double target, uint32_t &k_out, UnitShape &u_out) {
         const pchase_geom &G = geoms[base[i].cand];
         const ItemShape &sh = shape[i];
-        k_out = 1;
-        unit_shape(G, base[i], 1, sh, tn, u_out);
-        if (u_out.cost <= target) return;
+        // the whole item if it fits, else the first split that does
+        k_out = 0;
+        if (unit_shape(G, base[i], 1, sh, tn, u_out)) {
+            k_out = 1;
+            if (u_out.cost <= target) return;
+        }
         for (uint32_t K = 2; K <= max_split && K <= sh.groups && K <= sh.visited; ++K) {
             const uint32_t odd = K % 3 == 0 ? K / 3 : K;
             if ((odd & (odd - 1)) != 0 || sh.groups % K != 0) continue;
             UnitShape u;
             if (!unit_shape(G, base[i], K, sh, tn, u)) continue;
-            if (u.cost < u_out.cost * 0.97) {
+            if (k_out == 0 || u.cost < u_out.cost * 0.97) {
                 u_out = u;
                 k_out = K;
             }

@@ -274,6 +274,42 @@ def latency_noise_params():
             "spike_p": 0.005, "spike_lo": 2.0, "spike_hi": 10.0}
 
 
+# ------------------------------------------------------------- hierarchies
+def hierarchy_config(n_items: int = 1024, seed_base: int = 0x5EED0005):
+    """Two-level cache and two-level TLB hierarchies over P-chase streams (a
+    scaled-down mixed-hierarchy batch: L2 caches up to 3 MB, the most lines
+    one simulated geometry holds).  Item i draws from stream seed_base + i:
+      L1: C 16-256 KB (powers of two), b 32/64/128 B, 4/8/16 ways, a policy;
+      L2: C 0.5/1/2/3 MB, b 64/128 B, 8/16/32 ways, a policy;
+      TLBs (Sec. 4.4): a 16-entry fully associative L1 TLB and an 8-way L2 TLB
+      of 8-64 sets, both LRU, over 4 KB, 64 KB or 2 MB pages;
+      stream: s = 4 * 2^u B (u in 0..10), N = round_down(C_L2 * 2^v, s),
+      v in [-1, 1), length 16K * 32^x (x in [0, 1)), warm-up one pass.
+    Returns (l1, l2, tlb1, tlb2, runs), item i pairing entry i of each."""
+    l1, l2, t1, t2, runs = [], [], [], [], []
+    for i in range(n_items):
+        r = SplitMix64(seed_base + i)
+        a1 = 4 << r.below(3)
+        b1 = 32 << r.below(3)
+        C1 = (16 << 10) << r.below(5)
+        l1.append(Geom(C1, b1, a1, C1 // (a1 * b1), r.below(3), r.next()))
+        C2 = (512 << 10, 1 << 20, 2 << 20, 3 << 20)[r.below(4)]
+        b2 = 64 << r.below(2)
+        a2 = 8 << r.below(3)
+        l2.append(Geom(C2, b2, a2, C2 // (a2 * b2), r.below(3), r.next()))
+        page = (4096, 65536, 2 << 20)[r.below(3)]
+        sets2 = 8 << r.below(4)
+        t1.append(Geom(16 * page, page, 16, 1, LRU))
+        t2.append(Geom(sets2 * 8 * page, page, 8, sets2, LRU))
+        s_elems = 1 << r.below(11)
+        v = r.unit() * 2.0 - 1.0
+        n = max(s_elems, int(C2 * 2.0 ** v) // 4 // s_elems * s_elems)
+        L = int(16384 * 32.0 ** r.unit())
+        per = n // math.gcd(n, s_elems)
+        runs.append(Run(n, s_elems, L, min(per, L)))
+    return l1, l2, t1, t2, runs
+
+
 # --------------------------------------------------------- latency spectrum
 def spectrum_chain():
     """The non-uniform-stride chain of Sec. 5.2 (Fig. 10(b)), as element

@@ -79,6 +79,19 @@ def test_plan_accepts_mapping_and_weighted_policy():
     C.load().pchase_sim_plan_destroy(h)
 
 
+def test_plan_splits_items_too_large_for_one_warp():
+    # 2 MB, 64 B lines, 16 ways: 32768 lines of set state, more than one
+    # warp's shared memory holds; a stream over every set fits once split
+    g = W.Geom(2 << 20, 64, 16, 2048, 0)
+    tr = [(None, 200000, 0, (4 << 20) // 4, 16)]
+    rc, h = _plan([g], tr)
+    assert rc == C.OK
+    assert int(_describe(h)["units"]) > 1
+    C.load().pchase_sim_plan_destroy(h)
+    rc, _ = _plan([g], tr, tune={"max_split": 1})
+    assert rc == C.ERANGE
+
+
 def test_plan_rejects_bad_trace_and_pair():
     g = W.Geom(1024, 32, 4, 8)
     rc, _ = _plan([g], [(None, 10, 0, 0, 1)])
