@@ -783,11 +783,27 @@ def hierarchy_bench(dev, reps: int = 3):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
+    # each level alone (the same launches, timed one plan at a time)
+    level_ms = []
+    for k, plan in enumerate(data.plans + tlb.plans):
+        first = k in (0, len(data.plans))
+        prev = None if first else out[k - 1][0]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            if first:
+                plan.run()
+            else:
+                plan.run_filtered(prev, data._wo)
+        e1.record()
+        torch.cuda.synchronize()
+        level_ms.append(e0.elapsed_time(e1) / reps)
     total = sum(r.length for r in runs)
     miss = [int(o[1].view(-1, 2)[:, 0].sum().item()) for o in out]  # L1, L2, TLB1, TLB2
     level_accesses = 2 * total + miss[0] + miss[2]
     return {"trace_accesses_per_s": total / (ms * 1e-3), "ms_per_step": ms,
             "level_accesses_per_s": level_accesses / (ms * 1e-3), "items": len(runs),
+            "ms_by_level": dict(zip(("l1", "l2", "l1_tlb", "l2_tlb"), level_ms)),
             "trace_accesses": total, "served_from": {
                 "l1": 1.0 - miss[0] / total, "l2": (miss[0] - miss[1]) / total,
                 "memory": miss[1] / total},
