@@ -105,7 +105,9 @@ def test_latency_spectrum_chain_walk():
     arr[torch.tensor(path, dtype=torch.int64, device="cuda")] = torch.tensor(
         path[1:] + path[:1], dtype=torch.int32, device="cuda")
     lab = np.array(labels)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     for mode in (0, 1):
+        flush.fill_(1)  # the chain's lines out of L2 (the scatter and the last walk put them there)
         lat, vis, _, st = api.pchase_probe_latency(arr, n, iters=len(path), start=path[0],
                                                    cache_mode=mode)
         torch.cuda.synchronize()
@@ -113,5 +115,5 @@ def test_latency_spectrum_chain_walk():
         assert np.array_equal(vis.cpu().numpy().view(np.uint32), np.array(path, dtype=np.uint32))
         l = lat.cpu().numpy().view(np.uint32)
         assert np.median(l[lab == "D_same_line"]) < np.median(l[lab == "A_32MB"])
-    del arr
+    del arr, flush
     torch.cuda.empty_cache()
