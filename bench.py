@@ -165,8 +165,8 @@ class ClockSampler:
 
 # From one ncu capture (--set full) of the current sim_kernel on the batched
 # workload with items capped at 65,536 accesses.
-SIM_DRAM_BYTES_PER_ACCESS = (265.908224e6 + 7.31008e6) / 65559830
-SIM_WARP_INST_PER_ACCESS = 359570620 / 65559830
+SIM_DRAM_BYTES_PER_ACCESS = (265.572352e6 + 7.504896e6) / 65559830
+SIM_WARP_INST_PER_ACCESS = 413135353 / 65559830
 
 
 def measured_peaks():
