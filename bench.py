@@ -72,7 +72,7 @@ def parse():
                    help="skip the cache / TLB hierarchy section")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the set-mapping / weighted-policy section")
-    p.add_argument("--inverse-steps", type=int, default=600,
+    p.add_argument("--inverse-steps", type=int, default=2442,
                    help="training steps of 4096 synthetic traces for the learned inverse")
     p.add_argument("--inverse-eval", type=int, default=100000)
     p.add_argument("--ref-items-per-step", type=int, default=256)
@@ -855,7 +855,7 @@ def learned_bench(args, dev):
     net.classify(x[:1024], l2c_t, rates, 0.9)
     INV.lsq_match(rates, x[:1024])
     out = {}
-    for thr in (0.5, 0.7, 0.8, 0.9, 0.97):
+    for thr in (0.5, 0.6, 0.7, 0.8, 0.9, 0.97):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cand, nf = net.classify(x, l2c_t, rates, thr)
