@@ -404,6 +404,7 @@ struct pchase_sim_plan {
     bool filtered = false;  // every unit queued (pchase_sim_run_filtered)
     // runtime state, set on the first run
     int device = -1, sms = 0, grid = 0, jgrid = 0;
+    uint64_t n_isolated = 0;  // units given an SM of their own (in the jumbo launch)
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
 
@@ -425,16 +426,25 @@ int plan_runtime(pchase_sim_plan *p) {
     }
     p->sms = sm_count();
     if (p->sms <= 0) return fail(PCHASE_ECUDA, "no CUDA device");
+    // A CTA of either launch fills an SM's shared memory, so a main launch
+    // started over every SM would hold them all.  A one-warp launch of a few
+    // units (the isolated ones among them) gets an SM per unit, kept out of
+    // the main grid; one of many units takes SMs as main CTAs leave.
+    int jsms = 0;
+    if (p->jumbo.nwarps && p->layout.nwarps && p->n_jumbo <= 16 &&
+        (int)p->n_jumbo < p->sms / 2)
+        jsms = (int)p->n_jumbo;
     if (p->layout.nwarps) {
         const int per = sim_max_ctas_per_sm(p->layout);
         if (per <= 0) return fail(PCHASE_ECUDA, "simulator kernel cannot be resident");
         p->grid = (int)std::max<uint64_t>(
-            1, std::min<uint64_t>((uint64_t)per * p->sms, p->n_units - p->n_jumbo));
+            1, std::min<uint64_t>((uint64_t)per * (p->sms - jsms), p->n_units - p->n_jumbo));
     }
     if (p->jumbo.nwarps) {
         const int per = sim_max_ctas_per_sm(p->jumbo);
         if (per <= 0) return fail(PCHASE_ECUDA, "simulator kernel cannot be resident");
-        p->jgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)per * p->sms, p->n_jumbo));
+        p->jgrid = (int)std::max<uint64_t>(
+            1, std::min<uint64_t>((uint64_t)per * (jsms ? jsms : p->sms), p->n_jumbo));
         PCHASE_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "cudaStreamCreate");
         PCHASE_CUDA(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming), "cudaEventCreate");
         PCHASE_CUDA(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming), "cudaEventCreate");
@@ -723,6 +733,27 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         int c = 0;
         while (kCaps[c] < items[i].arena_bytes) ++c;
         cls[i] = c;
+    }
+    // The few units that set the plan's length (the 8 costliest within 30 %
+    // of the costliest, when the plan has far more work than they do) run
+    // alone on an SM: given the largest class, they go to the one-warp launch,
+    // whose CTAs fill an SM's shared memory, so no other warp slows their
+    // dependent chains down.
+    if (n_units > 64) {
+        double cmax = 0.0, csum = 0.0;
+        for (uint64_t i = 0; i < n_units; ++i) {
+            cmax = std::max(cmax, cost[i]);
+            csum += cost[i];
+        }
+        std::vector<uint64_t> top;
+        for (uint64_t i = 0; i < n_units; ++i)
+            if (cost[i] >= 0.7 * cmax) top.push_back(i);
+        std::sort(top.begin(), top.end(), [&](uint64_t x, uint64_t y) { return cost[x] > cost[y]; });
+        if (top.size() > 8) top.resize(8);
+        if (csum > 64.0 * cmax) {
+            for (uint64_t i : top) cls[i] = ncap - 1;
+            p->n_isolated = top.size();
+        }
     }
     std::vector<uint64_t> order(n_units);
     for (uint64_t i = 0; i < n_units; ++i) order[i] = i;
