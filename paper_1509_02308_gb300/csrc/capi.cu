@@ -242,11 +242,11 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     u.sets = Tl;
     u.table_n = (uint32_t)std::min<uint64_t>(table_n, 0xFFFFFFFFull);
     // candidates: batch mode (eligible for T' <= batch_max_sets, or when many
-    // same-set heads per step make rounds costly, as long as the unit still
-    // fits the shared slot mix) and the round-based scan / table mode; each
+    // same-set heads per step make rounds costly, as long as the unit fits
+    // one warp's arena) and the round-based scan / table mode; each
     // with its cost per step while lines are first touched (cold) and after
-    const bool many_rounds =
-        rounds >= kBatchRounds && 2 * (kStageBytes + batch) <= tn.smem_budget_bytes;
+    // (a batch arena above half the CTA budget runs in the one-warp launch)
+    const bool many_rounds = rounds >= kBatchRounds && kStageBytes + batch <= kMaxArena;
     const bool batch_ok = tn.batch_max_sets && (Tl <= tn.batch_max_sets || many_rounds) &&
                           kStageBytes + batch <= kMaxArena && ring <= 32768;
     const bool scan = a <= tn.scan_max_ways;
@@ -431,7 +431,7 @@ int plan_runtime(pchase_sim_plan *p) {
     // units (the isolated ones among them) gets an SM per unit, kept out of
     // the main grid; one of many units takes SMs as main CTAs leave.
     int jsms = 0;
-    if (p->jumbo.nwarps && p->layout.nwarps && p->n_jumbo <= 16 &&
+    if (p->jumbo.nwarps && p->layout.nwarps && p->n_jumbo <= 32 &&
         (int)p->n_jumbo < p->sms / 2)
         jsms = (int)p->n_jumbo;
     if (p->layout.nwarps) {
