@@ -856,6 +856,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             }
         L.nwarps = w;
         L.smem_bytes = off;
+        // first-pop stagger: 4 us per slot for plans of long units, a
+        // 2000th of the longest unit's estimate below that
+        L.stagger_ns = (uint32_t)std::min(4000.0, p->est_max_unit / 2000.0);
         // jumbo layout: one warp, the largest jumbo arena; serves jumbo classes
         SlotLayout &J = p->jumbo;
         memset(&J, 0, sizeof J);

@@ -141,6 +141,7 @@ struct SlotLayout {
     uint32_t nclasses;
     uint32_t smem_bytes;                      // dynamic shared memory per CTA
     uint32_t pad;                             // lowest class a warp may take
+    uint32_t stagger_ns;                      // first pop of warp w waits w * this
     uint32_t warp_class[kMaxWarpsPerCta];     // class served first by warp w
     uint32_t warp_off[kMaxWarpsPerCta];       // byte offset of warp w's arena
     uint32_t cls_first[kMaxClasses];          // first item of class c (sorted table)

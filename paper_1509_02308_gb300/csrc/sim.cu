@@ -1307,11 +1307,12 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
     const uint32_t cnt = (watch ? L.cls_count[wc] : 0u) * nrep;
     const uint32_t first = watch ? L.cls_first[wc] : 0u;
     const bool prune = out.dist != nullptr && out.stop_above != ~0ull;
-    // First pops staggered by slot (4 us apart, a bounded sleep): slot 0 of
-    // every CTA, which holds every class, takes the costliest units first, one
-    // per SM, instead of whichever SM's warps reach the queues first taking
-    // several of the long units side by side.
-    if (warp > 0) __nanosleep(4000u * (uint32_t)warp);
+    // First pops staggered by slot (up to 4 us apart, a bounded sleep; the
+    // planner scales it to the plan's longest unit): slot 0 of every CTA,
+    // which holds every class, takes the costliest units first, one per SM,
+    // instead of whichever SM's warps reach the queues first taking several
+    // of the long units side by side.
+    if (warp > 0 && L.stagger_ns) __nanosleep(L.stagger_ns * (uint32_t)warp);
     for (;;) {
         // longest first: the class whose next unit costs most
         uint32_t key = 0;
