@@ -424,8 +424,11 @@ struct BatchFR {
             insw = evicts ? random_way(seed, global_set(set, psh, kcnt, kres), m.y + (k - a), a, wtd)
                           : k;
         }
-        const uint32_t sw = __match_any_sync(kFull, head ? set * a + insw
-                                                          : (0x80000000u | (uint32_t)lane));
+        // FIFO groups of at most a misses write distinct ways (p + L + r mod a)
+        const uint32_t sw =
+            (POLICY == PCHASE_FIFO && __all_sync(kFull, !head || M <= a))
+                ? (1u << lane)
+                : __match_any_sync(kFull, head ? set * a + insw : (0x80000000u | (uint32_t)lane));
         // the first writer of a way that was in use evicts the line it held
         // (a line of the step is written again only after its earlier way
         // was taken over, so only last writers stay)
@@ -657,7 +660,18 @@ struct BatchLRU {
         // or past the step's own lines that do not stay
         uint32_t new_tail = m.y + (D > a ? D - a : 0u), evd = 0;
         bool found = false;
-        for (uint32_t p0 = m.x; p0 < m.y && (evd < E || !found); p0 += 32) {
+        if (m.w) {
+            // compact ring: the E oldest held lines are positions tail .. tail+E-1
+            for (uint32_t q = (uint32_t)lane; q < E; q += 32) {
+                const uint32_t pq = (m.x + q) & rmask;
+                tab[rg[pq]] = 0;
+                rg[pq] = kStale;
+            }
+            found = E < m.z;
+            if (found) new_tail = m.x + E;
+            evd = E;
+        }
+        for (uint32_t p0 = m.x; !m.w && p0 < m.y && (evd < E || !found); p0 += 32) {
             const uint32_t p = p0 + (uint32_t)lane;
             const uint32_t e = p < m.y ? rg[p & rmask] : kStale;
             const bool live = e != kStale;
