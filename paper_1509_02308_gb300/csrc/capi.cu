@@ -734,7 +734,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         while (kCaps[c] < items[i].arena_bytes) ++c;
         cls[i] = c;
     }
-    // The few units that set the plan's length (the 8 costliest within 30 %
+    // The few units that set the plan's length (the 12 costliest within 40 %
     // of the costliest, when the plan has far more work than they do) run
     // alone on an SM: given the largest class, they go to the one-warp launch,
     // whose CTAs fill an SM's shared memory, so no other warp slows their
@@ -747,9 +747,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         }
         std::vector<uint64_t> top;
         for (uint64_t i = 0; i < n_units; ++i)
-            if (cost[i] >= 0.7 * cmax) top.push_back(i);
+            if (cost[i] >= 0.6 * cmax) top.push_back(i);
         std::sort(top.begin(), top.end(), [&](uint64_t x, uint64_t y) { return cost[x] > cost[y]; });
-        if (top.size() > 8) top.resize(8);
+        if (top.size() > 12) top.resize(12);
         if (csum > 64.0 * cmax) {
             for (uint64_t i : top) cls[i] = ncap - 1;
             p->n_isolated = top.size();
