@@ -681,12 +681,12 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         best_split(i, 0.0, k, u);
         critical = std::max(critical, u.cost);
     }
-    // (0.75 of the critical estimate: the estimates scatter by about that
+    // (0.6 of the critical estimate: the estimates scatter by about that
     // much, and a split unit near the critical one costs little once the
     // other work has drained)
     const double target = tn.split_cost_ns
                               ? (double)tn.split_cost_ns
-                              : std::max({total / (kPlanSms * 36.0), 0.75 * critical, 2.0e5});
+                              : std::max({total / (kPlanSms * 36.0), 0.6 * critical, 2.0e5});
     p->est_critical = critical;
     p->est_target = target;
     std::vector<SimItem> items;
