@@ -150,8 +150,10 @@ typedef struct {
     uint32_t ctas_per_sm_cap;    /* 0 = as many as fit */
     uint32_t batch_max_sets;     /* T <= this: whole-step batch resolution per set (default 64;
                                     0 keeps the default, 0xFFFFFFFF disables batch mode) */
-    uint32_t max_split;          /* most parts a long item's sets are split into (power of two,
-                                    default 32; 1 = never split) */
+    uint32_t max_split;          /* most parts a long item's sets are split into (2^j or
+                                    3 * 2^j, default 32; 1 = never split).  An LRU item
+                                    whose sets do not split is cut in time instead, into at
+                                    most min(this, 16) parts of whole 1024-access blocks */
     uint32_t split_cost_ns;      /* split items whose estimated warp time is above this
                                     (0 = automatic, from the whole plan's estimated work) */
     uint32_t filtered;           /* 1: the plan is a lower level of a hierarchy; every unit
@@ -190,8 +192,9 @@ uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);
  * pchase_match_run queues one fewer (no output clear). */
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
 /*
- * Writes a one-line text description of the plan (units per set mode, units
- * that step over their accesses directly, size classes, the per-CTA slot mix,
+ * Writes a one-line text description of the plan (items split by sets and
+ * cut in time, units per set mode, units that step over their accesses
+ * directly, size classes, the per-CTA slot mix,
  * and the cost model's estimates in ms of one
  * warp: est_ms=<longest unsplittable unit>,<split target>,<longest unit>,<sum>)
  * into buf (host, `bytes` long, always NUL-terminated); returns the length the

@@ -109,6 +109,8 @@ constexpr double kStepHeldTableNs = 435.0;
 constexpr double kStepNoHitFifoNs = 1060.0;
 constexpr double kStepNoHitLruNs = 600.0, kNoHitLruSetNs = 480.0;
 constexpr double kGatherNs = 350.0;
+// A time part's backward read of 32 accesses while it rebuilds the recency order.
+constexpr double kRebuildNs = 300.0;
 constexpr double kBatchRounds = 6.0;   // this many rounds: batch mode whatever T'
 constexpr double kPlanSms = 152.0;     // SMs the automatic split target assumes
 
@@ -674,12 +676,60 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             if (u_out.cost <= target) break;
         }
     };
+    // An LRU item stepped directly whose sets do not split is cut in time
+    // instead: P parts of whole 1024-access blocks (so every bitmap word has
+    // one writer), each part after the first first reading the trace back
+    // until every set holds its a most recent lines (the LRU stack property:
+    // that is the whole set state).  Returns P (1: no cut) and the costliest
+    // part; bounds gets the parts' first steps and the end, pcost their costs.
+    auto time_split = [&](uint64_t i, const UnitShape &u, double tgt, double &pmax_cost,
+                          std::vector<uint32_t> *bounds, std::vector<double> *pcost) -> uint32_t {
+        const SimItem &b = base[i];
+        const ItemShape &sh = shape[i];
+        const pchase_geom &G = geoms[b.cand];
+        pmax_cost = u.cost;
+        const uint32_t nsteps = (b.len + 31) / 32, nblk = (nsteps + 31) / 32;
+        if (G.policy != PCHASE_LRU || !u.direct || u.mode != kModeBatch || u.cost <= tgt)
+            return 1;
+        const uint32_t pmax = std::min({max_split, 16u, nblk});
+        // accesses read back before every set is full (a set that never
+        // fills makes the read go back to the trace's start)
+        const double fill = !sh.held && sh.visited >= (double)G.sets ? 1.5 * sh.cold + 1024.0
+                                                                     : 1e300;
+        auto bound = [&](uint32_t j, uint32_t P) {
+            return std::min(nsteps, (uint32_t)((uint64_t)nblk * j / P) * 32);
+        };
+        auto part_cost = [&](uint32_t j, uint32_t P) {
+            const uint32_t s0 = bound(j, P), s1 = bound(j + 1, P);
+            const double rb = j ? std::min(32.0 * s0, fill) / 32.0 * kRebuildNs : 0.0;
+            return u.cost * (s1 - s0) / nsteps + rb;
+        };
+        uint32_t best_p = 1;
+        for (uint32_t P = 2; P <= pmax; ++P) {
+            double mx = 0.0;
+            for (uint32_t j = 0; j < P; ++j) mx = std::max(mx, part_cost(j, P));
+            if (mx < pmax_cost * 0.97) {
+                pmax_cost = mx;
+                best_p = P;
+            }
+            if (pmax_cost <= tgt) break;
+        }
+        if (bounds && best_p > 1) {
+            bounds->clear();
+            pcost->clear();
+            for (uint32_t j = 0; j <= best_p; ++j) bounds->push_back(bound(j, best_p));
+            for (uint32_t j = 0; j < best_p; ++j) pcost->push_back(part_cost(j, best_p));
+        }
+        return best_p;
+    };
     double critical = 0.0;
     for (uint64_t i = 0; i < n_items; ++i) {
         uint32_t k;
         UnitShape u;
         best_split(i, 0.0, k, u);
-        critical = std::max(critical, u.cost);
+        double c = u.cost;
+        if (k == 1) time_split(i, u, 0.0, c, nullptr, nullptr);
+        critical = std::max(critical, c);
     }
     // (0.6 of the critical estimate: the estimates scatter by about that
     // much, and a split unit near the critical one costs little once the
@@ -701,6 +751,28 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             uint32_t best_k;
             UnitShape best;
             best_split(i, target, best_k, best);
+            if (best_k == 1) {
+                double part_max;
+                std::vector<uint32_t> bounds;
+                std::vector<double> pcost;
+                const uint32_t P = time_split(i, best, target, part_max, &bounds, &pcost);
+                if (P > 1) {
+                    for (uint32_t j = 0; j < P; ++j) {
+                        SimItem it = base[i];
+                        apply_unit(it, best);
+                        it.ks1 = 1;
+                        it.kres = bounds[j];
+                        it.kmagic = bounds[j + 1];
+                        it.lead = j == 0;
+                        it.cost = (float)pcost[j];
+                        items.push_back(it);
+                        cost.push_back(it.cost);
+                        p->est_sum += it.cost;
+                        p->est_max_unit = std::max(p->est_max_unit, (double)it.cost);
+                    }
+                    continue;
+                }
+            }
             const DivMagic kdm = make_div_magic(best_k);
             for (uint32_t r = 0; r < best_k; ++r) {
                 SimItem it = base[i];
@@ -915,18 +987,20 @@ uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
 size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes) {
     std::string d;
     if (plan) {
-        uint64_t modes[3] = {0, 0, 0}, split = 0, direct = 0;
+        uint64_t modes[3] = {0, 0, 0}, split = 0, direct = 0, tsplit = 0;
         for (const SimItem &it : plan->items) {
             modes[it.mode < 3 ? it.mode : 0]++;
             split += it.kcnt > 1 && it.lead;
+            tsplit += it.kcnt == 1 && it.ks1 && it.lead;
             direct += it.direct;
         }
         char tmp[256];
         snprintf(tmp, sizeof tmp,
-                 "items=%llu units=%llu split=%llu scan=%llu table=%llu batch=%llu direct=%llu "
-                 "jumbo=%llu classes=%u warps=%u smem=%u slots=",
+                 "items=%llu units=%llu split=%llu time_split=%llu scan=%llu table=%llu "
+                 "batch=%llu direct=%llu jumbo=%llu classes=%u warps=%u smem=%u slots=",
                  (unsigned long long)plan->n_items, (unsigned long long)plan->n_units,
-                 (unsigned long long)split, (unsigned long long)modes[0],
+                 (unsigned long long)split, (unsigned long long)tsplit,
+                 (unsigned long long)modes[0],
                  (unsigned long long)modes[1], (unsigned long long)modes[2],
                  (unsigned long long)direct,
                  (unsigned long long)plan->n_jumbo, plan->layout.nclasses, plan->layout.nwarps,

@@ -83,6 +83,11 @@ enum SetMode : uint8_t { kModeScan = 0, kModeTable = 1, kModeBatch = 2 };
 // its sets are split: unit r owns the sets s with (s >> psh) mod K == r,
 // renumbered locally as (((s >> psh) div K) << psh) | (s & (2^psh - 1)), and
 // sees each line as the local line  local set + T' * (line div T), T' = T / K.
+// A whole LRU item that steps directly over its accesses may instead be cut in
+// time: a unit with kcnt = 1 and ks1 = 1 covers steps [kres, kmagic) (32
+// accesses a step, bounds multiples of 32 steps so that every bitmap word has
+// one writer) and first rebuilds the sets' recency order from the accesses
+// before its first one.
 struct SimItem {
     const uint32_t *idx;  // NULL: analytic uniform chain
     uint32_t len;

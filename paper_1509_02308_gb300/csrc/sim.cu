@@ -601,6 +601,10 @@ struct BatchLRU {
         ways = it.ways;
         R = it.ring;
         rmask = R - 1;
+        sets_m = it.magic_m;
+        sets_s1 = it.s1;
+        sets_s2 = it.s2;
+        nsets = it.sets;
         size_t off = 0;
         perm = reinterpret_cast<uint32_t *>(arena);
         off += 256;
@@ -704,6 +708,55 @@ struct BatchLRU {
         const uint32_t cpt = (m.w || !found) ? 1u : 0u;
         if (lane == 0) meta[s] = make_uint4(new_tail, m.y + D, D <= a ? m.z - E + D : a, cpt);
         __syncwarp();
+    }
+
+    // The state at access c0 of a time part: every set's a most recent
+    // distinct lines before c0, newest last (by the stack property that is
+    // the whole of an LRU set's state).  The trace is read backwards 32
+    // accesses at a time; the newest occurrence of a line not yet taken goes
+    // below the set's lines taken so far, until every set holds a lines or
+    // the trace's start is reached.  load(t) gives the line of access t, or
+    // kInvalidLine for an access the simulation skips.
+    template <typename Load>
+    __device__ __forceinline__ void rebuild(uint32_t c0, uint32_t T, int lane, uint32_t lt,
+                                            Load load) {
+        const uint32_t a = ways;
+        uint32_t full = 0;
+        // the line of the next chunk back is loaded one chunk ahead
+        int64_t tn = (int64_t)c0 - 32 + lane;
+        uint32_t nx = tn >= 0 ? load((uint32_t)tn) : kInvalidLine;
+        for (int64_t b = c0; b > 0 && full < T; b -= 32) {
+            const uint32_t ln = nx;
+            tn -= 32;
+            nx = tn >= 0 ? load((uint32_t)tn) : kInvalidLine;
+            const bool valid = ln != kInvalidLine;
+            const uint32_t set = valid ? set_of(ln) : 0u;
+            const uint32_t lm = __match_any_sync(kFull, valid ? ln : (0x80000000u | (uint32_t)lane));
+            const bool newest = valid && (lm & ~(lt | (1u << lane))) == 0;
+            const bool cand = newest && tab[ln] == 0;
+            const uint32_t sm = __match_any_sync(kFull, cand ? set : (0x80000000u | (uint32_t)lane));
+            const uint32_t k = cand ? meta[set].y : 0u;
+            const uint32_t q = k + (uint32_t)__popc(sm & ~(lt | (1u << lane)));  // newer ones first
+            const bool lead_s = cand && (sm & lt) == 0;
+            full += (uint32_t)__popc(
+                __ballot_sync(kFull, lead_s && k < a && k + (uint32_t)__popc(sm) >= a));
+            __syncwarp();
+            if (cand && q < a) {
+                ring[(size_t)set * R + (a - 1 - q)] = ln;
+                tab[ln] = (uint16_t)(a - q);
+            }
+            if (lead_s) meta[set].y = min(a, k + (uint32_t)__popc(sm));
+            __syncwarp();
+        }
+        for (uint32_t s = (uint32_t)lane; s < T; s += 32) {
+            const uint32_t k = meta[s].y;
+            meta[s] = make_uint4(a - k, a, k, 1u);
+        }
+        __syncwarp();
+    }
+    uint32_t sets_m, sets_s1, sets_s2, nsets;
+    __device__ __forceinline__ uint32_t set_of(uint32_t ln) const {
+        return ln - div_q(ln, sets_m, sets_s1, sets_s2) * nsets;
     }
 
     // All set groups at once.  A group of g heads can push out at most g
@@ -1123,11 +1176,36 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
         // consecutive accesses as they come (repeats ride along as hits) and
         // the unit, sole writer of its words, stores 32 steps' words at once
         const uint32_t nsteps = (len + 31) >> 5;
+        // a time part of an LRU item (whole sets, ks1 = 1) runs steps
+        // [kres, kmagic) only, from the set state its first access sees
+        const bool tpart = K == 1 && ks1 != 0 && kind == kBatchLru;
+        const uint32_t sfirst = tpart ? min(kres, nsteps) : 0u;
+        const uint32_t send = tpart ? min(km, nsteps) : nsteps;
         uint32_t carry = kInvalidLine, myword = 0;
-        uint32_t pf = (idxp && (uint32_t)lane < len) ? idxp[lane] : 0u;
+        if (sfirst && sfirst < send) {
+            // index of access t, and its line as the steps see it
+            auto index_at = [&](uint32_t t) -> uint32_t {
+                return idxp ? idxp[t] : (N ? (uint32_t)(((uint64_t)t * it.stride) % N) : 0u);
+            };
+            auto line_of = [&](uint32_t j) -> uint32_t {
+                const uint32_t ln = j >> lsh;
+                return mk ? remap_line(ln, mk, gT, gm, gs1, gs2) : ln;
+            };
+            BatchLRU S;
+            S.bind(st, it);
+            S.rebuild(sfirst << 5, sets, lane, lt, [&](uint32_t t) -> uint32_t {
+                const uint32_t j = index_at(t);
+                return j < N ? line_of(j) : kInvalidLine;
+            });
+            carry = line_of(index_at((sfirst << 5) - 1));
+            if (!idxp && N)
+                aj = (uint32_t)((((uint64_t)(sfirst << 5) + (uint32_t)lane) * it.stride) % N);
+        }
+        const uint32_t t1 = (sfirst << 5) + (uint32_t)lane;
+        uint32_t pf = (idxp && t1 < len) ? idxp[t1] : 0u;
         // matcher: the observed word of the step, loaded one step ahead
-        uint32_t pw = (ham && len) ? observed[obase] : 0u;
-        for (uint32_t s0 = 0; s0 < nsteps; ++s0) {
+        uint32_t pw = (ham && len) ? observed[obase + sfirst] : 0u;
+        for (uint32_t s0 = sfirst; s0 < send; ++s0) {
             const uint32_t t = (s0 << 5) + (uint32_t)lane;
             bool active = t < len;
             uint32_t j;
@@ -1169,7 +1247,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             }
             const uint32_t slot = s0 & 31;
             if ((uint32_t)lane == slot) myword = bits;
-            if (slot == 31 || s0 + 1 == nsteps) {
+            if (slot == 31 || s0 + 1 == send) {
                 const uint32_t w0 = s0 & ~31u;
                 if ((uint32_t)lane <= slot && bm) bm[w0 + lane] = myword;
                 myword = 0;

@@ -139,7 +139,8 @@ def test_plan_sizes_and_layout():
 def test_planner_splits_only_what_can_gain():
     """Host-side split rules: a split part owns a power-of-two share of the
     sets the trace actually visits; fully associative caches and traces whose
-    stride keeps them in one set stay whole; splitting is off at max_split 1."""
+    stride keeps them in one set do not split by sets, and (LRU) are cut in
+    time instead; splitting is off at max_split 1."""
     L = C.load()
     geoms = [W.Geom(64 * 8 * 64, 64, 8, 64),   # T = 64
              W.Geom(8 * 64, 64, 8, 1),          # fully associative
@@ -157,17 +158,18 @@ def test_planner_splits_only_what_can_gain():
         # T=96 with the dense trace: up to 8 parts (K must divide the set groups
         # and be 2^j or 3 * 2^j); with the 4 KB stride the visited sets are the
         # multiples of 32, three set groups, so K = 3.
-        # (how many parts the dense items get depends on the cost model)
+        # (how many parts the dense items get depends on the cost model).
+        # The three items that stay whole by sets are cut in time into 2 .. 8.
         assert int(d["items"]) == 6
-        assert int(d["split"]) == 3
-        assert 3 + 3 + 2 + 2 <= int(d["units"]) <= 3 + 3 + 8 + 8
+        assert int(d["split"]) == 3 and int(d["time_split"]) == 3
+        assert 3 + 2 + 2 + 3 * 2 <= int(d["units"]) <= 3 + 8 + 8 + 3 * 8
     finally:
         L.pchase_sim_plan_destroy(h)
     rc, h = _plan(geoms, traces, tune={"max_split": 1, "split_cost_ns": 1})
     assert rc == C.OK
     try:
         d = _describe(h)
-        assert int(d["split"]) == 0 and int(d["units"]) == 6
+        assert int(d["split"]) == 0 and int(d["time_split"]) == 0 and int(d["units"]) == 6
     finally:
         L.pchase_sim_plan_destroy(h)
 
