@@ -109,8 +109,10 @@ constexpr double kStepHeldTableNs = 435.0;
 constexpr double kStepNoHitFifoNs = 1060.0;
 constexpr double kStepNoHitLruNs = 600.0, kNoHitLruSetNs = 480.0;
 constexpr double kGatherNs = 350.0;
-// A time part's backward read of 32 accesses while it rebuilds the recency order.
-constexpr double kRebuildNs = 300.0;
+// A time part's backward read of 32 accesses while it rebuilds the recency
+// order: while lines are still being taken, and once every line read is taken
+// or in a full set.
+constexpr double kRebuildNs = 300.0, kRebuildSkipNs = 60.0;
 constexpr double kBatchRounds = 6.0;   // this many rounds: batch mode whatever T'
 constexpr double kPlanSms = 152.0;     // SMs the automatic split target assumes
 
@@ -692,16 +694,20 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         if (G.policy != PCHASE_LRU || !u.direct || u.mode != kModeBatch || u.cost <= tgt)
             return 1;
         const uint32_t pmax = std::min({max_split, 16u, nblk});
-        // accesses read back before every set is full (a set that never
-        // fills makes the read go back to the trace's start)
-        const double fill = !sh.held && sh.visited >= (double)G.sets ? 1.5 * sh.cold + 1024.0
-                                                                     : 1e300;
+        // accesses read back before every line met is taken or in a full set
+        // (after that the read skips ahead, to the trace's start if a set
+        // never fills)
+        const double fill = 1.5 * sh.cold + 1024.0;
+        const bool fills = !sh.held && sh.visited >= (double)G.sets;
         auto bound = [&](uint32_t j, uint32_t P) {
             return std::min(nsteps, (uint32_t)((uint64_t)nblk * j / P) * 32);
         };
         auto part_cost = [&](uint32_t j, uint32_t P) {
             const uint32_t s0 = bound(j, P), s1 = bound(j + 1, P);
-            const double rb = j ? std::min(32.0 * s0, fill) / 32.0 * kRebuildNs : 0.0;
+            const double back = 32.0 * s0;
+            const double rb = j ? std::min(back, fill) / 32.0 * kRebuildNs +
+                                      (fills ? 0.0 : std::max(0.0, back - fill) / 32.0 * kRebuildSkipNs)
+                                : 0.0;
             return u.cost * (s1 - s0) / nsteps + rb;
         };
         uint32_t best_p = 1;

@@ -722,24 +722,19 @@ struct BatchLRU {
                                             Load load) {
         const uint32_t a = ways;
         uint32_t full = 0;
-        // the line of the next chunk back is loaded one chunk ahead
-        int64_t tn = (int64_t)c0 - 32 + lane;
-        uint32_t nx = tn >= 0 ? load((uint32_t)tn) : kInvalidLine;
-        for (int64_t b = c0; b > 0 && full < T; b -= 32) {
-            const uint32_t ln = nx;
-            tn -= 32;
-            nx = tn >= 0 ? load((uint32_t)tn) : kInvalidLine;
+        auto chunk = [&](uint32_t ln) {
             const bool valid = ln != kInvalidLine;
             const uint32_t set = valid ? set_of(ln) : 0u;
+            // a chunk whose lines are all taken or in full sets changes nothing
+            const bool need = valid && tab[ln] == 0 && meta[set].y < a;
+            if (!__any_sync(kFull, need)) return;
             const uint32_t lm = __match_any_sync(kFull, valid ? ln : (0x80000000u | (uint32_t)lane));
-            const bool newest = valid && (lm & ~(lt | (1u << lane))) == 0;
-            const bool cand = newest && tab[ln] == 0;
+            const bool cand = need && (lm & ~(lt | (1u << lane))) == 0;  // newest in the chunk
             const uint32_t sm = __match_any_sync(kFull, cand ? set : (0x80000000u | (uint32_t)lane));
             const uint32_t k = cand ? meta[set].y : 0u;
             const uint32_t q = k + (uint32_t)__popc(sm & ~(lt | (1u << lane)));  // newer ones first
             const bool lead_s = cand && (sm & lt) == 0;
-            full += (uint32_t)__popc(
-                __ballot_sync(kFull, lead_s && k < a && k + (uint32_t)__popc(sm) >= a));
+            full += (uint32_t)__popc(__ballot_sync(kFull, lead_s && k + (uint32_t)__popc(sm) >= a));
             __syncwarp();
             if (cand && q < a) {
                 ring[(size_t)set * R + (a - 1 - q)] = ln;
@@ -747,6 +742,24 @@ struct BatchLRU {
             }
             if (lead_s) meta[set].y = min(a, k + (uint32_t)__popc(sm));
             __syncwarp();
+        };
+        // chunks of 32 accesses, newest first; the lines of the next kAhead
+        // chunks back are loaded while these are taken
+        constexpr int kAhead = 4;
+        uint32_t v[kAhead];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            const int64_t t = (int64_t)c0 - 32 * (k + 1) + lane;
+            v[k] = t >= 0 ? load((uint32_t)t) : kInvalidLine;
+        }
+        for (int64_t b = c0; b > 0 && full < T; b -= 32 * kAhead) {
+#pragma unroll
+            for (int k = 0; k < kAhead; ++k) {
+                const uint32_t ln = v[k];
+                const int64_t t = b - 32 * (kAhead + k + 1) + lane;
+                v[k] = t >= 0 ? load((uint32_t)t) : kInvalidLine;
+                if (b - 32 * k > 0 && full < T) chunk(ln);
+            }
         }
         for (uint32_t s = (uint32_t)lane; s < T; s += 32) {
             const uint32_t k = meta[s].y;

@@ -202,3 +202,19 @@ def test_probe_argument_checks():
     assert L.pchase_probe_latency(1, 0, 0, 0, 1, 0, 1, 1, 1, 1, None) == C.EINVAL
     assert L.pchase_probe_latency(1, 10, 0, 0, (1 << 24) + 1, 0, 1, 1, 1, 1, None) == C.ERANGE
     assert L.pchase_build(0, 1, None, 10, 1, None, None, None) == C.EINVAL
+
+
+def test_only_lru_items_are_cut_in_time():
+    """Time parts rebuild an LRU set's state from its recency order; FIFO and
+    RANDOM states depend on past misses, so those items stay whole."""
+    L = C.load()
+    geoms = [W.Geom(64 * 32, 32, 64, 1, p, 3) for p in (W.LRU, W.FIFO, W.RANDOM, W.WEIGHTED)]
+    traces = [(None, 1 << 18, 0, 1 << 12, 8)]  # 32 B stride over 4096 elements: thrashes
+    rc, h = _plan(geoms, traces, tune={"max_split": 16, "split_cost_ns": 1})
+    assert rc == C.OK
+    try:
+        d = _describe(h)
+        assert int(d["split"]) == 0 and int(d["time_split"]) == 1
+        assert 3 + 2 <= int(d["units"]) <= 3 + 16
+    finally:
+        L.pchase_sim_plan_destroy(h)
