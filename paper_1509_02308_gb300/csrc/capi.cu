@@ -409,6 +409,7 @@ struct pchase_sim_plan {
     // runtime state, set on the first run
     int device = -1, sms = 0, grid = 0, jgrid = 0;
     uint64_t n_isolated = 0;  // units given an SM of their own (in the jumbo launch)
+    std::vector<uint32_t> class_caps;  // arena cap of each size class present
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
 
@@ -734,7 +735,13 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         UnitShape u;
         best_split(i, 0.0, k, u);
         double c = u.cost;
-        if (k == 1) time_split(i, u, 0.0, c, nullptr, nullptr);
+        UnitShape whole;
+        if (k == 1) {
+            time_split(i, u, 0.0, c, nullptr, nullptr);
+        } else if (unit_shape(geoms[base[i].cand], base[i], 1, shape[i], tn, whole)) {
+            double tc;
+            if (time_split(i, whole, 0.0, tc, nullptr, nullptr) > 1) c = std::min(c, tc);
+        }
         critical = std::max(critical, c);
     }
     // (0.6 of the critical estimate: the estimates scatter by about that
@@ -757,11 +764,36 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             uint32_t best_k;
             UnitShape best;
             best_split(i, target, best_k, best);
-            if (best_k == 1) {
-                double part_max;
+            {
+                double part_max = best.cost;
                 std::vector<uint32_t> bounds;
                 std::vector<double> pcost;
-                const uint32_t P = time_split(i, best, target, part_max, &bounds, &pcost);
+                uint32_t P = 1;
+                UnitShape whole;
+                if (best_k == 1) {
+                    P = time_split(i, best, target, part_max, &bounds, &pcost);
+                } else if (unit_shape(G, base[i], 1, sh, tn, whole)) {
+                    // an LRU item that splits by sets may do better cut in time:
+                    // a set-part re-reads the whole trace, a time part only
+                    // what it reads back
+                    double tmax;
+                    std::vector<uint32_t> tb;
+                    std::vector<double> tc;
+                    const uint32_t tp = time_split(i, whole, target, tmax, &tb, &tc);
+                    double tsum = 0.0;
+                    for (double c : tc) tsum += c;
+                    const bool better =
+                        tp > 1 && (tmax <= target ? best.cost > target || tsum < best.cost * best_k
+                                                  : tmax < best.cost);
+                    if (better) {
+                        P = tp;
+                        part_max = tmax;
+                        bounds.swap(tb);
+                        pcost.swap(tc);
+                        best = whole;
+                        best_k = 1;
+                    }
+                }
                 if (P > 1) {
                     for (uint32_t j = 0; j < P; ++j) {
                         SimItem it = base[i];
@@ -882,6 +914,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         // slot also serves every smaller class.
         std::vector<uint32_t> caps(nclass), slots(nclass, 0);
         for (uint32_t q = 0; q < nclass; ++q) caps[q] = kCaps[present[q]];
+        p->class_caps = caps;
         const uint32_t budget = tn.smem_budget_bytes;
         int main_top = -1;
         for (uint32_t q = 0; q < nclass; ++q)
@@ -1021,6 +1054,20 @@ size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t b
         d += " class_items=";
         for (uint32_t q = 0; q < plan->layout.nclasses; ++q) {
             snprintf(tmp, sizeof tmp, "%s%u", q ? "," : "", plan->layout.cls_count[q]);
+            d += tmp;
+        }
+        // each class's arena cap and its units' summed estimate
+        d += " class_caps=";
+        for (uint32_t q = 0; q < plan->class_caps.size(); ++q) {
+            snprintf(tmp, sizeof tmp, "%s%u", q ? "," : "", plan->class_caps[q]);
+            d += tmp;
+        }
+        d += " class_ms=";
+        for (uint32_t q = 0; q < plan->layout.nclasses; ++q) {
+            double w = 0.0;
+            for (uint32_t k = 0; k < plan->layout.cls_count[q]; ++k)
+                w += plan->items[plan->layout.cls_first[q] + k].cost;
+            snprintf(tmp, sizeof tmp, "%s%.1f", q ? "," : "", w * 1e-6);
             d += tmp;
         }
         snprintf(tmp, sizeof tmp, " est_ms=%.2f,%.2f,%.2f,%.1f", plan->est_critical * 1e-6,
