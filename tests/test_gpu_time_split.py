@@ -59,7 +59,7 @@ def host_traces(rng):
     return [t for t, _ in out], descs
 
 
-def _want(g, tr, warm):
+def _want(g, tr):
     return oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed,
                             mapping=g.mapping)
 
@@ -80,7 +80,7 @@ def test_time_split_matches_oracle(tune_name):
     for gi, g in enumerate(geoms):
         for ti, (tr, ds) in enumerate(zip(host, descs)):
             i = gi * len(host) + ti
-            want = _want(g, tr, ds[2])
+            want = _want(g, tr)
             got = api.unpack_bits(b[int(plan.word_offsets[i]):], tr.size)
             assert np.array_equal(got, want), (tune_name, g, ti, int(np.argmax(got != want)))
             assert c[i, 0] == want.sum() and c[i, 1] == want[ds[2]:].sum(), (tune_name, g, ti)
@@ -102,7 +102,7 @@ def test_time_split_matcher_distances():
     t = W.random_index_trace(7000, 3000, seed=8, hot=3)
     host.append(t)
     descs.append((torch.from_numpy(t.view(np.int32)).cuda(), t.size, 0, 3000, 1))
-    obs_host = [_want(truth, tr, 0) for tr in host]
+    obs_host = [_want(truth, tr) for tr in host]
     plan = api.SimPlan(cands, descs, tune={"split_cost_ns": 1, "max_split": 8})
     assert " time_split=0 " not in plan.description, plan.description
     words, offs = [], [0]
@@ -114,7 +114,18 @@ def test_time_split_matcher_distances():
     obs = torch.from_numpy(np.concatenate(words).view(np.int32)).cuda()
     owo = torch.tensor(offs[:-1], dtype=torch.int64, device="cuda")
     dist = plan.match(obs, owo).cpu().numpy()
+    wants = []
     for ci, g in enumerate(cands):
-        want = sum(int((_want(g, tr, 0) != o).sum()) for tr, o in zip(host, obs_host))
+        want = sum(int((_want(g, tr) != o).sum()) for tr, o in zip(host, obs_host))
+        wants.append(want)
         assert dist[ci] == want, (g, dist[ci], want)
     assert dist[0] == 0 and (dist[1:] > 0).all()
+    # with a bound, distances at or under it stay exact and the others are
+    # only known to be above it, whichever time part stopped first
+    for bound in (0, min(wants[1:])):
+        db = plan.match(obs, owo, stop_above=bound).cpu().numpy()
+        for ci, want in enumerate(wants):
+            if want <= bound:
+                assert db[ci] == want, (bound, ci)
+            else:
+                assert db[ci] > bound, (bound, ci)
