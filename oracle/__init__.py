@@ -70,6 +70,8 @@ def lib():
             L.or_weighted_victim.argtypes = [ctypes.c_uint64, ctypes.c_uint32,
                                              ctypes.c_uint64, ctypes.c_uint32]
             L.or_weighted_victim.restype = ctypes.c_uint32
+            L.or_cache_sim_uneq.argtypes = [ctypes.c_uint32] * 5 + [
+                ctypes.c_int, _u32p, ctypes.c_uint64, ctypes.c_void_p, _u8p]
             L.or_cache_sim_counts.argtypes = [ctypes.c_uint32] * 4 + [
                 ctypes.c_int, ctypes.c_uint64, _u32p, ctypes.c_uint64, ctypes.c_uint64,
                 ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
@@ -171,16 +173,39 @@ def cache_sim(C: int, b: int, ways: int, T: int, policy: int, trace: np.ndarray,
     return tuple(res) if len(res) > 1 else out
 
 
+def cache_sim_uneq(C: int, b: int, ways: int, T: int, extra: int, policy: int,
+                   trace: np.ndarray, filter=None) -> np.ndarray:
+    """Per-access miss flags of a cache whose set 0 has `extra` more ways
+    (the unequal-set L2 TLB of Sec. 4.4); see or_cache_sim_uneq.  filter as
+    in cache_sim."""
+    trace = np.ascontiguousarray(trace, dtype=np.uint32)
+    flt = None
+    if filter is not None:
+        flt = np.ascontiguousarray(filter, dtype=np.uint8)
+        if flt.size != trace.size:
+            raise ValueError("filter must flag every access")
+    out = np.empty(trace.size, dtype=np.uint8)
+    _check(lib().or_cache_sim_uneq(C, b, ways, T, extra, policy, trace, trace.size,
+                                   flt.ctypes.data if flt is not None else None, out),
+           "cache_sim_uneq")
+    return out
+
+
 def hierarchy(levels, trace):
     """Miss flags of each level of a cascade: levels[0] sees every access,
     levels[k] only the misses of levels[k-1] (Sec. 3's L1 -> L2 path; with
     page-sized lines, an L1 TLB -> L2 TLB path).  levels: dicts with C, b,
-    ways, T, policy and optionally seed, mapping.  The level an access is
-    served from is the sum of its flags."""
+    ways, T, policy and optionally seed, mapping, extra (unequal sets, see
+    cache_sim_uneq).  The level an access is served from is the sum of its
+    flags."""
     out, flt = [], None
     for g in levels:
-        m = cache_sim(g["C"], g["b"], g["ways"], g["T"], g["policy"], trace,
-                      seed=g.get("seed", 0), mapping=g.get("mapping", 0), filter=flt)
+        if g.get("extra", 0):
+            m = cache_sim_uneq(g["C"], g["b"], g["ways"], g["T"], g["extra"], g["policy"],
+                               trace, filter=flt)
+        else:
+            m = cache_sim(g["C"], g["b"], g["ways"], g["T"], g["policy"], trace,
+                          seed=g.get("seed", 0), mapping=g.get("mapping", 0), filter=flt)
         out.append(m)
         flt = m
     return out

@@ -248,6 +248,72 @@ int or_cache_sim(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int policy,
                             n_victims, miss_out, final_tags, NULL, NULL, 0, NULL);
 }
 
+/*
+ * A cache with unequal sets: the L2 TLB of Sec. 4.4 (Fig. 9), whose miss
+ * count grows set by set as N grows, with one large set of 17 entries and six
+ * of 8.  The paper gives the set sizes but not the page-to-set rule.  Reading:
+ * the M = T * a + extra lines of capacity are residues of line mod M; residue
+ * r < T * a goes to set r mod T, the other `extra` residues to set 0, so set 0
+ * holds a + extra lines and the others a.  A chain of n > M lines then
+ * overflows set 0 first (n = M + 1) and then sets 1, 2, ... one line at a
+ * time, the order Fig. 9's steps show.  With extra = 0 this is set = line mod
+ * T.  LRU or FIFO; a miss fills the lowest invalid way of its set, else evicts
+ * the oldest use (LRU) or fill (FIFO) among the set's ways.  filter (or NULL)
+ * flags the accesses that reach this cache, as in or_cache_sim_ext.
+ */
+int or_cache_sim_uneq(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, uint32_t extra,
+                      int policy, const uint32_t *trace, uint64_t len, const uint8_t *filter,
+                      uint8_t *miss_out)
+{
+    if (b < 4 || (b & (b - 1)) || ways == 0 || T == 0) return OR_EINVAL;
+    if (policy != OR_LRU && policy != OR_FIFO) return OR_EINVAL;
+    uint64_t M = (uint64_t)T * ways + extra;
+    if (M * b != C) return OR_EINVAL;
+    uint32_t wmax = ways + extra;
+    uint64_t nslots = (uint64_t)T * wmax;
+    uint64_t *held = (uint64_t *)malloc(nslots * sizeof(uint64_t));
+    uint8_t *valid = (uint8_t *)calloc(nslots, 1);
+    uint64_t *stamp = (uint64_t *)malloc(nslots * sizeof(uint64_t));
+    if (!held || !valid || !stamp) {
+        free(held); free(valid); free(stamp);
+        return OR_ENOMEM;
+    }
+    for (uint64_t t = 0; t < len; t++) {
+        if (filter && !filter[t]) {
+            /* the access never reaches this cache */
+            miss_out[t] = 0;
+            continue;
+        }
+        uint64_t line = 4ull * trace[t] / b;
+        uint64_t r = line % M;
+        uint32_t set = r < (uint64_t)T * ways ? (uint32_t)(r % T) : 0;
+        uint32_t nw = set == 0 ? wmax : ways;
+        uint64_t base = (uint64_t)set * wmax;
+        int64_t hit_way = -1;
+        for (uint32_t w = 0; w < nw; w++)
+            if (valid[base + w] && held[base + w] == line) { hit_way = w; break; }
+        if (hit_way >= 0) {
+            miss_out[t] = 0;
+            if (policy == OR_LRU) stamp[base + hit_way] = t;
+            continue;
+        }
+        miss_out[t] = 1;
+        int64_t victim = -1;
+        for (uint32_t w = 0; w < nw; w++)
+            if (!valid[base + w]) { victim = w; break; }
+        if (victim < 0) {
+            victim = 0;
+            for (uint32_t w = 1; w < nw; w++)
+                if (stamp[base + w] < stamp[base + victim]) victim = w;
+        }
+        held[base + victim] = line;
+        valid[base + victim] = 1;
+        stamp[base + victim] = t;  /* last use (LRU) = fill (FIFO) here */
+    }
+    free(held); free(valid); free(stamp);
+    return OR_OK;
+}
+
 /* Miss counts of one replay: total, and after the first `warmup` accesses. */
 int or_cache_sim_counts(uint32_t C, uint32_t b, uint32_t ways, uint32_t T, int policy,
                         uint64_t seed, const uint32_t *trace, uint64_t len,

@@ -563,3 +563,112 @@ def test_canonical_order():
     assert oracle.canonical_pick(cands, dist) == (3, 5)
     dist = np.array([0, 3, 0, 1, 1], dtype=np.uint64)
     assert oracle.canonical_pick(cands, dist) == (2, 2)
+
+
+# ------------------------------------------------------- unequal sets (TLB)
+def _uneq_list_model(b, a, T, extra, policy, trace):
+    """Unequal sets as Python lists (set 0 holds a + extra lines, the others
+    a), the residue rule of or_cache_sim_uneq written out per access."""
+    M = T * a + extra
+    sets = [[] for _ in range(T)]
+    out = []
+    for idx in trace:
+        line = (4 * int(idx)) // b
+        r = line % M
+        s = r % T if r < T * a else 0
+        cap = a + extra if s == 0 else a
+        lst = sets[s]
+        if line in lst:
+            out.append(0)
+            if policy == oracle.LRU:
+                lst.remove(line)
+                lst.append(line)
+            continue
+        out.append(1)
+        if len(lst) == cap:
+            lst.pop(0)
+        lst.append(line)
+    return np.array(out, dtype=np.uint8)
+
+
+def test_unequal_l2_tlb_fig9_steps():
+    """Sec. 4.4, Fig. 9: the L2 TLB (2 MB pages, LRU) holds 65 entries, one
+    set of 17 and six of 8, and its misses grow set by set as N passes 130 MB:
+    the large set first (at 132 MB), then 8 more entries per 2 MB step up to
+    144 MB.  Counted as this model counts Eq. (2)'s steps, an overflowing set
+    of w ways misses on all of its w + 1 pages, so a steady pass misses 18 at
+    132 MB, 9 more per step to 144 MB, and every access from then on."""
+    page = 2 << 20
+    C = 65 * page
+    steady = {}
+    for n_pages in range(60, 80):
+        n = n_pages * page // 4
+        tr = oracle.pchase_trace(n, page // 4, 3 * n_pages)
+        m = oracle.cache_sim_uneq(C, page, 8, 7, 9, oracle.LRU, tr)
+        assert m[:n_pages].all()                      # the first pass: cold
+        assert np.array_equal(m[n_pages:2 * n_pages], m[2 * n_pages:])  # periodic
+        steady[n_pages] = int(m[n_pages:2 * n_pages].sum())
+    assert all(steady[k] == 0 for k in range(60, 66))  # up to 130 MB: all held
+    assert steady[66] == 17 + 1                        # 132 MB: the large set
+    for k in range(67, 73):                            # 134 .. 144 MB
+        assert steady[k] - steady[k - 1] == 8 + 1
+    assert all(steady[k] == k for k in range(72, 80))  # every set overflows
+
+
+def test_unequal_sets_with_no_extra_ways_is_the_standard_cache():
+    rng = np.random.Generator(np.random.PCG64(65))
+    for (b, a, T) in ((4, 2, 3), (8, 4, 7), (32, 8, 7), (64, 1, 5)):
+        for policy in (oracle.LRU, oracle.FIFO):
+            for _ in range(10):
+                tr = rng.integers(0, 3 * a * T * b // 4 + 5, size=400).astype(np.uint32)
+                assert np.array_equal(
+                    oracle.cache_sim_uneq(a * T * b, b, a, T, 0, policy, tr),
+                    oracle.cache_sim(a * T * b, b, a, T, policy, tr))
+
+
+def test_unequal_sets_hold_any_m_consecutive_lines():
+    """Capacity: the M = T*a + extra residues each have a place, so a chain
+    over any M consecutive lines misses only on its first pass (LRU, FIFO)."""
+    for (a, T, extra) in ((8, 7, 9), (2, 3, 1), (4, 5, 7), (1, 1, 3)):
+        M = T * a + extra
+        for start in (0, 5, M - 1):
+            lines = np.arange(start, start + M, dtype=np.uint32)
+            tr = np.tile(lines, 3) * 8          # b = 32 B: 8 elements per line
+            for policy in (oracle.LRU, oracle.FIFO):
+                m = oracle.cache_sim_uneq(M * 32, 32, a, T, extra, policy, tr)
+                assert m[:M].all() and m[M:].sum() == 0
+            # one line more than fits, cycled: it shares the set of line
+            # `start` (same residue), whose w + 1 lines then miss on every
+            # access under LRU while the other sets never do
+            tr1 = np.tile(np.arange(start, start + M + 1, dtype=np.uint32), 3) * 8
+            m1 = oracle.cache_sim_uneq(M * 32, 32, a, T, extra, oracle.LRU, tr1)
+            r0 = start % M
+            w = a + extra if (r0 >= T * a or r0 % T == 0) else a
+            assert m1[M + 1:2 * (M + 1)].sum() == w + 1
+            assert np.array_equal(m1[M + 1:2 * (M + 1)], m1[2 * (M + 1):])
+
+
+def test_bruteforce_unequal_sets():
+    rng = np.random.Generator(np.random.PCG64(17))
+    n = 0
+    for b in (4, 8):
+        for (a, T, extra) in ((1, 1, 1), (1, 3, 2), (2, 3, 1), (3, 2, 4), (2, 7, 5), (8, 7, 9)):
+            M = T * a + extra
+            for policy in (oracle.LRU, oracle.FIFO):
+                for _ in range(10):
+                    L = int(rng.integers(1, 80))
+                    tr = rng.integers(0, int(rng.integers(1, 3 * M + 3)) * b // 4 + 1,
+                                      size=L).astype(np.uint32)
+                    got = oracle.cache_sim_uneq(M * b, b, a, T, extra, policy, tr)
+                    want = _uneq_list_model(b, a, T, extra, policy, tr)
+                    assert np.array_equal(got, want), (b, a, T, extra, policy, tr)
+                    n += 1
+    assert n == 240
+
+
+def test_unequal_sets_reject_bad_geometry():
+    tr = np.zeros(4, dtype=np.uint32)
+    with pytest.raises(Exception):
+        oracle.cache_sim_uneq(65 * 32 + 32, 32, 8, 7, 9, oracle.LRU, tr)   # C != M * b
+    with pytest.raises(Exception):
+        oracle.cache_sim_uneq(65 * 32, 32, 8, 7, 9, oracle.RANDOM, tr)     # LRU / FIFO only
