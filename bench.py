@@ -769,8 +769,9 @@ def variants_bench(dev):
 
 def hierarchy_bench(dev, reps: int = 3):
     """Cache and TLB hierarchies (workloads.hierarchy_config: 1024 items, L1
-    16-256 KB -> L2 0.5-3 MB, and a 16-entry L1 TLB -> 8-way L2 TLB over 4 KB,
-    64 KB or 2 MB pages, 142 M trace accesses).  One step runs both cascades
+    16-256 KB -> L2 0.5-3 MB, and a 16-entry L1 TLB -> 8-way L2 TLB over 4 KB
+    or 64 KB pages, or the unequal-set L2 TLB of Sec. 4.4 over 2 MB pages,
+    142 M trace accesses).  One step runs both cascades
     (4 levels: L1, L2 on L1's misses, L1 TLB, L2 TLB on its misses).  Reports
     trace accesses/s through both cascades, level accesses simulated per
     second, and where the accesses were served."""

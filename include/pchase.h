@@ -85,7 +85,14 @@ typedef struct {
     uint32_t ways;
     uint32_t sets;
     uint32_t policy;  /* pchase_policy */
-    uint32_t mapping; /* set = (line >> mapping) mod T; 0: set = line mod T */
+    uint32_t mapping; /* bits 0-7: m, set = (line >> m) mod T (0: set = line mod T, at most
+                         16).  Bits 8-15: extra, unequal sets as in the L2 TLB of Sec. 4.4
+                         (Fig. 9: one set of 17 entries, six of 8): set 0 has ways + extra
+                         ways, C = (sets*ways + extra) * line_bytes, and line residue
+                         r = line mod (sets*ways + extra) goes to set r mod sets when
+                         r < sets*ways, else to set 0 (a reading: the paper gives the set
+                         sizes, not the rule).  Unequal sets take m = 0 and LRU or FIFO,
+                         run as way scans and are never split.  Bits 16-31: zero. */
     uint64_t seed;    /* RANDOM and WEIGHTED only */
 } pchase_geom;
 

@@ -156,8 +156,8 @@ def stream_handle(stream=None) -> int | None:
 def geom_array(geoms) -> ctypes.Array:
     arr = (Geom * max(1, len(geoms)))()
     for i, g in enumerate(geoms):
-        arr[i] = Geom(g.C, g.b, g.ways, g.sets, g.policy, getattr(g, "mapping", 0),
-                      g.seed & 0xFFFFFFFFFFFFFFFF)
+        mapping = getattr(g, "mapping", 0) | (getattr(g, "extra", 0) << 8)
+        arr[i] = Geom(g.C, g.b, g.ways, g.sets, g.policy, mapping, g.seed & 0xFFFFFFFFFFFFFFFF)
     return arr
 
 

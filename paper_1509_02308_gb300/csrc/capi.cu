@@ -145,13 +145,19 @@ uint64_t gcd64(uint64_t a, uint64_t b) {
     return a;
 }
 
+// The geometry's mapping field: bits 0-7 the shift m of set = (line >> m)
+// mod T; bits 8-15 the extra ways of set 0 in a cache with unequal sets.
+uint32_t map_shift(const pchase_geom &G) { return G.mapping & 255u; }
+uint32_t extra_ways(const pchase_geom &G) { return (G.mapping >> 8) & 255u; }
+
 // Largest line id a unit sees: (n_elems - 1) >> lsh, renumbered when the
 // mapping takes the set from higher bits (id = ((hi << m) | lo) * T + set).
 uint64_t top_line(const pchase_geom &G, uint32_t n_elems) {
     const uint64_t top = (uint64_t)(n_elems - 1) / (G.line_bytes / 4);
-    if (!G.mapping) return top;
+    const uint32_t m = map_shift(G);
+    if (!m) return top;
     const uint64_t T = G.sets;
-    return ((top >> G.mapping) / T + 1) * (T << G.mapping) - 1;
+    return ((top >> m) / T + 1) * (T << m) - 1;
 }
 
 void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
@@ -206,7 +212,7 @@ void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
             sh.cyclic = se == g;  // one ascending sweep a pass
         }
     }
-    if (G.mapping) {
+    if (map_shift(G)) {
         // sets from higher line bits: only the bound over all line ids holds
         sh.visited = (double)T;
         sh.psh = 0;
@@ -216,12 +222,42 @@ void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
         if (Tr.stride && !se) per_set = 1;
     }
     sh.held = per_set <= G.ways;
+    if (extra_ways(G)) {
+        // unequal sets: no prediction, and no split (set 0 is unlike the rest)
+        sh.visited = (double)T;
+        sh.psh = 0;
+        sh.groups = 1;
+        sh.cyclic = false;
+        sh.held = false;
+    }
     sh.cold = std::min((double)Tr.len, (double)pass);
 }
 
 // Set mode, arena and cost of one unit of a K-way split (K = 1: whole).
 bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemShape &sh,
                 const pchase_tune &tn, UnitShape &u) {
+    if (extra_ways(G)) {
+        // unequal sets run as way scans (the mode that keeps a way count per
+        // set), whole: T sets of a + extra way slots, set 0 using all of them
+        if (K != 1) return false;
+        const uint32_t T = G.sets, amax = G.ways + extra_ways(G);
+        const int pol = (int)G.policy;
+        const double rounds = std::ceil(32.0 / std::min(32.0, (double)T));
+        const double step_ns = (kStepScanNs[pol] + kRoundScanNs[pol] * (rounds - 1.0)) *
+                               std::max(1.0, (double)amax / std::max(1u, tn.scan_max_ways));
+        const double chunks = std::ceil((double)it.len / 32.0);
+        const double steps = std::ceil(sh.heads / 32.0);
+        const double direct_cost = chunks * step_ns;
+        const double queued_cost = steps * step_ns + chunks * kGatherNs;
+        u.direct = direct_cost <= queued_cost && !tn.filtered;
+        u.mode = kModeScan;
+        u.sets = T;
+        u.table_n = 0;
+        u.ring = 0;
+        u.arena = align16(8ull * T * amax) + (u.direct ? 0u : kStageBytes);
+        u.cost = u.direct ? direct_cost : queued_cost;
+        return u.arena <= kMaxArena;
+    }
     const uint32_t T = G.sets, a = G.ways;
     const uint32_t Tl = T / K;
     const uint64_t lines = (uint64_t)Tl * a;
@@ -345,23 +381,28 @@ int check_geom(const pchase_geom &g, uint32_t i) {
                  g.line_bytes);
         return fail(PCHASE_EINVAL, buf);
     }
-    if (g.ways == 0 || g.sets == 0 ||
-        (uint64_t)g.sets * g.ways * g.line_bytes != (uint64_t)g.C_bytes) {
-        snprintf(buf, sizeof buf, "geometry %u: sets*ways*line (%u*%u*%u) != C (%u)", i, g.sets,
-                 g.ways, g.line_bytes, g.C_bytes);
+    const uint32_t m = map_shift(g), extra = extra_ways(g);
+    const uint64_t lines = (uint64_t)g.sets * g.ways + extra;
+    if (g.ways == 0 || g.sets == 0 || lines * g.line_bytes != (uint64_t)g.C_bytes) {
+        snprintf(buf, sizeof buf, "geometry %u: (sets*ways + extra)*line ((%u*%u + %u)*%u) != C (%u)",
+                 i, g.sets, g.ways, extra, g.line_bytes, g.C_bytes);
         return fail(PCHASE_EINVAL, buf);
     }
-    if (g.policy > PCHASE_WEIGHTED || g.mapping > 16 || (uint64_t)g.sets << g.mapping > (1ull << 30) ||
-        (g.policy == PCHASE_WEIGHTED && g.ways < 3)) {
+    if (g.policy > PCHASE_WEIGHTED || m > 16 || (uint64_t)g.sets << m > (1ull << 30) ||
+        (g.mapping >> 16) != 0 || (g.policy == PCHASE_WEIGHTED && g.ways < 3)) {
         snprintf(buf, sizeof buf,
                  "geometry %u: unknown policy %u, mapping %u above 16 (or T << mapping above 2^30),"
-                 " or WEIGHTED with fewer than 3 ways", i, g.policy,
-                 g.mapping);
+                 " bits above 15 set, or WEIGHTED with fewer than 3 ways", i, g.policy, m);
         return fail(PCHASE_EINVAL, buf);
     }
-    if ((uint64_t)g.sets * g.ways > kMaxLines) {
+    if (extra && (m != 0 || g.policy > PCHASE_FIFO)) {
+        snprintf(buf, sizeof buf,
+                 "geometry %u: unequal sets take LRU or FIFO and the plain mapping", i);
+        return fail(PCHASE_EINVAL, buf);
+    }
+    if (lines > kMaxLines) {
         snprintf(buf, sizeof buf, "geometry %u: %llu lines is above the limit of %u", i,
-                 (unsigned long long)g.sets * g.ways, kMaxLines);
+                 (unsigned long long)lines, kMaxLines);
         return fail(PCHASE_ERANGE, buf);
     }
     return PCHASE_OK;
@@ -609,7 +650,8 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         it.stride = Tr.stride % Tr.n_elems;
         it.ways = G.ways;
         it.policy = (uint8_t)G.policy;
-        it.lsh = (ilog2(G.line_bytes) - 2) | (G.mapping << 8);
+        it.lsh = (ilog2(G.line_bytes) - 2) | (map_shift(G) << 8) |
+                 (extra_ways(G) ? 1u << 16 : 0u);
         it.seed = G.seed;
         it.word_off = word;
         word += (Tr.len + 31) / 32;
@@ -617,7 +659,13 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         it.cand = g;
         it.obs = t;
         it.gsets = G.sets;
-        const DivMagic gdm = make_div_magic(G.sets);
+        if (extra_ways(G)) {
+            // unequal sets: M = T*a + extra residues, set 0 with a + extra ways
+            it.gsets = G.sets * G.ways + extra_ways(G);
+            it.ways = G.ways + extra_ways(G);
+            it.kmagic = G.ways;
+        }
+        const DivMagic gdm = make_div_magic(it.gsets);
         it.gmagic = gdm.m;
         it.gs1 = (uint8_t)gdm.s1;
         it.gs2 = (uint8_t)gdm.s2;
@@ -816,7 +864,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                 SimItem it = base[i];
                 it.psh = (uint8_t)(best_k > 1 ? sh.psh : 0);
                 it.kcnt = (uint8_t)best_k;
-                it.kmagic = kdm.m;
+                if (!extra_ways(G)) it.kmagic = kdm.m;  // unequal sets keep a there
                 it.ks1 = (uint8_t)kdm.s1;
                 it.ks2 = (uint8_t)kdm.s2;
                 it.kres = r;

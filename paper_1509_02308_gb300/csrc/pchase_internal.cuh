@@ -98,7 +98,9 @@ struct SimItem {
     uint32_t sets;        // local sets T' = T / K
     uint32_t magic_m;     // local set = local line mod T', by DivMagic of T'
     uint8_t s1, s2, policy, mode;
-    uint32_t lsh;         // line = index >> (lsh & 255) (b = 4 << that); lsh >> 8: mapping m
+    uint32_t lsh;         // line = index >> (lsh & 255) (b = 4 << that); bits 8-15: mapping m;
+                          // bit 16: unequal sets (gsets/gmagic: M = T*a + extra, kmagic: a,
+                          // ways: a + extra, the ways of set 0)
     uint32_t table_n;     // line-table entries (local lines)
     uint64_t seed;
     uint64_t word_off;    // plan-owned bitmap layout

@@ -63,12 +63,14 @@ struct ScanSets {
     uint2 *slot;
     uint32_t *evict;
     uint32_t ways;
+    uint32_t ways_rest;        // unequal sets: ways of sets 1.. (set 0 has `ways`)
     uint64_t seed;
     bool wtd;                  // WEIGHTED victims (RANDOM code path)
     uint32_t psh, kcnt, kres;  // local -> global set (RANDOM's key)
 
     __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
+        ways_rest = (it.lsh >> 16) & 1u ? it.kmagic : it.ways;
         seed = it.seed;
         wtd = it.policy == PCHASE_WEIGHTED;
         psh = it.psh;
@@ -87,11 +89,12 @@ struct ScanSets {
 
     __device__ __forceinline__ bool access(uint32_t set, uint32_t line, uint32_t t) {
         const uint32_t a = ways;
+        const uint32_t na = set ? ways_rest : a;  // ways this set has
         uint2 *s = slot + set * a;
         int hit = -1;
         uint32_t best = 0xFFFFFFFFu;
         uint32_t bw = 0;
-        for (uint32_t w = 0; w < a; ++w) {
+        for (uint32_t w = 0; w < na; ++w) {
             const uint2 e = s[w];
             if (e.x == line) hit = (int)w;
             if (e.y < best) { best = e.y; bw = w; }
@@ -1158,10 +1161,21 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     const uint32_t len = it.len;
     const uint32_t *__restrict__ idxp = it.idx;
     const uint32_t N = it.n_elems;
-    const uint32_t lsh = it.lsh & 255u, mk = it.lsh >> 8;  // line shift, mapping
+    const uint32_t lsh = it.lsh & 255u, mk = (it.lsh >> 8) & 255u;  // line shift, mapping
+    // unequal sets: the residue r = line mod M (M in gsets) goes to set r mod T
+    // below T * a (a: it.kmagic), else to set 0
+    const bool uneq = (it.lsh >> 16) & 1u;
+    const uint32_t uta = uneq ? it.sets * it.kmagic : 0u;
     const uint32_t sets = it.sets, mm = it.magic_m, s1 = it.s1, s2 = it.s2;
     const bool split = it.kcnt > 1;
     const uint32_t gT = it.gsets, gm = it.gmagic, gs1 = it.gs1, gs2 = it.gs2;
+    auto set_of = [&](uint32_t l) -> uint32_t {
+        if (uneq) {
+            const uint32_t r = l - div_q(l, gm, gs1, gs2) * gT;
+            return r < uta ? r - div_q(r, mm, s1, s2) * sets : 0u;
+        }
+        return l - div_q(l, mm, s1, s2) * sets;
+    };
     const uint32_t psh = it.psh, K = it.kcnt, kres = it.kres;
     const uint32_t km = it.kmagic, ks1 = it.ks1, ks2 = it.ks2;
     const uint32_t pmask = (1u << psh) - 1u;
@@ -1236,7 +1250,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             }
             uint32_t ln = j >> lsh;
             if (mk) ln = remap_line(ln, mk, gT, gm, gs1, gs2);
-            const uint32_t set = ln - div_q(ln, mm, s1, s2) * sets;
+            const uint32_t set = set_of(ln);
             const uint32_t rot = __shfl_sync(kFull, ln, (lane + 31) & 31);
             const uint32_t prev = lane == 0 ? carry : rot;
             carry = rot;
@@ -1361,7 +1375,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             __syncwarp();
             const uint32_t line = e.x;
             const uint32_t pos = e.y & 0x7FFFFFFFu;
-            const uint32_t set = line - div_q(line, mm, s1, s2) * sets;
+            const uint32_t set = set_of(line);
             const uint32_t rot = __shfl_sync(kFull, line, (lane + 31) & 31);
             const uint32_t prev = lane == 0 ? ccarry : rot;
             ccarry = rot;

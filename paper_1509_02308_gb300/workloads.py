@@ -53,6 +53,10 @@ class Geom:
     policy: int = LRU
     seed: int = 0
     mapping: int = 0  # set = (line >> mapping) mod T
+    # unequal sets (the L2 TLB of Sec. 4.4): set 0 has `extra` more ways and
+    # C = (T * ways + extra) * b; line residues mod T*ways + extra below
+    # T*ways go to set residue mod T, the others to set 0
+    extra: int = 0
 
     def row(self):
         return (self.C, self.b, self.ways, self.sets, self.policy)
@@ -282,7 +286,8 @@ def hierarchy_config(n_items: int = 1024, seed_base: int = 0x5EED0005):
       L1: C 16-256 KB (powers of two), b 32/64/128 B, 4/8/16 ways, a policy;
       L2: C 0.5/1/2/3 MB, b 64/128 B, 8/16/32 ways, a policy;
       TLBs (Sec. 4.4): a 16-entry fully associative L1 TLB and an 8-way L2 TLB
-      of 8-64 sets, both LRU, over 4 KB, 64 KB or 2 MB pages;
+      of 8-64 sets, both LRU, over 4 KB or 64 KB pages; over 2 MB pages the
+      L2 TLB the paper measures (Fig. 9): one set of 17 entries and six of 8;
       stream: s = 4 * 2^u B (u in 0..10), N = round_down(C_L2 * 2^v, s),
       v in [-1, 1), length 16K * 32^x (x in [0, 1)), warm-up one pass.
     Returns (l1, l2, tlb1, tlb2, runs), item i pairing entry i of each."""
@@ -300,7 +305,10 @@ def hierarchy_config(n_items: int = 1024, seed_base: int = 0x5EED0005):
         page = (4096, 65536, 2 << 20)[r.below(3)]
         sets2 = 8 << r.below(4)
         t1.append(Geom(16 * page, page, 16, 1, LRU))
-        t2.append(Geom(sets2 * 8 * page, page, 8, sets2, LRU))
+        if page == 2 << 20:
+            t2.append(Geom(65 * page, page, 8, 7, LRU, extra=9))
+        else:
+            t2.append(Geom(sets2 * 8 * page, page, 8, sets2, LRU))
         s_elems = 1 << r.below(11)
         v = r.unit() * 2.0 - 1.0
         n = max(s_elems, int(C2 * 2.0 ** v) // 4 // s_elems * s_elems)

@@ -227,3 +227,26 @@ def test_only_lru_items_are_cut_in_time():
         assert 3 + 2 <= int(d["units"]) <= 3 + 16
     finally:
         L.pchase_sim_plan_destroy(h)
+
+
+def test_unequal_sets_checks():
+    """Unequal sets (mapping bits 8-15): C = (T*a + extra) * b, LRU or FIFO,
+    plain mapping; such items run as whole way-scan units."""
+    L = C.load()
+    page = 2 << 20
+    tlb = W.Geom(65 * page, page, 8, 7, W.LRU, extra=9)
+    rc, h = _plan([tlb, W.Geom(65 * page, page, 8, 7, W.FIFO, extra=9)],
+                  [(None, 1 << 16, 0, 80 * page // 4, page // 4)],
+                  tune={"max_split": 16, "split_cost_ns": 1})
+    assert rc == C.OK
+    try:
+        d = _describe(h)
+        assert d["units"] == "2" and d["scan"] == "2"
+        assert d["split"] == "0" and d["time_split"] == "0"
+    finally:
+        L.pchase_sim_plan_destroy(h)
+    for bad in (W.Geom(64 * page, page, 8, 7, W.LRU, extra=9),        # C != (T*a + extra) * b
+                W.Geom(65 * page, page, 8, 7, W.RANDOM, extra=9),     # LRU / FIFO only
+                W.Geom(65 * page, page, 8, 7, W.LRU, mapping=1, extra=9)):
+        rc, _ = _plan([bad], [(None, 10, 0, 100, 1)])
+        assert rc == C.EINVAL, bad

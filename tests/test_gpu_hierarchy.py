@@ -16,7 +16,7 @@ if torch.cuda.is_available():
 
 def _lv(g):
     return dict(C=g.C, b=g.b, ways=g.ways, T=g.sets, policy=g.policy, seed=g.seed,
-                mapping=g.mapping)
+                mapping=g.mapping, extra=g.extra)
 
 
 def _check(levels, traces_host, traces_dev, pairs, tune=None, tag=""):
@@ -102,3 +102,17 @@ def test_filtered_run_needs_a_filtered_plan():
         plan.run_filtered(bm, wo)
     L = C.load()
     assert L.pchase_last_error_string()
+
+
+def test_hierarchy_workload_sample_matches_oracle():
+    """A sample of the hierarchy workload the bench times (cache cascade and
+    TLB cascade, the unequal L2 TLB over 2 MB pages among them), every level
+    against the oracle's cascade."""
+    l1, l2, t1, t2, runs = W.hierarchy_config(n_items=48)
+    keep = [i for i, r in enumerate(runs) if r.length <= 120000][:24]
+    assert any(t2[i].extra for i in keep)
+    host = [oracle.pchase_trace(runs[i].n_elems, runs[i].stride, runs[i].length) for i in keep]
+    dev = [(None, runs[i].length, runs[i].warmup, runs[i].n_elems, runs[i].stride) for i in keep]
+    for levels in ([[l1[i] for i in keep], [l2[i] for i in keep]],
+                   [[t1[i] for i in keep], [t2[i] for i in keep]]):
+        _check(levels, host, dev, [(k, k) for k in range(len(keep))])
