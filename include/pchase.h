@@ -179,9 +179,12 @@ typedef struct pchase_sim_plan pchase_sim_plan;
  * independent units (sets never interact, so the result is unchanged); units
  * are sorted costliest first into shared-memory size classes served by one
  * persistent launch with a per-CTA mix of arenas (S6); units too large for
- * that mix get a second launch on a side stream.  Errors: EINVAL for a bad geometry,
- * pair or trace; ERANGE if a geometry is too large for any class
- * (more than 65535 lines, or state above the workspace limits).
+ * that mix get a second launch on a side stream.  An item whose set state fits
+ * no shared-memory arena even split (a cache of many lines, or a line table
+ * over a wide stream) runs as one way-scan unit with its state in global
+ * memory, inside the plan's workspace (pchase_sim_plan_workspace_bytes counts
+ * it).  Errors: EINVAL for a bad geometry, pair or trace; ERANGE for a
+ * geometry of more than 2^24 lines, or global set state above 64 GB.
  */
 int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom,
                            const pchase_trace *traces, uint32_t n_trace,
@@ -369,7 +372,9 @@ int infer_geometry(const pchase_sim_plan *plan, void *workspace, const float *la
  * pick_out[2o], pick_out[2o + 1].  The candidates' items run once per
  * observation inside the same launches.  Scratch (device, 256-byte aligned):
  * pchase_infer_batch_scratch_bytes(plan, n_obs).  Errors: EINVAL as
- * infer_geometry; ERANGE when n_obs > 1024 or n_obs x plan traces > 65535.
+ * infer_geometry, or when a unit of the plan keeps its set state in global
+ * memory (it cannot run for several observations at once); ERANGE when
+ * n_obs > 1024 or n_obs x plan traces > 65535.
  */
 size_t pchase_infer_batch_scratch_bytes(const pchase_sim_plan *plan, uint32_t n_obs);
 int infer_geometry_batch(const pchase_sim_plan *plan, void *workspace, const float *lat,

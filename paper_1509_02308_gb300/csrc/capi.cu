@@ -82,7 +82,7 @@ uint32_t ilog2(uint32_t x) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-constexpr uint32_t kMaxLines = 65535;
+constexpr uint32_t kMaxLines = 1u << 24;  // with the set state in global memory above 227 KB
 constexpr uint32_t kMaxBatchObs = 1024;  // observations per infer_geometry_batch call
 constexpr uint32_t kMaxArena = 232448;  // 227 KB, one warp per CTA
 // size classes of unit arenas (bytes; queued units add their queue and staging ring)
@@ -109,6 +109,8 @@ constexpr double kStepHeldTableNs = 435.0;
 constexpr double kStepNoHitFifoNs = 1060.0;
 constexpr double kStepNoHitLruNs = 600.0, kNoHitLruSetNs = 480.0;
 constexpr double kGatherNs = 350.0;
+// Way scans over set state in global memory (L2-resident) against shared memory.
+constexpr double kGlobalScanFactor = 2.0;
 // A time part's backward read of 32 accesses while it rebuilds the recency
 // order: while lines are still being taken, and once every line read is taken
 // or in a full set.
@@ -231,6 +233,37 @@ void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
         sh.held = false;
     }
     sh.cold = std::min((double)Tr.len, (double)pass);
+}
+
+// Bytes of set state of a whole way-scan unit: {line, stamp} per way slot,
+// and RANDOM's eviction counters.
+uint64_t scan_state_bytes(const pchase_geom &G) {
+    const uint64_t T = G.sets, amax = G.ways + extra_ways(G);
+    return align16(8 * T * amax + (G.policy >= PCHASE_RANDOM ? 4 * T : 0));
+}
+
+// A whole item whose set state fits no shared-memory arena: way scans with
+// the state in global memory (only the queue and staging of a queued unit
+// stay in shared memory).
+void global_unit(const pchase_geom &G, const SimItem &it, const ItemShape &sh,
+                 const pchase_tune &tn, UnitShape &u) {
+    const uint32_t amax = G.ways + extra_ways(G);
+    const int pol = G.policy > PCHASE_RANDOM ? PCHASE_RANDOM : (int)G.policy;
+    const double rounds = std::ceil(32.0 / std::min(32.0, std::max(1.0, sh.visited)));
+    const double step_ns = (kStepScanNs[pol] + kRoundScanNs[pol] * (rounds - 1.0)) *
+                           std::max(1.0, (double)amax / std::max(1u, tn.scan_max_ways)) *
+                           kGlobalScanFactor;
+    const double chunks = std::ceil((double)it.len / 32.0);
+    const double steps = std::ceil(sh.heads / 32.0);
+    const double direct_cost = chunks * step_ns;
+    const double queued_cost = steps * step_ns + chunks * kGatherNs;
+    u.direct = direct_cost <= queued_cost && !tn.filtered;
+    u.mode = kModeScan;
+    u.sets = G.sets;
+    u.table_n = 0;
+    u.ring = 0;
+    u.arena = u.direct ? 0u : kStageBytes;
+    u.cost = u.direct ? direct_cost : queued_cost;
 }
 
 // Set mode, arena and cost of one unit of a K-way split (K = 1: whole).
@@ -450,6 +483,9 @@ struct pchase_sim_plan {
     // runtime state, set on the first run
     int device = -1, sms = 0, grid = 0, jgrid = 0;
     uint64_t n_isolated = 0;  // units given an SM of their own (in the jumbo launch)
+    uint64_t n_gmem = 0;        // units with their set state in global memory
+    uint64_t gstate_bytes = 0;  // their state area (workspace, after the pooled offsets)
+    size_t off_gstate = 0;
     std::vector<uint32_t> class_caps;  // arena cap of each size class present
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -506,6 +542,7 @@ int plan_launch(pchase_sim_plan *p, void *ws, const SimOut &out, cudaStream_t st
     PCHASE_CUDA(cudaMemsetAsync(w, 0, 256, st), "cudaMemsetAsync(queues)");
     SimOut o = out;
     if (!o.status) o.status = reinterpret_cast<uint32_t *>(w + 128);
+    o.gstate = w + p->off_gstate;
     const SimItem *items = reinterpret_cast<const SimItem *>(w + p->off_items);
     uint32_t *queues = reinterpret_cast<uint32_t *>(w);
     PCHASE_CUDA(launch_sim_zero(items, p->n_units, p->sms, o, st), "output clear");
@@ -616,9 +653,13 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     // by sets into 2^ksh units (see SimItem) so no unit dominates the launch.
     std::vector<SimItem> base;
     std::vector<ItemShape> shape;
+    std::vector<uint8_t> gmem;      // set state in global memory
+    std::vector<UnitShape> gshape;  // and its unit
     try {
         base.resize(n_items);
         shape.resize(n_items);
+        gmem.assign(n_items, 0);
+        gshape.resize(n_items);
     } catch (...) {
         delete p;
         return fail(PCHASE_ENOMEM, "item table allocation");
@@ -688,13 +729,10 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                 need = std::min(need, (uint64_t)uk.arena);
             }
             if (!fits) {
-                delete p;
-                char buf[200];
-                snprintf(buf, sizeof buf,
-                         "item %llu needs %llu bytes of set state (in its smallest allowed part), "
-                         "above the %u-byte limit",
-                         (unsigned long long)i, (unsigned long long)need, kMaxArena);
-                return fail(PCHASE_ERANGE, buf);
+                // no shared-memory arena holds it, even split: global memory
+                global_unit(G, it, sh, tn, u);
+                gmem[i] = 1;
+                gshape[i] = u;
             }
         }
         sh.cost = u.cost;
@@ -779,6 +817,10 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     };
     double critical = 0.0;
     for (uint64_t i = 0; i < n_items; ++i) {
+        if (gmem[i]) {
+            critical = std::max(critical, gshape[i].cost);
+            continue;
+        }
         uint32_t k;
         UnitShape u;
         best_split(i, 0.0, k, u);
@@ -808,6 +850,25 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         for (uint64_t i = 0; i < n_items; ++i) {
             const pchase_geom &G = geoms[base[i].cand];
             const ItemShape &sh = shape[i];
+            if (gmem[i]) {
+                // one whole unit, its set state at 16 * kres bytes of the state area
+                SimItem it = base[i];
+                apply_unit(it, gshape[i]);
+                it.lsh |= 1u << 17;
+                if ((p->gstate_bytes >> 4) > 0xFFFFFFFFull) {
+                    delete p;
+                    return fail(PCHASE_ERANGE, "set state in global memory above 64 GB");
+                }
+                it.kres = (uint32_t)(p->gstate_bytes >> 4);
+                p->gstate_bytes += scan_state_bytes(G);
+                it.cost = (float)gshape[i].cost;
+                items.push_back(it);
+                cost.push_back(gshape[i].cost);
+                p->est_sum += gshape[i].cost;
+                p->est_max_unit = std::max(p->est_max_unit, gshape[i].cost);
+                p->n_gmem += 1;
+                continue;
+            }
             // smallest split that meets the target, else the cheapest one
             uint32_t best_k;
             UnitShape best;
@@ -1050,6 +1111,8 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     off = align256(off + (size_t)n_trace * sizeof(uint64_t));
     p->off_pool = off;
     off = align256(off + 2 * sizeof(uint64_t));
+    p->off_gstate = off;
+    off = align256(off + p->gstate_bytes);
     p->ws_bytes = off;
     *plan_out = p;
     return PCHASE_OK;
@@ -1074,19 +1137,20 @@ uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
 size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes) {
     std::string d;
     if (plan) {
-        uint64_t modes[3] = {0, 0, 0}, split = 0, direct = 0, tsplit = 0;
+        uint64_t modes[3] = {0, 0, 0}, split = 0, direct = 0, tsplit = 0, gmem = 0;
         for (const SimItem &it : plan->items) {
             modes[it.mode < 3 ? it.mode : 0]++;
             split += it.kcnt > 1 && it.lead;
             tsplit += it.kcnt == 1 && it.ks1 && it.lead;
+            gmem += (it.lsh >> 17) & 1u;
             direct += it.direct;
         }
         char tmp[256];
         snprintf(tmp, sizeof tmp,
-                 "items=%llu units=%llu split=%llu time_split=%llu scan=%llu table=%llu "
-                 "batch=%llu direct=%llu jumbo=%llu classes=%u warps=%u smem=%u slots=",
+                 "items=%llu units=%llu split=%llu time_split=%llu global_state=%llu scan=%llu "
+                 "table=%llu batch=%llu direct=%llu jumbo=%llu classes=%u warps=%u smem=%u slots=",
                  (unsigned long long)plan->n_items, (unsigned long long)plan->n_units,
-                 (unsigned long long)split, (unsigned long long)tsplit,
+                 (unsigned long long)split, (unsigned long long)tsplit, (unsigned long long)gmem,
                  (unsigned long long)modes[0],
                  (unsigned long long)modes[1], (unsigned long long)modes[2],
                  (unsigned long long)direct,
@@ -1332,6 +1396,10 @@ int infer_geometry_batch(const pchase_sim_plan *plan, void *workspace, const flo
     if (!plan || !workspace || !lat || !scratch || !dist_out || !pick_out)
         return fail(PCHASE_EINVAL, "infer_geometry_batch: NULL argument");
     if (!plan->cross) return fail(PCHASE_EINVAL, "infer_geometry_batch needs a candidates x traces plan");
+    if (plan->n_gmem)
+        return fail(PCHASE_EINVAL,
+                    "infer_geometry_batch: a unit keeps its set state in global memory and "
+                    "cannot run for several observations at once (use infer_geometry)");
     if (n_obs == 0) return PCHASE_OK;
     if ((uint64_t)n_obs * plan->n_trace > 65535 || n_obs > kMaxBatchObs)
         return fail(PCHASE_ERANGE, "infer_geometry_batch: too many observations for one call");

@@ -100,7 +100,8 @@ struct SimItem {
     uint8_t s1, s2, policy, mode;
     uint32_t lsh;         // line = index >> (lsh & 255) (b = 4 << that); bits 8-15: mapping m;
                           // bit 16: unequal sets (gsets/gmagic: M = T*a + extra, kmagic: a,
-                          // ways: a + extra, the ways of set 0)
+                          // ways: a + extra, the ways of set 0); bit 17: way scans with the
+                          // set state in global memory at 16 * kres bytes (whole units)
     uint32_t table_n;     // line-table entries (local lines)
     uint64_t seed;
     uint64_t word_off;    // plan-owned bitmap layout
@@ -178,6 +179,9 @@ struct SimOut {
     // in filter + filter_word_offsets[i] (queued units only; not with the matcher)
     const uint32_t *filter;
     const uint64_t *filter_word_offsets;
+    // set state of the units that keep it in global memory (SimItem lsh bit
+    // 17), each at 16 * kres bytes from here
+    uint8_t *gstate;
 };
 
 // Records the text pchase_last_error_string() returns on this thread and

@@ -75,7 +75,7 @@ struct ScanSets {
         wtd = it.policy == PCHASE_WEIGHTED;
         psh = it.psh;
         kcnt = it.kcnt;
-        kres = it.kres;
+        kres = (it.lsh >> 17) & 1u ? 0u : it.kres;  // global state: kres is its offset
         slot = reinterpret_cast<uint2 *>(arena);
         evict = reinterpret_cast<uint32_t *>(arena + 8ull * it.sets * ways);
     }
@@ -1085,6 +1085,11 @@ enum : uint32_t {
     kBatchLru = kModeBatch * 3 + PCHASE_LRU,
     kBatchFifo = kModeBatch * 3 + PCHASE_FIFO,
     kBatchRandom = kModeBatch * 3 + PCHASE_RANDOM,
+    // way scans whose set state lives in global memory (caches too large for
+    // any shared-memory arena)
+    kGlobalScanLru = 9 + PCHASE_LRU,
+    kGlobalScanFifo = 9 + PCHASE_FIFO,
+    kGlobalScanRandom = 9 + PCHASE_RANDOM,
 };
 
 // One step of heads through the unit's set state.  The state's views are
@@ -1092,10 +1097,17 @@ enum : uint32_t {
 // only copy of every mode's code: all modes share one unit loop, which keeps
 // the simulator's hot code within the instruction cache while warps of many
 // different units share an SM.
-__device__ __forceinline__ bool resolve_step(uint32_t kind, uint8_t *st, const SimItem &it,
-                                             uint32_t line, uint32_t set, bool head, uint32_t pos,
-                                             int lane, uint32_t lt, uint32_t step) {
+__device__ __forceinline__ bool resolve_step(uint32_t kind, uint8_t *st, uint8_t *gst,
+                                             const SimItem &it, uint32_t line, uint32_t set,
+                                             bool head, uint32_t pos, int lane, uint32_t lt,
+                                             uint32_t step) {
     switch (kind) {
+    case kGlobalScanLru: { RoundResolver<ScanSets<PCHASE_LRU>> R; R.S.bind(gst, it);
+                           return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kGlobalScanFifo: { RoundResolver<ScanSets<PCHASE_FIFO>> R; R.S.bind(gst, it);
+                            return R.resolve(line, set, head, pos, lane, lt, step); }
+    case kGlobalScanRandom: { RoundResolver<ScanSets<PCHASE_RANDOM>> R; R.S.bind(gst, it);
+                              return R.resolve(line, set, head, pos, lane, lt, step); }
     case kScanLru: { RoundResolver<ScanSets<PCHASE_LRU>> R; R.S.bind(st, it);
                      return R.resolve(line, set, head, pos, lane, lt, step); }
     case kScanFifo: { RoundResolver<ScanSets<PCHASE_FIFO>> R; R.S.bind(st, it);
@@ -1117,9 +1129,13 @@ __device__ __forceinline__ bool resolve_step(uint32_t kind, uint8_t *st, const S
     }
 }
 
-__device__ __forceinline__ void clear_state(uint32_t kind, uint8_t *st, const SimItem &it,
-                                            int lane) {
+__device__ __forceinline__ void clear_state(uint32_t kind, uint8_t *st, uint8_t *gst,
+                                            const SimItem &it, int lane) {
     switch (kind) {
+    case kGlobalScanLru: { ScanSets<PCHASE_LRU> S; S.bind(gst, it); S.clear(it, lane); break; }
+    case kGlobalScanFifo: { ScanSets<PCHASE_FIFO> S; S.bind(gst, it); S.clear(it, lane); break; }
+    case kGlobalScanRandom: {
+        ScanSets<PCHASE_RANDOM> S; S.bind(gst, it); S.clear(it, lane); break; }
     case kScanLru: { ScanSets<PCHASE_LRU> S; S.bind(st, it); S.clear(it, lane); break; }
     case kScanFifo: { ScanSets<PCHASE_FIFO> S; S.bind(st, it); S.clear(it, lane); break; }
     case kScanRandom: { ScanSets<PCHASE_RANDOM> S; S.bind(st, it); S.clear(it, lane); break; }
@@ -1153,10 +1169,15 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     uint2 *const queue = reinterpret_cast<uint2 *>(g_smem + arena);
     uint8_t *const st = g_smem + arena + (it.direct ? 0u : kStageBytes);
     // WEIGHTED runs the RANDOM code with its own victim ways
-    const uint32_t kind = (uint32_t)it.mode * 3u + (it.policy < 2u ? it.policy : 2u);
+    const uint32_t pol = it.policy < 2u ? it.policy : 2u;
+    // set state in global memory (lsh bit 17): way scans at 16 * kres bytes
+    // into the plan's state area, owned by this unit alone
+    const bool gmem = (it.lsh >> 17) & 1u;
+    uint8_t *const gst = gmem ? out.gstate + 16ull * it.kres : nullptr;
+    const uint32_t kind = gmem ? 9u + pol : (uint32_t)it.mode * 3u + pol;
     // matcher: a candidate whose other units already exceed the bound is out
     if (out.dist && over_bound(out, it.cand, 0, lane)) return;
-    clear_state(kind, st, it, lane);
+    clear_state(kind, st, gst, it, lane);
     __syncwarp();
     const uint32_t len = it.len;
     const uint32_t *__restrict__ idxp = it.idx;
@@ -1255,7 +1276,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             const uint32_t prev = lane == 0 ? carry : rot;
             carry = rot;
             const bool head = active && ln != prev;
-            const bool miss = resolve_step(kind, st, it, ln, set, head, t, lane, lt, s0 + 1);
+            const bool miss = resolve_step(kind, st, gst, it, ln, set, head, t, lane, lt, s0 + 1);
             const uint32_t bits = __ballot_sync(kFull, miss);
             const uint32_t base = s0 << 5;
             const uint32_t after = base >= warmup ? kFull
@@ -1381,7 +1402,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             ccarry = rot;
             const bool head = act && line != prev;
             ++step;
-            const bool miss = resolve_step(kind, st, it, line, set, head, pos, lane, lt, step);
+            const bool miss = resolve_step(kind, st, gst, it, line, set, head, pos, lane, lt, step);
             const uint32_t bits = __ballot_sync(kFull, miss);
             tot += __popc(bits);
             aft += __popc(__ballot_sync(kFull, miss && pos >= warmup));

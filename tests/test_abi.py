@@ -57,7 +57,7 @@ def _describe(h) -> dict:
     (W.Geom(1024, 32, 2, 8), C.EINVAL),       # T*a*b != C
     (W.Geom(1024, 2, 4, 128), C.EINVAL),      # b < 4
     (W.Geom(1024, 32, 0, 32), C.EINVAL),      # no ways
-    (W.Geom(1 << 22, 32, 1 << 17, 1), C.ERANGE),  # 131072 lines
+    (W.Geom(1 << 30, 32, 1 << 25, 1), C.ERANGE),  # 2^25 lines
     (W.Geom(1024, 32, 4, 8, 7), C.EINVAL),    # unknown policy
     (W.Geom(1024, 32, 2, 16, 3), C.EINVAL),   # WEIGHTED needs 3 ways
     (W.Geom(1024, 32, 4, 8, 0, mapping=17), C.EINVAL),  # mapping above 16
@@ -88,8 +88,10 @@ def test_plan_splits_items_too_large_for_one_warp():
     assert rc == C.OK
     assert int(_describe(h)["units"]) > 1
     C.load().pchase_sim_plan_destroy(h)
-    rc, _ = _plan([g], tr, tune={"max_split": 1})
-    assert rc == C.ERANGE
+    # with splits off it keeps its set state in global memory instead
+    rc, h = _plan([g], tr, tune={"max_split": 1})
+    assert rc == C.OK and _describe(h)["global_state"] == "1"
+    C.load().pchase_sim_plan_destroy(h)
 
 
 def test_planner_isolates_the_costliest_units():
@@ -183,11 +185,23 @@ def test_planner_splits_only_what_can_gain():
             L.pchase_sim_plan_destroy(h)
 
 
-def test_item_too_large_for_shared_memory_is_refused():
-    # fully associative 65535-line cache over a 64 Mi-element array: the line
-    # table alone exceeds the largest class
-    rc, _ = _plan([W.Geom(65535 * 32, 32, 65535, 1)], [(None, 10, 0, 1 << 26, 1)])
-    assert rc == C.ERANGE
+def test_set_state_beyond_shared_memory_goes_to_global_memory():
+    """Items whose set state fits no shared-memory arena, even split (a fully
+    associative 65535-line cache over a 64 Mi-element array; a 128 MB L2 of
+    1 Mi lines), become whole way-scan units with the state in global memory,
+    counted in the workspace; batched inference refuses such plans."""
+    L = C.load()
+    geoms = [W.Geom(65535 * 32, 32, 65535, 1), W.Geom(128 << 20, 128, 16, 65536),
+             W.Geom(128 << 20, 128, 16, 65536, W.RANDOM, 5), W.Geom(16 << 10, 64, 4, 64)]
+    rc, h = _plan(geoms, [(None, 1 << 12, 0, 1 << 26, 1)])
+    assert rc == C.OK
+    try:
+        d = _describe(h)
+        assert d["global_state"] == "3" and d["units"] == "4"
+        state = 8 * 65535 + 2 * 8 * (1 << 20) + 4 * 65536
+        assert L.pchase_sim_plan_workspace_bytes(h) >= state
+    finally:
+        L.pchase_sim_plan_destroy(h)
 
 
 def test_one_shot_reports_workspace_need():
