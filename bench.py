@@ -166,8 +166,8 @@ class ClockSampler:
 # From one ncu capture (--set full) of the current sim_kernel on the batched
 # workload with items capped at 65,536 accesses: the slot-mix launch and the
 # one-warp launch of one run, summed.
-SIM_DRAM_BYTES_PER_ACCESS = (264.571904e6 + 7.42656e6 + 2.597632e6) / 65559830
-SIM_WARP_INST_PER_ACCESS = (431137917 + 8958842) / 65559830
+SIM_DRAM_BYTES_PER_ACCESS = (263.807488e6 + 7.867392e6 + 2.604544e6) / 65559830
+SIM_WARP_INST_PER_ACCESS = (442310117 + 9148504) / 65559830
 
 
 def measured_peaks():
