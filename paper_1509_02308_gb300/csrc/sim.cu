@@ -1174,7 +1174,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     // into the plan's state area, owned by this unit alone
     const bool gmem = (it.lsh >> 17) & 1u;
     uint8_t *const gst = gmem ? out.gstate + 16ull * it.kres : nullptr;
-    const uint32_t kind = gmem ? 9u + pol : (uint32_t)it.mode * 3u + pol;
+    const uint32_t kind = gmem ? (uint32_t)kGlobalScanLru + pol : (uint32_t)it.mode * 3u + pol;
     // matcher: a candidate whose other units already exceed the bound is out
     if (out.dist && over_bound(out, it.cand, 0, lane)) return;
     clear_state(kind, st, gst, it, lane);
