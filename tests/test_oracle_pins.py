@@ -672,3 +672,44 @@ def test_unequal_sets_reject_bad_geometry():
         oracle.cache_sim_uneq(65 * 32 + 32, 32, 8, 7, 9, oracle.LRU, tr)   # C != M * b
     with pytest.raises(Exception):
         oracle.cache_sim_uneq(65 * 32, 32, 8, 7, 9, oracle.RANDOM, tr)     # LRU / FIFO only
+
+
+# ------------------------------------------------- LRU stack property (cuts)
+def _recent_lines(trace, b, T, a, c0):
+    """Per set, the a most recently used distinct lines before access c0,
+    read backwards from c0 (the state a time part of an LRU item rebuilds)."""
+    held = [[] for _ in range(T)]
+    for t in range(c0 - 1, -1, -1):
+        line = (4 * int(trace[t])) // b
+        s = line % T
+        if line not in held[s] and len(held[s]) < a:
+            held[s].append(line)
+    return held
+
+
+def test_lru_state_is_the_most_recent_lines_of_each_set():
+    """Sec. 3's LRU: the lines a set holds at any access are exactly its a
+    most recently used distinct lines, so the state at a cut needs no
+    simulation of the accesses before it.  The oracle's held lines after
+    every prefix agree; under FIFO they need not (FIFO keeps the a most
+    recently inserted lines, which depends on past misses)."""
+    rng = np.random.Generator(np.random.PCG64(303))
+    fifo_differs = 0
+    for _ in range(60):
+        b = int(rng.choice([4, 8, 32]))
+        a, T = int(rng.integers(1, 6)), int(rng.integers(1, 5))
+        n_lines = int(rng.integers(a * T, 4 * a * T + 3))
+        L = int(rng.integers(20, 200))
+        tr = rng.integers(0, n_lines * b // 4, size=L).astype(np.uint32)
+        for c0 in sorted(set(int(x) for x in rng.integers(1, L, size=4))):
+            want = _recent_lines(tr, b, T, a, c0)
+            for policy in (oracle.LRU, oracle.FIFO):
+                _, fin = oracle.cache_sim(a * T * b, b, a, T, policy, tr[:c0], want_final=True)
+                fin = fin.reshape(T, a)
+                got = [sorted(int(x) for x in row if x != 0xFFFFFFFF) for row in fin]
+                same = got == [sorted(h) for h in want]
+                if policy == oracle.LRU:
+                    assert same, (b, a, T, c0, tr[:c0])
+                else:
+                    fifo_differs += not same
+    assert fifo_differs > 0
