@@ -212,6 +212,33 @@ uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
  */
 size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes);
 
+/* One unit of a plan, as pchase_sim_plan_units reports it (host, 48 bytes). */
+typedef struct {
+    uint32_t item;         /* the caller's item it simulates (part of) */
+    uint32_t mode;         /* set mode: 0 way scans, 1 line table, 2 batch */
+    uint32_t parts;        /* K of a split by sets (1: all of the item's sets) */
+    uint32_t residue;      /* the set groups this part owns: (set >> p) mod K == residue */
+    uint32_t first_step;   /* steps of 32 accesses it covers: [first_step, end_step) */
+    uint32_t end_step;
+    uint32_t flags;        /* PCHASE_UNIT_* bits */
+    uint32_t arena_bytes;  /* shared memory the unit needs */
+    uint64_t state_offset; /* PCHASE_UNIT_GLOBAL_STATE: byte offset of its set state in the */
+    uint64_t state_bytes;  /*   workspace's state area, and its size; else 0, 0 */
+} pchase_unit_info;
+#define PCHASE_UNIT_DIRECT 1u        /* steps over consecutive accesses (no queue) */
+#define PCHASE_UNIT_TIME_PART 2u     /* an LRU item cut in time (rebuilds its start state) */
+#define PCHASE_UNIT_GLOBAL_STATE 4u  /* way scans over set state in global memory */
+#define PCHASE_UNIT_UNEQUAL 8u       /* unequal sets (pchase_geom.mapping bits 8-15) */
+#define PCHASE_UNIT_LEAD 16u         /* the one unit of its item that clears the outputs */
+/*
+ * Copies the plan's units, in the order the kernels take them, into out
+ * (host, up to `cap` entries; out may be NULL with cap 0) and returns how
+ * many units the plan has.  Host only: a view of the plan for checks and
+ * tools (every bitmap word has one writer; global-memory set state regions
+ * are disjoint).
+ */
+size_t pchase_sim_plan_units(const pchase_sim_plan *plan, pchase_unit_info *out, size_t cap);
+
 /*
  * Copies the plan's tables into `workspace` (device, at least
  * pchase_sim_plan_workspace_bytes, 256-byte aligned).  Needed once per

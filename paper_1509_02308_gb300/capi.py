@@ -37,6 +37,15 @@ class Pair(ctypes.Structure):
     _fields_ = [("geom", _c_u32), ("trace", _c_u32)]
 
 
+class UnitInfo(ctypes.Structure):
+    _fields_ = [("item", _c_u32), ("mode", _c_u32), ("parts", _c_u32), ("residue", _c_u32),
+                ("first_step", _c_u32), ("end_step", _c_u32), ("flags", _c_u32),
+                ("arena_bytes", _c_u32), ("state_offset", _c_u64), ("state_bytes", _c_u64)]
+
+
+UNIT_DIRECT, UNIT_TIME_PART, UNIT_GLOBAL_STATE, UNIT_UNEQUAL, UNIT_LEAD = 1, 2, 4, 8, 16
+
+
 class Tune(ctypes.Structure):
     _fields_ = [("scan_max_ways", _c_u32), ("smem_budget_bytes", _c_u32),
                 ("max_warps_per_cta", _c_u32), ("ctas_per_sm_cap", _c_u32),
@@ -44,7 +53,7 @@ class Tune(ctypes.Structure):
                 ("filtered", _c_u32)]
 
 
-assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32
+assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32 and ctypes.sizeof(UnitInfo) == 48
 
 # every exported symbol of include/pchase.h with (restype, argtypes)
 SIGNATURES = {
@@ -58,6 +67,7 @@ SIGNATURES = {
     "pchase_sim_plan_bitmap_words": (_c_u64, [_c_p]),
     "pchase_sim_plan_launches": (_c_u32, [_c_p]),
     "pchase_sim_plan_describe": (ctypes.c_size_t, [_c_p, ctypes.c_char_p, ctypes.c_size_t]),
+    "pchase_sim_plan_units": (ctypes.c_size_t, [_c_p, _c_p, ctypes.c_size_t]),
     "pchase_sim_plan_upload": (ctypes.c_int, [_c_p, _c_p, ctypes.c_size_t, _c_p]),
     "pchase_sim_run": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
     "pchase_sim_run_profiled": (ctypes.c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
@@ -159,6 +169,15 @@ def geom_array(geoms) -> ctypes.Array:
         mapping = getattr(g, "mapping", 0) | (getattr(g, "extra", 0) << 8)
         arr[i] = Geom(g.C, g.b, g.ways, g.sets, g.policy, mapping, g.seed & 0xFFFFFFFFFFFFFFFF)
     return arr
+
+
+def plan_units(h) -> list:
+    """The plan's units (pchase_sim_plan_units) as a list of UnitInfo."""
+    L = load()
+    n = int(L.pchase_sim_plan_units(h, None, 0))
+    arr = (UnitInfo * max(1, n))()
+    L.pchase_sim_plan_units(h, ctypes.addressof(arr), n)
+    return list(arr[:n])
 
 
 def trace_array(descs) -> ctypes.Array:

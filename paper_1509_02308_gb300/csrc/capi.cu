@@ -1134,6 +1134,34 @@ uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
            (plan->jumbo.nwarps ? 1u : 0u);
 }
 
+size_t pchase_sim_plan_units(const pchase_sim_plan *plan, pchase_unit_info *out, size_t cap) {
+    if (!plan) return 0;
+    const size_t n = plan->items.size();
+    for (size_t k = 0; k < n && k < cap && out; ++k) {
+        const SimItem &it = plan->items[k];
+        pchase_unit_info &u = out[k];
+        memset(&u, 0, sizeof u);
+        const bool gm = (it.lsh >> 17) & 1u, uneq = (it.lsh >> 16) & 1u;
+        const bool tpart = it.kcnt == 1 && it.ks1 != 0 && !gm;
+        const uint32_t nsteps = (it.len + 31) / 32;
+        u.item = it.out_item;
+        u.mode = it.mode;
+        u.parts = it.kcnt;
+        u.residue = it.kcnt > 1 ? it.kres : 0u;
+        u.first_step = tpart ? it.kres : 0u;
+        u.end_step = tpart ? it.kmagic : nsteps;
+        u.flags = (it.direct ? PCHASE_UNIT_DIRECT : 0u) | (tpart ? PCHASE_UNIT_TIME_PART : 0u) |
+                  (gm ? PCHASE_UNIT_GLOBAL_STATE : 0u) | (uneq ? PCHASE_UNIT_UNEQUAL : 0u) |
+                  (it.lead ? PCHASE_UNIT_LEAD : 0u);
+        u.arena_bytes = it.arena_bytes;
+        if (gm) {
+            u.state_offset = 16ull * it.kres;
+            u.state_bytes = scan_state_bytes(plan->geoms[it.cand]);
+        }
+    }
+    return n;
+}
+
 size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes) {
     std::string d;
     if (plan) {

@@ -264,3 +264,79 @@ def test_unequal_sets_checks():
                 W.Geom(65 * page, page, 8, 7, W.LRU, mapping=1, extra=9)):
         rc, _ = _plan([bad], [(None, 10, 0, 100, 1)])
         assert rc == C.EINVAL, bad
+
+
+def _units_hold_invariants(h, lens):
+    """Every item: one lead unit; its units are one whole unit, K set-parts
+    with each residue once, or time parts tiling its steps in whole
+    1024-access blocks (so each bitmap word has one writer); global-memory
+    set state regions are disjoint and inside the workspace."""
+    L = C.load()
+    units = C.plan_units(h)
+    by_item = {}
+    for u in units:
+        by_item.setdefault(u.item, []).append(u)
+    assert sorted(by_item) == list(range(len(lens)))
+    regions = []
+    for item, us in by_item.items():
+        nsteps = (lens[item] + 31) // 32
+        assert sum(1 for u in us if u.flags & C.UNIT_LEAD) == 1, item
+        tparts = [u for u in us if u.flags & C.UNIT_TIME_PART]
+        if tparts:
+            assert len(tparts) == len(us) >= 2 and all(u.parts == 1 for u in us)
+            spans = sorted((u.first_step, u.end_step) for u in us)
+            assert spans[0][0] == 0 and spans[-1][1] == nsteps, (item, spans)
+            for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+                assert a1 == b0 and a0 < a1 and b0 % 32 == 0, (item, spans)
+            assert all(u.mode == 2 and u.flags & C.UNIT_DIRECT for u in us)
+        elif us[0].parts > 1:
+            K = us[0].parts
+            assert len(us) == K and sorted(u.residue for u in us) == list(range(K))
+            assert all(u.first_step == 0 and u.end_step == nsteps for u in us)
+        else:
+            assert len(us) == 1 and us[0].end_step == nsteps
+        for u in us:
+            if u.flags & C.UNIT_GLOBAL_STATE:
+                assert u.parts == 1 and u.mode == 0 and u.state_bytes > 0
+                assert u.state_offset % 16 == 0
+                regions.append((u.state_offset, u.state_offset + u.state_bytes))
+            else:
+                assert u.state_bytes == 0
+    regions.sort()
+    for (a0, a1), (b0, b1) in zip(regions, regions[1:]):
+        assert a1 <= b0
+    if regions:
+        assert regions[-1][1] <= L.pchase_sim_plan_workspace_bytes(h)
+    return units
+
+
+def test_plan_units_tile_items_and_state():
+    geoms, runs = W.config2()
+    lens = [r.length for r in runs]
+    traces = [(None, r.length, r.warmup, r.n_elems, r.stride) for r in runs]
+    for tune in (None, {"max_split": 16, "split_cost_ns": 1}, {"max_split": 3, "split_cost_ns": 1}):
+        rc, h = _plan(geoms, traces, pairs=[(i, i) for i in range(len(runs))], tune=tune)
+        assert rc == C.OK
+        try:
+            units = _units_hold_invariants(h, lens)
+            d = _describe(h)
+            assert len(units) == int(d["units"])
+            leads = [u for u in units if u.flags & C.UNIT_TIME_PART and u.flags & C.UNIT_LEAD]
+            assert len(leads) == int(d["time_split"])
+        finally:
+            C.load().pchase_sim_plan_destroy(h)
+    # large caches (global-memory state) and unequal sets beside ordinary items
+    MB, page = 1 << 20, 2 << 20
+    geoms = [W.Geom(128 * MB, 128, 16, 65536), W.Geom(8 * MB, 32, 16, 16384, W.RANDOM, 3),
+             W.Geom(65 * page, page, 8, 7, W.LRU, extra=9), W.Geom(16 << 10, 64, 4, 64)]
+    traces = [(None, 100000, 0, (160 * MB) // 4, 32), (None, 5000, 0, (40 * MB) // 4, 8)]
+    lens = [t[1] for _ in geoms for t in traces]
+    for tune in (None, {"max_split": 1}):
+        rc, h = _plan(geoms, traces, tune=tune)
+        assert rc == C.OK
+        try:
+            units = _units_hold_invariants(h, lens)
+            assert sum(1 for u in units if u.flags & C.UNIT_GLOBAL_STATE) >= 2
+            assert sum(1 for u in units if u.flags & C.UNIT_UNEQUAL) == 2
+        finally:
+            C.load().pchase_sim_plan_destroy(h)
