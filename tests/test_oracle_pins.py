@@ -713,3 +713,24 @@ def test_lru_state_is_the_most_recent_lines_of_each_set():
                 else:
                     fifo_differs += not same
     assert fifo_differs > 0
+
+
+def test_unequal_l2_tlb_behind_a_thrashing_l1_tlb():
+    """Sec. 4.4's path with the measured L2 TLB: past 16 pages the L1 TLB
+    (16 entries, LRU) misses on every access of a 2 MB chain, so the
+    unequal L2 TLB sees the whole stream and behaves as it does alone
+    (Fig. 9's steps); within 16 pages it sees only the first touches."""
+    page = 2 << 20
+    l1 = dict(C=16 * page, b=page, ways=16, T=1, policy=oracle.LRU)
+    l2 = dict(C=65 * page, b=page, ways=8, T=7, policy=oracle.LRU, extra=9)
+    for n_pages in (17, 40, 65, 66, 69, 72, 90):
+        n = n_pages * page // 4
+        tr = oracle.pchase_trace(n, page // 4, 4 * n_pages)
+        m1, m2 = oracle.hierarchy([l1, l2], tr)
+        assert m1.all()
+        assert np.array_equal(m2, oracle.cache_sim_uneq(65 * page, page, 8, 7, 9, oracle.LRU, tr))
+    for n_pages in (1, 9, 16):
+        n = n_pages * page // 4
+        tr = oracle.pchase_trace(n, page // 4, 4 * n_pages)
+        m1, m2 = oracle.hierarchy([l1, l2], tr)
+        assert m1[n_pages:].sum() == 0 and m2.sum() == n_pages
