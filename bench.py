@@ -205,9 +205,15 @@ def cpu_baseline(geoms, runs, n_items):
     idx = oracle_sample(geoms, runs, n_items)
     cores = os.cpu_count() or 1
     acc, dt, _ = run_oracle(geoms, runs, idx, cores)
+    # and on one core, over a sixteenth of the same items
+    idx1 = idx[:max(1, len(idx) // 16)]
+    acc1, dt1, _ = run_oracle(geoms, runs, idx1, 1)
     return {"value": acc / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(idx)} seeded items of the 4096-item batch at full length "
-                      f"({acc} accesses, {dt:.1f} s wall, one item per thread)"}
+                      f"({acc} accesses, {dt:.1f} s wall, one item per thread)",
+            "single_thread": {"value": acc1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{len(idx1)} of those items ({acc1} accesses, "
+                                        f"{dt1:.1f} s)"}}
 
 
 # ------------------------------------------------------------- our arm
