@@ -734,3 +734,39 @@ def test_unequal_l2_tlb_behind_a_thrashing_l1_tlb():
         tr = oracle.pchase_trace(n, page // 4, 4 * n_pages)
         m1, m2 = oracle.hierarchy([l1, l2], tr)
         assert m1[n_pages:].sum() == 0 and m2.sum() == n_pages
+
+
+def test_spectrum_chain_reaches_the_paper_patterns():
+    """Sec. 5.2 (Fig. 10, the pattern table of Fig. 11): the non-uniform
+    chain's segments land in the patterns they are built for, under the
+    cache model with a data cache that holds its lines (256 lines of 128 B,
+    fully associative, LRU: with sets taken from the low line bits, lines
+    1 MB apart would all share one set), the 16-entry L1 TLB and the unequal
+    L2 TLB over 2 MB pages:
+    B misses the data cache and the L1 TLB on each new page only; A misses
+    both; C hits the data cache, and misses the L1 TLB on its first return
+    to each page (A's sweep flushed them); D hits everything after its first
+    access."""
+    path, labels, n = W.spectrum_chain()
+    tr = np.array(path, dtype=np.uint32)
+    lab = np.array(labels)
+    page = 2 << 20
+    data = oracle.cache_sim(256 * 128, 128, 256, 1, oracle.LRU, tr)
+    t1, t2 = oracle.hierarchy([dict(C=16 * page, b=page, ways=16, T=1, policy=oracle.LRU),
+                               dict(C=65 * page, b=page, ways=8, T=7, policy=oracle.LRU,
+                                    extra=9)], tr)
+    assert len(path) == 65 + 64 + 65 + 32 and len(set(path)) == len(path)
+    assert data[lab == "B_new_page"].all() and data[lab == "B_same_page"].all()
+    assert t1[lab == "B_new_page"].all() and not t1[lab == "B_same_page"].any()
+    assert data[lab == "A_32MB"].all() and t1[lab == "A_32MB"].all()
+    c = np.flatnonzero(lab == "C_revisit")
+    c_pages = (4 * tr[c].astype(np.uint64)) // page
+    first = np.zeros(c.size, dtype=bool)
+    first[np.unique(c_pages, return_index=True)[1]] = True
+    assert not data[c].any()
+    assert t1[c][first].all()
+    d = np.flatnonzero(lab == "D_same_line")
+    assert not data[d[1:]].any() and not t1[d[1:]].any()
+    # the L2 TLB tells the C accesses apart: their pages were last used
+    # before A's 64 new pages went through it
+    assert t2[lab == "C_revisit"].sum() > 0
