@@ -66,6 +66,8 @@ def parse():
                         "(for profilers that cannot follow stream capture)")
     p.add_argument("--cpu-sample", type=int, default=512, help="items in the oracle sample")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner (default knobs)")
+    p.add_argument("--retune", action="store_true",
+                   help="run the autotuner afresh instead of using the shipped knobs")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-inverse section")
     p.add_argument("--no-probes", action="store_true", help="skip the on-device probe section")
     p.add_argument("--no-hierarchy", action="store_true",
@@ -75,7 +77,6 @@ def parse():
     p.add_argument("--inverse-steps", type=int, default=2442,
                    help="training steps of 4096 synthetic traces for the learned inverse")
     p.add_argument("--inverse-eval", type=int, default=100000)
-    p.add_argument("--ref-items-per-step", type=int, default=256)
     return p.parse_args()
 
 
@@ -185,13 +186,14 @@ def oracle_sample(geoms, runs, n_items, seed=0xC0DE):
 
 
 def run_oracle(geoms, runs, idx, threads):
+    """The oracle's full output (per-access miss flags) for items idx, one item
+    per thread; returns (accesses, wall seconds, flags per item)."""
     import oracle
 
     def one(i):
         g, r = geoms[i], runs[i]
         tr = oracle.pchase_trace(r.n_elems, r.stride, r.length)
-        return oracle.cache_sim_counts(g.C, g.b, g.ways, g.sets, g.policy, tr, r.warmup,
-                                       seed=g.seed)
+        return oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed)
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
@@ -201,19 +203,49 @@ def run_oracle(geoms, runs, idx, threads):
     return acc, dt, res
 
 
+def oracle_cost(g, r) -> float:
+    """The oracle's work for one item, roughly: it scans every way of a set on
+    each access, so accesses x ways."""
+    return float(r.length) * max(1, g.ways)
+
+
 def cpu_baseline(geoms, runs, n_items):
+    """The oracle on a fixed seeded sample of the batch (all host cores, one
+    item per thread), and on one core over every 16th item of that sample in
+    order of oracle cost, so both see the same mix of cheap and costly items.
+    Also returns the sample and its flags for the parity check."""
     idx = oracle_sample(geoms, runs, n_items)
     cores = os.cpu_count() or 1
-    acc, dt, _ = run_oracle(geoms, runs, idx, cores)
-    # and on one core, over a sixteenth of the same items
-    idx1 = idx[:max(1, len(idx) // 16)]
+    acc, dt, flags = run_oracle(geoms, runs, idx, cores)
+    by_cost = sorted(idx, key=lambda i: oracle_cost(geoms[i], runs[i]))
+    idx1 = by_cost[8::16] or by_cost[:1]
     acc1, dt1, _ = run_oracle(geoms, runs, idx1, 1)
     return {"value": acc / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(idx)} seeded items of the 4096-item batch at full length "
-                      f"({acc} accesses, {dt:.1f} s wall, one item per thread)",
+                      f"({acc} accesses, {dt:.1f} s wall, one item per thread, per-access "
+                      f"miss flags out)",
             "single_thread": {"value": acc1 / dt1, "unit": UNIT, "cores": 1,
-                              "sample": f"{len(idx1)} of those items ({acc1} accesses, "
-                                        f"{dt1:.1f} s)"}}
+                              "sample": f"every 16th of those items by oracle cost "
+                                        f"({len(idx1)} items, {acc1} accesses, {dt1:.1f} s)"}}, \
+        idx, flags
+
+
+def parity_check(bitmaps_host, counts_host, word_offsets, runs, idx, flags) -> dict:
+    """Bit-exact comparison of the timed run's outputs (bitmaps and both miss
+    counts) with the oracle's flags for the sampled items."""
+    bad = []
+    acc = 0
+    for i, want in zip(idx, flags):
+        n = runs[i].length
+        w0 = int(word_offsets[i])
+        got = np.unpackbits(bitmaps_host[w0:w0 + (n + 31) // 32].view(np.uint8),
+                            bitorder="little")[:n]
+        acc += n
+        if (not np.array_equal(got, want) or int(counts_host[i, 0]) != int(want.sum())
+                or int(counts_host[i, 1]) != int(want[runs[i].warmup:].sum())):
+            bad.append(int(i))
+    return {"parity_ok": not bad, "parity_items_checked": len(idx),
+            "parity_accesses_checked": acc, "parity_mismatched_items": bad[:16]}
 
 
 # ------------------------------------------------------------- our arm
@@ -239,7 +271,15 @@ def ours(args):
     pairs = [(i, i) for i in range(len(runs))]
     tune = None
     tune_note = "defaults"
-    if not args.no_tune:
+    shipped = None
+    if not args.no_tune and not args.retune:
+        from paper_1509_02308_gb300 import autotune
+        shipped = autotune.lookup(geoms, traces, pairs)
+    if shipped is not None:
+        tune = shipped
+        tune_note = ("autotuned on a GB300 (coordinate descent on this workload), knobs shipped "
+                     "in the package's tuned.json")
+    elif not args.no_tune:
         from paper_1509_02308_gb300 import autotune
         # the traces must exist before candidate plans are timed: build them once
         from paper_1509_02308_gb300 import capi as _C
@@ -249,8 +289,8 @@ def ours(args):
         _C.check(_C.load().pchase_build_batch(_ct.addressof(_d), len(runs), _C.ptr(flat),
                                               _o.ctypes.data, _C.stream_handle()))
         torch.cuda.synchronize()
-        tune = autotune.tune(geoms, traces, pairs=pairs, reps=2, sweeps=1)
-        tune_note = "autotuned (coordinate descent on this workload)"
+        tune = autotune.tune(geoms, traces, pairs=pairs, reps=2, sweeps=1, fresh=args.retune)
+        tune_note = "autotuned in this run (coordinate descent on this workload)"
     plan = api.SimPlan(geoms, traces, pairs=pairs, tune=tune)
     bitmaps = torch.empty(max(1, plan.bitmap_words), dtype=torch.int32, device=dev)
     counts = torch.empty(2 * len(runs), dtype=torch.int64, device=dev)
@@ -331,6 +371,9 @@ def ours(args):
         torch.cuda.synchronize()
         build_ms.append(a.elapsed_time(b))
     clk = clocks.stop()
+    # outputs of the last run of the timed plan, for the parity check below
+    bits_host = bitmaps.cpu().numpy().view(np.uint32)
+    counts_host = counts.view(-1, 2).cpu().numpy()
 
     # max over ranks
     t_step = max_over_ranks(ms / args.steps, world, dev)
@@ -417,7 +460,10 @@ def ours(args):
             "single_unbounded": a["traces_per_s"] / inf["traces_inferred_per_s"],
             "batched_bound0": a["traces_per_s"] / inf["batched"]["stop0"]["traces_inferred_per_s"]}
     if rank == 0 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_baseline(geoms, runs, args.cpu_sample)
+        result["cpu_baseline"], sample, flags = cpu_baseline(geoms, runs, args.cpu_sample)
+        # the outputs of the last timed-plan run, checked against the oracle
+        result.update(parity_check(bits_host, counts_host, plan.word_offsets, runs, sample,
+                                   flags))
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
@@ -913,20 +959,18 @@ def reference(args):
     if rank != 0:
         return
     from paper_1509_02308_gb300 import workloads as W
-    geoms, runs = W.config2(n_items=args.items)
+    geoms, runs = W.config2(n_items=args.items, max_len=args.max_len)
     cores = os.cpu_count() or 1
-    rng = np.random.Generator(np.random.PCG64(0xBEEF))
-    per_step = max(4, min(args.ref_items_per_step, len(runs)))
-
-    def sample():
-        return sorted(rng.choice(len(runs), size=per_step, replace=False).tolist())
+    # the same seeded sample our arm's cpu_baseline times, every step
+    idx = oracle_sample(geoms, runs, args.cpu_sample)
+    per_step = len(idx)
 
     for _ in range(args.warmup):
-        run_oracle(geoms, runs, sample()[:4], cores)
+        run_oracle(geoms, runs, idx[:4], cores)
     acc = 0
     dt = 0.0
     for _ in range(args.steps):
-        a, t, _ = run_oracle(geoms, runs, sample(), cores)
+        a, t, _ = run_oracle(geoms, runs, idx, cores)
         acc += a
         dt += t
     value = acc / dt
@@ -936,7 +980,9 @@ def reference(args):
            "impl": "reference",
            "config": {"workload": WORKLOAD, "items_per_step": per_step},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{per_step} seeded items per step at full length"},
+                            "sample": f"the same {per_step} seeded items of the batch every "
+                                      f"step, at full length, one item per thread, per-access "
+                                      f"miss flags out"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

@@ -315,6 +315,11 @@ int cache_sim_batch(const pchase_geom *geoms, uint32_t n_geom, const pchase_trac
  * Writes packed miss bits (LSB first) for observation o at
  * bits_out + bit_word_offsets[o] (device) and the cut to thresh_out[o].
  * offsets, bit_word_offsets: device uint64, n_obs + 1 and n_obs entries.
+ * max_len must be at least every observation's length n: the workspace holds
+ * 2 * max_len buckets per observation.  An observation with n > max_len (or
+ * with offsets[o+1] < offsets[o]) is refused on the device: its thresh_out[o]
+ * is NaN, its bits are all 0, and it touches no workspace byte outside its
+ * own slice; the other observations are unaffected.
  * Work buffers: `workspace` (device) of pchase_classify_workspace_bytes.
  */
 size_t pchase_classify_workspace_bytes(uint32_t n_obs, uint64_t max_len);
@@ -328,11 +333,13 @@ int pchase_classify(const float *lat, const uint64_t *offsets, uint32_t n_obs,
  * example a measurement loop that classifies probe latencies between probe
  * runs, where a cudaMalloc would synchronise the device and disturb the very
  * timings being taken, or a process whose device memory is owned entirely by
- * another allocator.  Same inputs, outputs and reading as pchase_classify; its
- * scratch is a fixed 8 MiB array inside the library (every GPU that loads the
- * library holds it until the process exits), so the request must satisfy
- * 16 * n_obs * (max_len + 1) bytes (rounded up to 256) <= 8 MiB, else the call
- * returns PCHASE_ERANGE without queuing anything.  The first call on a device
+ * another allocator.  Same inputs, outputs, reading and max_len contract (an
+ * observation longer than max_len gets a NaN cut and all-0 bits) as
+ * pchase_classify; its scratch is a fixed 8 MiB array inside the library
+ * (every GPU that loads the library holds it until the process exits), so the
+ * request must satisfy r(16 * n_obs) + r(16 * n_obs * max_len) <= 8 MiB, r(x)
+ * being x rounded up to a multiple of 256, else the call returns
+ * PCHASE_ERANGE without queuing anything.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) and should come
  * before any stream capture.  Every call on a device shares the one array:
  * calls whose work overlaps on the GPU (different streams, or another thread)
@@ -516,6 +523,14 @@ size_t pchase_inverse_status_offset(const pchase_inverse *h);
  * [B][positions][64] for the last chunk of the last forward pass; 0 for a
  * layer out of range.  For inspection and tests. */
 size_t pchase_inverse_activation_offset(const pchase_inverse *h, uint32_t layer);
+
+/* Byte offset in `params` of one of its arrays, each pchase_inverse_param_count
+ * entries in the weight order above: which = 0 the FP32 master weights, 1
+ * their BF16 copies (the operands every product uses), 2 the FP32 gradient of
+ * the last pchase_inverse_train_step (left in place by the step), 3 and 4 the
+ * FP32 Adam moments m and v.  (size_t)-1 for another `which`.  For
+ * checkpoints, inspection and tests. */
+size_t pchase_inverse_param_offset(const pchase_inverse *h, uint32_t which);
 
 /* Uniform init of every weight in +-sqrt(6 / fan_in) (SplitMix64 keyed on
  * seed and index), biases 0, Adam moments 0. */

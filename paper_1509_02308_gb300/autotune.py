@@ -3,9 +3,15 @@ the CTA shape by timing the caller's own workload on the device.
 
 Coordinate descent over the knobs of pchase_tune: for each knob in turn every
 candidate value is timed (median of `reps` CUDA-event-timed runs of the whole
-planned batch, bitmaps and counts written) with the other knobs at their best so far; two sweeps.  The
-winner is cached as JSON, keyed by the device name and a signature of the
-workload (geometry and trace shapes), so later runs reuse it.
+planned batch, bitmaps and counts written) with the other knobs at their
+best so far; two sweeps.  The winner is cached as JSON, keyed by the device
+name and a signature of the workload (geometry and trace shapes), so later
+runs reuse it.
+
+``tuned.json`` beside this file ships the knobs the tuner chose on a GB300
+for the workloads this package benchmarks (same key).  They are looked up
+first, so a benchmark times, and a test replays, one fixed plan rather than
+whatever a noisy tuning run picks; ``tune(fresh=True)`` ignores them.
 """
 from __future__ import annotations
 
@@ -28,6 +34,7 @@ KNOBS = {
 DEFAULT = {"batch_max_sets": 64, "scan_max_ways": 4, "max_warps_per_cta": 16,
            "smem_budget_bytes": 220 * 1024, "max_split": 32}
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
 def signature(geoms, traces, pairs) -> str:
@@ -38,6 +45,21 @@ def signature(geoms, traces, pairs) -> str:
         h.update(f"{t[1]},{t[2]},{t[3]},{t[4]},{t[0] is None};".encode())
     h.update(str(len(pairs) if pairs is not None else -1).encode())
     return h.hexdigest()[:16]
+
+
+def key(geoms, traces, pairs, device: str | None = None) -> str:
+    dev = device if device is not None else torch.cuda.get_device_name()
+    return f"{dev}|{signature(geoms, traces, pairs)}"
+
+
+def lookup(geoms, traces, pairs=None, device: str | None = None) -> dict | None:
+    """The shipped knobs for this workload on this device, or None."""
+    if not os.path.exists(SHIPPED):
+        return None
+    with open(SHIPPED) as f:
+        db = json.load(f)
+    e = db.get(key(geoms, traces, pairs, device))
+    return dict(e["tune"]) if e else None
 
 
 def _time(geoms, traces, pairs, tune, reps):
@@ -56,20 +78,24 @@ def _time(geoms, traces, pairs, tune, reps):
 
 
 def tune(geoms, traces, pairs=None, reps: int = 3, sweeps: int = 2, cache: str | None = CACHE,
-         log=None) -> dict:
-    """Best pchase_tune settings (dict) for this workload on this device."""
-    dev = torch.cuda.get_device_name()
-    sig = signature(geoms, traces, pairs)
-    key = f"{dev}|{sig}"
+         log=None, fresh: bool = False) -> dict:
+    """Best pchase_tune settings (dict) for this workload on this device:
+    the shipped knobs, else the cached ones, else a tuning run (fresh=True:
+    always a tuning run, whose result is then cached)."""
+    k = key(geoms, traces, pairs)
+    if not fresh:
+        shipped = lookup(geoms, traces, pairs)
+        if shipped is not None:
+            return shipped
     db = {}
-    if cache and os.path.exists(cache):
+    if cache and os.path.exists(cache) and not fresh:
         try:
             with open(cache) as f:
                 db = json.load(f)
         except Exception:
             db = {}
-        if key in db:
-            return dict(db[key]["tune"])
+        if k in db:
+            return dict(db[k]["tune"])
     best = dict(DEFAULT)
     best_ms = _time(geoms, traces, pairs, best, reps)
     trials = [(dict(best), best_ms)]
@@ -91,9 +117,56 @@ def tune(geoms, traces, pairs=None, reps: int = 3, sweeps: int = 2, cache: str |
             break
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
-        db[key] = {"tune": best, "ms": best_ms, "default_ms": trials[0][1], "trials": len(trials)}
+        if fresh and os.path.exists(cache):
+            try:
+                with open(cache) as f:
+                    db = json.load(f)
+            except Exception:
+                db = {}
+        db[k] = {"tune": best, "ms": best_ms, "default_ms": trials[0][1], "trials": len(trials)}
         tmp = cache + f".tmp{os.getpid()}"
         with open(tmp, "w") as f:
             json.dump(db, f, indent=1)
         os.replace(tmp, cache)
     return best
+
+
+def _main():
+    """Tunes the batched-simulation benchmark workload (4096 items) on this
+    device and writes its entry into the shipped table (or --out)."""
+    import argparse
+
+    from . import api, workloads as W
+    p = argparse.ArgumentParser()
+    p.add_argument("--out", default=SHIPPED)
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--sweeps", type=int, default=2)
+    a = p.parse_args()
+    geoms, runs = W.config2()
+    flat, offs = api.pchase_build_batch(runs)
+    traces = [(flat[int(offs[i]):int(offs[i + 1])], r.length, r.warmup, r.n_elems, r.stride)
+              for i, r in enumerate(runs)]
+    pairs = [(i, i) for i in range(len(runs))]
+    torch.cuda.synchronize()
+    log = []
+    best = tune(geoms, traces, pairs=pairs, reps=a.reps, sweeps=a.sweeps, cache=None,
+                log=log.append, fresh=True)
+    ms_best = _time(geoms, traces, pairs, best, 5)
+    ms_default = _time(geoms, traces, pairs, dict(DEFAULT), 5)
+    db = {}
+    if os.path.exists(a.out):
+        with open(a.out) as f:
+            db = json.load(f)
+    db[key(geoms, traces, pairs)] = {
+        "workload": "batched simulation, 4096 items (workloads.config2 defaults)",
+        "tune": best, "ms": round(ms_best, 3), "default_ms": round(ms_default, 3),
+        "trials": len(log) + 1}
+    with open(a.out, "w") as f:
+        json.dump(db, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print("\n".join(log))
+    print(json.dumps(db[key(geoms, traces, pairs)]))
+
+
+if __name__ == "__main__":
+    _main()

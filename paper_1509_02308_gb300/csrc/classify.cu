@@ -63,6 +63,14 @@ __global__ void __launch_bounds__(1024) select_cut_kernel(const float *lat,
         if (threadIdx.x == 0) meta[o] = ObsMeta{0, 0, 0, 0.0f};
         return;
     }
+    if (n > max_len) {
+        // the observation's bucket slice holds 2 * max_len buckets: an
+        // observation longer than the caller's max_len is refused (NaN cut, so
+        // no latency is above it and every bit stays 0) instead of writing
+        // into the next observation's slice or past the scratch
+        if (threadIdx.x == 0) meta[o] = ObsMeta{0, 0, 0, __int_as_float(0x7FC00000)};
+        return;
+    }
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;

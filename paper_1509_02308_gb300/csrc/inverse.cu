@@ -6,9 +6,12 @@
 // Network (per trace, channel-last activations [L, C]):
 //   4 x [conv1d k=5, stride 2, pad 2, 64 channels, GELU]: 512x1 -> 256 -> 128 -> 64 -> 32
 //   flatten 32*64 = 2048 -> FC 256 -> GELU -> FC 31 = heads of 17 + 4 + 7 + 3 logits
-// Convolutions run as im2col + GEMM.  All GEMMs use BF16 operands and FP32
-// accumulation on the tensor cores (mma.sync m16n8k16); master weights, Adam
-// moments and gradients stay FP32.
+// Every product takes BF16 operands with FP32 accumulation; master weights,
+// Adam moments and gradients stay FP32.  Inference runs the 64-channel
+// convolutions and FC + heads on the tcgen05 tensor cores (conv_tc.cu); the
+// training step's GEMMs (forward with kept pre-activations, backward, weight
+// gradients) run here on warp-level mma.sync m16n8k16 tiles, the first
+// convolution (one input channel) on CUDA cores.
 //
 // The synthetic traces follow Sec. 4.1's mean-latency model t = t0 + t_m r
 // with r the miss rate the simulator reports for each plan point.
@@ -1076,6 +1079,17 @@ size_t pchase_inverse_work_bytes(const pchase_inverse *h) { return h ? h->work_b
 size_t pchase_inverse_status_offset(const pchase_inverse *h) { return h ? h->status : 0; }
 size_t pchase_inverse_activation_offset(const pchase_inverse *h, uint32_t layer) {
     return h && layer < 4 ? h->act[layer] : 0;
+}
+size_t pchase_inverse_param_offset(const pchase_inverse *h, uint32_t which) {
+    if (!h) return (size_t)-1;
+    switch (which) {
+        case 0: return h->p_w;
+        case 1: return h->p_wb;
+        case 2: return h->p_g;
+        case 3: return h->p_m;
+        case 4: return h->p_v;
+        default: return (size_t)-1;
+    }
 }
 
 int pchase_inverse_init(const pchase_inverse *h, void *params, uint64_t seed,

@@ -127,7 +127,14 @@ class LearnedInverse:
 
     def weights(self) -> torch.Tensor:
         """FP32 master weights (a view into the parameter buffer)."""
-        off = self._p - C.ptr(self.params)
+        return self.param_array(0)
+
+    def param_array(self, which: int) -> torch.Tensor:
+        """A view of one parameter array: 0 FP32 weights, 1 BF16 copies, 2 the
+        last train step's FP32 gradient, 3 / 4 the Adam moments."""
+        off = (self._p - C.ptr(self.params)) + int(self.L.pchase_inverse_param_offset(self.h, which))
+        if which == 1:
+            return self.params[off:off + 2 * self.n_params].view(torch.bfloat16)
         return self.params[off:off + 4 * self.n_params].view(torch.float32)
 
     def status(self) -> int:

@@ -1,0 +1,68 @@
+"""Bit-exact parity of the whole batched-simulation workload (4096 seeded
+items, 0.64 G accesses, every item at full length) with the CPU oracle,
+under the plan the benchmark times (the shipped autotuned knobs) and under the
+default knobs.  Every item's miss bitmap is compared access by access, and
+both of its miss counts (Assumptions 1-3, Sec. 4.1; LRU, FIFO and the RANDOM
+reading).  The oracle runs one item per host thread."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1509_02308_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1509_02308_gb300 import api, autotune
+    from paper_1509_02308_gb300.api import SimPlan
+
+
+def _run(geoms, traces, pairs, tune):
+    plan = SimPlan(geoms, traces, pairs=pairs, tune=tune)
+    bitmaps, counts = plan.run()
+    torch.cuda.synchronize()
+    out = (bitmaps.cpu().numpy().view(np.uint32), counts.view(-1, 2).cpu().numpy(),
+           plan.word_offsets.copy(), plan.description)
+    del plan, bitmaps, counts
+    return out
+
+
+def test_config2_whole_batch_bit_exact_under_the_timed_plan():
+    geoms, runs = W.config2()
+    assert len(runs) == 4096
+    flat, offs = api.pchase_build_batch(runs)
+    traces = [(flat[int(offs[i]):int(offs[i + 1])], r.length, r.warmup, r.n_elems, r.stride)
+              for i, r in enumerate(runs)]
+    pairs = [(i, i) for i in range(len(runs))]
+    timed = autotune.lookup(geoms, traces, pairs)
+    if timed is None:  # the benchmark tunes in its own run then; so does this test
+        timed = autotune.tune(geoms, traces, pairs=pairs, reps=2, sweeps=1)
+    results = {"timed": _run(geoms, traces, pairs, timed),
+               "default": _run(geoms, traces, pairs, None)}
+    del traces, flat
+    torch.cuda.empty_cache()
+
+    def one(i):
+        g, r = geoms[i], runs[i]
+        want = oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy,
+                                oracle.pchase_trace(r.n_elems, r.stride, r.length), seed=g.seed)
+        bad = []
+        for name, (bits, counts, woffs, _) in results.items():
+            w0 = int(woffs[i])
+            got = api.unpack_bits(bits[w0:w0 + (r.length + 31) // 32], r.length)
+            if not np.array_equal(got, want):
+                bad.append((name, i, "bitmap", int(np.argmax(got != want))))
+            elif (int(counts[i, 0]) != int(want.sum())
+                  or int(counts[i, 1]) != int(want[r.warmup:].sum())):
+                bad.append((name, i, "counts"))
+        return bad
+
+    # costliest items first so the pool ends evenly
+    order = sorted(range(len(runs)), key=lambda i: -runs[i].length * max(1, geoms[i].ways))
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        bad = [b for r in ex.map(one, order) for b in r]
+    assert not bad, (bad[:10], {k: v[3] for k, v in results.items()})

@@ -50,6 +50,52 @@ def test_classify_edge_cases_batch():
         assert np.array_equal(got, want), i
 
 
+def test_classify_refuses_an_observation_longer_than_max_len():
+    """An observation longer than the caller's max_len gets a NaN cut and all-0
+    bits and writes no workspace byte outside its own bucket slice; the other
+    observations keep the oracle's answer.  A guard region after the
+    workspace proves nothing past the last slice is written."""
+    from paper_1509_02308_gb300 import capi as C
+    L = C.load()
+    rng = np.random.Generator(np.random.PCG64(11))
+    sizes = [900, 400, 3000]          # max_len below: 1000, so the last one is too long
+    max_len = 1000
+    lats = []
+    for n in sizes:
+        miss = (rng.random(n) < 0.4).astype(np.uint8)
+        lats.append(synth_latency(miss, n))
+    offs = np.zeros(len(sizes) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(sizes)
+    words = np.zeros(len(sizes), dtype=np.int64)
+    words[1:] = np.cumsum([(n + 31) // 32 for n in sizes])[:-1]
+    nwords = sum((n + 31) // 32 for n in sizes)
+    flat = torch.from_numpy(np.concatenate(lats)).cuda()
+    d_offs, d_w = torch.from_numpy(offs).cuda(), torch.from_numpy(words).cuda()
+    bits = torch.full((nwords,), -1, dtype=torch.int32, device="cuda")
+    thr = torch.zeros(len(sizes), dtype=torch.float32, device="cuda")
+    need = int(L.pchase_classify_workspace_bytes(len(sizes), max_len))
+    guard = 1 << 16
+    ws = torch.full((need + 256 + guard,), 0xA5, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) & ~255
+    lead = base - ws.data_ptr()
+    C.check(L.pchase_classify(flat.data_ptr(), d_offs.data_ptr(), len(sizes), max_len,
+                              bits.data_ptr(), d_w.data_ptr(), thr.data_ptr(), base, None))
+    torch.cuda.synchronize()
+    tail = ws[lead + need:].cpu().numpy()
+    assert (tail == 0xA5).all(), int(np.argmax(tail != 0xA5))
+    b = bits.cpu().numpy().view(np.uint32)
+    t = thr.cpu().numpy()
+    for i, n in enumerate(sizes):
+        got = api.unpack_bits(b[int(words[i]):], n)
+        if n > max_len:
+            assert np.isnan(t[i])
+            assert not got.any()
+        else:
+            want, wthr = oracle.classify(lats[i])
+            assert np.float32(t[i]) == np.float32(wthr)
+            assert np.array_equal(got, want)
+
+
 def small_candidates():
     grid = W.geometry_grid(capacities=(512, 768, 1024, 1536), line_sizes=(32, 64),
                            way_choices=(1, 2, 4, 8, 0))

@@ -87,3 +87,145 @@ def test_cross_entropy_of_flat_logits():
     assert abs(R.xent(z, lab) - want) < 1e-12
     pred, conf = R.predict(z)
     assert (pred == 0).all() and np.allclose(conf, 1 / (17 * 4 * 7 * 3))
+
+
+# ----------------------------------------------------------- training step
+TINY = R.Spec(points=32, ch=3, hidden=6)
+
+
+def _tiny_net(seed, B=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = rng.standard_normal(R.param_count(TINY)) * 0.7
+    x = rng.random((B, TINY.points))
+    lab = np.stack([rng.integers(0, n, size=B) for n in (17, 4, 7, 3)], axis=1)
+    return w, x, lab
+
+
+def test_backward_equals_finite_differences_on_every_parameter():
+    """The chain-rule gradient of the mean cross-entropy against central
+    differences of the float64 loss, on every parameter of a tiny network
+    (32 points, 3 channels, hidden 6: all four convolutions, the dense layer,
+    the heads and every bias)."""
+    for seed in (1, 2):
+        w, x, lab = _tiny_net(seed)
+        g, mag = R.backward(R.forward_cache(w, x, round_bf16=False, spec=TINY), lab)
+        assert g.size == w.size == R.param_count(TINY) and (mag >= np.abs(g) - 1e-15).all()
+        h = 1e-6
+        fd = np.empty_like(g)
+        for i in range(w.size):
+            wp, wm = w.copy(), w.copy()
+            wp[i] += h
+            wm[i] -= h
+            fd[i] = (R.xent(R.forward(wp, x, False, TINY), lab) -
+                     R.xent(R.forward(wm, x, False, TINY), lab)) / (2 * h)
+        err = np.abs(g - fd)
+        assert (err <= 1e-7 + 1e-5 * np.abs(fd)).all(), (int(err.argmax()), err.max())
+        # every layer's weights and biases carry signal
+        o = 0
+        for r, c in R.layer_shapes(TINY):
+            assert np.abs(g[o:o + r * c]).max() > 1e-4
+            o += r * c + r
+
+
+def test_flatten_is_position_major_by_brute_force():
+    """The oracle's forward pass against plain loops over (trace, position,
+    channel) that write the dense layer's input feature p * ch + c (the
+    layout the C header states), on the tiny network."""
+    w, x, _ = _tiny_net(3, B=2)
+    layers = R.unpack(w, TINY)
+    h = [[[x[b, p]] for p in range(TINY.points)] for b in range(2)]
+    cin = 1
+    for l in range(4):
+        W, bias = layers[l]
+        L = len(h[0])
+        out = [[[0.0] * TINY.ch for _ in range(L // 2)] for _ in range(2)]
+        for b in range(2):
+            for lo in range(L // 2):
+                for co in range(TINY.ch):
+                    acc = bias[co]
+                    for kk in range(R.K):
+                        li = 2 * lo + kk - 2
+                        if 0 <= li < L:
+                            for ci in range(cin):
+                                acc += W[co, kk * cin + ci] * h[b][li][ci]
+                    out[b][lo][co] = R.gelu(np.array(acc))
+        h, cin = out, TINY.ch
+    W4, b4 = layers[4]
+    W5, b5 = layers[5]
+    for b in range(2):
+        feat = np.zeros(TINY.flat)
+        for p in range(len(h[b])):
+            for c in range(TINY.ch):
+                feat[p * TINY.ch + c] = h[b][p][c]
+        hid = R.gelu(W4 @ feat + b4)
+        want = W5 @ hid + b5
+        got = R.forward(w, x[b:b + 1], round_bf16=False, spec=TINY)[0]
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_adam_closed_forms():
+    """Kingma & Ba's bias corrections make the first step, and every step of
+    a constant gradient, move each weight by lr * g / (|g| + eps); a zero
+    gradient from zero moments moves nothing."""
+    rng = np.random.Generator(np.random.PCG64(4))
+    w = rng.standard_normal(50)
+    g = rng.standard_normal(50) * np.logspace(-6, 2, 50)
+    lr = 1e-3
+    w1, m1, v1 = R.adam(w, g, np.zeros(50), np.zeros(50), lr, 0)
+    assert np.allclose(w - w1, lr * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
+    wt, mt, vt = w, np.zeros(50), np.zeros(50)
+    for t in range(6):
+        w_prev = wt
+        wt, mt, vt = R.adam(wt, g, mt, vt, lr, t)
+        assert np.allclose(w_prev - wt, lr * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=0), t
+    w0, m0, v0 = R.adam(w, np.zeros(50), np.zeros(50), np.zeros(50), lr, 3)
+    assert np.array_equal(w0, w) and not m0.any() and not v0.any()
+
+
+def test_train_step_with_bfloat16_rounding_tracks_the_exact_step():
+    """The rounded step (operands rounded to bfloat16, 8 significant bits,
+    where the device rounds them) stays within a few bfloat16 units of the
+    exact float64 step, in the norm of the whole gradient, on the tiny
+    network; and the step's loss is the oracle's cross-entropy."""
+    for seed in (5, 6, 7):
+        w, x, lab = _tiny_net(seed)
+        z = np.zeros_like(w)
+        loss, g, _, w1, m1, v1 = R.train_step(w, z, z, x, lab, 1e-3, 0, round_bf16=True, spec=TINY)
+        _, g64, *_ = R.train_step(w, z, z, x, lab, 1e-3, 0, round_bf16=False, spec=TINY)
+        assert np.linalg.norm(g - g64) <= 2 ** -5 * np.linalg.norm(g64)
+        assert loss == R.xent(R.forward(w, x, True, TINY), lab)
+        assert np.allclose((w1, m1, v1), R.adam(w, g, z, z, 1e-3, 0))
+
+
+def test_predict_two_rows_by_hand():
+    """Argmax per head (the first on ties) and confidence = product of the
+    heads' top softmax probabilities, worked out by hand."""
+    z = np.zeros((2, R.LOGITS))
+    z[0, 5] = np.log(3.0)            # capacity head: top 3 / (16 + 3)
+    z[0, 17] = np.log(2.0)           # line-size head: top 2 / (3 + 2)
+    z[0, 21 + 6] = np.log(4.0)       # ways head: top 4 / (6 + 4)
+    #                                  policy head flat: 1 / 3, first index
+    z[1, 2] = z[1, 9] = np.log(4.0)  # tie: index 2 wins, 4 / (15 + 8)
+    z[1, 20] = 1.0                   # last of the line-size head
+    z[1, 21:28] = -5.0               # flat ways head: 1 / 7
+    z[1, 29] = 7.0                   # policy head: e^7 / (2 + e^7)
+    pred, conf = R.predict(z)
+    assert pred.tolist() == [[5, 0, 6, 0], [2, 3, 0, 1]]
+    assert abs(conf[0] - (3 / 19) * (2 / 5) * (4 / 10) * (1 / 3)) < 1e-15
+    e = math.e
+    want1 = (4 / 23) * (e / (3 + e)) * (1 / 7) * (e ** 7 / (2 + e ** 7))
+    assert abs(conf[1] - want1) < 1e-15
+
+
+def test_cross_entropy_head_boundaries():
+    """A dominant logit at index 17, the first of the line-size head, makes
+    only that head's loss vanish: the heads are 17, 4, 7 and 3 logits in
+    that order."""
+    z = np.zeros((1, R.LOGITS))
+    z[0, 17] = 60.0
+    lab = np.zeros((1, 4), dtype=np.int64)
+    want = (math.log(17) + 0.0 + math.log(7) + math.log(3)) / 4
+    assert abs(R.xent(z, lab) - want) < 1e-12
+    g = R.xent_grad(z, lab)
+    assert abs(g[0, 17]) < 1e-20 and abs(g[0, 0] - (1 / 17 - 1) / 4) < 1e-12

@@ -70,10 +70,51 @@ def test_noalloc_matches_workspace_classifier_twice():
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch():
+    """The largest request the scratch holds is accepted and agrees with the
+    workspace form; one latency more per observation is refused before
+    anything is queued.  Both calls get real, consistent device buffers, so a
+    regression of the size check shows up as a wrong return code."""
     L = C.load()
     limit = int(L.pchase_classify_noalloc_limit_bytes())
     assert limit == 8 << 20
-    n_obs, max_len = 64, limit // 16  # 16 bytes per latency per observation: far too much
-    rc = L.pchase_classify_noalloc(1, 1, n_obs, max_len, 1, 1, 1, None)
+    # one observation: 256 B of metadata + 16 B per latency of max_len
+    fit = (limit - 256) // 16
+    assert 256 + 16 * fit == limit
+    lat = _inputs(3, [fit])[0]
+    got = _classify([lat], noalloc=True)
+    want = _classify([lat], noalloc=False)
+    assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[1].view(np.uint32), want[1].view(np.uint32))
+    # one more latency does not fit
+    flat, offs, words, max_len, nwords = _device_layout(_inputs(4, [fit + 1]))
+    bits = torch.zeros(nwords, dtype=torch.int32, device="cuda")
+    thr = torch.zeros(1, dtype=torch.float32, device="cuda")
+    rc = L.pchase_classify_noalloc(flat.data_ptr(), offs.data_ptr(), 1, max_len, bits.data_ptr(),
+                                   words.data_ptr(), thr.data_ptr(), None)
     assert rc == C.ERANGE
     assert b"static scratch" in L.pchase_last_error_string()
+    torch.cuda.synchronize()
+    assert int(bits.abs().sum()) == 0 and float(thr[0]) == 0.0
+
+
+def test_noalloc_refuses_an_observation_longer_than_max_len():
+    """An observation longer than the max_len the caller passed gets a NaN cut
+    and all-0 bits, and writes nothing outside its slice of the shared scratch:
+    the call right after it still agrees with the workspace form."""
+    L = C.load()
+    lats = _inputs(5, [700, 2500])
+    flat, offs, words, _, nwords = _device_layout(lats)
+    bits = torch.full((nwords,), -1, dtype=torch.int32, device="cuda")
+    thr = torch.zeros(2, dtype=torch.float32, device="cuda")
+    C.check(L.pchase_classify_noalloc(flat.data_ptr(), offs.data_ptr(), 2, 1000, bits.data_ptr(),
+                                      words.data_ptr(), thr.data_ptr(), None))
+    torch.cuda.synchronize()
+    b = bits.cpu().numpy()
+    t = thr.cpu().numpy()
+    w1 = int(words[1])
+    assert np.isnan(t[1]) and not b[w1:].any()
+    short = _classify(lats[:1], noalloc=False)
+    assert np.array_equal(b[:w1], short[0]) and t[0] == short[1][0]
+    nxt = _inputs(6, [1000, 64])
+    assert all(np.array_equal(x, y) for x, y in zip(_classify(nxt, noalloc=True),
+                                                   _classify(nxt, noalloc=False)))
