@@ -598,6 +598,33 @@ int pchase_inverse_classify(const pchase_inverse *h, const void *params, void *w
                             uint32_t *fallback_list, uint32_t *n_fallback, float *fb_rows,
                             uint32_t *fb_idx, void *lsq_work, pchase_stream_t stream);
 
+/*
+ * Miss-rate table of a candidates x points plan (the learned inverse's
+ * latency model t = t0 + t_m r, Sec. 4.1, needs r per point): from the
+ * simulator's counts (device, n_geoms x n_points x 2 uint64 as
+ * pchase_sim_run writes them for a pairs == NULL plan, item g * n_points + p)
+ * and the measured accesses per point (device, n_points uint64: length minus
+ * warm-up), rates_out[g * n_points + p] (device float) = misses after warm-up
+ * / measured, divided in double and rounded once; 0 where nothing is
+ * measured.
+ */
+int pchase_miss_rates(const uint64_t *counts, uint32_t n_geoms, uint32_t n_points,
+                      const uint64_t *measured, float *rates_out, pchase_stream_t stream);
+
+/*
+ * Answer classes of candidates under a plan: single-linkage groups of rows
+ * of `rates` (device, n_geoms x n_points float) whose difference is at most
+ * `tol` at every point (compared exactly in double; tol = 0 groups identical
+ * rows).  rep_out[g] (device uint32) is the lowest index in g's group, so a
+ * table sorted canonically names each group by its canonical member.  No
+ * observation of mean latencies separates the members of one group.  Work
+ * buffer (device): pchase_answer_classes_work_bytes(n_geoms), the adjacency
+ * bit matrix.  n_geoms <= 65536 (ERANGE above).
+ */
+size_t pchase_answer_classes_work_bytes(uint32_t n_geoms);
+int pchase_answer_classes(const float *rates, uint32_t n_geoms, uint32_t n_points, double tol,
+                          uint32_t *rep_out, void *work, pchase_stream_t stream);
+
 /* Last host-side failure of the S7 calls on this thread. */
 const char *pchase_inverse_last_error(void);
 

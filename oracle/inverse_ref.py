@@ -151,6 +151,15 @@ def xent(logits: np.ndarray, labels: np.ndarray) -> float:
     return tot / (4 * logits.shape[0])
 
 
+def logit_scale(cache: dict) -> np.ndarray:
+    """Per logit, the sum of the magnitudes of the terms it adds (|h4| . |W5|
+    + |b5|): the scale of its rounding error when the operands agree up to
+    their bfloat16 rounding."""
+    r = _rounder(cache["round"])
+    W5, b5 = cache["layers"][5]
+    return np.abs(cache["h4"]) @ np.abs(r(W5)).T + np.abs(np.asarray(b5, dtype=np.float64))
+
+
 def gelu_grad(x):
     """Derivative of the tanh form of GELU."""
     k0, k1 = 0.7978845608028654, 0.044715

@@ -101,6 +101,10 @@ SIGNATURES = {
     "pchase_inverse_work_bytes": (ctypes.c_size_t, [_c_p]),
     "pchase_inverse_status_offset": (ctypes.c_size_t, [_c_p]),
     "pchase_inverse_activation_offset": (ctypes.c_size_t, [_c_p, _c_u32]),
+    "pchase_miss_rates": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_p, _c_p, _c_p]),
+    "pchase_answer_classes_work_bytes": (ctypes.c_size_t, [_c_u32]),
+    "pchase_answer_classes": (ctypes.c_int, [_c_p, _c_u32, _c_u32, ctypes.c_double, _c_p, _c_p,
+                                             _c_p]),
     "pchase_inverse_param_offset": (ctypes.c_size_t, [_c_p, _c_u32]),
     "pchase_inverse_init": (ctypes.c_int, [_c_p, _c_p, _c_u64, _c_p]),
     "pchase_inverse_synth": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_u64, _c_u64, _c_u32, _c_p,

@@ -41,28 +41,38 @@ def plan_traces():
     """The 512 plan points as simulator trace descriptors (explicit traces on
     the device for the hot re-touch points)."""
     pts = W.p512_plan()
+    traces, keep = _traces_of(pts)
+    return pts, traces, keep
+
+
+def rate_table(cands, tune=None, pts=None):
+    """Miss rate after warm-up of every candidate at every plan point
+    (FP32 [G, points]), by one simulator plan over candidates x points and
+    pchase_miss_rates."""
+    if pts is None:
+        pts, traces, keep = plan_traces()
+    else:
+        traces, keep = _traces_of(pts)
+    plan = SimPlan(cands, traces, tune=tune)
+    _, counts = plan.run(want_bitmaps=False)
+    meas = torch.tensor([r.length - r.warmup for r, _ in pts], dtype=torch.int64, device=DEV)
+    rates = torch.empty(len(cands), len(pts), dtype=torch.float32, device=DEV)
+    _check(C.load().pchase_miss_rates(C.ptr(counts), len(cands), len(pts), C.ptr(meas),
+                                      C.ptr(rates), C.stream_handle()))
+    torch.cuda.synchronize()
+    return rates, counts.view(len(cands), len(pts), 2)
+
+
+def _traces_of(pts):
     traces, keep = [], []
     for run, tr in pts:
         if tr is None:
             traces.append((None, run.length, run.warmup, run.n_elems, run.stride))
         else:
-            t = torch.from_numpy(tr.view(np.int32)).to(DEV)
+            t = torch.from_numpy(np.ascontiguousarray(tr, dtype=np.uint32).view(np.int32)).to(DEV)
             keep.append(t)
             traces.append((t, run.length, run.warmup, run.n_elems, 1))
-    return pts, traces, keep
-
-
-def rate_table(cands, tune=None):
-    """Miss rate after warm-up of every candidate at every plan point
-    (FP32 [G, 512]), by one simulator plan over candidates x points."""
-    pts, traces, keep = plan_traces()
-    plan = SimPlan(cands, traces, tune=tune)
-    _, counts = plan.run(want_bitmaps=False)
-    torch.cuda.synchronize()
-    c = counts.view(-1, 2)[:, 1].view(len(cands), len(pts)).double()
-    meas = torch.tensor([r.length - r.warmup for r, _ in pts], dtype=torch.float64, device=DEV)
-    rates = (c / meas).float().contiguous()
-    return rates, counts.view(len(cands), len(pts), 2)
+    return traces, keep
 
 
 # Two geometries whose miss rates differ by at most this much at every plan
@@ -72,28 +82,19 @@ CLASS_TOLERANCE = 0.01
 
 
 def classes_from_rates(cands, rates: torch.Tensor, tol: float = CLASS_TOLERANCE):
-    """Answer classes of the candidates under the plan: single-linkage groups
-    of rate rows within `tol` of each other at every point (tol = 0: identical
-    rows).  Returns per candidate its class representative (the first member
-    in canonical order), the targets (labels of the representative) and the
-    label -> candidate table."""
-    r = rates.cpu().numpy().astype(np.float64)
+    """Answer classes of the candidates under the plan (pchase_answer_classes:
+    single-linkage groups of rate rows within `tol` of each other at every
+    point; tol = 0: identical rows).  Returns per candidate its class
+    representative (the first member in canonical order), the targets (labels
+    of the representative) and the label -> candidate table."""
+    L = C.load()
     n = len(cands)
-    parent = np.arange(n)
-
-    def find(x):
-        while parent[x] != x:
-            parent[x] = parent[parent[x]]
-            x = parent[x]
-        return x
-
-    for i in range(n):
-        close = np.nonzero(np.abs(r[i + 1:] - r[i]).max(axis=1) <= tol)[0] + i + 1
-        for j in close:
-            a, b = find(i), find(int(j))
-            if a != b:
-                parent[max(a, b)] = min(a, b)  # the lower index (canonical order) leads
-    rep_of = np.array([find(i) for i in range(n)], dtype=np.int64)
+    rep = torch.empty(max(1, n), dtype=torch.int32, device=DEV)
+    work = torch.empty(int(L.pchase_answer_classes_work_bytes(n)) + 256, dtype=torch.uint8,
+                       device=DEV)
+    _check(L.pchase_answer_classes(C.ptr(rates), n, rates.shape[1], float(tol), C.ptr(rep),
+                                   (C.ptr(work) + 255) & ~255, C.stream_handle()))
+    rep_of = rep[:n].cpu().numpy().astype(np.int64)
     targets = np.array([W.geometry_label(cands[rep_of[i]]) for i in range(n)], dtype=np.uint32)
     l2c = np.full(N_LABELS, 0xFFFFFFFF, dtype=np.uint32)
     for i, g in enumerate(cands):

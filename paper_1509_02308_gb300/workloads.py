@@ -105,6 +105,67 @@ def geometry_grid(capacities=CAPACITIES, line_sizes=LINE_SIZES, way_choices=WAY_
     return out
 
 
+# The cache geometries of Table 4 (Secs. 4.3-4.5) beyond the grid, as matcher
+# candidates: the texture L1 caches (12 KB on Fermi/Kepler, 24 KB on Maxwell;
+# 32 B lines, 4 sets, so 96 and 192 ways) under the standard mapping and under
+# the bits 7-8 mapping Sec. 4.3 measured, and the Fermi L1 data cache (16 KB,
+# 128 B, 32 sets, in the grid) under its measured non-LRU policy.
+TABLE4_EXTRA = ((12288, 32, 96, 4), (24576, 32, 192, 4))
+
+
+def table4_candidates(seed_base: int = 0x7AB1E4):
+    out = []
+    for C, b, a, T in TABLE4_EXTRA:
+        for m in (0, 2):
+            for p in (LRU, FIFO, RANDOM):
+                out.append(Geom(C, b, a, T, p, seed_base + len(out), mapping=m))
+    out.append(Geom(16384, 128, 4, 32, WEIGHTED, seed_base + len(out)))
+    return out
+
+
+def matcher_candidates(seed_base: int = 0x5EED):
+    """The exhaustive matcher's candidates: every grid geometry under LRU,
+    FIFO and RANDOM, then the Table 4 geometries outside the grid."""
+    grid = [Geom(C, b, a, T, p, seed_base + i)
+            for i, (C, b, a, T) in enumerate(geometry_grid()) for p in (LRU, FIFO, RANDOM)]
+    return grid + table4_candidates()
+
+
+def capacity_sweep(capacities=None):
+    """Stage 1 of Fig. 6 (Sec. 4.2): s = 1 element over array sizes N equal to
+    each candidate capacity, one warm-up pass and two more; the capacity is
+    the largest N whose passes after the first all hit."""
+    caps = sorted(set(capacities or (list(CAPACITIES) + [g[0] for g in TABLE4_EXTRA])))
+    return caps, [Run(c // 4, 1, 3 * (c // 4), c // 4) for c in caps]
+
+
+def two_stage_plan(C: int, with_retouch: bool = True):
+    """Stage 2 of Fig. 6 (Sec. 4.2) for a cache whose capacity stage 1 found
+    to be C bytes, as (Run, explicit trace or None) pairs:
+      - s = 1 element, N = C + 4j bytes: the misses per pass jump once N
+        passes C + b (the line size);
+      - s = 32 B (the smallest line size), N = C + 32k bytes: each step makes
+        one more set overflow (the number of sets, and the set mapping);
+      - Fig. 10-style hot re-touch chains, streams of 32 B steps over C + 256 B,
+        1.5C and 2C bytes: every set then receives more lines than it has
+        ways, so a hot line touched every other access stays under LRU and
+        is evicted in turn under FIFO (the policy, step 4).
+    Each uniform run is one warm-up pass and two more."""
+    pts = []
+    for j in (1, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65):
+        n = (C + 4 * j) // 4
+        pts.append((Run(n, 1, 3 * n, n), None))
+    for k in (1, 2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 48, 64, 128):
+        n = (C + 32 * k) // 4
+        per = n // math.gcd(n, 8)
+        pts.append((Run(n, 8, 3 * per, per), None))
+    if with_retouch:
+        for nb in (C + 256, 3 * C // 2, 2 * C):
+            tr = hot_retouch_trace(nb, stream_stride=32)
+            pts.append((Run(int(tr.max()) + 1, 1, tr.size, tr.size // 2), tr))
+    return pts
+
+
 # ------------------------------------------------------------------- config 1
 def config1():
     """One LRU cache (16 KB, 128 B lines, 4 ways, 32 sets); arrays of 12 KB to

@@ -234,3 +234,131 @@ def test_batched_inference_equals_one_by_one():
             else:
                 # nothing within the bound: both say so
                 assert dist_b[o][int(pick_b[o, 0])] > stop
+
+
+# ------------------------------------------- every candidate, Table 4 caches
+def _canonical(cands, members):
+    """Canonical member of a set of candidate indices, in the order the C
+    header states: LRU < FIFO < RANDOM (< WEIGHTED), larger b, fewer ways,
+    smaller C, lower index."""
+    return min(members, key=lambda g: (cands[g].policy, -cands[g].b, cands[g].ways, cands[g].C, g))
+
+
+def _plan_tensors(pts):
+    traces, keep = [], []
+    for r, tr in pts:
+        if tr is None:
+            traces.append((None, r.length, r.warmup, r.n_elems, r.stride))
+        else:
+            t = torch.from_numpy(np.ascontiguousarray(tr, dtype=np.uint32).view(np.int32)).cuda()
+            keep.append(t)
+            traces.append((t, r.length, r.warmup, r.n_elems, 1))
+    return traces, keep
+
+
+def _outcome_rows(plan, n_cand, lens):
+    """Per candidate, its miss bits over all plan traces back to back (host
+    uint8), from one simulation of the candidates x traces plan."""
+    bits, _ = plan.run()
+    torch.cuda.synchronize()
+    b = bits.cpu().numpy().view(np.uint32)
+    rows = []
+    k = 0
+    for g in range(n_cand):
+        row = []
+        for n in lens:
+            w0 = int(plan.word_offsets[k])
+            row.append(api.unpack_bits(b[w0:w0 + (n + 31) // 32], n))
+            k += 1
+        rows.append(np.concatenate(row))
+    return rows
+
+
+def test_round_trip_every_matcher_candidate_is_the_truth():
+    """Every candidate of the matcher (the whole grid under LRU, FIFO and
+    RANDOM plus the Table 4 additions: 1321 geometries) is the truth in
+    turn, on the one-geometry configuration's plan (97 stride-128 B arrays
+    around 16 KB plus an s = 4 B sweep), through infer_geometry_batch with
+    distance bound 0.  Noise-free latencies (100 cycles for a hit, 400 for a
+    miss) of the truth's own outcome: the pick is the canonical member of the
+    truth's identical-outcome class on the plan, and the number of
+    candidates at distance 0 is that class's size."""
+    from paper_1509_02308_gb300.api import SimPlan, infer_batch
+    cands = W.matcher_candidates()
+    _, runs = W.config1()
+    C0 = 16384
+    for nb in (C0 - 4, C0, C0 + 4, C0 + 32, C0 + 36, C0 + 64, C0 + 68, C0 + 128, C0 + 132,
+               C0 + 256, C0 + 260):
+        n = nb // 4
+        runs.append(W.Run(n, 1, 3 * n, n))
+    traces = [(None, r.length, r.warmup, r.n_elems, r.stride) for r in runs]
+    lens = [r.length for r in runs]
+    plan = SimPlan(cands, traces)
+    rows = _outcome_rows(plan, len(cands), lens)
+    # a sample of the rows against the oracle (the simulator's own parity tests
+    # cover the rest)
+    for g in list(range(0, len(cands), 97)) + [len(cands) - 1]:
+        G = cands[g]
+        want = np.concatenate([oracle.cache_sim(G.C, G.b, G.ways, G.sets, G.policy,
+                                                oracle.pchase_trace(r.n_elems, r.stride, r.length),
+                                                seed=G.seed, mapping=G.mapping) for r in runs])
+        assert np.array_equal(rows[g], want), g
+    keys = [np.packbits(r).tobytes() for r in rows]
+    classes = {}
+    for g, k in enumerate(keys):
+        classes.setdefault(k, []).append(g)
+    assert len(classes) > 100
+    step = 512  # observations per call: 512 x 108 plan traces < 65536
+    for o0 in range(0, len(cands), step):
+        truths = list(range(o0, min(len(cands), o0 + step)))
+        lat = torch.from_numpy(np.stack([(100.0 + 300.0 * rows[t]).astype(np.float32)
+                                         for t in truths])).cuda()
+        st = api.status_word()
+        dist, pick = infer_batch(plan, lat, stop_above=0, status=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        dist, pick = dist.cpu().numpy(), pick.cpu().numpy()
+        for k, t in enumerate(truths):
+            cls = classes[keys[t]]
+            assert dist[k, t] == 0
+            assert int(pick[k, 0]) == _canonical(cands, cls), (t, int(pick[k, 0]), cls)
+            assert int(pick[k, 1]) == len(cls), (t, int(pick[k, 1]), cls)
+        del lat
+
+
+def test_table4_geometries_recovered_by_the_two_stage_procedure():
+    """Table 4's caches (Secs. 4.3-4.5) recovered on the GPU from their own
+    noise-free outcomes: stage 1 of Fig. 6 (s = 1 element over every
+    candidate capacity, simulated for the truth) finds C; stage 2 runs
+    infer_geometry over every matcher candidate (1321) on the two-stage plan
+    for that C; the truth is the only candidate at distance 0 and the pick.
+    Truths: the 12 KB and 24 KB texture L1 caches (32 B lines, 4 sets,
+    address bits 7-8, LRU) and the Fermi L1 data cache (16 KB, 128 B lines,
+    32 sets, the weighted non-LRU policy)."""
+    from paper_1509_02308_gb300.api import SimPlan
+    cands = W.matcher_candidates()
+    truths = [g for g in W.table4_candidates() if g.policy == W.LRU and g.mapping == 2]
+    truths.append([g for g in W.table4_candidates() if g.policy == W.WEIGHTED][0])
+    caps, sweep = W.capacity_sweep()
+    s_traces = [(None, r.length, r.warmup, r.n_elems, r.stride) for r in sweep]
+    for truth in truths:
+        _, counts, _ = api.cache_sim_batch([truth], s_traces, [(0, i) for i in range(len(sweep))])
+        steady = counts[:, 1].cpu().numpy()
+        C_est = max(c for c, m in zip(caps, steady) if m == 0)
+        assert C_est == truth.C
+        pts = W.two_stage_plan(C_est)
+        traces, keep = _plan_tensors(pts)
+        tb, _, toffs = api.cache_sim_batch([truth], traces, [(0, i) for i in range(len(pts))])
+        tbw = tb.cpu().numpy().view(np.uint32)
+        miss = np.concatenate([api.unpack_bits(tbw[int(toffs[i]):], r.length)
+                               for i, (r, _) in enumerate(pts)])
+        plan = SimPlan(cands, traces)
+        lat = torch.from_numpy((100.0 + 300.0 * miss).astype(np.float32)).cuda()
+        st = api.status_word()
+        dist, pick = plan.infer(lat, status=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        dist = dist.cpu().numpy()
+        ti = cands.index(truth)
+        assert np.nonzero(dist == 0)[0].tolist() == [ti], [cands[i] for i in np.nonzero(dist == 0)[0]]
+        assert int(pick[0]) == ti and int(pick[1]) == 1

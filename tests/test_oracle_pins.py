@@ -1,6 +1,8 @@
 """Pins for the CPU oracle: the paper's worked examples, closed forms,
 special cases and brute force.  None of these calls a GPU."""
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -770,3 +772,79 @@ def test_spectrum_chain_reaches_the_paper_patterns():
     # the L2 TLB tells the C accesses apart: their pages were last used
     # before A's 64 new pages went through it
     assert t2[lab == "C_revisit"].sum() > 0
+
+
+# ------------------------------------------ matcher: every candidate, Table 4
+def _canonical(cands, members):
+    """The canonical member of a set of candidate indices, by the order the
+    C header states: LRU < FIFO < RANDOM (< WEIGHTED), larger b, fewer ways,
+    smaller C, lower index."""
+    return min(members, key=lambda g: (cands[g].policy, -cands[g].b, cands[g].ways, cands[g].C, g))
+
+
+def _sim(g, tr):
+    return oracle.cache_sim(g.C, g.b, g.ways, g.sets, g.policy, tr, seed=g.seed, mapping=g.mapping)
+
+
+def _plan_traces(pts):
+    return [t if t is not None else oracle.pchase_trace(r.n_elems, r.stride, r.length)
+            for r, t in pts]
+
+
+def test_match_round_trip_every_candidate_is_the_truth():
+    """Sec. 4.2's procedure mechanised, noise-free, with the oracle alone:
+    every candidate of a reduced grid (512 B - 1.5 KB, 32 / 64 B lines, 1-8
+    ways or full, LRU / FIFO / RANDOM) is the truth in turn.  The candidates
+    at distance 0 are exactly the truth's identical-outcome class on the plan,
+    and the canonical pick is that class's canonical member."""
+    grid = W.geometry_grid(capacities=(512, 768, 1024, 1536), line_sizes=(32, 64),
+                           way_choices=(1, 2, 4, 8, 0))
+    cands = [W.Geom(C, b, a, T, p, 0x900D + i) for i, (C, b, a, T) in enumerate(grid)
+             for p in (0, 1, 2)]
+    rows = np.array([(g.C, g.b, g.ways, g.sets, g.policy) for g in cands], dtype=np.uint32)
+    seeds = np.array([g.seed for g in cands], dtype=np.uint64)
+    traces = _small_plan(768) + [W.hot_retouch_trace(nb, 64) for nb in (1152, 1536, 3072)]
+    outcome = [[_sim(g, t) for t in traces] for g in cands]
+    keys = [b"".join(np.packbits(o).tobytes() for o in out) for out in outcome]
+    assert len(set(keys)) > len(cands) // 3  # the plan separates most of the grid
+    for ti in range(len(cands)):
+        dist = oracle.match(rows, seeds, traces, outcome[ti])
+        cls = [g for g in range(len(cands)) if keys[g] == keys[ti]]
+        assert sorted(np.nonzero(dist == 0)[0].tolist()) == cls, ti
+        pick, nb = oracle.canonical_pick(rows, dist)
+        assert pick == _canonical(cands, cls) and nb == len(cls), (ti, pick, cls)
+
+
+def test_table4_geometries_recovered_by_the_two_stage_procedure():
+    """Table 4's caches (Secs. 4.3-4.5) are recovered exactly by the oracle
+    from their own noise-free outcomes: stage 1 of Fig. 6 (s = 1 element over
+    the candidate capacities) finds C, stage 2 (two_stage_plan) separates
+    line size, sets, mapping and policy among every candidate of that
+    capacity (grid and Table 4 additions): the truth is the one candidate at
+    distance 0: the 12 KB and 24 KB texture L1 caches (32 B lines, 4 sets, address
+    bits 7-8, LRU) and the Fermi L1 data cache (16 KB, 128 B, 32 sets, the
+    weighted non-LRU policy)."""
+    cands = W.matcher_candidates()
+    truths = [g for g in W.table4_candidates() if g.policy == W.LRU and g.mapping == 2]
+    truths.append([g for g in W.table4_candidates() if g.policy == W.WEIGHTED][0])
+    assert [(g.C, g.b, g.sets) for g in truths] == [(12288, 32, 4), (24576, 32, 4),
+                                                    (16384, 128, 32)]
+    caps, sweep = W.capacity_sweep()
+    for truth in truths:
+        steady = []
+        for r in sweep:
+            m = _sim(truth, oracle.pchase_trace(r.n_elems, r.stride, r.length))
+            steady.append(int(m[r.warmup:].sum()))
+        C_est = max(c for c, s in zip(caps, steady) if s == 0)
+        assert C_est == truth.C
+        pool = [i for i, g in enumerate(cands) if g.C == C_est]
+        traces = _plan_traces(W.two_stage_plan(C_est))
+        obs = [_sim(truth, t) for t in traces]
+
+        def dist(i):
+            return sum(int((_sim(cands[i], t) != o).sum()) for t, o in zip(traces, obs))
+
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+            d = dict(zip(pool, ex.map(dist, pool)))
+        zero = [i for i in pool if d[i] == 0]
+        assert zero == [cands.index(truth)], [cands[i] for i in zero]
