@@ -169,6 +169,11 @@ class ClockSampler:
 # one-warp launch of one run, summed.
 SIM_DRAM_BYTES_PER_ACCESS = (263.807488e6 + 7.867392e6 + 2.604544e6) / 65559830
 SIM_WARP_INST_PER_ACCESS = (442310117 + 9148504) / 65559830
+# Algorithmic work of one simulated access in the warp-per-set mapping: the
+# decode (line, set and tag by shift and multiply-high), one warp-wide tag
+# compare (ballot / match), the replacement-state update and the miss bit,
+# about 4-6 warp instructions; the middle of that range.
+ALG_WARP_INST_PER_ACCESS = 5.0
 
 
 def measured_peaks():
@@ -388,19 +393,32 @@ def ours(args):
     # kernel on this workload with items capped at 64 K accesses (273.2 MB for
     # 65,559,830 accesses), scaled to this launch set by its accesses
     traffic = SIM_DRAM_BYTES_PER_ACCESS * total_acc
-    # issue roofline: warp instructions per access from the same capture
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    issue_peak = sms * 4 * sm_mhz * 1e6 / SIM_WARP_INST_PER_ACCESS  # accesses/s
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "issue": {"warp_inst_per_access": SIM_WARP_INST_PER_ACCESS,
-                      "peak_accesses_per_s": issue_peak,
-                      "frac": total_acc / (sim_avg * 1e-3) / issue_peak,
-                      "note": "SMs x 4 schedulers x median SM clock / measured instructions"},
+    # The simulator is bound by integer / shared-memory instruction issue, not
+    # by HBM or tensor cores: its roofline is the SMs' warp-instruction issue
+    # rate (SMs x 4 schedulers x 1 warp instruction per cycle x the maximum SM
+    # clock) against ALG_WARP_INST_PER_ACCESS algorithmic warp instructions per
+    # access; HBM (trace streaming) is the secondary bound.
+    f_max = peaks.get("sm_max_mhz", 2070.0)
+    issue_peak = sms * 4 * f_max * 1e6 / 1e9  # G warp instructions / s
+    alg_inst = total_acc * ALG_WARP_INST_PER_ACCESS
+    achieved_inst = alg_inst / (sim_avg * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved_inst, "peak": issue_peak,
+            "unit": "G warp-instructions/s", "frac": achieved_inst / issue_peak,
+            "traffic": traffic,
+            "peak_kind": (f"{sms} SMs x 4 warp schedulers x {f_max:.0f} MHz (maximum SM clock, "
+                          f"{peak_kind} peaks file)"),
+            "algorithmic_warp_inst_per_access": ALG_WARP_INST_PER_ACCESS,
+            "algorithmic_warp_inst_per_launch": alg_inst,
+            "measured_warp_inst_per_access": SIM_WARP_INST_PER_ACCESS,
+            "measured_issue_frac": (total_acc * SIM_WARP_INST_PER_ACCESS / (sim_avg * 1e-3) / 1e9
+                                    / issue_peak),
+            "hbm": {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"],
+                    "algorithmic_bytes_per_launch": alg_bytes,
+                    "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                    "nominal_8TBs_frac": achieved / 8000.0},
             "kernel": "sim_kernel (all size classes of one pchase_sim_run)",
-            "kernel_ms": sim_avg, "peak_kind": f"{peak_kind} HBM copy bandwidth",
-            "algorithmic_bytes_per_launch": alg_bytes,
-            "nominal_hbm_frac": achieved / 8000.0}
+            "kernel_ms": sim_avg}
     torch.cuda.synchronize()
 
     result = {
@@ -672,6 +690,99 @@ def probe_bench(dev):
     torch.cuda.empty_cache()
     out["smem_throughput"] = smem_throughput_sweep(dev)
     out["latency_spectrum"] = latency_spectrum(dev)
+    out["pchase_sweep"] = pchase_sweep(dev)
+    out["global_throughput_sweep"] = global_throughput_sweep(dev)
+    return out
+
+
+def pchase_sweep(dev, runs: int = 10, timed: int = 256, max_warm: int = 65536):
+    """The fine-grained P-chase (Listing 3) over every array size N = 4 KB ..
+    512 MB and stride s = 32 B .. 2 MB (powers of two, s <= N / 2) on this GPU,
+    L1 on (ld.global.ca).  Each run starts after a 256 MB write has cleared
+    L2, preheats with one pass over the chain's N / s elements (at most
+    max_warm accesses: beyond that the timed accesses are first touches) and
+    times the next `timed` accesses; a point reports the median over `runs`
+    runs of each run's median latency, in cycles with the clock overhead
+    removed."""
+    import torch
+
+    from paper_1509_02308_gb300 import api
+
+    Ns = [1 << k for k in range(12, 30)]
+    Ss = [1 << k for k in range(5, 22)]
+    table = []
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    for nb in Ns:
+        n = nb // 4
+        row = []
+        for sb in Ss:
+            if sb > nb // 2:
+                row.append(None)
+                continue
+            _, arr = api.pchase_build(n, sb // 4, 1, with_array=True)
+            per = nb // sb
+            meds = []
+            for _ in range(runs):
+                flush.fill_(1)
+                lat, _, _, st = api.pchase_probe_latency(arr, n, iters=timed,
+                                                         warmup=min(per, max_warm), cache_mode=0)
+                torch.cuda.synchronize()
+                if int(st.item()):
+                    return {"error": f"probe status {int(st.item())} at N={nb} s={sb}"}
+                meds.append(float(np.median(lat.cpu().numpy().view(np.uint32))))
+            row.append(float(np.median(meds)))
+            del arr
+        table.append(row)
+    del flush
+    torch.cuda.empty_cache()
+    return {"N_bytes": Ns, "s_bytes": Ss, "median_cycles": table, "runs_per_point": runs,
+            "timed_accesses_per_run": timed, "preheat_accesses_max": max_warm,
+            "cache_mode": "ld.global.ca (L1 and L2)", "wall_s": time.perf_counter() - t0}
+
+
+def global_throughput_sweep(dev, reps: int = 10):
+    """Sec. 5.1's throughput sweep on this GPU: read, write and copy (copy
+    counts 2 x bytes, as the paper does) over buffers of 1 MB .. 4 GB (powers
+    of two) with 4-byte (fp32) and 16-byte (int4) vectors; per point the best,
+    over CTAs per SM {2, 4, 8} x loads in flight per thread {1, 2, 4, 8}, of
+    the median of `reps` timed launches.  Buffers up to the 129 MB L2 are
+    served from it, so only larger ones are against the HBM copy peak."""
+    import torch
+
+    from paper_1509_02308_gb300 import api
+
+    peaks, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sizes = [1 << k for k in range(20, 33)]
+    top = sizes[-1]
+    a = torch.zeros(top, dtype=torch.uint8, device=dev)
+    b = torch.empty(top, dtype=torch.uint8, device=dev)
+    out = {"bytes": sizes, "peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
+           "l2_bytes": 129 * 10 ** 6}
+    t0 = time.perf_counter()
+    for kind, kname in ((0, "read"), (1, "write"), (2, "copy")):
+        for vec, vname in ((4, "fp32"), (16, "int4")):
+            gbs, cfgs = [], []
+            for nb in sizes:
+                best, cfg = 0.0, None
+                for per_sm in (2, 4, 8):
+                    for ilp in (1, 2, 4, 8):
+                        if nb % (vec * ilp):
+                            continue
+                        g = api.pchase_probe_global_throughput(kind, vec, sms * per_sm, 256, ilp,
+                                                               a, b, nb, reps=reps)
+                        if g > best:
+                            best, cfg = g, [per_sm, ilp]
+                gbs.append(best)
+                cfgs.append(cfg)
+            out[f"{kname}_{vname}"] = {
+                "gbs": gbs, "best_ctas_per_sm_ilp": cfgs,
+                "frac_of_measured_above_l2": [g / peaks["hbm_gbs"] if nb > 129 * 10 ** 6 else None
+                                              for g, nb in zip(gbs, sizes)]}
+    out["wall_s"] = time.perf_counter() - t0
+    del a, b
+    torch.cuda.empty_cache()
     return out
 
 

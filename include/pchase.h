@@ -467,6 +467,21 @@ int pchase_probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas,
                                    pchase_stream_t stream);
 
 /*
+ * The three probes above under the short names of the library's call list
+ * (probe_pchase = pchase_probe_latency, probe_smem_bank =
+ * pchase_probe_smem_bank, probe_global_throughput =
+ * pchase_probe_global_throughput): same arguments, limits and behaviour.
+ */
+int probe_pchase(const uint32_t *array, uint32_t n_elems, uint32_t start, uint32_t warmup,
+                 uint32_t iters, int cache_mode, uint32_t *lat_out, uint32_t *idx_out,
+                 uint32_t *overhead_out, uint32_t *dev_status, pchase_stream_t stream);
+int probe_smem_bank(uint32_t max_stride, uint32_t repeats, float *cycles_out,
+                    uint32_t *degree_out, pchase_stream_t stream);
+int probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas, uint32_t threads,
+                            uint32_t ilp, const void *src, void *dst, uint64_t bytes,
+                            uint32_t reps, double *gbs_out, pchase_stream_t stream);
+
+/*
  * Shared-memory throughput probe (Sec. 6.1, Table 6): `ctas` CTAs of
  * `threads` threads (a multiple of 32, <= 1024); every thread copies `ilp`
  * (1, 2, 4, 6 or 8) 4-byte words from one shared region to another, `iters`
@@ -624,6 +639,34 @@ int pchase_miss_rates(const uint64_t *counts, uint32_t n_geoms, uint32_t n_point
 size_t pchase_answer_classes_work_bytes(uint32_t n_geoms);
 int pchase_answer_classes(const float *rates, uint32_t n_geoms, uint32_t n_points, double tol,
                           uint32_t *rep_out, void *work, pchase_stream_t stream);
+
+/*
+ * A learned-inverse model the library owns, for callers that hold only a
+ * weights blob.  inverse_load copies `weights` (HOST memory, exactly
+ * 4 * pchase_inverse_param_count bytes of FP32 weights in the layer order
+ * above, as a checkpoint of pchase_inverse_param_offset(h, 0) holds them)
+ * into device memory it allocates on the current device, with their BF16
+ * copies, a work area and fallback scratch for 4096 traces at a time; it is
+ * synchronous.  inverse_free releases everything (NULL is a no-op).
+ * Errors: EINVAL for a NULL argument or a wrong size, ENOMEM when an
+ * allocation fails.
+ */
+typedef struct pchase_inverse_model pchase_inverse_model;
+int inverse_load(const void *weights, size_t bytes, pchase_inverse_model **handle);
+void inverse_free(pchase_inverse_model *handle);
+
+/*
+ * pchase_inverse_classify on a loaded model, its scratch held by the model:
+ * n traces (device x, n x 512 FP32) in chunks of 4096; cand_out (device, n)
+ * the geometry index of each trace, conf_out (device, n) the network's
+ * confidence, *n_fallback (device uint32) how many traces the least-squares
+ * matcher resolved.  label_to_cand, rates, n_geoms and conf_thresh as in
+ * pchase_inverse_classify.  Calls on one model must not overlap on the GPU.
+ */
+int inverse_classify(const pchase_inverse_model *model, const float *x, uint32_t n,
+                     const uint32_t *label_to_cand, const float *rates, uint32_t n_geoms,
+                     float conf_thresh, uint32_t *cand_out, float *conf_out,
+                     uint32_t *n_fallback, pchase_stream_t stream);
 
 /* Last host-side failure of the S7 calls on this thread. */
 const char *pchase_inverse_last_error(void);

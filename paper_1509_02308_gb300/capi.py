@@ -101,6 +101,16 @@ SIGNATURES = {
     "pchase_inverse_work_bytes": (ctypes.c_size_t, [_c_p]),
     "pchase_inverse_status_offset": (ctypes.c_size_t, [_c_p]),
     "pchase_inverse_activation_offset": (ctypes.c_size_t, [_c_p, _c_u32]),
+    "probe_pchase": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.c_int, _c_p,
+                                    _c_p, _c_p, _c_p, _c_p]),
+    "probe_smem_bank": (ctypes.c_int, [_c_u32, _c_u32, _c_p, _c_p, _c_p]),
+    "probe_global_throughput": (ctypes.c_int, [ctypes.c_int, _c_u32, _c_u32, _c_u32, _c_u32,
+                                               _c_p, _c_p, _c_u64, _c_u32,
+                                               ctypes.POINTER(ctypes.c_double), _c_p]),
+    "inverse_load": (ctypes.c_int, [_c_p, ctypes.c_size_t, _c_p]),
+    "inverse_free": (None, [_c_p]),
+    "inverse_classify": (ctypes.c_int, [_c_p, _c_p, _c_u32, _c_p, _c_p, _c_u32, ctypes.c_float,
+                                        _c_p, _c_p, _c_p, _c_p]),
     "pchase_miss_rates": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_p, _c_p, _c_p]),
     "pchase_answer_classes_work_bytes": (ctypes.c_size_t, [_c_u32]),
     "pchase_answer_classes": (ctypes.c_int, [_c_p, _c_u32, _c_u32, ctypes.c_double, _c_p, _c_p,

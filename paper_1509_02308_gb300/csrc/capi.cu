@@ -1533,3 +1533,28 @@ int pchase_probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ probe_* names
+// The probe calls under the short names of the library's call list; same
+// arguments, same behaviour.
+extern "C" int probe_pchase(const uint32_t *array, uint32_t n_elems, uint32_t start,
+                            uint32_t warmup, uint32_t iters, int cache_mode, uint32_t *lat_out,
+                            uint32_t *idx_out, uint32_t *overhead_out, uint32_t *dev_status,
+                            pchase_stream_t stream) {
+    return pchase_probe_latency(array, n_elems, start, warmup, iters, cache_mode, lat_out,
+                                idx_out, overhead_out, dev_status, stream);
+}
+
+extern "C" int probe_smem_bank(uint32_t max_stride, uint32_t repeats, float *cycles_out,
+                               uint32_t *degree_out, pchase_stream_t stream) {
+    return pchase_probe_smem_bank(max_stride, repeats, cycles_out, degree_out, stream);
+}
+
+extern "C" int probe_global_throughput(int kind, uint32_t vec_bytes, uint32_t ctas,
+                                       uint32_t threads, uint32_t ilp, const void *src, void *dst,
+                                       uint64_t bytes, uint32_t reps, double *gbs_out,
+                                       pchase_stream_t stream) {
+    return pchase_probe_global_throughput(kind, vec_bytes, ctas, threads, ilp, src, dst, bytes,
+                                          reps, gbs_out, stream);
+}
+

@@ -1313,3 +1313,109 @@ int pchase_inverse_classify(const pchase_inverse *h, const void *params, void *w
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------- a library-owned model
+// inverse_load / inverse_free / inverse_classify: the learned inverse with its
+// parameters, work area and fallback scratch in device memory the library
+// allocates at load, for callers that hold only a weights blob.  Traces are
+// classified in chunks of kModelChunk.
+namespace pchase {
+namespace {
+constexpr uint32_t kModelChunk = 4096;
+
+__global__ void add_count_kernel(uint32_t *total, const uint32_t *part) { *total += *part; }
+}  // namespace
+}  // namespace pchase
+
+struct pchase_inverse_model {
+    pchase_inverse *h = nullptr;
+    void *params = nullptr, *work = nullptr, *scratch = nullptr;
+    size_t off_pred = 0, off_fl = 0, off_nf = 0, off_rows = 0, off_idx = 0, off_lsq = 0;
+};
+
+extern "C" {
+
+void inverse_free(pchase_inverse_model *m) {
+    if (!m) return;
+    cudaFree(m->params);
+    cudaFree(m->work);
+    cudaFree(m->scratch);
+    pchase_inverse_destroy(m->h);
+    delete m;
+}
+
+int inverse_load(const void *weights, size_t bytes, pchase_inverse_model **handle) {
+    if (!weights || !handle) return inv_fail(PCHASE_EINVAL, "inverse_load: NULL argument");
+    *handle = nullptr;
+    auto *m = new (std::nothrow) pchase_inverse_model();
+    if (!m) return inv_fail(PCHASE_ENOMEM, "inverse_load: allocation");
+    int rc = pchase_inverse_create(kModelChunk, &m->h);
+    if (rc) {
+        delete m;
+        return rc;
+    }
+    const size_t n = m->h->L.n_params;
+    if (bytes != 4 * n) {
+        inverse_free(m);
+        return inv_fail(PCHASE_EINVAL, "inverse_load: bytes must be 4 x pchase_inverse_param_count");
+    }
+    const size_t B = kModelChunk;
+    size_t o = 0;
+    m->off_pred = o; o = a256(o + 16 * B);
+    m->off_fl = o; o = a256(o + 4 * B);
+    m->off_nf = o; o = a256(o + 4);
+    m->off_rows = o; o = a256(o + 4 * B * kPoints);
+    m->off_idx = o; o = a256(o + 4 * B);
+    m->off_lsq = o; o = a256(o + pchase_lsq_work_bytes((uint32_t)B));
+    cudaError_t e = cudaMalloc(&m->params, m->h->p_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&m->work, m->h->work_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&m->scratch, o);
+    if (e != cudaSuccess) {
+        inverse_free(m);
+        return inv_fail(PCHASE_ENOMEM, "inverse_load: cudaMalloc failed");
+    }
+    // FP32 masters from the blob, their BF16 copies by the library's own
+    // conversion kernel, zero moments; synchronous (the blob is host memory)
+    float *w = at<float>(m->params, m->h->p_w);
+    e = cudaMemcpy(w, weights, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        f2b_kernel<<<grid_for(n), 256>>>(w, n, at<__nv_bfloat16>(m->params, m->h->p_wb));
+        e = cudaMemset(at<float>(m->params, m->h->p_m), 0, 4 * n);
+    }
+    if (e == cudaSuccess) e = cudaMemset(at<float>(m->params, m->h->p_v), 0, 4 * n);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        inverse_free(m);
+        return inv_fail(PCHASE_ECUDA, cudaGetErrorString(e));
+    }
+    *handle = m;
+    return PCHASE_OK;
+}
+
+int inverse_classify(const pchase_inverse_model *m, const float *x, uint32_t n,
+                     const uint32_t *label_to_cand, const float *rates, uint32_t n_geoms,
+                     float conf_thresh, uint32_t *cand_out, float *conf_out, uint32_t *n_fallback,
+                     pchase_stream_t stream) {
+    if (!m || !x || !label_to_cand || !rates || !cand_out || !conf_out || !n_fallback)
+        return inv_fail(PCHASE_EINVAL, "inverse_classify: NULL argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    INV_CUDA(cudaMemsetAsync(n_fallback, 0, 4, st));
+    uint8_t *s = static_cast<uint8_t *>(m->scratch);
+    uint32_t *part = reinterpret_cast<uint32_t *>(s + m->off_nf);
+    for (uint32_t b0 = 0; b0 < n; b0 += kModelChunk) {
+        const uint32_t c = std::min(kModelChunk, n - b0);
+        int rc = pchase_inverse_classify(
+            m->h, m->params, m->work, x + (size_t)b0 * kPoints, c, label_to_cand, rates, n_geoms,
+            conf_thresh, reinterpret_cast<uint32_t *>(s + m->off_pred), conf_out + b0,
+            cand_out + b0, reinterpret_cast<uint32_t *>(s + m->off_fl), part,
+            reinterpret_cast<float *>(s + m->off_rows), reinterpret_cast<uint32_t *>(s + m->off_idx),
+            s + m->off_lsq, stream);
+        if (rc) return rc;
+        add_count_kernel<<<1, 1, 0, st>>>(n_fallback, part);
+    }
+    INV_CUDA(cudaGetLastError());
+    return PCHASE_OK;
+}
+
+}  // extern "C"
+

@@ -288,3 +288,53 @@ def test_miss_rates_from_counts():
     with np.errstate(divide="ignore", invalid="ignore"):
         want = np.where(meas > 0, counts[:, :, 1] / np.maximum(meas, 1), 0.0).astype(np.float32)
     assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_loaded_model_classifies_like_the_caller_owned_one():
+    """inverse_load from a HOST weights blob (a checkpoint of the FP32
+    weights), then inverse_classify, against pchase_inverse_classify on the
+    caller-owned parameters the blob came from: the same candidate for every
+    trace, the same confidences and fallback count, over 5000 traces (two
+    chunks).  A blob of the wrong size is refused; inverse_free(NULL) is a
+    no-op."""
+    import ctypes
+
+    from paper_1509_02308_gb300 import capi as C
+    L = C.load()
+    rng = np.random.Generator(np.random.PCG64(17))
+    G = 40
+    rates = torch.from_numpy(rng.random((G, R.POINTS)).astype(np.float32)).cuda()
+    targets = np.stack([rng.integers(0, k, G) for k in (17, 4, 7, 3)], axis=1).astype(np.int32)
+    # every label names some geometry, so threshold 0 never falls back
+    l2c = (np.arange(17 * 4 * 7 * 3) % G).astype(np.uint32)
+    d_l2c = torch.from_numpy(l2c.view(np.int32)).cuda()
+    net = INV.LearnedInverse(max_batch=4096)
+    net.init(seed=23)
+    x, _, _ = INV.LearnedInverse.synth(rates, torch.from_numpy(targets).cuda(), 5000, seed=3)
+    blob = net.weights().cpu().numpy().copy()
+    h = ctypes.c_void_p()
+    assert L.inverse_load(blob.ctypes.data, blob.nbytes - 4, ctypes.byref(h)) == C.EINVAL
+    C.check(L.inverse_load(blob.ctypes.data, blob.nbytes, ctypes.byref(h)))
+    try:
+        # threshold 0: the network answers wherever its labels name a
+        # geometry; 0.5: the untrained network is never that sure, so every
+        # trace falls back
+        for thr in (0.0, 0.5):
+            want_cand, want_nf = net.classify(x, d_l2c, rates, thr)
+            cand = torch.empty(5000, dtype=torch.int32, device="cuda")
+            conf = torch.empty(5000, dtype=torch.float32, device="cuda")
+            nf = torch.zeros(1, dtype=torch.int32, device="cuda")
+            C.check(L.inverse_classify(h, x.data_ptr(), 5000, d_l2c.data_ptr(), rates.data_ptr(),
+                                       G, thr, cand.data_ptr(), conf.data_ptr(), nf.data_ptr(),
+                                       None))
+            torch.cuda.synchronize()
+            assert np.array_equal(cand.cpu().numpy(), want_cand.cpu().numpy()), thr
+            assert int(nf.item()) == int(want_nf.item())
+            assert int(nf.item()) == (5000 if thr == 0.5 else 0)
+            # the FC + heads kernel adds partial logits atomically, so the
+            # order of those FP32 additions (and the last bits) vary by run
+            _, wconf, _ = net.infer(x)
+            assert np.allclose(conf.cpu().numpy(), wconf.cpu().numpy(), rtol=2.0 ** -14, atol=0)
+    finally:
+        L.inverse_free(h)
+    L.inverse_free(None)

@@ -117,3 +117,46 @@ def test_latency_spectrum_chain_walk():
         assert np.median(l[lab == "D_same_line"]) < np.median(l[lab == "A_32MB"])
     del arr, flush
     torch.cuda.empty_cache()
+
+
+def test_probe_short_names_are_the_same_calls():
+    """probe_pchase, probe_smem_bank and probe_global_throughput (the call
+    list's names) through the C ABI: the same index trace and bank degrees as
+    the pchase_probe_* calls, host results where the call returns one, and
+    the same argument checks."""
+    import ctypes
+
+    from paper_1509_02308_gb300 import capi as C
+    L = C.load()
+    n = 4096
+    _, arr = api.pchase_build(n, 16, 1, with_array=True)
+    outs = []
+    for fn in (L.probe_pchase, L.pchase_probe_latency):
+        lat = torch.zeros(300, dtype=torch.int32, device="cuda")
+        idx = torch.zeros(300, dtype=torch.int32, device="cuda")
+        ovh = torch.zeros(2, dtype=torch.int32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        C.check(fn(arr.data_ptr(), n, 0, 256, 300, 0, lat.data_ptr(), idx.data_ptr(),
+                   ovh.data_ptr(), st.data_ptr(), None))
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0 and (lat.cpu().numpy() >= 0).all()
+        outs.append(idx.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0].view(np.uint32), oracle.pchase_trace(n, 16, 556)[256:])
+    degs = []
+    for fn in (L.probe_smem_bank, L.pchase_probe_smem_bank):
+        cyc = torch.zeros(64, dtype=torch.float32, device="cuda")
+        deg = torch.zeros(64, dtype=torch.int32, device="cuda")
+        C.check(fn(64, 3, cyc.data_ptr(), deg.data_ptr(), None))
+        degs.append(deg.cpu().numpy())
+    assert np.array_equal(degs[0], degs[1])
+    a = torch.zeros(64 << 20, dtype=torch.uint8, device="cuda")
+    b = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    g = ctypes.c_double(0)
+    C.check(L.probe_global_throughput(2, 16, 152 * 4, 256, 4, a.data_ptr(), b.data_ptr(), 64 << 20,
+                                      3, ctypes.byref(g), None))
+    assert g.value > 0
+    assert torch.equal(a, b)  # a copy copies
+    assert L.probe_smem_bank(65, 3, cyc.data_ptr(), deg.data_ptr(), None) == C.EINVAL
+    assert L.probe_pchase(arr.data_ptr(), n, 0, 0, (1 << 24) + 1, 0, lat.data_ptr(),
+                          idx.data_ptr(), ovh.data_ptr(), st.data_ptr(), None) == C.ERANGE
