@@ -468,13 +468,14 @@ def ours(args):
             result["learned_inverse"] = {"error": repr(ex)}
 
     li, inf = result.get("learned_inverse", {}), result.get("inference", {})
-    if "at_99pct" in li and "batched" in inf:
-        # learned + fallback at >= 99 % exact against the exhaustive
-        # simulate-and-compare matcher (S5), whose recovery is exact; the two
-        # read different observations of a cache (a 512-point mean-latency
-        # vector vs per-access latencies of 108 plan traces)
+    if li.get("at_99pct", {}).get("threshold") is not None and "batched" in inf:
+        # against the per-access simulate-and-compare matcher (S5): a
+        # DIFFERENT observation of a cache (per-access latencies of the 108
+        # traces of the one-geometry plan, not a 512-point mean-latency
+        # vector), so context only; the like-for-like comparisons are
+        # speedup_vs_judge and speedup_vs_exhaustive_with_simulation
         a = li["at_99pct"]
-        a["speedup_vs_exhaustive_matcher"] = {
+        a["ratio_to_per_access_matcher_other_observation"] = {
             "single_unbounded": a["traces_per_s"] / inf["traces_inferred_per_s"],
             "batched_bound0": a["traces_per_s"] / inf["batched"]["stop0"]["traces_inferred_per_s"]}
     if rank == 0 and not args.no_cpu:
@@ -1038,29 +1039,42 @@ def learned_bench(args, dev):
     torch.cuda.synchronize()
     t_net = time.perf_counter() - t0
     rep_exact, _, _ = INV.classes_from_rates(cands, rates, tol=0.0)
+    rep_near, _, _ = INV.classes_from_rates(cands, rates, tol=0.01)
+    # the exhaustive path on the same observation, simulation included: the
+    # candidates x plan simulation that yields the rate table, then the
+    # least-squares fit of every observation against every candidate
+    t_exh = t_rates + t_lsq
     res = {"candidates": len(cands), "classes": int(len(set(rep_of.tolist()))),
            "class_tolerance": INV.CLASS_TOLERANCE,
            "classes_identical_rows": int(len(set(rep_exact.tolist()))),
+           "classes_rows_within_0.01": int(len(set(rep_near.tolist()))),
            "plan_points": 512, "rate_table_s": t_rates,
            "train_samples": args.inverse_steps * 4096, "train_s": t_train,
            "train_ms_per_step": t_train / max(1, args.inverse_steps) * 1e3,
            "loss_history": hist, "eval_traces": n,
            "judge_traces_per_s": n / t_lsq,
+           "exhaustive_with_simulation_traces_per_s": n / t_exh,
            "judge_accuracy_vs_truth": float((judge == rep_of[truth]).mean()),
            "judge_accuracy_identical_rows": float(
                (rep_exact[best.cpu().numpy()] == rep_exact[truth]).mean()),
-           "network_only_traces_per_s": n / t_net}
+           "network_only_traces_per_s": n / t_net,
+           "exact_recovery": "identical_rows: the pick's miss-rate row equals the truth's at "
+                             "all 512 points (the plan's identifiability classes)"}
     pick = None
     for thr, (dt, cand, nf) in out.items():
         acc = float((rep_of[cand] == rep_of[truth]).mean())
+        acc_id = float((rep_exact[cand] == rep_exact[truth]).mean())
         res[f"thr{thr}"] = {"traces_per_s": n / dt, "fallback": nf,
                             "agreement_with_judge": float((rep_of[cand] == judge).mean()),
                             "accuracy_vs_truth": acc,
-                            "speedup_vs_judge": (n / dt) / (n / t_lsq)}
-        if acc >= 0.99 and (pick is None or n / dt > res[f"thr{pick}"]["traces_per_s"]):
+                            "accuracy_identical_rows": acc_id,
+                            "speedup_vs_judge": (n / dt) / (n / t_lsq),
+                            "speedup_vs_exhaustive_with_simulation": (n / dt) / (n / t_exh)}
+        if acc_id >= 0.99 and (pick is None or n / dt > res[f"thr{pick}"]["traces_per_s"]):
             pick = thr
-    res["at_99pct"] = ({"threshold": pick, **res[f"thr{pick}"]} if pick is not None
-                       else {"threshold": None, "note": "no threshold reached 99 % accuracy"})
+    res["at_99pct"] = ({"threshold": pick, "definition": "identical_rows", **res[f"thr{pick}"]}
+                       if pick is not None else
+                       {"threshold": None, "note": "no threshold reached 99 % on identical rows"})
     return res
 
 

@@ -76,9 +76,11 @@ def _traces_of(pts):
 
 
 # Two geometries whose miss rates differ by at most this much at every plan
-# point are one answer class: under the timing noise of the synthetic traces
-# (2 % jitter) no matcher separates them.
-CLASS_TOLERANCE = 0.01
+# point are one answer class.  0: identical rows, the plan's identifiability
+# classes (no observation of the plan separates their members).  The plan's
+# hot/stream chains separate LRU from FIFO, so no two distinct rows are within
+# 0.01 of each other everywhere and a wider tolerance would merge nothing.
+CLASS_TOLERANCE = 0.0
 
 
 def classes_from_rates(cands, rates: torch.Tensor, tol: float = CLASS_TOLERANCE):

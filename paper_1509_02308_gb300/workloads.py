@@ -294,13 +294,39 @@ def hot_retouch_trace(n_bytes: int, stream_stride: int = 64, words: int = 8,
     return np.where(k % 2 == 0, hot, st).astype(np.uint32)
 
 
+def hot_stream_trace(span: int, step: int, stream_bytes: int = 1 << 20,
+                     max_len: int = 1 << 15, warm_periods: int = 4):
+    """A non-uniform chain in the style of Fig. 10 that tells LRU from FIFO:
+    every period walks a hot region of span/2 bytes, then the next span/2
+    bytes of a 1 MB stream region that follows it (both in `step`-byte steps,
+    the stream wrapping around).  When the period's lines fit in a set's ways
+    (span <= C at step <= b), LRU keeps the hot lines and misses only the
+    stream, while FIFO evicts each hot line once its set has taken `ways`
+    misses since it came in, so a quarter or so of the hot accesses miss.
+    Returns (element indices, warm-up accesses): warm_periods periods of
+    warm-up, then periods up to max_len measured accesses."""
+    H = max(step, (span // 2) // step * step)
+    hot = np.arange(0, H, step, dtype=np.int64) // 4
+    per = len(hot)
+    n_stream = stream_bytes // step
+    periods = warm_periods + max(1, -(-max_len // (2 * per)))
+    out = []
+    for p in range(periods):
+        k = (p * per + np.arange(per)) % n_stream
+        out.append(hot)
+        out.append((H + k * step) // 4)
+    return np.concatenate(out).astype(np.uint32), warm_periods * 2 * per
+
+
 def p512_plan():
     """The 512-point plan of the learned inverse: list of (Run, explicit
     trace or None).  Points: 176 with s = 4 B and 176 with s = 32 B over array
     sizes log-spaced from 512 B to 512 KB; 61 with s = 128 B over 1-512 KB;
-    35 Saavedra stride sweeps (N = 512 KB and 1 MB, s = 4 B * 2^j); 64 hot
-    re-touch traces over 1-512 KB.  Each uniform point runs one warm-up pass
-    (at most 2^17 accesses) and then at most 2^15 measured accesses."""
+    35 Saavedra stride sweeps (N = 512 KB and 1 MB, s = 4 B * 2^j); 64
+    hot/stream chains (hot_stream_trace) over spans log-spaced from 1 KB to
+    256 KB, 32 in 32-byte steps and 32 in 256-byte steps.  Each uniform point
+    runs one warm-up pass (at most 2^17 accesses) and then at most 2^15
+    measured accesses."""
     pts = []
 
     def uni(nb, sb):
@@ -319,11 +345,10 @@ def p512_plan():
     for nb, jmax in ((512 << 10, 17), (1 << 20, 18)):
         for j in range(jmax):
             uni(nb, 4 << j)
-    for nb in _logspace_bytes(1024, 512 << 10, 64, 64):
-        tr = hot_retouch_trace(nb)
-        n = int(tr.max()) + 1
-        warm = tr.size // 2
-        pts.append((Run(n, 1, tr.size, warm), tr))
+    for step in (32, 256):
+        for span in _logspace_bytes(1024, 256 << 10, 32, step):
+            tr, warm = hot_stream_trace(span, step)
+            pts.append((Run(int(tr.max()) + 1, 1, tr.size, warm), tr))
     assert len(pts) == PLAN_POINTS, len(pts)
     return pts
 
