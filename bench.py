@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--no-probes", action="store_true", help="skip the on-device probe section")
     p.add_argument("--no-hierarchy", action="store_true",
                    help="skip the cache / TLB hierarchy section")
+    p.add_argument("--no-mixed", action="store_true",
+                   help="skip the large mixed batch (65,536 cache and TLB hierarchies)")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the set-mapping / weighted-policy section")
     p.add_argument("--inverse-steps", type=int, default=2442,
@@ -456,6 +458,13 @@ def ours(args):
             result["hierarchy"] = hierarchy_bench(dev)
         except Exception as ex:  # noqa: BLE001
             result["hierarchy"] = {"error": repr(ex)}
+    if not args.no_mixed and rank == 0:
+        try:
+            result["mixed"] = mixed_bench(dev)
+        except Exception as ex:  # noqa: BLE001
+            result["mixed"] = {"error": repr(ex)}
+        import torch as _t
+        _t.cuda.empty_cache()
     if not args.no_variants and rank == 0:
         try:
             result["variants"] = variants_bench(dev)
@@ -985,6 +994,89 @@ def hierarchy_bench(dev, reps: int = 3):
                 "memory": miss[1] / total},
             "translated_by": {"l1_tlb": 1.0 - miss[2] / total, "l2_tlb": (miss[2] - miss[3]) / total,
                               "page_walk": miss[3] / total},
+            "plans": [p.description for p in data.plans + tlb.plans]}
+
+
+def mixed_bench(dev, sample: int = 24):
+    """The large mixed batch (workloads.mixed_config): 65,536 items, each an
+    L1 (16-256 KB) -> L2 (1-128 MB) cache cascade and a 16-entry L1 TLB ->
+    L2 TLB cascade (4 KB, 64 KB or 2 MB pages; over 2 MB pages the unequal
+    L2 TLB of Sec. 4.4), over analytic P-chase streams of 4K-16M accesses
+    (37 G in all).  One warm-up run, then one timed run of all four levels;
+    the L2 caches that no shared-memory arena holds run as way scans over
+    set state in the global-memory pool.  A seeded sample of items (the
+    longest among them) is checked level by level against the oracle's
+    cascade."""
+    import torch
+
+    import oracle
+    from paper_1509_02308_gb300 import api, workloads as W
+
+    l1, l2, t1, t2, runs = W.mixed_config()
+    traces = [(None, r.length, r.warmup, r.n_elems, r.stride) for r in runs]
+    pairs = [(i, i) for i in range(len(runs))]
+    t0 = time.perf_counter()
+    data = api.HierarchyPlan([l1, l2], traces, pairs=pairs)
+    tlb = api.HierarchyPlan([t1, t2], traces, pairs=pairs)
+    t_plan = time.perf_counter() - t0
+    out = data.run() + tlb.run()
+    torch.cuda.synchronize()
+    del out
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev[0].record()
+    o1 = data.plans[0].run()
+    ev[1].record()
+    o2 = data.plans[1].run_filtered(o1[0], data._wo)
+    ev[2].record()
+    o3 = tlb.plans[0].run()
+    ev[3].record()
+    o4 = tlb.plans[1].run_filtered(o3[0], tlb._wo)
+    ev[4].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[4])
+    level_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+    outs = [o1, o2, o3, o4]
+    total = sum(r.length for r in runs)
+    miss = [int(o[1].view(-1, 2)[:, 0].sum().item()) for o in outs]
+    # parity: a seeded sample, half of it among the longest items
+    rng = np.random.Generator(np.random.PCG64(0x5EED15))
+    longest = sorted(range(len(runs)), key=lambda i: -runs[i].length)[:200]
+    idx = sorted(set(rng.choice(len(runs), sample // 2, replace=False).tolist()) |
+                 set(rng.choice(longest, sample // 2, replace=False).tolist()))
+    words = [o[0] for o in outs]
+
+    def want_of(i):
+        r = runs[i]
+        tr = oracle.pchase_trace(r.n_elems, r.stride, r.length)
+        lv = [dict(C=g.C, b=g.b, ways=g.ways, T=g.sets, policy=g.policy, seed=g.seed,
+                   extra=g.extra) for g in (l1[i], l2[i])]
+        lt = [dict(C=g.C, b=g.b, ways=g.ways, T=g.sets, policy=g.policy, seed=g.seed,
+                   extra=g.extra) for g in (t1[i], t2[i])]
+        return oracle.hierarchy(lv, tr) + oracle.hierarchy(lt, tr)
+
+    bad, acc = [], 0
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        for i, want in zip(idx, ex.map(want_of, idx)):
+            r = runs[i]
+            w0, nw = int(data.word_offsets[i]), (r.length + 31) // 32
+            for k in range(4):
+                got = api.unpack_bits(words[k][w0:w0 + nw].cpu().numpy().view(np.uint32),
+                                      r.length)
+                if not np.array_equal(got, want[k]):
+                    bad.append((int(i), k))
+            acc += r.length
+    return {"items": len(runs), "trace_accesses": total, "ms_per_step": ms,
+            "trace_accesses_per_s": total / (ms * 1e-3),
+            "level_accesses_per_s": (2 * total + miss[0] + miss[2]) / (ms * 1e-3),
+            "ms_by_level": dict(zip(("l1", "l2", "l1_tlb", "l2_tlb"), level_ms)),
+            "plan_s": t_plan, "longest_trace": max(r.length for r in runs),
+            "served_from": {"l1": 1.0 - miss[0] / total, "l2": (miss[0] - miss[1]) / total,
+                            "memory": miss[1] / total},
+            "translated_by": {"l1_tlb": 1.0 - miss[2] / total,
+                              "l2_tlb": (miss[2] - miss[3]) / total,
+                              "page_walk": miss[3] / total},
+            "parity_ok": not bad, "parity_items_checked": len(idx),
+            "parity_accesses_checked": acc, "parity_mismatches": bad[:8],
             "plans": [p.description for p in data.plans + tlb.plans]}
 
 

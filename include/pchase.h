@@ -166,6 +166,9 @@ typedef struct {
     uint32_t filtered;           /* 1: the plan is a lower level of a hierarchy; every unit
                                     gathers its accesses, so pchase_sim_run_filtered can skip
                                     the ones a filter bitmap leaves out (default 0) */
+    uint32_t pool_warps;         /* most warps of the global-state pool launch, each owning
+                                    one state region (default and at most 608; rounded up
+                                    to a multiple of 4) */
 } pchase_tune;
 
 typedef struct pchase_sim_plan pchase_sim_plan;
@@ -181,10 +184,15 @@ typedef struct pchase_sim_plan pchase_sim_plan;
  * persistent launch with a per-CTA mix of arenas (S6); units too large for
  * that mix get a second launch on a side stream.  An item whose set state fits
  * no shared-memory arena even split (a cache of many lines, or a line table
- * over a wide stream) runs as one way-scan unit with its state in global
- * memory, inside the plan's workspace (pchase_sim_plan_workspace_bytes counts
- * it).  Errors: EINVAL for a bad geometry, pair or trace; ERANGE for a
- * geometry of more than 2^24 lines, or global set state above 64 GB.
+ * over a wide stream), or whose splits cost more warp time in all, runs as one
+ * way-scan unit with its state in global memory: a third launch of at most
+ * 608 warps, each owning one region of a pool inside the plan's workspace
+ * (at most 16 GB in all; pchase_sim_plan_workspace_bytes counts it) and
+ * reusing it from unit to unit.  Analytic chains (idx == NULL) whose visited
+ * lines are every lstep-th line key a whole unit's state by line / lstep, so
+ * their line tables cover the chain's lines, not the array's.  Errors: EINVAL
+ * for a bad geometry, pair or trace; ERANGE for a geometry of more than 2^24
+ * lines.
  */
 int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom,
                            const pchase_trace *traces, uint32_t n_trace,
@@ -222,8 +230,8 @@ typedef struct {
     uint32_t end_step;
     uint32_t flags;        /* PCHASE_UNIT_* bits */
     uint32_t arena_bytes;  /* shared memory the unit needs */
-    uint64_t state_offset; /* PCHASE_UNIT_GLOBAL_STATE: byte offset of its set state in the */
-    uint64_t state_bytes;  /*   workspace's state area, and its size; else 0, 0 */
+    uint64_t state_offset; /* PCHASE_UNIT_GLOBAL_STATE: offset of its set state in the pool */
+    uint64_t state_bytes;  /*   region of the warp that runs it (0), and its size; else 0, 0 */
 } pchase_unit_info;
 #define PCHASE_UNIT_DIRECT 1u        /* steps over consecutive accesses (no queue) */
 #define PCHASE_UNIT_TIME_PART 2u     /* an LRU item cut in time (rebuilds its start state) */
@@ -234,8 +242,8 @@ typedef struct {
  * Copies the plan's units, in the order the kernels take them, into out
  * (host, up to `cap` entries; out may be NULL with cap 0) and returns how
  * many units the plan has.  Host only: a view of the plan for checks and
- * tools (every bitmap word has one writer; global-memory set state regions
- * are disjoint).
+ * tools (every bitmap word has one writer; a unit's global-memory set state
+ * fits a pool region).
  */
 size_t pchase_sim_plan_units(const pchase_sim_plan *plan, pchase_unit_info *out, size_t cap);
 

@@ -117,6 +117,11 @@ constexpr double kGlobalScanFactor = 2.0;
 constexpr double kRebuildNs = 300.0, kRebuildSkipNs = 60.0;
 constexpr double kBatchRounds = 6.0;   // this many rounds: batch mode whatever T'
 constexpr double kPlanSms = 152.0;     // SMs the automatic split target assumes
+// the global-state pool: warps of its launch (one state region each), their
+// CTA width, and the most memory its regions take together
+constexpr uint64_t kPoolMaxWarps = 608;
+constexpr uint32_t kPoolWarpsPerCta = 4;
+constexpr uint64_t kPoolMaxBytes = 16ull << 30;
 
 // What the planner assumes about an item's access stream, from its trace's
 // stride (exact for uniform chains, a hint for explicit traces).
@@ -129,6 +134,8 @@ struct ItemShape {
     bool cyclic = false;   // each set cycles through its lines in a fixed order every pass
     double cold = 0.0;     // accesses before every line has been touched
     double cost = 0.0;
+    uint32_t lstep = 1;    // analytic chain visiting only the multiples of lstep lines:
+                           // a whole unit keys its state by line / lstep (compact lines)
 };
 
 struct UnitShape {
@@ -233,6 +240,25 @@ void item_shape(const pchase_geom &G, const pchase_trace &Tr, ItemShape &sh) {
         sh.held = false;
     }
     sh.cold = std::min((double)Tr.len, (double)pass);
+    // compact lines: an analytic chain (no index array to hold anything else)
+    // with gcd(N, s) a whole number of lines visits only the lines k * lstep,
+    // lstep = 4 gcd(N, s) / b; a whole unit numbers them k, so its line
+    // table holds the chain's lines, not the array's
+    if (!Tr.idx && se && !map_shift(G) && !extra_ways(G)) {
+        const uint64_t gb = 4 * gcd64(N, se);
+        if (gb % b == 0 && gb / b >= 2 && gb / b <= 0xFFFFFFFFull) sh.lstep = (uint32_t)(gb / b);
+    }
+}
+
+// A whole unit of an item with compact lines keys its state by line / lstep.
+void apply_compact(SimItem &it, const ItemShape &sh) {
+    if (sh.lstep < 2) return;
+    it.lsh |= 1u << 18;
+    it.gsets = sh.lstep;
+    const DivMagic dm = make_div_magic(sh.lstep);
+    it.gmagic = dm.m;
+    it.gs1 = (uint8_t)dm.s1;
+    it.gs2 = (uint8_t)dm.s2;
 }
 
 // Bytes of set state of a whole way-scan unit: {line, stamp} per way slot,
@@ -294,7 +320,8 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     const uint32_t T = G.sets, a = G.ways;
     const uint32_t Tl = T / K;
     const uint64_t lines = (uint64_t)Tl * a;
-    const uint64_t top = top_line(G, it.n_elems);  // largest line id
+    uint64_t top = top_line(G, it.n_elems);  // largest line id
+    if (K == 1 && sh.lstep > 1) top /= sh.lstep;  // compact lines
     const uint64_t table_n = K > 1 ? (uint64_t)Tl * (top / T + 1) : top + 1;
     const double parts = (double)K;
     const double vis = std::max(1.0, sh.visited / parts);
@@ -463,6 +490,9 @@ struct pchase_sim_plan {
     std::vector<SimItem> items;
     SlotLayout layout{};
     SlotLayout jumbo{};   // items too large for the main slot mix (nwarps 0: none)
+    SlotLayout gpool{};   // units with global set state, one pool region per warp
+    uint32_t pool_warps = 0;    // warps (and state regions) of the pool launch
+    uint64_t pool_region = 0;   // bytes of one region
     uint32_t jumbo_first_class = 0;
     uint64_t n_jumbo = 0;
     uint64_t bitmap_words = 0;
@@ -481,19 +511,22 @@ struct pchase_sim_plan {
     double est_sum = 0.0, est_critical = 0.0, est_target = 0.0, est_max_unit = 0.0;
     bool filtered = false;  // every unit queued (pchase_sim_run_filtered)
     // runtime state, set on the first run
-    int device = -1, sms = 0, grid = 0, jgrid = 0;
+    int device = -1, sms = 0, grid = 0, jgrid = 0, ggrid = 0;
     uint64_t n_isolated = 0;  // units given an SM of their own (in the jumbo launch)
     uint64_t n_gmem = 0;        // units with their set state in global memory
     uint64_t gstate_bytes = 0;  // their state area (workspace, after the pooled offsets)
     size_t off_gstate = 0;
     std::vector<uint32_t> class_caps;  // arena cap of each size class present
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
 
     ~pchase_sim_plan() {
         if (side) cudaStreamDestroy(side);
+        if (side2) cudaStreamDestroy(side2);
         if (fork) cudaEventDestroy(fork);
         if (join) cudaEventDestroy(join);
+        if (fork2) cudaEventDestroy(fork2);
+        if (join2) cudaEventDestroy(join2);
     }
 };
 
@@ -531,6 +564,13 @@ int plan_runtime(pchase_sim_plan *p) {
         PCHASE_CUDA(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming), "cudaEventCreate");
         PCHASE_CUDA(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming), "cudaEventCreate");
     }
+    if (p->gpool.nwarps) {
+        // the pool launch has exactly pool_warps warps: one state region each
+        p->ggrid = (int)(p->pool_warps / p->gpool.nwarps);
+        PCHASE_CUDA(cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking), "cudaStreamCreate");
+        PCHASE_CUDA(cudaEventCreateWithFlags(&p->fork2, cudaEventDisableTiming), "cudaEventCreate");
+        PCHASE_CUDA(cudaEventCreateWithFlags(&p->join2, cudaEventDisableTiming), "cudaEventCreate");
+    }
     p->device = dev;
     return PCHASE_OK;
 }
@@ -546,6 +586,14 @@ int plan_launch(pchase_sim_plan *p, void *ws, const SimOut &out, cudaStream_t st
     const SimItem *items = reinterpret_cast<const SimItem *>(w + p->off_items);
     uint32_t *queues = reinterpret_cast<uint32_t *>(w);
     PCHASE_CUDA(launch_sim_zero(items, p->n_units, p->sms, o, st), "output clear");
+    if (p->gpool.nwarps) {
+        // units with global set state first (the longest of a hierarchy's
+        // large levels), on a side stream of their own joined back below
+        PCHASE_CUDA(cudaEventRecord(p->fork2, st), "cudaEventRecord");
+        PCHASE_CUDA(cudaStreamWaitEvent(p->side2, p->fork2, 0), "cudaStreamWaitEvent");
+        PCHASE_CUDA(launch_sim(items, p->gpool, queues, p->ggrid, o, p->side2), "pool launch");
+        PCHASE_CUDA(cudaEventRecord(p->join2, p->side2), "cudaEventRecord");
+    }
     if (p->jumbo.nwarps) {
         // jumbo items first, on a side stream joined back before returning
         PCHASE_CUDA(cudaEventRecord(p->fork, st), "cudaEventRecord");
@@ -556,6 +604,7 @@ int plan_launch(pchase_sim_plan *p, void *ws, const SimOut &out, cudaStream_t st
     if (p->layout.nwarps)
         PCHASE_CUDA(launch_sim(items, p->layout, queues, p->grid, o, st), "simulator launch");
     if (p->jumbo.nwarps) PCHASE_CUDA(cudaStreamWaitEvent(st, p->join, 0), "cudaStreamWaitEvent");
+    if (p->gpool.nwarps) PCHASE_CUDA(cudaStreamWaitEvent(st, p->join2, 0), "cudaStreamWaitEvent");
     return PCHASE_OK;
 }
 
@@ -606,7 +655,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     *plan_out = nullptr;
     if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
         return fail(PCHASE_EINVAL, "NULL descriptor array");
-    pchase_tune tn{4, 220 * 1024, 16, 0, 64, 32, 0, 0};
+    pchase_tune tn{4, 220 * 1024, 16, 0, 64, 32, 0, 0, (uint32_t)kPoolMaxWarps};
     if (tune) {
         if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
@@ -617,6 +666,8 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         if (tune->max_split) tn.max_split = std::min<uint32_t>(tune->max_split, 192);
         tn.split_cost_ns = tune->split_cost_ns;
         tn.filtered = tune->filtered ? 1u : 0u;
+        if (tune->pool_warps)
+            tn.pool_warps = std::min<uint32_t>(tune->pool_warps, (uint32_t)kPoolMaxWarps);
     }
     for (uint32_t i = 0; i < n_geom; ++i) {
         int rc = check_geom(geoms[i], i);
@@ -728,11 +779,15 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                 if (fits) u.cost = uk.cost * K;
                 need = std::min(need, (uint64_t)uk.arena);
             }
-            if (!fits) {
-                // no shared-memory arena holds it, even split: global memory
-                global_unit(G, it, sh, tn, u);
+            // no shared-memory arena holds it, even split, or every split
+            // that does costs more warp time in all (each part re-reads the
+            // whole trace): way scans over set state in global memory
+            UnitShape gu;
+            global_unit(G, it, sh, tn, gu);
+            if (!fits || gu.cost < u.cost) {
+                u = gu;
                 gmem[i] = 1;
-                gshape[i] = u;
+                gshape[i] = gu;
             }
         }
         sh.cost = u.cost;
@@ -842,7 +897,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                               : std::max({total / (kPlanSms * 36.0), 0.6 * critical, 2.0e5});
     p->est_critical = critical;
     p->est_target = target;
-    std::vector<SimItem> items;
+    std::vector<SimItem> items, gitems;
     std::vector<double> cost;
     try {
         items.reserve(n_items);
@@ -851,19 +906,16 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             const pchase_geom &G = geoms[base[i].cand];
             const ItemShape &sh = shape[i];
             if (gmem[i]) {
-                // one whole unit, its set state at 16 * kres bytes of the state area
+                // one whole unit; its set state goes in the pool region of
+                // the warp that runs it (kres 0: at the region's start)
                 SimItem it = base[i];
                 apply_unit(it, gshape[i]);
+                apply_compact(it, sh);
                 it.lsh |= 1u << 17;
-                if ((p->gstate_bytes >> 4) > 0xFFFFFFFFull) {
-                    delete p;
-                    return fail(PCHASE_ERANGE, "set state in global memory above 64 GB");
-                }
-                it.kres = (uint32_t)(p->gstate_bytes >> 4);
-                p->gstate_bytes += scan_state_bytes(G);
+                it.kres = 0;
+                p->pool_region = std::max<uint64_t>(p->pool_region, scan_state_bytes(G));
                 it.cost = (float)gshape[i].cost;
-                items.push_back(it);
-                cost.push_back(gshape[i].cost);
+                gitems.push_back(it);
                 p->est_sum += gshape[i].cost;
                 p->est_max_unit = std::max(p->est_max_unit, gshape[i].cost);
                 p->n_gmem += 1;
@@ -907,6 +959,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                     for (uint32_t j = 0; j < P; ++j) {
                         SimItem it = base[i];
                         apply_unit(it, best);
+                        apply_compact(it, sh);
                         it.ks1 = 1;
                         it.kres = bounds[j];
                         it.kmagic = bounds[j + 1];
@@ -931,6 +984,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                 it.kres = r;
                 it.lead = r == 0;
                 apply_unit(it, best);
+                if (best_k == 1) apply_compact(it, sh);
                 it.cost = (float)best.cost;
                 items.push_back(it);
                 cost.push_back(best.cost);
@@ -942,8 +996,25 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         delete p;
         return fail(PCHASE_ENOMEM, "unit table allocation");
     }
-    const uint64_t n_units = items.size();
-    p->n_units = n_units;
+    const uint64_t n_units = items.size();  // units of the size classes (the pool's apart)
+    p->n_units = n_units + gitems.size();
+    if (!gitems.empty()) {
+        // the pool: one region per warp, at most 608 warps (4 per SM of a
+        // full GPU) and 16 GB in all
+        const uint64_t region = align16(p->pool_region);
+        p->pool_region = region;
+        uint64_t w = std::min<uint64_t>(gitems.size(), tn.pool_warps);
+        w = std::min<uint64_t>(w, std::max<uint64_t>(1, kPoolMaxBytes / region));
+        w = (w + kPoolWarpsPerCta - 1) / kPoolWarpsPerCta * kPoolWarpsPerCta;
+        if (region * w > (64ull << 30) || (region >> 4) > 0xFFFFFFFFull) {
+            delete p;
+            return fail(PCHASE_ERANGE, "set state in global memory above 64 GB");
+        }
+        p->pool_warps = (uint32_t)w;
+        p->gstate_bytes = region * w;
+        std::stable_sort(gitems.begin(), gitems.end(),
+                         [](const SimItem &x, const SimItem &y) { return x.cost > y.cost; });
+    }
 
     // size classes, costliest units first inside each class
     std::vector<int> cls(n_units);
@@ -980,8 +1051,10 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         if (cls[x] != cls[y]) return cls[x] > cls[y];
         return cost[x] > cost[y];
     });
-    p->items.reserve(n_units);
+    p->items.reserve(n_units + gitems.size());
     for (uint64_t k = 0; k < n_units; ++k) p->items.push_back(items[order[k]]);
+    // the pool's units after every size class, costliest first
+    for (const SimItem &it : gitems) p->items.push_back(it);
     // queues: one per size class, smallest class first
     SlotLayout &L = p->layout;
     memset(&L, 0, sizeof L);
@@ -1099,10 +1172,30 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             p->n_jumbo = nj;
         }
     }
+    // pool layout: kPoolWarpsPerCta warps per CTA, each with a queued unit's
+    // staging arena, serving the one class after the size classes
+    {
+        SlotLayout &Gp = p->gpool;
+        memset(&Gp, 0, sizeof Gp);
+        if (!gitems.empty()) {
+            const uint32_t gc = nclass;  // queue counter of the pool's class
+            Gp.nclasses = gc + 1;
+            Gp.pad = gc;
+            Gp.cls_first[gc] = (uint32_t)n_units;
+            Gp.cls_count[gc] = (uint32_t)gitems.size();
+            Gp.nwarps = kPoolWarpsPerCta;
+            for (uint32_t w = 0; w < kPoolWarpsPerCta; ++w) {
+                Gp.warp_class[w] = gc;
+                Gp.warp_off[w] = w * kStageBytes;
+            }
+            Gp.smem_bytes = kPoolWarpsPerCta * kStageBytes;
+            Gp.pool16 = (uint32_t)(p->pool_region >> 4);
+        }
+    }
     // workspace: [queues + status: 256][items][geoms][seg offsets][obs word offsets][pool]
     size_t off = 256;
     p->off_items = off;
-    off = align256(off + n_units * sizeof(SimItem));
+    off = align256(off + p->n_units * sizeof(SimItem));  // size classes and pool
     p->off_geoms = off;
     off = align256(off + (size_t)n_geom * sizeof(pchase_geom));
     p->off_seg = off;
@@ -1131,7 +1224,7 @@ uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
     if (!plan) return 0;
     // output clear + main slot-mix launch + side launch of jumbo units
     return (plan->n_units ? 1u : 0u) + (plan->layout.nwarps ? 1u : 0u) +
-           (plan->jumbo.nwarps ? 1u : 0u);
+           (plan->jumbo.nwarps ? 1u : 0u) + (plan->gpool.nwarps ? 1u : 0u);
 }
 
 size_t pchase_sim_plan_units(const pchase_sim_plan *plan, pchase_unit_info *out, size_t cap) {
@@ -1155,7 +1248,8 @@ size_t pchase_sim_plan_units(const pchase_sim_plan *plan, pchase_unit_info *out,
                   (it.lead ? PCHASE_UNIT_LEAD : 0u);
         u.arena_bytes = it.arena_bytes;
         if (gm) {
-            u.state_offset = 16ull * it.kres;
+            // in the pool region of the warp that runs it, from its start
+            u.state_offset = 0;
             u.state_bytes = scan_state_bytes(plan->geoms[it.cand]);
         }
     }
@@ -1213,6 +1307,12 @@ size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t b
         snprintf(tmp, sizeof tmp, " est_ms=%.2f,%.2f,%.2f,%.1f", plan->est_critical * 1e-6,
                  plan->est_target * 1e-6, plan->est_max_unit * 1e-6, plan->est_sum * 1e-6);
         d += tmp;
+        if (plan->gpool.nwarps) {
+            // the global-state pool: warps (one region each) x region bytes
+            snprintf(tmp, sizeof tmp, " pool=%ux%llu", plan->pool_warps,
+                     (unsigned long long)plan->pool_region);
+            d += tmp;
+        }
     }
     if (buf && bytes) {
         const size_t n = d.size() < bytes - 1 ? d.size() : bytes - 1;

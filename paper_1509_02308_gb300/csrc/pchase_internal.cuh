@@ -101,7 +101,11 @@ struct SimItem {
     uint32_t lsh;         // line = index >> (lsh & 255) (b = 4 << that); bits 8-15: mapping m;
                           // bit 16: unequal sets (gsets/gmagic: M = T*a + extra, kmagic: a,
                           // ways: a + extra, the ways of set 0); bit 17: way scans with the
-                          // set state in global memory at 16 * kres bytes (whole units)
+                          // set state in global memory at 16 * kres bytes (whole units);
+                          // bit 18: compact lines (whole units of analytic chains whose
+                          // visited lines are the multiples of gsets: the unit keys its
+                          // state by line / gsets, gmagic/gs1/gs2 its DivMagic, and takes
+                          // the set from the line itself)
     uint32_t table_n;     // line-table entries (local lines)
     uint64_t seed;
     uint64_t word_off;    // plan-owned bitmap layout
@@ -143,13 +147,16 @@ constexpr uint32_t kStageBytes = kQueueBytes + kRing * 32 * 4 + kRing * 4;
 // slot can hold (pad .. warp_class[w]), the next unit of the class whose next
 // unit has the highest estimated cost (each class queue is costliest first).
 constexpr int kMaxWarpsPerCta = 16;
-constexpr int kMaxClasses = 24;
+constexpr int kMaxClasses = 25;  // size classes + the global-state pool's
 struct SlotLayout {
     uint32_t nwarps;                          // warps per CTA
     uint32_t nclasses;
     uint32_t smem_bytes;                      // dynamic shared memory per CTA
     uint32_t pad;                             // lowest class a warp may take
     uint32_t stagger_ns;                      // first pop of warp w waits w * this
+    uint32_t pool16;                          // global-state pool: warp g = CTA * nwarps + w
+                                              // keeps its units' state at g * 16 * pool16
+                                              // bytes of the state area (0: no pool)
     uint32_t warp_class[kMaxWarpsPerCta];     // class served first by warp w
     uint32_t warp_off[kMaxWarpsPerCta];       // byte offset of warp w's arena
     uint32_t cls_first[kMaxClasses];          // first item of class c (sorted table)

@@ -608,6 +608,7 @@ struct BatchLRU {
         sets_s1 = it.s1;
         sets_s2 = it.s2;
         nsets = it.sets;
+        lstep = ((it.lsh >> 18) & 1u) ? it.gsets : 1u;  // compact lines: id * lstep is the line
         size_t off = 0;
         perm = reinterpret_cast<uint32_t *>(arena);
         off += 256;
@@ -770,9 +771,11 @@ struct BatchLRU {
         }
         __syncwarp();
     }
-    uint32_t sets_m, sets_s1, sets_s2, nsets;
+    uint32_t sets_m, sets_s1, sets_s2, nsets, lstep;
+    // set of a line as the unit keys it (a compact id stands for id * lstep)
     __device__ __forceinline__ uint32_t set_of(uint32_t ln) const {
-        return ln - div_q(ln, sets_m, sets_s1, sets_s2) * nsets;
+        const uint32_t l = ln * lstep;
+        return l - div_q(l, sets_m, sets_s1, sets_s2) * nsets;
     }
 
     // All set groups at once.  A group of g heads can push out at most g
@@ -1187,6 +1190,10 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     // below T * a (a: it.kmagic), else to set 0
     const bool uneq = (it.lsh >> 16) & 1u;
     const uint32_t uta = uneq ? it.sets * it.kmagic : 0u;
+    // compact lines: a strided chain visits only the multiples of lstep, so
+    // the unit keys its state by line / lstep (dense ids, small line tables)
+    const bool lcomp = (it.lsh >> 18) & 1u;
+    const uint32_t lstep = lcomp ? it.gsets : 1u;
     const uint32_t sets = it.sets, mm = it.magic_m, s1 = it.s1, s2 = it.s2;
     const bool split = it.kcnt > 1;
     const uint32_t gT = it.gsets, gm = it.gmagic, gs1 = it.gs1, gs2 = it.gs2;
@@ -1237,6 +1244,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             };
             auto line_of = [&](uint32_t j) -> uint32_t {
                 const uint32_t ln = j >> lsh;
+                if (lcomp) return div_q(ln, gm, gs1, gs2);
                 return mk ? remap_line(ln, mk, gT, gm, gs1, gs2) : ln;
             };
             BatchLRU S;
@@ -1272,6 +1280,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             uint32_t ln = j >> lsh;
             if (mk) ln = remap_line(ln, mk, gT, gm, gs1, gs2);
             const uint32_t set = set_of(ln);
+            if (lcomp) ln = div_q(ln, gm, gs1, gs2);
             const uint32_t rot = __shfl_sync(kFull, ln, (lane + 31) & 31);
             const uint32_t prev = lane == 0 ? carry : rot;
             carry = rot;
@@ -1356,7 +1365,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
                 const uint32_t prevl = lane == 0 ? ocarry : rot;
                 ocarry = rot;
                 bool mine = valid;
-                uint32_t lp = ln;
+                uint32_t lp = lcomp ? div_q(ln, gm, gs1, gs2) : ln;
                 if (split) {
                     const uint32_t q = div_q(ln, gm, gs1, gs2);
                     const uint32_t set = ln - q * gT;
@@ -1396,7 +1405,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             __syncwarp();
             const uint32_t line = e.x;
             const uint32_t pos = e.y & 0x7FFFFFFFu;
-            const uint32_t set = set_of(line);
+            const uint32_t set = set_of(line * lstep);
             const uint32_t rot = __shfl_sync(kFull, line, (lane + 31) & 31);
             const uint32_t prev = lane == 0 ? ccarry : rot;
             ccarry = rot;
@@ -1496,6 +1505,9 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
             const uint32_t u = k / nrep, rep = k - u * nrep;
             const SimItem it = items[L.cls_first[c] + u];
             SimOut o = out;
+            if (L.pool16)  // global set state: this warp's region of the pool
+                o.gstate = out.gstate + ((uint64_t)blockIdx.x * L.nwarps + (uint32_t)warp) *
+                                            ((uint64_t)L.pool16 << 4);
             if (rep) {
                 o.dist += rep * out.rep_dist_stride;
                 o.observed += rep * out.rep_obs_stride;

@@ -404,6 +404,47 @@ def hierarchy_config(n_items: int = 1024, seed_base: int = 0x5EED0005):
     return l1, l2, t1, t2, runs
 
 
+def mixed_config(n_items: int = 65536, seed_base: int = 0x5EED0015):
+    """The large mixed batch: two-level cache and two-level TLB hierarchies
+    over P-chase streams of uneven length.  Item i draws from stream
+    seed_base + i:
+      L1: C 16-256 KB (powers of two), b 32/64/128 B, 4/8/16 ways, a policy;
+      L2: C 1-128 MB (powers of two), b 64/128 B, 8/16/32 ways, a policy;
+      TLBs (Sec. 4.4): a 16-entry fully associative L1 TLB and an 8-way L2 TLB
+      of 8-64 sets, both LRU, over 4 KB or 64 KB pages; over 2 MB pages the
+      L2 TLB the paper measures (Fig. 9): one set of 17 entries and six of 8;
+      stream: s = 4 * 2^u B (u in 0..10), N = round_down(C_L2 * 2^v, s),
+      v in [-1, 1), warm-up one pass;
+      length 4096 * 4096^(x^4) accesses (x in [0, 1)): 4K to 16M, most short,
+      a long tail (about 0.57M on average).
+    Returns (l1, l2, tlb1, tlb2, runs), item i pairing entry i of each."""
+    l1, l2, t1, t2, runs = [], [], [], [], []
+    for i in range(n_items):
+        r = SplitMix64(seed_base + i)
+        a1 = 4 << r.below(3)
+        b1 = 32 << r.below(3)
+        C1 = (16 << 10) << r.below(5)
+        l1.append(Geom(C1, b1, a1, C1 // (a1 * b1), r.below(3), r.next()))
+        C2 = (1 << 20) << r.below(8)
+        b2 = 64 << r.below(2)
+        a2 = 8 << r.below(3)
+        l2.append(Geom(C2, b2, a2, C2 // (a2 * b2), r.below(3), r.next()))
+        page = (4096, 65536, 2 << 20)[r.below(3)]
+        sets2 = 8 << r.below(4)
+        t1.append(Geom(16 * page, page, 16, 1, LRU))
+        if page == 2 << 20:
+            t2.append(Geom(65 * page, page, 8, 7, LRU, extra=9))
+        else:
+            t2.append(Geom(sets2 * 8 * page, page, 8, sets2, LRU))
+        s_elems = 1 << r.below(11)
+        v = r.unit() * 2.0 - 1.0
+        n = max(s_elems, int(C2 * 2.0 ** v) // 4 // s_elems * s_elems)
+        L = int(4096 * 4096.0 ** (r.unit() ** 4))
+        per = n // math.gcd(n, s_elems)
+        runs.append(Run(n, s_elems, L, min(per, L)))
+    return l1, l2, t1, t2, runs
+
+
 # --------------------------------------------------------- latency spectrum
 def spectrum_chain():
     """The non-uniform-stride chain of Sec. 5.2 (Fig. 10(b)), as element

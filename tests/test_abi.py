@@ -269,15 +269,18 @@ def test_unequal_sets_checks():
 def _units_hold_invariants(h, lens):
     """Every item: one lead unit; its units are one whole unit, K set-parts
     with each residue once, or time parts tiling its steps in whole
-    1024-access blocks (so each bitmap word has one writer); global-memory
-    set state regions are disjoint and inside the workspace."""
+    1024-access blocks (so each bitmap word has one writer); a unit with
+    global-memory set state fits one region of the plan's pool, and the
+    pool (warps x region bytes) fits the workspace."""
     L = C.load()
     units = C.plan_units(h)
     by_item = {}
     for u in units:
         by_item.setdefault(u.item, []).append(u)
     assert sorted(by_item) == list(range(len(lens)))
-    regions = []
+    pool = _describe(h).get("pool")
+    region = int(pool.split("x")[1]) if pool else 0
+    pool_bytes = int(pool.split("x")[0]) * region if pool else 0
     for item, us in by_item.items():
         nsteps = (lens[item] + 31) // 32
         assert sum(1 for u in us if u.flags & C.UNIT_LEAD) == 1, item
@@ -298,15 +301,17 @@ def _units_hold_invariants(h, lens):
         for u in us:
             if u.flags & C.UNIT_GLOBAL_STATE:
                 assert u.parts == 1 and u.mode == 0 and u.state_bytes > 0
-                assert u.state_offset % 16 == 0
-                regions.append((u.state_offset, u.state_offset + u.state_bytes))
+                assert u.state_offset == 0 and u.state_bytes <= region and region % 16 == 0
             else:
                 assert u.state_bytes == 0
-    regions.sort()
-    for (a0, a1), (b0, b1) in zip(regions, regions[1:]):
-        assert a1 <= b0
-    if regions:
-        assert regions[-1][1] <= L.pchase_sim_plan_workspace_bytes(h)
+    # the workspace holds the queues, the whole unit table (112 bytes a unit,
+    # the pool's units included) and the pool
+    assert L.pchase_sim_plan_workspace_bytes(h) >= 256 + 112 * len(units) + pool_bytes
+    if pool_bytes:
+        assert pool_bytes <= min(L.pchase_sim_plan_workspace_bytes(h), 16 << 30)
+        # the pool's units run last in the unit table, after every size class
+        gm = [k for k, u in enumerate(units) if u.flags & C.UNIT_GLOBAL_STATE]
+        assert gm == list(range(len(units) - len(gm), len(units)))
     return units
 
 

@@ -109,3 +109,76 @@ def test_batched_inference_refuses_global_state():
     lats = torch.zeros(2, 1000, dtype=torch.float32, device="cuda")
     with pytest.raises(Exception):
         api.infer_batch(plan, lats)
+
+
+def test_pool_regions_are_reused_from_unit_to_unit():
+    """Global-state units of 24 large caches (1 Mi and 256 Ki lines, every
+    policy) through a pool of only 4 warps, so each warp's region holds one
+    unit's state after another (larger and smaller caches in turn): every
+    bitmap and count against the oracle."""
+    geoms = [W.Geom(128 * MB, 128, 16, 65536, W.LRU), W.Geom(8 * MB, 32, 16, 16384, W.FIFO),
+             W.Geom(8 * MB, 32, 16, 16384, W.RANDOM, 11), W.Geom(6 * MB, 64, 12, 8192, W.WEIGHTED, 3),
+             W.Geom(64 * MB, 64, 8, 131072, W.FIFO), W.Geom(32 * MB, 128, 32, 8192, W.RANDOM, 5)]
+    host, descs, pairs = [], [], []
+    for k in range(24):
+        gi = k % len(geoms)
+        g = geoms[gi]
+        if k % 3 == 2:
+            t = W.random_index_trace(6000 + 97 * k, g.C // 4 * 2, seed=300 + k, hot=5)
+            host.append(t)
+            descs.append((torch.from_numpy(t.view(np.int32)).cuda(), t.size, 0, int(t.max()) + 1, 1))
+        else:
+            s = g.b // 4 * (1 + k % 2)
+            n = int(g.C * (0.6 + 0.15 * (k % 5))) // 4 // s * s
+            L = 5000 + 131 * k
+            host.append(oracle.pchase_trace(n, s, L))
+            descs.append((None, L, min(L, n // s), n, s))
+        pairs.append((gi, k))
+    plan = api.SimPlan(geoms, descs, pairs=pairs, tune={"max_split": 1, "pool_warps": 4})
+    d = dict(kv.split("=", 1) for kv in plan.description.split())
+    assert int(d["global_state"]) == 24 and d["pool"].startswith("4x"), plan.description
+    for _ in range(2):  # a second run reuses the regions the first one left dirty
+        bitmaps, counts = plan.run()
+        torch.cuda.synchronize()
+        b = bitmaps.cpu().numpy().view(np.uint32)
+        c = counts.view(-1, 2).cpu().numpy()
+        for i, (gi, ti) in enumerate(pairs):
+            want = _sim(geoms[gi], host[ti])
+            got = api.unpack_bits(b[int(plan.word_offsets[i]):], host[ti].size)
+            assert np.array_equal(got, want), (i, geoms[gi], int(np.argmax(got != want)))
+            assert c[i, 0] == want.sum() and c[i, 1] == want[descs[ti][2]:].sum()
+
+
+def test_compact_lines_of_strided_analytic_chains():
+    """Analytic chains whose stride is a whole number of lines over arrays far
+    larger than any line table (tens of MB) visit only every lstep-th line;
+    whole units key their state by line / lstep, so line-table and batch set
+    modes fit where before only way scans did.  Single-set and few-set
+    streams under LRU (also cut in time), FIFO and RANDOM, every bitmap
+    against the oracle."""
+    geoms = [W.Geom(16 << 10, 32, 16, 32, W.LRU), W.Geom(16 << 10, 32, 16, 32, W.FIFO),
+             W.Geom(16 << 10, 128, 16, 8, W.RANDOM, 9), W.Geom(64 << 10, 64, 8, 128, W.LRU),
+             W.Geom(32 << 10, 32, 4, 256, W.FIFO)]
+    streams = [(14 * MB, 4096), (57 * MB, 256), (24 * MB, 2048), (9 * MB, 1024)]
+    host, descs = [], []
+    for nb, sb in streams:
+        n, s = nb // 4, sb // 4
+        L = 150000
+        host.append(oracle.pchase_trace(n, s, L))
+        descs.append((None, L, min(L, n // s), n, s))
+    pairs = [(g, t) for g in range(len(geoms)) for t in range(len(streams))]
+    for tune in (None, {"split_cost_ns": 1, "max_split": 8}):
+        plan = api.SimPlan(geoms, descs, pairs=pairs, tune=tune)
+        d = dict(kv.split("=", 1) for kv in plan.description.split())
+        assert int(d["table"]) + int(d["batch"]) > 0, plan.description
+        if tune:
+            assert int(d["time_split"]) > 0, plan.description
+        bitmaps, counts = plan.run()
+        torch.cuda.synchronize()
+        b = bitmaps.cpu().numpy().view(np.uint32)
+        c = counts.view(-1, 2).cpu().numpy()
+        for i, (gi, ti) in enumerate(pairs):
+            want = _sim(geoms[gi], host[ti])
+            got = api.unpack_bits(b[int(plan.word_offsets[i]):], host[ti].size)
+            assert np.array_equal(got, want), (tune, i, geoms[gi], int(np.argmax(got != want)))
+            assert c[i, 0] == want.sum() and c[i, 1] == want[descs[ti][2]:].sum()
