@@ -338,3 +338,37 @@ def test_loaded_model_classifies_like_the_caller_owned_one():
     finally:
         L.inverse_free(h)
     L.inverse_free(None)
+
+
+def test_classify_captured_in_a_cuda_graph_equals_eager():
+    """The learned classification with its fallback (network chunks, routing,
+    least-squares matcher over the low-confidence traces) captured in one
+    CUDA graph and replayed twice gives the eager call's answers."""
+    rng = np.random.Generator(np.random.PCG64(19))
+    G = 30
+    rates = torch.from_numpy(rng.random((G, R.POINTS)).astype(np.float32)).cuda()
+    l2c = torch.from_numpy((np.arange(17 * 4 * 7 * 3) % G).astype(np.int32)).cuda()
+    net = INV.LearnedInverse(max_batch=1024)
+    net.init(seed=29)
+    targets = torch.from_numpy(rng.integers(0, 3, (G, 4)).astype(np.int32)).cuda()
+    x, _, _ = INV.LearnedInverse.synth(rates, targets, 5000, seed=8)
+    # a threshold in the widest gap between middle confidences, so that the
+    # last bits of the confidences (their FC + heads sums are added
+    # atomically) cannot move a trace across it
+    _, conf, _ = net.infer(x)
+    c = np.sort(conf.cpu().numpy().astype(np.float64))
+    k = 1250 + int(np.argmax(np.diff(c[1250:3751])))
+    thr = float((c[k] + c[k + 1]) / 2)
+    want, wnf = net.classify(x, l2c, rates, thr)
+    want, wnf = want.cpu().numpy(), int(wnf.item())
+    assert 1000 < wnf < 4000
+    net.classify(x[:64], l2c, rates, thr)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cand, nf = net.classify(x, l2c, rates, thr)
+    for _ in range(2):
+        cand.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(cand.cpu().numpy(), want) and int(nf.item()) == wnf
