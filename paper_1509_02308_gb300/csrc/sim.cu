@@ -1100,17 +1100,25 @@ enum : uint32_t {
 // only copy of every mode's code: all modes share one unit loop, which keeps
 // the simulator's hot code within the instruction cache while warps of many
 // different units share an SM.
+// POOL: the kernel of the global-state pool, whose units all keep their set
+// state in global memory (way scans); the other kernel has no such unit, so
+// neither instantiation carries the other's resolvers.
+template <bool POOL>
 __device__ __forceinline__ bool resolve_step(uint32_t kind, uint8_t *st, uint8_t *gst,
                                              const SimItem &it, uint32_t line, uint32_t set,
                                              bool head, uint32_t pos, int lane, uint32_t lt,
                                              uint32_t step) {
+    if constexpr (POOL) {
+        switch (kind) {
+        case kGlobalScanLru: { RoundResolver<ScanSets<PCHASE_LRU>> R; R.S.bind(gst, it);
+                               return R.resolve(line, set, head, pos, lane, lt, step); }
+        case kGlobalScanFifo: { RoundResolver<ScanSets<PCHASE_FIFO>> R; R.S.bind(gst, it);
+                                return R.resolve(line, set, head, pos, lane, lt, step); }
+        default: { RoundResolver<ScanSets<PCHASE_RANDOM>> R; R.S.bind(gst, it);
+                   return R.resolve(line, set, head, pos, lane, lt, step); }
+        }
+    }
     switch (kind) {
-    case kGlobalScanLru: { RoundResolver<ScanSets<PCHASE_LRU>> R; R.S.bind(gst, it);
-                           return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kGlobalScanFifo: { RoundResolver<ScanSets<PCHASE_FIFO>> R; R.S.bind(gst, it);
-                            return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kGlobalScanRandom: { RoundResolver<ScanSets<PCHASE_RANDOM>> R; R.S.bind(gst, it);
-                              return R.resolve(line, set, head, pos, lane, lt, step); }
     case kScanLru: { RoundResolver<ScanSets<PCHASE_LRU>> R; R.S.bind(st, it);
                      return R.resolve(line, set, head, pos, lane, lt, step); }
     case kScanFifo: { RoundResolver<ScanSets<PCHASE_FIFO>> R; R.S.bind(st, it);
@@ -1132,13 +1140,18 @@ __device__ __forceinline__ bool resolve_step(uint32_t kind, uint8_t *st, uint8_t
     }
 }
 
+template <bool POOL>
 __device__ __forceinline__ void clear_state(uint32_t kind, uint8_t *st, uint8_t *gst,
                                             const SimItem &it, int lane) {
+    if constexpr (POOL) {
+        switch (kind) {
+        case kGlobalScanLru: { ScanSets<PCHASE_LRU> S; S.bind(gst, it); S.clear(it, lane); return; }
+        case kGlobalScanFifo: {
+            ScanSets<PCHASE_FIFO> S; S.bind(gst, it); S.clear(it, lane); return; }
+        default: { ScanSets<PCHASE_RANDOM> S; S.bind(gst, it); S.clear(it, lane); return; }
+        }
+    }
     switch (kind) {
-    case kGlobalScanLru: { ScanSets<PCHASE_LRU> S; S.bind(gst, it); S.clear(it, lane); break; }
-    case kGlobalScanFifo: { ScanSets<PCHASE_FIFO> S; S.bind(gst, it); S.clear(it, lane); break; }
-    case kGlobalScanRandom: {
-        ScanSets<PCHASE_RANDOM> S; S.bind(gst, it); S.clear(it, lane); break; }
     case kScanLru: { ScanSets<PCHASE_LRU> S; S.bind(st, it); S.clear(it, lane); break; }
     case kScanFifo: { ScanSets<PCHASE_FIFO> S; S.bind(st, it); S.clear(it, lane); break; }
     case kScanRandom: { ScanSets<PCHASE_RANDOM> S; S.bind(st, it); S.clear(it, lane); break; }
@@ -1166,6 +1179,7 @@ __device__ __forceinline__ bool over_bound(const SimOut &out, uint32_t cand, uin
 
 // One unit: gather trips fill the queue with the unit's run heads, and each
 // step hands the next 32 of them to the unit's set state in trace order.
+template <bool POOL>
 __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, const SimOut &out,
                                          int lane) {
     // arena: [queue + staging ring (units that compact their heads)][set state]
@@ -1175,12 +1189,12 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     const uint32_t pol = it.policy < 2u ? it.policy : 2u;
     // set state in global memory (lsh bit 17): way scans at 16 * kres bytes
     // into the plan's state area, owned by this unit alone
-    const bool gmem = (it.lsh >> 17) & 1u;
+    const bool gmem = POOL;  // the planner puts every global-state unit in the pool
     uint8_t *const gst = gmem ? out.gstate + 16ull * it.kres : nullptr;
     const uint32_t kind = gmem ? (uint32_t)kGlobalScanLru + pol : (uint32_t)it.mode * 3u + pol;
     // matcher: a candidate whose other units already exceed the bound is out
     if (out.dist && over_bound(out, it.cand, 0, lane)) return;
-    clear_state(kind, st, gst, it, lane);
+    clear_state<POOL>(kind, st, gst, it, lane);
     __syncwarp();
     const uint32_t len = it.len;
     const uint32_t *__restrict__ idxp = it.idx;
@@ -1285,7 +1299,8 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             const uint32_t prev = lane == 0 ? carry : rot;
             carry = rot;
             const bool head = active && ln != prev;
-            const bool miss = resolve_step(kind, st, gst, it, ln, set, head, t, lane, lt, s0 + 1);
+            const bool miss =
+                resolve_step<POOL>(kind, st, gst, it, ln, set, head, t, lane, lt, s0 + 1);
             const uint32_t bits = __ballot_sync(kFull, miss);
             const uint32_t base = s0 << 5;
             const uint32_t after = base >= warmup ? kFull
@@ -1411,7 +1426,8 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             ccarry = rot;
             const bool head = act && line != prev;
             ++step;
-            const bool miss = resolve_step(kind, st, gst, it, line, set, head, pos, lane, lt, step);
+            const bool miss =
+                resolve_step<POOL>(kind, st, gst, it, line, set, head, pos, lane, lt, step);
             const uint32_t bits = __ballot_sync(kFull, miss);
             tot += __popc(bits);
             aft += __popc(__ballot_sync(kFull, miss && pos >= warmup));
@@ -1442,6 +1458,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     }
 }
 
+template <bool POOL>
 __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ items,
                                                   const __grid_constant__ SlotLayout L,
                                                   uint32_t *queues, SimOut out) {
@@ -1514,7 +1531,7 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
             }
             uint64_t t_start = 0;
             if (out.timeline) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
-            run_unit(it, arena, o, lane);
+            run_unit<POOL>(it, arena, o, lane);
             __syncwarp();
             if (out.timeline && lane == 0) {
                 // units of a split item share the entry: first start, last end
@@ -1559,10 +1576,12 @@ __global__ void __launch_bounds__(256) sim_zero_kernel(const SimItem *__restrict
 
 cudaError_t launch_sim(const SimItem *items, const SlotLayout &layout, uint32_t *queues, int grid,
                        const SimOut &out, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the pool's layout (pool16 set) runs the global-state instantiation
+    const auto k = layout.pool16 ? sim_kernel<true> : sim_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)layout.smem_bytes);
     if (e != cudaSuccess) return e;
-    sim_kernel<<<grid, layout.nwarps * 32, layout.smem_bytes, st>>>(items, layout, queues, out);
+    k<<<grid, layout.nwarps * 32, layout.smem_bytes, st>>>(items, layout, queues, out);
     return cudaGetLastError();
 }
 
@@ -1575,11 +1594,11 @@ cudaError_t launch_sim_zero(const SimItem *items, uint64_t n_units, int sms, con
 }
 
 int sim_max_ctas_per_sm(const SlotLayout &layout) {
-    if (cudaFuncSetAttribute(sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(sim_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)layout.smem_bytes) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_kernel, layout.nwarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_kernel<false>, layout.nwarps * 32,
                                                       layout.smem_bytes) != cudaSuccess)
         return 0;
     return n;
