@@ -169,8 +169,8 @@ class ClockSampler:
 # From one ncu capture (--set full) of the current sim_kernel on the batched
 # workload with items capped at 65,536 accesses: the slot-mix launch and the
 # one-warp launch of one run, summed.
-SIM_DRAM_BYTES_PER_ACCESS = (263.807488e6 + 7.867392e6 + 2.604544e6) / 65559830
-SIM_WARP_INST_PER_ACCESS = (442310117 + 9148504) / 65559830
+SIM_DRAM_BYTES_PER_ACCESS = (264.532224e6 + 7.433216e6 + 2.598144e6) / 65559830
+SIM_WARP_INST_PER_ACCESS = (444888722 + 9218020) / 65559830
 # Algorithmic work of one simulated access in the warp-per-set mapping: the
 # decode (line, set and tag by shift and multiply-high), one warp-wide tag
 # compare (ballot / match), the replacement-state update and the miss bit,

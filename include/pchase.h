@@ -169,6 +169,8 @@ typedef struct {
     uint32_t pool_warps;         /* most warps of the global-state pool launch, each owning
                                     one state region (default and at most 608; rounded up
                                     to a multiple of 4) */
+    uint32_t big_slots;          /* slots per CTA placed for the largest size classes before
+                                    the greedy fill of the slot mix (default 1, at most 4) */
 } pchase_tune;
 
 typedef struct pchase_sim_plan pchase_sim_plan;

@@ -50,7 +50,7 @@ class Tune(ctypes.Structure):
     _fields_ = [("scan_max_ways", _c_u32), ("smem_budget_bytes", _c_u32),
                 ("max_warps_per_cta", _c_u32), ("ctas_per_sm_cap", _c_u32),
                 ("batch_max_sets", _c_u32), ("max_split", _c_u32), ("split_cost_ns", _c_u32),
-                ("filtered", _c_u32), ("pool_warps", _c_u32)]
+                ("filtered", _c_u32), ("pool_warps", _c_u32), ("big_slots", _c_u32)]
 
 
 assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32 and ctypes.sizeof(UnitInfo) == 48

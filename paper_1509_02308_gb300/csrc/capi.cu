@@ -655,7 +655,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     *plan_out = nullptr;
     if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
         return fail(PCHASE_EINVAL, "NULL descriptor array");
-    pchase_tune tn{4, 220 * 1024, 16, 0, 64, 32, 0, 0, (uint32_t)kPoolMaxWarps};
+    pchase_tune tn{4, 220 * 1024, 16, 0, 64, 32, 0, 0, (uint32_t)kPoolMaxWarps, 1};
     if (tune) {
         if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
@@ -668,6 +668,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         tn.filtered = tune->filtered ? 1u : 0u;
         if (tune->pool_warps)
             tn.pool_warps = std::min<uint32_t>(tune->pool_warps, (uint32_t)kPoolMaxWarps);
+        if (tune->big_slots) tn.big_slots = std::min<uint32_t>(tune->big_slots, 4);
     }
     for (uint32_t i = 0; i < n_geom; ++i) {
         int rc = check_geom(geoms[i], i);
@@ -1117,6 +1118,19 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             slots[main_top] = 1;
             used = caps[main_top];
             nw = 1;
+            // extra large slots first (big_slots - 1 of them, each the largest
+            // class that leaves half of what is left to the greedy fill): the
+            // greedy alone spends the budget on small slots before the large
+            // classes' work, which only the first slot holds, would pay
+            for (uint32_t k = 1; k < tn.big_slots && nw < tn.max_warps_per_cta; ++k) {
+                int q2 = -1;
+                for (int q = main_top; q >= 0; --q)
+                    if (caps[q] <= (budget - used) / 2 && work[q] > 0.0) { q2 = q; break; }
+                if (q2 < 0) break;
+                slots[q2] += 1;
+                used += caps[q2];
+                nw += 1;
+            }
             while (nw < tn.max_warps_per_cta) {
                 int best = -1;
                 double best_ms = makespan(slots);
