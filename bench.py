@@ -1100,6 +1100,11 @@ def learned_bench(args, dev):
                      log_every=max(1, args.inverse_steps // 4))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    # inference in 65,536-trace chunks (fewer, fuller launches) over the trained
+    # weights: a handle that shares the parameters and holds only the
+    # inference buffers
+    train_net = net
+    net = INV.LearnedInverse(max_batch=65536, share_params=train_net, infer_only=True)
     n = args.inverse_eval
     x, _, truth = INV.LearnedInverse.synth(rates, tt, n, seed=0x5EED1004)
     truth = truth.cpu().numpy()

@@ -539,6 +539,13 @@ void pchase_inverse_destroy(pchase_inverse *h);
 uint64_t pchase_inverse_param_count(const pchase_inverse *h);
 size_t pchase_inverse_param_bytes(const pchase_inverse *h);
 size_t pchase_inverse_work_bytes(const pchase_inverse *h);
+/* The leading part of `work` that pchase_inverse_infer and
+ * pchase_inverse_classify use (status, inputs, activations, logits): a handle
+ * made only for inference, whose max_batch sets its chunk (larger chunks run
+ * faster), may allocate just this many bytes; pchase_inverse_train_step needs
+ * all of pchase_inverse_work_bytes.  The parameter layout does not depend on
+ * max_batch, so handles of different max_batch share one `params`. */
+size_t pchase_inverse_infer_work_bytes(const pchase_inverse *h);
 
 /* Byte offset in `work` of a device uint32 status word: pchase_inverse_infer,
  * _classify and _train_step clear it when called, and a tensor-core

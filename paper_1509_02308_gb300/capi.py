@@ -99,6 +99,7 @@ SIGNATURES = {
     "pchase_inverse_param_count": (_c_u64, [_c_p]),
     "pchase_inverse_param_bytes": (ctypes.c_size_t, [_c_p]),
     "pchase_inverse_work_bytes": (ctypes.c_size_t, [_c_p]),
+    "pchase_inverse_infer_work_bytes": (ctypes.c_size_t, [_c_p]),
     "pchase_inverse_status_offset": (ctypes.c_size_t, [_c_p]),
     "pchase_inverse_activation_offset": (ctypes.c_size_t, [_c_p, _c_u32]),
     "probe_pchase": (ctypes.c_int, [_c_p, _c_u32, _c_u32, _c_u32, _c_u32, ctypes.c_int, _c_p,

@@ -906,7 +906,7 @@ struct pchase_inverse {
     uint32_t max_batch;
     size_t p_w, p_wb, p_g, p_m, p_v, p_bytes;
     size_t status, xb, cols[4], pre[4], act[4], pre4, h4, logits, dlog, dlogb, dh, dzf, dzb, dbig,
-        dsmall, work_bytes;
+        dsmall, work_bytes, infer_bytes;
 };
 
 namespace {
@@ -1044,22 +1044,28 @@ int pchase_inverse_create(uint32_t max_batch, pchase_inverse **out) {
     h->p_v = o; o = a256(o + 4 * n);
     h->p_bytes = o;
     const size_t B = max_batch;
+    // inference's buffers first (a caller that only infers allocates that
+    // prefix, pchase_inverse_infer_work_bytes), then the training step's
     o = 0;
     h->status = o; o = a256(o + 4);
     h->xb = o; o = a256(o + 2 * B * kPoints);
+    for (int l = 0; l < 4; ++l) {
+        const size_t lout = h->L.lin[l] / 2;
+        h->act[l] = o; o = a256(o + 2 * B * lout * kCh);
+    }
+    h->logits = o; o = a256(o + 4 * B * kLogits);
+    h->infer_bytes = o;
     size_t big = B * kFlat;  // largest per-layer fp32 gradient
     for (int l = 0; l < 4; ++l) {
         const size_t lout = h->L.lin[l] / 2, cin = h->L.cin[l];
         h->cols[l] = o; o = a256(o + 2 * B * lout * kKer * cin);
         h->pre[l] = o; o = a256(o + 4 * B * lout * kCh);
-        h->act[l] = o; o = a256(o + 2 * B * lout * kCh);
         big = std::max(big, B * lout * kKer * cin);
         big = std::max(big, B * lout * kCh);
         big = std::max(big, B * (size_t)h->L.lin[l] * cin);
     }
     h->pre4 = o; o = a256(o + 4 * B * kHidden);
     h->h4 = o; o = a256(o + 2 * B * kHidden);
-    h->logits = o; o = a256(o + 4 * B * kLogits);
     h->dlog = o; o = a256(o + 4 * B * kLogits);
     h->dlogb = o; o = a256(o + 2 * B * kLogits);
     h->dh = o; o = a256(o + 4 * B * kHidden);
@@ -1076,6 +1082,7 @@ void pchase_inverse_destroy(pchase_inverse *h) { delete h; }
 uint64_t pchase_inverse_param_count(const pchase_inverse *h) { return h ? h->L.n_params : 0; }
 size_t pchase_inverse_param_bytes(const pchase_inverse *h) { return h ? h->p_bytes : 0; }
 size_t pchase_inverse_work_bytes(const pchase_inverse *h) { return h ? h->work_bytes : 0; }
+size_t pchase_inverse_infer_work_bytes(const pchase_inverse *h) { return h ? h->infer_bytes : 0; }
 size_t pchase_inverse_status_offset(const pchase_inverse *h) { return h ? h->status : 0; }
 size_t pchase_inverse_activation_offset(const pchase_inverse *h, uint32_t layer) {
     return h && layer < 4 ? h->act[layer] : 0;

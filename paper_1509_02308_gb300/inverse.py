@@ -106,18 +106,28 @@ def classes_from_rates(cands, rates: torch.Tensor, tol: float = CLASS_TOLERANCE)
 
 
 class LearnedInverse:
-    def __init__(self, max_batch: int = 4096):
+    def __init__(self, max_batch: int = 4096, share_params: "LearnedInverse | None" = None,
+                 infer_only: bool = False):
+        """max_batch: the training batch and the inference chunk.  share_params:
+        another model whose parameter buffer this one uses (an inference handle
+        with larger chunks over trained weights); infer_only: allocate only the
+        work buffers inference needs."""
         self.L = C.load()
         h = ctypes.c_void_p()
         _check(self.L.pchase_inverse_create(max_batch, ctypes.byref(h)))
         self.h = h
         self.max_batch = max_batch
         self.n_params = int(self.L.pchase_inverse_param_count(h))
-        self.params = torch.empty(int(self.L.pchase_inverse_param_bytes(h)) + 256,
-                                  dtype=torch.uint8, device=DEV)
-        self.work = torch.empty(int(self.L.pchase_inverse_work_bytes(h)) + 256,
-                                dtype=torch.uint8, device=DEV)
-        self._p = (C.ptr(self.params) + 255) & ~255
+        if share_params is not None:
+            self.params = share_params.params
+            self._p = share_params._p
+        else:
+            self.params = torch.empty(int(self.L.pchase_inverse_param_bytes(h)) + 256,
+                                      dtype=torch.uint8, device=DEV)
+            self._p = (C.ptr(self.params) + 255) & ~255
+        wb = (self.L.pchase_inverse_infer_work_bytes(h) if infer_only
+              else self.L.pchase_inverse_work_bytes(h))
+        self.work = torch.empty(int(wb) + 256, dtype=torch.uint8, device=DEV)
         self._w = (C.ptr(self.work) + 255) & ~255
 
     def __del__(self):

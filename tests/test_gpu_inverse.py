@@ -372,3 +372,24 @@ def test_classify_captured_in_a_cuda_graph_equals_eager():
         g.replay()
         torch.cuda.synchronize()
         assert np.array_equal(cand.cpu().numpy(), want) and int(nf.item()) == wnf
+
+
+def test_inference_handle_with_larger_chunks_shares_trained_weights():
+    """An inference-only handle (only pchase_inverse_infer_work_bytes of work)
+    with 8192-trace chunks over the parameters of a 1024-chunk training handle
+    gives the same predictions and, up to the atomic FC sums' last bits, the
+    same confidences, over 20,000 traces."""
+    rng = np.random.Generator(np.random.PCG64(21))
+    net = INV.LearnedInverse(max_batch=1024)
+    net.init(seed=31)
+    inf = INV.LearnedInverse(max_batch=8192, share_params=net, infer_only=True)
+    assert inf.work.numel() < int(inf.L.pchase_inverse_work_bytes(inf.h)) // 2
+    x = torch.from_numpy(rng.random((20000, R.POINTS)).astype(np.float32)).cuda()
+    p1, c1, l1 = net.infer(x, want_logits=True)
+    p2, c2, l2 = inf.infer(x, want_logits=True)
+    assert inf.status() == 0
+    l1, l2 = l1.cpu().numpy(), l2.cpu().numpy()
+    assert np.allclose(l1, l2, rtol=2.0 ** -14, atol=2.0 ** -14 * np.abs(l1).max())
+    same = (p1.cpu().numpy() == p2.cpu().numpy()).all(axis=1).mean()
+    assert same > 0.999
+    assert np.allclose(c1.cpu().numpy(), c2.cpu().numpy(), rtol=2.0 ** -12, atol=0)
