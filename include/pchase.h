@@ -520,8 +520,9 @@ int pchase_probe_smem_throughput(uint32_t ctas, uint32_t threads, uint32_t ilp, 
  * positions), flatten 2048 -> FC 256 + GELU -> FC 31 logits, read as heads of
  * 17 (capacity), 4 (line size), 7 (ways), 3 (policy).  BF16 GEMM operands,
  * FP32 accumulation; FP32 master weights, Adam moments and gradients.  At
- * inference the 64-channel convolutions run on the tcgen05 tensor cores with
- * TMEM accumulators.
+ * inference the 64-channel convolutions and FC + heads run on the tcgen05
+ * tensor cores with TMEM accumulators, the first layer computed by producer
+ * warps straight into the second layer's operand tiles.
  *
  * Buffers: the caller allocates `params` (pchase_inverse_param_bytes; its
  * first 4 * param_count bytes are the FP32 weights in layer order, each
@@ -553,7 +554,9 @@ size_t pchase_inverse_infer_work_bytes(const pchase_inverse *h);
 size_t pchase_inverse_status_offset(const pchase_inverse *h);
 /* Byte offset in `work` of convolution layer `layer`'s (0..3) BF16 output,
  * [B][positions][64] for the last chunk of the last forward pass; 0 for a
- * layer out of range.  For inspection and tests. */
+ * layer out of range.  Inference computes layers 1 and 2 in one kernel whose
+ * layer-1 outputs never leave the SM, so layer 0's buffer holds the last
+ * training step's.  For inspection and tests. */
 size_t pchase_inverse_activation_offset(const pchase_inverse *h, uint32_t layer);
 
 /* Byte offset in `params` of one of its arrays, each pchase_inverse_param_count

@@ -294,6 +294,290 @@ __global__ void __launch_bounds__(kThreads, 1)
                      : "memory");
 }
 
+// ------------------------------------------- first two layers, fused
+// Inference of layers 1 and 2 without the first layer's activations ever
+// leaving the SM.  One tile is one trace: layer 2's 128 output positions are
+// exactly an M=128 accumulator.  Its input slab (the two planes of 18 x 8
+// rows of layer-1 outputs described above, 36 KB) is computed by eight
+// producer warps straight from the trace's 512 FP32 inputs (rounded to BF16
+// as the unfused path rounds them): row 8G + i of plane pl holds layer-1
+// position q = 32i + 2G - 2 + pl, channels in 16-byte chunks with the
+// 128-byte swizzle, zeros outside 0 <= q < 256.  The other eight warps issue
+// the MMAs (one thread) and run the epilogue, as conv_tc_kernel does.  The two
+// roles meet on mbarriers: slab_full (the producers' 256 arrivals after a
+// proxy fence), slab_empty (tcgen05.commit once the MMAs that read a slab
+// are done; three slabs in flight) and acc_full (two TMEM accumulators).
+// Every wait gives up after 2 s: the CTA then ORs PCHASE_DEV_TIMEOUT into
+// *status, each role leaves its loop at its next group barrier, the MMAs
+// already issued are waited for, and TMEM is freed.
+constexpr int kFusedThreads = 512;
+constexpr uint32_t kFusedXs = 520;  // staged inputs: xs[q + 2] = x[q], zeros around
+constexpr uint32_t kFusedSmem = 1024 + kWBytes + kSlabs * kSlabBytes + 4 * kFusedXs + 128;
+
+__device__ __forceinline__ bool group_any(int bar_id, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n"
+        " bar.red.or.pred p, %2, 256, q;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(bar_id)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void group_sync(int bar_id) {
+    asm volatile("bar.sync %0, 256;" ::"r"(bar_id) : "memory");
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    conv12_tc_kernel(const float *__restrict__ x, int nb, const __nv_bfloat16 *__restrict__ W1,
+                     const float *__restrict__ bias1, const __nv_bfloat16 *__restrict__ W2,
+                     const float *__restrict__ bias2, __nv_bfloat16 *__restrict__ out,
+                     uint32_t *__restrict__ status) {
+    constexpr int kLin = 512, kL1 = 256, kL2 = 128;
+    extern __shared__ uint8_t dsm[];
+    const uint32_t raw = smem_u32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *const gbase = dsm + (base - raw);
+    const uint32_t sW = base;
+    const uint32_t sSlab = base + kWBytes;
+    float *const xs = reinterpret_cast<float *>(gbase + kWBytes + kSlabs * kSlabBytes);
+    const uint32_t sBar = base + kWBytes + kSlabs * kSlabBytes + 4 * kFusedXs;
+    // barriers: slab_full[3] at sBar + 8b, slab_empty[3] at sBar + 24 + 8b,
+    // acc_full[2] at sBar + 48 + 8a; then the TMEM address and the abort flag
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + (sBar - base) + 64);
+    volatile uint32_t *const abort_flag = tslot + 1;
+    volatile uint32_t *const last_issued = tslot + 2;  // tiles whose MMAs were issued
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = nb;
+
+    // layer 2's weights, as conv_tc_kernel loads them
+    for (int e = tid; e < kTaps * kCh * 8; e += kFusedThreads) {
+        const int k = e >> 9, co = (e >> 3) & 63, c = e & 7;
+        cp_async16(sW + k * 8192 + co * 128 + ((c ^ (co & 7)) << 4),
+                   W2 + (size_t)co * (kTaps * kCh) + k * kCh + c * 8, true);
+    }
+    cp_async_commit();
+    if (tid == 0) {
+        for (int q = 0; q < 3; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" ::"r"(sBar + 8 * q) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 24 + 8 * q)
+                         : "memory");
+        }
+        for (int a = 0; a < 2; ++a)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 48 + 8 * a)
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+        *last_issued = 0;
+    }
+    if (tid < 2) xs[tid] = 0.0f;
+    if (tid < (int)kFusedXs - kLin - 2) xs[kLin + 2 + tid] = 0.0f;
+    // slab rows of positions -2, -1 (row 0 of each plane) and 256, 257 (row
+    // 8 * 17 + 7) are zero padding, written once: the producers never write them
+    for (int e = tid; e < kSlabs * 2 * 2 * 8; e += kFusedThreads) {
+        const int sb = e / 32, pl = (e / 16) & 1, which = (e / 8) & 1, c = e & 7;
+        const int row = which ? 8 * 17 + 7 : 0;
+        uint4 *d = reinterpret_cast<uint4 *>(gbase + kWBytes + (size_t)sb * kSlabBytes +
+                                             (size_t)pl * kPlaneBytes + (size_t)row * 128 + c * 16);
+        *d = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 8) {
+        // ---------------- producers: layer 1 into the slabs (barrier id 2)
+        const int p = tid;             // 0..255
+        const int c = p & 7;           // the 8 channels this thread computes
+        const int r0 = p >> 3;         // rows r0, r0 + 32, ... of the 288 slab rows
+        float w[8][kTaps], bs[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            bs[j] = bias1[c * 8 + j];
+#pragma unroll
+            for (int k = 0; k < kTaps; ++k) w[j][k] = __bfloat162float(W1[(c * 8 + j) * kTaps + k]);
+        }
+        // the next trace's inputs are loaded while this one's slab is computed
+        float xa = 0.0f, xb = 0.0f;
+        if ((int)blockIdx.x < ntiles) {
+            xa = x[(size_t)blockIdx.x * kLin + p];
+            xb = x[(size_t)blockIdx.x * kLin + 256 + p];
+        }
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * (int)gridDim.x;
+            if (t >= ntiles) break;
+            const int b = j % kSlabs;
+            bool ok = true;
+            if (j >= kSlabs) ok = mbar_wait(sBar + 24 + 8 * b, (uint32_t)(j / kSlabs - 1) & 1u);
+            // also: every producer is done with the previous tile's inputs
+            if (group_any(2, !ok || *abort_flag != 0)) {
+                if (p == 0) *abort_flag = 1;
+                break;
+            }
+            xs[p + 2] = __bfloat162float(__float2bfloat16(xa));
+            xs[p + 258] = __bfloat162float(__float2bfloat16(xb));
+            group_sync(2);
+            const int tn = t + (int)gridDim.x;
+            if (tn < ntiles) {
+                xa = x[(size_t)tn * kLin + p];
+                xb = x[(size_t)tn * kLin + 256 + p];
+            }
+            const uint32_t slab = sSlab + (uint32_t)b * kSlabBytes;
+            // each layer-1 position once (a warp takes 4 consecutive ones, so
+            // its input reads fall in different banks), stored to the slab row
+            // that holds it and, for the positions two row groups repeat, to
+            // the second one too; the rows outside 0..255 stay zero
+#pragma unroll 2
+            for (int q = r0; q < kL1; q += 32) {
+                float xin[kTaps];
+#pragma unroll
+                for (int k = 0; k < kTaps; ++k) xin[k] = xs[2 * q + k];  // x[2q + k - 2]
+                uint32_t pk[4];
+#pragma unroll
+                for (int jj = 0; jj < 8; jj += 2) {
+                    float v[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < kTaps; ++k) acc = fmaf(w[jj + h][k], xin[k], acc);
+                        v[h] = acc + bs[jj + h];
+                    }
+                    const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_fast(v[0]), gelu_fast(v[1]));
+                    pk[jj >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
+                }
+                // q = 32i + 2G - 2 + pl: row 8G + i of plane pl (i < 8), and
+                // row 8(G + 16) + (i - 1) when G < 2 and i > 0
+                const int pl = q & 1, u = (q + 2 - pl) >> 1;
+                const int i = u >> 4, G = u & 15;
+                const uint32_t pbase = slab + (uint32_t)pl * kPlaneBytes;
+                uint32_t dst;
+                if (i < 8) {
+                    dst = pbase + (uint32_t)(8 * G + i) * 128u + ((uint32_t)(c ^ i) << 4);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
+                                 "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3])
+                                 : "memory");
+                }
+                if (G < 2 && i > 0) {
+                    dst = pbase + (uint32_t)(8 * (G + 16) + i - 1) * 128u +
+                          ((uint32_t)(c ^ (i - 1)) << 4);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
+                                 "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3])
+                                 : "memory");
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(sBar + 8 * b)
+                         : "memory");
+        }
+    } else {
+        // ---------------- MMA issue and epilogue (barrier id 1)
+        const int g = tid - 256, gw = warp - 8;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * (int)gridDim.x;
+            const bool have = t < ntiles;
+            tc_fence_before();
+            const bool stop = group_any(1, *abort_flag != 0);
+            tc_fence_after();
+            if (stop) break;
+            if (have && g == 0) {
+                const int b = j % kSlabs;
+                if (!mbar_wait(sBar + 8 * b, (uint32_t)(j / kSlabs) & 1u)) {
+                    *abort_flag = 1;
+                } else {
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(j & 1) * 64u;
+                    const uint32_t slab = sSlab + (uint32_t)b * kSlabBytes;
+#pragma unroll
+                    for (int k = 0; k < kTaps; ++k) {
+                        const uint32_t a0 = slab + (uint32_t)(k & 1) * kPlaneBytes + (uint32_t)(k >> 1) * 1024u;
+                        const uint32_t b0 = sW + (uint32_t)k * 8192u;
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+                            mma_bf16(d, sw128_desc(a0 + 32u * s), sw128_desc(b0 + 32u * s),
+                                     (k | s) != 0 ? 1u : 0u);
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            sBar + 48u + 8u * (uint32_t)(j & 1))
+                        : "memory");
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            sBar + 24u + 8u * (uint32_t)b)
+                        : "memory");
+                    *last_issued = (uint32_t)(j + 1);
+                }
+            }
+            if (j > 0) {
+                // epilogue of tile j - 1 (issued: tile j - 1 had its MMAs unless aborted)
+                const int jp = j - 1;
+                const bool got = mbar_wait(sBar + 48 + 8 * (jp & 1), (uint32_t)(jp >> 1) & 1u);
+                if (group_any(1, !got)) {
+                    if (g == 0) *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const int tp = t - (int)gridDim.x;
+                const int quarter = gw & 3, half = gw >> 2;
+                const uint32_t taddr = tmem + (uint32_t)(jp & 1) * 64u + (uint32_t)half * 32u +
+                                       ((uint32_t)(quarter * 32) << 16);
+                uint32_t v[2][16];
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) tmem_ld16(taddr + qq * 16, v[qq]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int r = quarter * 32 + lane;
+                const int m = 16 * (r & 7) + (r >> 3);  // output position of TMEM lane r
+                uint4 *o4 = reinterpret_cast<uint4 *>(out + ((size_t)tp * kL2 + m) * kCh + half * 32);
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int e = 0; e < 16; e += 2) {
+                        const int n = half * 32 + qq * 16 + e;
+                        const float a0 = __uint_as_float(v[qq][e]) + __ldg(bias2 + n);
+                        const float a1 = __uint_as_float(v[qq][e + 1]) + __ldg(bias2 + n + 1);
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_fast(a0), gelu_fast(a1));
+                        pk[e >> 1] = *reinterpret_cast<const uint32_t *>(&h2);
+                    }
+                    o4[2 * qq] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    o4[2 * qq + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+            if (!have) break;
+        }
+        // every commit's arrival lands before the CTA leaves (the last tiles'
+        // slab_empty arrivals have no producer waiting for them; after a
+        // timeout, MMAs issued but never waited for must also finish before
+        // TMEM is freed)
+        if (g == 0) {
+            const uint32_t li = *last_issued;
+            if (li && *abort_flag)
+                mbar_wait(sBar + 48 + 8 * ((li - 1) & 1), (uint32_t)((li - 1) >> 1) & 1u);
+            for (uint32_t jj = li > (uint32_t)kSlabs ? li - kSlabs : 0u; jj < li; ++jj)
+                mbar_wait(sBar + 24 + 8 * (jj % kSlabs), (jj / kSlabs) & 1u);
+        }
+    }
+    if (tid == 0 && *abort_flag) atomicOr(status, PCHASE_DEV_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+}
+
 // ------------------------------------------------------------ FC + heads
 // logits[m][h] = bias5[h] + sum_n bf16(GELU(bias4[n] + sum_k act[m][k] W4[n][k])) W5[h][n]
 // act [B][2048] BF16, W4 [256][2048] BF16, W5 [31][256] BF16.  CTA (s, t)
@@ -511,6 +795,21 @@ cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16
     const long long ntiles = ((long long)nb * lout + kTileRows - 1) / kTileRows;
     const int grid = (int)std::min<long long>(ntiles, std::max(1, sms));
     conv_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, nb, lin, W, bias, out, pre, status);
+    return cudaGetLastError();
+}
+
+cudaError_t conv12_tc(const float *x, int nb, const __nv_bfloat16 *W1, const float *bias1,
+                      const __nv_bfloat16 *W2, const float *bias2, __nv_bfloat16 *out,
+                      uint32_t *status, int sms, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    if (!status) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(conv12_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kFusedSmem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nb, std::max(1, sms));
+    conv12_tc_kernel<<<grid, kFusedThreads, kFusedSmem, st>>>(x, nb, W1, bias1, W2, bias2, out,
+                                                               status);
     return cudaGetLastError();
 }
 

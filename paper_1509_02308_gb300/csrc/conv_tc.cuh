@@ -19,6 +19,15 @@ cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16
                     const float *bias, __nv_bfloat16 *out, float *pre, uint32_t *status,
                     int sms, cudaStream_t st);
 
+// Inference of the first two layers in one kernel: out [nb][128][64] BF16 =
+// layer 2's GELU outputs for x [nb][512] FP32 (rounded to BF16 as inputs),
+// W1 [64][5] BF16 + bias1, W2 [64][5*64] BF16 + bias2.  The first layer's
+// outputs never leave the SM.  A wait that gives up ORs PCHASE_DEV_TIMEOUT
+// into *status (device).
+cudaError_t conv12_tc(const float *x, int nb, const __nv_bfloat16 *W1, const float *bias1,
+                      const __nv_bfloat16 *W2, const float *bias2, __nv_bfloat16 *out,
+                      uint32_t *status, int sms, cudaStream_t st);
+
 // logits [nb][31] FP32 = heads(GELU(FC(act))) for act [nb][2048] BF16 (the
 // flattened last convolution), W4 [256][2048] BF16 + bias4, W5 [31][256] BF16
 // + bias5; hidden activations rounded to BF16 as the heads' operands.  The

@@ -938,12 +938,22 @@ int device_sms() {
 }
 
 int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B, cudaStream_t st,
-            bool train) {
+            bool train, const float *xf = nullptr) {
     const InverseLayout &L = h->L;
     const __nv_bfloat16 *wb = at<__nv_bfloat16>(params, h->p_wb);
     const float *wf = at<float>(params, h->p_w);
     const __nv_bfloat16 *in = at<__nv_bfloat16>(work, h->xb);
-    for (int l = 0; l < 4; ++l) {
+    int l0 = 0;
+    if (!train) {
+        // inference: layers 1 and 2 in one tcgen05 kernel from the FP32 inputs
+        // (layer 1's activations stay on chip)
+        __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[1]);
+        INV_CUDA(conv12_tc(xf, (int)B, wb + L.w[0], wf + L.b[0], wb + L.w[1], wf + L.b[1], o,
+                           at<uint32_t>(work, h->status), device_sms(), st));
+        in = o;
+        l0 = 2;
+    }
+    for (int l = l0; l < 4; ++l) {
         const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
         if (cin == kCh && !train) {
             // inference: tcgen05 tensor cores, TMEM accumulators, implicit im2col
@@ -1237,9 +1247,7 @@ int pchase_inverse_infer(const pchase_inverse *h, const void *params, void *work
     INV_CUDA(cudaMemsetAsync(at<uint32_t>(work, h->status), 0, 4, st));
     for (uint32_t b0 = 0; b0 < n; b0 += h->max_batch) {
         const uint32_t B = std::min(h->max_batch, n - b0);
-        f2b_kernel<<<grid_for((size_t)B * kPoints), 256, 0, st>>>(
-            x + (size_t)b0 * kPoints, (size_t)B * kPoints, at<__nv_bfloat16>(work, h->xb));
-        int rc = forward(h, params, work, B, st, false);
+        int rc = forward(h, params, work, B, st, false, x + (size_t)b0 * kPoints);
         if (rc) return rc;
         const float *lg = at<float>(work, h->logits);
         predict_kernel<<<(B + 127) / 128, 128, 0, st>>>(lg, (int)B, pred_out + (size_t)b0 * 4,
