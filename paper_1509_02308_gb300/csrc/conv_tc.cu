@@ -580,35 +580,39 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
 
 // ------------------------------------------------------------ FC + heads
 // logits[m][h] = bias5[h] + sum_n bf16(GELU(bias4[n] + sum_k act[m][k] W4[n][k])) W5[h][n]
-// act [B][2048] BF16, W4 [256][2048] BF16, W5 [31][256] BF16.  CTA (s, t)
-// takes rows 128t .. 128t+127 and hidden units 64s .. 64s+63:
-//   * FC on the tensor cores: M128 N64, K = 2048 in 32 blocks of 64 through a
-//     6-buffer cp.async ring loaded 3 blocks ahead; an mbarrier per buffer
+// act [B][2048] BF16, W4 [256][2048] BF16, W5 [31][256] BF16.  CTA t takes
+// rows 128t .. 128t+127 and all 256 hidden units, so each activation row is
+// read once:
+//   * FC on the tensor cores: M128 N256, K = 2048 in 32 blocks of 64 through a
+//     4-buffer cp.async ring loaded 2 blocks ahead; an mbarrier per buffer
 //     frees it once that block's MMAs are done;
-//   * epilogue: bias, GELU, BF16 rounding of the 128 x 64 hidden slice into a
-//     swizzled shared tile, then the heads as a second MMA (M128 N32 K64 with
-//     W5's slice padded to 32 rows) into 32 more TMEM columns;
-//   * the 31 head partial sums per row are added atomically into logits
-//     (zeroed by the launcher; slice 0 adds bias5).
-constexpr int kFcK = 2048, kFcN = 256, kHeads = 31, kFcSlice = 64, kHeadsPad = 32;
-constexpr int kFcStages = 6;   // ring buffers
-constexpr int kFcAhead = 3;    // blocks loaded ahead; a buffer is refilled once the
+//   * epilogue: bias, GELU, BF16 rounding of the 128 x 256 hidden tile into
+//     four swizzled 64-column K blocks in shared memory (the ring's space),
+//     then the heads as a second MMA (M128 N32 K256, W5 padded to 32 rows)
+//     into 32 more TMEM columns, read back and stored with bias5 (no atomics:
+//     each CTA owns its rows).
+constexpr int kFcK = 2048, kFcN = 256, kHeads = 31, kHeadsPad = 32;
+constexpr int kFcStages = 4;   // ring buffers
+constexpr int kFcAhead = 2;    // blocks loaded ahead; a buffer is refilled once the
                                // MMAs of the block kFcStages back are done (2 blocks of slack)
-constexpr uint32_t kFcABytes = kTileRows * 128, kFcBBytes = kFcSlice * 128;
-constexpr uint32_t kFcStageBytes = kFcABytes + kFcBBytes;  // 24 KB
-constexpr uint32_t kW5Bytes = kHeadsPad * 128;             // 32 rows x 64 BF16, swizzled
+constexpr uint32_t kFcABytes = kTileRows * 128, kFcBBytes = kFcN * 128;
+constexpr uint32_t kFcStageBytes = kFcABytes + kFcBBytes;  // 48 KB
+constexpr uint32_t kW5Bytes = 4 * kHeadsPad * 128;         // 4 K blocks of 32 rows x 64 BF16
 constexpr uint32_t kFcSmemBytes =
     1024 + kFcStages * kFcStageBytes + kW5Bytes + 8 * (kFcStages + 1) + 16;
+constexpr uint32_t kFcTmemCols = 512;  // 256 FC + 32 heads, rounded to a power of two
+constexpr uint32_t kIdescFc = (1u << 4) | (1u << 7) | (1u << 10) |
+                              ((uint32_t)(kFcN >> 3) << 17) | ((uint32_t)(kTileRows >> 4) << 24);
 constexpr uint32_t kIdescHeads = (1u << 4) | (1u << 7) | (1u << 10) |
                                  ((uint32_t)(kHeadsPad >> 3) << 17) |
                                  ((uint32_t)(kTileRows >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16_n32(uint32_t d_tmem, uint64_t a, uint64_t b,
-                                             uint32_t acc) {
+__device__ __forceinline__ void mma_bf16_id(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdescHeads), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 
@@ -627,23 +631,23 @@ __global__ void __launch_bounds__(128, 1)
     uint32_t *const tslot = reinterpret_cast<uint32_t *>(
         gbase + kFcStages * kFcStageBytes + kW5Bytes + 8 * (kFcStages + 1));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n0 = blockIdx.x * kFcSlice;
-    const int m0 = blockIdx.y * kTileRows;
+    const int m0 = blockIdx.x * kTileRows;
     constexpr int kBlocks = kFcK / 64;
 
-    // W5 columns n0 .. n0+63 as a B operand: 32 rows (row 31 zero) x 128 B, swizzled
-    for (int e = tid; e < kHeadsPad * 8; e += 128) {
-        const int h = e >> 3, c = e & 7;
+    // W5 as the heads' B operand: K block kb holds hidden units 64kb .. +63 of
+    // its 32 rows (row 31 zero), 128-byte swizzle
+    for (int e = tid; e < 4 * kHeadsPad * 8; e += 128) {
+        const int kb = e >> 8, h = (e >> 3) & 31, c = e & 7;
         const bool ok = h < kHeads;
-        cp_async16(sW5 + h * 128 + ((c ^ (h & 7)) << 4),
-                   ok ? W5 + (size_t)h * kFcN + n0 + c * 8 : W5, ok);
+        cp_async16(sW5 + kb * (kHeadsPad * 128) + h * 128 + ((c ^ (h & 7)) << 4),
+                   ok ? W5 + (size_t)h * kFcN + kb * 64 + c * 8 : W5, ok);
     }
     auto load = [&](int kb) {
         if (kb < kBlocks) {
             const uint32_t st = sStage + (kb % kFcStages) * kFcStageBytes;
             const int k0 = kb * 64;
-            // A: 128 rows x 8 chunks; B: 64 rows x 8 chunks; 128-byte swizzle
-            for (int e = tid; e < (kTileRows + kFcSlice) * 8; e += 128) {
+            // A: 128 rows x 8 chunks; B: 256 rows x 8 chunks; 128-byte swizzle
+            for (int e = tid; e < (kTileRows + kFcN) * 8; e += 128) {
                 const int r = e >> 3, c = e & 7;
                 if (r < kTileRows) {
                     const int m = m0 + r;
@@ -653,7 +657,7 @@ __global__ void __launch_bounds__(128, 1)
                 } else {
                     const int rn = r - kTileRows;
                     cp_async16(st + kFcABytes + rn * 128 + ((c ^ (rn & 7)) << 4),
-                               W4 + (size_t)(n0 + rn) * kFcK + k0 + c * 8, true);
+                               W4 + (size_t)rn * kFcK + k0 + c * 8, true);
                 }
             }
         }
@@ -667,7 +671,7 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tslot)),
-                     "r"(128)
+                     "r"(kFcTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -675,7 +679,7 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;  // columns 0..63: FC; 64..95: heads
+    const uint32_t tmem = *tslot;  // columns 0..255: FC; 256..287: heads
 
     bool ok = true;
     for (int kb = 0; kb < kBlocks; ++kb) {
@@ -698,8 +702,8 @@ __global__ void __launch_bounds__(128, 1)
             const uint32_t st = sStage + (kb % kFcStages) * kFcStageBytes;
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem, sw128_desc(st + 32u * s), sw128_desc(st + kFcABytes + 32u * s),
-                         (kb | s) != 0 ? 1u : 0u);
+                mma_bf16_id(tmem, sw128_desc(st + 32u * s), sw128_desc(st + kFcABytes + 32u * s),
+                            kIdescFc, (kb | s) != 0 ? 1u : 0u);
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     sBar + 8u * (uint32_t)(kb % kFcStages))
@@ -713,28 +717,29 @@ __global__ void __launch_bounds__(128, 1)
     }
     const int r = warp * 32 + lane;  // TMEM lane = tile row
     if (ok) {
-        // hidden slice -> BF16 A tile of the heads MMA (buffer 0 is free now)
+        // hidden tile -> BF16 A operand of the heads MMA: K block kb (hidden
+        // units 64kb .. +63) at sStage + kb * 16 KB, rows of 128 bytes swizzled
         tc_fence_after();
-        const uint32_t hA = sStage;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
+#pragma unroll 1
+        for (int q = 0; q < 16; ++q) {
             uint32_t v[16];
             tmem_ld16(taddr + q * 16, v);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             uint32_t pk[8];
 #pragma unroll
             for (int e = 0; e < 16; e += 2) {
-                const int n = n0 + q * 16 + e;
+                const int n = q * 16 + e;
                 const float z0 = __uint_as_float(v[e]) + __ldg(bias4 + n);
                 const float z1 = __uint_as_float(v[e + 1]) + __ldg(bias4 + n + 1);
                 const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_fast(z0), gelu_fast(z1));
                 pk[e >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
             }
-            // 16 columns = chunks 2q, 2q+1 of row r
-            uint4 *row = reinterpret_cast<uint4 *>(gbase + (hA - base) + r * 128);
-            row[(2 * q) ^ (r & 7)] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            row[(2 * q + 1) ^ (r & 7)] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            // 16 columns = chunks 2(q % 4), +1 of row r in K block q / 4
+            uint4 *row = reinterpret_cast<uint4 *>(gbase + (q >> 2) * kFcABytes + r * 128);
+            const int c0 = 2 * (q & 3);
+            row[c0 ^ (r & 7)] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            row[(c0 + 1) ^ (r & 7)] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
@@ -742,9 +747,12 @@ __global__ void __launch_bounds__(128, 1)
         tc_fence_after();
         if (tid == 0) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
-                mma_bf16_n32(tmem + 64u, sw128_desc(hA + 32u * s), sw128_desc(sW5 + 32u * s),
-                             s != 0 ? 1u : 0u);
+            for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    mma_bf16_id(tmem + 256u, sw128_desc(sStage + kb * kFcABytes + 32u * s),
+                                sw128_desc(sW5 + kb * (kHeadsPad * 128) + 32u * s), kIdescHeads,
+                                (kb | s) != 0 ? 1u : 0u);
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     sBar + 8u * kFcStages)
@@ -755,16 +763,14 @@ __global__ void __launch_bounds__(128, 1)
         if (ok) {
             tc_fence_after();
             uint32_t v[2][16];
-            tmem_ld16(taddr + 64, v[0]);
-            tmem_ld16(taddr + 80, v[1]);
+            tmem_ld16(taddr + 256, v[0]);
+            tmem_ld16(taddr + 272, v[1]);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int m = m0 + r;
             if (m < nb) {
 #pragma unroll
                 for (int h = 0; h < kHeads; ++h)
-                    atomicAdd(logits + (size_t)m * kHeads + h,
-                              __uint_as_float(v[h >> 4][h & 15]) +
-                                  (blockIdx.x == 0 ? __ldg(bias5 + h) : 0.0f));
+                    logits[(size_t)m * kHeads + h] = __uint_as_float(v[h >> 4][h & 15]) + __ldg(bias5 + h);
             }
         }
     }
@@ -774,7 +780,8 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kFcTmemCols)
                      : "memory");
 }
 
@@ -822,9 +829,7 @@ cudaError_t fc_heads_tc(const __nv_bfloat16 *act, int nb, const __nv_bfloat16 *W
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kFcSmemBytes);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(logits, 0, (size_t)nb * kHeads * sizeof(float), st);
-    if (e != cudaSuccess) return e;
-    dim3 grid(kFcN / kFcSlice, (nb + kTileRows - 1) / kTileRows);
+    const int grid = (nb + kTileRows - 1) / kTileRows;
     fc_heads_tc_kernel<<<grid, 128, kFcSmemBytes, st>>>(act, nb, W4, bias4, W5, bias5, logits,
                                                         status);
     return cudaGetLastError();
