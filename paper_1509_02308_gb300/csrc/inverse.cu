@@ -7,8 +7,9 @@
 //   4 x [conv1d k=5, stride 2, pad 2, 64 channels, GELU]: 512x1 -> 256 -> 128 -> 64 -> 32
 //   flatten 32*64 = 2048 -> FC 256 -> GELU -> FC 31 = heads of 17 + 4 + 7 + 3 logits
 // Every product takes BF16 operands with FP32 accumulation; master weights,
-// Adam moments and gradients stay FP32.  Inference runs the 64-channel
-// convolutions and FC + heads on the tcgen05 tensor cores (conv_tc.cu); the
+// Adam moments and gradients stay FP32.  Inference runs on the tcgen05 tensor
+// cores (conv_tc.cu): layers 1 and 2 in one kernel (layer 1 computed on chip
+// from the FP32 inputs), layers 3 and 4, then FC + heads in one kernel; the
 // training step's GEMMs (forward with kept pre-activations, backward, weight
 // gradients) run here on warp-level mma.sync m16n8k16 tiles, the first
 // convolution (one input channel) on CUDA cores.

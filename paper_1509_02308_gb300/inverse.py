@@ -242,3 +242,34 @@ def lsq_match(rates: torch.Tensor, y: torch.Tensor):
     _check(L.pchase_lsq_match(C.ptr(rates), rates.shape[0], C.ptr(y), n, C.ptr(best), C.ptr(res),
                               (C.ptr(lw) + 255) & ~255, C.stream_handle()))
     return best[:n], res[:n]
+
+
+def _main():
+    """Inference timing on random traces with freshly initialised weights:
+    ``python -m paper_1509_02308_gb300.inverse --traces N --passes P`` runs P
+    passes of the network over N traces in one inference-only handle and
+    prints the CUDA-event time of each."""
+    import argparse
+
+    p = argparse.ArgumentParser()
+    p.add_argument("--traces", type=int, default=65536)
+    p.add_argument("--passes", type=int, default=3)
+    p.add_argument("--seed", type=int, default=1)
+    a = p.parse_args()
+    g = torch.Generator(device=DEV).manual_seed(a.seed)
+    x = torch.rand(a.traces, W.PLAN_POINTS, device=DEV, generator=g)
+    net = LearnedInverse(max_batch=a.traces, infer_only=True)
+    net.init(seed=a.seed)
+    for i in range(a.passes):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        net.infer(x)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        print(f"pass {i}: {ms:.3f} ms, {a.traces / ms / 1e3:.2f} M traces/s")
+    _check(net.status())
+
+
+if __name__ == "__main__":
+    _main()
