@@ -126,17 +126,51 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
 }
 
-// tanh form of GELU (Hendrycks & Gimpel 2016) with the hardware tanh
-// (tanh.approx.f32, relative error about 2^-11, below the BF16 output's 2^-8),
-// arranged as h + h tanh(x (k0 + k0 k1 x^2)), h = x / 2: five FP32 operations
-// and the tanh
-__device__ __forceinline__ float gelu_fast(float x) {
+// Two FP32 lanes in one 64-bit register pair (low = first).  The f32x2
+// forms issue one instruction for two IEEE operations with the same
+// rounding as their scalar forms, so results are bit-identical.
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2split(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// tanh form of GELU (Hendrycks & Gimpel 2016) on both lanes, rounded to a
+// BF16 pair (low lane in the low half), with the hardware tanh
+// (tanh.approx.f32, relative error about 2^-11, below the BF16 output's
+// 2^-8), arranged per lane as h + h tanh(x (k0 + k0 k1 x^2)), h = x / 2:
+// four f32x2 operations, two tanh and one conversion per pair
+__device__ __forceinline__ uint32_t gelu2_bf16(uint64_t x) {
     const float k0 = 0.7978845608028654f, k01 = 0.7978845608028654f * 0.044715f;
-    const float u = x * fmaf(k01, x * x, k0);
-    float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-    const float h = 0.5f * x;
-    return fmaf(h, t, h);
+    const uint64_t u = mul2(x, fma2(f2(k01, k01), mul2(x, x), f2(k0, k0)));
+    float u0, u1, t0, t1;
+    f2split(u, u0, u1);
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(u0));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(u1));
+    const uint64_t h = mul2(f2(0.5f, 0.5f), x);
+    float r0, r1;
+    f2split(fma2(h, f2(t0, t1), h), r0, r1);
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(r1), "f"(r0));
+    return d;
 }
 
 constexpr int kThreads = 256;
@@ -243,8 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         pr[q * 16 + e] = a0;
                         pr[q * 16 + e + 1] = a1;
                     }
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(gelu_fast(a0), gelu_fast(a1));
-                    pk[e >> 1] = *reinterpret_cast<const uint32_t *>(&h);
+                    pk[e >> 1] = gelu2_bf16(f2(a0, a1));
                 }
                 o4[2 * q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 o4[2 * q + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
@@ -405,12 +438,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         const int p = tid;             // 0..255
         const int c = p & 7;           // the 8 channels this thread computes
         const int r0 = p >> 3;         // rows r0, r0 + 32, ... of the 288 slab rows
-        float w[8][kTaps], bs[8];
+        // the weights and biases of channels (2jj, 2jj + 1) of this thread's 8
+        uint64_t w2[4][kTaps], b2[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            bs[j] = bias1[c * 8 + j];
+        for (int jj = 0; jj < 4; ++jj) {
+            const int c0 = c * 8 + 2 * jj;
+            b2[jj] = f2(bias1[c0], bias1[c0 + 1]);
 #pragma unroll
-            for (int k = 0; k < kTaps; ++k) w[j][k] = __bfloat162float(W1[(c * 8 + j) * kTaps + k]);
+            for (int k = 0; k < kTaps; ++k)
+                w2[jj][k] = f2(__bfloat162float(W1[c0 * kTaps + k]),
+                               __bfloat162float(W1[(c0 + 1) * kTaps + k]));
         }
         // the next trace's inputs are loaded while this one's slab is computed
         float xa = 0.0f, xb = 0.0f;
@@ -444,22 +481,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             // the second one too; the rows outside 0..255 stay zero
 #pragma unroll 2
             for (int q = r0; q < kL1; q += 32) {
-                float xin[kTaps];
+                uint64_t xin[kTaps];
 #pragma unroll
-                for (int k = 0; k < kTaps; ++k) xin[k] = xs[2 * q + k];  // x[2q + k - 2]
+                for (int k = 0; k < kTaps; ++k) {
+                    const float xv = xs[2 * q + k];  // x[2q + k - 2]
+                    xin[k] = f2(xv, xv);
+                }
                 uint32_t pk[4];
 #pragma unroll
-                for (int jj = 0; jj < 8; jj += 2) {
-                    float v[2];
+                for (int jj = 0; jj < 4; ++jj) {
+                    // channels 2jj and 2jj + 1 side by side: sum over the taps
+                    // in order from 0, then the bias, as one FMA chain
+                    uint64_t acc = fma2(w2[jj][0], xin[0], 0ull);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        float acc = 0.0f;
-#pragma unroll
-                        for (int k = 0; k < kTaps; ++k) acc = fmaf(w[jj + h][k], xin[k], acc);
-                        v[h] = acc + bs[jj + h];
-                    }
-                    const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_fast(v[0]), gelu_fast(v[1]));
-                    pk[jj >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
+                    for (int k = 1; k < kTaps; ++k) acc = fma2(w2[jj][k], xin[k], acc);
+                    pk[jj] = gelu2_bf16(add2(acc, b2[jj]));
                 }
                 // q = 32i + 2G - 2 + pl: row 8G + i of plane pl (i < 8), and
                 // row 8(G + 16) + (i - 1) when G < 2 and i > 0
@@ -549,10 +585,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
 #pragma unroll
                     for (int e = 0; e < 16; e += 2) {
                         const int n = half * 32 + qq * 16 + e;
-                        const float a0 = __uint_as_float(v[qq][e]) + __ldg(bias2 + n);
-                        const float a1 = __uint_as_float(v[qq][e + 1]) + __ldg(bias2 + n + 1);
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_fast(a0), gelu_fast(a1));
-                        pk[e >> 1] = *reinterpret_cast<const uint32_t *>(&h2);
+                        pk[e >> 1] = gelu2_bf16(add2(f2(__uint_as_float(v[qq][e]),
+                                                        __uint_as_float(v[qq][e + 1])),
+                                                     f2(__ldg(bias2 + n), __ldg(bias2 + n + 1))));
                     }
                     o4[2 * qq] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     o4[2 * qq + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
@@ -734,10 +769,8 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
             for (int e = 0; e < 16; e += 2) {
                 const int n = q * 16 + e;
-                const float z0 = __uint_as_float(v[e]) + __ldg(bias4 + n);
-                const float z1 = __uint_as_float(v[e + 1]) + __ldg(bias4 + n + 1);
-                const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_fast(z0), gelu_fast(z1));
-                pk[e >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
+                pk[e >> 1] = gelu2_bf16(add2(f2(__uint_as_float(v[e]), __uint_as_float(v[e + 1])),
+                                             f2(__ldg(bias4 + n), __ldg(bias4 + n + 1))));
             }
             // 16 columns = chunks 2(q % 4), +1 of row r in K block q / 4
             uint4 *row = reinterpret_cast<uint4 *>(gbase + (q >> 2) * kFcABytes + r * 128);
