@@ -171,6 +171,14 @@ typedef struct {
                                     to a multiple of 4) */
     uint32_t big_slots;          /* slots per CTA placed for the largest size classes before
                                     the greedy fill of the slot mix (default 1, at most 4) */
+    uint32_t kind_affinity;      /* 0 (default) or 1: each SM of the slot-mix launch starts
+                                    on one kind of unit (set mode x policy, WEIGHTED with
+                                    RANDOM), SMs shared among the kinds by estimated work,
+                                    and keeps to it while it has units, so an SM's warps
+                                    mostly share one kind's code, with one copy of the unit
+                                    loop per kind; 0xFFFFFFFF: every warp takes the
+                                    costliest next unit of any kind, and all kinds share
+                                    one unit loop */
 } pchase_tune;
 
 typedef struct pchase_sim_plan pchase_sim_plan;
@@ -181,8 +189,13 @@ typedef struct pchase_sim_plan pchase_sim_plan;
  * g * n_trace + t.  geoms, traces and pairs are host arrays; the trace index
  * pointers inside `traces` are device pointers used later by pchase_sim_run.
  * Items whose estimated work dominates the batch are split by sets into
- * independent units (sets never interact, so the result is unchanged); units
- * are sorted costliest first into shared-memory size classes served by one
+ * independent units (sets never interact, so the result is unchanged).  In a
+ * plan of explicit pairs that is not a hierarchy's lower level, the parts of
+ * a split item do not each gather their accesses from the whole trace: a pass
+ * before the simulator writes each part's run heads (with their positions,
+ * 8 bytes each, at most one per access of the item) into the workspace, and
+ * the part steps over those; pchase_match_run, and plans of all pairs, gather
+ * instead.  Units are sorted costliest first into shared-memory size classes served by one
  * persistent launch with a per-CTA mix of arenas (S6); units too large for
  * that mix get a second launch on a side stream.  An item whose set state fits
  * no shared-memory arena even split (a cache of many lines, or a line table
@@ -207,9 +220,11 @@ size_t pchase_sim_plan_workspace_bytes(const pchase_sim_plan *plan);
 /* Number of items, and of bitmap words when the plan lays bitmaps out itself. */
 uint64_t pchase_sim_plan_items(const pchase_sim_plan *plan);
 uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);
-/* Kernel launches one pchase_sim_run queues (the output clear, the slot-mix
- * launch and, when the plan has jumbo units, the side launch);
- * pchase_match_run queues one fewer (no output clear). */
+/* Kernel launches one pchase_sim_run queues (the output clear; when the plan
+ * splits items by sets, the three launches of their head streams; the
+ * slot-mix launch; and the side launches of jumbo and pool units, when it has
+ * them); pchase_match_run queues neither the output clear nor the head
+ * streams. */
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
 /*
  * Writes a one-line text description of the plan (items split by sets and
@@ -222,7 +237,7 @@ uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan);
  */
 size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t bytes);
 
-/* One unit of a plan, as pchase_sim_plan_units reports it (host, 48 bytes). */
+/* One unit of a plan, as pchase_sim_plan_units reports it (host, 56 bytes). */
 typedef struct {
     uint32_t item;         /* the caller's item it simulates (part of) */
     uint32_t mode;         /* set mode: 0 way scans, 1 line table, 2 batch */
@@ -234,6 +249,8 @@ typedef struct {
     uint32_t arena_bytes;  /* shared memory the unit needs */
     uint64_t state_offset; /* PCHASE_UNIT_GLOBAL_STATE: offset of its set state in the pool */
     uint64_t state_bytes;  /*   region of the warp that runs it (0), and its size; else 0, 0 */
+    float est_ns;          /* the planner's estimate of its warp time */
+    uint32_t policy;       /* the item's replacement policy (PCHASE_LRU ...) */
 } pchase_unit_info;
 #define PCHASE_UNIT_DIRECT 1u        /* steps over consecutive accesses (no queue) */
 #define PCHASE_UNIT_TIME_PART 2u     /* an LRU item cut in time (rebuilds its start state) */

@@ -31,9 +31,10 @@ KNOBS = {
     "smem_budget_bytes": [64 * 1024, 96 * 1024, 128 * 1024, 160 * 1024, 200 * 1024, 220 * 1024],
     "max_split": [1, 8, 32],
     "big_slots": [1, 2, 3],
+    "kind_affinity": [1, 0xFFFFFFFF],
 }
 DEFAULT = {"batch_max_sets": 64, "scan_max_ways": 4, "max_warps_per_cta": 16,
-           "smem_budget_bytes": 220 * 1024, "max_split": 32, "big_slots": 1}
+           "smem_budget_bytes": 220 * 1024, "max_split": 32, "big_slots": 1, "kind_affinity": 1}
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 

@@ -40,7 +40,8 @@ class Pair(ctypes.Structure):
 class UnitInfo(ctypes.Structure):
     _fields_ = [("item", _c_u32), ("mode", _c_u32), ("parts", _c_u32), ("residue", _c_u32),
                 ("first_step", _c_u32), ("end_step", _c_u32), ("flags", _c_u32),
-                ("arena_bytes", _c_u32), ("state_offset", _c_u64), ("state_bytes", _c_u64)]
+                ("arena_bytes", _c_u32), ("state_offset", _c_u64), ("state_bytes", _c_u64),
+                ("est_ns", ctypes.c_float), ("policy", _c_u32)]
 
 
 UNIT_DIRECT, UNIT_TIME_PART, UNIT_GLOBAL_STATE, UNIT_UNEQUAL, UNIT_LEAD = 1, 2, 4, 8, 16
@@ -50,10 +51,11 @@ class Tune(ctypes.Structure):
     _fields_ = [("scan_max_ways", _c_u32), ("smem_budget_bytes", _c_u32),
                 ("max_warps_per_cta", _c_u32), ("ctas_per_sm_cap", _c_u32),
                 ("batch_max_sets", _c_u32), ("max_split", _c_u32), ("split_cost_ns", _c_u32),
-                ("filtered", _c_u32), ("pool_warps", _c_u32), ("big_slots", _c_u32)]
+                ("filtered", _c_u32), ("pool_warps", _c_u32), ("big_slots", _c_u32),
+                ("kind_affinity", _c_u32)]
 
 
-assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32 and ctypes.sizeof(UnitInfo) == 48
+assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32 and ctypes.sizeof(UnitInfo) == 56
 
 # every exported symbol of include/pchase.h with (restype, argtypes)
 SIGNATURES = {

@@ -109,6 +109,9 @@ constexpr double kStepHeldTableNs = 435.0;
 constexpr double kStepNoHitFifoNs = 1060.0;
 constexpr double kStepNoHitLruNs = 600.0, kNoHitLruSetNs = 480.0;
 constexpr double kGatherNs = 350.0;
+// A step of a split part that reads its heads from its head stream instead
+// (the entries' loads run two steps ahead; the streams' own pass is apart).
+constexpr double kStreamStepNs = 20.0;
 // Way scans over set state in global memory (L2-resident) against shared memory.
 constexpr double kGlobalScanFactor = 2.0;
 // A time part's backward read of 32 accesses while it rebuilds the recency
@@ -122,6 +125,13 @@ constexpr double kPlanSms = 152.0;     // SMs the automatic split target assumes
 constexpr uint64_t kPoolMaxWarps = 608;
 constexpr uint32_t kPoolWarpsPerCta = 4;
 constexpr uint64_t kPoolMaxBytes = 16ull << 30;
+
+// The tuning knobs as the planner reads them, and whether the plan's split
+// parts read head streams (plans of explicit pairs that are not a lower level
+// of a hierarchy; the matcher and filtered runs gather instead).
+struct PlanTune : pchase_tune {
+    bool streams = false;
+};
 
 // What the planner assumes about an item's access stream, from its trace's
 // stride (exact for uniform chains, a hint for explicit traces).
@@ -272,7 +282,7 @@ uint64_t scan_state_bytes(const pchase_geom &G) {
 // the state in global memory (only the queue and staging of a queued unit
 // stay in shared memory).
 void global_unit(const pchase_geom &G, const SimItem &it, const ItemShape &sh,
-                 const pchase_tune &tn, UnitShape &u) {
+                 const PlanTune &tn, UnitShape &u) {
     const uint32_t amax = G.ways + extra_ways(G);
     const int pol = G.policy > PCHASE_RANDOM ? PCHASE_RANDOM : (int)G.policy;
     const double rounds = std::ceil(32.0 / std::min(32.0, std::max(1.0, sh.visited)));
@@ -294,7 +304,7 @@ void global_unit(const pchase_geom &G, const SimItem &it, const ItemShape &sh,
 
 // Set mode, arena and cost of one unit of a K-way split (K = 1: whole).
 bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemShape &sh,
-                const pchase_tune &tn, UnitShape &u) {
+                const PlanTune &tn, UnitShape &u) {
     if (extra_ways(G)) {
         // unequal sets run as way scans (the mode that keeps a way count per
         // set), whole: T sets of a + extra way slots, set 0 using all of them
@@ -401,8 +411,9 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     for (int k = 0; k < n_opt; ++k) {
         const Option &o = opt[k];
         const double direct_cost = cold_chunks * o.cold_ns + (chunks - cold_chunks) * o.warm_ns;
+        const double gather = K > 1 && tn.streams ? steps * kStreamStepNs : chunks * kGatherNs;
         const double queued_cost = cold_steps * o.cold_ns + (steps - cold_steps) * o.warm_ns +
-                                   chunks * kGatherNs;
+                                   gather;
         const bool direct = K == 1 && direct_cost <= queued_cost && !tn.filtered;
         const uint64_t arena = align16(o.arena) + (direct ? 0u : kStageBytes);
         const double cost = direct ? direct_cost : queued_cost;
@@ -517,6 +528,18 @@ struct pchase_sim_plan {
     uint64_t gstate_bytes = 0;  // their state area (workspace, after the pooled offsets)
     size_t off_gstate = 0;
     std::vector<uint32_t> class_caps;  // arena cap of each size class present
+    // head streams of the split items (streams.cu): jobs, each segment's job,
+    // each caller item's first part slot (or ~0), and the sizes of the count,
+    // part and entry arrays
+    std::vector<StreamJob> jobs;
+    std::vector<uint32_t> seg_job, item_slot;
+    uint64_t n_cnt = 0, n_ents = 0;
+    uint32_t n_slots = 0;
+    size_t off_jobs = 0, off_segjob = 0, off_itemslot = 0, off_cnt = 0, off_parts = 0,
+           off_ents = 0;
+    double gwork_main[kUnitGroups] = {};  // estimated work of each unit group in the
+                                          // slot-mix launch
+    bool affinity = false;
     cudaStream_t side = nullptr, side2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
 
@@ -531,6 +554,52 @@ struct pchase_sim_plan {
 };
 
 namespace {
+
+// Unit-group homes of the slot-mix launch: `sites` SMs (CTA b sits on site
+// b mod sites) shared among the groups with work in proportion to their
+// estimated work, at least one each.  Affinity stays off with fewer than two
+// groups, or fewer sites than groups.
+void set_homes(SlotLayout &L, const double *work, bool on, uint32_t sites) {
+    // with affinity, the per-kind unit loops: an SM then holds few kinds' code
+    L.spec = on ? 1u : 0u;
+    L.affinity = 0;
+    L.home_mod = sites;
+    for (int g = 0; g < kUnitGroups; ++g) L.home_end[g] = sites;
+    double total = 0.0;
+    uint32_t with = 0;
+    for (int g = 0; g < kUnitGroups; ++g)
+        if (work[g] > 0.0) {
+            total += work[g];
+            ++with;
+        }
+    if (!on || with < 2 || sites < with) return;
+    uint32_t n[kUnitGroups] = {}, sum = 0;
+    for (int g = 0; g < kUnitGroups; ++g)
+        if (work[g] > 0.0) {
+            n[g] = std::max<uint32_t>(1, (uint32_t)std::lround(sites * work[g] / total));
+            sum += n[g];
+        }
+    while (sum > sites) {  // take from the group with the least work per site that can spare one
+        int best = -1;
+        for (int g = 0; g < kUnitGroups; ++g)
+            if (n[g] > 1 && (best < 0 || work[g] / n[g] < work[best] / n[best])) best = g;
+        --n[best];
+        --sum;
+    }
+    while (sum < sites) {  // give to the group with the most work per site
+        int best = -1;
+        for (int g = 0; g < kUnitGroups; ++g)
+            if (work[g] > 0.0 && (best < 0 || work[g] / n[g] > work[best] / n[best])) best = g;
+        ++n[best];
+        ++sum;
+    }
+    uint32_t end = 0;
+    for (int g = 0; g < kUnitGroups; ++g) {
+        end += n[g];
+        L.home_end[g] = end;
+    }
+    L.affinity = 1;
+}
 
 int plan_runtime(pchase_sim_plan *p) {
     int dev = 0;
@@ -554,6 +623,8 @@ int plan_runtime(pchase_sim_plan *p) {
         if (per <= 0) return fail(PCHASE_ECUDA, "simulator kernel cannot be resident");
         p->grid = (int)std::max<uint64_t>(
             1, std::min<uint64_t>((uint64_t)per * (p->sms - jsms), p->n_units - p->n_jumbo));
+        set_homes(p->layout, p->gwork_main, p->affinity,
+                  (uint32_t)std::max(1, std::min(p->grid, p->sms - jsms)));
     }
     if (p->jumbo.nwarps) {
         const int per = sim_max_ctas_per_sm(p->jumbo);
@@ -579,13 +650,27 @@ int plan_launch(pchase_sim_plan *p, void *ws, const SimOut &out, cudaStream_t st
     int rc = plan_runtime(p);
     if (rc) return rc;
     uint8_t *w = static_cast<uint8_t *>(ws);
-    PCHASE_CUDA(cudaMemsetAsync(w, 0, 256, st), "cudaMemsetAsync(queues)");
+    PCHASE_CUDA(cudaMemsetAsync(w, 0, kQueueHeader, st), "cudaMemsetAsync(queues)");
     SimOut o = out;
-    if (!o.status) o.status = reinterpret_cast<uint32_t *>(w + 128);
+    if (!o.status) o.status = reinterpret_cast<uint32_t *>(w + kStatusOffset);
     o.gstate = w + p->off_gstate;
     const SimItem *items = reinterpret_cast<const SimItem *>(w + p->off_items);
     uint32_t *queues = reinterpret_cast<uint32_t *>(w);
     PCHASE_CUDA(launch_sim_zero(items, p->n_units, p->sms, o, st), "output clear");
+    if (!p->jobs.empty() && !o.dist && !o.filter) {
+        // the split parts' head streams, before any launch that reads them
+        o.item_slot = reinterpret_cast<const uint32_t *>(w + p->off_itemslot);
+        o.parts = reinterpret_cast<const PartInfo *>(w + p->off_parts);
+        o.ents = reinterpret_cast<const uint2 *>(w + p->off_ents);
+        PCHASE_CUDA(launch_streams(items, reinterpret_cast<const StreamJob *>(w + p->off_jobs),
+                                   (uint32_t)p->jobs.size(),
+                                   reinterpret_cast<const uint32_t *>(w + p->off_segjob),
+                                   (uint32_t)p->seg_job.size(),
+                                   reinterpret_cast<uint32_t *>(w + p->off_cnt),
+                                   reinterpret_cast<PartInfo *>(w + p->off_parts),
+                                   reinterpret_cast<uint2 *>(w + p->off_ents), o.status, st),
+                    "head streams");
+    }
     if (p->gpool.nwarps) {
         // units with global set state first (the longest of a hierarchy's
         // large levels), on a side stream of their own joined back below
@@ -655,7 +740,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     *plan_out = nullptr;
     if ((n_geom && !geoms) || (n_trace && !traces) || (n_pairs && !pairs))
         return fail(PCHASE_EINVAL, "NULL descriptor array");
-    pchase_tune tn{4, 220 * 1024, 16, 0, 64, 32, 0, 0, (uint32_t)kPoolMaxWarps, 1};
+    PlanTune tn;
+    static_cast<pchase_tune &>(tn) =
+        pchase_tune{4, 220 * 1024, 16, 0, 64, 32, 0, 0, (uint32_t)kPoolMaxWarps, 1, 1};
     if (tune) {
         if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
@@ -669,7 +756,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         if (tune->pool_warps)
             tn.pool_warps = std::min<uint32_t>(tune->pool_warps, (uint32_t)kPoolMaxWarps);
         if (tune->big_slots) tn.big_slots = std::min<uint32_t>(tune->big_slots, 4);
+        tn.kind_affinity = tune->kind_affinity == 0xFFFFFFFFu ? 0u : 1u;
     }
+    tn.streams = pairs != nullptr && !tn.filtered;
     for (uint32_t i = 0; i < n_geom; ++i) {
         int rc = check_geom(geoms[i], i);
         if (rc) return rc;
@@ -986,6 +1075,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                 it.lead = r == 0;
                 apply_unit(it, best);
                 if (best_k == 1) apply_compact(it, sh);
+                if (best_k > 1 && tn.streams) it.direct = 2;  // reads its head stream
                 it.cost = (float)best.cost;
                 items.push_back(it);
                 cost.push_back(best.cost);
@@ -1050,16 +1140,57 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     for (uint64_t i = 0; i < n_units; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
         if (cls[x] != cls[y]) return cls[x] > cls[y];
+        const uint32_t gx = unit_group(items[x].mode, items[x].policy),
+                       gy = unit_group(items[y].mode, items[y].policy);
+        if (gx != gy) return gx < gy;
         return cost[x] > cost[y];
     });
     p->items.reserve(n_units + gitems.size());
     for (uint64_t k = 0; k < n_units; ++k) p->items.push_back(items[order[k]]);
     // the pool's units after every size class, costliest first
     for (const SimItem &it : gitems) p->items.push_back(it);
+    // head streams: one job per caller item whose parts read them, its K
+    // streams side by side in an entry area as long as its trace
+    try {
+        bool any = false;
+        for (const SimItem &it : p->items) any = any || it.direct == 2;
+        if (any) {
+            p->item_slot.assign(n_items, 0xFFFFFFFFu);
+            uint64_t ent = 0, cntw = 0;
+            uint32_t seg = 0, slot = 0;
+            for (uint64_t k = 0; k < p->items.size(); ++k) {
+                const SimItem &it = p->items[k];
+                if (it.direct != 2 || p->item_slot[it.out_item] != 0xFFFFFFFFu) continue;
+                StreamJob J{};
+                J.ent_base = ent;
+                J.cnt_off = cntw;
+                J.unit = (uint32_t)k;
+                J.K = it.kcnt;
+                J.nseg = (it.len + kSegAccesses - 1) / kSegAccesses;
+                J.seg_first = seg;
+                J.slot_first = slot;
+                p->item_slot[it.out_item] = slot;
+                for (uint32_t s = 0; s < J.nseg; ++s) p->seg_job.push_back((uint32_t)p->jobs.size());
+                p->jobs.push_back(J);
+                ent += it.len;
+                cntw += (uint64_t)J.nseg * J.K;
+                seg += J.nseg;
+                slot += J.K;
+            }
+            p->n_ents = ent;
+            p->n_cnt = cntw;
+            p->n_slots = slot;
+        }
+    } catch (...) {
+        delete p;
+        return fail(PCHASE_ENOMEM, "head stream table allocation");
+    }
     // queues: one per size class, smallest class first
     SlotLayout &L = p->layout;
     memset(&L, 0, sizeof L);
     std::vector<double> work(ncap, 0.0);
+    std::vector<double> gwork[kUnitGroups];
+    for (auto &v : gwork) v.assign(ncap, 0.0);
     int top = -1;
     uint32_t nclass = 0;
     {
@@ -1075,18 +1206,22 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             delete p;
             return fail(PCHASE_ERANGE, "too many size classes");
         }
-        // sorted table is class-descending: find each class's run
+        // sorted table is class-descending, then by group: find each run
         for (uint32_t q = 0; q < nclass; ++q) {
             const int c = present[q];
-            uint64_t first = n_units, count = 0;
-            for (uint64_t k = 0; k < n_units; ++k)
-                if (cls[order[k]] == c) {
-                    if (first == n_units) first = k;
-                    ++count;
-                    work[q] += cost[order[k]];
-                }
-            L.cls_first[q] = (uint32_t)first;
-            L.cls_count[q] = (uint32_t)count;
+            for (uint32_t g = 0; g < (uint32_t)kUnitGroups; ++g) {
+                uint64_t first = n_units, count = 0;
+                for (uint64_t k = 0; k < n_units; ++k)
+                    if (cls[order[k]] == c &&
+                        unit_group(items[order[k]].mode, items[order[k]].policy) == g) {
+                        if (first == n_units) first = k;
+                        ++count;
+                        work[q] += cost[order[k]];
+                        gwork[g][q] += cost[order[k]];
+                    }
+                L.cls_first[g][q] = (uint32_t)(count ? first : 0);
+                L.cls_count[g][q] = (uint32_t)count;
+            }
         }
         L.nclasses = nclass;
         top = (int)nclass - 1;
@@ -1166,23 +1301,26 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         // first-pop stagger: 4 us per slot for plans of long units, a
         // 2000th of the longest unit's estimate below that
         L.stagger_ns = (uint32_t)std::min(4000.0, p->est_max_unit / 2000.0);
+        for (int g = 0; g < kUnitGroups; ++g)
+            for (int q = 0; q <= main_top; ++q) p->gwork_main[g] += gwork[g][q];
+        p->affinity = tn.kind_affinity != 0;
         // jumbo layout: one warp, the largest jumbo arena; serves jumbo classes
         SlotLayout &J = p->jumbo;
         memset(&J, 0, sizeof J);
         J.nclasses = nclass;
-        for (uint32_t q = 0; q < nclass; ++q) {
-            J.cls_first[q] = L.cls_first[q];
-            J.cls_count[q] = L.cls_count[q];
-        }
+        memcpy(J.cls_first, L.cls_first, sizeof J.cls_first);
+        memcpy(J.cls_count, L.cls_count, sizeof J.cls_count);
         if (main_top + 1 < (int)nclass) {
             J.nwarps = 1;
+            J.spec = 1;  // one warp per SM: no other unit's code competes for its cache
             J.warp_class[0] = nclass - 1;
             J.warp_off[0] = 0;
             J.smem_bytes = caps[nclass - 1];
             // the jumbo warp must not steal main classes
             J.pad = (uint32_t)(main_top + 1);
             uint64_t nj = 0;
-            for (uint32_t q = main_top + 1; q < nclass; ++q) nj += L.cls_count[q];
+            for (uint32_t q = main_top + 1; q < nclass; ++q)
+                for (int g = 0; g < kUnitGroups; ++g) nj += L.cls_count[g][q];
             p->n_jumbo = nj;
         }
     }
@@ -1195,8 +1333,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             const uint32_t gc = nclass;  // queue counter of the pool's class
             Gp.nclasses = gc + 1;
             Gp.pad = gc;
-            Gp.cls_first[gc] = (uint32_t)n_units;
-            Gp.cls_count[gc] = (uint32_t)gitems.size();
+            // one queue (group 0's) for all of them, costliest first
+            Gp.cls_first[0][gc] = (uint32_t)n_units;
+            Gp.cls_count[0][gc] = (uint32_t)gitems.size();
             Gp.nwarps = kPoolWarpsPerCta;
             for (uint32_t w = 0; w < kPoolWarpsPerCta; ++w) {
                 Gp.warp_class[w] = gc;
@@ -1206,8 +1345,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             Gp.pool16 = (uint32_t)(p->pool_region >> 4);
         }
     }
-    // workspace: [queues + status: 256][items][geoms][seg offsets][obs word offsets][pool]
-    size_t off = 256;
+    // workspace: [queues + status: kQueueHeader][items][geoms][seg offsets][obs word
+    // offsets][pool]
+    size_t off = kQueueHeader;
     p->off_items = off;
     off = align256(off + p->n_units * sizeof(SimItem));  // size classes and pool
     p->off_geoms = off;
@@ -1220,6 +1360,18 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     off = align256(off + 2 * sizeof(uint64_t));
     p->off_gstate = off;
     off = align256(off + p->gstate_bytes);
+    p->off_jobs = off;
+    off = align256(off + p->jobs.size() * sizeof(StreamJob));
+    p->off_segjob = off;
+    off = align256(off + p->seg_job.size() * sizeof(uint32_t));
+    p->off_itemslot = off;
+    off = align256(off + p->item_slot.size() * sizeof(uint32_t));
+    p->off_cnt = off;
+    off = align256(off + p->n_cnt * sizeof(uint32_t));
+    p->off_parts = off;
+    off = align256(off + (size_t)p->n_slots * sizeof(PartInfo));
+    p->off_ents = off;
+    off = align256(off + p->n_ents * sizeof(uint2));
     p->ws_bytes = off;
     *plan_out = p;
     return PCHASE_OK;
@@ -1236,8 +1388,10 @@ uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan) {
 }
 uint32_t pchase_sim_plan_launches(const pchase_sim_plan *plan) {
     if (!plan) return 0;
-    // output clear + main slot-mix launch + side launch of jumbo units
-    return (plan->n_units ? 1u : 0u) + (plan->layout.nwarps ? 1u : 0u) +
+    // output clear + head streams (offsets; count and write when there are
+    // segments) + main slot-mix launch + side launch of jumbo units + pool
+    return (plan->n_units ? 1u : 0u) + (plan->jobs.empty() ? 0u : 1u) +
+           (plan->seg_job.empty() ? 0u : 2u) + (plan->layout.nwarps ? 1u : 0u) +
            (plan->jumbo.nwarps ? 1u : 0u) + (plan->gpool.nwarps ? 1u : 0u);
 }
 
@@ -1257,10 +1411,12 @@ size_t pchase_sim_plan_units(const pchase_sim_plan *plan, pchase_unit_info *out,
         u.residue = it.kcnt > 1 ? it.kres : 0u;
         u.first_step = tpart ? it.kres : 0u;
         u.end_step = tpart ? it.kmagic : nsteps;
-        u.flags = (it.direct ? PCHASE_UNIT_DIRECT : 0u) | (tpart ? PCHASE_UNIT_TIME_PART : 0u) |
+        u.flags = (it.direct == 1 ? PCHASE_UNIT_DIRECT : 0u) | (tpart ? PCHASE_UNIT_TIME_PART : 0u) |
                   (gm ? PCHASE_UNIT_GLOBAL_STATE : 0u) | (uneq ? PCHASE_UNIT_UNEQUAL : 0u) |
                   (it.lead ? PCHASE_UNIT_LEAD : 0u);
         u.arena_bytes = it.arena_bytes;
+        u.est_ns = it.cost;
+        u.policy = it.policy;
         if (gm) {
             // in the pool region of the warp that runs it, from its start
             u.state_offset = 0;
@@ -1279,7 +1435,7 @@ size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t b
             split += it.kcnt > 1 && it.lead;
             tsplit += it.kcnt == 1 && it.ks1 && it.lead;
             gmem += (it.lsh >> 17) & 1u;
-            direct += it.direct;
+            direct += it.direct == 1;
         }
         char tmp[256];
         snprintf(tmp, sizeof tmp,
@@ -1301,7 +1457,9 @@ size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t b
         }
         d += " class_items=";
         for (uint32_t q = 0; q < plan->layout.nclasses; ++q) {
-            snprintf(tmp, sizeof tmp, "%s%u", q ? "," : "", plan->layout.cls_count[q]);
+            uint32_t n = 0;
+            for (int g = 0; g < kUnitGroups; ++g) n += plan->layout.cls_count[g][q];
+            snprintf(tmp, sizeof tmp, "%s%u", q ? "," : "", n);
             d += tmp;
         }
         // each class's arena cap and its units' summed estimate
@@ -1313,14 +1471,30 @@ size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t b
         d += " class_ms=";
         for (uint32_t q = 0; q < plan->layout.nclasses; ++q) {
             double w = 0.0;
-            for (uint32_t k = 0; k < plan->layout.cls_count[q]; ++k)
-                w += plan->items[plan->layout.cls_first[q] + k].cost;
+            for (int g = 0; g < kUnitGroups; ++g)
+                for (uint32_t k = 0; k < plan->layout.cls_count[g][q]; ++k)
+                    w += plan->items[plan->layout.cls_first[g][q] + k].cost;
             snprintf(tmp, sizeof tmp, "%s%.1f", q ? "," : "", w * 1e-6);
             d += tmp;
         }
         snprintf(tmp, sizeof tmp, " est_ms=%.2f,%.2f,%.2f,%.1f", plan->est_critical * 1e-6,
                  plan->est_target * 1e-6, plan->est_max_unit * 1e-6, plan->est_sum * 1e-6);
         d += tmp;
+        // the slot-mix launch's estimated work per unit group (mode * 3 +
+        // policy) and whether SMs start on a home group
+        d += " group_ms=";
+        for (int g = 0; g < kUnitGroups; ++g) {
+            snprintf(tmp, sizeof tmp, "%s%.1f", g ? "," : "", plan->gwork_main[g] * 1e-6);
+            d += tmp;
+        }
+        snprintf(tmp, sizeof tmp, " affinity=%d", plan->affinity ? 1 : 0);
+        d += tmp;
+        if (!plan->jobs.empty()) {
+            // head streams: split items, their parts, entries (8 bytes each)
+            snprintf(tmp, sizeof tmp, " streams=%zu,%u,%llu", plan->jobs.size(), plan->n_slots,
+                     (unsigned long long)plan->n_ents);
+            d += tmp;
+        }
         if (plan->gpool.nwarps) {
             // the global-state pool: warps (one region each) x region bytes
             snprintf(tmp, sizeof tmp, " pool=%ux%llu", plan->pool_warps,
@@ -1365,6 +1539,20 @@ int pchase_sim_plan_upload(const pchase_sim_plan *plan, void *workspace, size_t 
     const uint64_t pool[2] = {0, plan->total_len};
     PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_pool, pool, sizeof pool, cudaMemcpyHostToDevice, st),
                 "upload pooled offsets");
+    if (!plan->jobs.empty()) {
+        PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_jobs, plan->jobs.data(),
+                                    plan->jobs.size() * sizeof(StreamJob), cudaMemcpyHostToDevice, st),
+                    "upload stream jobs");
+        if (!plan->seg_job.empty())
+            PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_segjob, plan->seg_job.data(),
+                                        plan->seg_job.size() * sizeof(uint32_t),
+                                        cudaMemcpyHostToDevice, st),
+                        "upload stream segments");
+        PCHASE_CUDA(cudaMemcpyAsync(w + plan->off_itemslot, plan->item_slot.data(),
+                                    plan->item_slot.size() * sizeof(uint32_t),
+                                    cudaMemcpyHostToDevice, st),
+                    "upload stream slots");
+    }
     return PCHASE_OK;
 }
 

@@ -119,7 +119,9 @@ struct SimItem {
     uint8_t gs1, gs2, psh, ks1;
     uint32_t kres;        // this unit's residue (0 when not split)
     uint8_t lead;         // 1 on exactly one unit of each caller item
-    uint8_t direct;       // step over consecutive accesses (dense, unsplit), no queue
+    uint8_t direct;       // 1: step over consecutive accesses (dense, unsplit), no queue;
+                          // 2: a part of a split that reads its head stream (when the
+                          // run has streams; else it gathers like 0)
     uint8_t kcnt;         // K: parts of the split (1: whole)
     uint8_t ks2;
     float cost;           // planner's estimate of the unit's warp time (ns)
@@ -146,8 +148,24 @@ constexpr uint32_t kStageBytes = kQueueBytes + kRing * 32 * 4 + kRing * 4;
 // shared-memory arenas ("slots"); a free warp takes, among the classes its
 // slot can hold (pad .. warp_class[w]), the next unit of the class whose next
 // unit has the highest estimated cost (each class queue is costliest first).
+//
+// Units are also grouped by kind (set mode x policy, WEIGHTED with RANDOM,
+// whose code it runs), one queue per group and class.  With affinity on, CTA
+// b starts on the group whose site range [home_end[g - 1], home_end[g]) holds
+// b mod home_mod (the SM it sits on, for CTAs placed round-robin) and keeps
+// to it while its classes have units, so the warps sharing an SM's
+// instruction cache mostly run one kind's code; a warp whose group is out of
+// units takes the costliest next unit of any group and keeps to that group.
+// Without affinity every pop looks at all groups.
 constexpr int kMaxWarpsPerCta = 16;
 constexpr int kMaxClasses = 25;  // size classes + the global-state pool's
+constexpr int kUnitGroups = 9;
+constexpr uint32_t kQueueStride = 32;  // queue counter of (group g, class c): g * 32 + c
+constexpr size_t kQueueHeader = 2048;  // workspace head: the queue counters, then the status word
+constexpr size_t kStatusOffset = 1536;
+__host__ __device__ __forceinline__ uint32_t unit_group(uint32_t mode, uint32_t policy) {
+    return mode * 3u + (policy < 2u ? policy : 2u);
+}
 struct SlotLayout {
     uint32_t nwarps;                          // warps per CTA
     uint32_t nclasses;
@@ -157,10 +175,14 @@ struct SlotLayout {
     uint32_t pool16;                          // global-state pool: warp g = CTA * nwarps + w
                                               // keeps its units' state at g * 16 * pool16
                                               // bytes of the state area (0: no pool)
+    uint32_t spec;                            // 1: per-mode unit loops (units alone on an SM)
+    uint32_t affinity;                        // 1: CTAs start on a home group
+    uint32_t home_mod;                        // CTA b sits on site b mod home_mod
+    uint32_t home_end[kUnitGroups];               // sites [home_end[g-1], home_end[g]) start on g
     uint32_t warp_class[kMaxWarpsPerCta];     // class served first by warp w
     uint32_t warp_off[kMaxWarpsPerCta];       // byte offset of warp w's arena
-    uint32_t cls_first[kMaxClasses];          // first item of class c (sorted table)
-    uint32_t cls_count[kMaxClasses];
+    uint32_t cls_first[kUnitGroups][kMaxClasses]; // first item of (group, class) (sorted table)
+    uint32_t cls_count[kUnitGroups][kMaxClasses];
 };
 
 // Simulation output sinks.
@@ -189,6 +211,36 @@ struct SimOut {
     // set state of the units that keep it in global memory (SimItem lsh bit
     // 17), each at 16 * kres bytes from here
     uint8_t *gstate;
+    // head streams of the parts of items split by sets (SimItem direct = 2):
+    // part k of caller item i reads parts[item_slot[i] + k].len entries
+    // {local line, position} from ents + parts[...].start, in trace order.
+    // NULL: such units gather their heads from the trace themselves.
+    const uint32_t *item_slot;
+    const struct PartInfo *parts;
+    const uint2 *ents;
+};
+
+// Head streams (streams.cu).  Every item split by sets into K parts is one
+// job: its trace is cut into segments of kSegAccesses accesses, one warp per
+// segment counts each part's run heads (an access whose line differs from the
+// previous access's line, falling in the part's sets), a warp per job turns
+// the counts into offsets, and the segments' warps write the heads out, so
+// each part's stream holds exactly the heads the part would gather itself.
+constexpr uint32_t kSegAccesses = 8192;
+struct PartInfo {
+    uint64_t start;  // first entry of the part's stream
+    uint32_t len;    // entries
+    uint32_t pad;
+};
+struct StreamJob {
+    uint64_t ent_base;    // first entry of the item's K streams
+    uint64_t cnt_off;     // counts: cnt_off + segment * K + part
+    uint32_t unit;        // one of the item's units (any part: they share trace and split)
+    uint32_t K;
+    uint32_t nseg;
+    uint32_t seg_first;   // its first segment in the plan's segment list
+    uint32_t slot_first;  // parts[slot_first + k]
+    uint32_t pad;
 };
 
 // Records the text pchase_last_error_string() returns on this thread and
@@ -203,5 +255,9 @@ cudaError_t launch_sim(const SimItem *items, const SlotLayout &layout, uint32_t 
 cudaError_t launch_sim_zero(const SimItem *items, uint64_t n_units, int sms, const SimOut &out,
                             cudaStream_t st);
 int sim_max_ctas_per_sm(const SlotLayout &layout);
+// The head streams of a plan's split items (three launches on `st`).
+cudaError_t launch_streams(const SimItem *items, const StreamJob *jobs, uint32_t n_jobs,
+                           const uint32_t *seg_job, uint32_t n_seg, uint32_t *cnt,
+                           PartInfo *parts, uint2 *ents, uint32_t *status, cudaStream_t st);
 
 }  // namespace pchase

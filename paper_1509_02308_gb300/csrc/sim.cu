@@ -237,6 +237,7 @@ struct TableSets {
 template <typename Sets>
 struct RoundResolver {
     Sets S;
+    __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) { S.bind(arena, it); }
     __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t t,
                                             int lane, uint32_t lt, uint32_t) {
         // only a miss evicts: when every head's line is held at the start of
@@ -1095,50 +1096,66 @@ enum : uint32_t {
     kGlobalScanRandom = 9 + PCHASE_RANDOM,
 };
 
-// One step of heads through the unit's set state.  The state's views are
-// rebuilt from the arena each step (a few integer ops), so that this is the
-// only copy of every mode's code: all modes share one unit loop, which keeps
-// the simulator's hot code within the instruction cache while warps of many
-// different units share an SM.
 // POOL: the kernel of the global-state pool, whose units all keep their set
 // state in global memory (way scans); the other kernel has no such unit, so
 // neither instantiation carries the other's resolvers.
+// Every set mode behind one resolve call.  The state's views are rebuilt
+// from the arena each step (a few integer ops), so all modes share one copy
+// of the unit loop: the form for launches whose warps run units of many
+// kinds side by side, where per-kind copies of the loop would not stay in
+// the instruction cache together.
 template <bool POOL>
-__device__ __forceinline__ bool resolve_step(uint32_t kind, uint8_t *st, uint8_t *gst,
-                                             const SimItem &it, uint32_t line, uint32_t set,
-                                             bool head, uint32_t pos, int lane, uint32_t lt,
-                                             uint32_t step) {
-    if constexpr (POOL) {
+struct AnyResolver {
+    uint8_t *sp;
+    const SimItem *it;
+    uint32_t kind;
+    __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &i) {
+        sp = arena;
+        it = &i;
+        const uint32_t pol = i.policy < 2u ? i.policy : 2u;
+        kind = POOL ? (uint32_t)kGlobalScanLru + pol : (uint32_t)i.mode * 3u + pol;
+    }
+    template <typename R>
+    __device__ __forceinline__ bool run(uint32_t line, uint32_t set, bool head, uint32_t pos,
+                                        int lane, uint32_t lt, uint32_t step) {
+        R r;
+        r.bind(sp, *it);
+        return r.resolve(line, set, head, pos, lane, lt, step);
+    }
+    __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t pos,
+                                            int lane, uint32_t lt, uint32_t step) {
+        if constexpr (POOL) {
+            switch (kind) {
+            case kGlobalScanLru:
+                return run<RoundResolver<ScanSets<PCHASE_LRU>>>(line, set, head, pos, lane, lt, step);
+            case kGlobalScanFifo:
+                return run<RoundResolver<ScanSets<PCHASE_FIFO>>>(line, set, head, pos, lane, lt, step);
+            default:
+                return run<RoundResolver<ScanSets<PCHASE_RANDOM>>>(line, set, head, pos, lane, lt, step);
+            }
+        }
         switch (kind) {
-        case kGlobalScanLru: { RoundResolver<ScanSets<PCHASE_LRU>> R; R.S.bind(gst, it);
-                               return R.resolve(line, set, head, pos, lane, lt, step); }
-        case kGlobalScanFifo: { RoundResolver<ScanSets<PCHASE_FIFO>> R; R.S.bind(gst, it);
-                                return R.resolve(line, set, head, pos, lane, lt, step); }
-        default: { RoundResolver<ScanSets<PCHASE_RANDOM>> R; R.S.bind(gst, it);
-                   return R.resolve(line, set, head, pos, lane, lt, step); }
+        case kScanLru:
+            return run<RoundResolver<ScanSets<PCHASE_LRU>>>(line, set, head, pos, lane, lt, step);
+        case kScanFifo:
+            return run<RoundResolver<ScanSets<PCHASE_FIFO>>>(line, set, head, pos, lane, lt, step);
+        case kScanRandom:
+            return run<RoundResolver<ScanSets<PCHASE_RANDOM>>>(line, set, head, pos, lane, lt, step);
+        case kTableLru:
+            return run<RoundResolver<TableSets<PCHASE_LRU>>>(line, set, head, pos, lane, lt, step);
+        case kTableFifo:
+            return run<RoundResolver<TableSets<PCHASE_FIFO>>>(line, set, head, pos, lane, lt, step);
+        case kTableRandom:
+            return run<RoundResolver<TableSets<PCHASE_RANDOM>>>(line, set, head, pos, lane, lt, step);
+        case kBatchLru:
+            return run<BatchLRU>(line, set, head, pos, lane, lt, step);
+        case kBatchFifo:
+            return run<BatchFR<PCHASE_FIFO>>(line, set, head, pos, lane, lt, step);
+        default:
+            return run<BatchFR<PCHASE_RANDOM>>(line, set, head, pos, lane, lt, step);
         }
     }
-    switch (kind) {
-    case kScanLru: { RoundResolver<ScanSets<PCHASE_LRU>> R; R.S.bind(st, it);
-                     return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kScanFifo: { RoundResolver<ScanSets<PCHASE_FIFO>> R; R.S.bind(st, it);
-                      return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kScanRandom: { RoundResolver<ScanSets<PCHASE_RANDOM>> R; R.S.bind(st, it);
-                        return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kTableLru: { RoundResolver<TableSets<PCHASE_LRU>> R; R.S.bind(st, it);
-                      return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kTableFifo: { RoundResolver<TableSets<PCHASE_FIFO>> R; R.S.bind(st, it);
-                       return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kTableRandom: { RoundResolver<TableSets<PCHASE_RANDOM>> R; R.S.bind(st, it);
-                         return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kBatchLru: { BatchLRU R; R.bind(st, it);
-                      return R.resolve(line, set, head, pos, lane, lt, step); }
-    case kBatchFifo: { BatchFR<PCHASE_FIFO> R; R.bind(st, it);
-                       return R.resolve(line, set, head, pos, lane, lt, step); }
-    default: { BatchFR<PCHASE_RANDOM> R; R.bind(st, it);
-               return R.resolve(line, set, head, pos, lane, lt, step); }
-    }
-}
+};
 
 template <bool POOL>
 __device__ __forceinline__ void clear_state(uint32_t kind, uint8_t *st, uint8_t *gst,
@@ -1179,23 +1196,15 @@ __device__ __forceinline__ bool over_bound(const SimOut &out, uint32_t cand, uin
 
 // One unit: gather trips fill the queue with the unit's run heads, and each
 // step hands the next 32 of them to the unit's set state in trace order.
-template <bool POOL>
-__device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, const SimOut &out,
-                                         int lane) {
-    // arena: [queue + staging ring (units that compact their heads)][set state]
+// The steps of one unit with its set mode's resolver R, bound once to the
+// unit's set state at sp (shared memory, or global memory for the pool).
+template <typename R>
+__device__ __forceinline__ void run_steps(const SimItem &it, uint32_t arena, uint8_t *st,
+                                          uint8_t *sp, uint32_t kind, const SimOut &out,
+                                          int lane) {
     uint2 *const queue = reinterpret_cast<uint2 *>(g_smem + arena);
-    uint8_t *const st = g_smem + arena + (it.direct ? 0u : kStageBytes);
-    // WEIGHTED runs the RANDOM code with its own victim ways
-    const uint32_t pol = it.policy < 2u ? it.policy : 2u;
-    // set state in global memory (lsh bit 17): way scans at 16 * kres bytes
-    // into the plan's state area, owned by this unit alone
-    const bool gmem = POOL;  // the planner puts every global-state unit in the pool
-    uint8_t *const gst = gmem ? out.gstate + 16ull * it.kres : nullptr;
-    const uint32_t kind = gmem ? (uint32_t)kGlobalScanLru + pol : (uint32_t)it.mode * 3u + pol;
-    // matcher: a candidate whose other units already exceed the bound is out
-    if (out.dist && over_bound(out, it.cand, 0, lane)) return;
-    clear_state<POOL>(kind, st, gst, it, lane);
-    __syncwarp();
+    R res;
+    res.bind(sp, it);
     const uint32_t len = it.len;
     const uint32_t *__restrict__ idxp = it.idx;
     const uint32_t N = it.n_elems;
@@ -1240,7 +1249,37 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
         aj = (uint32_t)(((uint64_t)lane * it.stride) % N);
         ainc = (uint32_t)((32ull * it.stride) % N);
     }
-    if (it.direct) {
+    if (it.direct == 2 && out.parts) {
+        // ---- a part of an item split by sets: its heads come gathered, in
+        // trace order, from its head stream; a step takes the next 32 of them
+        // (the grouping a queued unit's steps have), two steps' entries in flight
+        const PartInfo pi = out.parts[out.item_slot[it.out_item] + it.kres];
+        const uint2 *const es = out.ents + pi.start;
+        const uint32_t n = pi.len;
+        const uint2 none = make_uint2(kInvalidLine, 0u);
+        uint2 e1 = (uint32_t)lane < n ? es[lane] : none;
+        uint2 e2 = (uint32_t)lane + 32u < n ? es[lane + 32] : none;
+        uint32_t ccarry = kInvalidLine, step = 0;
+        for (uint32_t b = 0; b < n; b += 32) {
+            const uint2 e = e1;
+            e1 = e2;
+            const uint32_t nx = b + 64u + (uint32_t)lane;
+            e2 = nx < n ? es[nx] : none;
+            const bool act = b + (uint32_t)lane < n;
+            const uint32_t line = e.x, pos = e.y;
+            const uint32_t set = set_of(line * lstep);
+            const uint32_t rot = __shfl_sync(kFull, line, (lane + 31) & 31);
+            const uint32_t prev = lane == 0 ? ccarry : rot;
+            ccarry = rot;
+            const bool head = act && line != prev;
+            ++step;
+            const bool miss = res.resolve(line, set, head, pos, lane, lt, step);
+            const uint32_t bits = __ballot_sync(kFull, miss);
+            tot += __popc(bits);
+            aft += __popc(__ballot_sync(kFull, miss && pos >= warmup));
+            if (bm && bits) emit_bits(bm, pos, miss, act, lane);
+        }
+    } else if (it.direct == 1) {
         // ---- direct: nearly every access is a head, so each step takes 32
         // consecutive accesses as they come (repeats ride along as hits) and
         // the unit, sole writer of its words, stores 32 steps' words at once
@@ -1299,8 +1338,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             const uint32_t prev = lane == 0 ? carry : rot;
             carry = rot;
             const bool head = active && ln != prev;
-            const bool miss =
-                resolve_step<POOL>(kind, st, gst, it, ln, set, head, t, lane, lt, s0 + 1);
+            const bool miss = res.resolve(ln, set, head, t, lane, lt, s0 + 1);
             const uint32_t bits = __ballot_sync(kFull, miss);
             const uint32_t base = s0 << 5;
             const uint32_t after = base >= warmup ? kFull
@@ -1426,8 +1464,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
             ccarry = rot;
             const bool head = act && line != prev;
             ++step;
-            const bool miss =
-                resolve_step<POOL>(kind, st, gst, it, line, set, head, pos, lane, lt, step);
+            const bool miss = res.resolve(line, set, head, pos, lane, lt, step);
             const uint32_t bits = __ballot_sync(kFull, miss);
             tot += __popc(bits);
             aft += __popc(__ballot_sync(kFull, miss && pos >= warmup));
@@ -1458,7 +1495,61 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     }
 }
 
-template <bool POOL>
+// SPEC: one copy of the unit loop per set mode, chosen once per unit (the
+// form for units that run alone on an SM); else AnyResolver's shared loop.
+template <bool POOL, bool SPEC>
+__device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, const SimOut &out,
+                                         int lane) {
+    // arena: [queue + staging ring (units that compact their heads)][set state]
+    uint8_t *const st = g_smem + arena + (it.direct == 1 ? 0u : kStageBytes);
+    // WEIGHTED runs the RANDOM code with its own victim ways
+    const uint32_t pol = it.policy < 2u ? it.policy : 2u;
+    // set state in global memory (lsh bit 17): way scans at 16 * kres bytes
+    // into the plan's state area, owned by this unit alone
+    const bool gmem = POOL;  // the planner puts every global-state unit in the pool
+    uint8_t *const gst = gmem ? out.gstate + 16ull * it.kres : nullptr;
+    const uint32_t kind = gmem ? (uint32_t)kGlobalScanLru + pol : (uint32_t)it.mode * 3u + pol;
+    // matcher: a candidate whose other units already exceed the bound is out
+    if (out.dist && over_bound(out, it.cand, 0, lane)) return;
+    clear_state<POOL>(kind, st, gst, it, lane);
+    __syncwarp();
+    if constexpr (!SPEC) {
+        return run_steps<AnyResolver<POOL>>(it, arena, st, POOL ? gst : st, kind, out, lane);
+    }
+    // one dispatch per unit: every step then calls its resolver directly
+    if constexpr (POOL) {
+        switch (kind) {
+        case kGlobalScanLru:
+            return run_steps<RoundResolver<ScanSets<PCHASE_LRU>>>(it, arena, st, gst, kind, out, lane);
+        case kGlobalScanFifo:
+            return run_steps<RoundResolver<ScanSets<PCHASE_FIFO>>>(it, arena, st, gst, kind, out, lane);
+        default:
+            return run_steps<RoundResolver<ScanSets<PCHASE_RANDOM>>>(it, arena, st, gst, kind, out, lane);
+        }
+    }
+    switch (kind) {
+    case kScanLru:
+        return run_steps<RoundResolver<ScanSets<PCHASE_LRU>>>(it, arena, st, st, kind, out, lane);
+    case kScanFifo:
+        return run_steps<RoundResolver<ScanSets<PCHASE_FIFO>>>(it, arena, st, st, kind, out, lane);
+    case kScanRandom:
+        return run_steps<RoundResolver<ScanSets<PCHASE_RANDOM>>>(it, arena, st, st, kind, out, lane);
+    case kTableLru:
+        return run_steps<RoundResolver<TableSets<PCHASE_LRU>>>(it, arena, st, st, kind, out, lane);
+    case kTableFifo:
+        return run_steps<RoundResolver<TableSets<PCHASE_FIFO>>>(it, arena, st, st, kind, out, lane);
+    case kTableRandom:
+        return run_steps<RoundResolver<TableSets<PCHASE_RANDOM>>>(it, arena, st, st, kind, out, lane);
+    case kBatchLru:
+        return run_steps<BatchLRU>(it, arena, st, st, kind, out, lane);
+    case kBatchFifo:
+        return run_steps<BatchFR<PCHASE_FIFO>>(it, arena, st, st, kind, out, lane);
+    default:
+        return run_steps<BatchFR<PCHASE_RANDOM>>(it, arena, st, st, kind, out, lane);
+    }
+}
+
+template <bool POOL, bool SPEC>
 __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ items,
                                                   const __grid_constant__ SlotLayout L,
                                                   uint32_t *queues, SimOut out) {
@@ -1466,13 +1557,26 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
     const int warp = threadIdx.x >> 5;
     const uint32_t arena = L.warp_off[warp];
     const uint32_t top = L.warp_class[warp];
-    // class this lane watches (pad + lane <= top)
+    // class this lane watches (pad + lane <= top), in every group
     const uint32_t wc = L.pad + (uint32_t)lane;
     const bool watch = wc <= top && wc < L.nclasses;
     const uint32_t nrep = out.n_rep ? out.n_rep : 1u;
-    const uint32_t cnt = (watch ? L.cls_count[wc] : 0u) * nrep;
-    const uint32_t first = watch ? L.cls_first[wc] : 0u;
     const bool prune = out.dist != nullptr && out.stop_above != ~0ull;
+    // this warp's group: the CTA's home group with affinity, else none
+    uint32_t grp = kUnitGroups;
+    if (L.affinity) {
+        const uint32_t site = blockIdx.x % L.home_mod;
+        grp = 0;
+        while (grp + 1 < (uint32_t)kUnitGroups && site >= L.home_end[grp]) ++grp;
+    }
+    // the cost of the next unit of (g, this lane's class) as an ordered key, 0: none
+    auto head_key = [&](uint32_t g) -> uint32_t {
+        if (!watch) return 0u;
+        const uint32_t h = *reinterpret_cast<volatile uint32_t *>(queues + g * kQueueStride + wc);
+        return h < L.cls_count[g][wc] * nrep
+                   ? __float_as_uint(fmaxf(items[L.cls_first[g][wc] + h / nrep].cost, 1.0f))
+                   : 0u;
+    };
     // First pops staggered by slot (up to 4 us apart, a bounded sleep; the
     // planner scales it to the plan's longest unit): slot 0 of every CTA,
     // which holds every class, takes the costliest units first, one per SM,
@@ -1480,25 +1584,37 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
     // of the long units side by side.
     if (warp > 0 && L.stagger_ns) __nanosleep(L.stagger_ns * (uint32_t)warp);
     for (;;) {
-        // longest first: the class whose next unit costs most
-        uint32_t key = 0;
-        if (watch) {
-            const uint32_t h = *reinterpret_cast<volatile uint32_t *>(queues + wc);
-            if (h < cnt) key = __float_as_uint(fmaxf(items[first + h / nrep].cost, 1.0f));
+        // longest first: the class whose next unit costs most, in this warp's
+        // group while it has one for this slot, else in any group
+        uint32_t key = 0, kg = grp;
+        if (grp < (uint32_t)kUnitGroups) key = head_key(grp);
+        uint32_t kmax = __reduce_max_sync(kFull, key);
+        if (kmax == 0) {
+            for (uint32_t g = 0; g < (uint32_t)kUnitGroups; ++g) {
+                const uint32_t k = head_key(g);
+                if (k > key) {
+                    key = k;
+                    kg = g;
+                }
+            }
+            kmax = __reduce_max_sync(kFull, key);
+            if (kmax == 0) break;  // every class this slot can hold is done
         }
-        const uint32_t kmax = __reduce_max_sync(kFull, key);
-        if (kmax == 0) break;  // every class this slot can hold is done
         const int src = __ffs(__ballot_sync(kFull, key == kmax)) - 1;
+        const uint32_t g = __shfl_sync(kFull, kg, src);
+        if (L.affinity) grp = g;
         const uint32_t c = L.pad + (uint32_t)src;
-        const uint32_t cper = L.cls_count[c];
+        const uint32_t cfirst = L.cls_first[g][c];
+        const uint32_t cper = L.cls_count[g][c];
         const uint32_t total = cper * nrep;
+        uint32_t *const queue = queues + g * kQueueStride + c;
         // matcher with a bound over several observations: take up to 32 queue
         // entries at once (unit-major, so one unit for up to 32 observations),
         // screen them against their candidates' distances in parallel and run
         // only the survivors (most entries belong to candidates already out)
         const uint32_t grab = prune ? (nrep < 32u ? nrep : 32u) : 1u;
         uint32_t k0 = 0;
-        if (lane == src) k0 = atomicAdd(queues + c, grab);
+        if (lane == src) k0 = atomicAdd(queue, grab);
         k0 = __shfl_sync(kFull, k0, src);
         if (k0 >= total) continue;  // taken meanwhile: look again
         uint32_t todo = 1u;
@@ -1507,7 +1623,7 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
             bool alive = false;
             if (lane < (int)grab && kk < total) {
                 const uint32_t uu = kk / nrep, rr = kk - uu * nrep;
-                const uint32_t cand = items[L.cls_first[c] + uu].cand;
+                const uint32_t cand = items[cfirst + uu].cand;
                 const unsigned long long d = *reinterpret_cast<volatile const unsigned long long *>(
                     out.dist + rr * out.rep_dist_stride + cand);
                 alive = d <= out.stop_above;
@@ -1520,7 +1636,7 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
             // unit-major: each unit runs for every observation in turn, so the
             // costliest (most discriminating) units come first for all of them
             const uint32_t u = k / nrep, rep = k - u * nrep;
-            const SimItem it = items[L.cls_first[c] + u];
+            const SimItem it = items[cfirst + u];
             SimOut o = out;
             if (L.pool16)  // global set state: this warp's region of the pool
                 o.gstate = out.gstate + ((uint64_t)blockIdx.x * L.nwarps + (uint32_t)warp) *
@@ -1531,7 +1647,7 @@ __global__ void __launch_bounds__(512) sim_kernel(const SimItem *__restrict__ it
             }
             uint64_t t_start = 0;
             if (out.timeline) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
-            run_unit<POOL>(it, arena, o, lane);
+            run_unit<POOL, SPEC>(it, arena, o, lane);
             __syncwarp();
             if (out.timeline && lane == 0) {
                 // units of a split item share the entry: first start, last end
@@ -1576,8 +1692,10 @@ __global__ void __launch_bounds__(256) sim_zero_kernel(const SimItem *__restrict
 
 cudaError_t launch_sim(const SimItem *items, const SlotLayout &layout, uint32_t *queues, int grid,
                        const SimOut &out, cudaStream_t st) {
-    // the pool's layout (pool16 set) runs the global-state instantiation
-    const auto k = layout.pool16 ? sim_kernel<true> : sim_kernel<false>;
+    // the pool's layout (pool16 set) runs the global-state instantiation; a
+    // layout with spec set, the per-mode unit loops
+    const auto k = layout.pool16 ? sim_kernel<true, false>
+                                 : layout.spec ? sim_kernel<false, true> : sim_kernel<false, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)layout.smem_bytes);
     if (e != cudaSuccess) return e;
@@ -1594,11 +1712,12 @@ cudaError_t launch_sim_zero(const SimItem *items, uint64_t n_units, int sms, con
 }
 
 int sim_max_ctas_per_sm(const SlotLayout &layout) {
-    if (cudaFuncSetAttribute(sim_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const auto k = layout.spec ? sim_kernel<false, true> : sim_kernel<false, false>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)layout.smem_bytes) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_kernel<false>, layout.nwarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, layout.nwarps * 32,
                                                       layout.smem_bytes) != cudaSuccess)
         return 0;
     return n;

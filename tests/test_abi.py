@@ -306,7 +306,7 @@ def _units_hold_invariants(h, lens):
                 assert u.state_bytes == 0
     # the workspace holds the queues, the whole unit table (112 bytes a unit,
     # the pool's units included) and the pool
-    assert L.pchase_sim_plan_workspace_bytes(h) >= 256 + 112 * len(units) + pool_bytes
+    assert L.pchase_sim_plan_workspace_bytes(h) >= 512 + 112 * len(units) + pool_bytes
     if pool_bytes:
         assert pool_bytes <= min(L.pchase_sim_plan_workspace_bytes(h), 16 << 30)
         # the pool's units run last in the unit table, after every size class

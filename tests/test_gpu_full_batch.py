@@ -1,9 +1,10 @@
 """Bit-exact parity of the whole batched-simulation workload (4096 seeded
 items, 0.64 G accesses, every item at full length) with the CPU oracle,
 under the plan the benchmark times (the shipped autotuned knobs), under the
-default knobs, and under two plans that move many items to other set modes
-and split long items far more often.  Every item's miss bitmap is compared
-access by access, and both of its miss counts (Assumptions 1-3, Sec. 4.1;
+default knobs, under two plans that move many items to other set modes and
+split long items far more often, and with every kind of unit mixed on every
+SM in one shared unit loop.  Every item's miss bitmap is compared access by
+access, and both of its miss counts (Assumptions 1-3, Sec. 4.1;
 LRU, FIFO and the RANDOM reading).  The oracle runs one item per host
 thread, once per item for all plans."""
 import os
@@ -48,7 +49,9 @@ def test_config2_whole_batch_bit_exact_under_the_timed_plan():
                 "scans": {"batch_max_sets": 0xFFFFFFFF, "scan_max_ways": 16, "max_split": 8},
                 # batch mode at any set count, and every item above 2 ms of
                 # estimated warp time split by sets or cut in time
-                "splits": {"batch_max_sets": 1 << 30, "split_cost_ns": 2_000_000}}
+                "splits": {"batch_max_sets": 1 << 30, "split_cost_ns": 2_000_000},
+                # every warp on any kind's queue, all kinds in one shared unit loop
+                "shared_loop": dict(timed, kind_affinity=0xFFFFFFFF)}
     results = {k: _run(geoms, traces, pairs, v) for k, v in variants.items()}
     del traces, flat
     torch.cuda.empty_cache()
