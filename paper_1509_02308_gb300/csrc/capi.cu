@@ -107,7 +107,7 @@ constexpr double kStepHeldTableNs = 435.0;
 // A batch step whose sets are each all hits or all misses (LRU / FIFO over
 // cyclic streams): FIFO, and LRU plus a cost per set in the step.
 constexpr double kStepNoHitFifoNs = 1060.0;
-constexpr double kStepNoHitLruNs = 600.0, kNoHitLruSetNs = 480.0;
+constexpr double kStepNoHitLruNs = 900.0, kNoHitLruSetNs = 720.0;
 constexpr double kGatherNs = 350.0;
 // A step of a split part that reads its heads from its head stream instead
 // (the entries' loads run two steps ahead; the streams' own pass is apart).

@@ -287,6 +287,7 @@ struct RoundResolver {
 struct Grouped {
     uint32_t x, set;   // line and set of the head now on this lane
     bool act;          // lane holds a head
+    bool same;         // no head moved (every lane holds its own)
     uint32_t gmask;    // lanes of this head's set group
     uint32_t gb;       // first lane of the group
     uint32_t dest;     // where this lane's own head went
@@ -306,6 +307,7 @@ __device__ __forceinline__ Grouped group_heads(uint32_t line, uint32_t set, bool
         g.gmask = hb;
         g.gb = 0;
         g.dest = (uint32_t)lane;
+        g.same = true;
         return g;
     }
     const uint32_t key = head ? set : (0x80000000u | (uint32_t)lane);
@@ -333,6 +335,7 @@ __device__ __forceinline__ Grouped group_heads(uint32_t line, uint32_t set, bool
     g.gmask = __match_any_sync(kFull, act ? g.set : (0x80000000u | (uint32_t)lane));
     g.gb = __ffs(g.gmask) - 1;
     g.dest = dest;
+    g.same = false;
     return g;
 }
 
@@ -375,6 +378,10 @@ struct BatchFR {
     uint64_t seed;
     bool wtd;
     uint32_t psh, kcnt, kres;
+    // steps left before the pure-set test is tried again: a unit whose steps
+    // are not pure (hits and misses in one set) skips it for a while (bound
+    // once per unit, the count lives across its steps)
+    uint32_t pure_skip = 0;
 
     __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &it) {
         ways = it.ways;
@@ -466,15 +473,16 @@ struct BatchFR {
         // the step, all of them hit and nothing changes.
         const uint32_t w0 = head ? tab[line] : 1u;
         if (__all_sync(kFull, w0 != 0u)) return false;
-        {
+        const uint32_t lm0 = __match_any_sync(kFull, head ? line : (0x80000000u | (uint32_t)lane));
+        if (pure_skip) {
+            --pure_skip;
+        } else {
             // Pure sets: in a group where no head can hit all miss; a group
             // whose heads all hold their lines all hits.  If every earlier
             // head of its group misses, a first use misses when its line is
             // not held or (FIFO) is pushed out by those misses, and a repeat
             // (FIFO) when at least a misses of its set came since its previous
             // use.  RANDOM takes only groups of new lines not held.
-            const uint32_t lm0 =
-                __match_any_sync(kFull, head ? line : (0x80000000u | (uint32_t)lane));
             const uint32_t sm0 =
                 __match_any_sync(kFull, head ? set : (0x80000000u | (uint32_t)lane));
             const uint32_t pm0 = lm0 & lt;
@@ -497,14 +505,16 @@ struct BatchFR {
             const bool gheld = head && (hbal & sm0) == sm0;
             if (__all_sync(kFull, !head || gheld || (nbal & sm0) == sm0))
                 return fresh_step(line, set, head && !gheld, lane, lt, sm0);
+            pure_skip = 7;
         }
         const Grouped g = group_heads(line, set, head, lane, lt, perm);
         const uint32_t a = ways;
         const uint32_t ltg = g.gmask & lt;
         const uint32_t r = (uint32_t)lane - g.gb;
         const uint4 m = g.act ? meta[g.set] : make_uint4(0, 0, 0, 0);
-        const uint32_t w1 = g.act ? tab[g.x] : 0u;
-        const uint32_t lm = __match_any_sync(kFull, g.act ? g.x : (0x80000000u | (uint32_t)lane));
+        const uint32_t w1 = !g.act ? 0u : g.same ? w0 : tab[g.x];
+        const uint32_t lm =
+            g.same ? lm0 : __match_any_sync(kFull, g.act ? g.x : (0x80000000u | (uint32_t)lane));
         const uint32_t pm = lm & lt;
         const int prev = pm ? 31 - __clz(pm) : -1;
         // way of the group's r-th miss, and whether it evicts
