@@ -169,8 +169,8 @@ class ClockSampler:
 # From one ncu capture (--set full) of the current sim_kernel on the batched
 # workload with items capped at 65,536 accesses: the slot-mix launch and the
 # one-warp launch of one run, summed.
-SIM_DRAM_BYTES_PER_ACCESS = (264.532224e6 + 7.433216e6 + 2.598144e6) / 65559830
-SIM_WARP_INST_PER_ACCESS = (444888722 + 9218020) / 65559830
+SIM_DRAM_BYTES_PER_ACCESS = (279.363584e6 + 8.221440e6 + 2.172160e6) / 65559830
+SIM_WARP_INST_PER_ACCESS = (351888331 + 3918992) / 65559830
 # Algorithmic work of one simulated access in the warp-per-set mapping: the
 # decode (line, set and tag by shift and multiply-high), one warp-wide tag
 # compare (ballot / match), the replacement-state update and the miss bit,
@@ -524,6 +524,13 @@ def e2e_run(args, geoms, runs, dev, world):
     args_ = (ctypes.addressof(ga), n, ctypes.addressof(tdescs), n, ctypes.addressof(pa), n,
              C.ptr(bitmaps), C.ptr(d_words), C.ptr(counts), None)
     L.cache_sim_batch(*args_, None, ctypes.byref(need), None)
+    # what one call copies to the device: the plan's tables (cache_sim_batch
+    # plans with the default knobs, as this plan does)
+    hp = ctypes.c_void_p()
+    C.check(L.pchase_sim_plan_create(ctypes.addressof(ga), n, ctypes.addressof(tdescs), n,
+                                     ctypes.addressof(pa), n, None, ctypes.byref(hp)))
+    upload = int(L.pchase_sim_plan_upload_bytes(hp))
+    L.pchase_sim_plan_destroy(hp)
     ws = torch.empty(need.value + 256, dtype=torch.uint8, device=dev)
     wp = (C.ptr(ws) + 255) & ~255
     st = torch.cuda.current_stream()
@@ -545,8 +552,7 @@ def e2e_run(args, geoms, runs, dev, world):
         one()
     dt = (time.perf_counter() - t0) / k
     total = int(offs[-1])
-    h2d = n * (ctypes.sizeof(C.Geom) + ctypes.sizeof(C.Trace) + ctypes.sizeof(C.Pair)) + \
-        need.value + n * 24
+    h2d = upload + n * 24
     d2h = int(words[-1]) * 4 + 2 * n * 8
     return {"value": total * world / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3,

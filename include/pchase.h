@@ -179,6 +179,10 @@ typedef struct {
                                     loop per kind; 0xFFFFFFFF: every warp takes the
                                     costliest next unit of any kind, and all kinds share
                                     one unit loop */
+    uint32_t head_streams;       /* 0 (default) or 1: in a plan of explicit pairs that is not
+                                    filtered, the parts of items split by sets read head
+                                    streams written by a pass before the simulator;
+                                    0xFFFFFFFF: every part gathers its heads itself */
 } pchase_tune;
 
 typedef struct pchase_sim_plan pchase_sim_plan;
@@ -217,6 +221,9 @@ void pchase_sim_plan_destroy(pchase_sim_plan *plan);
 
 /* Bytes of device workspace pchase_sim_run needs for this plan. */
 size_t pchase_sim_plan_workspace_bytes(const pchase_sim_plan *plan);
+/* Bytes pchase_sim_plan_upload copies from the host (the plan's tables; the
+ * rest of the workspace is written on the device). */
+size_t pchase_sim_plan_upload_bytes(const pchase_sim_plan *plan);
 /* Number of items, and of bitmap words when the plan lays bitmaps out itself. */
 uint64_t pchase_sim_plan_items(const pchase_sim_plan *plan);
 uint64_t pchase_sim_plan_bitmap_words(const pchase_sim_plan *plan);

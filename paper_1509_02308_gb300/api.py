@@ -74,7 +74,7 @@ class SimPlan:
                         tune.get("batch_max_sets", 0), tune.get("max_split", 0),
                         tune.get("split_cost_ns", 0), tune.get("filtered", 0),
                         tune.get("pool_warps", 0), tune.get("big_slots", 0),
-                        tune.get("kind_affinity", 0))
+                        tune.get("kind_affinity", 0), tune.get("head_streams", 0))
         h = ctypes.c_void_p()
         C.check(self.L.pchase_sim_plan_create(
             ctypes.addressof(ga), len(self.geoms), ctypes.addressof(ta), len(self.traces),

@@ -52,7 +52,7 @@ class Tune(ctypes.Structure):
                 ("max_warps_per_cta", _c_u32), ("ctas_per_sm_cap", _c_u32),
                 ("batch_max_sets", _c_u32), ("max_split", _c_u32), ("split_cost_ns", _c_u32),
                 ("filtered", _c_u32), ("pool_warps", _c_u32), ("big_slots", _c_u32),
-                ("kind_affinity", _c_u32)]
+                ("kind_affinity", _c_u32), ("head_streams", _c_u32)]
 
 
 assert ctypes.sizeof(Geom) == 32 and ctypes.sizeof(Trace) == 32 and ctypes.sizeof(UnitInfo) == 56
@@ -65,6 +65,7 @@ SIGNATURES = {
                                               ctypes.POINTER(_c_p)]),
     "pchase_sim_plan_destroy": (None, [_c_p]),
     "pchase_sim_plan_workspace_bytes": (ctypes.c_size_t, [_c_p]),
+    "pchase_sim_plan_upload_bytes": (ctypes.c_size_t, [_c_p]),
     "pchase_sim_plan_items": (_c_u64, [_c_p]),
     "pchase_sim_plan_bitmap_words": (_c_u64, [_c_p]),
     "pchase_sim_plan_launches": (_c_u32, [_c_p]),

@@ -112,6 +112,13 @@ constexpr double kGatherNs = 350.0;
 // A step of a split part that reads its heads from its head stream instead
 // (the entries' loads run two steps ahead; the streams' own pass is apart).
 constexpr double kStreamStepNs = 20.0;
+// Only items at least this long get head streams: below it the pass's own
+// cost and the extra parts it invites outweigh the gathering it saves.
+constexpr uint32_t kStreamMinLen = 1u << 18;
+// SMs keep to one kind of unit only when the slot-mix launch holds at least
+// this much estimated work per SM (ns): a short batch gains less from a warm
+// instruction cache than it loses to the kinds' uneven shares of SMs.
+constexpr double kAffinityMinNsPerSm = 20.0e6;
 // Way scans over set state in global memory (L2-resident) against shared memory.
 constexpr double kGlobalScanFactor = 2.0;
 // A time part's backward read of 32 accesses while it rebuilds the recency
@@ -411,7 +418,9 @@ bool unit_shape(const pchase_geom &G, const SimItem &it, uint32_t K, const ItemS
     for (int k = 0; k < n_opt; ++k) {
         const Option &o = opt[k];
         const double direct_cost = cold_chunks * o.cold_ns + (chunks - cold_chunks) * o.warm_ns;
-        const double gather = K > 1 && tn.streams ? steps * kStreamStepNs : chunks * kGatherNs;
+        const double gather = K > 1 && tn.streams && it.len >= kStreamMinLen
+                                  ? steps * kStreamStepNs
+                                  : chunks * kGatherNs;
         const double queued_cost = cold_steps * o.cold_ns + (steps - cold_steps) * o.warm_ns +
                                    gather;
         const bool direct = K == 1 && direct_cost <= queued_cost && !tn.filtered;
@@ -557,8 +566,9 @@ namespace {
 
 // Unit-group homes of the slot-mix launch: `sites` SMs (CTA b sits on site
 // b mod sites) shared among the groups with work in proportion to their
-// estimated work, at least one each.  Affinity stays off with fewer than two
-// groups, or fewer sites than groups.
+// estimated work, at least one each.  Affinity (and with it the per-kind
+// unit loops) stays off with fewer than two groups, fewer sites than groups,
+// or under kAffinityMinNsPerSm of work per site.
 void set_homes(SlotLayout &L, const double *work, bool on, uint32_t sites) {
     // with affinity, the per-kind unit loops: an SM then holds few kinds' code
     L.spec = on ? 1u : 0u;
@@ -572,7 +582,10 @@ void set_homes(SlotLayout &L, const double *work, bool on, uint32_t sites) {
             total += work[g];
             ++with;
         }
-    if (!on || with < 2 || sites < with) return;
+    if (!on || with < 2 || sites < with || total < kAffinityMinNsPerSm * sites) {
+        L.spec = 0;
+        return;
+    }
     uint32_t n[kUnitGroups] = {}, sum = 0;
     for (int g = 0; g < kUnitGroups; ++g)
         if (work[g] > 0.0) {
@@ -742,7 +755,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         return fail(PCHASE_EINVAL, "NULL descriptor array");
     PlanTune tn;
     static_cast<pchase_tune &>(tn) =
-        pchase_tune{4, 220 * 1024, 16, 0, 64, 32, 0, 0, (uint32_t)kPoolMaxWarps, 1, 1};
+        pchase_tune{4, 220 * 1024, 16, 0, 64, 32, 0, 0, (uint32_t)kPoolMaxWarps, 1, 1, 1};
     if (tune) {
         if (tune->batch_max_sets) tn.batch_max_sets = tune->batch_max_sets == 0xFFFFFFFFu ? 0 : tune->batch_max_sets;
         if (tune->scan_max_ways) tn.scan_max_ways = std::min<uint32_t>(tune->scan_max_ways, 32);
@@ -757,8 +770,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             tn.pool_warps = std::min<uint32_t>(tune->pool_warps, (uint32_t)kPoolMaxWarps);
         if (tune->big_slots) tn.big_slots = std::min<uint32_t>(tune->big_slots, 4);
         tn.kind_affinity = tune->kind_affinity == 0xFFFFFFFFu ? 0u : 1u;
+        tn.head_streams = tune->head_streams == 0xFFFFFFFFu ? 0u : 1u;
     }
-    tn.streams = pairs != nullptr && !tn.filtered;
+    tn.streams = pairs != nullptr && !tn.filtered && tn.head_streams;
     for (uint32_t i = 0; i < n_geom; ++i) {
         int rc = check_geom(geoms[i], i);
         if (rc) return rc;
@@ -1075,7 +1089,8 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
                 it.lead = r == 0;
                 apply_unit(it, best);
                 if (best_k == 1) apply_compact(it, sh);
-                if (best_k > 1 && tn.streams) it.direct = 2;  // reads its head stream
+                if (best_k > 1 && tn.streams && it.len >= kStreamMinLen)
+                    it.direct = 2;  // reads its head stream
                 it.cost = (float)best.cost;
                 items.push_back(it);
                 cost.push_back(best.cost);
@@ -1378,6 +1393,17 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
 }
 
 void pchase_sim_plan_destroy(pchase_sim_plan *plan) { delete plan; }
+
+size_t pchase_sim_plan_upload_bytes(const pchase_sim_plan *plan) {
+    if (!plan) return 0;
+    return plan->items.size() * sizeof(SimItem) + plan->geoms.size() * sizeof(pchase_geom) +
+           plan->seg_offsets.size() * sizeof(uint64_t) +
+           plan->obs_word_offsets.size() * sizeof(uint64_t) + 2 * sizeof(uint64_t) +
+           (plan->jobs.empty() ? 0
+                               : plan->jobs.size() * sizeof(StreamJob) +
+                                     plan->seg_job.size() * sizeof(uint32_t) +
+                                     plan->item_slot.size() * sizeof(uint32_t));
+}
 
 size_t pchase_sim_plan_workspace_bytes(const pchase_sim_plan *plan) {
     return plan ? plan->ws_bytes : 0;

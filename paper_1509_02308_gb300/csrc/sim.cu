@@ -546,21 +546,25 @@ struct BatchFR {
                 e0 = q.x == stamp ? (int32_t)q.y : kBig;
             }
         }
-        // fixed point over (miss, eviction index after this access)
+        // Fixed point over the miss vector.  Before access i its line's way
+        // is next evicted at the group rank nx(rho) if an earlier access of
+        // the line missed, rho the miss rank of the last such one (a hit
+        // moves nothing), else at e0; i misses when more misses precede it
+        // in its group than that rank.  Every lane reads its line's last
+        // earlier miss from the current vector, so a run of repeats settles
+        // in one round.
         bool miss = g.act && (w1 == 0 ? prev < 0 : e0 < (int32_t)r);
-        int32_t eaft = miss ? kBig : e0;
+        const uint32_t lme = lm & lt;  // earlier lanes of this lane's line
         for (int it = 0; it < 33; ++it) {
             const uint32_t bal = __ballot_sync(kFull, miss);
             const int32_t mi = __popc(bal & ltg);
-            const int32_t pe = __shfl_sync(kFull, eaft, prev < 0 ? lane : prev);
-            const int32_t epre = prev < 0 ? e0 : pe;
-            const bool nm = g.act && mi > epre;
+            // where a line this lane inserted would be evicted next
             const int32_t nxm = __shfl_sync(kFull, nx, (g.gb + (uint32_t)mi) & 31u);
-            const int32_t ne = nm ? nxm : epre;
-            const bool same = nm == miss && ne == eaft;
+            const uint32_t pmiss = lme & bal;
+            const int32_t pe = __shfl_sync(kFull, nxm, pmiss ? 31 - __clz(pmiss) : lane);
+            const bool nm = g.act && mi > (pmiss ? pe : e0);
+            if (__all_sync(kFull, nm == miss)) break;
             miss = nm;
-            eaft = ne;
-            if (__all_sync(kFull, same)) break;
         }
         // state update
         const uint32_t bal = __ballot_sync(kFull, miss);

@@ -2,8 +2,9 @@
 items, 0.64 G accesses, every item at full length) with the CPU oracle,
 under the plan the benchmark times (the shipped autotuned knobs), under the
 default knobs, under two plans that move many items to other set modes and
-split long items far more often, and with every kind of unit mixed on every
-SM in one shared unit loop.  Every item's miss bitmap is compared access by
+split long items far more often, with every kind of unit mixed on every SM
+in one shared unit loop, and with split parts that gather their own heads
+instead of reading head streams.  Every item's miss bitmap is compared access by
 access, and both of its miss counts (Assumptions 1-3, Sec. 4.1;
 LRU, FIFO and the RANDOM reading).  The oracle runs one item per host
 thread, once per item for all plans."""
@@ -51,7 +52,9 @@ def test_config2_whole_batch_bit_exact_under_the_timed_plan():
                 # estimated warp time split by sets or cut in time
                 "splits": {"batch_max_sets": 1 << 30, "split_cost_ns": 2_000_000},
                 # every warp on any kind's queue, all kinds in one shared unit loop
-                "shared_loop": dict(timed, kind_affinity=0xFFFFFFFF)}
+                "shared_loop": dict(timed, kind_affinity=0xFFFFFFFF),
+                # split parts that gather their heads from the trace themselves
+                "gather": dict(timed, head_streams=0xFFFFFFFF)}
     results = {k: _run(geoms, traces, pairs, v) for k, v in variants.items()}
     del traces, flat
     torch.cuda.empty_cache()
