@@ -367,6 +367,10 @@ __device__ __forceinline__ uint32_t lanes_below(uint32_t key, uint32_t thr) {
 
 // FIFO / RANDOM.  Arena: uint4 meta[T] ({p, L} or {filled, evictions});
 // uint32 sline[T*a]; (RANDOM) uint2 scr[T*a]; uint16 tab[table_n] (way + 1).
+// A FIFO / RANDOM step of one set goes miss by miss (BatchFR::seq_step) when
+// at most this many of its heads start out not held.
+constexpr int kSeqMaxFirst = 4;
+
 template <int POLICY>
 struct BatchFR {
     uint4 *meta;
@@ -413,6 +417,78 @@ struct BatchFR {
             for (uint32_t i = lane; i < n; i += 32) scr[i] = make_uint2(0, 0);
         uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
         for (uint32_t i = lane; i < (it.table_n + 1) / 2; i += 32) t32[i] = 0;
+    }
+
+    // The way the group's r-th miss of this step fills, given the set's
+    // counters m at the step's start, and whether that miss evicts.
+    __device__ __forceinline__ uint32_t rank_way(uint4 m, uint32_t set, uint32_t r,
+                                                 bool &evicts) const {
+        const uint32_t a = ways;
+        if (POLICY == PCHASE_FIFO) {
+            evicts = m.y + r >= a;
+            return mod_ways(m.x + m.y + r, a);
+        }
+        const uint32_t k = m.x + r;
+        evicts = k >= a;
+        return evicts ? random_way(seed, global_set(set, psh, kcnt, kres), m.y + (k - a), a, wtd) : k;
+    }
+
+    // The set's counters after M more misses (FIFO: {ring pointer, lines
+    // held}; RANDOM: {lines held, evictions}).
+    __device__ __forceinline__ uint4 after_misses(uint4 m, uint32_t M) const {
+        const uint32_t a = ways;
+        uint4 n = m;
+        if (POLICY == PCHASE_FIFO) {
+            const uint32_t tot = m.y + M;
+            n.y = tot < a ? tot : a;
+            n.x = mod_ways(m.x + (tot > a ? tot - a : 0u), a);
+        } else {
+            const uint32_t tot = m.x + M;
+            n.x = tot < a ? tot : a;
+            n.y = m.y + (tot > a ? tot - a : 0u);
+        }
+        return n;
+    }
+
+    // One set's heads (in lane order), resolved miss by miss, for a <= 32
+    // ways.  A hit changes nothing, so between misses every head whose line
+    // is held hits; the first head whose line is not held misses, fills the
+    // way of the step's next miss (rank_way), and from there on the line it
+    // evicted is not held and its own line is.  The set's ways sit one per
+    // lane in a register for the step (lane w: way w), so a miss costs a few
+    // votes and shuffles; the line table is brought up to date at the end
+    // (lines that left first, then the ways' final lines).  res: the lane's
+    // line is held as of the misses handled so far.
+    __device__ __forceinline__ bool seq_step(uint32_t line, uint32_t set, bool head, bool res,
+                                             uint32_t cand, int lane) {
+        const uint32_t a = ways;
+        const uint4 m = meta[set];
+        bool ev;
+        const uint32_t vw = rank_way(m, set, (uint32_t)lane, ev);  // the way of miss `lane`
+        uint32_t *const sl = sline + (size_t)set * a;
+        const uint32_t orig = (uint32_t)lane < a ? sl[lane] : kInvalidLine;
+        uint32_t cur = orig;
+        uint32_t bits = 0, nm = 0;
+        while (cand) {
+            const int j = __ffs(cand) - 1;
+            const uint32_t v = __shfl_sync(kFull, vw, nm);
+            const uint32_t xj = __shfl_sync(kFull, line, j);
+            const uint32_t old = __shfl_sync(kFull, cur, v);
+            if ((uint32_t)lane == v) cur = xj;
+            if (lane > j) res = line == xj || (res && line != old);
+            bits |= 1u << j;
+            ++nm;
+            cand = __ballot_sync(kFull, head && !res && lane > j);
+        }
+        if (cur != orig) {
+            if (orig != kInvalidLine) tab[orig] = 0;
+            sl[lane] = cur;
+        }
+        __syncwarp();
+        if (cur != orig) tab[cur] = (uint16_t)(lane + 1);
+        if (lane == 0) meta[set] = after_misses(m, nm);
+        __syncwarp();
+        return head && ((bits >> lane) & 1u);
     }
 
     // A step whose heads are all new lines, none held at its start: every
@@ -468,7 +544,8 @@ struct BatchFR {
 
     __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t,
                                             int lane, uint32_t lt, uint32_t stamp) {
-        if (__ballot_sync(kFull, head) == 0) return false;
+        const uint32_t hb = __ballot_sync(kFull, head);
+        if (hb == 0) return false;
         // Only a miss evicts: when every head's line is held at the start of
         // the step, all of them hit and nothing changes.
         const uint32_t w0 = head ? tab[line] : 1u;
@@ -507,6 +584,14 @@ struct BatchFR {
                 return fresh_step(line, set, head && !gheld, lane, lt, sm0);
             pure_skip = 7;
         }
+        {
+            // one set with few lines not held: miss by miss
+            const uint32_t s0 = __shfl_sync(kFull, set, __ffs(hb) - 1);
+            const uint32_t cand = __ballot_sync(kFull, head && w0 == 0u);
+            if (ways <= 32u && __popc(cand) <= kSeqMaxFirst &&
+                __all_sync(kFull, !head || set == s0))
+                return seq_step(line, s0, head, w0 != 0u, cand, lane);
+        }
         const Grouped g = group_heads(line, set, head, lane, lt, perm);
         const uint32_t a = ways;
         const uint32_t ltg = g.gmask & lt;
@@ -518,17 +603,8 @@ struct BatchFR {
         const uint32_t pm = lm & lt;
         const int prev = pm ? 31 - __clz(pm) : -1;
         // way of the group's r-th miss, and whether it evicts
-        uint32_t insw;
         bool evicts;
-        if (POLICY == PCHASE_FIFO) {
-            evicts = m.y + r >= a;
-            insw = mod_ways(m.x + m.y + r, a);
-        } else {
-            const uint32_t k = m.x + r;
-            evicts = k >= a;
-            insw = evicts ? random_way(seed, global_set(g.set, psh, kcnt, kres), m.y + (k - a), a, wtd)
-                          : k;
-        }
+        const uint32_t insw = rank_way(m, g.set, r, evicts);
         // next group rank with the same way
         const uint32_t sw = __match_any_sync(kFull, g.act ? g.set * a + insw
                                                            : (0x80000000u | (uint32_t)lane));
@@ -553,7 +629,8 @@ struct BatchFR {
         // in its group than that rank.  Every lane reads its line's last
         // earlier miss from the current vector, so a run of repeats settles
         // in one round.
-        bool miss = g.act && (w1 == 0 ? prev < 0 : e0 < (int32_t)r);
+        // (from the sure misses: first uses of lines not held)
+        bool miss = g.act && w1 == 0 && prev < 0;
         const uint32_t lme = lm & lt;  // earlier lanes of this lane's line
         for (int it = 0; it < 33; ++it) {
             const uint32_t bal = __ballot_sync(kFull, miss);
@@ -570,8 +647,11 @@ struct BatchFR {
         const uint32_t bal = __ballot_sync(kFull, miss);
         const uint32_t mi = __popc(bal & ltg);
         const uint32_t M = __popc(bal & g.gmask);
-        const uint32_t myw = __shfl_sync(kFull, insw, (g.gb + mi) & 31u);
-        const bool myev = __shfl_sync(kFull, evicts ? 1u : 0u, (g.gb + mi) & 31u) != 0;
+        // the way this lane's miss fills (bit 31: it evicts; ways < 2^24)
+        const uint32_t wv = __shfl_sync(kFull, insw | (evicts ? 0x80000000u : 0u),
+                                        (g.gb + mi) & 31u);
+        const uint32_t myw = wv & 0x7FFFFFFFu;
+        const bool myev = (wv >> 31) != 0;
         const uint32_t smw = __match_any_sync(kFull, miss ? g.set * a + myw
                                                          : (0x80000000u | (uint32_t)lane));
         const uint32_t below = smw & lt;
@@ -600,6 +680,7 @@ struct BatchFR {
             meta[g.set] = n;
         }
         __syncwarp();
+        if (g.same) return miss && head;
         return __shfl_sync(kFull, miss ? 1u : 0u, head ? g.dest : (uint32_t)lane) != 0 && head;
     }
 };
