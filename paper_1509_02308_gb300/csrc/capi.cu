@@ -119,6 +119,10 @@ constexpr uint32_t kStreamMinLen = 1u << 18;
 // this much estimated work per SM (ns): a short batch gains less from a warm
 // instruction cache than it loses to the kinds' uneven shares of SMs.
 constexpr double kAffinityMinNsPerSm = 20.0e6;
+// The units that set a long plan's length run alone on an SM (the one-warp
+// launch): the costliest kIsolateMax within kIsolateFrac of the costliest.
+constexpr double kIsolateFrac = 0.6;
+constexpr size_t kIsolateMax = 12;
 // Way scans over set state in global memory (L2-resident) against shared memory.
 constexpr double kGlobalScanFactor = 2.0;
 // A time part's backward read of 32 accesses while it rebuilds the recency
@@ -1130,7 +1134,7 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         while (kCaps[c] < items[i].arena_bytes) ++c;
         cls[i] = c;
     }
-    // The few units that set the plan's length (the 12 costliest within 40 %
+    // The few units that set the plan's length (the kIsolateMax costliest within kIsolateFrac
     // of the costliest, when the plan has far more work than they do) run
     // alone on an SM: given the largest class, they go to the one-warp launch,
     // whose CTAs fill an SM's shared memory, so no other warp slows their
@@ -1143,9 +1147,9 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         }
         std::vector<uint64_t> top;
         for (uint64_t i = 0; i < n_units; ++i)
-            if (cost[i] >= 0.6 * cmax) top.push_back(i);
+            if (cost[i] >= kIsolateFrac * cmax) top.push_back(i);
         std::sort(top.begin(), top.end(), [&](uint64_t x, uint64_t y) { return cost[x] > cost[y]; });
-        if (top.size() > 12) top.resize(12);
+        if (top.size() > kIsolateMax) top.resize(kIsolateMax);
         if (csum > 64.0 * cmax) {
             for (uint64_t i : top) cls[i] = ncap - 1;
             p->n_isolated = top.size();
