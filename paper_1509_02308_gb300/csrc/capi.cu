@@ -546,10 +546,10 @@ struct pchase_sim_plan {
     // part and entry arrays
     std::vector<StreamJob> jobs;
     std::vector<uint32_t> seg_job, item_slot;
-    uint64_t n_cnt = 0, n_ents = 0;
-    uint32_t n_slots = 0;
+    uint64_t n_cnt = 0, n_ents = 0, n_tgt = 0;
+    uint32_t n_slots = 0, n_census = 0;
     size_t off_jobs = 0, off_segjob = 0, off_itemslot = 0, off_cnt = 0, off_parts = 0,
-           off_ents = 0;
+           off_ents = 0, off_tgt = 0;
     double gwork_main[kUnitGroups] = {};  // estimated work of each unit group in the
                                           // slot-mix launch
     bool affinity = false;
@@ -679,13 +679,19 @@ int plan_launch(pchase_sim_plan *p, void *ws, const SimOut &out, cudaStream_t st
         o.item_slot = reinterpret_cast<const uint32_t *>(w + p->off_itemslot);
         o.parts = reinterpret_cast<const PartInfo *>(w + p->off_parts);
         o.ents = reinterpret_cast<const uint2 *>(w + p->off_ents);
+        o.targets = p->n_census ? reinterpret_cast<const uint32_t *>(w + p->off_tgt) : nullptr;
+        // the census bitmaps start empty every run
+        if (p->n_census)
+            PCHASE_CUDA(cudaMemsetAsync(w + p->off_cnt, 0, p->n_cnt * sizeof(uint32_t), st),
+                        "cudaMemsetAsync(census)");
         PCHASE_CUDA(launch_streams(items, reinterpret_cast<const StreamJob *>(w + p->off_jobs),
                                    (uint32_t)p->jobs.size(),
                                    reinterpret_cast<const uint32_t *>(w + p->off_segjob),
                                    (uint32_t)p->seg_job.size(),
                                    reinterpret_cast<uint32_t *>(w + p->off_cnt),
                                    reinterpret_cast<PartInfo *>(w + p->off_parts),
-                                   reinterpret_cast<uint2 *>(w + p->off_ents), o.status, st),
+                                   reinterpret_cast<uint2 *>(w + p->off_ents),
+                                   reinterpret_cast<uint32_t *>(w + p->off_tgt), o.status, st),
                     "head streams");
     }
     if (p->gpool.nwarps) {
@@ -948,7 +954,10 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
         // (after that the read skips ahead, to the trace's start if a set
         // never fills)
         const double fill = 1.5 * sh.cold + 1024.0;
-        const bool fills = !sh.held && sh.visited >= (double)G.sets;
+        // (with a census of the sets' lines the read stops once every set has
+        // all the lines it will get, held or not)
+        const bool census = tn.streams && u.table_n <= kCensusMaxLines && u.sets <= kCensusMaxSets;
+        const bool fills = census || (!sh.held && sh.visited >= (double)G.sets);
         auto bound = [&](uint32_t j, uint32_t P) {
             return std::min(nsteps, (uint32_t)((uint64_t)nblk * j / P) * 32);
         };
@@ -1200,6 +1209,34 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             p->n_cnt = cntw;
             p->n_slots = slot;
         }
+        // census jobs: LRU items cut in time, small enough line tables
+        if (tn.streams) {
+            for (uint64_t k = 0; k < p->items.size(); ++k) {
+                const SimItem &it = p->items[k];
+                const bool tpart = it.kcnt == 1 && it.ks1 != 0 && it.direct == 1 &&
+                                   it.mode == kModeBatch && it.policy == PCHASE_LRU &&
+                                   !((it.lsh >> 17) & 1u);
+                if (!tpart || it.table_n > kCensusMaxLines || it.sets > kCensusMaxSets) continue;
+                if (p->item_slot.empty()) p->item_slot.assign(n_items, 0xFFFFFFFFu);
+                if (p->item_slot[it.out_item] != 0xFFFFFFFFu) continue;
+                StreamJob J{};
+                J.kind = kJobCensus;
+                J.ent_base = p->n_tgt;
+                J.cnt_off = p->n_cnt;
+                J.unit = (uint32_t)k;
+                J.K = 1;
+                J.nseg = (it.len + kSegAccesses - 1) / kSegAccesses;
+                J.seg_first = (uint32_t)p->seg_job.size();
+                J.slot_first = p->n_slots;
+                p->item_slot[it.out_item] = p->n_slots;
+                for (uint32_t s = 0; s < J.nseg; ++s) p->seg_job.push_back((uint32_t)p->jobs.size());
+                p->jobs.push_back(J);
+                p->n_tgt += it.sets;
+                p->n_cnt += kCensusMaxLines / 32;
+                p->n_slots += 1;
+                p->n_census += 1;
+            }
+        }
     } catch (...) {
         delete p;
         return fail(PCHASE_ENOMEM, "head stream table allocation");
@@ -1391,6 +1428,8 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     off = align256(off + (size_t)p->n_slots * sizeof(PartInfo));
     p->off_ents = off;
     off = align256(off + p->n_ents * sizeof(uint2));
+    p->off_tgt = off;
+    off = align256(off + p->n_tgt * sizeof(uint32_t));
     p->ws_bytes = off;
     *plan_out = p;
     return PCHASE_OK;
@@ -1520,9 +1559,11 @@ size_t pchase_sim_plan_describe(const pchase_sim_plan *plan, char *buf, size_t b
         snprintf(tmp, sizeof tmp, " affinity=%d", plan->affinity ? 1 : 0);
         d += tmp;
         if (!plan->jobs.empty()) {
-            // head streams: split items, their parts, entries (8 bytes each)
-            snprintf(tmp, sizeof tmp, " streams=%zu,%u,%llu", plan->jobs.size(), plan->n_slots,
-                     (unsigned long long)plan->n_ents);
+            // head streams: split items, their parts, entries (8 bytes each);
+            // census: LRU items cut in time whose sets' lines are counted
+            snprintf(tmp, sizeof tmp, " streams=%zu,%u,%llu census=%u",
+                     plan->jobs.size() - plan->n_census, plan->n_slots - plan->n_census,
+                     (unsigned long long)plan->n_ents, plan->n_census);
             d += tmp;
         }
         if (plan->gpool.nwarps) {

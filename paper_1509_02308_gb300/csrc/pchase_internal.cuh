@@ -218,6 +218,10 @@ struct SimOut {
     const uint32_t *item_slot;
     const struct PartInfo *parts;
     const uint2 *ents;
+    // LRU items cut in time: parts[item_slot[i]].start indexes targets, one
+    // per set: min(a, the set's distinct lines over the whole trace), the
+    // lines a time part's read-back needs before the set is complete
+    const uint32_t *targets;
 };
 
 // Head streams (streams.cu).  Every item split by sets into K parts is one
@@ -226,21 +230,27 @@ struct SimOut {
 // previous access's line, falling in the part's sets), a warp per job turns
 // the counts into offsets, and the segments' warps write the heads out, so
 // each part's stream holds exactly the heads the part would gather itself.
+// A census job (an LRU item cut in time, at most kCensusMaxLines line ids and
+// kCensusMaxSets sets) marks the lines its trace uses in a bitmap instead, and
+// its warp counts each set's distinct lines into the targets.
 constexpr uint32_t kSegAccesses = 8192;
+constexpr uint32_t kCensusMaxLines = 4096;
+constexpr uint32_t kCensusMaxSets = 256;
+enum : uint32_t { kJobHeads = 0, kJobCensus = 1 };
 struct PartInfo {
     uint64_t start;  // first entry of the part's stream
     uint32_t len;    // entries
     uint32_t pad;
 };
 struct StreamJob {
-    uint64_t ent_base;    // first entry of the item's K streams
-    uint64_t cnt_off;     // counts: cnt_off + segment * K + part
+    uint64_t ent_base;    // first entry of the item's K streams (census: first target)
+    uint64_t cnt_off;     // counts: cnt_off + segment * K + part (census: the line bitmap)
     uint32_t unit;        // one of the item's units (any part: they share trace and split)
     uint32_t K;
     uint32_t nseg;
     uint32_t seg_first;   // its first segment in the plan's segment list
     uint32_t slot_first;  // parts[slot_first + k]
-    uint32_t pad;
+    uint32_t kind;        // kJobHeads or kJobCensus
 };
 
 // Records the text pchase_last_error_string() returns on this thread and
@@ -258,6 +268,7 @@ int sim_max_ctas_per_sm(const SlotLayout &layout);
 // The head streams of a plan's split items (three launches on `st`).
 cudaError_t launch_streams(const SimItem *items, const StreamJob *jobs, uint32_t n_jobs,
                            const uint32_t *seg_job, uint32_t n_seg, uint32_t *cnt,
-                           PartInfo *parts, uint2 *ents, uint32_t *status, cudaStream_t st);
+                           PartInfo *parts, uint2 *ents, uint32_t *targets, uint32_t *status,
+                           cudaStream_t st);
 
 }  // namespace pchase

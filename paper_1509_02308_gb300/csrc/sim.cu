@@ -817,16 +817,27 @@ struct BatchLRU {
     // below the set's lines taken so far, until every set holds a lines or
     // the trace's start is reached.  load(t) gives the line of access t, or
     // kInvalidLine for an access the simulation skips.
+    //
+    // tgt (may be NULL): per set, the lines it needs before it is complete,
+    // min(a, its distinct lines over the whole trace); sets that need none
+    // are complete from the start, and the read stops once every set is.
     template <typename Load>
     __device__ __forceinline__ void rebuild(uint32_t c0, uint32_t T, int lane, uint32_t lt,
-                                            Load load) {
+                                            Load load, const uint32_t *tgt) {
         const uint32_t a = ways;
         uint32_t full = 0;
+        if (tgt) {
+            for (uint32_t s0 = 0; s0 < T; s0 += 32) {
+                const uint32_t s = s0 + (uint32_t)lane;
+                full += (uint32_t)__popc(__ballot_sync(kFull, s < T && tgt[s] == 0));
+            }
+        }
+        auto need_of = [&](uint32_t set) -> uint32_t { return tgt ? tgt[set] : a; };
         auto chunk = [&](uint32_t ln) {
             const bool valid = ln != kInvalidLine;
             const uint32_t set = valid ? set_of(ln) : 0u;
-            // a chunk whose lines are all taken or in full sets changes nothing
-            const bool need = valid && tab[ln] == 0 && meta[set].y < a;
+            // a chunk whose lines are all taken or in complete sets changes nothing
+            const bool need = valid && tab[ln] == 0 && meta[set].y < need_of(set);
             if (!__any_sync(kFull, need)) return;
             const uint32_t lm = __match_any_sync(kFull, valid ? ln : (0x80000000u | (uint32_t)lane));
             const bool cand = need && (lm & ~(lt | (1u << lane))) == 0;  // newest in the chunk
@@ -834,7 +845,8 @@ struct BatchLRU {
             const uint32_t k = cand ? meta[set].y : 0u;
             const uint32_t q = k + (uint32_t)__popc(sm & ~(lt | (1u << lane)));  // newer ones first
             const bool lead_s = cand && (sm & lt) == 0;
-            full += (uint32_t)__popc(__ballot_sync(kFull, lead_s && k + (uint32_t)__popc(sm) >= a));
+            full += (uint32_t)__popc(
+                __ballot_sync(kFull, lead_s && k + (uint32_t)__popc(sm) >= need_of(set)));
             __syncwarp();
             if (cand && q < a) {
                 ring[(size_t)set * R + (a - 1 - q)] = ln;
@@ -1397,10 +1409,16 @@ __device__ __forceinline__ void run_steps(const SimItem &it, uint32_t arena, uin
             };
             BatchLRU S;
             S.bind(st, it);
+            // the census of the item's sets, when the run took one
+            const uint32_t *tgt = nullptr;
+            if (out.targets && out.item_slot) {
+                const uint32_t sl = out.item_slot[it.out_item];
+                if (sl != 0xFFFFFFFFu) tgt = out.targets + out.parts[sl].start;
+            }
             S.rebuild(sfirst << 5, sets, lane, lt, [&](uint32_t t) -> uint32_t {
                 const uint32_t j = index_at(t);
                 return j < N ? line_of(j) : kInvalidLine;
-            });
+            }, tgt);
             carry = line_of(index_at((sfirst << 5) - 1));
             if (!idxp && N)
                 aj = (uint32_t)((((uint64_t)(sfirst << 5) + (uint32_t)lane) * it.stride) % N);
