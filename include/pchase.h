@@ -578,9 +578,10 @@ size_t pchase_inverse_infer_work_bytes(const pchase_inverse *h);
 size_t pchase_inverse_status_offset(const pchase_inverse *h);
 /* Byte offset in `work` of convolution layer `layer`'s (0..3) BF16 output,
  * [B][positions][64] for the last chunk of the last forward pass; 0 for a
- * layer out of range.  Inference computes layers 1 and 2 in one kernel whose
- * layer-1 outputs never leave the SM, so layer 0's buffer holds the last
- * training step's.  For inspection and tests. */
+ * layer out of range.  Inference computes layers 1 and 2 in one kernel and
+ * layers 3 and 4 in another, whose layer-1 and layer-3 outputs never leave
+ * the SM, so the buffers of layers 0 and 2 hold the last training step's.
+ * For inspection and tests. */
 size_t pchase_inverse_activation_offset(const pchase_inverse *h, uint32_t layer);
 
 /* Byte offset in `params` of one of its arrays, each pchase_inverse_param_count

@@ -822,6 +822,243 @@ __global__ void __launch_bounds__(128, 1)
                      : "memory");
 }
 
+// ------------------------------------------------------------ layers 3 + 4
+// Inference of layers 3 and 4 in one kernel.  An iteration takes 4 traces
+// (one 128-row tile of layer 4): the layer-3 outputs of its two 128-row tiles
+// (2 traces each) go from TMEM through bias and GELU straight into layer 4's
+// input slab in shared memory, laid out as conv_tc_kernel stages an input
+// (row 8g + i of plane pl holds position 32 (i & 1) + 2 (g - 1) + pl of the
+// tile's trace i / 2), and layer 4's MMAs run from there; only layer 4's
+// outputs go to global memory.  A layer-3 position q of trace b lands in row
+// 8 ((q >> 1) + 1) + 2b when q <= 33 and in row 8 ((q >> 1) - 15) + 2b + 1
+// when q >= 30 (plane q & 1); rows 2b of group 0 and 2b + 1 of group 17 are
+// the zero padding, written once.  Layer-3 input slabs are loaded as in
+// conv_tc_kernel, three buffers.
+constexpr int kL34Threads = 256;
+constexpr uint32_t kL34TmemCols = 256;  // accumulators: layer-3 tiles A, B and layer 4
+constexpr uint32_t kL34Smem = 1024 + 2 * kWBytes + kSlabs * kSlabBytes + kSlabBytes + 64;
+
+__global__ void __launch_bounds__(kL34Threads, 1)
+    conv34_tc_kernel(const __nv_bfloat16 *__restrict__ x, int nb,
+                     const __nv_bfloat16 *__restrict__ W3, const float *__restrict__ bias3,
+                     const __nv_bfloat16 *__restrict__ W4, const float *__restrict__ bias4,
+                     __nv_bfloat16 *__restrict__ out, uint32_t *__restrict__ status) {
+    constexpr int kLin3 = 128, kL3 = 64, kL4 = 32;
+    extern __shared__ uint8_t dsm[];
+    const uint32_t raw = smem_u32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *const gbase = dsm + (base - raw);
+    const uint32_t sW3 = base, sW4 = base + kWBytes;
+    const uint32_t sSlab = base + 2 * kWBytes;         // layer-3 input slabs
+    const uint32_t sL4 = sSlab + kSlabs * kSlabBytes;  // layer-4 input slab
+    const uint32_t sBar = sL4 + kSlabBytes;            // mbarriers: tile A, tile B, layer 4
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + (sBar - base) + 32);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int M3 = nb * kL3, M4 = nb * kL4;
+    const int n4 = (M4 + kTileRows - 1) / kTileRows;  // iterations of 4 traces
+    const int n3 = 2 * n4;                            // layer-3 tiles: 2 it and 2 it + 1
+
+    for (int e = tid; e < kTaps * kCh * 8; e += kL34Threads) {
+        const int k = e >> 9, co = (e >> 3) & 63, c = e & 7;
+        const uint32_t off = k * 8192 + co * 128 + ((c ^ (co & 7)) << 4);
+        const size_t src = (size_t)co * (kTaps * kCh) + k * kCh + c * 8;
+        cp_async16(sW3 + off, W3 + src, true);
+        cp_async16(sW4 + off, W4 + src, true);
+    }
+    cp_async_commit();
+
+    const int ld_c = tid & 7, ld_i = (tid >> 3) & 7, ld_pl = (tid >> 6) & 1, ld_h = tid >> 7;
+    const int ld_g0 = ld_h * (kGroups / 2);
+    auto load_slab = [&](int buf, int u) {
+        if (u < n3) {
+            const int mi = u * kTileRows + 16 * ld_i;
+            const int b = mi / kL3, p0 = mi - b * kL3;
+            const bool row_ok = mi < M3;
+            const int q0 = 2 * p0 + 2 * (ld_g0 - 1) + ld_pl;
+            const __nv_bfloat16 *src = x + ((size_t)(row_ok ? b : 0) * kLin3) * kCh + ld_c * 8;
+            const uint32_t dst = sSlab + buf * kSlabBytes + ld_pl * kPlaneBytes +
+                                 (8 * ld_g0 + ld_i) * 128 + ((ld_c ^ ld_i) << 4);
+#pragma unroll
+            for (int gg = 0; gg < kGroups / 2; ++gg) {
+                const int q = q0 + 2 * gg;
+                const bool ok = row_ok && q >= 0 && q < kLin3;
+                cp_async16(dst + gg * 1024, ok ? src + (size_t)q * kCh : x, ok);
+            }
+        }
+        cp_async_commit();  // one group per call, empty or not
+    };
+
+    // the layer-4 slab's padding rows (never written again)
+    if (tid < 2 * 4 * 2 * 8) {
+        const int pl = tid >> 6, b = (tid >> 4) & 3, which = (tid >> 3) & 1, c = tid & 7;
+        const int row = which ? 8 * 17 + 2 * b + 1 : 2 * b;
+        *reinterpret_cast<uint4 *>(gbase + (sL4 - base) + pl * kPlaneBytes + row * 128 +
+                                   ((c ^ (row & 7)) << 4)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        for (int q = 0; q < 3; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8 * q) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kL34TmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    load_slab(0, 2 * (int)blockIdx.x);
+    load_slab(1, 2 * (int)blockIdx.x + 1);
+    load_slab(2, 2 * ((int)blockIdx.x + (int)gridDim.x));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    // one thread: the 20 MMAs of a tile from slab a0 with weights sw into d
+    auto mma_tile = [&](uint32_t d, uint32_t slab, uint32_t sw, uint32_t bar) {
+#pragma unroll
+        for (int k = 0; k < kTaps; ++k) {
+            const uint32_t a0 = slab + (uint32_t)(k & 1) * kPlaneBytes + (uint32_t)(k >> 1) * 1024u;
+            const uint32_t b0 = sw + (uint32_t)k * 8192u;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(d, sw128_desc(a0 + 32u * s), sw128_desc(b0 + 32u * s),
+                         (k | s) != 0 ? 1u : 0u);
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            : "memory");
+    };
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;          // this thread's TMEM lane
+    const int mt = 16 * (r & 7) + (r >> 3);     // ... and the tile row it holds
+    const uint32_t lane_off = ((uint32_t)(quarter * 32) << 16) + (uint32_t)half * 32u;
+    // bias + GELU of this thread's 32 columns of accumulator acc, as BF16 pairs
+    auto finish = [&](uint32_t acc, const float *bias, uint32_t (&pk)[16]) {
+        uint32_t v[2][16];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) tmem_ld16(tmem + acc + lane_off + q * 16, v[q]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                const int n = half * 32 + q * 16 + e;
+                pk[q * 8 + (e >> 1)] = gelu2_bf16(add2(f2(__uint_as_float(v[q][e]),
+                                                           __uint_as_float(v[q][e + 1])),
+                                                        f2(__ldg(bias + n), __ldg(bias + n + 1))));
+            }
+    };
+
+    // Software pipeline over iterations n (tiles 2n, 2n + 1 of layer 3; one
+    // tile of layer 4): both layer-3 tiles' MMAs go out together, layer 4's
+    // epilogue of iteration n - 1 runs while they execute, then the layer-3
+    // epilogues fill the slab and layer 4's MMAs of iteration n go out, to
+    // complete while the next iteration's loads are awaited.  Tile s sits in
+    // buffer s mod 3, and tile s + 3 is loaded into it as soon as the
+    // epilogue of tile s has seen s's MMAs complete.
+    // layer 4's epilogue of the iteration at it (phase ph)
+    auto epilogue4 = [&](int it, uint32_t ph) -> bool {
+        const bool got = mbar_wait(sBar + 16u, ph);
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
+            return false;
+        }
+        tc_fence_after();
+        uint32_t pk[16];
+        finish(128u, bias4, pk);
+        const int m = it * kTileRows + mt;
+        if (m < M4) {
+            uint4 *o4 = reinterpret_cast<uint4 *>(out + (size_t)m * kCh + half * 32);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+                o4[cc] = make_uint4(pk[4 * cc], pk[4 * cc + 1], pk[4 * cc + 2], pk[4 * cc + 3]);
+        }
+        tc_fence_before();
+        return true;
+    };
+    int n = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < n4; it += gridDim.x, ++n) {
+        const uint32_t ph = (uint32_t)n & 1u;
+        const int itn = it + (int)gridDim.x;
+        // tiles 2n and 2n + 1 loaded (tile 2n + 2 may still be in flight)
+        cp_async_wait1();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            mma_tile(tmem, sSlab + (uint32_t)((2 * n) % kSlabs) * kSlabBytes, sW3, sBar);
+            mma_tile(tmem + 64u, sSlab + (uint32_t)((2 * n + 1) % kSlabs) * kSlabBytes, sW3,
+                     sBar + 8u);
+        }
+        if (n > 0 && !epilogue4(it - (int)gridDim.x, ph ^ 1u)) {
+            ok = false;
+            break;
+        }
+        // layer-3 epilogues into the layer-4 slab (layer 4's last MMAs
+        // completed: its epilogue just waited for them)
+        for (int X = 0; X < 2; ++X) {
+            const bool got = mbar_wait(sBar + 8u * (uint32_t)X, ph);
+            if (!__syncthreads_and(got)) {
+                if (tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            // this tile's buffer is free: tile 2n + X + 3 of the sequence goes
+            // there (iteration n + 1's tile B, or iteration n + 2's tile A)
+            load_slab((2 * n + X) % kSlabs, X == 0 ? 2 * itn + 1 : 2 * (itn + (int)gridDim.x));
+            uint32_t pk[16];
+            finish(64u * (uint32_t)X, bias3, pk);
+            const int b = 2 * X + (mt >> 6), q = mt & 63;
+            const uint32_t pbase = sL4 + (uint32_t)(q & 1) * kPlaneBytes;
+            if (q <= 33) {
+                const uint32_t row = 8u * (uint32_t)((q >> 1) + 1) + 2u * (uint32_t)b;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const uint32_t dst = pbase + row * 128u + ((uint32_t)((half * 4 + cc) ^ (row & 7)) << 4);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
+                                 "r"(pk[4 * cc]), "r"(pk[4 * cc + 1]), "r"(pk[4 * cc + 2]),
+                                 "r"(pk[4 * cc + 3])
+                                 : "memory");
+                }
+            }
+            if (q >= 30) {
+                const uint32_t row = 8u * (uint32_t)((q >> 1) - 15) + 2u * (uint32_t)b + 1u;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const uint32_t dst = pbase + row * 128u + ((uint32_t)((half * 4 + cc) ^ (row & 7)) << 4);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
+                                 "r"(pk[4 * cc]), "r"(pk[4 * cc + 1]), "r"(pk[4 * cc + 2]),
+                                 "r"(pk[4 * cc + 3])
+                                 : "memory");
+                }
+            }
+            tc_fence_before();
+        }
+        if (!ok) break;
+        // layer 4 from the slab just written
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) mma_tile(tmem + 128u, sL4, sW4, sBar + 16u);
+    }
+    if (ok && n > 0) epilogue4(blockIdx.x + (n - 1) * (int)gridDim.x, (uint32_t)(n - 1) & 1u);
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kL34TmemCols)
+                     : "memory");
+}
+
 }  // namespace
 
 cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16 *W,
@@ -839,6 +1076,21 @@ cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16
     const long long ntiles = ((long long)nb * lout + kTileRows - 1) / kTileRows;
     const int grid = (int)std::min<long long>(ntiles, std::max(1, sms));
     conv_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, nb, lin, W, bias, out, pre, status);
+    return cudaGetLastError();
+}
+
+cudaError_t conv34_tc(const __nv_bfloat16 *x, int nb, const __nv_bfloat16 *W3, const float *bias3,
+                      const __nv_bfloat16 *W4, const float *bias4, __nv_bfloat16 *out,
+                      uint32_t *status, int sms, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    if (!status) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(conv34_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kL34Smem);
+    if (e != cudaSuccess) return e;
+    const long long iters = ((long long)nb * 32 + kTileRows - 1) / kTileRows;
+    const int grid = (int)std::min<long long>(iters, std::max(1, sms));
+    conv34_tc_kernel<<<grid, kL34Threads, kL34Smem, st>>>(x, nb, W3, bias3, W4, bias4, out, status);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,8 @@
 // Every product takes BF16 operands with FP32 accumulation; master weights,
 // Adam moments and gradients stay FP32.  Inference runs on the tcgen05 tensor
 // cores (conv_tc.cu): layers 1 and 2 in one kernel (layer 1 computed on chip
-// from the FP32 inputs), layers 3 and 4, then FC + heads in one kernel; the
+// from the FP32 inputs), layers 3 and 4 in one kernel (layer 3 on chip), then
+// FC + heads in one kernel; the
 // training step's GEMMs (forward with kept pre-activations, backward, weight
 // gradients) run here on warp-level mma.sync m16n8k16 tiles, the first
 // convolution (one input channel) on CUDA cores.
@@ -951,8 +952,12 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
         __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[1]);
         INV_CUDA(conv12_tc(xf, (int)B, wb + L.w[0], wf + L.b[0], wb + L.w[1], wf + L.b[1], o,
                            at<uint32_t>(work, h->status), device_sms(), st));
-        in = o;
-        l0 = 2;
+        // layers 3 and 4 in one tcgen05 kernel (layer 3's activations stay on chip)
+        __nv_bfloat16 *o4 = at<__nv_bfloat16>(work, h->act[3]);
+        INV_CUDA(conv34_tc(o, (int)B, wb + L.w[2], wf + L.b[2], wb + L.w[3], wf + L.b[3], o4,
+                           at<uint32_t>(work, h->status), device_sms(), st));
+        in = o4;
+        l0 = 4;
     }
     for (int l = l0; l < 4; ++l) {
         const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
