@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(128, 1)
 // when q >= 30 (plane q & 1); rows 2b of group 0 and 2b + 1 of group 17 are
 // the zero padding, written once.  Layer-3 input slabs are loaded as in
 // conv_tc_kernel, three buffers.
-constexpr int kL34Threads = 256;
+constexpr int kL34Threads = 512;  // the first 256 load slabs; all run the epilogues
 constexpr uint32_t kL34TmemCols = 256;  // accumulators: layer-3 tiles A, B and layer 4
 constexpr uint32_t kL34Smem = 1024 + 2 * kWBytes + kSlabs * kSlabBytes + kSlabBytes + 64;
 
@@ -871,7 +871,7 @@ __global__ void __launch_bounds__(kL34Threads, 1)
     const int ld_c = tid & 7, ld_i = (tid >> 3) & 7, ld_pl = (tid >> 6) & 1, ld_h = tid >> 7;
     const int ld_g0 = ld_h * (kGroups / 2);
     auto load_slab = [&](int buf, int u) {
-        if (u < n3) {
+        if (u < n3 && tid < 256) {
             const int mi = u * kTileRows + 16 * ld_i;
             const int b = mi / kL3, p0 = mi - b * kL3;
             const bool row_ok = mi < M3;
@@ -931,25 +931,38 @@ __global__ void __launch_bounds__(kL34Threads, 1)
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
             : "memory");
     };
-    const int quarter = warp & 3, half = warp >> 2;
+    // warp w reads TMEM lane quarter w mod 4 (its hardware quarter) and
+    // columns 16 (w / 4) .. + 15: a thread holds 16 values of one tile row
+    const int quarter = warp & 3, colq = warp >> 2;
     const int r = quarter * 32 + lane;          // this thread's TMEM lane
     const int mt = 16 * (r & 7) + (r >> 3);     // ... and the tile row it holds
-    const uint32_t lane_off = ((uint32_t)(quarter * 32) << 16) + (uint32_t)half * 32u;
-    // bias + GELU of this thread's 32 columns of accumulator acc, as BF16 pairs
-    auto finish = [&](uint32_t acc, const float *bias, uint32_t (&pk)[16]) {
-        uint32_t v[2][16];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) tmem_ld16(tmem + acc + lane_off + q * 16, v[q]);
+    const uint32_t lane_off = ((uint32_t)(quarter * 32) << 16) + (uint32_t)colq * 16u;
+    // bias + GELU of this thread's 16 columns of accumulator acc, as BF16 pairs
+    auto finish = [&](uint32_t acc, const float *bias, uint32_t (&pk)[8]) {
+        uint32_t v[16];
+        tmem_ld16(tmem + acc + lane_off, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int e = 0; e < 16; e += 2) {
+            const int n = colq * 16 + e;
+            pk[e >> 1] = gelu2_bf16(add2(f2(__uint_as_float(v[e]), __uint_as_float(v[e + 1])),
+                                         f2(__ldg(bias + n), __ldg(bias + n + 1))));
+        }
+    };
+    // the two 16-byte chunks of a row written in an order that alternates
+    // with the lane, so that a store instruction's lanes spread over more banks
+    auto put_row = [&](uint32_t pbase, uint32_t row, const uint32_t (&pk)[8]) {
 #pragma unroll
-            for (int e = 0; e < 16; e += 2) {
-                const int n = half * 32 + q * 16 + e;
-                pk[q * 8 + (e >> 1)] = gelu2_bf16(add2(f2(__uint_as_float(v[q][e]),
-                                                           __uint_as_float(v[q][e + 1])),
-                                                        f2(__ldg(bias + n), __ldg(bias + n + 1))));
-            }
+        for (int k = 0; k < 2; ++k) {
+            const int cc = k ^ (lane & 1);
+            const uint32_t dst =
+                pbase + row * 128u + ((uint32_t)((colq * 2 + cc) ^ (int)(row & 7)) << 4);
+            const uint32_t w0 = cc ? pk[4] : pk[0], w1 = cc ? pk[5] : pk[1];
+            const uint32_t w2 = cc ? pk[6] : pk[2], w3 = cc ? pk[7] : pk[3];
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w0), "r"(w1),
+                         "r"(w2), "r"(w3)
+                         : "memory");
+        }
     };
 
     // Software pipeline over iterations n (tiles 2n, 2n + 1 of layer 3; one
@@ -967,14 +980,13 @@ __global__ void __launch_bounds__(kL34Threads, 1)
             return false;
         }
         tc_fence_after();
-        uint32_t pk[16];
+        uint32_t pk[8];
         finish(128u, bias4, pk);
         const int m = it * kTileRows + mt;
         if (m < M4) {
-            uint4 *o4 = reinterpret_cast<uint4 *>(out + (size_t)m * kCh + half * 32);
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc)
-                o4[cc] = make_uint4(pk[4 * cc], pk[4 * cc + 1], pk[4 * cc + 2], pk[4 * cc + 3]);
+            uint4 *o4 = reinterpret_cast<uint4 *>(out + (size_t)m * kCh + colq * 16);
+            o4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            o4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
         tc_fence_before();
         return true;
@@ -1012,32 +1024,12 @@ __global__ void __launch_bounds__(kL34Threads, 1)
             // this tile's buffer is free: tile 2n + X + 3 of the sequence goes
             // there (iteration n + 1's tile B, or iteration n + 2's tile A)
             load_slab((2 * n + X) % kSlabs, X == 0 ? 2 * itn + 1 : 2 * (itn + (int)gridDim.x));
-            uint32_t pk[16];
+            uint32_t pk[8];
             finish(64u * (uint32_t)X, bias3, pk);
             const int b = 2 * X + (mt >> 6), q = mt & 63;
             const uint32_t pbase = sL4 + (uint32_t)(q & 1) * kPlaneBytes;
-            if (q <= 33) {
-                const uint32_t row = 8u * (uint32_t)((q >> 1) + 1) + 2u * (uint32_t)b;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const uint32_t dst = pbase + row * 128u + ((uint32_t)((half * 4 + cc) ^ (row & 7)) << 4);
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
-                                 "r"(pk[4 * cc]), "r"(pk[4 * cc + 1]), "r"(pk[4 * cc + 2]),
-                                 "r"(pk[4 * cc + 3])
-                                 : "memory");
-                }
-            }
-            if (q >= 30) {
-                const uint32_t row = 8u * (uint32_t)((q >> 1) - 15) + 2u * (uint32_t)b + 1u;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const uint32_t dst = pbase + row * 128u + ((uint32_t)((half * 4 + cc) ^ (row & 7)) << 4);
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
-                                 "r"(pk[4 * cc]), "r"(pk[4 * cc + 1]), "r"(pk[4 * cc + 2]),
-                                 "r"(pk[4 * cc + 3])
-                                 : "memory");
-                }
-            }
+            if (q <= 33) put_row(pbase, 8u * (uint32_t)((q >> 1) + 1) + 2u * (uint32_t)b, pk);
+            if (q >= 30) put_row(pbase, 8u * (uint32_t)((q >> 1) - 15) + 2u * (uint32_t)b + 1u, pk);
             tc_fence_before();
         }
         if (!ok) break;
