@@ -991,12 +991,11 @@ __global__ void __launch_bounds__(kL34Threads, 1)
     // buffer s mod 3, and tile s + 3 is loaded into it as soon as the
     // epilogue of tile s has seen s's MMAs complete.
     // layer 4's epilogue of the iteration at it (phase ph)
-    auto epilogue4 = [&](int it, uint32_t ph) -> bool {
-        const bool got = mbar_wait(sBar + 16u, ph);
-        if (!__syncthreads_and(got)) {
-            if (tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
-            return false;
-        }
+    // (a wait that gives up marks `bad`; the block learns of it at its next
+    // barrier, so the waits themselves need none)
+    bool bad = false;
+    auto epilogue4 = [&](int it, uint32_t ph) {
+        if (!mbar_wait(sBar + 16u, ph)) bad = true;
         tc_fence_after();
         uint32_t pk[8];
         finish(128u, bias4, pk);
@@ -1007,7 +1006,6 @@ __global__ void __launch_bounds__(kL34Threads, 1)
             o4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
         tc_fence_before();
-        return true;
     };
     int n = 0;
     bool ok = true;
@@ -1018,26 +1016,21 @@ __global__ void __launch_bounds__(kL34Threads, 1)
         cp_async_wait1();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
-        __syncthreads();
+        if (__syncthreads_or(bad)) {
+            ok = false;
+            break;
+        }
         tc_fence_after();
         if (tid == 0) {
             mma_tile(tmem, sSlab + (uint32_t)((2 * n) % kSlabs) * kSlabBytes, sW3, sBar);
             mma_tile(tmem + 64u, sSlab + (uint32_t)((2 * n + 1) % kSlabs) * kSlabBytes, sW3,
                      sBar + 8u);
         }
-        if (n > 0 && !epilogue4(it - (int)gridDim.x, ph ^ 1u)) {
-            ok = false;
-            break;
-        }
+        if (n > 0) epilogue4(it - (int)gridDim.x, ph ^ 1u);
         // layer-3 epilogues into the layer-4 slab (layer 4's last MMAs
         // completed: its epilogue just waited for them)
         for (int X = 0; X < 2; ++X) {
-            const bool got = mbar_wait(sBar + 8u * (uint32_t)X, ph);
-            if (!__syncthreads_and(got)) {
-                if (tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
-                ok = false;
-                break;
-            }
+            if (!mbar_wait(sBar + 8u * (uint32_t)X, ph)) bad = true;
             tc_fence_after();
             // this tile's buffer is free: tile 2n + X + 3 of the sequence goes
             // there (iteration n + 1's tile B, or iteration n + 2's tile A)
@@ -1050,15 +1043,18 @@ __global__ void __launch_bounds__(kL34Threads, 1)
             if (q >= 30) put_row(pbase, 8u * (uint32_t)((q >> 1) - 15) + 2u * (uint32_t)b + 1u, pk);
             tc_fence_before();
         }
-        if (!ok) break;
         // layer 4 from the slab just written
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
-        __syncthreads();
+        if (__syncthreads_or(bad)) {
+            ok = false;
+            break;
+        }
         tc_fence_after();
         if (tid == 0) mma_tile(tmem + 128u, sL4, sW4, sBar + 16u);
     }
     if (ok && n > 0) epilogue4(blockIdx.x + (n - 1) * (int)gridDim.x, (uint32_t)(n - 1) & 1u);
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
     cp_async_wait_all();
     tc_fence_before();
     __syncthreads();
