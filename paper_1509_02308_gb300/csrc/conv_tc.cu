@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // already issued are waited for, and TMEM is freed.
 constexpr int kFusedThreads = 512;
 constexpr uint32_t kFusedXs = 520;  // staged inputs: xs[q + 2] = x[q], zeros around
-constexpr uint32_t kFusedSmem = 1024 + kWBytes + kSlabs * kSlabBytes + 4 * kFusedXs + 128;
+// two buffers of staged inputs, a trace's and the next one's
+constexpr uint32_t kFusedSmem = 1024 + kWBytes + kSlabs * kSlabBytes + 2 * 4 * kFusedXs + 128;
 
 __device__ __forceinline__ bool group_any(int bar_id, bool v) {
     uint32_t r;
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     const uint32_t sW = base;
     const uint32_t sSlab = base + kWBytes;
     float *const xs = reinterpret_cast<float *>(gbase + kWBytes + kSlabs * kSlabBytes);
-    const uint32_t sBar = base + kWBytes + kSlabs * kSlabBytes + 4 * kFusedXs;
+    const uint32_t sBar = base + kWBytes + kSlabs * kSlabBytes + 2 * 4 * kFusedXs;
     // barriers: slab_full[3] at sBar + 8b, slab_empty[3] at sBar + 24 + 8b,
     // acc_full[2] at sBar + 48 + 8a; then the TMEM address and the abort flag
     uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + (sBar - base) + 64);
@@ -425,8 +426,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         *abort_flag = 0;
         *last_issued = 0;
     }
-    if (tid < 2) xs[tid] = 0.0f;
-    if (tid < (int)kFusedXs - kLin - 2) xs[kLin + 2 + tid] = 0.0f;
+    if (tid < 2) xs[tid] = xs[kFusedXs + tid] = 0.0f;
+    if (tid < (int)kFusedXs - kLin - 2) xs[kLin + 2 + tid] = xs[kFusedXs + kLin + 2 + tid] = 0.0f;
     // slab rows of positions -2, -1 (row 0 of each plane) and 256, 257 (row
     // 8 * 17 + 7) are zero padding, written once: the producers never write them
     for (int e = tid; e < kSlabs * 2 * 2 * 8; e += kFusedThreads) {
@@ -479,14 +480,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             const int b = j % kSlabs;
             bool ok = true;
             if (j >= kSlabs) ok = mbar_wait(sBar + 24 + 8 * b, (uint32_t)(j / kSlabs - 1) & 1u);
-            // also: every producer is done with the previous tile's inputs
+            // this trace's inputs into buffer j mod 2 (every producer finished
+            // trace j - 2, the last user of that buffer, before the barrier of
+            // trace j - 1), then one barrier: the inputs are in, and no wait
+            // gave up
+            float *const xb_ = xs + (j & 1) * kFusedXs;
+            xb_[p + 2] = __bfloat162float(__float2bfloat16(xa));
+            xb_[p + 258] = __bfloat162float(__float2bfloat16(xb));
             if (group_any(2, !ok || *abort_flag != 0)) {
                 if (p == 0) *abort_flag = 1;
                 break;
             }
-            xs[p + 2] = __bfloat162float(__float2bfloat16(xa));
-            xs[p + 258] = __bfloat162float(__float2bfloat16(xb));
-            group_sync(2);
             const int tn = t + (int)gridDim.x;
             if (tn < ntiles) {
                 xa = x[(size_t)tn * kLin + p];
@@ -502,7 +506,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 uint64_t xin[kTaps];
 #pragma unroll
                 for (int k = 0; k < kTaps; ++k) {
-                    const float xv = xs[2 * q + k];  // x[2q + k - 2]
+                    const float xv = xb_[2 * q + k];  // x[2q + k - 2]
                     xin[k] = f2(xv, xv);
                 }
                 uint32_t pk[4];
@@ -542,13 +546,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     } else {
         // ---------------- MMA issue and epilogue (barrier id 1)
         const int g = tid - 256, gw = warp - 8;
+        bool bad = false;  // an accumulator wait of this thread gave up
         for (int j = 0;; ++j) {
             const int t = blockIdx.x + j * (int)gridDim.x;
             const bool have = t < ntiles;
             tc_fence_before();
-            const bool stop = group_any(1, *abort_flag != 0);
+            const bool stop = group_any(1, bad || *abort_flag != 0);
             tc_fence_after();
-            if (stop) break;
+            if (stop) {
+                if (bad) *abort_flag = 1;
+                break;
+            }
             if (have && g == 0) {
                 const int b = j % kSlabs;
                 if (!mbar_wait(sBar + 8 * b, (uint32_t)(j / kSlabs) & 1u)) {
@@ -580,11 +588,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             if (j > 0) {
                 // epilogue of tile j - 1 (issued: tile j - 1 had its MMAs unless aborted)
                 const int jp = j - 1;
-                const bool got = mbar_wait(sBar + 48 + 8 * (jp & 1), (uint32_t)(jp >> 1) & 1u);
-                if (group_any(1, !got)) {
-                    if (g == 0) *abort_flag = 1;
-                    break;
-                }
+                if (!mbar_wait(sBar + 48 + 8 * (jp & 1), (uint32_t)(jp >> 1) & 1u)) bad = true;
                 tc_fence_after();
                 const int tp = t - (int)gridDim.x;
                 const int quarter = gw & 3, half = gw >> 2;
@@ -613,6 +617,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             }
             if (!have) break;
         }
+        if (bad) *abort_flag = 1;
         // every commit's arrival lands before the CTA leaves (the last tiles'
         // slab_empty arrivals have no producer waiting for them; after a
         // timeout, MMAs issued but never waited for must also finish before
@@ -625,10 +630,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 mbar_wait(sBar + 24 + 8 * (jj % kSlabs), (jj / kSlabs) & 1u);
         }
     }
-    if (tid == 0 && *abort_flag) atomicOr(status, PCHASE_DEV_TIMEOUT);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (tid == 0 && *abort_flag) atomicOr(status, PCHASE_DEV_TIMEOUT);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols)
