@@ -1,7 +1,9 @@
-// Tensor-core convolution of the learned inverse's 64-channel layers
-// (kernel 5, stride 2, zero padding 2; S7) on sm_103a's fifth-generation
-// tensor cores: tcgen05.mma with both operands in shared memory and the FP32
-// accumulator in tensor memory (TMEM), implicit im2col.
+// The learned inverse's network at inference (S7) on sm_103a's fifth-
+// generation tensor cores: tcgen05.mma with both operands in shared memory
+// and the FP32 accumulator in tensor memory (TMEM).  Three kernels: layers 1
+// and 2 (conv12_tc_kernel), layers 3 and 4 (conv34_tc_kernel), FC + heads
+// (fc_heads_tc_kernel).  The 64-channel layers (kernel 5, stride 2, zero
+// padding 2) use an implicit im2col:
 //
 // out[b][p][co] = GELU(bias[co] + sum_k sum_ci W[co][k*64 + ci] * x[b][2p + k - 2][ci])
 //
@@ -16,16 +18,11 @@
 // row group k / 2 on: 128 consecutive rows of 128 bytes (64 BF16 channels), a
 // canonical K-major operand with the 128-byte swizzle, every tap starting on
 // a 1024-byte swizzle-atom boundary.  The weights are five such N=64 x K=64
-// tiles, loaded once per CTA.
-//
-// Each persistent CTA (256 threads) loops over tiles: slabs stream in by
-// cp.async two tiles ahead (three buffers), the MMAs of tile j run while the
-// epilogue of tile j-1 (tcgen05.ld from the other TMEM accumulator, bias,
-// GELU, BF16 store) runs on all eight warps: warp w reads TMEM lanes
-// 32 (w % 4) .. +31 (the lanes its quarter of the CTA may access) and
-// columns 32 (w / 4) .. +31.  Completion waits on an mbarrier
-// give up after 2 s of %globaltimer: the kernel then ORs PCHASE_DEV_TIMEOUT
-// into *status, stops, waits for its own copies, frees its TMEM and returns.
+// tiles, loaded once per CTA.  An epilogue warp w reads TMEM lanes
+// 32 (w % 4) .. +31 (the lanes its quarter of the CTA may access).
+// Completion waits on an mbarrier give up after 2 s of %globaltimer: the
+// kernel then ORs PCHASE_DEV_TIMEOUT into *status, stops, waits for its own
+// copies and MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -44,7 +41,6 @@ constexpr uint32_t kSlabBytes = 2 * kPlaneBytes;      // 36 KB
 constexpr int kSlabs = 3;
 constexpr uint32_t kWBytes = kTaps * kCh * 128;       // 40 KB
 constexpr uint32_t kTmemCols = 128;                   // two 64-column accumulators
-constexpr uint32_t kSmemBytes = 1024 + kWBytes + kSlabs * kSlabBytes + 64;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 // Instruction descriptor of tcgen05.mma .kind::f16: FP32 accumulator (bits
@@ -190,164 +186,6 @@ __device__ __forceinline__ uint32_t gelu2h_bf16(uint64_t xh) {
     return d;
 }
 
-constexpr int kThreads = 256;
-
-__global__ void __launch_bounds__(kThreads, 1)
-    conv_tc_kernel(const __nv_bfloat16 *__restrict__ x, int nb, int lin,
-                   const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
-                   __nv_bfloat16 *__restrict__ out, float *__restrict__ pre,
-                   uint32_t *__restrict__ status) {
-    extern __shared__ uint8_t dsm[];
-    const uint32_t raw = smem_u32(dsm);
-    const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
-    uint8_t *const gbase = dsm + (base - raw);
-    const uint32_t sW = base;
-    const uint32_t sSlab = base + kWBytes;
-    const uint32_t sBar = base + kWBytes + kSlabs * kSlabBytes;  // two mbarriers
-    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + kWBytes + kSlabs * kSlabBytes + 16);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lout = lin >> 1;
-    const int M = nb * lout;
-    const int ntiles = (M + kTileRows - 1) / kTileRows;
-
-    // weights: tap k is W[:, 64k .. 64k+63], 64 rows of 128 bytes, swizzled
-    for (int e = tid; e < kTaps * kCh * 8; e += kThreads) {
-        const int k = e >> 9, co = (e >> 3) & 63, c = e & 7;
-        cp_async16(sW + k * 8192 + co * 128 + ((c ^ (co & 7)) << 4),
-                   W + (size_t)co * (kTaps * kCh) + k * kCh + c * 8, true);
-    }
-    cp_async_commit();
-
-    // slab loader: thread (plane, i, c, half) copies 16-byte chunk c of rows
-    // 8G + i, G in its half of 0..17: nine copies two input positions apart
-    const int ld_c = tid & 7, ld_i = (tid >> 3) & 7, ld_pl = (tid >> 6) & 1, ld_h = tid >> 7;
-    const int ld_g0 = ld_h * (kGroups / 2);
-    auto load_slab = [&](int buf, int tile) {
-        if (tile < ntiles) {
-            const int mi = tile * kTileRows + 16 * ld_i;  // first of the 16 output rows of group i
-            const int b = mi / lout, p0 = mi - b * lout;
-            const bool row_ok = mi < M;
-            const int q0 = 2 * p0 + 2 * (ld_g0 - 1) + ld_pl;
-            const __nv_bfloat16 *src = x + ((size_t)(row_ok ? b : 0) * lin) * kCh + ld_c * 8;
-            const uint32_t dst = sSlab + buf * kSlabBytes + ld_pl * kPlaneBytes +
-                                 (8 * ld_g0 + ld_i) * 128 + ((ld_c ^ ld_i) << 4);
-#pragma unroll
-            for (int gg = 0; gg < kGroups / 2; ++gg) {
-                const int q = q0 + 2 * gg;
-                const bool ok = row_ok && q >= 0 && q < lin;
-                cp_async16(dst + gg * 1024, ok ? src + (size_t)q * kCh : x, ok);
-            }
-        }
-        cp_async_commit();  // one group per call, empty or not
-    };
-
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tslot)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    load_slab(0, blockIdx.x);
-    load_slab(1, blockIdx.x + gridDim.x);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-
-    // epilogue of the tile whose MMAs went to accumulator acc
-    auto epilogue = [&](int tile, int j) -> bool {
-        const int acc = j & 1;
-        const bool got = mbar_wait(sBar + 8 * acc, (uint32_t)(j >> 1) & 1u);
-        if (!__syncthreads_and(got)) {
-            if (tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
-            return false;
-        }
-        tc_fence_after();
-        const int quarter = warp & 3, half = warp >> 2;
-        const uint32_t taddr = tmem + (uint32_t)acc * 64u + (uint32_t)half * 32u +
-                               ((uint32_t)(quarter * 32) << 16);
-        uint32_t v[2][16];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) tmem_ld16(taddr + q * 16, v[q]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int r = quarter * 32 + lane;
-        const int m = tile * kTileRows + 16 * (r & 7) + (r >> 3);
-        if (m < M) {
-            float *pr = pre ? pre + (size_t)m * kCh + half * 32 : nullptr;
-            uint4 *o4 = reinterpret_cast<uint4 *>(out + (size_t)m * kCh + half * 32);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                uint32_t pk[8];
-#pragma unroll
-                for (int e = 0; e < 16; e += 2) {
-                    const int n = half * 32 + q * 16 + e;
-                    const float a0 = __uint_as_float(v[q][e]) + __ldg(bias + n);
-                    const float a1 = __uint_as_float(v[q][e + 1]) + __ldg(bias + n + 1);
-                    if (pr) {
-                        pr[q * 16 + e] = a0;
-                        pr[q * 16 + e + 1] = a1;
-                    }
-                    pk[e >> 1] = gelu2_bf16(f2(a0, a1));
-                }
-                o4[2 * q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                o4[2 * q + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-        }
-        tc_fence_before();
-        return true;
-    };
-
-    int j = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-        // slab j (and the weights) in shared memory, visible to the tensor cores
-        cp_async_wait1();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-            const uint32_t d = tmem + (uint32_t)(j & 1) * 64u;
-            const uint32_t slab = sSlab + (uint32_t)(j % kSlabs) * kSlabBytes;
-#pragma unroll
-            for (int k = 0; k < kTaps; ++k) {
-                const uint32_t a0 = slab + (uint32_t)(k & 1) * kPlaneBytes + (uint32_t)(k >> 1) * 1024u;
-                const uint32_t b0 = sW + (uint32_t)k * 8192u;
-#pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    mma_bf16(d, sw128_desc(a0 + 32u * s), sw128_desc(b0 + 32u * s),
-                             (k | s) != 0 ? 1u : 0u);
-            }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    sBar + 8u * (uint32_t)(j & 1))
-                : "memory");
-        }
-        if (j > 0 && !epilogue(t - (int)gridDim.x, j - 1)) {
-            ok = false;
-            break;
-        }
-        // the buffer of tile j - 1 is free once its MMAs completed
-        load_slab((j + 2) % kSlabs, t + 2 * (int)gridDim.x);
-    }
-    if (ok && j > 0) epilogue(blockIdx.x + (j - 1) * (int)gridDim.x, j - 1);
-    cp_async_wait_all();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
-                     : "memory");
-}
-
 // ------------------------------------------- first two layers, fused
 // Inference of layers 1 and 2 without the first layer's activations ever
 // leaving the SM.  One tile is one trace: layer 2's 128 output positions are
@@ -357,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // as the unfused path rounds them): row 8G + i of plane pl holds layer-1
 // position q = 32i + 2G - 2 + pl, channels in 16-byte chunks with the
 // 128-byte swizzle, zeros outside 0 <= q < 256.  The other eight warps issue
-// the MMAs (one thread) and run the epilogue, as conv_tc_kernel does.  The two
+// the MMAs (one thread) and run the epilogue (bias, GELU, BF16 store).  The two
 // roles meet on mbarriers: slab_full (the producers' 256 arrivals after a
 // proxy fence), slab_empty (tcgen05.commit once the MMAs that read a slab
 // are done; three slabs in flight) and acc_full (two TMEM accumulators).
@@ -378,9 +216,6 @@ __device__ __forceinline__ bool group_any(int bar_id, bool v) {
         : "r"((uint32_t)v), "r"(bar_id)
         : "memory");
     return r != 0;
-}
-__device__ __forceinline__ void group_sync(int bar_id) {
-    asm volatile("bar.sync %0, 256;" ::"r"(bar_id) : "memory");
 }
 
 __global__ void __launch_bounds__(kFusedThreads, 1)
@@ -406,7 +241,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = nb;
 
-    // layer 2's weights, as conv_tc_kernel loads them
+    // layer 2's weights: tap k is W2[:, 64k .. 64k+63], 64 rows of 128 bytes, swizzled
     for (int e = tid; e < kTaps * kCh * 8; e += kFusedThreads) {
         const int k = e >> 9, co = (e >> 3) & 63, c = e & 7;
         cp_async16(sW + k * 8192 + co * 128 + ((c ^ (co & 7)) << 4),
@@ -849,14 +684,14 @@ __global__ void __launch_bounds__(128, 1)
 // Inference of layers 3 and 4 in one kernel.  An iteration takes 4 traces
 // (one 128-row tile of layer 4): the layer-3 outputs of its two 128-row tiles
 // (2 traces each) go from TMEM through bias and GELU straight into layer 4's
-// input slab in shared memory, laid out as conv_tc_kernel stages an input
+// input slab in shared memory, laid out as the implicit im2col above wants
 // (row 8g + i of plane pl holds position 32 (i & 1) + 2 (g - 1) + pl of the
 // tile's trace i / 2), and layer 4's MMAs run from there; only layer 4's
 // outputs go to global memory.  A layer-3 position q of trace b lands in row
 // 8 ((q >> 1) + 1) + 2b when q <= 33 and in row 8 ((q >> 1) - 15) + 2b + 1
 // when q >= 30 (plane q & 1); rows 2b of group 0 and 2b + 1 of group 17 are
-// the zero padding, written once.  Layer-3 input slabs are loaded as in
-// conv_tc_kernel, three buffers.
+// the zero padding, written once.  Layer-3 input slabs stream in by cp.async
+// (three buffers).
 constexpr int kL34Threads = 512;  // the first 256 load slabs; all run the epilogues
 constexpr uint32_t kL34TmemCols = 256;  // accumulators: layer-3 tiles A, B and layer 4
 constexpr uint32_t kL34Smem = 1024 + 2 * kWBytes + kSlabs * kSlabBytes + kSlabBytes + 64;
@@ -1071,24 +906,6 @@ __global__ void __launch_bounds__(kL34Threads, 1)
 }
 
 }  // namespace
-
-cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16 *W,
-                    const float *bias, __nv_bfloat16 *out, float *pre, uint32_t *status,
-                    int sms, cudaStream_t st) {
-    const int lout = lin / 2;
-    if (nb <= 0) return cudaSuccess;
-    if (lin % 2 || lout % 16 || !(lout >= kTileRows ? lout % kTileRows == 0 : kTileRows % lout == 0))
-        return cudaErrorInvalidValue;
-    if (!status) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
-    if (e != cudaSuccess) return e;
-    const long long ntiles = ((long long)nb * lout + kTileRows - 1) / kTileRows;
-    const int grid = (int)std::min<long long>(ntiles, std::max(1, sms));
-    conv_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, nb, lin, W, bias, out, pre, status);
-    return cudaGetLastError();
-}
 
 cudaError_t conv34_tc(const __nv_bfloat16 *x, int nb, const __nv_bfloat16 *W3, const float *bias3,
                       const __nv_bfloat16 *W4, const float *bias4, __nv_bfloat16 *out,

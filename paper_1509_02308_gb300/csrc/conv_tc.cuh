@@ -9,16 +9,6 @@
 
 namespace pchase {
 
-// out[b][p][:] = GELU(bias + conv(x)[b][p][:]) for x [nb][lin][64] BF16 (row
-// of 64 channels per position), W [64][5*64] BF16 (column k*64 + ci), lout =
-// lin / 2 output positions; pre (may be NULL) receives the FP32 values before
-// GELU.  lout must be a multiple of 16 that divides 128 or is a multiple of
-// it.  A tensor-core completion wait that gives up ORs PCHASE_DEV_TIMEOUT into
-// *status (device).  Returns cudaErrorInvalidValue for unsupported shapes.
-cudaError_t conv_tc(const __nv_bfloat16 *x, int nb, int lin, const __nv_bfloat16 *W,
-                    const float *bias, __nv_bfloat16 *out, float *pre, uint32_t *status,
-                    int sms, cudaStream_t st);
-
 // Inference of the first two layers in one kernel: out [nb][128][64] BF16 =
 // layer 2's GELU outputs for x [nb][512] FP32 (rounded to BF16 as inputs),
 // W1 [64][5] BF16 + bias1, W2 [64][5*64] BF16 + bias2.  The first layer's

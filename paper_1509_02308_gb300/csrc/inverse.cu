@@ -961,14 +961,6 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
     }
     for (int l = l0; l < 4; ++l) {
         const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
-        if (cin == kCh && !train) {
-            // inference: tcgen05 tensor cores, TMEM accumulators, implicit im2col
-            __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
-            INV_CUDA(conv_tc(in, (int)B, lin, wb + L.w[l], wf + L.b[l], o, nullptr,
-                             at<uint32_t>(work, h->status), device_sms(), st));
-            in = o;
-            continue;
-        }
         if (cin == kCh) {
             // implicit im2col; training also keeps the explicit columns for dW
             if (train) {
