@@ -28,6 +28,7 @@
 #include <algorithm>
 
 #include "conv_tc.cuh"
+#include "tc_common.cuh"
 
 namespace pchase {
 namespace {
@@ -41,7 +42,6 @@ constexpr uint32_t kSlabBytes = 2 * kPlaneBytes;      // 36 KB
 constexpr int kSlabs = 3;
 constexpr uint32_t kWBytes = kTaps * kCh * 128;       // 40 KB
 constexpr uint32_t kTmemCols = 128;                   // two 64-column accumulators
-constexpr unsigned long long kWaitNs = 2000000000ull;
 
 // Instruction descriptor of tcgen05.mma .kind::f16: FP32 accumulator (bits
 // 4-5 = 1), BF16 A and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 =
@@ -49,141 +49,8 @@ constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
                             ((uint32_t)(kTileRows >> 4) << 24);
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
-// bytes in 8-row atoms of 1024 bytes (stride byte offset 1024), descriptor
-// version 1 (bits 46-47), layout type 2 = SWIZZLE_128B (bits 61-63).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(16u >> 4) << 16) |
-           ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
-    const int n = valid ? 16 : 0;  // 0: zero-fill (padding, rows past the end)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait1() {
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const unsigned long long t0 = globaltimer();
-    for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (globaltimer() - t0 > kWaitNs) return false;
-    }
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-
-// Two FP32 lanes in one 64-bit register pair (low = first).  The f32x2
-// forms issue one instruction for two IEEE operations with the same
-// rounding as their scalar forms, so results are bit-identical.
-__device__ __forceinline__ uint64_t f2(float lo, float hi) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2split(uint64_t v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-// tanh form of GELU (Hendrycks & Gimpel 2016) on both lanes, rounded to a
-// BF16 pair (low lane in the low half), with the hardware tanh
-// (tanh.approx.f32, relative error about 2^-11, below the BF16 output's
-// 2^-8), arranged per lane as h + h tanh(x (k0 + k0 k1 x^2)), h = x / 2:
-// four f32x2 operations, two tanh and one conversion per pair
-__device__ __forceinline__ uint32_t gelu2_bf16(uint64_t x) {
-    const float k0 = 0.7978845608028654f, k01 = 0.7978845608028654f * 0.044715f;
-    const uint64_t u = mul2(x, fma2(f2(k01, k01), mul2(x, x), f2(k0, k0)));
-    float u0, u1, t0, t1;
-    f2split(u, u0, u1);
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(u0));
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(u1));
-    const uint64_t h = mul2(f2(0.5f, 0.5f), x);
-    float r0, r1;
-    f2split(fma2(h, f2(t0, t1), h), r0, r1);
-    uint32_t d;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(r1), "f"(r0));
-    return d;
-}
-
-// gelu2_bf16 of 2 xh, given xh (both lanes halved exactly): with x = 2 xh,
-// h = xh and u = xh (2 k0 + 8 k0 k1 xh^2), the same values as gelu2_bf16
-// computes, one multiply fewer
-__device__ __forceinline__ uint32_t gelu2h_bf16(uint64_t xh) {
-    const float k0 = 0.7978845608028654f, k01 = 0.7978845608028654f * 0.044715f;
-    const uint64_t u = mul2(xh, fma2(f2(8.0f * k01, 8.0f * k01), mul2(xh, xh), f2(2.0f * k0, 2.0f * k0)));
-    float u0, u1, t0, t1;
-    f2split(u, u0, u1);
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(u0));
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(u1));
-    float r0, r1;
-    f2split(fma2(xh, f2(t0, t1), xh), r0, r1);
-    uint32_t d;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(r1), "f"(r0));
-    return d;
+    mma_bf16_id(d_tmem, a, b, kIdesc, acc);
 }
 
 // ------------------------------------------- first two layers, fused
@@ -206,17 +73,6 @@ constexpr int kFusedThreads = 512;
 constexpr uint32_t kFusedXs = 520;  // staged inputs: xs[q + 2] = x[q], zeros around
 // two buffers of staged inputs, a trace's and the next one's
 constexpr uint32_t kFusedSmem = 1024 + kWBytes + kSlabs * kSlabBytes + 2 * 4 * kFusedXs + 128;
-
-__device__ __forceinline__ bool group_any(int bar_id, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n"
-        " bar.red.or.pred p, %2, 256, q;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "r"(bar_id)
-        : "memory");
-    return r != 0;
-}
 
 __global__ void __launch_bounds__(kFusedThreads, 1)
     conv12_tc_kernel(const float *__restrict__ x, int nb, const __nv_bfloat16 *__restrict__ W1,
@@ -503,15 +359,6 @@ constexpr uint32_t kIdescFc = (1u << 4) | (1u << 7) | (1u << 10) |
 constexpr uint32_t kIdescHeads = (1u << 4) | (1u << 7) | (1u << 10) |
                                  ((uint32_t)(kHeadsPad >> 3) << 17) |
                                  ((uint32_t)(kTileRows >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16_id(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                            uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
 
 __global__ void __launch_bounds__(128, 1)
     fc_heads_tc_kernel(const __nv_bfloat16 *__restrict__ act, int nb,

@@ -1,4 +1,5 @@
-// Tensor-core (tcgen05) convolution of the learned inverse (conv_tc.cu).
+// Tensor-core (tcgen05) kernels of the learned inverse: inference
+// (conv_tc.cu) and the training step's convolution backward (train_tc.cu).
 #pragma once
 
 #include <cstdint>
@@ -35,5 +36,22 @@ cudaError_t conv34_tc(const __nv_bfloat16 *x, int nb, const __nv_bfloat16 *W3, c
 cudaError_t fc_heads_tc(const __nv_bfloat16 *act, int nb, const __nv_bfloat16 *W4,
                         const float *bias4, const __nv_bfloat16 *W5, const float *bias5,
                         float *logits, uint32_t *status, cudaStream_t st);
+
+// Training step, backward of one 64-channel convolution layer (lout = 128,
+// 64 or 32 output positions per trace; lin = 2 lout): given dact [nb * lout][64]
+// FP32 (gradient of the layer's GELU outputs), pre [nb * lout][64] FP32 (its
+// pre-activations), x [nb][lin][64] BF16 (its inputs) and W [64][5*64] BF16,
+// adds the weight gradient into gW [64][5*64] and the bias gradient into
+// gb [64] (FP32 atomics: both must hold their running sums, usually zero),
+// and writes the input gradient dx [nb][lin][64] FP32.  tcgen05 tensor cores;
+// a wait that gives up ORs PCHASE_DEV_TIMEOUT into *status (device).
+cudaError_t conv_back_tc(const float *dact, const float *pre, const __nv_bfloat16 *x, int nb,
+                         int lout, const __nv_bfloat16 *W, float *gW, float *gb, float *dx,
+                         uint32_t *status, int sms, cudaStream_t st);
+
+// The same for the first layer (one input channel, x [nb][512] BF16, W
+// [64][5]; no input gradient), on CUDA cores.
+cudaError_t conv0_back(const float *dact, const float *pre, const __nv_bfloat16 *x, int nb,
+                       float *gW, float *gb, int sms, cudaStream_t st);
 
 }  // namespace pchase

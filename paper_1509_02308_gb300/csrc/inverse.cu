@@ -383,50 +383,6 @@ constexpr int kFlat = 32 * kCh;
 constexpr int kLogits = 31;
 __constant__ int c_head_off[5] = {0, 17, 21, 28, 31};
 
-// im2col for a stride-2, pad-2, k=5 convolution over channel-last input
-// x[b][li][ci] (li < lin) -> cols[b*lout + lo][kk*cin + ci]
-__global__ void im2col_kernel(const __nv_bfloat16 *x, int nb, int lin, int cin,
-                              __nv_bfloat16 *cols) {
-    const int lout = lin / 2;
-    const size_t total = (size_t)nb * lout * kKer * cin;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int ci = (int)(e % cin);
-        size_t r = e / cin;
-        const int kk = (int)(r % kKer);
-        r /= kKer;
-        const int lo = (int)(r % lout);
-        const int b = (int)(r / lout);
-        const int li = 2 * lo + kk - 2;
-        __nv_bfloat16 v = __float2bfloat16(0.0f);
-        if (li >= 0 && li < lin) v = x[((size_t)b * lin + li) * cin + ci];
-        cols[e] = v;
-    }
-}
-
-// gather-form col2im: dx[b][li][ci] = sum over (lo, kk) with 2 lo + kk - 2 = li
-__global__ void col2im_kernel(const float *dcols, int nb, int lin, int cin, float *dx) {
-    const int lout = lin / 2;
-    const size_t total = (size_t)nb * lin * cin;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int ci = (int)(e % cin);
-        const size_t r = e / cin;
-        const int li = (int)(r % lin);
-        const int b = (int)(r / lin);
-        float s = 0.0f;
-#pragma unroll
-        for (int kk = 0; kk < kKer; ++kk) {
-            const int t = li + 2 - kk;
-            if (t < 0 || (t & 1)) continue;
-            const int lo = t >> 1;
-            if (lo >= lout) continue;
-            s += dcols[((size_t)b * lout + lo) * (kKer * cin) + kk * cin + ci];
-        }
-        dx[e] = s;
-    }
-}
-
 // dz = dy * gelu'(pre) (FP32 in, BF16 out for the next GEMMs)
 __global__ void gelu_back_kernel(const float *dy, const float *pre, size_t n, float *dzf,
                                  __nv_bfloat16 *dzb) {
@@ -436,15 +392,6 @@ __global__ void gelu_back_kernel(const float *dy, const float *pre, size_t n, fl
         if (dzf) dzf[i] = v;
         dzb[i] = __float2bfloat16(v);
     }
-}
-
-// column sums of a row-major [rows, cols] FP32 matrix (bias gradients)
-__global__ void colsum_kernel(const float *x, int rows, int cols, float *out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += x[(size_t)r * cols + c];
-    out[c] = s;
 }
 
 // softmax cross-entropy over the four heads; loss (mean over the batch and
@@ -907,7 +854,7 @@ struct pchase_inverse {
     InverseLayout L;
     uint32_t max_batch;
     size_t p_w, p_wb, p_g, p_m, p_v, p_bytes;
-    size_t status, xb, cols[4], pre[4], act[4], pre4, h4, logits, dlog, dlogb, dh, dzf, dzb, dbig,
+    size_t status, xb, pre[4], act[4], pre4, h4, logits, dlog, dlogb, dh, dzf, dzb, dbig,
         dsmall, work_bytes, infer_bytes;
 };
 
@@ -962,12 +909,7 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
     for (int l = l0; l < 4; ++l) {
         const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
         if (cin == kCh) {
-            // implicit im2col; training also keeps the explicit columns for dW
-            if (train) {
-                __nv_bfloat16 *cols = at<__nv_bfloat16>(work, h->cols[l]);
-                const size_t nc = (size_t)B * lout * kKer * cin;
-                im2col_kernel<<<grid_for(nc), 256, 0, st>>>(in, (int)B, lin, cin, cols);
-            }
+            // implicit im2col
             __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
             const int M = (int)(B * lout);
             conv64_kernel<<<(M + CBM - 1) / CBM, 256, 0, st>>>(
@@ -976,13 +918,7 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
             in = o;
             continue;
         }
-        // first layer (one input channel): direct; training keeps the
-        // explicit columns for its weight gradient
-        if (train) {
-            __nv_bfloat16 *cols = at<__nv_bfloat16>(work, h->cols[l]);
-            const size_t nc = (size_t)B * lout * kKer * cin;
-            im2col_kernel<<<grid_for(nc), 256, 0, st>>>(in, (int)B, lin, cin, cols);
-        }
+        // first layer (one input channel): direct
         __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
         conv1_kernel<<<std::min<uint32_t>(B, 152u * 8u), 256, 0, st>>>(
             in, (int)B, wb + L.w[l], wf + L.b[l], o, train ? at<float>(work, h->pre[l]) : nullptr);
@@ -1063,22 +999,19 @@ int pchase_inverse_create(uint32_t max_batch, pchase_inverse **out) {
     }
     h->logits = o; o = a256(o + 4 * B * kLogits);
     h->infer_bytes = o;
-    size_t big = B * kFlat;  // largest per-layer fp32 gradient
+    size_t big = B * kFlat;  // largest per-layer FP32 activation gradient
     for (int l = 0; l < 4; ++l) {
-        const size_t lout = h->L.lin[l] / 2, cin = h->L.cin[l];
-        h->cols[l] = o; o = a256(o + 2 * B * lout * kKer * cin);
+        const size_t lout = h->L.lin[l] / 2;
         h->pre[l] = o; o = a256(o + 4 * B * lout * kCh);
-        big = std::max(big, B * lout * kKer * cin);
         big = std::max(big, B * lout * kCh);
-        big = std::max(big, B * (size_t)h->L.lin[l] * cin);
     }
     h->pre4 = o; o = a256(o + 4 * B * kHidden);
     h->h4 = o; o = a256(o + 2 * B * kHidden);
     h->dlog = o; o = a256(o + 4 * B * kLogits);
     h->dlogb = o; o = a256(o + 2 * B * kLogits);
     h->dh = o; o = a256(o + 4 * B * kHidden);
-    h->dzf = o; o = a256(o + 4 * big);
-    h->dzb = o; o = a256(o + 2 * big);
+    h->dzf = o; o = a256(o + 4 * B * kHidden);
+    h->dzb = o; o = a256(o + 2 * B * kHidden);
     h->dbig = o; o = a256(o + 4 * big);
     h->dsmall = o; o = a256(o + 4 * big);
     h->work_bytes = o;
@@ -1204,27 +1137,21 @@ int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work,
         d.Cf = dbig; d.ldc = kFlat;  // d(act3) [B, 32, 64]
         INV_CUDA(gemm(false, true, d, st));
     }
-    // convolutions, last to first
-    for (int l = 3; l >= 0; --l) {
-        const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
-        const size_t rows = (size_t)B * lout, m = rows * kCh;
-        gelu_back_kernel<<<grid_for(m), 256, 0, st>>>(dbig, at<float>(work, h->pre[l]), m, dzf, dzb);
-        GemmArgs g{};
-        g.A = dzb; g.B = at<__nv_bfloat16>(work, h->cols[l]);
-        g.M = kCh; g.N = kKer * cin; g.K = (int)rows; g.lda = kCh; g.ldb = kKer * cin;
-        g.Cf = grad + L.w[l]; g.ldc = kKer * cin; g.splitk = splitk_for(g.M, g.N, g.K);
-        INV_CUDA(gemm(true, true, g, st));
-        colsum_atomic_kernel<<<dim3(1, (unsigned)((rows + 1023) / 1024)), 64, 0, st>>>(
-            dzf, (int)rows, kCh, 1024, grad + L.b[l]);
-        if (l > 0) {
-            GemmArgs d{};
-            d.A = dzb; d.B = wb + L.w[l];
-            d.M = (int)rows; d.N = kKer * cin; d.K = kCh; d.lda = kCh; d.ldb = kKer * cin;
-            d.Cf = dsmall; d.ldc = kKer * cin;
-            INV_CUDA(gemm(false, true, d, st));
-            const size_t nx = (size_t)B * lin * cin;
-            col2im_kernel<<<grid_for(nx), 256, 0, st>>>(dsmall, (int)B, lin, cin, dbig);
+    // convolutions, last to first: the three 64-channel layers on the tensor
+    // cores (gelu backward, weight and bias gradients, input gradient into
+    // the other FP32 buffer), the first layer on CUDA cores
+    {
+        float *dcur = dbig, *dnext = dsmall;
+        const int sms = device_sms();
+        for (int l = 3; l >= 1; --l) {
+            INV_CUDA(conv_back_tc(dcur, at<float>(work, h->pre[l]),
+                                  at<__nv_bfloat16>(work, h->act[l - 1]), (int)B, L.lin[l] / 2,
+                                  wb + L.w[l], grad + L.w[l], grad + L.b[l], dnext,
+                                  at<uint32_t>(work, h->status), sms, st));
+            std::swap(dcur, dnext);
         }
+        INV_CUDA(conv0_back(dcur, at<float>(work, h->pre[0]), at<__nv_bfloat16>(work, h->xb),
+                            (int)B, grad + L.w[0], grad + L.b[0], sms, st));
     }
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)step + 1.0f), c2 = 1.0f - powf(b2, (float)step + 1.0f);

@@ -1,0 +1,462 @@
+// The learned inverse's training step (S7), backward through the four
+// convolution layers (kernel 5, stride 2, zero padding 2, 64 output channels):
+//
+//   out[b][lo][co] = GELU(pre[b][lo][co]),
+//   pre[b][lo][co] = bias[co] + sum_kk sum_ci W[co][kk*cin + ci] * x[b][2 lo + kk - 2][ci]
+//
+// Given dact = dL/d(out) in FP32, each layer's backward is
+//
+//   dz  = dact * GELU'(pre)                                  (FP32)
+//   gb[co]             += sum_(b,lo) dz[b][lo][co]           (FP32)
+//   gW[co][kk*cin+ci]  += sum_(b,lo) bf16(dz)[b][lo][co] * x[b][2 lo + kk - 2][ci]
+//   dx[b][p][ci]        = sum_(kk,lo : 2 lo + kk - 2 = p) sum_co bf16(dz)[b][lo][co] * W[co][kk*cin + ci]
+//
+// with the weights' BF16 copies and the layer's BF16 inputs as operands,
+// FP32 sums (the chain rule through Sec. 4.1's network; the rounding points
+// are the ones the forward pass uses).
+//
+// The three 64-channel layers run conv_back_tc_kernel on the tcgen05 tensor
+// cores.  A tile is 128 consecutive rows (b, lo), i.e. whole traces (lout is
+// 128, 64 or 32), so no sum ever crosses a tile edge.  Per tile:
+//   * dz from dact and pre (coalesced FP32 rows), its BF16 copy written three
+//     times into K-major 128-byte-swizzled operands S_j, S_j[q] = dz[q + 1 - j]
+//     (zero across a trace edge);
+//   * dx as two 128 x 64 sums in one N=128 accumulator: even positions
+//     dx[2q] = S_0 W_0 + S_1 W_2 + S_2 W_4, odd dx[2q + 1] = S_0 W_1 + S_1 W_3,
+//     with W_kk[co][ci] = W[co][kk*64 + ci] staged once per CTA as B operands
+//     (row n < 64: tap 2j, n >= 64: tap 2j + 1);
+//   * gW transposed, D[(kk, ci)][co] (320 rows in three M=128 tiles, N=64),
+//     accumulated in TMEM over all of the CTA's tiles with K = the tile's 128
+//     rows: both operands need the rows contiguous, so the layer's input
+//     window (32 KB, staged with cp.async) and dz are transposed in shared
+//     memory by ldmatrix.trans (the stride-2 gather of the input rows is in
+//     the ldmatrix row addresses) and stored K-major with the 128-byte swizzle.
+// The third gW tile reads 64 rows past the 320 it needs (whatever lies beyond
+// in shared memory): those accumulator rows are never read.  At the end each
+// CTA adds its gW and gb partial sums to the gradient with FP32 atomics.
+//
+// The first layer (one input channel, K = 5) has no tensor-core shape and
+// needs no dx: conv0_back_kernel does dz, gb and gW on CUDA cores.
+//
+// Completion waits on the mbarrier give up after 2 s of %globaltimer: the
+// CTA then ORs PCHASE_DEV_TIMEOUT into *status, waits (again with a limit) for
+// the MMAs it issued, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "conv_tc.cuh"
+#include "tc_common.cuh"
+
+namespace pchase {
+namespace {
+
+constexpr int kCh = 64;
+constexpr int kTaps = 5;
+constexpr int kRowsPerTile = 128;
+constexpr int kBackThreads = 256;
+
+// shared-memory layout (bytes from the 1024-aligned base)
+constexpr uint32_t kOffS = 0;                       // S_0, S_1, S_2: 128 rows x 128 B each
+constexpr uint32_t kOffWT = 3 * 16384;              // 3 B tiles of 128 rows (n) x 64 co
+constexpr uint32_t kOffXT = kOffWT + 3 * 16384;     // 2 K atoms of 320 rows (kk, ci) x 64 rows
+constexpr uint32_t kXTAtom = 320 * 128;
+constexpr uint32_t kOffDZT = kOffXT + 2 * kXTAtom;  // 2 K atoms of 64 rows (co) x 64 rows
+constexpr uint32_t kOffXS = kOffDZT + 2 * 8192;     // input window: 256 rows x 128 B
+constexpr uint32_t kOffZero = kOffXS + 256 * 128;   // one zero row (padding source)
+constexpr uint32_t kOffBar = kOffZero + 128;        // mbarrier, TMEM address, flags
+constexpr uint32_t kOffBias = kOffBar + 16;         // 64 FP32 bias partial sums
+constexpr uint32_t kBackSmem = 1024 + kOffBias + 64 * 4;
+static_assert(kOffXT + kXTAtom + 3 * 16384 <= kOffZero, "third gW tile reads past the window");
+static_assert(kBackSmem <= 232448, "shared memory");
+
+// tcgen05 instruction descriptors (FP32 accumulator, BF16 A and B, both
+// K-major, M = 128): N = 128 for dx, N = 64 for gW
+constexpr uint32_t idesc_n(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+constexpr uint32_t kIdescDx = idesc_n(128);
+constexpr uint32_t kIdescGw = idesc_n(64);
+constexpr uint32_t kBackTmemCols = 512;  // dx 128 + gW 3 x 64, rounded to a power of two
+
+__device__ __forceinline__ float gelu_grad_f(float x) {
+    // derivative of the tanh form of GELU (Hendrycks & Gimpel 2016)
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    const float u = k0 * (x + k1 * x * x * x);
+    const float t = tanhf(u);
+    return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * x * x);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1,
+                                              uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void st_shared_b32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// byte offset of 16-byte chunk c of row r in a K-major operand whose rows are
+// 128 bytes (64 BF16) with the 128-byte swizzle
+__device__ __forceinline__ uint32_t sw_chunk(uint32_t r, uint32_t c) {
+    return r * 128u + ((c ^ (r & 7u)) << 4);
+}
+
+__global__ void __launch_bounds__(kBackThreads, 1)
+    conv_back_tc_kernel(const float *__restrict__ dact, const float *__restrict__ pre,
+                        const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ W,
+                        int nb, int lout, float *__restrict__ gW, float *__restrict__ gb,
+                        float *__restrict__ dx, uint32_t *status) {
+    extern __shared__ uint8_t dsm[];
+    const uint32_t raw = smem_u32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *const gbase = dsm + (base - raw);
+    const uint32_t sS = base + kOffS, sWT = base + kOffWT, sXT = base + kOffXT;
+    const uint32_t sDZT = base + kOffDZT, sXS = base + kOffXS, sZero = base + kOffZero;
+    const uint32_t sBar = base + kOffBar;
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + kOffBar + 8);
+    float *const sbias = reinterpret_cast<float *>(gbase + kOffBias);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lin = 2 * lout;
+    const int nrows = nb * lout;
+    const int ntiles = (nrows + kRowsPerTile - 1) / kRowsPerTile;
+    const int tpt = kRowsPerTile / lout;  // traces per tile
+
+    // B operands of dx: tile j, row n = (tap 2j + n / 64, ci = n % 64), K = co
+    for (int e = tid; e < 3 * 128 * 8; e += kBackThreads) {
+        const int j = e >> 10, n = (e >> 3) & 127, c = e & 7;
+        const int kk = 2 * j + (n >> 6), ci = n & 63;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (kk < kTaps) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int co = c * 8 + 2 * q;
+                const __nv_bfloat16 a = W[(size_t)co * (kTaps * kCh) + kk * kCh + ci];
+                const __nv_bfloat16 b = W[(size_t)(co + 1) * (kTaps * kCh) + kk * kCh + ci];
+                w[q] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+            }
+        }
+        st_shared_v4(sWT + (uint32_t)j * 16384u + sw_chunk((uint32_t)n, (uint32_t)c),
+                     make_uint4(w[0], w[1], w[2], w[3]));
+    }
+    if (tid < 8) st_shared_v4(sZero + 16u * (uint32_t)tid, make_uint4(0u, 0u, 0u, 0u));
+    if (tid < kCh) sbias[tid] = 0.0f;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kBackTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int c = tid & 7;  // the 8 channels this thread takes in the dz phase
+    float bacc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) bacc[e] = 0.0f;
+    int it = 0;
+    bool timed_out = false;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int row0 = t * kRowsPerTile;
+        // ---- the input window of the tile's traces: row tb * lin + p holds
+        // position p of trace b0 + tb, chunk c at c ^ ((row / 2) mod 8)
+        const int b0 = t * tpt;
+        for (int e = tid; e < 256 * 8; e += kBackThreads) {
+            const int r = e >> 3, cc = e & 7;
+            const bool ok = b0 + r / lin < nb;
+            cp_async16(sXS + (uint32_t)r * 128u + (uint32_t)((cc ^ ((r >> 1) & 7)) << 4),
+                       x + ((size_t)b0 * lin + (ok ? r : 0)) * kCh + cc * 8, ok);
+        }
+        cp_async_commit();
+        // ---- dz (rows r0 + 32 i, channels 8c .. 8c + 7) into S_0, S_1, S_2
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = (tid >> 3) + 32 * i;
+            const int grow = row0 + r;
+            float d[8];
+            if (grow < nrows) {
+                const float4 *da = reinterpret_cast<const float4 *>(dact + (size_t)grow * kCh + c * 8);
+                const float4 *pa = reinterpret_cast<const float4 *>(pre + (size_t)grow * kCh + c * 8);
+                const float4 a0 = __ldg(da), a1 = __ldg(da + 1), p0 = __ldg(pa), p1 = __ldg(pa + 1);
+                d[0] = a0.x * gelu_grad_f(p0.x);
+                d[1] = a0.y * gelu_grad_f(p0.y);
+                d[2] = a0.z * gelu_grad_f(p0.z);
+                d[3] = a0.w * gelu_grad_f(p0.w);
+                d[4] = a1.x * gelu_grad_f(p1.x);
+                d[5] = a1.y * gelu_grad_f(p1.y);
+                d[6] = a1.z * gelu_grad_f(p1.z);
+                d[7] = a1.w * gelu_grad_f(p1.w);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) d[e] = 0.0f;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) bacc[e] += d[e];
+            const uint4 v = make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]),
+                                       pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+            const int lo = r % lout;
+            st_shared_v4(sS + 16384u + sw_chunk((uint32_t)r, (uint32_t)c), v);
+            // S_0[q] = dz[q + 1]
+            if (lo != 0) st_shared_v4(sS + sw_chunk((uint32_t)(r - 1), (uint32_t)c), v);
+            if (lo == lout - 1) st_shared_v4(sS + sw_chunk((uint32_t)r, (uint32_t)c), z);
+            // S_2[q] = dz[q - 1]
+            if (lo != lout - 1) st_shared_v4(sS + 32768u + sw_chunk((uint32_t)(r + 1), (uint32_t)c), v);
+            if (lo == 0) st_shared_v4(sS + 32768u + sw_chunk((uint32_t)r, (uint32_t)c), z);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // ---- transposes by ldmatrix.trans: 8 x 8 blocks of (8 channels) x
+        // (8 rows), four per instruction (channel chunks 4g .. 4g + 3).  A
+        // thread receives, per block, channel 8 cc + lane / 4 of rows
+        // 8 rb + 2 (lane % 4) and the next, stored as one 32-bit word.
+        {
+            const int mi = lane >> 3, j = lane & 7;
+            // input windows: XT[(kk, ci)][row], row = (b, lo) of the tile,
+            // = x[b][2 lo + kk - 2][ci] (zero outside the trace)
+            for (int u = warp; u < kTaps * 2 * 16; u += kBackThreads / 32) {
+                const int kk = u / 32, g = (u >> 4) & 1, rb = u & 15;
+                const int r = rb * 8 + j, tb = r / lout, lo = r % lout;
+                const int p = 2 * lo + kk - 2;
+                const int cc = 4 * g + mi;
+                uint32_t src = sZero;
+                if (p >= 0 && p < lin) {
+                    const int xr = tb * lin + p;
+                    src = sXS + (uint32_t)xr * 128u + (uint32_t)((cc ^ ((xr >> 1) & 7)) << 4);
+                }
+                uint32_t v[4];
+                ldsm_x4_trans(src, v[0], v[1], v[2], v[3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t m = (uint32_t)(kk * kCh + (4 * g + q) * 8 + (lane >> 2));
+                    st_shared_b32(sXT + (uint32_t)(rb >> 3) * kXTAtom + m * 128u +
+                                      ((((uint32_t)rb & 7u) ^ (m & 7u)) << 4) + 4u * (lane & 3),
+                                  v[q]);
+                }
+            }
+            // dz: DZT[co][row] from S_1
+            for (int u = warp; u < 2 * 16; u += kBackThreads / 32) {
+                const int g = u >> 4, rb = u & 15;
+                const uint32_t q0 = (uint32_t)(rb * 8 + j);
+                uint32_t v[4];
+                ldsm_x4_trans(sS + 16384u + sw_chunk(q0, (uint32_t)(4 * g + mi)), v[0], v[1], v[2],
+                              v[3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t co = (uint32_t)((4 * g + q) * 8 + (lane >> 2));
+                    st_shared_b32(sDZT + (uint32_t)(rb >> 3) * 8192u + co * 128u +
+                                      ((((uint32_t)rb & 7u) ^ (co & 7u)) << 4) + 4u * (lane & 3),
+                                  v[q]);
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // ---- MMAs (one thread): dx into columns 0..127, gW into 128 + 64 mt
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    mma_bf16_id(tmem, sw128_desc(sS + (uint32_t)j * 16384u + 32u * s),
+                                sw128_desc(sWT + (uint32_t)j * 16384u + 32u * s), kIdescDx,
+                                (j | s) != 0 ? 1u : 0u);
+#pragma unroll
+            for (int mt = 0; mt < 3; ++mt)
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+                        mma_bf16_id(tmem + 128u + 64u * (uint32_t)mt,
+                                    sw128_desc(sXT + (uint32_t)a * kXTAtom + (uint32_t)mt * 16384u + 32u * s),
+                                    sw128_desc(sDZT + (uint32_t)a * 8192u + 32u * s), kIdescGw,
+                                    (it | a | s) != 0 ? 1u : 0u);
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sBar)
+                : "memory");
+        }
+        const bool ok = mbar_wait(sBar, (uint32_t)it & 1u);
+        tc_fence_after();
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            ++it;
+            break;
+        }
+        // ---- dx epilogue: warp w reads lanes 32 (w % 4) .., columns 64 (w / 4) ..
+        {
+            const int lg = warp & 3, h = warp >> 2;
+            const int q = 32 * lg + lane;
+            uint32_t v[4][16];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(64 * h + 16 * k), v[k]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int grow = row0 + q;
+            if (grow < nrows) {
+                const int b = grow / lout, lo = grow % lout;
+                float4 *o = reinterpret_cast<float4 *>(dx + ((size_t)b * lin + 2 * lo + h) * kCh);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        o[4 * k + e] = make_float4(__uint_as_float(v[k][4 * e]),
+                                                   __uint_as_float(v[k][4 * e + 1]),
+                                                   __uint_as_float(v[k][4 * e + 2]),
+                                                   __uint_as_float(v[k][4 * e + 3]));
+            }
+        }
+        tc_fence_before();
+    }
+    // ---- partial sums into the gradient
+#pragma unroll
+    for (int e = 0; e < 8; ++e) atomicAdd(&sbias[c * 8 + e], bacc[e]);
+    if (it > 0 && !timed_out) {
+        const int lg = warp & 3;
+        for (int u = warp >> 2; u < 6; u += 2) {
+            const int mt = u >> 1, hh = u & 1;
+            uint32_t v[2][16];
+            tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 128u + 64u * (uint32_t)mt + 32u * hh, v[0]);
+            tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 128u + 64u * (uint32_t)mt + 32u * hh + 16u,
+                      v[1]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int m = mt * 128 + 32 * lg + lane;
+            if (m < kTaps * kCh) {
+                const int kk = m >> 6, ci = m & 63;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int co = 32 * hh + 16 * k + e;
+                        atomicAdd(gW + (size_t)co * (kTaps * kCh) + kk * kCh + ci,
+                                  __uint_as_float(v[k][e]));
+                    }
+            }
+        }
+    }
+    if (timed_out && tid == 0) {
+        // the last MMAs must finish before TMEM is freed
+        mbar_wait(sBar, (uint32_t)(it - 1) & 1u);
+        atomicOr(status, PCHASE_DEV_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < kCh) atomicAdd(gb + tid, sbias[tid]);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kBackTmemCols)
+                     : "memory");
+}
+
+// First layer (one input channel): dact, pre [nb * 256][64] FP32, x [nb][512]
+// BF16.  Thread (row, 8-channel chunk) over a grid-stride loop of rows; the
+// partial sums meet in shared memory, then one atomic per value and CTA.
+__global__ void __launch_bounds__(256) conv0_back_kernel(const float *__restrict__ dact,
+                                                         const float *__restrict__ pre,
+                                                         const __nv_bfloat16 *__restrict__ x,
+                                                         int nb, float *__restrict__ gW,
+                                                         float *__restrict__ gb) {
+    constexpr int kLout = 256, kLin = 512;
+    __shared__ float sw[kCh * kTaps], sb[kCh];
+    for (int e = threadIdx.x; e < kCh * kTaps; e += blockDim.x) sw[e] = 0.0f;
+    if (threadIdx.x < kCh) sb[threadIdx.x] = 0.0f;
+    __syncthreads();
+    const int c = threadIdx.x & 7;
+    float aw[8][kTaps], ab[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        ab[e] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kTaps; ++k) aw[e][k] = 0.0f;
+    }
+    const size_t nrows = (size_t)nb * kLout;
+    for (size_t row = (size_t)blockIdx.x * 32 + (threadIdx.x >> 3); row < nrows;
+         row += (size_t)gridDim.x * 32) {
+        const size_t b = row / kLout;
+        const int lo = (int)(row % kLout);
+        float xv[kTaps];
+#pragma unroll
+        for (int k = 0; k < kTaps; ++k) {
+            const int p = 2 * lo + k - 2;
+            xv[k] = (p >= 0 && p < kLin) ? __bfloat162float(x[b * kLin + p]) : 0.0f;
+        }
+        const float4 *da = reinterpret_cast<const float4 *>(dact + row * kCh + c * 8);
+        const float4 *pa = reinterpret_cast<const float4 *>(pre + row * kCh + c * 8);
+        const float4 a0 = __ldg(da), a1 = __ldg(da + 1), p0 = __ldg(pa), p1 = __ldg(pa + 1);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float d = av[e] * gelu_grad_f(pv[e]);
+            ab[e] += d;
+            const float db = __bfloat162float(__float2bfloat16(d));
+#pragma unroll
+            for (int k = 0; k < kTaps; ++k) aw[e][k] = fmaf(db, xv[k], aw[e][k]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        atomicAdd(&sb[c * 8 + e], ab[e]);
+#pragma unroll
+        for (int k = 0; k < kTaps; ++k) atomicAdd(&sw[(c * 8 + e) * kTaps + k], aw[e][k]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kCh * kTaps; e += blockDim.x) atomicAdd(gW + e, sw[e]);
+    if (threadIdx.x < kCh) atomicAdd(gb + threadIdx.x, sb[threadIdx.x]);
+}
+
+}  // namespace
+
+cudaError_t conv_back_tc(const float *dact, const float *pre, const __nv_bfloat16 *x, int nb,
+                         int lout, const __nv_bfloat16 *W, float *gW, float *gb, float *dx,
+                         uint32_t *status, int sms, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    if (lout != 128 && lout != 64 && lout != 32) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            conv_back_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBackSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntiles = (nb * lout + kRowsPerTile - 1) / kRowsPerTile;
+    const int grid = std::max(1, std::min(ntiles, sms));
+    conv_back_tc_kernel<<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, x, W, nb, lout, gW, gb,
+                                                               dx, status);
+    return cudaGetLastError();
+}
+
+cudaError_t conv0_back(const float *dact, const float *pre, const __nv_bfloat16 *x, int nb,
+                       float *gW, float *gb, int sms, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    const size_t rows = (size_t)nb * 256;
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>((rows + 31) / 32, (size_t)sms * 4));
+    conv0_back_kernel<<<grid, 256, 0, st>>>(dact, pre, x, nb, gW, gb);
+    return cudaGetLastError();
+}
+
+}  // namespace pchase
