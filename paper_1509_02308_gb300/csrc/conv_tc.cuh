@@ -54,4 +54,22 @@ cudaError_t conv_back_tc(const float *dact, const float *pre, const __nv_bfloat1
 cudaError_t conv0_back(const float *dact, const float *pre, const __nv_bfloat16 *x, int nb,
                        float *gW, float *gb, int sms, cudaStream_t st);
 
+// C = A B^T on the tcgen05 tensor cores: A [M][K], B [N][K] BF16 with row
+// strides lda, ldb (multiples of 8 elements, 16-byte aligned bases).  Tiles of
+// 128 x bn (bn = 32 or 128; 64 for the GELU form); K split into k_slices
+// slices.  Without pre: C[m * ldc + n] (C[n * ldc + m] when transposed)
+// = sum + bias[n] (bias optional), FP32 atomics when atomic (required for
+// k_slices > 1).  With pre (bn = 64, one slice): pre[m * ldc + n] = sum + bias[n]
+// and Cb[m * ldc + n] = BF16(GELU(that)).  A wait that gives up ORs
+// PCHASE_DEV_TIMEOUT into *status.
+cudaError_t tc_gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N,
+                    int K, int bn, int k_slices, const float *bias, float *C, int ldc, bool atomic,
+                    bool transposed, float *pre, __nv_bfloat16 *Cb, uint32_t *status,
+                    cudaStream_t st);
+
+// out [Cpad][ldo] = transpose of in [R][C] (row stride ldi), zero beyond R
+// columns and C rows.
+cudaError_t transpose_bf16(const __nv_bfloat16 *in, int R, int C, int ldi, __nv_bfloat16 *out,
+                           int ldo, int Cpad, cudaStream_t st);
+
 }  // namespace pchase

@@ -31,29 +31,6 @@ namespace pchase {
 
 namespace {
 
-// ------------------------------------------------------------------ GEMM
-// C[M,N] = sum_k A(m,k) B(k,n).  A is row-major (A[m*lda+k]) or column-major
-// (A[k*lda+m]); B is row-major (B[k*ldb+n]) or column-major (B[n*ldb+k]).
-// Tiles 128x128x32, 256 threads (8 warps of 64x32), BF16 tiles in shared
-// memory with k contiguous, fragments by ldmatrix, FP32 accumulators.
-// Epilogue: + bias[n] (optional), then GELU (optional); writes FP32 and/or
-// BF16 copies; `pre` (optional, FP32) receives the value before GELU.
-constexpr int GBM = 128, GBN = 128, GBK = 32, GPAD = 8;
-
-struct GemmArgs {
-    const __nv_bfloat16 *A;
-    const __nv_bfloat16 *B;
-    int M, N, K, lda, ldb;
-    const float *bias;
-    float *Cf;
-    __nv_bfloat16 *Cb;
-    float *pre;
-    int ldc;
-    int gelu;
-    int splitk;  // > 1: blockIdx.z takes a K slice and atomically adds into Cf
-    int vec_a, vec_b;  // 16-byte loads allowed along the contiguous dimension
-};
-
 __device__ __forceinline__ float gelu_f(float x) {
     // tanh form of GELU (Hendrycks & Gimpel 2016)
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
@@ -91,170 +68,6 @@ __device__ __forceinline__ void mma_bf16(float *c, uint32_t a0, uint32_t a1, uin
         "{%8,%9}, {%0,%1,%2,%3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-template <bool A_COL, bool B_ROW>
-__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g) {
-    __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
-    float acc[4][4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    // K slice of this block (split-K)
-    const int kchunk = ((g.K + g.splitk - 1) / g.splitk + GBK - 1) / GBK * GBK;
-    const int kbeg = blockIdx.z * kchunk;
-    const int kend = min(g.K, kbeg + kchunk);
-    for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-        // ---- tiles into shared memory, k contiguous
-        if (g.vec_a) {
-            // 8 consecutive elements along the contiguous dimension per load
-            for (int e = tid; e < GBM * GBK / 8; e += 256) {
-                int r, c;
-                if (A_COL) { c = e / (GBM / 8); r = (e % (GBM / 8)) * 8; } else { r = e / (GBK / 8); c = (e % (GBK / 8)) * 8; }
-                const int m = m0 + r, k = k0 + c;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (A_COL) {
-                    if (k < kend && m + 7 < g.M) v = *reinterpret_cast<const uint4 *>(g.A + (size_t)k * g.lda + m);
-                    else if (k < kend) {
-                        __nv_bfloat16 t[8];
-                        for (int q = 0; q < 8; ++q) t[q] = m + q < g.M ? g.A[(size_t)k * g.lda + m + q] : zero;
-                        v = *reinterpret_cast<uint4 *>(t);
-                    }
-                    const __nv_bfloat16 *t = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) As[r + q][c] = t[q];
-                } else {
-                    if (m < g.M && k + 7 < kend) v = *reinterpret_cast<const uint4 *>(g.A + (size_t)m * g.lda + k);
-                    else if (m < g.M) {
-                        __nv_bfloat16 t[8];
-                        for (int q = 0; q < 8; ++q) t[q] = k + q < kend ? g.A[(size_t)m * g.lda + k + q] : zero;
-                        v = *reinterpret_cast<uint4 *>(t);
-                    }
-                    *reinterpret_cast<uint4 *>(&As[r][c]) = v;
-                }
-            }
-        } else {
-            for (int e = tid; e < GBM * GBK; e += 256) {
-                int r, c;
-                if (A_COL) { c = e / GBM; r = e % GBM; } else { r = e / GBK; c = e % GBK; }
-                const int m = m0 + r, k = k0 + c;
-                __nv_bfloat16 v = zero;
-                if (m < g.M && k < kend) v = A_COL ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
-                As[r][c] = v;
-            }
-        }
-        if (g.vec_b) {
-            for (int e = tid; e < GBN * GBK / 8; e += 256) {
-                int r, c;
-                if (B_ROW) { c = e / (GBN / 8); r = (e % (GBN / 8)) * 8; } else { r = e / (GBK / 8); c = (e % (GBK / 8)) * 8; }
-                const int n = n0 + r, k = k0 + c;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (B_ROW) {
-                    if (k < kend && n + 7 < g.N) v = *reinterpret_cast<const uint4 *>(g.B + (size_t)k * g.ldb + n);
-                    else if (k < kend) {
-                        __nv_bfloat16 t[8];
-                        for (int q = 0; q < 8; ++q) t[q] = n + q < g.N ? g.B[(size_t)k * g.ldb + n + q] : zero;
-                        v = *reinterpret_cast<uint4 *>(t);
-                    }
-                    const __nv_bfloat16 *t = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) Bs[r + q][c] = t[q];
-                } else {
-                    if (n < g.N && k + 7 < kend) v = *reinterpret_cast<const uint4 *>(g.B + (size_t)n * g.ldb + k);
-                    else if (n < g.N) {
-                        __nv_bfloat16 t[8];
-                        for (int q = 0; q < 8; ++q) t[q] = k + q < kend ? g.B[(size_t)n * g.ldb + k + q] : zero;
-                        v = *reinterpret_cast<uint4 *>(t);
-                    }
-                    *reinterpret_cast<uint4 *>(&Bs[r][c]) = v;
-                }
-            }
-        } else {
-            for (int e = tid; e < GBN * GBK; e += 256) {
-                int r, c;
-                if (B_ROW) { c = e / GBN; r = e % GBN; } else { r = e / GBK; c = e % GBK; }
-                const int n = n0 + r, k = k0 + c;
-                __nv_bfloat16 v = zero;
-                if (n < g.N && k < kend) v = B_ROW ? g.B[(size_t)k * g.ldb + n] : g.B[(size_t)n * g.ldb + k];
-                Bs[r][c] = v;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GBK; kk += 16) {
-            uint32_t af[4][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int row = wm + i * 16 + (lane & 15);
-                const int col = kk + ((lane >> 4) << 3);
-                ldsm_x4((uint32_t)__cvta_generic_to_shared(&As[row][col]), af[i][0], af[i][1],
-                        af[i][2], af[i][3]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j += 2) {
-                // two n8 tiles per x4: matrices (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, ...)
-                const int row = wn + j * 8 + (lane & 7) + ((lane >> 4) << 3);
-                const int col = kk + (((lane >> 3) & 1) << 3);
-                uint32_t r0, r1, r2, r3;
-                ldsm_x4((uint32_t)__cvta_generic_to_shared(&Bs[row][col]), r0, r1, r2, r3);
-                bfr[j][0] = r0;
-                bfr[j][1] = r1;
-                bfr[j + 1][0] = r2;
-                bfr[j + 1][1] = r3;
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_bf16(acc[i][j], af[i][0], af[i][1], af[i][2], af[i][3], bfr[j][0], bfr[j][1]);
-        }
-        __syncthreads();
-    }
-    // ---- epilogue
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int m = m0 + wm + i * 16 + (lane >> 2) + ((q >> 1) << 3);
-                const int n = n0 + wn + j * 8 + ((lane & 3) << 1) + (q & 1);
-                if (m >= g.M || n >= g.N) continue;
-                float v = acc[i][j][q];
-                const size_t o = (size_t)m * g.ldc + n;
-                if (g.splitk > 1) {
-                    atomicAdd(g.Cf + o, v);
-                    continue;
-                }
-                if (g.bias) v += g.bias[n];
-                if (g.pre) g.pre[o] = v;
-                if (g.gelu) v = gelu_f(v);
-                if (g.Cf) g.Cf[o] = v;
-                if (g.Cb) g.Cb[o] = __float2bfloat16(v);
-            }
-}
-
-cudaError_t gemm(bool a_col, bool b_row, const GemmArgs &g0, cudaStream_t st) {
-    if (g0.M <= 0 || g0.N <= 0) return cudaSuccess;
-    GemmArgs g = g0;
-    if (g.splitk < 1) g.splitk = 1;
-    // 16-byte loads need an 8-element-aligned leading dimension and base
-    g.vec_a = (g.lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0);
-    g.vec_b = (g.ldb % 8 == 0) && ((reinterpret_cast<uintptr_t>(g.B) & 15) == 0);
-    dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, g.splitk);
-    if (!a_col && !b_row) gemm_kernel<false, false><<<grid, 256, 0, st>>>(g);
-    else if (!a_col && b_row) gemm_kernel<false, true><<<grid, 256, 0, st>>>(g);
-    else if (a_col && !b_row) gemm_kernel<true, false><<<grid, 256, 0, st>>>(g);
-    else gemm_kernel<true, true><<<grid, 256, 0, st>>>(g);
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------- convolution as implicit GEMM
@@ -381,6 +194,7 @@ constexpr int kKer = 5;
 constexpr int kHidden = 256;
 constexpr int kFlat = 32 * kCh;
 constexpr int kLogits = 31;
+constexpr int kLogitsPad = 32;  // BF16 logit gradients: rows of 64 bytes
 __constant__ int c_head_off[5] = {0, 17, 21, 28, 31};
 
 // dz = dy * gelu'(pre) (FP32 in, BF16 out for the next GEMMs)
@@ -415,9 +229,10 @@ __global__ void xent_kernel(const float *logits, const uint32_t *labels, int nb,
             const float p = expf(z[i] - mx) / se;
             const float d = (p - (i == (int)(o0 + y) ? 1.0f : 0.0f)) * inv;
             dlog[(size_t)b * kLogits + i] = d;
-            dlogb[(size_t)b * kLogits + i] = __float2bfloat16(d);
+            dlogb[(size_t)b * kLogitsPad + i] = __float2bfloat16(d);
         }
     }
+    dlogb[(size_t)b * kLogitsPad + kLogits] = __float2bfloat16(0.0f);
     atomicAdd(loss, l * inv);
 }
 
@@ -602,17 +417,6 @@ __global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restr
             *reinterpret_cast<uint4 *>(out + row * kCh + g * 8) =
                 make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-    }
-}
-
-// acc (split-K sums, M x N FP32) += bias; out = BF16(GELU(acc)).
-__global__ void bias_gelu_kernel(float *acc, const float *bias, int M, int N,
-                                 __nv_bfloat16 *out) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)M * N;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const float v = acc[i] + bias[i % N];
-        acc[i] = v;
-        out[i] = __float2bfloat16(gelu_f(v));
     }
 }
 
@@ -828,14 +632,6 @@ InverseLayout inverse_layout() {
 
 namespace {
 
-// enough K slices to give every SM a few tiles, each slice >= 512 deep
-int splitk_for(int M, int N, int K) {
-    const int tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
-    int s = (4 * 152 + tiles - 1) / tiles;
-    s = std::min(s, std::max(1, K / 512));
-    return std::max(1, s);
-}
-
 int grid_for(size_t n, int threads = 256) {
     size_t b = (n + threads - 1) / threads;
     if (b > 8192) b = 8192;
@@ -854,7 +650,7 @@ struct pchase_inverse {
     InverseLayout L;
     uint32_t max_batch;
     size_t p_w, p_wb, p_g, p_m, p_v, p_bytes;
-    size_t status, xb, pre[4], act[4], pre4, h4, logits, dlog, dlogb, dh, dzf, dzb, dbig,
+    size_t status, xb, pre[4], act[4], pre4, h4, logits, dlog, dlogb, tA, tB, w4t, w5t, dh, dzf, dzb, dbig,
         dsmall, work_bytes, infer_bytes;
 };
 
@@ -931,38 +727,15 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
                              at<float>(work, h->logits), at<uint32_t>(work, h->status), st));
         return PCHASE_OK;
     }
-    // FC 2048 -> 256: split-K into FP32 sums (B x 256 is too few 128 x 128
-    // tiles to fill the GPU over K = 2048), then bias + GELU
-    float *acc4 = at<float>(work, h->pre4);
-    INV_CUDA(cudaMemsetAsync(acc4, 0, (size_t)B * kHidden * sizeof(float), st));
-    GemmArgs f{};
-    f.A = in;
-    f.B = wb + L.w[4];
-    f.M = (int)B;
-    f.N = kHidden;
-    f.K = kFlat;
-    f.lda = kFlat;
-    f.ldb = kFlat;
-    f.Cf = acc4;
-    f.ldc = kHidden;
-    f.splitk = 8;
-    INV_CUDA(gemm(false, false, f, st));
-    bias_gelu_kernel<<<grid_for((size_t)B * kHidden), 256, 0, st>>>(
-        acc4, wf + L.b[4], (int)B, kHidden, at<__nv_bfloat16>(work, h->h4));
-    INV_CUDA(cudaGetLastError());
-    f.Cb = at<__nv_bfloat16>(work, h->h4);
-    GemmArgs o{};
-    o.A = f.Cb;
-    o.B = wb + L.w[5];
-    o.M = (int)B;
-    o.N = kLogits;
-    o.K = kHidden;
-    o.lda = kHidden;
-    o.ldb = kHidden;
-    o.bias = wf + L.b[5];
-    o.Cf = at<float>(work, h->logits);
-    o.ldc = kLogits;
-    INV_CUDA(gemm(false, false, o, st));
+    // FC 2048 -> 256 with bias and GELU (pre-activations kept), then the
+    // heads, on the tcgen05 tensor cores
+    uint32_t *status = at<uint32_t>(work, h->status);
+    __nv_bfloat16 *h4 = at<__nv_bfloat16>(work, h->h4);
+    INV_CUDA(tc_gemm(in, kFlat, wb + L.w[4], kFlat, (int)B, kHidden, kFlat, 64, 1, wf + L.b[4],
+                     nullptr, kHidden, false, false, at<float>(work, h->pre4), h4, status, st));
+    INV_CUDA(tc_gemm(h4, kHidden, wb + L.w[5], kHidden, (int)B, kLogits, kHidden, 32, 1,
+                     wf + L.b[5], at<float>(work, h->logits), kLogits, false, false, nullptr,
+                     nullptr, status, st));
     return PCHASE_OK;
 }
 
@@ -1008,7 +781,16 @@ int pchase_inverse_create(uint32_t max_batch, pchase_inverse **out) {
     h->pre4 = o; o = a256(o + 4 * B * kHidden);
     h->h4 = o; o = a256(o + 2 * B * kHidden);
     h->dlog = o; o = a256(o + 4 * B * kLogits);
-    h->dlogb = o; o = a256(o + 2 * B * kLogits);
+    h->dlogb = o; o = a256(o + 2 * B * kLogitsPad);
+    {
+        // transposed operands of the weight gradients (rows of the batch
+        // padded to a multiple of 8) and of the input gradients
+        const size_t ldk = (B + 7) / 8 * 8;
+        h->tA = o; o = a256(o + 2 * kHidden * ldk);
+        h->tB = o; o = a256(o + 2 * kFlat * ldk);
+        h->w4t = o; o = a256(o + 2 * (size_t)kFlat * kHidden);
+        h->w5t = o; o = a256(o + 2 * (size_t)kHidden * kLogitsPad);
+    }
     h->dh = o; o = a256(o + 4 * B * kHidden);
     h->dzf = o; o = a256(o + 4 * B * kHidden);
     h->dzb = o; o = a256(o + 2 * B * kHidden);
@@ -1100,22 +882,30 @@ int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work,
     __nv_bfloat16 *dlogb = at<__nv_bfloat16>(work, h->dlogb);
     xent_kernel<<<(B + 127) / 128, 128, 0, st>>>(at<float>(work, h->logits), labels, (int)B, dlog,
                                                  dlogb, loss_accum);
-    // heads
+    // heads and FC on the tcgen05 tensor cores.  Products over the batch
+    // (weight gradients) take both operands batch-contiguous: transposed
+    // copies, rows padded with zeros to a multiple of 8 traces, K split over
+    // CTAs with FP32 atomics into the zeroed gradient.
+    uint32_t *status = at<uint32_t>(work, h->status);
+    const int ldk = (int)((B + 7) / 8 * 8);
+    __nv_bfloat16 *h4 = at<__nv_bfloat16>(work, h->h4);
+    __nv_bfloat16 *tA = at<__nv_bfloat16>(work, h->tA), *tB = at<__nv_bfloat16>(work, h->tB);
+    __nv_bfloat16 *w4t = at<__nv_bfloat16>(work, h->w4t), *w5t = at<__nv_bfloat16>(work, h->w5t);
+    INV_CUDA(transpose_bf16(wb + L.w[4], kHidden, kFlat, kFlat, w4t, kHidden, kFlat, st));
+    INV_CUDA(transpose_bf16(wb + L.w[5], kLogits, kHidden, kHidden, w5t, kLogitsPad, kHidden, st));
     {
-        GemmArgs g{};
-        g.A = dlogb; g.B = at<__nv_bfloat16>(work, h->h4);
-        g.M = kLogits; g.N = kHidden; g.K = (int)B; g.lda = kLogits; g.ldb = kHidden;
-        g.Cf = grad + L.w[5]; g.ldc = kHidden; g.splitk = splitk_for(g.M, g.N, g.K);
-        INV_CUDA(gemm(true, true, g, st));
+        // grad W5 [31][256] = dlogb^T h4, as (h4^T) (dlogb^T)^T stored transposed
+        INV_CUDA(transpose_bf16(h4, (int)B, kHidden, kHidden, tA, ldk, kHidden, st));
+        INV_CUDA(transpose_bf16(dlogb, (int)B, kLogitsPad, kLogitsPad, tB, ldk, kLogitsPad, st));
+        INV_CUDA(tc_gemm(tA, ldk, tB, ldk, kHidden, kLogits, ldk, 32, 32, nullptr, grad + L.w[5],
+                         kHidden, true, true, nullptr, nullptr, status, st));
         colsum_atomic_kernel<<<dim3(1, (B + 255) / 256), 32, 0, st>>>(dlog, (int)B, kLogits, 256,
                                                                        grad + L.b[5]);
-        GemmArgs d{};
-        d.A = dlogb; d.B = wb + L.w[5];
-        d.M = (int)B; d.N = kHidden; d.K = kLogits; d.lda = kLogits; d.ldb = kHidden;
-        d.Cf = at<float>(work, h->dh); d.ldc = kHidden;
-        INV_CUDA(gemm(false, true, d, st));
+        // dh [B][256] = dlogb W5
+        INV_CUDA(tc_gemm(dlogb, kLogitsPad, w5t, kLogitsPad, (int)B, kHidden, kLogitsPad, 128, 1,
+                         nullptr, at<float>(work, h->dh), kHidden, false, false, nullptr, nullptr,
+                         status, st));
     }
-    // FC
     float *dzf = at<float>(work, h->dzf);
     __nv_bfloat16 *dzb = at<__nv_bfloat16>(work, h->dzb);
     float *dbig = at<float>(work, h->dbig);
@@ -1124,18 +914,17 @@ int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work,
         const size_t m = (size_t)B * kHidden;
         gelu_back_kernel<<<grid_for(m), 256, 0, st>>>(at<float>(work, h->dh),
                                                       at<float>(work, h->pre4), m, dzf, dzb);
-        GemmArgs g{};
-        g.A = dzb; g.B = at<__nv_bfloat16>(work, h->act[3]);
-        g.M = kHidden; g.N = kFlat; g.K = (int)B; g.lda = kHidden; g.ldb = kFlat;
-        g.Cf = grad + L.w[4]; g.ldc = kFlat; g.splitk = splitk_for(g.M, g.N, g.K);
-        INV_CUDA(gemm(true, true, g, st));
+        // grad W4 [256][2048] = dzb^T act3
+        INV_CUDA(transpose_bf16(dzb, (int)B, kHidden, kHidden, tA, ldk, kHidden, st));
+        INV_CUDA(transpose_bf16(at<__nv_bfloat16>(work, h->act[3]), (int)B, kFlat, kFlat, tB, ldk,
+                                kFlat, st));
+        INV_CUDA(tc_gemm(tA, ldk, tB, ldk, kHidden, kFlat, ldk, 128, 4, nullptr, grad + L.w[4],
+                         kFlat, true, false, nullptr, nullptr, status, st));
         colsum_atomic_kernel<<<dim3((kHidden + 127) / 128, (B + 255) / 256), 128, 0, st>>>(
             dzf, (int)B, kHidden, 256, grad + L.b[4]);
-        GemmArgs d{};
-        d.A = dzb; d.B = wb + L.w[4];
-        d.M = (int)B; d.N = kFlat; d.K = kHidden; d.lda = kHidden; d.ldb = kFlat;
-        d.Cf = dbig; d.ldc = kFlat;  // d(act3) [B, 32, 64]
-        INV_CUDA(gemm(false, true, d, st));
+        // d(act3) [B][32 x 64] = dzb W4
+        INV_CUDA(tc_gemm(dzb, kHidden, w4t, kHidden, (int)B, kFlat, kHidden, 128, 1, nullptr, dbig,
+                         kFlat, false, false, nullptr, nullptr, status, st));
     }
     // convolutions, last to first: the three 64-channel layers on the tensor
     // cores (gelu backward, weight and bias gradients, input gradient into

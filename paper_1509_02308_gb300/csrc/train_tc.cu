@@ -429,6 +429,206 @@ __global__ void __launch_bounds__(256) conv0_back_kernel(const float *__restrict
     if (threadIdx.x < kCh) atomicAdd(gb + threadIdx.x, sb[threadIdx.x]);
 }
 
+// ------------------------------------------------------------------ GEMM
+// C = A B^T over K for the training step's dense layers: A [M][K] and B [N][K]
+// BF16, both K-major (row strides lda, ldb elements, multiples of 8, 16-byte
+// aligned bases), FP32 sums in TMEM.  A CTA takes a 128 x BN tile and a slice
+// of the K blocks (gridDim.z slices of 64-element blocks); blocks stream
+// through a 4-buffer cp.async ring loaded two ahead, an mbarrier per buffer
+// freeing it once its MMAs are done (rows past M or N and columns past K are
+// zero-filled).  Epilogues: kStore (C[m][n], or C[n][m] when transposed,
+// + bias[n] if given; FP32 atomics when K is sliced) and kGelu (v = sum +
+// bias[n]: pre[m][n] = v, Cb[m][n] = BF16(GELU(v)) with the exact tanh).
+constexpr int kGemmStages = 4, kGemmAhead = 2;
+enum GemmEpi { kStore = 0, kGelu = 1 };
+
+struct TcGemm {
+    const __nv_bfloat16 *A, *B;
+    int M, N, K, lda, ldb;
+    int blocks_per_slice;  // K blocks of 64 per blockIdx.z
+    const float *bias;
+    float *C;              // kStore
+    int ldc, atomic, transposed;
+    float *pre;            // kGelu
+    __nv_bfloat16 *Cb;
+    uint32_t *status;
+};
+
+__device__ __forceinline__ float gelu_exact(float x) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
+}
+
+template <int BN>
+struct GemmShape {
+    static constexpr uint32_t kABytes = 128 * 128, kBBytes = BN * 128;
+    static constexpr uint32_t kStageBytes = kABytes + kBBytes;
+    static constexpr uint32_t kSmem = 1024 + kGemmStages * kStageBytes + 8 * kGemmStages + 16;
+    static constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+    static constexpr uint32_t kIdesc = idesc_n(BN);
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128) tc_gemm_kernel(const TcGemm g) {
+    using S = GemmShape<BN>;
+    extern __shared__ uint8_t dsm[];
+    const uint32_t raw = smem_u32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *const gbase = dsm + (base - raw);
+    const uint32_t sBar = base + kGemmStages * S::kStageBytes;
+    uint32_t *const tslot =
+        reinterpret_cast<uint32_t *>(gbase + kGemmStages * S::kStageBytes + 8 * kGemmStages);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+    const int nkb = (g.K + 63) / 64;
+    const int kb0 = blockIdx.z * g.blocks_per_slice;
+    const int nblk = max(0, min(nkb, kb0 + g.blocks_per_slice) - kb0);
+
+    auto load = [&](int j) {
+        if (j < nblk) {
+            const uint32_t st = base + (uint32_t)(j % kGemmStages) * S::kStageBytes;
+            const int k0 = (kb0 + j) * 64;
+            for (int e = tid; e < (128 + BN) * 8; e += 128) {
+                const int r = e >> 3, c = e & 7;
+                const int k = k0 + c * 8;
+                if (r < 128) {
+                    const int m = m0 + r;
+                    const bool ok = m < g.M && k < g.K;
+                    cp_async16(st + sw_chunk((uint32_t)r, (uint32_t)c),
+                               ok ? g.A + (size_t)m * g.lda + k : g.A, ok);
+                } else {
+                    const int rn = r - 128, n = n0 + rn;
+                    const bool ok = n < g.N && k < g.K;
+                    cp_async16(st + S::kABytes + sw_chunk((uint32_t)rn, (uint32_t)c),
+                               ok ? g.B + (size_t)n * g.ldb + k : g.B, ok);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    if (tid == 0) {
+        for (int q = 0; q < kGemmStages; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8 * q) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(S::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int j = 0; j < kGemmAhead; ++j) load(j);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    bool ok = true;
+    for (int j = 0; j < nblk; ++j) {
+        // block j + ahead refills the buffer of block j + ahead - stages
+        const int pb = j + kGemmAhead - kGemmStages;
+        if (pb >= 0) {
+            const bool got = mbar_wait(sBar + 8 * (pb % kGemmStages), (uint32_t)(pb / kGemmStages) & 1u);
+            if (!__syncthreads_and(got)) {
+                ok = false;
+                break;
+            }
+        }
+        load(j + kGemmAhead);
+        asm volatile("cp.async.wait_group %0;" ::"n"(kGemmAhead) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t st = base + (uint32_t)(j % kGemmStages) * S::kStageBytes;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16_id(tmem, sw128_desc(st + 32u * s), sw128_desc(st + S::kABytes + 32u * s),
+                            S::kIdesc, (j | s) != 0 ? 1u : 0u);
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    sBar + 8u * (uint32_t)(j % kGemmStages))
+                : "memory");
+        }
+    }
+    if (ok && nblk > 0) {
+        const int lb = nblk - 1;  // the last commit covers every earlier MMA
+        const bool got = mbar_wait(sBar + 8 * (lb % kGemmStages), (uint32_t)(lb / kGemmStages) & 1u);
+        ok = __syncthreads_and(got);
+        if (ok) {
+            tc_fence_after();
+            const int m = m0 + warp * 32 + lane;  // TMEM lane = tile row
+#pragma unroll 1
+            for (int q = 0; q < BN / 16; ++q) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * q), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (m >= g.M) continue;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int n = n0 + 16 * q + e;
+                    if (n >= g.N) break;
+                    float val = __uint_as_float(v[e]);
+                    if (g.bias) val += __ldg(g.bias + n);
+                    if (EPI == kGelu) {
+                        g.pre[(size_t)m * g.ldc + n] = val;
+                        g.Cb[(size_t)m * g.ldc + n] = __float2bfloat16(gelu_exact(val));
+                    } else {
+                        float *dst = g.C + (g.transposed ? (size_t)n * g.ldc + m : (size_t)m * g.ldc + n);
+                        if (g.atomic) atomicAdd(dst, val);
+                        else *dst = val;
+                    }
+                }
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicOr(g.status, PCHASE_DEV_TIMEOUT);
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(S::kTmemCols)
+                     : "memory");
+}
+
+// out[c][r] = in[r][c] for r < R, c < C (out row stride ldo); columns R ..
+// ldo - 1 of each out row and rows C .. Cpad - 1 are zero.  32 x 32 tiles
+// through shared memory.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, int R, int C, int ldi,
+                                      __nv_bfloat16 *__restrict__ out, int ldo, int Cpad) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int i = ty; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + tx;
+        t[i][tx] = (r < R && c < C) ? in[(size_t)r * ldi + c] : __float2bfloat16(0.0f);
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + tx;
+        if (c < Cpad && r < ldo) out[(size_t)c * ldo + r] = t[tx][i];
+    }
+}
+
+template <int BN, int EPI>
+cudaError_t launch_tc_gemm(const TcGemm &g, int slices, cudaStream_t st) {
+    using S = GemmShape<BN>;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            tc_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, slices);
+    tc_gemm_kernel<BN, EPI><<<grid, 128, S::kSmem, st>>>(g);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t conv_back_tc(const float *dact, const float *pre, const __nv_bfloat16 *x, int nb,
@@ -456,6 +656,38 @@ cudaError_t conv0_back(const float *dact, const float *pre, const __nv_bfloat16 
     const size_t rows = (size_t)nb * 256;
     const int grid = (int)std::max<size_t>(1, std::min<size_t>((rows + 31) / 32, (size_t)sms * 4));
     conv0_back_kernel<<<grid, 256, 0, st>>>(dact, pre, x, nb, gW, gb);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N,
+                    int K, int bn, int k_slices, const float *bias, float *C, int ldc, bool atomic,
+                    bool transposed, float *pre, __nv_bfloat16 *Cb, uint32_t *status,
+                    cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
+        (reinterpret_cast<uintptr_t>(B) & 15))
+        return cudaErrorInvalidValue;
+    TcGemm g{A, B, M, N, K, lda, ldb, 0, bias, C, ldc, atomic ? 1 : 0, transposed ? 1 : 0,
+             pre, Cb, status};
+    const int nkb = (K + 63) / 64;
+    const int slices = std::max(1, std::min(k_slices, nkb));
+    g.blocks_per_slice = (nkb + slices - 1) / slices;
+    if (slices > 1 && !atomic && !pre) return cudaErrorInvalidValue;
+    if (pre) {
+        if (slices > 1 || !Cb) return cudaErrorInvalidValue;
+        if (bn == 64) return launch_tc_gemm<64, kGelu>(g, 1, st);
+        return cudaErrorInvalidValue;
+    }
+    if (bn == 32) return launch_tc_gemm<32, kStore>(g, slices, st);
+    if (bn == 128) return launch_tc_gemm<128, kStore>(g, slices, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t transpose_bf16(const __nv_bfloat16 *in, int R, int C, int ldi, __nv_bfloat16 *out,
+                           int ldo, int Cpad, cudaStream_t st) {
+    if (R <= 0 || Cpad <= 0) return cudaSuccess;
+    dim3 grid((std::max(R, ldo) + 31) / 32, (Cpad + 31) / 32);
+    transpose_bf16_kernel<<<grid, 256, 0, st>>>(in, R, C, ldi, out, ldo, Cpad);
     return cudaGetLastError();
 }
 
