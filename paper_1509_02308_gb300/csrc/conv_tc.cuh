@@ -37,6 +37,15 @@ cudaError_t fc_heads_tc(const __nv_bfloat16 *act, int nb, const __nv_bfloat16 *W
                         const float *bias4, const __nv_bfloat16 *W5, const float *bias5,
                         float *logits, uint32_t *status, cudaStream_t st);
 
+// Training step, forward of one 64-channel convolution layer (lout = 128, 64
+// or 32; lin = 2 lout): pre [nb * lout][64] FP32 = the pre-activations for x
+// [nb][lin][64] BF16, W [64][5*64] BF16 + bias; out [nb * lout][64] BF16 =
+// GELU(pre) with the exact tanh.  tcgen05 tensor cores; a wait that gives up
+// ORs PCHASE_DEV_TIMEOUT into *status (device).
+cudaError_t conv_fwd_tc(const __nv_bfloat16 *x, int nb, int lout, const __nv_bfloat16 *W,
+                        const float *bias, float *pre, __nv_bfloat16 *out, uint32_t *status, int sms,
+                        cudaStream_t st);
+
 // Training step, backward of one 64-channel convolution layer (lout = 128,
 // 64 or 32 output positions per trace; lin = 2 lout): given dact [nb * lout][64]
 // FP32 (gradient of the layer's GELU outputs), pre [nb * lout][64] FP32 (its

@@ -10,10 +10,11 @@
 // Adam moments and gradients stay FP32.  Inference runs on the tcgen05 tensor
 // cores (conv_tc.cu): layers 1 and 2 in one kernel (layer 1 computed on chip
 // from the FP32 inputs), layers 3 and 4 in one kernel (layer 3 on chip), then
-// FC + heads in one kernel; the
-// training step's GEMMs (forward with kept pre-activations, backward, weight
-// gradients) run here on warp-level mma.sync m16n8k16 tiles, the first
-// convolution (one input channel) on CUDA cores.
+// FC + heads in one kernel.  The training step (train_tc.cu) runs the
+// 64-channel convolutions forward (pre-activations kept) and backward, and
+// the FC and heads layers as GEMMs, on the tcgen05 tensor cores too; the
+// first convolution (one input channel, five taps) runs on CUDA cores both
+// ways.
 //
 // The synthetic traces follow Sec. 4.1's mean-latency model t = t0 + t_m r
 // with r the miss rate the simulator reports for each plan point.
@@ -37,16 +38,6 @@ __device__ __forceinline__ float gelu_f(float x) {
     return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
 }
 
-// GELU with the hardware tanh (tanh.approx.f32, relative error about 2^-11,
-// below the BF16 rounding of every activation): inference only, so training's
-// forward and backward keep the same tanhf.
-__device__ __forceinline__ float gelu_fast(float x) {
-    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-    float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(k0 * (x + k1 * x * x * x)));
-    return 0.5f * x * (1.0f + t);
-}
-
 __device__ __forceinline__ float gelu_grad(float x) {
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
     const float u = k0 * (x + k1 * x * x * x);
@@ -54,138 +45,6 @@ __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * x * x);
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
-                                        uint32_t &r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float *c, uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// ---------------------------------------------- convolution as implicit GEMM
-// out[(b, lo), co] = bias[co] + sum_{kk, ci} W[co][kk*64 + ci] * x[b][2 lo + kk - 2][ci]
-// for 64 input and 64 output channels, x channel-last BF16.  The A tile
-// (128 output positions x 32 reduction entries, i.e. half the channels of
-// one tap) is gathered straight from x with 16-byte cp.async copies (zero
-// fill outside the sequence); W tiles likewise; two stages in flight.
-constexpr int CBM = 128, CBN = 64, CBK = 32, CPAD = 8;
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
-    const int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-__global__ void __launch_bounds__(256) conv64_kernel(const __nv_bfloat16 *__restrict__ x, int nb,
-                                                     int lin, const __nv_bfloat16 *__restrict__ W,
-                                                     const float *__restrict__ bias,
-                                                     __nv_bfloat16 *__restrict__ out,
-                                                     float *__restrict__ pre) {
-    constexpr int CIN = 64, KTOT = 5 * CIN, NKT = KTOT / CBK;
-    __shared__ __align__(16) __nv_bfloat16 As[2][CBM][CBK + CPAD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[2][CBN][CBK + CPAD];
-    const int lout = lin / 2;
-    const int M = nb * lout;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * CBM;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-    auto load = [&](int stage, int kt) {
-        const int kk = kt >> 1, ci0 = (kt & 1) * 32;
-        for (int e = tid; e < CBM * 4; e += 256) {
-            const int r = e >> 2, c = (e & 3) * 8;
-            const int m = m0 + r;
-            const int b = m / lout, lo = m - b * lout;
-            const int li = 2 * lo + kk - 2;
-            const bool ok = m < M && li >= 0 && li < lin;
-            const __nv_bfloat16 *src = ok ? x + ((size_t)b * lin + li) * CIN + ci0 + c : x;
-            cp_async16((uint32_t)__cvta_generic_to_shared(&As[stage][r][c]), src, ok);
-        }
-        {
-            const int r = tid >> 2, c = (tid & 3) * 8;
-            cp_async16((uint32_t)__cvta_generic_to_shared(&Bs[stage][r][c]),
-                       W + (size_t)r * KTOT + kt * CBK + c, true);
-        }
-        cp_async_commit();
-    };
-    load(0, 0);
-    for (int kt = 0; kt < NKT; ++kt) {
-        const int st = kt & 1;
-        if (kt + 1 < NKT) {
-            load(st ^ 1, kt + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < CBK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int row = wm + i * 16 + (lane & 15);
-                const int col = kk + ((lane >> 4) << 3);
-                ldsm_x4((uint32_t)__cvta_generic_to_shared(&As[st][row][col]), af[i][0], af[i][1],
-                        af[i][2], af[i][3]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j += 2) {
-                const int row = wn + j * 8 + (lane & 7) + ((lane >> 4) << 3);
-                const int col = kk + (((lane >> 3) & 1) << 3);
-                uint32_t r0, r1, r2, r3;
-                ldsm_x4((uint32_t)__cvta_generic_to_shared(&Bs[st][row][col]), r0, r1, r2, r3);
-                bfr[j][0] = r0;
-                bfr[j][1] = r1;
-                bfr[j + 1][0] = r2;
-                bfr[j + 1][1] = r3;
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_bf16(acc[i][j], af[i][0], af[i][1], af[i][2], af[i][3], bfr[j][0], bfr[j][1]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = m0 + wm + i * 16 + (lane >> 2) + h * 8;
-                const int n = wn + j * 8 + ((lane & 3) << 1);
-                if (m >= M) continue;
-                const float v0 = acc[i][j][2 * h] + bias[n];
-                const float v1 = acc[i][j][2 * h + 1] + bias[n + 1];
-                const size_t o = (size_t)m * CBN + n;
-                if (pre) {
-                    pre[o] = v0;
-                    pre[o + 1] = v1;
-                }
-                __nv_bfloat162 pk;
-                pk.x = __float2bfloat16(gelu_f(v0));
-                pk.y = __float2bfloat16(gelu_f(v1));
-                *reinterpret_cast<__nv_bfloat162 *>(out + o) = pk;
-            }
-}
 
 // --------------------------------------------------------- network plumbing
 constexpr int kPoints = 512;
@@ -361,12 +220,13 @@ __global__ void colsum_atomic_kernel(const float *x, int rows, int cols, int row
     atomicAdd(out + c, s);
 }
 
-// First convolution (1 input channel): out[b][p][co] = GELU(bias[co] +
-// sum_k W[co][k] * x[b][2p + k - 2]) with BF16 operands and FP32 sums, the
-// same products as the GEMM form.  One block per trace: the 512 inputs are
-// staged in shared memory (zero padding around them); thread t computes
-// channels 8 (t % 8) .. +7 at positions 8 (t / 8) .. +7, one 16-byte store per
-// position.  HBM-bound on the 32 KB output per trace.
+// First convolution (1 input channel) of the training forward pass:
+// pre[b][p][co] = bias[co] + sum_k W[co][k] * x[b][2p + k - 2] (BF16 operands,
+// FP32 sums) and out = BF16(GELU(pre)).  One block per trace: the 512 inputs
+// are staged in shared memory (zero padding around them); thread t computes
+// channels 8 (t % 8) .. +7 at positions 8 (t / 8) .. +7: per position one
+// 16-byte store of out and two of pre.  HBM-bound on the 96 KB written per
+// trace.
 __global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restrict__ x, int nb,
                                                     const __nv_bfloat16 *__restrict__ W,
                                                     const float *__restrict__ bias,
@@ -397,21 +257,21 @@ __global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restr
 #pragma unroll
             for (int k = 0; k < kKer; ++k) xin[k] = xs[2 * p + k];  // x[2p + k - 2]
             const size_t row = (size_t)b * lout + p;
+            float v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < kKer; ++k) acc = fmaf(w[c][k], xin[k], acc);
+                v[c] = acc + bs[c];
+            }
+            float4 *po = reinterpret_cast<float4 *>(pre + row * kCh + g * 8);
+            po[0] = make_float4(v[0], v[1], v[2], v[3]);
+            po[1] = make_float4(v[4], v[5], v[6], v[7]);
             uint32_t pk[4];
 #pragma unroll
             for (int c = 0; c < 8; c += 2) {
-                float v[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < kKer; ++k) acc = fmaf(w[c + h][k], xin[k], acc);
-                    v[h] = acc + bs[c + h];
-                    if (pre) pre[row * kCh + g * 8 + c + h] = v[h];
-                }
-                const __nv_bfloat162 hv =
-                    pre ? __floats2bfloat162_rn(gelu_f(v[0]), gelu_f(v[1]))
-                        : __floats2bfloat162_rn(gelu_fast(v[0]), gelu_fast(v[1]));
+                const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_f(v[c]), gelu_f(v[c + 1]));
                 pk[c >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
             }
             *reinterpret_cast<uint4 *>(out + row * kCh + g * 8) =
@@ -705,19 +565,18 @@ int forward(const pchase_inverse *h, const void *params, void *work, uint32_t B,
     for (int l = l0; l < 4; ++l) {
         const int lin = L.lin[l], cin = L.cin[l], lout = lin / 2;
         if (cin == kCh) {
-            // implicit im2col
+            // tcgen05 tensor cores, pre-activations kept
             __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
-            const int M = (int)(B * lout);
-            conv64_kernel<<<(M + CBM - 1) / CBM, 256, 0, st>>>(
-                in, (int)B, lin, wb + L.w[l], wf + L.b[l], o, train ? at<float>(work, h->pre[l]) : nullptr);
-            INV_CUDA(cudaGetLastError());
+            INV_CUDA(conv_fwd_tc(in, (int)B, lout, wb + L.w[l], wf + L.b[l],
+                                 at<float>(work, h->pre[l]), o, at<uint32_t>(work, h->status),
+                                 device_sms(), st));
             in = o;
             continue;
         }
         // first layer (one input channel): direct
         __nv_bfloat16 *o = at<__nv_bfloat16>(work, h->act[l]);
         conv1_kernel<<<std::min<uint32_t>(B, 152u * 8u), 256, 0, st>>>(
-            in, (int)B, wb + L.w[l], wf + L.b[l], o, train ? at<float>(work, h->pre[l]) : nullptr);
+            in, (int)B, wb + L.w[l], wf + L.b[l], o, at<float>(work, h->pre[l]));
         INV_CUDA(cudaGetLastError());
         in = o;
     }

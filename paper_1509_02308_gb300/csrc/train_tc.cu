@@ -87,6 +87,13 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
     return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * x * x);
 }
 
+// the tanh form of GELU (Hendrycks & Gimpel 2016), as the training forward
+// pass computes it
+__device__ __forceinline__ float gelu_exact(float x) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
@@ -178,28 +185,51 @@ __global__ void __launch_bounds__(kBackThreads, 1)
     for (int e = 0; e < 8; ++e) bacc[e] = 0.0f;
     int it = 0;
     bool timed_out = false;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const int row0 = t * kRowsPerTile;
-        // ---- the input window of the tile's traces: row tb * lin + p holds
-        // position p of trace b0 + tb, chunk c at c ^ ((row / 2) mod 8)
-        const int b0 = t * tpt;
-        for (int e = tid; e < 256 * 8; e += kBackThreads) {
-            const int r = e >> 3, cc = e & 7;
-            const bool ok = b0 + r / lin < nb;
-            cp_async16(sXS + (uint32_t)r * 128u + (uint32_t)((cc ^ ((r >> 1) & 7)) << 4),
-                       x + ((size_t)b0 * lin + (ok ? r : 0)) * kCh + cc * 8, ok);
+    // ---- the input window of tile t's traces: row tb * lin + p holds
+    // position p of trace b0 + tb, chunk c at c ^ ((row / 2) mod 8)
+    auto fetch_window = [&](int t) {
+        if (t < ntiles) {
+            const int b0 = t * tpt;
+            for (int e = tid; e < 256 * 8; e += kBackThreads) {
+                const int r = e >> 3, cc = e & 7;
+                const bool ok = b0 + r / lin < nb;
+                cp_async16(sXS + (uint32_t)r * 128u + (uint32_t)((cc ^ ((r >> 1) & 7)) << 4),
+                           x + ((size_t)b0 * lin + (ok ? r : 0)) * kCh + cc * 8, ok);
+            }
         }
         cp_async_commit();
-        // ---- dz (rows r0 + 32 i, channels 8c .. 8c + 7) into S_0, S_1, S_2
+    };
+    // ---- this thread's dact and pre of tile t (rows r0 + 32 i, channels
+    // 8c .. 8c + 7), loaded a tile ahead
+    float4 fa[4][2], fp[4][2];
+    auto fetch_rows = [&](int t) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int grow = t * kRowsPerTile + (tid >> 3) + 32 * i;
+            if (t < ntiles && grow < nrows) {
+                const float4 *da = reinterpret_cast<const float4 *>(dact + (size_t)grow * kCh + c * 8);
+                const float4 *pa = reinterpret_cast<const float4 *>(pre + (size_t)grow * kCh + c * 8);
+                fa[i][0] = __ldg(da);
+                fa[i][1] = __ldg(da + 1);
+                fp[i][0] = __ldg(pa);
+                fp[i][1] = __ldg(pa + 1);
+            } else {
+                fa[i][0] = fa[i][1] = fp[i][0] = fp[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+    fetch_window(blockIdx.x);
+    fetch_rows(blockIdx.x);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int row0 = t * kRowsPerTile;
+        // ---- dz into S_0, S_1, S_2 (rows past the end hold zeros)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = (tid >> 3) + 32 * i;
             const int grow = row0 + r;
             float d[8];
             if (grow < nrows) {
-                const float4 *da = reinterpret_cast<const float4 *>(dact + (size_t)grow * kCh + c * 8);
-                const float4 *pa = reinterpret_cast<const float4 *>(pre + (size_t)grow * kCh + c * 8);
-                const float4 a0 = __ldg(da), a1 = __ldg(da + 1), p0 = __ldg(pa), p1 = __ldg(pa + 1);
+                const float4 a0 = fa[i][0], a1 = fa[i][1], p0 = fp[i][0], p1 = fp[i][1];
                 d[0] = a0.x * gelu_grad_f(p0.x);
                 d[1] = a0.y * gelu_grad_f(p0.y);
                 d[2] = a0.z * gelu_grad_f(p0.z);
@@ -299,6 +329,10 @@ __global__ void __launch_bounds__(kBackThreads, 1)
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sBar)
                 : "memory");
         }
+        // the next tile's loads fly during the MMAs and the epilogue (the
+        // window's buffer was last read by the transposes above)
+        fetch_window(t + gridDim.x);
+        fetch_rows(t + gridDim.x);
         const bool ok = mbar_wait(sBar, (uint32_t)it & 1u);
         tc_fence_after();
         if (__syncthreads_or(!ok)) {
@@ -362,6 +396,7 @@ __global__ void __launch_bounds__(kBackThreads, 1)
         mbar_wait(sBar, (uint32_t)(it - 1) & 1u);
         atomicOr(status, PCHASE_DEV_TIMEOUT);
     }
+    cp_async_wait_all();  // a window fetched ahead of a timeout
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -373,19 +408,23 @@ __global__ void __launch_bounds__(kBackThreads, 1)
 }
 
 // First layer (one input channel): dact, pre [nb * 256][64] FP32, x [nb][512]
-// BF16.  Thread (row, 8-channel chunk) over a grid-stride loop of rows; the
-// partial sums meet in shared memory, then one atomic per value and CTA.
+// BF16.  A CTA takes whole traces (a grid-stride loop): the trace's inputs
+// are staged in shared memory and thread t takes channels 8 (t % 8) .. +7 at
+// positions 8 (t / 8) .. +7, two positions' dact and pre (eight 16-byte
+// loads) in flight at a time.  Partial sums stay in registers over all of the
+// CTA's traces, then meet across the warp (shuffles), in shared memory, and
+// in one atomic per value and CTA.
 __global__ void __launch_bounds__(256) conv0_back_kernel(const float *__restrict__ dact,
                                                          const float *__restrict__ pre,
                                                          const __nv_bfloat16 *__restrict__ x,
                                                          int nb, float *__restrict__ gW,
                                                          float *__restrict__ gb) {
     constexpr int kLout = 256, kLin = 512;
+    __shared__ float xs[kLin + 8];  // xs[q + 2] = x[q], zeros outside
     __shared__ float sw[kCh * kTaps], sb[kCh];
-    for (int e = threadIdx.x; e < kCh * kTaps; e += blockDim.x) sw[e] = 0.0f;
-    if (threadIdx.x < kCh) sb[threadIdx.x] = 0.0f;
-    __syncthreads();
-    const int c = threadIdx.x & 7;
+    const int t = threadIdx.x, c = t & 7, p0 = (t >> 3) * 8;
+    for (int e = t; e < kCh * kTaps; e += blockDim.x) sw[e] = 0.0f;
+    if (t < kCh) sb[t] = 0.0f;
     float aw[8][kTaps], ab[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -393,40 +432,214 @@ __global__ void __launch_bounds__(256) conv0_back_kernel(const float *__restrict
 #pragma unroll
         for (int k = 0; k < kTaps; ++k) aw[e][k] = 0.0f;
     }
-    const size_t nrows = (size_t)nb * kLout;
-    for (size_t row = (size_t)blockIdx.x * 32 + (threadIdx.x >> 3); row < nrows;
-         row += (size_t)gridDim.x * 32) {
-        const size_t b = row / kLout;
-        const int lo = (int)(row % kLout);
-        float xv[kTaps];
-#pragma unroll
-        for (int k = 0; k < kTaps; ++k) {
-            const int p = 2 * lo + k - 2;
-            xv[k] = (p >= 0 && p < kLin) ? __bfloat162float(x[b * kLin + p]) : 0.0f;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        __syncthreads();  // the previous trace's reads are done
+        for (int q = t; q < kLin + 8; q += blockDim.x) {
+            const int src = q - 2;
+            xs[q] = (src >= 0 && src < kLin) ? __bfloat162float(x[(size_t)b * kLin + src]) : 0.0f;
         }
-        const float4 *da = reinterpret_cast<const float4 *>(dact + row * kCh + c * 8);
-        const float4 *pa = reinterpret_cast<const float4 *>(pre + row * kCh + c * 8);
-        const float4 a0 = __ldg(da), a1 = __ldg(da + 1), p0 = __ldg(pa), p1 = __ldg(pa + 1);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+        __syncthreads();
+#pragma unroll 1
+        for (int i = 0; i < 8; i += 2) {
+            float4 a[2][2], pr[2][2];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const float d = av[e] * gelu_grad_f(pv[e]);
-            ab[e] += d;
-            const float db = __bfloat162float(__float2bfloat16(d));
+            for (int h = 0; h < 2; ++h) {
+                const size_t row = (size_t)b * kLout + p0 + i + h;
+                const float4 *da = reinterpret_cast<const float4 *>(dact + row * kCh + c * 8);
+                const float4 *pa = reinterpret_cast<const float4 *>(pre + row * kCh + c * 8);
+                a[h][0] = __ldg(da);
+                a[h][1] = __ldg(da + 1);
+                pr[h][0] = __ldg(pa);
+                pr[h][1] = __ldg(pa + 1);
+            }
 #pragma unroll
-            for (int k = 0; k < kTaps; ++k) aw[e][k] = fmaf(db, xv[k], aw[e][k]);
+            for (int h = 0; h < 2; ++h) {
+                const int p = p0 + i + h;
+                float xv[kTaps];
+#pragma unroll
+                for (int k = 0; k < kTaps; ++k) xv[k] = xs[2 * p + k];  // x[2p + k - 2]
+                const float av[8] = {a[h][0].x, a[h][0].y, a[h][0].z, a[h][0].w,
+                                     a[h][1].x, a[h][1].y, a[h][1].z, a[h][1].w};
+                const float pv[8] = {pr[h][0].x, pr[h][0].y, pr[h][0].z, pr[h][0].w,
+                                     pr[h][1].x, pr[h][1].y, pr[h][1].z, pr[h][1].w};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float d = av[e] * gelu_grad_f(pv[e]);
+                    ab[e] += d;
+                    const float db = __bfloat162float(__float2bfloat16(d));
+#pragma unroll
+                    for (int k = 0; k < kTaps; ++k) aw[e][k] = fmaf(db, xv[k], aw[e][k]);
+                }
+            }
         }
     }
+    // lanes l, l ^ 8, l ^ 16, l ^ 24 hold the same channels
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        atomicAdd(&sb[c * 8 + e], ab[e]);
+        ab[e] += __shfl_xor_sync(0xffffffffu, ab[e], 8);
+        ab[e] += __shfl_xor_sync(0xffffffffu, ab[e], 16);
 #pragma unroll
-        for (int k = 0; k < kTaps; ++k) atomicAdd(&sw[(c * 8 + e) * kTaps + k], aw[e][k]);
+        for (int k = 0; k < kTaps; ++k) {
+            aw[e][k] += __shfl_xor_sync(0xffffffffu, aw[e][k], 8);
+            aw[e][k] += __shfl_xor_sync(0xffffffffu, aw[e][k], 16);
+        }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kCh * kTaps; e += blockDim.x) atomicAdd(gW + e, sw[e]);
-    if (threadIdx.x < kCh) atomicAdd(gb + threadIdx.x, sb[threadIdx.x]);
+    if ((t & 31) < 8) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            atomicAdd(&sb[c * 8 + e], ab[e]);
+#pragma unroll
+            for (int k = 0; k < kTaps; ++k) atomicAdd(&sw[(c * 8 + e) * kTaps + k], aw[e][k]);
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < kCh * kTaps; e += blockDim.x) atomicAdd(gW + e, sw[e]);
+    if (t < kCh) atomicAdd(gb + t, sb[t]);
+}
+
+// ------------------------------------------------------- forward (training)
+// One 64-channel layer with the pre-activations kept for the backward pass:
+// pre[row][co] = bias[co] + sum_kk sum_ci W[co][kk*64 + ci] x[b][2 lo + kk - 2][ci]
+// (FP32) and out[row][co] = BF16(GELU(pre)) with the exact tanh, row = (b, lo).
+// A tile is 128 rows (whole traces); its five tap operands A_kk[row][ci] =
+// x[b][2 lo + kk - 2][ci] (zero outside the trace) are gathered from global
+// memory by cp.async straight into K-major 128-byte-swizzled tiles, two tiles'
+// worth in flight (the next tile loads while this one's MMAs and epilogue
+// run); the weights W_kk[co][ci] are five B tiles loaded once.  20 MMAs
+// (M128 N64 K16) per tile into one of two TMEM accumulators.
+constexpr int kFwdThreads = 256;
+constexpr uint32_t kFwdW = 5 * 8192;             // B tiles: 64 rows x 128 B per tap
+constexpr uint32_t kFwdA = 5 * 16384;            // A tiles of one tile: 128 rows x 128 B per tap
+constexpr uint32_t kFwdSmem = 1024 + kFwdW + 2 * kFwdA + 32;
+static_assert(kFwdSmem <= 232448, "shared memory");
+
+__global__ void __launch_bounds__(kFwdThreads, 1)
+    conv_fwd_tc_kernel(const __nv_bfloat16 *__restrict__ x, int nb, int lout,
+                       const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
+                       float *__restrict__ pre, __nv_bfloat16 *__restrict__ out,
+                       uint32_t *status) {
+    extern __shared__ uint8_t dsm[];
+    const uint32_t raw = smem_u32(dsm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *const gbase = dsm + (base - raw);
+    const uint32_t sW = base, sA = base + kFwdW;
+    const uint32_t sBar = base + kFwdW + 2 * kFwdA;  // 2 mbarriers (one per accumulator)
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + kFwdW + 2 * kFwdA + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lin = 2 * lout, nrows = nb * lout;
+    const int ntiles = (nrows + kRowsPerTile - 1) / kRowsPerTile;
+    const int tpt = kRowsPerTile / lout;
+
+    for (int e = tid; e < kTaps * kCh * 8; e += kFwdThreads) {
+        const int kk = e >> 9, co = (e >> 3) & 63, c = e & 7;
+        cp_async16(sW + (uint32_t)kk * 8192u + sw_chunk((uint32_t)co, (uint32_t)c),
+                   W + (size_t)co * (kTaps * kCh) + kk * kCh + c * 8, true);
+    }
+    // the tap operands of tile t into buffer s
+    auto load = [&](int t, int s) {
+        if (t < ntiles) {
+            const int b0 = t * tpt;
+            for (int e = tid; e < kTaps * kRowsPerTile * 8; e += kFwdThreads) {
+                const int kk = e >> 10, r = (e >> 3) & 127, c = e & 7;
+                const int tb = r / lout, lo = r % lout, p = 2 * lo + kk - 2;
+                const bool ok = b0 + tb < nb && p >= 0 && p < lin;
+                cp_async16(sA + (uint32_t)s * kFwdA + (uint32_t)kk * 16384u +
+                               sw_chunk((uint32_t)r, (uint32_t)c),
+                           ok ? x + ((size_t)(b0 + tb) * lin + p) * kCh + c * 8 : x, ok);
+            }
+        }
+        cp_async_commit();
+    };
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8 * q) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(128u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    load(blockIdx.x, 0);  // the weights ride in the first group
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    bool ok = true;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+        const int s = j & 1;
+        // buffer s ^ 1 was last read by tile j - 1's MMAs, waited for below
+        load(t + gridDim.x, s ^ 1);
+        cp_async_wait1();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t a0 = sA + (uint32_t)s * kFwdA;
+#pragma unroll
+            for (int kk = 0; kk < kTaps; ++kk)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    mma_bf16_id(tmem + 64u * (uint32_t)s, sw128_desc(a0 + (uint32_t)kk * 16384u + 32u * q),
+                                sw128_desc(sW + (uint32_t)kk * 8192u + 32u * q), kIdescGw,
+                                (kk | q) != 0 ? 1u : 0u);
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    sBar + 8u * (uint32_t)s)
+                : "memory");
+        }
+        const bool got = mbar_wait(sBar + 8u * (uint32_t)s, (uint32_t)(j >> 1) & 1u);
+        tc_fence_after();
+        if (!__syncthreads_and(got)) {
+            ok = false;
+            if (tid == 0) mbar_wait(sBar + 8u * (uint32_t)s, (uint32_t)(j >> 1) & 1u);
+            break;
+        }
+        // epilogue: warp w takes TMEM lanes 32 (w % 4) .. (rows), channels 32 (w / 4) ..
+        const int lg = warp & 3, half = warp >> 2;
+        uint32_t v[2][16];
+        tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 64u * (uint32_t)s + 32u * half, v[0]);
+        tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 64u * (uint32_t)s + 32u * half + 16u, v[1]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int grow = t * kRowsPerTile + 32 * lg + lane;
+        if (grow < nrows) {
+            float4 *po = reinterpret_cast<float4 *>(pre + (size_t)grow * kCh + 32 * half);
+            uint4 *ao = reinterpret_cast<uint4 *>(out + (size_t)grow * kCh + 32 * half);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                float y[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    y[e] = __uint_as_float(v[k][e]) + __ldg(bias + 32 * half + 16 * k + e);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    po[4 * k + e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
+                ao[2 * k] = make_uint4(pack_bf16(gelu_exact(y[0]), gelu_exact(y[1])),
+                                       pack_bf16(gelu_exact(y[2]), gelu_exact(y[3])),
+                                       pack_bf16(gelu_exact(y[4]), gelu_exact(y[5])),
+                                       pack_bf16(gelu_exact(y[6]), gelu_exact(y[7])));
+                ao[2 * k + 1] = make_uint4(pack_bf16(gelu_exact(y[8]), gelu_exact(y[9])),
+                                           pack_bf16(gelu_exact(y[10]), gelu_exact(y[11])),
+                                           pack_bf16(gelu_exact(y[12]), gelu_exact(y[13])),
+                                           pack_bf16(gelu_exact(y[14]), gelu_exact(y[15])));
+            }
+        }
+        tc_fence_before();
+    }
+    if (!ok && tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u)
+                     : "memory");
 }
 
 // ------------------------------------------------------------------ GEMM
@@ -454,17 +667,13 @@ struct TcGemm {
     uint32_t *status;
 };
 
-__device__ __forceinline__ float gelu_exact(float x) {
-    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-    return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
-}
-
 template <int BN>
 struct GemmShape {
     static constexpr uint32_t kABytes = 128 * 128, kBBytes = BN * 128;
     static constexpr uint32_t kStageBytes = kABytes + kBBytes;
     static constexpr uint32_t kSmem = 1024 + kGemmStages * kStageBytes + 8 * kGemmStages + 16;
     static constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+    static_assert(4 * 32 * (BN + 1) * 4 <= kGemmStages * kStageBytes, "epilogue staging");
     static constexpr uint32_t kIdesc = idesc_n(BN);
 };
 
@@ -557,7 +766,8 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcGemm g) {
         const int lb = nblk - 1;  // the last commit covers every earlier MMA
         const bool got = mbar_wait(sBar + 8 * (lb % kGemmStages), (uint32_t)(lb / kGemmStages) & 1u);
         ok = __syncthreads_and(got);
-        if (ok) {
+        if (ok && g.transposed) {
+            // C[n][m]: lanes hold consecutive m, so each store is coalesced
             tc_fence_after();
             const int m = m0 + warp * 32 + lane;  // TMEM lane = tile row
 #pragma unroll 1
@@ -572,13 +782,44 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcGemm g) {
                     if (n >= g.N) break;
                     float val = __uint_as_float(v[e]);
                     if (g.bias) val += __ldg(g.bias + n);
+                    float *dst = g.C + (size_t)n * g.ldc + m;
+                    if (g.atomic) atomicAdd(dst, val);
+                    else *dst = val;
+                }
+            }
+        } else if (ok) {
+            // row-major C: each warp stages its 32 rows in shared memory (the
+            // ring, idle now; row stride BN + 1 words, no bank conflicts) and
+            // writes them back a row at a time, 32 consecutive columns per
+            // store
+            tc_fence_after();
+            float *stage = reinterpret_cast<float *>(gbase) + warp * 32 * (BN + 1);
+#pragma unroll 1
+            for (int q = 0; q < BN / 16; ++q) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * q), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int e = 0; e < 16; ++e) stage[lane * (BN + 1) + 16 * q + e] = __uint_as_float(v[e]);
+            }
+            __syncwarp();
+            for (int rr = 0; rr < 32; ++rr) {
+                const int m = m0 + warp * 32 + rr;
+                if (m >= g.M) break;
+#pragma unroll
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    const int n = n0 + c0 + lane;
+                    if (n >= g.N) continue;
+                    float val = stage[rr * (BN + 1) + c0 + lane];
+                    if (g.bias) val += __ldg(g.bias + n);
+                    const size_t o = (size_t)m * g.ldc + n;
                     if (EPI == kGelu) {
-                        g.pre[(size_t)m * g.ldc + n] = val;
-                        g.Cb[(size_t)m * g.ldc + n] = __float2bfloat16(gelu_exact(val));
+                        g.pre[o] = val;
+                        g.Cb[o] = __float2bfloat16(gelu_exact(val));
+                    } else if (g.atomic) {
+                        atomicAdd(g.C + o, val);
                     } else {
-                        float *dst = g.C + (g.transposed ? (size_t)n * g.ldc + m : (size_t)m * g.ldc + n);
-                        if (g.atomic) atomicAdd(dst, val);
-                        else *dst = val;
+                        g.C[o] = val;
                     }
                 }
             }
@@ -653,8 +894,7 @@ cudaError_t conv_back_tc(const float *dact, const float *pre, const __nv_bfloat1
 cudaError_t conv0_back(const float *dact, const float *pre, const __nv_bfloat16 *x, int nb,
                        float *gW, float *gb, int sms, cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
-    const size_t rows = (size_t)nb * 256;
-    const int grid = (int)std::max<size_t>(1, std::min<size_t>((rows + 31) / 32, (size_t)sms * 4));
+    const int grid = std::max(1, std::min(nb, sms * 4));
     conv0_back_kernel<<<grid, 256, 0, st>>>(dact, pre, x, nb, gW, gb);
     return cudaGetLastError();
 }
@@ -688,6 +928,26 @@ cudaError_t transpose_bf16(const __nv_bfloat16 *in, int R, int C, int ldi, __nv_
     if (R <= 0 || Cpad <= 0) return cudaSuccess;
     dim3 grid((std::max(R, ldo) + 31) / 32, (Cpad + 31) / 32);
     transpose_bf16_kernel<<<grid, 256, 0, st>>>(in, R, C, ldi, out, ldo, Cpad);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_fwd_tc(const __nv_bfloat16 *x, int nb, int lout, const __nv_bfloat16 *W,
+                        const float *bias, float *pre, __nv_bfloat16 *out, uint32_t *status, int sms,
+                        cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    if (lout != 128 && lout != 64 && lout != 32) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(W) & 15))
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            conv_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntiles = (nb * lout + kRowsPerTile - 1) / kRowsPerTile;
+    const int grid = std::max(1, std::min(ntiles, sms));
+    conv_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, st>>>(x, nb, lout, W, bias, pre, out, status);
     return cudaGetLastError();
 }
 
