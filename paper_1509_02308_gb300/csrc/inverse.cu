@@ -27,23 +27,12 @@
 
 #include "conv_tc.cuh"
 #include "pchase_internal.cuh"
+#include "tc_common.cuh"
 
 namespace pchase {
 
 namespace {
 
-__device__ __forceinline__ float gelu_f(float x) {
-    // tanh form of GELU (Hendrycks & Gimpel 2016)
-    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-    return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
-}
-
-__device__ __forceinline__ float gelu_grad(float x) {
-    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-    const float u = k0 * (x + k1 * x * x * x);
-    const float t = tanhf(u);
-    return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * x * x);
-}
 
 
 // --------------------------------------------------------- network plumbing
@@ -61,7 +50,7 @@ __global__ void gelu_back_kernel(const float *dy, const float *pre, size_t n, fl
                                  __nv_bfloat16 *dzb) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        const float v = dy[i] * gelu_grad(pre[i]);
+        const float v = dy[i] * gelu_grad_t(pre[i]);
         if (dzf) dzf[i] = v;
         dzb[i] = __float2bfloat16(v);
     }
@@ -271,7 +260,7 @@ __global__ void __launch_bounds__(256) conv1_kernel(const __nv_bfloat16 *__restr
             uint32_t pk[4];
 #pragma unroll
             for (int c = 0; c < 8; c += 2) {
-                const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_f(v[c]), gelu_f(v[c + 1]));
+                const __nv_bfloat162 hv = __floats2bfloat162_rn(gelu_t(v[c]), gelu_t(v[c + 1]));
                 pk[c >> 1] = *reinterpret_cast<const uint32_t *>(&hv);
             }
             *reinterpret_cast<uint4 *>(out + row * kCh + g * 8) =

@@ -166,5 +166,31 @@ __device__ __forceinline__ uint32_t gelu2h_bf16(uint64_t xh) {
     return d;
 }
 
+// The tanh form of GELU (Hendrycks & Gimpel 2016), 0.5 x (1 + tanh(u)) with
+// u = k0 (x + k1 x^3), written as x s with s = 1 / (1 + exp(-2u)) (the same
+// function: 1 + tanh(u) = 2 / (1 + exp(-2u))), and its derivative
+// s + 2 x s (1 - s) k0 (1 + 3 k1 x^2), with 1 - s = exp(-2u) s.  One ex2.approx
+// and one rcp.approx (a few ulp each) per value and no cancellation in either
+// tail; exp(-2u) is capped at 2^126 so that it stays finite.
+__device__ __forceinline__ float gelu_sig_parts(float x, float &e) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f, log2e = 1.4426950408889634f;
+    const float c0 = -2.0f * k0 * log2e, c1 = -2.0f * k0 * k1 * log2e;
+    const float v = fminf(x * fmaf(c1, x * x, c0), 126.0f);  // -2u log2(e)
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(v));
+    float s;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(1.0f + e));
+    return s;
+}
+__device__ __forceinline__ float gelu_t(float x) {
+    float e;
+    return x * gelu_sig_parts(x, e);
+}
+__device__ __forceinline__ float gelu_grad_t(float x) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    float e;
+    const float s = gelu_sig_parts(x, e);
+    return fmaf(2.0f * k0 * x * s * (e * s), fmaf(3.0f * k1, x * x, 1.0f), s);
+}
+
 }  // namespace
 }  // namespace pchase

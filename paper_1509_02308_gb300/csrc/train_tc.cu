@@ -54,7 +54,7 @@ namespace {
 constexpr int kCh = 64;
 constexpr int kTaps = 5;
 constexpr int kRowsPerTile = 128;
-constexpr int kBackThreads = 256;
+constexpr int kBackThreads = 512;
 
 // shared-memory layout (bytes from the 1024-aligned base)
 constexpr uint32_t kOffS = 0;                       // S_0, S_1, S_2: 128 rows x 128 B each
@@ -78,21 +78,6 @@ constexpr uint32_t idesc_n(uint32_t n) {
 constexpr uint32_t kIdescDx = idesc_n(128);
 constexpr uint32_t kIdescGw = idesc_n(64);
 constexpr uint32_t kBackTmemCols = 512;  // dx 128 + gW 3 x 64, rounded to a power of two
-
-__device__ __forceinline__ float gelu_grad_f(float x) {
-    // derivative of the tanh form of GELU (Hendrycks & Gimpel 2016)
-    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-    const float u = k0 * (x + k1 * x * x * x);
-    const float t = tanhf(u);
-    return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * x * x);
-}
-
-// the tanh form of GELU (Hendrycks & Gimpel 2016), as the training forward
-// pass computes it
-__device__ __forceinline__ float gelu_exact(float x) {
-    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-    return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
-}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     uint32_t d;
@@ -122,11 +107,13 @@ __device__ __forceinline__ uint32_t sw_chunk(uint32_t r, uint32_t c) {
     return r * 128u + ((c ^ (r & 7u)) << 4);
 }
 
+template <int LOUT>
 __global__ void __launch_bounds__(kBackThreads, 1)
     conv_back_tc_kernel(const float *__restrict__ dact, const float *__restrict__ pre,
                         const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ W,
-                        int nb, int lout, float *__restrict__ gW, float *__restrict__ gb,
+                        int nb, float *__restrict__ gW, float *__restrict__ gb,
                         float *__restrict__ dx, uint32_t *status) {
+    constexpr int lout = LOUT;
     extern __shared__ uint8_t dsm[];
     const uint32_t raw = smem_u32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -201,11 +188,11 @@ __global__ void __launch_bounds__(kBackThreads, 1)
     };
     // ---- this thread's dact and pre of tile t (rows r0 + 32 i, channels
     // 8c .. 8c + 7), loaded a tile ahead
-    float4 fa[4][2], fp[4][2];
+    float4 fa[2][2], fp[2][2];
     auto fetch_rows = [&](int t) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int grow = t * kRowsPerTile + (tid >> 3) + 32 * i;
+        for (int i = 0; i < 2; ++i) {
+            const int grow = t * kRowsPerTile + (tid >> 3) + 64 * i;
             if (t < ntiles && grow < nrows) {
                 const float4 *da = reinterpret_cast<const float4 *>(dact + (size_t)grow * kCh + c * 8);
                 const float4 *pa = reinterpret_cast<const float4 *>(pre + (size_t)grow * kCh + c * 8);
@@ -224,20 +211,20 @@ __global__ void __launch_bounds__(kBackThreads, 1)
         const int row0 = t * kRowsPerTile;
         // ---- dz into S_0, S_1, S_2 (rows past the end hold zeros)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = (tid >> 3) + 32 * i;
+        for (int i = 0; i < 2; ++i) {
+            const int r = (tid >> 3) + 64 * i;
             const int grow = row0 + r;
             float d[8];
             if (grow < nrows) {
                 const float4 a0 = fa[i][0], a1 = fa[i][1], p0 = fp[i][0], p1 = fp[i][1];
-                d[0] = a0.x * gelu_grad_f(p0.x);
-                d[1] = a0.y * gelu_grad_f(p0.y);
-                d[2] = a0.z * gelu_grad_f(p0.z);
-                d[3] = a0.w * gelu_grad_f(p0.w);
-                d[4] = a1.x * gelu_grad_f(p1.x);
-                d[5] = a1.y * gelu_grad_f(p1.y);
-                d[6] = a1.z * gelu_grad_f(p1.z);
-                d[7] = a1.w * gelu_grad_f(p1.w);
+                d[0] = a0.x * gelu_grad_t(p0.x);
+                d[1] = a0.y * gelu_grad_t(p0.y);
+                d[2] = a0.z * gelu_grad_t(p0.z);
+                d[3] = a0.w * gelu_grad_t(p0.w);
+                d[4] = a1.x * gelu_grad_t(p1.x);
+                d[5] = a1.y * gelu_grad_t(p1.y);
+                d[6] = a1.z * gelu_grad_t(p1.z);
+                d[7] = a1.w * gelu_grad_t(p1.w);
             } else {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) d[e] = 0.0f;
@@ -340,21 +327,23 @@ __global__ void __launch_bounds__(kBackThreads, 1)
             ++it;
             break;
         }
-        // ---- dx epilogue: warp w reads lanes 32 (w % 4) .., columns 64 (w / 4) ..
+        // ---- dx epilogue: warp w reads lanes 32 (w % 4) .. (rows q) and
+        // columns 32 (w / 4) .. +31: even positions for w / 4 < 2, odd after
         {
-            const int lg = warp & 3, h = warp >> 2;
+            const int lg = warp & 3, qq = warp >> 2, h = qq >> 1;
             const int q = 32 * lg + lane;
-            uint32_t v[4][16];
+            uint32_t v[2][16];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(64 * h + 16 * k), v[k]);
+            for (int k = 0; k < 2; ++k)
+                tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * qq + 16 * k), v[k]);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int grow = row0 + q;
             if (grow < nrows) {
                 const int b = grow / lout, lo = grow % lout;
-                float4 *o = reinterpret_cast<float4 *>(dx + ((size_t)b * lin + 2 * lo + h) * kCh);
+                float4 *o = reinterpret_cast<float4 *>(dx + ((size_t)b * lin + 2 * lo + h) * kCh +
+                                                       32 * (qq & 1));
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < 2; ++k)
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
                         o[4 * k + e] = make_float4(__uint_as_float(v[k][4 * e]),
@@ -370,7 +359,7 @@ __global__ void __launch_bounds__(kBackThreads, 1)
     for (int e = 0; e < 8; ++e) atomicAdd(&sbias[c * 8 + e], bacc[e]);
     if (it > 0 && !timed_out) {
         const int lg = warp & 3;
-        for (int u = warp >> 2; u < 6; u += 2) {
+        for (int u = warp >> 2; u < 6; u += kBackThreads / 128) {
             const int mt = u >> 1, hh = u & 1;
             uint32_t v[2][16];
             tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 128u + 64u * (uint32_t)mt + 32u * hh, v[0]);
@@ -464,7 +453,7 @@ __global__ void __launch_bounds__(256) conv0_back_kernel(const float *__restrict
                                      pr[h][1].x, pr[h][1].y, pr[h][1].z, pr[h][1].w};
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const float d = av[e] * gelu_grad_f(pv[e]);
+                    const float d = av[e] * gelu_grad_t(pv[e]);
                     ab[e] += d;
                     const float db = __bfloat162float(__float2bfloat16(d));
 #pragma unroll
@@ -508,17 +497,19 @@ __global__ void __launch_bounds__(256) conv0_back_kernel(const float *__restrict
 // worth in flight (the next tile loads while this one's MMAs and epilogue
 // run); the weights W_kk[co][ci] are five B tiles loaded once.  20 MMAs
 // (M128 N64 K16) per tile into one of two TMEM accumulators.
-constexpr int kFwdThreads = 256;
+constexpr int kFwdThreads = 512;
 constexpr uint32_t kFwdW = 5 * 8192;             // B tiles: 64 rows x 128 B per tap
 constexpr uint32_t kFwdA = 5 * 16384;            // A tiles of one tile: 128 rows x 128 B per tap
 constexpr uint32_t kFwdSmem = 1024 + kFwdW + 2 * kFwdA + 32;
 static_assert(kFwdSmem <= 232448, "shared memory");
 
+template <int LOUT>
 __global__ void __launch_bounds__(kFwdThreads, 1)
-    conv_fwd_tc_kernel(const __nv_bfloat16 *__restrict__ x, int nb, int lout,
+    conv_fwd_tc_kernel(const __nv_bfloat16 *__restrict__ x, int nb,
                        const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
                        float *__restrict__ pre, __nv_bfloat16 *__restrict__ out,
                        uint32_t *status) {
+    constexpr int lout = LOUT;
     extern __shared__ uint8_t dsm[];
     const uint32_t raw = smem_u32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -601,34 +592,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             if (tid == 0) mbar_wait(sBar + 8u * (uint32_t)s, (uint32_t)(j >> 1) & 1u);
             break;
         }
-        // epilogue: warp w takes TMEM lanes 32 (w % 4) .. (rows), channels 32 (w / 4) ..
-        const int lg = warp & 3, half = warp >> 2;
-        uint32_t v[2][16];
-        tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 64u * (uint32_t)s + 32u * half, v[0]);
-        tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 64u * (uint32_t)s + 32u * half + 16u, v[1]);
+        // epilogue: warp w takes TMEM lanes 32 (w % 4) .. (rows), channels 16 (w / 4) ..
+        const int lg = warp & 3, qq = warp >> 2;
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 64u * (uint32_t)s + 16u * (uint32_t)qq, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int grow = t * kRowsPerTile + 32 * lg + lane;
         if (grow < nrows) {
-            float4 *po = reinterpret_cast<float4 *>(pre + (size_t)grow * kCh + 32 * half);
-            uint4 *ao = reinterpret_cast<uint4 *>(out + (size_t)grow * kCh + 32 * half);
+            float4 *po = reinterpret_cast<float4 *>(pre + (size_t)grow * kCh + 16 * qq);
+            uint4 *ao = reinterpret_cast<uint4 *>(out + (size_t)grow * kCh + 16 * qq);
+            float y[16];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                float y[16];
+            for (int e = 0; e < 16; ++e) y[e] = __uint_as_float(v[e]) + __ldg(bias + 16 * qq + e);
 #pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    y[e] = __uint_as_float(v[k][e]) + __ldg(bias + 32 * half + 16 * k + e);
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    po[4 * k + e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
-                ao[2 * k] = make_uint4(pack_bf16(gelu_exact(y[0]), gelu_exact(y[1])),
-                                       pack_bf16(gelu_exact(y[2]), gelu_exact(y[3])),
-                                       pack_bf16(gelu_exact(y[4]), gelu_exact(y[5])),
-                                       pack_bf16(gelu_exact(y[6]), gelu_exact(y[7])));
-                ao[2 * k + 1] = make_uint4(pack_bf16(gelu_exact(y[8]), gelu_exact(y[9])),
-                                           pack_bf16(gelu_exact(y[10]), gelu_exact(y[11])),
-                                           pack_bf16(gelu_exact(y[12]), gelu_exact(y[13])),
-                                           pack_bf16(gelu_exact(y[14]), gelu_exact(y[15])));
-            }
+            for (int e = 0; e < 4; ++e)
+                po[e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
+            ao[0] = make_uint4(pack_bf16(gelu_t(y[0]), gelu_t(y[1])), pack_bf16(gelu_t(y[2]), gelu_t(y[3])),
+                               pack_bf16(gelu_t(y[4]), gelu_t(y[5])), pack_bf16(gelu_t(y[6]), gelu_t(y[7])));
+            ao[1] = make_uint4(pack_bf16(gelu_t(y[8]), gelu_t(y[9])), pack_bf16(gelu_t(y[10]), gelu_t(y[11])),
+                               pack_bf16(gelu_t(y[12]), gelu_t(y[13])), pack_bf16(gelu_t(y[14]), gelu_t(y[15])));
         }
         tc_fence_before();
     }
@@ -815,7 +797,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcGemm g) {
                     const size_t o = (size_t)m * g.ldc + n;
                     if (EPI == kGelu) {
                         g.pre[o] = val;
-                        g.Cb[o] = __float2bfloat16(gelu_exact(val));
+                        g.Cb[o] = __float2bfloat16(gelu_t(val));
                     } else if (g.atomic) {
                         atomicAdd(g.C + o, val);
                     } else {
@@ -879,15 +861,21 @@ cudaError_t conv_back_tc(const float *dact, const float *pre, const __nv_bfloat1
     if (lout != 128 && lout != 64 && lout != 32) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            conv_back_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBackSmem);
-        if (e != cudaSuccess) return e;
+        for (auto k : {conv_back_tc_kernel<128>, conv_back_tc_kernel<64>, conv_back_tc_kernel<32>}) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBackSmem);
+            if (e != cudaSuccess) return e;
+        }
         attr = true;
     }
     const int ntiles = (nb * lout + kRowsPerTile - 1) / kRowsPerTile;
     const int grid = std::max(1, std::min(ntiles, sms));
-    conv_back_tc_kernel<<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, x, W, nb, lout, gW, gb,
-                                                               dx, status);
+    if (lout == 128)
+        conv_back_tc_kernel<128><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, x, W, nb, gW, gb, dx, status);
+    else if (lout == 64)
+        conv_back_tc_kernel<64><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, x, W, nb, gW, gb, dx, status);
+    else
+        conv_back_tc_kernel<32><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, x, W, nb, gW, gb, dx, status);
     return cudaGetLastError();
 }
 
@@ -940,14 +928,21 @@ cudaError_t conv_fwd_tc(const __nv_bfloat16 *x, int nb, int lout, const __nv_bfl
         return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            conv_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-        if (e != cudaSuccess) return e;
+        for (auto k : {conv_fwd_tc_kernel<128>, conv_fwd_tc_kernel<64>, conv_fwd_tc_kernel<32>}) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+            if (e != cudaSuccess) return e;
+        }
         attr = true;
     }
     const int ntiles = (nb * lout + kRowsPerTile - 1) / kRowsPerTile;
     const int grid = std::max(1, std::min(ntiles, sms));
-    conv_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, st>>>(x, nb, lout, W, bias, pre, out, status);
+    if (lout == 128)
+        conv_fwd_tc_kernel<128><<<grid, kFwdThreads, kFwdSmem, st>>>(x, nb, W, bias, pre, out, status);
+    else if (lout == 64)
+        conv_fwd_tc_kernel<64><<<grid, kFwdThreads, kFwdSmem, st>>>(x, nb, W, bias, pre, out, status);
+    else
+        conv_fwd_tc_kernel<32><<<grid, kFwdThreads, kFwdSmem, st>>>(x, nb, W, bias, pre, out, status);
     return cudaGetLastError();
 }
 
