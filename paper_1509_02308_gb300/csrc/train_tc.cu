@@ -41,6 +41,8 @@
 // Completion waits on the mbarrier give up after 2 s of %globaltimer: the
 // CTA then ORs PCHASE_DEV_TIMEOUT into *status, waits (again with a limit) for
 // the MMAs it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -490,62 +492,81 @@ __global__ void __launch_bounds__(256) conv0_back_kernel(const float *__restrict
 // ------------------------------------------------------- forward (training)
 // One 64-channel layer with the pre-activations kept for the backward pass:
 // pre[row][co] = bias[co] + sum_kk sum_ci W[co][kk*64 + ci] x[b][2 lo + kk - 2][ci]
-// (FP32) and out[row][co] = BF16(GELU(pre)) with the exact tanh, row = (b, lo).
-// A tile is 128 rows (whole traces); its five tap operands A_kk[row][ci] =
-// x[b][2 lo + kk - 2][ci] (zero outside the trace) are gathered from global
-// memory by cp.async straight into K-major 128-byte-swizzled tiles, two tiles'
-// worth in flight (the next tile loads while this one's MMAs and epilogue
-// run); the weights W_kk[co][ci] are five B tiles loaded once.  20 MMAs
-// (M128 N64 K16) per tile into one of two TMEM accumulators.
+// (FP32) and out[row][co] = BF16(GELU(pre)), row = (b, lo).  A tile is 128 rows
+// (whole traces).  Its five tap operands A_kk[row][ci] = x[b][2 lo + kk - 2][ci]
+// are TMA tile loads: x is described as a 4-D tensor (channel, parity, pair,
+// trace) = x[trace][2 pair + parity][channel], and tap kk is the box
+// (64 channels, parity kk % 2, pairs kk / 2 - 1 .. + LOUT - 1, the tile's
+// traces), 128 rows of 128 bytes with the 128-byte swizzle, i.e. a K-major
+// operand as the MMA reads it; pairs outside the trace (the zero padding)
+// and traces past the batch are out of the tensor and read as zeros.  One
+// thread issues the next tile's five loads (one mbarrier with the byte
+// count) while this tile's MMAs and epilogue run.  The weights W_kk[co][ci] are
+// five B tiles loaded once.  20 MMAs (M128 N64 K16) per tile.
 constexpr int kFwdThreads = 512;
 constexpr uint32_t kFwdW = 5 * 8192;             // B tiles: 64 rows x 128 B per tap
 constexpr uint32_t kFwdA = 5 * 16384;            // A tiles of one tile: 128 rows x 128 B per tap
-constexpr uint32_t kFwdSmem = 1024 + kFwdW + 2 * kFwdA + 32;
+constexpr uint32_t kFwdSmem = 1024 + kFwdW + 2 * kFwdA + 64;
 static_assert(kFwdSmem <= 232448, "shared memory");
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
 
 template <int LOUT>
 __global__ void __launch_bounds__(kFwdThreads, 1)
-    conv_fwd_tc_kernel(const __nv_bfloat16 *__restrict__ x, int nb,
+    conv_fwd_tc_kernel(const __grid_constant__ CUtensorMap xmap, int nb,
                        const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
                        float *__restrict__ pre, __nv_bfloat16 *__restrict__ out,
                        uint32_t *status) {
-    constexpr int lout = LOUT;
+    constexpr int tpt = kRowsPerTile / LOUT;
     extern __shared__ uint8_t dsm[];
     const uint32_t raw = smem_u32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *const gbase = dsm + (base - raw);
     const uint32_t sW = base, sA = base + kFwdW;
-    const uint32_t sBar = base + kFwdW + 2 * kFwdA;  // 2 mbarriers (one per accumulator)
-    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + kFwdW + 2 * kFwdA + 16);
+    // mbarriers: MMA done [2] at sBar + 8s, operands loaded [2] at sBar + 16 + 8s
+    const uint32_t sBar = base + kFwdW + 2 * kFwdA;
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + kFwdW + 2 * kFwdA + 32);
+    volatile uint32_t *const abort_flag = tslot + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lin = 2 * lout, nrows = nb * lout;
+    const int nrows = nb * LOUT;
     const int ntiles = (nrows + kRowsPerTile - 1) / kRowsPerTile;
-    const int tpt = kRowsPerTile / lout;
+    const int lg = warp & 3, qq = warp >> 2;  // epilogue: TMEM lanes 32 lg.., channels 16 qq..
+    float bq[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) bq[e] = __ldg(bias + 16 * qq + e);
 
     for (int e = tid; e < kTaps * kCh * 8; e += kFwdThreads) {
         const int kk = e >> 9, co = (e >> 3) & 63, c = e & 7;
         cp_async16(sW + (uint32_t)kk * 8192u + sw_chunk((uint32_t)co, (uint32_t)c),
                    W + (size_t)co * (kTaps * kCh) + kk * kCh + c * 8, true);
     }
-    // the tap operands of tile t into buffer s
+    cp_async_commit();
+    // the five tap boxes of tile t into buffer s (one thread)
     auto load = [&](int t, int s) {
-        if (t < ntiles) {
-            const int b0 = t * tpt;
-            for (int e = tid; e < kTaps * kRowsPerTile * 8; e += kFwdThreads) {
-                const int kk = e >> 10, r = (e >> 3) & 127, c = e & 7;
-                const int tb = r / lout, lo = r % lout, p = 2 * lo + kk - 2;
-                const bool ok = b0 + tb < nb && p >= 0 && p < lin;
-                cp_async16(sA + (uint32_t)s * kFwdA + (uint32_t)kk * 16384u +
-                               sw_chunk((uint32_t)r, (uint32_t)c),
-                           ok ? x + ((size_t)(b0 + tb) * lin + p) * kCh + c * 8 : x, ok);
-            }
-        }
-        cp_async_commit();
+        const uint32_t bar = sBar + 16u + 8u * (uint32_t)s;
+        mbar_expect_tx(bar, kFwdA);
+#pragma unroll
+        for (int kk = 0; kk < kTaps; ++kk)
+            tma_load_4d(sA + (uint32_t)s * kFwdA + (uint32_t)kk * 16384u, &xmap, 0, kk & 1,
+                        (kk >> 1) - 1, t * tpt, bar);
     };
     if (tid == 0) {
-        for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < 4; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8 * q) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+        if ((int)blockIdx.x < ntiles) load(blockIdx.x, 0);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -554,32 +575,44 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    load(blockIdx.x, 0);  // the weights ride in the first group
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
     bool ok = true;
-    int j = 0;
+    int j = 0, last_load = (int)blockIdx.x < ntiles ? 0 : -1;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
         const int s = j & 1;
-        // buffer s ^ 1 was last read by tile j - 1's MMAs, waited for below
-        load(t + gridDim.x, s ^ 1);
-        cp_async_wait1();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
+        if (j > 0) {
+            // every thread is done with the previous tile's accumulator
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        }
         if (tid == 0) {
-            const uint32_t a0 = sA + (uint32_t)s * kFwdA;
+            // buffer s ^ 1 was last read by tile j - 1's MMAs, complete
+            if (t + (int)gridDim.x < ntiles) {
+                load(t + gridDim.x, s ^ 1);
+                last_load = j + 1;
+            }
+            if (mbar_wait(sBar + 16u + 8u * (uint32_t)s, (uint32_t)(j >> 1) & 1u)) {
+                tc_fence_after();
+                const uint32_t a0 = sA + (uint32_t)s * kFwdA;
 #pragma unroll
-            for (int kk = 0; kk < kTaps; ++kk)
+                for (int kk = 0; kk < kTaps; ++kk)
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    mma_bf16_id(tmem + 64u * (uint32_t)s, sw128_desc(a0 + (uint32_t)kk * 16384u + 32u * q),
-                                sw128_desc(sW + (uint32_t)kk * 8192u + 32u * q), kIdescGw,
-                                (kk | q) != 0 ? 1u : 0u);
+                    for (int q = 0; q < 4; ++q)
+                        mma_bf16_id(tmem + 64u * (uint32_t)s,
+                                    sw128_desc(a0 + (uint32_t)kk * 16384u + 32u * q),
+                                    sw128_desc(sW + (uint32_t)kk * 8192u + 32u * q), kIdescGw,
+                                    (kk | q) != 0 ? 1u : 0u);
+            } else {
+                *abort_flag = 1;
+            }
+            // the commit arrives even without MMAs, so no thread waits in vain
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     sBar + 8u * (uint32_t)s)
@@ -587,13 +620,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         }
         const bool got = mbar_wait(sBar + 8u * (uint32_t)s, (uint32_t)(j >> 1) & 1u);
         tc_fence_after();
-        if (!__syncthreads_and(got)) {
+        if (__syncthreads_or(!got || *abort_flag != 0)) {
             ok = false;
-            if (tid == 0) mbar_wait(sBar + 8u * (uint32_t)s, (uint32_t)(j >> 1) & 1u);
             break;
         }
-        // epilogue: warp w takes TMEM lanes 32 (w % 4) .. (rows), channels 16 (w / 4) ..
-        const int lg = warp & 3, qq = warp >> 2;
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 64u * (uint32_t)s + 16u * (uint32_t)qq, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -603,7 +633,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             uint4 *ao = reinterpret_cast<uint4 *>(out + (size_t)grow * kCh + 16 * qq);
             float y[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) y[e] = __uint_as_float(v[e]) + __ldg(bias + 16 * qq + e);
+            for (int e = 0; e < 16; ++e) y[e] = __uint_as_float(v[e]) + bq[e];
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 po[e] = make_float4(y[4 * e], y[4 * e + 1], y[4 * e + 2], y[4 * e + 3]);
@@ -612,10 +642,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             ao[1] = make_uint4(pack_bf16(gelu_t(y[8]), gelu_t(y[9])), pack_bf16(gelu_t(y[10]), gelu_t(y[11])),
                                pack_bf16(gelu_t(y[12]), gelu_t(y[13])), pack_bf16(gelu_t(y[14]), gelu_t(y[15])));
         }
-        tc_fence_before();
     }
-    if (!ok && tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
-    cp_async_wait_all();
+    if (!ok && tid == 0) {
+        atomicOr(status, PCHASE_DEV_TIMEOUT);
+        // loads and MMAs still in flight land before the CTA leaves
+        if (last_load >= j)
+            mbar_wait(sBar + 16u + 8u * (uint32_t)(last_load & 1), (uint32_t)(last_load >> 1) & 1u);
+        mbar_wait(sBar + 8u * (uint32_t)(j & 1), (uint32_t)(j >> 1) & 1u);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -919,12 +953,40 @@ cudaError_t transpose_bf16(const __nv_bfloat16 *in, int R, int C, int ldi, __nv_
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
 cudaError_t conv_fwd_tc(const __nv_bfloat16 *x, int nb, int lout, const __nv_bfloat16 *W,
                         const float *bias, float *pre, __nv_bfloat16 *out, uint32_t *status, int sms,
                         cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
     if (lout != 128 && lout != 64 && lout != 32) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(W) & 15))
+        return cudaErrorInvalidValue;
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    // x[trace][2 pair + parity][channel] as (channel, parity, pair, trace)
+    alignas(64) CUtensorMap map;
+    const cuuint64_t dims[4] = {(cuuint64_t)kCh, 2, (cuuint64_t)lout, (cuuint64_t)nb};
+    const cuuint64_t strides[3] = {kCh * 2, 2 * kCh * 2, (cuuint64_t)lout * 2 * kCh * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)kCh, 1, (cuuint32_t)lout,
+                               (cuuint32_t)(kRowsPerTile / lout)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(x), dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
@@ -938,11 +1000,11 @@ cudaError_t conv_fwd_tc(const __nv_bfloat16 *x, int nb, int lout, const __nv_bfl
     const int ntiles = (nb * lout + kRowsPerTile - 1) / kRowsPerTile;
     const int grid = std::max(1, std::min(ntiles, sms));
     if (lout == 128)
-        conv_fwd_tc_kernel<128><<<grid, kFwdThreads, kFwdSmem, st>>>(x, nb, W, bias, pre, out, status);
+        conv_fwd_tc_kernel<128><<<grid, kFwdThreads, kFwdSmem, st>>>(map, nb, W, bias, pre, out, status);
     else if (lout == 64)
-        conv_fwd_tc_kernel<64><<<grid, kFwdThreads, kFwdSmem, st>>>(x, nb, W, bias, pre, out, status);
+        conv_fwd_tc_kernel<64><<<grid, kFwdThreads, kFwdSmem, st>>>(map, nb, W, bias, pre, out, status);
     else
-        conv_fwd_tc_kernel<32><<<grid, kFwdThreads, kFwdSmem, st>>>(x, nb, W, bias, pre, out, status);
+        conv_fwd_tc_kernel<32><<<grid, kFwdThreads, kFwdSmem, st>>>(map, nb, W, bias, pre, out, status);
     return cudaGetLastError();
 }
 

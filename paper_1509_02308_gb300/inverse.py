@@ -244,18 +244,53 @@ def lsq_match(rates: torch.Tensor, y: torch.Tensor):
     return best[:n], res[:n]
 
 
+def _train_timing(batch: int, steps: int, warmup: int, seed: int):
+    """CUDA-event time of `steps` training steps (after `warmup`) on one batch
+    of random traces and labels."""
+    g = torch.Generator(device=DEV).manual_seed(seed)
+    x = torch.rand(batch, W.PLAN_POINTS, device=DEV, generator=g)
+    lab = torch.stack([torch.randint(0, k, (batch,), device=DEV, generator=g) for k in (17, 4, 7, 3)],
+                      1).to(torch.int32).contiguous()
+    net = LearnedInverse(max_batch=batch)
+    net.init(seed=seed)
+    loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+
+    def step(s):
+        _check(net.L.pchase_inverse_train_step(net.h, net._p, net._w, C.ptr(x), C.ptr(lab), batch,
+                                               1e-3, s, C.ptr(loss), C.stream_handle()))
+    for s in range(warmup):
+        step(s)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for s in range(steps):
+        step(warmup + s)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / max(1, steps)
+    print(f"train step: {ms:.3f} ms per {batch} traces ({batch / ms / 1e3:.2f} M traces/s)")
+    _check(net.status())
+
+
 def _main():
     """Inference timing on random traces with freshly initialised weights:
     ``python -m paper_1509_02308_gb300.inverse --traces N --passes P`` runs P
     passes of the network over N traces in one inference-only handle and
-    prints the CUDA-event time of each."""
+    prints the CUDA-event time of each.  ``--train-steps K`` times K training
+    steps of ``--batch`` traces instead (after ``--warmup`` steps)."""
     import argparse
 
     p = argparse.ArgumentParser()
     p.add_argument("--traces", type=int, default=65536)
     p.add_argument("--passes", type=int, default=3)
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--train-steps", type=int, default=0)
+    p.add_argument("--batch", type=int, default=4096)
+    p.add_argument("--warmup", type=int, default=3)
     a = p.parse_args()
+    if a.train_steps:
+        _train_timing(a.batch, a.train_steps, a.warmup, a.seed)
+        return
     g = torch.Generator(device=DEV).manual_seed(a.seed)
     x = torch.rand(a.traces, W.PLAN_POINTS, device=DEV, generator=g)
     net = LearnedInverse(max_batch=a.traces, infer_only=True)
