@@ -64,10 +64,10 @@ constexpr uint32_t kOffWT = 3 * 16384;              // 3 B tiles of 128 rows (n)
 constexpr uint32_t kOffXT = kOffWT + 3 * 16384;     // 2 K atoms of 320 rows (kk, ci) x 64 rows
 constexpr uint32_t kXTAtom = 320 * 128;
 constexpr uint32_t kOffDZT = kOffXT + 2 * kXTAtom;  // 2 K atoms of 64 rows (co) x 64 rows
-constexpr uint32_t kOffXS = kOffDZT + 2 * 8192;     // input window: 256 rows x 128 B
+constexpr uint32_t kOffXS = kOffDZT + 2 * 8192;     // input window: 2 planes x 128 rows x 128 B
 constexpr uint32_t kOffZero = kOffXS + 256 * 128;   // one zero row (padding source)
-constexpr uint32_t kOffBar = kOffZero + 128;        // mbarrier, TMEM address, flags
-constexpr uint32_t kOffBias = kOffBar + 16;         // 64 FP32 bias partial sums
+constexpr uint32_t kOffBar = kOffZero + 128;        // mbarriers (MMA, window), TMEM address
+constexpr uint32_t kOffBias = kOffBar + 32;         // 64 FP32 bias partial sums
 constexpr uint32_t kBackSmem = 1024 + kOffBias + 64 * 4;
 static_assert(kOffXT + kXTAtom + 3 * 16384 <= kOffZero, "third gW tile reads past the window");
 static_assert(kBackSmem <= 232448, "shared memory");
@@ -109,10 +109,23 @@ __device__ __forceinline__ uint32_t sw_chunk(uint32_t r, uint32_t c) {
     return r * 128u + ((c ^ (r & 7u)) << 4);
 }
 
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
 template <int LOUT>
 __global__ void __launch_bounds__(kBackThreads, 1)
     conv_back_tc_kernel(const float *__restrict__ dact, const float *__restrict__ pre,
-                        const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ W,
+                        const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16 *__restrict__ W,
                         int nb, float *__restrict__ gW, float *__restrict__ gb,
                         float *__restrict__ dx, uint32_t *status) {
     constexpr int lout = LOUT;
@@ -123,7 +136,8 @@ __global__ void __launch_bounds__(kBackThreads, 1)
     const uint32_t sS = base + kOffS, sWT = base + kOffWT, sXT = base + kOffXT;
     const uint32_t sDZT = base + kOffDZT, sXS = base + kOffXS, sZero = base + kOffZero;
     const uint32_t sBar = base + kOffBar;
-    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + kOffBar + 8);
+    const uint32_t sXBar = sBar + 8;  // the window's TMA loads
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(gbase + kOffBar + 16);
     float *const sbias = reinterpret_cast<float *>(gbase + kOffBias);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -153,6 +167,7 @@ __global__ void __launch_bounds__(kBackThreads, 1)
     if (tid < kCh) sbias[tid] = 0.0f;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sXBar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -174,19 +189,21 @@ __global__ void __launch_bounds__(kBackThreads, 1)
     for (int e = 0; e < 8; ++e) bacc[e] = 0.0f;
     int it = 0;
     bool timed_out = false;
-    // ---- the input window of tile t's traces: row tb * lin + p holds
-    // position p of trace b0 + tb, chunk c at c ^ ((row / 2) mod 8)
+    // ---- the input window of tile t's traces as two TMA boxes, the even and
+    // the odd positions: row tb * LOUT + pr of plane pl holds position
+    // 2 pr + pl of trace t * tpt + tb (128-byte swizzle; traces past the batch
+    // read as zeros).  One thread issues them; every thread waits on the
+    // window's mbarrier before the transposes.
+    int windows = 0;  // window loads issued
     auto fetch_window = [&](int t) {
         if (t < ntiles) {
-            const int b0 = t * tpt;
-            for (int e = tid; e < 256 * 8; e += kBackThreads) {
-                const int r = e >> 3, cc = e & 7;
-                const bool ok = b0 + r / lin < nb;
-                cp_async16(sXS + (uint32_t)r * 128u + (uint32_t)((cc ^ ((r >> 1) & 7)) << 4),
-                           x + ((size_t)b0 * lin + (ok ? r : 0)) * kCh + cc * 8, ok);
+            if (tid == 0) {
+                mbar_expect_tx(sXBar, 2u * 16384u);
+                tma_load_4d(sXS, &xmap, 0, 0, 0, t * tpt, sXBar);
+                tma_load_4d(sXS + 16384u, &xmap, 0, 1, 0, t * tpt, sXBar);
             }
+            ++windows;
         }
-        cp_async_commit();
     };
     // ---- this thread's dact and pre of tile t (rows r0 + 32 i, channels
     // 8c .. 8c + 7), loaded a tile ahead
@@ -245,8 +262,11 @@ __global__ void __launch_bounds__(kBackThreads, 1)
             if (lo != lout - 1) st_shared_v4(sS + 32768u + sw_chunk((uint32_t)(r + 1), (uint32_t)c), v);
             if (lo == 0) st_shared_v4(sS + 32768u + sw_chunk((uint32_t)r, (uint32_t)c), z);
         }
-        cp_async_wait_all();
-        __syncthreads();
+        const bool wok = mbar_wait(sXBar, (uint32_t)(windows - 1) & 1u);
+        if (__syncthreads_or(!wok)) {
+            timed_out = true;
+            break;
+        }
         // ---- transposes by ldmatrix.trans: 8 x 8 blocks of (8 channels) x
         // (8 rows), four per instruction (channel chunks 4g .. 4g + 3).  A
         // thread receives, per block, channel 8 cc + lane / 4 of rows
@@ -258,13 +278,13 @@ __global__ void __launch_bounds__(kBackThreads, 1)
             for (int u = warp; u < kTaps * 2 * 16; u += kBackThreads / 32) {
                 const int kk = u / 32, g = (u >> 4) & 1, rb = u & 15;
                 const int r = rb * 8 + j, tb = r / lout, lo = r % lout;
-                const int p = 2 * lo + kk - 2;
+                // position 2 lo + kk - 2 = 2 pr + kk % 2
+                const int pr = lo + (kk >> 1) - 1;
                 const int cc = 4 * g + mi;
                 uint32_t src = sZero;
-                if (p >= 0 && p < lin) {
-                    const int xr = tb * lin + p;
-                    src = sXS + (uint32_t)xr * 128u + (uint32_t)((cc ^ ((xr >> 1) & 7)) << 4);
-                }
+                if (pr >= 0 && pr < lout)
+                    src = sXS + (uint32_t)(kk & 1) * 16384u +
+                          sw_chunk((uint32_t)(tb * lout + pr), (uint32_t)cc);
                 uint32_t v[4];
                 ldsm_x4_trans(src, v[0], v[1], v[2], v[3]);
 #pragma unroll
@@ -383,11 +403,11 @@ __global__ void __launch_bounds__(kBackThreads, 1)
         }
     }
     if (timed_out && tid == 0) {
-        // the last MMAs must finish before TMEM is freed
-        mbar_wait(sBar, (uint32_t)(it - 1) & 1u);
+        // the last MMAs and window loads land before TMEM is freed and the CTA leaves
+        if (it > 0) mbar_wait(sBar, (uint32_t)(it - 1) & 1u);
+        if (windows > 0) mbar_wait(sXBar, (uint32_t)(windows - 1) & 1u);
         atomicOr(status, PCHASE_DEV_TIMEOUT);
     }
-    cp_async_wait_all();  // a window fetched ahead of a timeout
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -508,19 +528,6 @@ constexpr uint32_t kFwdW = 5 * 8192;             // B tiles: 64 rows x 128 B per
 constexpr uint32_t kFwdA = 5 * 16384;            // A tiles of one tile: 128 rows x 128 B per tap
 constexpr uint32_t kFwdSmem = 1024 + kFwdW + 2 * kFwdA + 64;
 static_assert(kFwdSmem <= 232448, "shared memory");
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
-                                            int c2, int c3, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
 
 template <int LOUT>
 __global__ void __launch_bounds__(kFwdThreads, 1)
@@ -888,11 +895,48 @@ cudaError_t launch_tc_gemm(const TcGemm &g, int slices, cudaStream_t st) {
 
 }  // namespace
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// x [nb][2 lout][64] BF16 as the 4-D tensor (channel, parity, pair, trace)
+// with boxes of 64 channels x 1 parity x lout pairs x (128 / lout) traces,
+// 128-byte swizzle: the rows of one parity plane of a 128-row tile
+static cudaError_t x_plane_map(const __nv_bfloat16 *x, int nb, int lout, CUtensorMap *map) {
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {(cuuint64_t)kCh, 2, (cuuint64_t)lout, (cuuint64_t)nb};
+    const cuuint64_t strides[3] = {kCh * 2, 2 * kCh * 2, (cuuint64_t)lout * 2 * kCh * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)kCh, 1, (cuuint32_t)lout,
+                               (cuuint32_t)(kRowsPerTile / lout)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(x), dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
 cudaError_t conv_back_tc(const float *dact, const float *pre, const __nv_bfloat16 *x, int nb,
                          int lout, const __nv_bfloat16 *W, float *gW, float *gb, float *dx,
                          uint32_t *status, int sms, cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
     if (lout != 128 && lout != 64 && lout != 32) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(x) & 15) return cudaErrorInvalidValue;
+    alignas(64) CUtensorMap map;
+    const cudaError_t me = x_plane_map(x, nb, lout, &map);
+    if (me != cudaSuccess) return me;
     static bool attr = false;
     if (!attr) {
         for (auto k : {conv_back_tc_kernel<128>, conv_back_tc_kernel<64>, conv_back_tc_kernel<32>}) {
@@ -905,11 +949,11 @@ cudaError_t conv_back_tc(const float *dact, const float *pre, const __nv_bfloat1
     const int ntiles = (nb * lout + kRowsPerTile - 1) / kRowsPerTile;
     const int grid = std::max(1, std::min(ntiles, sms));
     if (lout == 128)
-        conv_back_tc_kernel<128><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, x, W, nb, gW, gb, dx, status);
+        conv_back_tc_kernel<128><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, map, W, nb, gW, gb, dx, status);
     else if (lout == 64)
-        conv_back_tc_kernel<64><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, x, W, nb, gW, gb, dx, status);
+        conv_back_tc_kernel<64><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, map, W, nb, gW, gb, dx, status);
     else
-        conv_back_tc_kernel<32><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, x, W, nb, gW, gb, dx, status);
+        conv_back_tc_kernel<32><<<grid, kBackThreads, kBackSmem, st>>>(dact, pre, map, W, nb, gW, gb, dx, status);
     return cudaGetLastError();
 }
 
@@ -953,21 +997,6 @@ cudaError_t transpose_bf16(const __nv_bfloat16 *in, int R, int C, int ldi, __nv_
     return cudaGetLastError();
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library)
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
 cudaError_t conv_fwd_tc(const __nv_bfloat16 *x, int nb, int lout, const __nv_bfloat16 *W,
                         const float *bias, float *pre, __nv_bfloat16 *out, uint32_t *status, int sms,
                         cudaStream_t st) {
@@ -975,19 +1004,9 @@ cudaError_t conv_fwd_tc(const __nv_bfloat16 *x, int nb, int lout, const __nv_bfl
     if (lout != 128 && lout != 64 && lout != 32) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(W) & 15))
         return cudaErrorInvalidValue;
-    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-    if (!encode) return cudaErrorNotSupported;
-    // x[trace][2 pair + parity][channel] as (channel, parity, pair, trace)
     alignas(64) CUtensorMap map;
-    const cuuint64_t dims[4] = {(cuuint64_t)kCh, 2, (cuuint64_t)lout, (cuuint64_t)nb};
-    const cuuint64_t strides[3] = {kCh * 2, 2 * kCh * 2, (cuuint64_t)lout * 2 * kCh * 2};
-    const cuuint32_t box[4] = {(cuuint32_t)kCh, 1, (cuuint32_t)lout,
-                               (cuuint32_t)(kRowsPerTile / lout)};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(x), dims,
-               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    const cudaError_t me = x_plane_map(x, nb, lout, &map);
+    if (me != cudaSuccess) return me;
     static bool attr = false;
     if (!attr) {
         for (auto k : {conv_fwd_tc_kernel<128>, conv_fwd_tc_kernel<64>, conv_fwd_tc_kernel<32>}) {
