@@ -176,6 +176,10 @@ SIM_WARP_INST_PER_ACCESS = (351888331 + 3918992) / 65559830
 # compare (ballot / match), the replacement-state update and the miss bit,
 # about 4-6 warp instructions; the middle of that range.
 ALG_WARP_INST_PER_ACCESS = 5.0
+# multiply-adds x 2 of one trace through the learned inverse: four k5 s2
+# convolutions to 64 channels (256 x 64 x 5, then 128, 64 and 32 positions x
+# 64 x 320), FC 2048 -> 256, heads 256 -> 31
+INVERSE_FLOP_PER_TRACE = 2 * (256 * 64 * 5 + (128 + 64 + 32) * 64 * 320 + 2048 * 256 + 256 * 31)
 
 
 def measured_peaks():
@@ -1201,6 +1205,17 @@ def learned_bench(args, dev):
                        "traces_per_s": n1 / (g_ms * 1e-3), "fallback": int(nf1.item()),
                        "accuracy_identical_rows": float((rep_exact[c1] == rep_exact[t1]).mean()),
                        "launch": "one CUDA graph replay (network chunks + fallback matcher)"}
+    # the network alone over the same million traces (16 full 65,536-trace
+    # chunks), CUDA events, after one untimed pass
+    net.infer(x1)
+    e0.record()
+    for _ in range(reps):
+        net.infer(x1)
+    e1.record()
+    torch.cuda.synchronize()
+    n_ms = e0.elapsed_time(e1) / reps
+    res["network_only_1M"] = {"traces": n1, "ms": n_ms, "traces_per_s": n1 / (n_ms * 1e-3),
+                              "gflops": n1 * INVERSE_FLOP_PER_TRACE / (n_ms * 1e-3) / 1e9}
     del x1, graph
     torch.cuda.empty_cache()
     return res
