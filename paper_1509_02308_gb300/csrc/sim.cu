@@ -563,26 +563,63 @@ struct BatchFR {
             const uint32_t sm0 =
                 __match_any_sync(kFull, head ? set : (0x80000000u | (uint32_t)lane));
             const uint32_t pm0 = lm0 & lt;
-            bool nohit = w0 == 0u && pm0 == 0u;
-            if (POLICY == PCHASE_FIFO) {
+            const int fh = __ffs(hb) - 1;
+            const bool one_set = POLICY == PCHASE_FIFO && __shfl_sync(kFull, sm0, fh) == hb;
+            if (one_set) {
+                // every head in one set s0: its counters are one broadcast
+                // load, a head's miss rank is its head rank r, and when all
+                // miss, the first a ranks find the ways in use (evicting
+                // their lines when the set is full) and the last a ranks are
+                // what stays (consecutive ranks fill consecutive ways)
+                const uint32_t s0 = __shfl_sync(kFull, set, fh);
+                const uint4 m = meta[s0];
+                const uint32_t a = ways;
+                const uint32_t r = __popc(hb & lt);
+                bool nh = w0 == 0u && pm0 == 0u;
                 if (pm0) {
                     const uint32_t below = (2u << (31 - __clz(pm0))) - 1u;
-                    nohit = (uint32_t)__popc(sm0 & lt & ~below) >= ways;
+                    nh = (uint32_t)__popc(hb & lt & ~below) >= a;
                 } else if (w0) {
-                    // held in way w, rho lines inserted before it: it leaves at
-                    // the (a - L + rho + 1)-th miss of its set
-                    const uint4 mf = head ? meta[set] : make_uint4(0, 0, 0, 0);
-                    const uint32_t rho = mod_ways(w0 - 1u + ways - mf.x, ways);
-                    nohit = (uint32_t)__popc(sm0 & lt) >= ways - mf.y + rho + 1u;
+                    const uint32_t rho = mod_ways(w0 - 1u + a - m.x, a);
+                    nh = r >= a - m.y + rho + 1u;
                 }
+                if (__all_sync(kFull, !head || nh)) {
+                    const uint32_t M = __popc(hb);
+                    const uint32_t insw = mod_ways(m.x + m.y + r, a);
+                    uint32_t *const sl = sline + (size_t)s0 * a;
+                    if (head && r < a && m.y + r >= a) tab[sl[insw]] = 0;
+                    __syncwarp();
+                    if (head && r + a >= M) {
+                        sl[insw] = line;
+                        tab[line] = (uint16_t)(insw + 1);
+                    }
+                    if (lane == fh) meta[s0] = after_misses(m, M);
+                    __syncwarp();
+                    return head;
+                }
+                pure_skip = 7;  // (the test below would fail the same way)
+            } else {
+                bool nohit = w0 == 0u && pm0 == 0u;
+                if (POLICY == PCHASE_FIFO) {
+                    if (pm0) {
+                        const uint32_t below = (2u << (31 - __clz(pm0))) - 1u;
+                        nohit = (uint32_t)__popc(sm0 & lt & ~below) >= ways;
+                    } else if (w0) {
+                        // held in way w, rho lines inserted before it: it leaves at
+                        // the (a - L + rho + 1)-th miss of its set
+                        const uint4 mf = head ? meta[set] : make_uint4(0, 0, 0, 0);
+                        const uint32_t rho = mod_ways(w0 - 1u + ways - mf.x, ways);
+                        nohit = (uint32_t)__popc(sm0 & lt) >= ways - mf.y + rho + 1u;
+                    }
+                }
+                // held groups hit and change nothing; the others all miss
+                const uint32_t hbal = __ballot_sync(kFull, head && w0 != 0u);
+                const uint32_t nbal = __ballot_sync(kFull, head && nohit);
+                const bool gheld = head && (hbal & sm0) == sm0;
+                if (__all_sync(kFull, !head || gheld || (nbal & sm0) == sm0))
+                    return fresh_step(line, set, head && !gheld, lane, lt, sm0);
+                pure_skip = 7;
             }
-            // held groups hit and change nothing; the others all miss
-            const uint32_t hbal = __ballot_sync(kFull, head && w0 != 0u);
-            const uint32_t nbal = __ballot_sync(kFull, head && nohit);
-            const bool gheld = head && (hbal & sm0) == sm0;
-            if (__all_sync(kFull, !head || gheld || (nbal & sm0) == sm0))
-                return fresh_step(line, set, head && !gheld, lane, lt, sm0);
-            pure_skip = 7;
         }
         {
             // one set with few lines not held: miss by miss
@@ -1359,19 +1396,23 @@ __device__ __forceinline__ void run_steps(const SimItem &it, uint32_t arena, uin
     if (it.direct == 2 && out.parts) {
         // ---- a part of an item split by sets: its heads come gathered, in
         // trace order, from its head stream; a step takes the next 32 of them
-        // (the grouping a queued unit's steps have), two steps' entries in flight
+        // (the grouping a queued unit's steps have), four steps' entries in flight
         const PartInfo pi = out.parts[out.item_slot[it.out_item] + it.kres];
         const uint2 *const es = out.ents + pi.start;
         const uint32_t n = pi.len;
         const uint2 none = make_uint2(kInvalidLine, 0u);
-        uint2 e1 = (uint32_t)lane < n ? es[lane] : none;
-        uint2 e2 = (uint32_t)lane + 32u < n ? es[lane + 32] : none;
+        uint2 ef[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            ef[q] = (uint32_t)lane + 32u * q < n ? es[lane + 32 * q] : none;
         uint32_t ccarry = kInvalidLine, step = 0;
         for (uint32_t b = 0; b < n; b += 32) {
-            const uint2 e = e1;
-            e1 = e2;
-            const uint32_t nx = b + 64u + (uint32_t)lane;
-            e2 = nx < n ? es[nx] : none;
+            const uint2 e = ef[0];
+            ef[0] = ef[1];
+            ef[1] = ef[2];
+            ef[2] = ef[3];
+            const uint32_t nx = b + 128u + (uint32_t)lane;
+            ef[3] = nx < n ? es[nx] : none;
             const bool act = b + (uint32_t)lane < n;
             const uint32_t line = e.x, pos = e.y;
             const uint32_t set = set_of(line * lstep);
@@ -1423,8 +1464,13 @@ __device__ __forceinline__ void run_steps(const SimItem &it, uint32_t arena, uin
             if (!idxp && N)
                 aj = (uint32_t)((((uint64_t)(sfirst << 5) + (uint32_t)lane) * it.stride) % N);
         }
+        // the trace is read four steps ahead (a step is about one memory
+        // latency, so a unit's chain of steps would otherwise wait on each load)
         const uint32_t t1 = (sfirst << 5) + (uint32_t)lane;
-        uint32_t pf = (idxp && t1 < len) ? idxp[t1] : 0u;
+        uint32_t pf[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            pf[q] = (idxp && t1 + 32u * q < len) ? idxp[t1 + 32u * q] : 0u;
         // matcher: the observed word of the step, loaded one step ahead
         uint32_t pw = (ham && len) ? observed[obase + sfirst] : 0u;
         for (uint32_t s0 = sfirst; s0 < send; ++s0) {
@@ -1432,9 +1478,12 @@ __device__ __forceinline__ void run_steps(const SimItem &it, uint32_t arena, uin
             bool active = t < len;
             uint32_t j;
             if (idxp) {
-                j = pf;
-                const uint32_t tn = t + 32;
-                pf = tn < len ? idxp[tn] : 0u;
+                j = pf[0];
+                pf[0] = pf[1];
+                pf[1] = pf[2];
+                pf[2] = pf[3];
+                const uint32_t tn = t + 128;
+                pf[3] = tn < len ? idxp[tn] : 0u;
             } else {
                 j = aj;
                 aj = (aj >= N - ainc) ? aj - (N - ainc) : aj + ainc;
