@@ -166,11 +166,11 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-# From one ncu capture (--set full) of the current sim_kernel on the batched
-# workload with items capped at 65,536 accesses: the slot-mix launch and the
-# one-warp launch of one run, summed.
-SIM_DRAM_BYTES_PER_ACCESS = (279.363584e6 + 8.221440e6 + 2.172160e6) / 65559830
-SIM_WARP_INST_PER_ACCESS = (351888331 + 3918992) / 65559830
+# From one ncu capture (three single-pass counters) of the current sim_kernel
+# on the full batched workload, 644,096,746 accesses: the slot-mix launch and
+# the one-warp launch of one run, summed.
+SIM_DRAM_BYTES_PER_ACCESS = (2790.483456e6 + 62.115584e6 + 24.692736e6) / 644096746
+SIM_WARP_INST_PER_ACCESS = (3408117654 + 47543930) / 644096746
 # Algorithmic work of one simulated access in the warp-per-set mapping: the
 # decode (line, set and tag by shift and multiply-high), one warp-wide tag
 # compare (ballot / match), the replacement-state update and the miss bit,
