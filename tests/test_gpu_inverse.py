@@ -156,7 +156,7 @@ def test_rate_table_matches_oracle():
 BF16_TERM_TOL = 2.0 ** -7
 
 
-@pytest.mark.parametrize("B,step", [(16, 0), (40, 0), (64, 3), (128, 1)])
+@pytest.mark.parametrize("B,step", [(16, 0), (37, 2), (40, 0), (64, 3), (128, 1)])
 def test_train_step_matches_oracle_element_by_element(B, step):
     """One pchase_inverse_train_step against the oracle's training step
     (chain-rule backward of every layer, softmax cross-entropy, Adam) on the
@@ -164,8 +164,11 @@ def test_train_step_matches_oracle_element_by_element(B, step):
     rounds: every gradient element within 2^-7 of the sum of its terms'
     magnitudes; the loss within 2^-12; the new moments and weights equal to
     Adam applied to the device's own gradient up to FP32 rounding.  Batches
-    of 16-128 traces (40 is ragged against every tile), first and later Adam
-    steps with non-zero moments."""
+    of 16-128 traces (none a multiple of the 128-row tiles of the dense
+    layers), first and later Adam steps with non-zero moments.  37 traces
+    leave partial tiles in the convolutions (the last 128-row tile of layers
+    3 and 4 holds 1 of its 2 and 1 of its 4 traces) and a batch that is not a
+    multiple of 8 for the batch-contiguous weight-gradient operands."""
     net = INV.LearnedInverse(max_batch=128)
     net.init(seed=31 + B)
     rng = np.random.Generator(np.random.PCG64(B))
