@@ -18,9 +18,10 @@
 // The three 64-channel layers run conv_back_tc_kernel on the tcgen05 tensor
 // cores.  A tile is 128 consecutive rows (b, lo), i.e. whole traces (lout is
 // 128, 64 or 32), so no sum ever crosses a tile edge.  Per tile:
-//   * dz from dact and pre (coalesced FP32 rows), its BF16 copy written three
-//     times into K-major 128-byte-swizzled operands S_j, S_j[q] = dz[q + 1 - j]
-//     (zero across a trace edge);
+//   * dz from dact and pre (coalesced FP32 rows, loaded a tile ahead into
+//     registers), its BF16 copy written three times into K-major
+//     128-byte-swizzled operands S_j, S_j[q] = dz[q + 1 - j] (zero across a
+//     trace edge);
 //   * dx as two 128 x 64 sums in one N=128 accumulator: even positions
 //     dx[2q] = S_0 W_0 + S_1 W_2 + S_2 W_4, odd dx[2q + 1] = S_0 W_1 + S_1 W_3,
 //     with W_kk[co][ci] = W[co][kk*64 + ci] staged once per CTA as B operands
@@ -28,7 +29,8 @@
 //   * gW transposed, D[(kk, ci)][co] (320 rows in three M=128 tiles, N=64),
 //     accumulated in TMEM over all of the CTA's tiles with K = the tile's 128
 //     rows: both operands need the rows contiguous, so the layer's input
-//     window (32 KB, staged with cp.async) and dz are transposed in shared
+//     window (32 KB: the even and the odd positions of the tile's traces as
+//     two TMA boxes, loaded a tile ahead) and dz are transposed in shared
 //     memory by ldmatrix.trans (the stride-2 gather of the input rows is in
 //     the ldmatrix row addresses) and stored K-major with the 128-byte swizzle.
 // The third gW tile reads 64 rows past the 320 it needs (whatever lies beyond
@@ -38,9 +40,13 @@
 // The first layer (one input channel, K = 5) has no tensor-core shape and
 // needs no dx: conv0_back_kernel does dz, gb and gW on CUDA cores.
 //
-// Completion waits on the mbarrier give up after 2 s of %globaltimer: the
-// CTA then ORs PCHASE_DEV_TIMEOUT into *status, waits (again with a limit) for
-// the MMAs it issued, frees its TMEM and returns.
+// The forward of the 64-channel layers (conv_fwd_tc_kernel, with the
+// pre-activations kept) and the FC and heads layers, forward and backward
+// (tc_gemm_kernel), are further below.
+//
+// Completion waits on an mbarrier give up after 2 s of %globaltimer: the CTA
+// then ORs PCHASE_DEV_TIMEOUT into *status, waits (again with a limit) for the
+// MMAs and TMA loads it issued, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
