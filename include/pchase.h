@@ -615,7 +615,13 @@ int pchase_inverse_synth(const float *rates, const uint32_t *targets, uint32_t n
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8; `step` counts from 0)
  * on the mean cross-entropy of the four heads over a batch of B <= max_batch
  * traces (device x, B x 512 FP32; labels B x 4).  The batch's mean loss is
- * added to *loss_accum (device float). */
+ * added to *loss_accum (device float).  The gradient (parameter array 2) is
+ * the chain rule through the network with BF16 operands and FP32 sums; the
+ * forward pass, the backward pass and the weight gradients run on the
+ * tcgen05 tensor cores (the one-channel first layer on CUDA cores).  Host
+ * errors return a status; a tensor-core wait that gives up sets
+ * PCHASE_DEV_TIMEOUT in the device status word (pchase_inverse_status_offset)
+ * and leaves the parameters undefined. */
 int pchase_inverse_train_step(const pchase_inverse *h, void *params, void *work, const float *x,
                               const uint32_t *labels, uint32_t B, float lr, uint32_t step,
                               float *loss_accum, pchase_stream_t stream);
