@@ -1247,7 +1247,6 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
     std::vector<double> work(ncap, 0.0);
     std::vector<double> gwork[kUnitGroups];
     for (auto &v : gwork) v.assign(ncap, 0.0);
-    int top = -1;
     uint32_t nclass = 0;
     {
         // classes present, in increasing cap order, renumbered 0..nclass-1
@@ -1280,7 +1279,6 @@ int pchase_sim_plan_create(const pchase_geom *geoms, uint32_t n_geom, const pcha
             }
         }
         L.nclasses = nclass;
-        top = (int)nclass - 1;
         // Slot mix.  Classes whose arena exceeds half the CTA budget ("jumbo")
         // get a launch of their own, one warp per CTA.  For the others, slots
         // are added one at a time to minimise the estimated makespan
