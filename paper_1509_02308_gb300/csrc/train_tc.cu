@@ -57,6 +57,39 @@
 #include "tc_common.cuh"
 
 namespace pchase {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// A [rows][K] BF16 matrix, row stride ld elements (a multiple of 8), as a 2-D
+// tensor (K, rows) read in boxes of 64 columns x box_rows rows with the
+// 128-byte swizzle: the K-major operand tile the MMA reads
+static bool kmajor_map(const __nv_bfloat16 *p, int rows, int K, int ld, int box_rows,
+                       CUtensorMap *map) {
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(p), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 namespace {
 
 constexpr int kCh = 64;
@@ -675,13 +708,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 // C = A B^T over K for the training step's dense layers: A [M][K] and B [N][K]
 // BF16, both K-major (row strides lda, ldb elements, multiples of 8, 16-byte
 // aligned bases), FP32 sums in TMEM.  A CTA takes a 128 x BN tile and a slice
-// of the K blocks (gridDim.z slices of 64-element blocks); blocks stream
-// through a 4-buffer cp.async ring loaded two ahead, an mbarrier per buffer
-// freeing it once its MMAs are done (rows past M or N and columns past K are
-// zero-filled).  Epilogues: kStore (C[m][n], or C[n][m] when transposed,
+// of the K blocks (gridDim.z slices of 64-element blocks).  One thread runs
+// the main loop: both operands' 64-column blocks are TMA tile loads (2-D
+// tensor maps, 128-byte swizzle; rows past M or N and columns past K are out
+// of the tensor and read as zeros) into a 4-stage ring, three blocks ahead;
+// a stage's mbarrier counts its bytes in, and a second one (tcgen05.commit)
+// frees it once its MMAs are done.  Epilogues: kStore (C[m][n], or C[n][m] when transposed,
 // + bias[n] if given; FP32 atomics when K is sliced) and kGelu (v = sum +
 // bias[n]: pre[m][n] = v, Cb[m][n] = BF16(GELU(v)) with the exact tanh).
-constexpr int kGemmStages = 4, kGemmAhead = 2;
+constexpr int kGemmStages = 4;
 enum GemmEpi { kStore = 0, kGelu = 1 };
 
 struct TcGemm {
@@ -700,54 +735,55 @@ template <int BN>
 struct GemmShape {
     static constexpr uint32_t kABytes = 128 * 128, kBBytes = BN * 128;
     static constexpr uint32_t kStageBytes = kABytes + kBBytes;
-    static constexpr uint32_t kSmem = 1024 + kGemmStages * kStageBytes + 8 * kGemmStages + 16;
+    static constexpr uint32_t kSmem = 1024 + kGemmStages * kStageBytes + 16 * kGemmStages + 16;
     static constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
     static_assert(4 * 32 * (BN + 1) * 4 <= kGemmStages * kStageBytes, "epilogue staging");
     static constexpr uint32_t kIdesc = idesc_n(BN);
 };
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(128) tc_gemm_kernel(const TcGemm g) {
+__global__ void __launch_bounds__(128)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+                   const TcGemm g) {
     using S = GemmShape<BN>;
     extern __shared__ uint8_t dsm[];
     const uint32_t raw = smem_u32(dsm);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *const gbase = dsm + (base - raw);
+    // mbarriers: stage loaded [S] at sBar + 8s, stage's MMAs done [S] at sBar + 8 (S + s)
     const uint32_t sBar = base + kGemmStages * S::kStageBytes;
     uint32_t *const tslot =
-        reinterpret_cast<uint32_t *>(gbase + kGemmStages * S::kStageBytes + 8 * kGemmStages);
+        reinterpret_cast<uint32_t *>(gbase + kGemmStages * S::kStageBytes + 16 * kGemmStages);
+    volatile uint32_t *const abort_flag = tslot + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
     const int nkb = (g.K + 63) / 64;
     const int kb0 = blockIdx.z * g.blocks_per_slice;
     const int nblk = max(0, min(nkb, kb0 + g.blocks_per_slice) - kb0);
+    const uint32_t full0 = sBar, done0 = sBar + 8u * kGemmStages;
 
+    // block j's A and B tiles into stage j mod S (one thread)
     auto load = [&](int j) {
-        if (j < nblk) {
-            const uint32_t st = base + (uint32_t)(j % kGemmStages) * S::kStageBytes;
-            const int k0 = (kb0 + j) * 64;
-            for (int e = tid; e < (128 + BN) * 8; e += 128) {
-                const int r = e >> 3, c = e & 7;
-                const int k = k0 + c * 8;
-                if (r < 128) {
-                    const int m = m0 + r;
-                    const bool ok = m < g.M && k < g.K;
-                    cp_async16(st + sw_chunk((uint32_t)r, (uint32_t)c),
-                               ok ? g.A + (size_t)m * g.lda + k : g.A, ok);
-                } else {
-                    const int rn = r - 128, n = n0 + rn;
-                    const bool ok = n < g.N && k < g.K;
-                    cp_async16(st + S::kABytes + sw_chunk((uint32_t)rn, (uint32_t)c),
-                               ok ? g.B + (size_t)n * g.ldb + k : g.B, ok);
-                }
-            }
-        }
-        cp_async_commit();
+        const uint32_t q = (uint32_t)(j % kGemmStages);
+        const uint32_t st = base + q * S::kStageBytes;
+        const int k0 = (kb0 + j) * 64;
+        mbar_expect_tx(full0 + 8u * q, S::kStageBytes);
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(st),
+            "l"(reinterpret_cast<uint64_t>(&amap)), "r"(k0), "r"(m0), "r"(full0 + 8u * q)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(st + S::kABytes),
+            "l"(reinterpret_cast<uint64_t>(&bmap)), "r"(k0), "r"(n0), "r"(full0 + 8u * q)
+            : "memory");
     };
     if (tid == 0) {
-        for (int q = 0; q < kGemmStages; ++q)
+        for (int q = 0; q < 2 * kGemmStages; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8 * q) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -756,44 +792,47 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcGemm g) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int j = 0; j < kGemmAhead; ++j) load(j);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    bool ok = true;
-    for (int j = 0; j < nblk; ++j) {
-        // block j + ahead refills the buffer of block j + ahead - stages
-        const int pb = j + kGemmAhead - kGemmStages;
-        if (pb >= 0) {
-            const bool got = mbar_wait(sBar + 8 * (pb % kGemmStages), (uint32_t)(pb / kGemmStages) & 1u);
-            if (!__syncthreads_and(got)) {
-                ok = false;
+    int loaded = 0;  // blocks whose loads went out (thread 0)
+    if (tid == 0) {
+        for (; loaded < min(nblk, kGemmStages - 1); ++loaded) load(loaded);
+        for (int j = 0; j < nblk; ++j) {
+            const uint32_t q = (uint32_t)(j % kGemmStages);
+            if (!mbar_wait(full0 + 8u * q, (uint32_t)(j / kGemmStages) & 1u)) {
+                *abort_flag = 1;
                 break;
             }
-        }
-        load(j + kGemmAhead);
-        asm volatile("cp.async.wait_group %0;" ::"n"(kGemmAhead) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-            const uint32_t st = base + (uint32_t)(j % kGemmStages) * S::kStageBytes;
+            tc_fence_after();
+            const uint32_t st = base + q * S::kStageBytes;
 #pragma unroll
             for (int s = 0; s < 4; ++s)
                 mma_bf16_id(tmem, sw128_desc(st + 32u * s), sw128_desc(st + S::kABytes + 32u * s),
                             S::kIdesc, (j | s) != 0 ? 1u : 0u);
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    sBar + 8u * (uint32_t)(j % kGemmStages))
+                    done0 + 8u * q)
                 : "memory");
+            // the stage of block j - 1 (its MMAs went out a step ago) takes block j + S - 1
+            if (loaded < nblk) {
+                const int pj = loaded - kGemmStages;  // the last block that used the stage
+                if (pj >= 0 && !mbar_wait(done0 + 8u * (uint32_t)(pj % kGemmStages),
+                                          (uint32_t)(pj / kGemmStages) & 1u)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                load(loaded++);
+            }
         }
     }
+    __syncthreads();
+    bool ok = *abort_flag == 0;
     if (ok && nblk > 0) {
         const int lb = nblk - 1;  // the last commit covers every earlier MMA
-        const bool got = mbar_wait(sBar + 8 * (lb % kGemmStages), (uint32_t)(lb / kGemmStages) & 1u);
+        const bool got = mbar_wait(done0 + 8u * (uint32_t)(lb % kGemmStages), (uint32_t)(lb / kGemmStages) & 1u);
         ok = __syncthreads_and(got);
         if (ok && g.transposed) {
             // C[n][m]: lanes hold consecutive m, so each store is coalesced
@@ -854,8 +893,15 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const TcGemm g) {
             }
         }
     }
-    if (!ok && tid == 0) atomicOr(g.status, PCHASE_DEV_TIMEOUT);
-    cp_async_wait_all();
+    if (!ok && tid == 0) {
+        atomicOr(g.status, PCHASE_DEV_TIMEOUT);
+        // the loads and MMAs issued land before TMEM is freed and the CTA leaves
+        for (int j = max(0, loaded - kGemmStages); j < loaded; ++j)
+            mbar_wait(full0 + 8u * (uint32_t)(j % kGemmStages), (uint32_t)(j / kGemmStages) & 1u);
+        if (loaded > 0)
+            mbar_wait(done0 + 8u * (uint32_t)((loaded - 1) % kGemmStages),
+                      (uint32_t)((loaded - 1) / kGemmStages) & 1u);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -894,27 +940,15 @@ cudaError_t launch_tc_gemm(const TcGemm &g, int slices, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    alignas(64) CUtensorMap amap, bmap;
+    if (!kmajor_map(g.A, g.M, g.K, g.lda, 128, &amap) || !kmajor_map(g.B, g.N, g.K, g.ldb, BN, &bmap))
+        return cudaErrorInvalidValue;
     dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, slices);
-    tc_gemm_kernel<BN, EPI><<<grid, 128, S::kSmem, st>>>(g);
+    tc_gemm_kernel<BN, EPI><<<grid, 128, S::kSmem, st>>>(amap, bmap, g);
     return cudaGetLastError();
 }
 
 }  // namespace
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library)
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
 
 // x [nb][2 lout][64] BF16 as the 4-D tensor (channel, parity, pair, trace)
 // with boxes of 64 channels x 1 parity x lout pairs x (128 / lout) traces,
