@@ -29,6 +29,7 @@
 
 #include "conv_tc.cuh"
 #include "tc_common.cuh"
+#include "tma_host.cuh"
 
 namespace pchase {
 namespace {
@@ -336,23 +337,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
 // act [B][2048] BF16, W4 [256][2048] BF16, W5 [31][256] BF16.  CTA t takes
 // rows 128t .. 128t+127 and all 256 hidden units, so each activation row is
 // read once:
-//   * FC on the tensor cores: M128 N256, K = 2048 in 32 blocks of 64 through a
-//     4-buffer cp.async ring loaded 2 blocks ahead; an mbarrier per buffer
-//     frees it once that block's MMAs are done;
+//   * FC on the tensor cores: M128 N256, K = 2048 in 32 blocks of 64; a block
+//     is two TMA tile loads (the activation tile and W4's, 2-D tensor maps with
+//     the 128-byte swizzle; rows past the batch read as zeros) into a 4-stage
+//     ring three blocks ahead, one thread issuing loads and MMAs; a stage's
+//     mbarrier counts its bytes in, a second one frees it once its MMAs are done;
 //   * epilogue: bias, GELU, BF16 rounding of the 128 x 256 hidden tile into
 //     four swizzled 64-column K blocks in shared memory (the ring's space),
 //     then the heads as a second MMA (M128 N32 K256, W5 padded to 32 rows)
 //     into 32 more TMEM columns, read back and stored with bias5 (no atomics:
 //     each CTA owns its rows).
 constexpr int kFcK = 2048, kFcN = 256, kHeads = 31, kHeadsPad = 32;
-constexpr int kFcStages = 4;   // ring buffers
-constexpr int kFcAhead = 2;    // blocks loaded ahead; a buffer is refilled once the
-                               // MMAs of the block kFcStages back are done (2 blocks of slack)
+constexpr int kFcStages = 4;   // ring stages, loaded kFcStages - 1 blocks ahead
 constexpr uint32_t kFcABytes = kTileRows * 128, kFcBBytes = kFcN * 128;
 constexpr uint32_t kFcStageBytes = kFcABytes + kFcBBytes;  // 48 KB
 constexpr uint32_t kW5Bytes = 4 * kHeadsPad * 128;         // 4 K blocks of 32 rows x 64 BF16
 constexpr uint32_t kFcSmemBytes =
-    1024 + kFcStages * kFcStageBytes + kW5Bytes + 8 * (kFcStages + 1) + 16;
+    1024 + kFcStages * kFcStageBytes + kW5Bytes + 8 * (2 * kFcStages + 1) + 16;
 constexpr uint32_t kFcTmemCols = 512;  // 256 FC + 32 heads, rounded to a power of two
 constexpr uint32_t kIdescFc = (1u << 4) | (1u << 7) | (1u << 10) |
                               ((uint32_t)(kFcN >> 3) << 17) | ((uint32_t)(kTileRows >> 4) << 24);
@@ -361,8 +362,8 @@ constexpr uint32_t kIdescHeads = (1u << 4) | (1u << 7) | (1u << 10) |
                                  ((uint32_t)(kTileRows >> 4) << 24);
 
 __global__ void __launch_bounds__(128, 1)
-    fc_heads_tc_kernel(const __nv_bfloat16 *__restrict__ act, int nb,
-                       const __nv_bfloat16 *__restrict__ W4, const float *__restrict__ bias4,
+    fc_heads_tc_kernel(const __grid_constant__ CUtensorMap amap,
+                       const __grid_constant__ CUtensorMap wmap, int nb, const float *__restrict__ bias4,
                        const __nv_bfloat16 *__restrict__ W5, const float *__restrict__ bias5,
                        float *__restrict__ logits, uint32_t *__restrict__ status) {
     extern __shared__ uint8_t dsm[];
@@ -371,9 +372,13 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t *const gbase = dsm + (base - raw);
     const uint32_t sStage = base;
     const uint32_t sW5 = base + kFcStages * kFcStageBytes;  // 1024-aligned
-    const uint32_t sBar = sW5 + kW5Bytes;  // kFcStages ring mbarriers + 1 for the heads
+    // mbarriers: stage loaded [S] at sBar + 8s, stage's MMAs done [S] at
+    // sBar + 8 (S + s), the heads MMAs at sBar + 16 S
+    const uint32_t sBar = sW5 + kW5Bytes;
+    const uint32_t full0 = sBar, done0 = sBar + 8u * kFcStages, hbar = sBar + 16u * kFcStages;
     uint32_t *const tslot = reinterpret_cast<uint32_t *>(
-        gbase + kFcStages * kFcStageBytes + kW5Bytes + 8 * (kFcStages + 1));
+        gbase + kFcStages * kFcStageBytes + kW5Bytes + 8 * (2 * kFcStages + 1));
+    volatile uint32_t *const abort_flag = tslot + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kTileRows;
     constexpr int kBlocks = kFcK / 64;
@@ -386,31 +391,20 @@ __global__ void __launch_bounds__(128, 1)
         cp_async16(sW5 + kb * (kHeadsPad * 128) + h * 128 + ((c ^ (h & 7)) << 4),
                    ok ? W5 + (size_t)h * kFcN + kb * 64 + c * 8 : W5, ok);
     }
+    // block kb's activation and W4 tiles into stage kb mod S (one thread)
     auto load = [&](int kb) {
-        if (kb < kBlocks) {
-            const uint32_t st = sStage + (kb % kFcStages) * kFcStageBytes;
-            const int k0 = kb * 64;
-            // A: 128 rows x 8 chunks; B: 256 rows x 8 chunks; 128-byte swizzle
-            for (int e = tid; e < (kTileRows + kFcN) * 8; e += 128) {
-                const int r = e >> 3, c = e & 7;
-                if (r < kTileRows) {
-                    const int m = m0 + r;
-                    const bool ok = m < nb;
-                    cp_async16(st + r * 128 + ((c ^ (r & 7)) << 4),
-                               ok ? act + (size_t)m * kFcK + k0 + c * 8 : act, ok);
-                } else {
-                    const int rn = r - kTileRows;
-                    cp_async16(st + kFcABytes + rn * 128 + ((c ^ (rn & 7)) << 4),
-                               W4 + (size_t)rn * kFcK + k0 + c * 8, true);
-                }
-            }
-        }
-        cp_async_commit();
+        const uint32_t q = (uint32_t)(kb % kFcStages);
+        const uint32_t st = sStage + q * kFcStageBytes;
+        mbar_expect_tx(full0 + 8u * q, kFcStageBytes);
+        tma_load_2d(st, &amap, kb * 64, m0, full0 + 8u * q);
+        tma_load_2d(st + kFcABytes, &wmap, kb * 64, 0, full0 + 8u * q);
     };
+    cp_async_commit();
     if (tid == 0) {
-        for (int q = 0; q <= kFcStages; ++q)
+        for (int q = 0; q <= 2 * kFcStages; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sBar + 8 * q) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -419,44 +413,49 @@ __global__ void __launch_bounds__(128, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int kb = 0; kb < kFcAhead; ++kb) load(kb);  // W5 rides in the first group
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;  // columns 0..255: FC; 256..287: heads
 
-    bool ok = true;
-    for (int kb = 0; kb < kBlocks; ++kb) {
-        // block kb + kFcAhead refills the buffer of block kb + kFcAhead - kFcStages
-        const int pb = kb + kFcAhead - kFcStages;
-        if (pb >= 0) {
-            const bool got = mbar_wait(sBar + 8 * (pb % kFcStages), (uint32_t)(pb / kFcStages) & 1u);
-            if (!__syncthreads_and(got)) {
-                ok = false;
+    int loaded = 0;  // blocks whose loads went out (thread 0)
+    if (tid == 0) {
+        for (; loaded < kFcStages - 1; ++loaded) load(loaded);
+        for (int kb = 0; kb < kBlocks; ++kb) {
+            const uint32_t q = (uint32_t)(kb % kFcStages);
+            if (!mbar_wait(full0 + 8u * q, (uint32_t)(kb / kFcStages) & 1u)) {
+                *abort_flag = 1;
                 break;
             }
-        }
-        load(kb + kFcAhead);
-        asm volatile("cp.async.wait_group %0;" ::"n"(kFcAhead) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-            const uint32_t st = sStage + (kb % kFcStages) * kFcStageBytes;
+            tc_fence_after();
+            const uint32_t st = sStage + q * kFcStageBytes;
 #pragma unroll
             for (int s = 0; s < 4; ++s)
                 mma_bf16_id(tmem, sw128_desc(st + 32u * s), sw128_desc(st + kFcABytes + 32u * s),
                             kIdescFc, (kb | s) != 0 ? 1u : 0u);
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    sBar + 8u * (uint32_t)(kb % kFcStages))
+                    done0 + 8u * q)
                 : "memory");
+            // the stage of block kb - 1 (its MMAs went out a step ago) takes block kb + S - 1
+            if (loaded < kBlocks) {
+                const int pj = loaded - kFcStages;
+                if (pj >= 0 && !mbar_wait(done0 + 8u * (uint32_t)(pj % kFcStages),
+                                          (uint32_t)(pj / kFcStages) & 1u)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                load(loaded++);
+            }
         }
     }
+    cp_async_wait_all();  // W5
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    bool ok = *abort_flag == 0;
     if (ok) {
         const int lb = kBlocks - 1;  // the last commit covers every earlier MMA
-        const bool got = mbar_wait(sBar + 8 * (lb % kFcStages), (uint32_t)(lb / kFcStages) & 1u);
+        const bool got = mbar_wait(done0 + 8u * (uint32_t)(lb % kFcStages), (uint32_t)(lb / kFcStages) & 1u);
         ok = __syncthreads_and(got);
     }
     const int r = warp * 32 + lane;  // TMEM lane = tile row
@@ -497,10 +496,10 @@ __global__ void __launch_bounds__(128, 1)
                                 (kb | s) != 0 ? 1u : 0u);
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    sBar + 8u * kFcStages)
+                    hbar)
                 : "memory");
         }
-        const bool got = mbar_wait(sBar + 8 * kFcStages, 0u);
+        const bool got = mbar_wait(hbar, 0u);
         ok = __syncthreads_and(got);
         if (ok) {
             tc_fence_after();
@@ -516,8 +515,15 @@ __global__ void __launch_bounds__(128, 1)
             }
         }
     }
-    if (!ok && tid == 0) atomicOr(status, PCHASE_DEV_TIMEOUT);
-    cp_async_wait_all();
+    if (!ok && tid == 0) {
+        atomicOr(status, PCHASE_DEV_TIMEOUT);
+        // the loads and MMAs issued land before TMEM is freed and the CTA leaves
+        for (int j = loaded > kFcStages ? loaded - kFcStages : 0; j < loaded; ++j)
+            mbar_wait(full0 + 8u * (uint32_t)(j % kFcStages), (uint32_t)(j / kFcStages) & 1u);
+        if (loaded > 0)
+            mbar_wait(done0 + 8u * (uint32_t)((loaded - 1) % kFcStages),
+                      (uint32_t)((loaded - 1) / kFcStages) & 1u);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -793,8 +799,14 @@ cudaError_t fc_heads_tc(const __nv_bfloat16 *act, int nb, const __nv_bfloat16 *W
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kFcSmemBytes);
     if (e != cudaSuccess) return e;
+    if ((reinterpret_cast<uintptr_t>(act) & 15) || (reinterpret_cast<uintptr_t>(W4) & 15))
+        return cudaErrorInvalidValue;
+    alignas(64) CUtensorMap amap, wmap;
+    if (!kmajor_map(act, nb, kFcK, kFcK, kTileRows, &amap) ||
+        !kmajor_map(W4, kFcN, kFcK, kFcK, kFcN, &wmap))
+        return cudaErrorInvalidValue;
     const int grid = (nb + kTileRows - 1) / kTileRows;
-    fc_heads_tc_kernel<<<grid, 128, kFcSmemBytes, st>>>(act, nb, W4, bias4, W5, bias5, logits,
+    fc_heads_tc_kernel<<<grid, 128, kFcSmemBytes, st>>>(amap, wmap, nb, bias4, W5, bias5, logits,
                                                         status);
     return cudaGetLastError();
 }

@@ -55,40 +55,9 @@
 
 #include "conv_tc.cuh"
 #include "tc_common.cuh"
+#include "tma_host.cuh"
 
 namespace pchase {
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library)
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-// A [rows][K] BF16 matrix, row stride ld elements (a multiple of 8), as a 2-D
-// tensor (K, rows) read in boxes of 64 columns x box_rows rows with the
-// 128-byte swizzle: the K-major operand tile the MMA reads
-static bool kmajor_map(const __nv_bfloat16 *p, int rows, int K, int ld, int box_rows,
-                       CUtensorMap *map) {
-    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-    if (!encode) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(p), dims,
-                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
 
 namespace {
 
@@ -148,18 +117,6 @@ __device__ __forceinline__ uint32_t sw_chunk(uint32_t r, uint32_t c) {
     return r * 128u + ((c ^ (r & 7u)) << 4);
 }
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
-                                            int c2, int c3, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
 
 template <int LOUT>
 __global__ void __launch_bounds__(kBackThreads, 1)
@@ -768,16 +725,8 @@ __global__ void __launch_bounds__(128)
         const uint32_t st = base + q * S::kStageBytes;
         const int k0 = (kb0 + j) * 64;
         mbar_expect_tx(full0 + 8u * q, S::kStageBytes);
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3}], [%4];" ::"r"(st),
-            "l"(reinterpret_cast<uint64_t>(&amap)), "r"(k0), "r"(m0), "r"(full0 + 8u * q)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3}], [%4];" ::"r"(st + S::kABytes),
-            "l"(reinterpret_cast<uint64_t>(&bmap)), "r"(k0), "r"(n0), "r"(full0 + 8u * q)
-            : "memory");
+        tma_load_2d(st, &amap, k0, m0, full0 + 8u * q);
+        tma_load_2d(st + S::kABytes, &bmap, k0, n0, full0 + 8u * q);
     };
     if (tid == 0) {
         for (int q = 0; q < 2 * kGemmStages; ++q)
