@@ -114,34 +114,6 @@ struct ScanSets {
     }
 };
 
-// ---------------------------------------------------------- direct-mapped
-// A cache with one way per set, under any policy (every victim is way 0):
-// the set holds the line of its last access, and a head misses exactly when
-// the line before it in its set differs: the line of the last earlier head
-// of its set in the step, else the set's line.  One pass per step, whatever
-// the heads per set.  Arena: uint32 line[T].
-struct DirectSets {
-    uint32_t *sl;
-    __device__ __forceinline__ void bind(uint8_t *arena, const SimItem &) {
-        sl = reinterpret_cast<uint32_t *>(arena);
-    }
-    __device__ __forceinline__ void clear(const SimItem &it, int lane) {
-        for (uint32_t i = lane; i < it.sets; i += 32) sl[i] = kInvalidLine;
-    }
-    __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t,
-                                            int lane, uint32_t lt, uint32_t) {
-        const uint32_t peers = __match_any_sync(kFull, head ? set : (0x80000000u | (uint32_t)lane));
-        const uint32_t below = peers & lt;
-        const uint32_t pl = __shfl_sync(kFull, line, below ? 31 - __clz(below) : lane);
-        const uint32_t before = below ? pl : (head ? sl[set] : 0u);
-        const bool last = head && (peers & ~(lt | (1u << lane))) == 0;
-        __syncwarp();
-        if (last) sl[set] = line;
-        __syncwarp();
-        return head && before != line;
-    }
-};
-
 // ---------------------------------------------------------- table sets
 // Arena: uint2 meta[T]; uint32 sline[T*a]; (LRU) uint16 prev[T*a], next[T*a];
 // uint16 table[table_n] (line -> way + 1, 0 = absent).
@@ -1266,19 +1238,7 @@ enum : uint32_t {
     kGlobalScanLru = 9 + PCHASE_LRU,
     kGlobalScanFifo = 9 + PCHASE_FIFO,
     kGlobalScanRandom = 9 + PCHASE_RANDOM,
-    // direct-mapped caches, any mode and policy (DirectSets), in shared or
-    // global memory
-    kDirect = 12,
 };
-
-// A unit of a direct-mapped cache runs DirectSets, except a time part of an
-// LRU item (it rebuilds the LRU state it starts from) and unequal sets.
-__device__ __forceinline__ bool direct_mapped(const SimItem &it) {
-    const bool uneq = (it.lsh >> 16) & 1u;
-    const bool tpart = it.kcnt == 1 && it.ks1 != 0 && it.mode == kModeBatch &&
-                       it.policy == PCHASE_LRU;
-    return it.ways == 1 && !uneq && !tpart;
-}
 
 // POOL: the kernel of the global-state pool, whose units all keep their set
 // state in global memory (way scans); the other kernel has no such unit, so
@@ -1297,9 +1257,7 @@ struct AnyResolver {
         sp = arena;
         it = &i;
         const uint32_t pol = i.policy < 2u ? i.policy : 2u;
-        kind = direct_mapped(i) ? (uint32_t)kDirect
-             : POOL             ? (uint32_t)kGlobalScanLru + pol
-                                : (uint32_t)i.mode * 3u + pol;
+        kind = POOL ? (uint32_t)kGlobalScanLru + pol : (uint32_t)i.mode * 3u + pol;
     }
     template <typename R>
     __device__ __forceinline__ bool run(uint32_t line, uint32_t set, bool head, uint32_t pos,
@@ -1310,7 +1268,6 @@ struct AnyResolver {
     }
     __device__ __forceinline__ bool resolve(uint32_t line, uint32_t set, bool head, uint32_t pos,
                                             int lane, uint32_t lt, uint32_t step) {
-        if (kind == kDirect) return run<DirectSets>(line, set, head, pos, lane, lt, step);
         if constexpr (POOL) {
             switch (kind) {
             case kGlobalScanLru:
@@ -1347,12 +1304,6 @@ struct AnyResolver {
 template <bool POOL>
 __device__ __forceinline__ void clear_state(uint32_t kind, uint8_t *st, uint8_t *gst,
                                             const SimItem &it, int lane) {
-    if (kind == kDirect) {
-        DirectSets S;
-        S.bind(POOL ? gst : st, it);
-        S.clear(it, lane);
-        return;
-    }
     if constexpr (POOL) {
         switch (kind) {
         case kGlobalScanLru: { ScanSets<PCHASE_LRU> S; S.bind(gst, it); S.clear(it, lane); return; }
@@ -1719,9 +1670,7 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
     // into the plan's state area, owned by this unit alone
     const bool gmem = POOL;  // the planner puts every global-state unit in the pool
     uint8_t *const gst = gmem ? out.gstate + 16ull * it.kres : nullptr;
-    const uint32_t kind = direct_mapped(it) ? (uint32_t)kDirect
-                        : gmem              ? (uint32_t)kGlobalScanLru + pol
-                                            : (uint32_t)it.mode * 3u + pol;
+    const uint32_t kind = gmem ? (uint32_t)kGlobalScanLru + pol : (uint32_t)it.mode * 3u + pol;
     // matcher: a candidate whose other units already exceed the bound is out
     if (out.dist && over_bound(out, it.cand, 0, lane)) return;
     clear_state<POOL>(kind, st, gst, it, lane);
@@ -1730,8 +1679,6 @@ __device__ __forceinline__ void run_unit(const SimItem &it, uint32_t arena, cons
         return run_steps<AnyResolver<POOL>>(it, arena, st, POOL ? gst : st, kind, out, lane);
     }
     // one dispatch per unit: every step then calls its resolver directly
-    if (kind == kDirect)
-        return run_steps<DirectSets>(it, arena, st, POOL ? gst : st, kind, out, lane);
     if constexpr (POOL) {
         switch (kind) {
         case kGlobalScanLru:
