@@ -31,6 +31,38 @@ def test_gelu_tanh_form_tracks_erf_form():
     assert R.gelu(np.array([0.0]))[0] == 0.0
 
 
+def test_gelu_sigmoid_form_equals_the_tanh_form():
+    """The training kernels compute GELU as x s with s = 1 / (1 + exp(-2u)) and
+    its derivative as s + 2 x s (1 - s) k0 (1 + 3 k1 x^2), (1 - s) = exp(-2u) s,
+    u = k0 (x + k1 x^3): the oracle's tanh form and its derivative, since
+    1 + tanh(u) = 2 / (1 + exp(-2u)) and 1 - tanh(u)^2 = 4 s (1 - s).  In float64
+    the two forms agree to rounding over both tails, and the derivative also
+    matches central differences of the oracle's GELU."""
+    k0, k1 = 0.7978845608028654, 0.044715
+    x = np.concatenate([np.linspace(-12, 12, 4801), [-40.0, -1e-6, 0.0, 1e-6, 40.0]])
+    u = k0 * (x + k1 * x ** 3)
+    e = np.exp(np.minimum(-2.0 * u, 700.0))
+    s = 1.0 / (1.0 + e)
+    gelu_sig = x * s
+    grad_sig = s + 2.0 * x * s * (e * s) * k0 * (1.0 + 3.0 * k1 * x * x)
+    ref, dref = R.gelu(x), R.gelu_grad(x)
+    assert np.max(np.abs(gelu_sig - ref) - 1e-14 * np.maximum(np.abs(x), 1.0)) <= 0.0
+    assert np.max(np.abs(grad_sig - dref)) < 1e-13
+    # in the negative tail 1 + tanh(u) cancels in the tanh form (float64 gives 0
+    # from about x = -7), while the sigmoid form keeps its relative accuracy:
+    # against 60-digit arithmetic it stays within a few ulp
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    for xv in (-3.0, -5.0, -7.5, -10.0, -20.0):
+        uu = k0 * (xv + k1 * xv ** 3)
+        want = float(mpmath.mpf(xv) / (1 + mpmath.exp(-2 * mpmath.mpf(uu))))
+        got = xv / (1.0 + np.exp(-2.0 * uu))
+        assert abs(got - want) <= 1e-14 * abs(want), (xv, got, want)
+    h = 1e-5
+    fd = (R.gelu(x + h) - R.gelu(x - h)) / (2 * h)
+    assert np.max(np.abs(grad_sig - fd)) < 1e-8
+
+
 def test_lsq_matches_numpy_lstsq():
     rng = np.random.Generator(np.random.PCG64(2))
     G, n = 6, 4
