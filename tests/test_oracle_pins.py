@@ -717,6 +717,51 @@ def test_lru_state_is_the_most_recent_lines_of_each_set():
     assert fifo_differs > 0
 
 
+def test_fifo_state_after_a_misses_per_set_is_the_most_recent_lines():
+    """Sec. 3's FIFO holds each set's a most recently inserted lines.  When
+    each set's last accesses before a cut (its last a, or all it had) were all
+    misses, every one of them was an insertion, so the set holds exactly its a
+    most recently used distinct lines, the state an LRU time part rebuilds: a
+    FIFO time part could start from that rebuild once the part before it has
+    seen those misses.  And a cyclic stream in which every reuse of a line
+    comes after at least a other accesses of its set misses on every access,
+    by induction from the cold start."""
+    rng = np.random.Generator(np.random.PCG64(404))
+    checked = 0
+    for _ in range(80):
+        b = int(rng.choice([4, 8, 32]))
+        a, T = int(rng.integers(1, 6)), int(rng.integers(1, 5))
+        n_lines = int(rng.integers(2 * a * T, 6 * a * T + 3))
+        L = int(rng.integers(20, 240))
+        tr = rng.integers(0, n_lines * b // 4, size=L).astype(np.uint32)
+        miss = oracle.cache_sim(a * T * b, b, a, T, oracle.FIFO, tr)
+        sets = ((4 * tr.astype(np.int64)) // b) % T
+        for c0 in sorted(set(int(x) for x in rng.integers(1, L, size=6))):
+            tails_missed = True
+            for st in range(T):
+                idx = np.nonzero(sets[:c0] == st)[0]
+                if not miss[idx[-a:]].all():
+                    tails_missed = False
+            if not tails_missed:
+                continue
+            want = _recent_lines(tr, b, T, a, c0)
+            _, fin = oracle.cache_sim(a * T * b, b, a, T, oracle.FIFO, tr[:c0], want_final=True)
+            got = [sorted(int(x) for x in row if x != 0xFFFFFFFF) for row in fin.reshape(T, a)]
+            assert got == [sorted(h) for h in want], (b, a, T, c0)
+            checked += 1
+    assert checked >= 20
+    # cyclic P-chase streams: N / s lines spread so that every set sees more
+    # than a distinct lines, each reused a period later
+    for (n, s, a, T, b) in ((3072 // 4, 256 // 4, 8, 2, 128), (131328 // 4, 16, 1536, 1, 64),
+                            (5632 // 4, 512 // 4, 2, 4, 256), (40000, 37, 4, 8, 32)):
+        tr = oracle.pchase_trace(n, s, 3 * n // np.gcd(n, s))
+        sets = ((4 * tr.astype(np.int64)) // b) % T
+        lines = (4 * tr.astype(np.int64)) // b
+        if any(len(np.unique(lines[sets == st])) <= a for st in np.unique(sets)):
+            continue
+        assert oracle.cache_sim(a * T * b, b, a, T, oracle.FIFO, tr).all(), (n, s, a, T, b)
+
+
 def test_unequal_l2_tlb_behind_a_thrashing_l1_tlb():
     """Sec. 4.4's path with the measured L2 TLB: past 16 pages the L1 TLB
     (16 entries, LRU) misses on every access of a 2 MB chain, so the
